@@ -1,0 +1,190 @@
+"""Pins of the oracle's full filter cycle (eq. filt + Sec. V) against the Kalman filter and invariants.
+
+For linear h and a Gaussian prior the exact filter is the continuous-discrete
+Kalman filter; with the exact-in-time multiplier and the trigonometric
+regrid the point-mass filter must reproduce its moments to round-off on a
+resolved grid, the Euler multiplier must approach it at first order in the
+sub-step, and the multilinear re-alignment at second order in the spacing.
+Nonlinear measurements (range, bearing) have no closed form: for them only
+self-convergence and invariants pin the oracle.
+"""
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle import filter as of
+from oracle import kalman, model, spectral
+from workloads import FilterConfig, MeasModel, simulate
+
+
+def _kalman_errors(sc, psi_mode, epochs=None):
+    cfg = sc.cfg
+    f = of.OracleFilter(cfg, psi_mode=psi_mode)
+    post, pred = kalman.run(cfg.m0, cfg.P0, cfg.A, cfg.Q, sc.meas.H, sc.meas.R, sc.z, sc.dt)
+    errs, realigns = [], 0
+    for k in range(epochs or sc.epochs):
+        f.meas_update(sc.meas, sc.z[k])
+        m, C = f.moments()
+        mk, Ck = post[k]
+        errs.append((np.abs(m - mk).max() / np.sqrt(np.trace(Ck)),
+                     np.abs(C - Ck).max() / np.abs(Ck).max()))
+        info = f.time_update(sc.dt)
+        realigns += info["realigned"]
+        m, C = f.moments()
+        mk, Ck = pred[k]
+        errs.append((np.abs(m - mk).max() / np.sqrt(np.trace(Ck)),
+                     np.abs(C - Ck).max() / np.abs(Ck).max()))
+    return np.array(errs), realigns
+
+
+def test_c1_exact_time_matches_kalman():
+    # +-6 sigma boxes truncate ~1e-8 of the Gaussian tail; +-8 sigma with 256 nodes
+    # (posterior resolved by ~3 nodes per sigma) puts every error below round-off.
+    sc = w.c1_scenario(N=256)
+    sc.cfg.span = 8.0
+    errs, _ = _kalman_errors(sc, "exact")
+    assert errs.max() < 1e-11, errs.max(axis=0)
+    sc = w.c1_scenario(N=128)
+    errs, _ = _kalman_errors(sc, "exact")
+    assert errs.max() < 3e-8, errs.max(axis=0)
+
+
+def test_c1_euler_first_order_vs_kalman():
+    e = []
+    for dt_sub in (0.01, 0.005):
+        sc = w.c1_scenario(N=128)
+        sc.cfg.dt_sub = dt_sub
+        errs, _ = _kalman_errors(sc, "euler")
+        e.append(errs.max())
+    assert 1.7 < e[0] / e[1] < 2.3, e
+
+
+def test_2d_linear_exact_time_matches_kalman():
+    # Resolved posterior (about 2 nodes per posterior sigma); the +-6 sigma box sets a ~1e-8 floor.
+    sc = w.small_2d_scenario(N=(128, 128), kind="linear", epochs=6)
+    errs, realigns = _kalman_errors(sc, "exact")
+    assert realigns == 0
+    assert errs.max() < 1e-7, errs.max(axis=0)
+
+
+def _cv_scenario(N):
+    cfg = FilterConfig(nx=2, N=N, A=np.array([[0.0, 1.0], [0.0, 0.0]]), Q=np.diag([0.01, 0.1]),
+                       m0=np.array([0.0, 1.0]), P0=np.diag([0.5, 0.5]))
+    meas = MeasModel("linear", R=np.array([[0.3 ** 2]]), H=np.array([[1.0, 0.0]]))
+    sc = w.Scenario("cv", cfg, meas, dt=0.2, epochs=12)
+    sc.truth, sc.z = simulate(cfg, meas, sc.dt, sc.epochs, seed=11)
+    return sc
+
+
+def test_realignment_converges_second_order():
+    """Constant-velocity model: the frame correlation exceeds the threshold and the
+    grid is re-aligned with multilinear interpolation (O(h^2))."""
+    e64, r64 = _kalman_errors(_cv_scenario((64, 64)), "exact")
+    e128, r128 = _kalman_errors(_cv_scenario((128, 128)), "exact")
+    assert r64 >= 3 and r128 >= 3
+    ratio = e64[6:].max() / e128[6:].max()
+    assert 3.0 < ratio < 6.0, ratio
+
+
+def test_c2_invariants_and_self_convergence():
+    """Range measurement (no closed form): unit mass, PSD covariance, and self-convergence:
+    moments on 64^2 and 128^2 grids approach those on 256^2, the finer one by >10x."""
+    res = {}
+    for N in ((64, 64), (128, 128), (256, 256)):
+        sc = w.c2_scenario(N=N, epochs=5)
+        f = of.OracleFilter(sc.cfg)
+        traj = []
+        for k in range(sc.epochs):
+            f.meas_update(sc.meas, sc.z[k])
+            assert abs(f.cell_volume * f.P.sum() - 1.0) < 1e-12
+            m, C = f.moments()
+            assert np.all(np.linalg.eigvalsh(C) > 0)
+            traj.append((m, C))
+            f.time_update(sc.dt)
+        res[N] = traj
+
+    def err(a, b):
+        return max(max(np.abs(m1 - m2).max() / np.sqrt(np.trace(C2)),
+                       np.abs(C1 - C2).max() / np.abs(C2).max())
+                   for (m1, C1), (m2, C2) in zip(res[a], res[b]))
+    e64, e128 = err((64, 64), (256, 256)), err((128, 128), (256, 256))
+    assert e128 < 5e-4 and e64 > 10 * e128, (e64, e128)
+
+
+def test_degenerate_measurement_leaves_state():
+    sc = w.c1_scenario()
+    f = of.OracleFilter(sc.cfg)
+    P0 = f.P.copy()
+    with pytest.raises(of.Degenerate):
+        f.meas_update(sc.meas, np.array([np.nan]))
+    assert np.array_equal(f.P, P0)
+
+
+def test_regrid_identity_map():
+    """A regrid whose target equals the current frame keeps the weights (exact)."""
+    N = 32
+    P = np.random.default_rng(2).uniform(size=(N, 24))
+    out = of._first_interp_axis(P, 0, np.arange(N, dtype=float), N)
+    np.testing.assert_allclose(out, P, atol=1e-13)
+
+
+# --- planted mistakes: each plausible error in the oracle must trip a pin ----------
+
+def _sheared_closed_form_error():
+    from tests.test_oracle_time_update import test_gaussian_fpe_exact_time_sheared_2d
+    try:
+        test_gaussian_fpe_exact_time_sheared_2d()
+    except AssertionError:
+        return True
+    return False
+
+
+def test_mutation_cross_term_sign(monkeypatch):
+    orig = of.OracleFilter.diffusion_multiplier
+
+    def bad(self, tau):
+        Q = self.Q
+        self.Q = Q * np.array([[1, -1], [-1, 1]]) if self.n == 2 else Q
+        try:
+            return orig(self, tau)
+        finally:
+            self.Q = Q
+    monkeypatch.setattr(of.OracleFilter, "diffusion_multiplier", bad)
+    assert _sheared_closed_form_error()
+
+
+def test_mutation_nyquist_in_cross_term(monkeypatch):
+    def bad_c1(N, L):
+        k = spectral.wavenumbers(N).astype(float)
+        return 2j * np.pi / L * k
+    monkeypatch.setattr(spectral, "c1_coeffs", bad_c1)
+    from tests.test_oracle_time_update import test_rough_data_sheared_frame_is_real
+    with pytest.raises(AssertionError):
+        test_rough_data_sheared_frame_is_real()
+
+
+def test_mutation_transposed_frame(monkeypatch):
+    def bad_points(c, M, N):
+        us = np.meshgrid(*[of.grid_u(n) for n in N], indexing="ij")
+        U = np.stack([u.ravel() for u in us], axis=1)
+        return c[None, :] + U @ M
+    monkeypatch.setattr(of, "frame_points", bad_points)
+    sc = w.small_2d_scenario(N=(48, 48), kind="linear", epochs=3)
+    sc.cfg.A = np.array([[0.0, 1.0], [-1.0, -0.2]])
+    errs, _ = _kalman_errors(sc, "exact")
+    assert errs.max() > 1e-6
+
+
+def test_mutation_trace_factor_sign(monkeypatch):
+    orig = of.OracleFilter.diffusion_multiplier
+
+    def bad(self, tau):
+        Psi, g = orig(self, tau)
+        l = self.substeps(tau)
+        return Psi, (1.0 + tau / l * np.trace(self.A)) ** l
+    monkeypatch.setattr(of.OracleFilter, "diffusion_multiplier", bad)
+    cfg = FilterConfig(nx=1, N=(32,), A=np.array([[-0.5]]), Q=np.array([[0.5]]),
+                       m0=np.array([0.0]), P0=np.array([[1.0]]))
+    f = of.OracleFilter(cfg)
+    f.spectral_step(0.1)
+    assert abs(f.last_mass_ratio - 1.0) > 5e-3

@@ -1,0 +1,231 @@
+"""Workload definitions and seeded generators.
+
+Model (Sec. I, eqs. dynam/meas): dx = A x dt + Q dw with E[dw dw^T] = I dt,
+read as Q being the diffusion (covariance-rate) matrix, and z_k = h(x_k) + v_k.
+
+The five workloads follow the model statement of the paper and the sizes of
+the benchmark configurations:
+
+* C1: n_x = 1, A = -0.5, Q = 0.5, prior N(1, 0.5^2), 64 points spanning
+  +-6 sigma, linear z = x + v with v ~ N(0, 0.1^2), 20 epochs at dt = 0.1.
+* C2: n_x = 2 damped oscillator, A = [[0, 1], [-1, -0.2]], Q = diag(0.1, 0.3),
+  128 x 128 grid, prior N((2, 0), 0.25 I), range measurement with
+  v ~ N(0, 0.05^2), 50 epochs at dt = 0.05.
+* C3: n_x = 3, seeded random stable A (real eigenvalues in [-1, -0.1]),
+  Q = diag(0.2, 0.2, 0.1), 96^3 grid, prior N((3, 1, 0), 0.25 I), bearing
+  atan2(x2, x1) plus linear x3 with v ~ N(0, diag(0.02^2, 0.1^2)), 30 epochs
+  at dt = 0.1.
+* C4: 4096 independent n_x = 2 filters, each with its own seeded stable A,
+  diagonal Q in [0.05, 0.5], axis sizes drawn from {32, 48, 64, 96, 128},
+  linear z = x + v with R = 0.1^2 I, 100 epochs at dt = 0.05.
+
+Truth trajectories are integrated with Euler-Maruyama on a fine step
+(``fine`` sub-steps per epoch); this is input simulation, independent of how
+the filter discretises the model.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+MEAS_KINDS = ("linear", "range", "bearing_linear3")
+
+
+@dataclass
+class FilterConfig:
+    """Model and grid of one filter.
+
+    N[m] is the number of grid points along axis m (even).  ``span`` is the
+    half-width of the grid in standard deviations, ``dt_sub`` the Euler
+    sub-step bound (l = ceil(dt / dt_sub) sub-steps per time update) and
+    ``realign_rho`` the whitened-correlation threshold above which the grid
+    frame is re-aligned to the predicted covariance.
+    """
+    nx: int
+    N: tuple
+    A: np.ndarray
+    Q: np.ndarray
+    m0: np.ndarray
+    P0: np.ndarray
+    span: float = 6.0
+    dt_sub: float = 0.01
+    realign_rho: float = 0.5
+
+
+@dataclass
+class MeasModel:
+    """Measurement model z = h(x) + v, v ~ N(0, R).
+
+    kind: 'linear' (h = H x), 'range' (h = |x_{1:2}|) or 'bearing_linear3'
+    (h = [atan2(x2, x1), x3]).
+    """
+    kind: str
+    R: np.ndarray
+    H: Optional[np.ndarray] = None
+
+    @property
+    def nz(self) -> int:
+        return self.R.shape[0]
+
+
+@dataclass
+class Scenario:
+    name: str
+    cfg: FilterConfig
+    meas: MeasModel
+    dt: float
+    epochs: int
+    truth: np.ndarray = field(default=None)
+    z: np.ndarray = field(default=None)
+
+
+def _h_true(meas: MeasModel, x: np.ndarray) -> np.ndarray:
+    """Noise-free measurement of a true state (input simulation only)."""
+    if meas.kind == "linear":
+        return meas.H @ x
+    if meas.kind == "range":
+        return np.array([np.hypot(x[0], x[1])])
+    if meas.kind == "bearing_linear3":
+        return np.array([np.arctan2(x[1], x[0]), x[2]])
+    raise ValueError(meas.kind)
+
+
+def _psd_sqrt(S: np.ndarray) -> np.ndarray:
+    """A square root L with L L^T = S for a symmetric PSD matrix."""
+    w, V = np.linalg.eigh(0.5 * (S + S.T))
+    return V * np.sqrt(np.clip(w, 0.0, None))
+
+
+def simulate(cfg: FilterConfig, meas: MeasModel, dt: float, epochs: int,
+             seed: int, fine: int = 200):
+    """Seeded truth x_0..x_{K-1} and measurements z_0..z_{K-1}.
+
+    x_0 ~ N(m0, P0); between epochs the SDE is integrated by Euler-Maruyama
+    with ``fine`` steps; z_k = h(x_k) + v_k.
+    """
+    rng = np.random.default_rng(seed)
+    n = cfg.nx
+    Lp = np.linalg.cholesky(cfg.P0)
+    Lq = _psd_sqrt(cfg.Q)
+    Lr = np.linalg.cholesky(meas.R)
+    x = cfg.m0 + Lp @ rng.standard_normal(n)
+    h = dt / fine
+    xs, zs = [], []
+    for k in range(epochs):
+        if k > 0:
+            for _ in range(fine):
+                x = x + h * (cfg.A @ x) + np.sqrt(h) * (Lq @ rng.standard_normal(n))
+        xs.append(x.copy())
+        zs.append(_h_true(meas, x) + Lr @ rng.standard_normal(meas.nz))
+    return np.array(xs), np.array(zs)
+
+
+def random_stable_matrix(n: int, rng, re_lo: float = -1.0, re_hi: float = -0.1,
+                         complex_pairs: bool = False, max_cond: float = 10.0):
+    """Seeded stable drift A = V diag-block(Lambda) V^{-1}.
+
+    Eigenvalues (or real parts of complex pairs) are uniform in
+    [re_lo, re_hi]; V is redrawn until cond(V) <= max_cond.
+    """
+    while True:
+        V = rng.standard_normal((n, n))
+        if np.linalg.cond(V) <= max_cond:
+            break
+    B = np.zeros((n, n))
+    i = 0
+    while i < n:
+        a = rng.uniform(re_lo, re_hi)
+        if complex_pairs and i + 1 < n and rng.uniform() < 0.5:
+            b = rng.uniform(0.2, 2.0)
+            B[i:i + 2, i:i + 2] = [[a, b], [-b, a]]
+            i += 2
+        else:
+            B[i, i] = a
+            i += 1
+    return V @ B @ np.linalg.inv(V)
+
+
+def c1_scenario(seed: int = 1, epochs: int = 20, N: int = 64) -> Scenario:
+    cfg = FilterConfig(nx=1, N=(N,), A=np.array([[-0.5]]), Q=np.array([[0.5]]),
+                       m0=np.array([1.0]), P0=np.array([[0.25]]))
+    meas = MeasModel("linear", R=np.array([[0.01]]), H=np.array([[1.0]]))
+    sc = Scenario("c1_1d_n64", cfg, meas, dt=0.1, epochs=epochs)
+    sc.truth, sc.z = simulate(cfg, meas, sc.dt, epochs, seed)
+    return sc
+
+
+def c2_scenario(seed: int = 2, epochs: int = 50, N=(128, 128)) -> Scenario:
+    cfg = FilterConfig(nx=2, N=tuple(N), A=np.array([[0.0, 1.0], [-1.0, -0.2]]),
+                       Q=np.diag([0.1, 0.3]), m0=np.array([2.0, 0.0]),
+                       P0=np.diag([0.25, 0.25]))
+    meas = MeasModel("range", R=np.array([[0.05 ** 2]]))
+    sc = Scenario("c2_2d_osc_128x128", cfg, meas, dt=0.05, epochs=epochs)
+    sc.truth, sc.z = simulate(cfg, meas, sc.dt, epochs, seed)
+    return sc
+
+
+def c3_scenario(seed: int = 3, epochs: int = 30, N=(96, 96, 96)) -> Scenario:
+    rng = np.random.default_rng(1000 + seed)
+    A = random_stable_matrix(3, rng)
+    cfg = FilterConfig(nx=3, N=tuple(N), A=A, Q=np.diag([0.2, 0.2, 0.1]),
+                       m0=np.array([3.0, 1.0, 0.0]), P0=0.25 * np.eye(3))
+    meas = MeasModel("bearing_linear3", R=np.diag([0.02 ** 2, 0.1 ** 2]))
+    sc = Scenario("c3_3d_96cube", cfg, meas, dt=0.1, epochs=epochs)
+    sc.truth, sc.z = simulate(cfg, meas, sc.dt, epochs, seed)
+    return sc
+
+
+def small_2d_scenario(seed: int = 5, epochs: int = 6, N=(48, 32),
+                      kind: str = "range") -> Scenario:
+    """A reduced C2-like problem for parity tests that finish in seconds."""
+    sc = c2_scenario(seed=seed, epochs=epochs, N=N)
+    if kind == "linear":
+        sc.meas = MeasModel("linear", R=0.1 ** 2 * np.eye(2), H=np.eye(2))
+        sc.truth, sc.z = simulate(sc.cfg, sc.meas, sc.dt, epochs, seed)
+    sc.name = f"small_2d_{N[0]}x{N[1]}_{kind}"
+    return sc
+
+
+def small_3d_scenario(seed: int = 6, epochs: int = 3, N=(16, 24, 32)) -> Scenario:
+    """A reduced C3-like problem for parity tests that finish in seconds."""
+    sc = c3_scenario(seed=seed, epochs=epochs, N=N)
+    sc.name = f"small_3d_{N[0]}x{N[1]}x{N[2]}"
+    return sc
+
+
+def c4_batch(count: int = 4096, seed: int = 4, epochs: int = 100,
+             sizes=(32, 48, 64, 96, 128), fine: int = 20):
+    """C4: independent n_x = 2 filters with their own stable A and diagonal Q.
+
+    Returns (configs, meas, dt, truth, z): a list of FilterConfig, the shared
+    measurement model, the epoch spacing, truth of shape (count, epochs, 2)
+    and measurements of shape (count, epochs, 2).  Axis sizes are drawn
+    independently and uniformly from ``sizes``; priors have mean ~ N(0, I)
+    and covariance 0.25 I; z = x + v with R = 0.1^2 I.
+    """
+    rng = np.random.default_rng(seed)
+    meas = MeasModel("linear", R=0.1 ** 2 * np.eye(2), H=np.eye(2))
+    dt = 0.05
+    cfgs = []
+    for _ in range(count):
+        A = random_stable_matrix(2, rng, complex_pairs=True)
+        Q = np.diag(rng.uniform(0.05, 0.5, size=2))
+        N = tuple(int(s) for s in rng.choice(sizes, size=2))
+        m0 = rng.standard_normal(2)
+        cfgs.append(FilterConfig(nx=2, N=N, A=A, Q=Q, m0=m0, P0=0.25 * np.eye(2)))
+    As = np.stack([c.A for c in cfgs])
+    sq = np.stack([np.sqrt(np.diag(c.Q)) for c in cfgs])
+    x = np.stack([c.m0 for c in cfgs]) + 0.5 * rng.standard_normal((count, 2))
+    h = dt / fine
+    truth = np.empty((count, epochs, 2))
+    z = np.empty((count, epochs, 2))
+    for k in range(epochs):
+        if k > 0:
+            for _ in range(fine):
+                x = x + h * np.einsum("fij,fj->fi", As, x) \
+                    + np.sqrt(h) * sq * rng.standard_normal((count, 2))
+        truth[:, k] = x
+        z[:, k] = x + 0.1 * rng.standard_normal((count, 2))
+    return cfgs, meas, dt, truth, z
