@@ -1,0 +1,169 @@
+/*
+ * pmf.h -- C ABI of the GB300 spectral point-mass filter (libpmf.so).
+ *
+ * The library implements the grid-based filter of Matousek, Dunik and Brandner,
+ * "Efficient Spectral Differentiation in Grid-Based Continuous State
+ * Estimation" (FUSION 2024) for the model of Sec. I:
+ *
+ *     dx = A x dt + Q dw,   E[dw dw^T] = I dt        (eq. dynam)
+ *     z_k = h(x_k) + v_k,   v_k ~ N(0, R)             (eq. meas)
+ *
+ * Q is the diffusion (covariance-rate) matrix of the Fokker-Planck equation
+ * (eq. fokker).  The density is a point-mass density (eq. PDF_pm) on an
+ * equidistant grid held in an affine frame x = c + M u, u_m = j_m - (N_m-1)/2,
+ * that moves with the dynamics (eq. gridMov).  A time update solves the moved
+ * Fokker-Planck equation (eq. easyFPE) with the spectral second derivative
+ * (eq. secDer) inside the Euler scheme of the Sec. V-B algorithm; a measurement
+ * update applies Bayes' rule (eq. filt).
+ *
+ * Conventions for every entry point
+ *   - Matrices are row-major float64 arrays, n_x <= PMF_MAX_NX.
+ *   - Grid arrays are C-order (axis n_x-1 fastest), N_m points along axis m.
+ *   - Host pointers are caller-owned and read (or written) only during the
+ *     call.  Device memory is owned by the context that allocated it.
+ *   - A CUDA stream handle (cudaStream_t passed as void*, NULL = legacy
+ *     default stream) is borrowed: all work of a context is enqueued on it
+ *     and it must outlive the context.  Calls return once the work is
+ *     enqueued, except the ones documented as synchronous.
+ *   - Functions return PMF_OK or a PMF_ERR_* code and never throw.  The text
+ *     of the last error of a context is available from pmf_last_error().
+ */
+#ifndef PMF_H
+#define PMF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PMF_MAX_NX 3
+#define PMF_MAX_NZ 3
+#define PMF_MAX_SUBSTEPS 256
+
+/* Return codes. */
+enum {
+  PMF_OK = 0,
+  PMF_ERR_ARG = 1,         /* invalid argument (sizes, non-finite values, Q not PSD ...) */
+  PMF_ERR_OOM = 2,         /* device allocation failed */
+  PMF_ERR_CUDA = 3,        /* CUDA runtime error (message in pmf_last_error) */
+  PMF_ERR_DEGENERATE = 4,  /* normaliser zero or non-finite; density left unchanged */
+  PMF_ERR_TIMEOUT = 5,     /* a bounded device wait expired */
+  PMF_ERR_ADMISSION = 6,   /* request exceeds the device-memory budget */
+  PMF_ERR_UNSUPPORTED = 7  /* configuration not supported by the selected path */
+};
+
+/* Arithmetic of the per-axis transforms (the differentiation GEMMs).
+ *   FP64    : float64 grid and float64 transforms (the plain reference path).
+ *   TF32    : float32 grid, one TF32 tensor-core product per transform.
+ *   TF32X3  : float32 grid, split TF32 (hi*hi + hi*lo + lo*hi), FP32 accumulate.
+ *   BF16X3  : float32 grid, split BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulate.
+ *   FP16X3  : float32 grid, split FP16 with power-of-two operand scaling,
+ *             (hi*hi + hi*lo + lo*hi), FP32 accumulate.
+ * Everything else of a step runs in float32 on the non-FP64 paths, with the
+ * frame, the normalisation constant and the moment combination in float64. */
+enum {
+  PMF_PREC_FP64 = 0,
+  PMF_PREC_TF32 = 1,
+  PMF_PREC_TF32X3 = 2,
+  PMF_PREC_BF16X3 = 3,
+  PMF_PREC_FP16X3 = 4
+};
+
+/* Diffusion multiplier of the time update.
+ *   EULER : the Sec. V-B algorithm, Psi = prod_{n=1..l} psi(t_k + n dt) and
+ *           trace factor (1 - dt tr A)^l, l = ceil(tau / dt_sub).
+ *   EXACT : exact in time, Psi = exp(int d(k, t) dt), trace factor e^{-tr A tau}
+ *           (the alternative time stepping named as future work in Sec. VII). */
+enum { PMF_PSI_EULER = 0, PMF_PSI_EXACT = 1 };
+
+/* Measurement functions h of eq. meas. */
+enum {
+  PMF_MEAS_LINEAR = 0,          /* h(x) = H x, nz rows of H */
+  PMF_MEAS_RANGE = 1,           /* h(x) = sqrt(x1^2 + x2^2), nz = 1 */
+  PMF_MEAS_BEARING_LINEAR3 = 2  /* h(x) = [atan2(x2, x1), x3], nz = 2; the bearing
+                                   residual is wrapped to (-pi, pi] */
+};
+
+typedef struct pmf_config {
+  int nx;                       /* state dimension, 1..PMF_MAX_NX */
+  int N[PMF_MAX_NX];            /* grid points per axis (even; the tensor-core
+                                   path needs multiples of 16 and N <= 128) */
+  double A[PMF_MAX_NX * PMF_MAX_NX];   /* drift, nx x nx row-major packed (a_ij at i*nx+j) */
+  double Q[PMF_MAX_NX * PMF_MAX_NX];   /* diffusion, symmetric PSD, packed like A */
+  double m0[PMF_MAX_NX];        /* prior mean */
+  double P0[PMF_MAX_NX * PMF_MAX_NX];  /* prior covariance, symmetric PD, packed like A */
+  double span_sigma;            /* grid half-width in standard deviations (default 6) */
+  double dt_sub;                /* Euler sub-step bound (default 0.01) */
+  double realign_rho;           /* whitened-correlation threshold for re-alignment (0.5) */
+  int precision;                /* PMF_PREC_* */
+  int psi_mode;                 /* PMF_PSI_* */
+} pmf_config;
+
+typedef struct pmf_meas {
+  int kind;                     /* PMF_MEAS_* */
+  int nz;                       /* measurement dimension */
+  double z[PMF_MAX_NZ];         /* measurement */
+  double R[PMF_MAX_NZ * PMF_MAX_NZ];   /* noise covariance, symmetric PD, nz x nz packed */
+  double H[PMF_MAX_NZ * PMF_MAX_NX];   /* LINEAR only: nz x nx row-major packed */
+} pmf_meas;
+
+typedef struct pmf_ctx pmf_ctx;
+
+/* Fill a config with the defaults (span 6, dt_sub 0.01, rho 0.5, FP64, EULER). */
+void pmf_config_defaults(pmf_config* cfg);
+
+/* Create a filter: allocate its device grid, build the transform tables and
+ * sample the prior N(m0, P0) on the initial frame c = m0,
+ * M = chol(P0) diag(2 span / N_m) (the box covers +-span whitened sigma).
+ * Eq. PDF_pm: weights normalised so that |det M| sum P = 1.
+ * Errors: PMF_ERR_ARG, PMF_ERR_OOM, PMF_ERR_CUDA, PMF_ERR_UNSUPPORTED
+ * (e.g. a tensor-core precision for a grid the fused kernel cannot hold).
+ * On error *out is NULL. */
+int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream);
+
+/* Time update over tau >= 0 (Sec. V-B algorithm on the moving grid of
+ * eq. gridMov), preceded by the regrid that re-centres the grid on the current
+ * mean and sizes it for +-span sigma of the predicted covariance pulled back by
+ * e^{-A tau}.  tau = 0 is a no-op.  Asynchronous.  Errors: PMF_ERR_ARG. */
+int pmf_time_update(pmf_ctx* ctx, double tau);
+
+/* Measurement update (eq. filt): weights times exp(-1/2 r^T R^-1 r),
+ * r = z - h(x), normalised; the mean and covariance are recomputed on the
+ * device.  Asynchronous; a degenerate normaliser is reported by the next
+ * synchronous call (pmf_moments / pmf_get_pdf / pmf_sync) as
+ * PMF_ERR_DEGENERATE, with the weights of before the update kept. */
+int pmf_meas_update(pmf_ctx* ctx, const pmf_meas* meas);
+
+/* One filter epoch: measurement update with *meas, then time update over tau.
+ * Same semantics as the two calls in sequence; on the fused tensor-core path
+ * it is a single kernel launch. */
+int pmf_step(pmf_ctx* ctx, const pmf_meas* meas, double tau);
+
+/* Mean (nx) and covariance (nx*nx, row-major) of the current density as point
+ * sums m = V sum P x, C = V sum P (x-m)(x-m)^T.  Synchronous on the stream. */
+int pmf_moments(pmf_ctx* ctx, double* mean_out, double* cov_out);
+
+/* Copy the normalised weights (prod N_m doubles, C-order) and the frame
+ * (c: nx, M: nx*nx) to host memory; any pointer may be NULL.  Synchronous. */
+int pmf_get_pdf(pmf_ctx* ctx, double* host_out, double* c_out, double* M_out);
+
+/* Wait for the context's stream and report a pending device-side status. */
+int pmf_sync(pmf_ctx* ctx);
+
+/* Number of grid points (prod N_m) and the selected path:
+ * 0 = plain FP64 kernels, 1 = fused tensor-core kernel, 2 = per-axis kernels. */
+long long pmf_num_points(const pmf_ctx* ctx);
+int pmf_path(const pmf_ctx* ctx);
+
+/* Kernel launches issued by this context so far (for launch accounting). */
+long long pmf_launch_count(const pmf_ctx* ctx);
+
+const char* pmf_last_error(const pmf_ctx* ctx);
+void pmf_destroy(pmf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMF_H */

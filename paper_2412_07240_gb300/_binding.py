@@ -1,0 +1,227 @@
+"""ctypes binding of libpmf (include/pmf.h): argument marshalling only.
+
+Every step of the filter runs in the library's CUDA kernels; this module
+converts Python/numpy arguments into the C structs, passes torch's current
+CUDA stream, and turns return codes into exceptions.  It raises on import of
+the library if libpmf.so has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAX_NX = 3
+MAX_NZ = 3
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_DEGENERATE, ERR_TIMEOUT, ERR_ADMISSION, ERR_UNSUPPORTED = range(8)
+PREC = {"fp64": 0, "tf32": 1, "tf32x3": 2, "bf16x3": 3, "fp16x3": 4}
+PSI = {"euler": 0, "exact": 1}
+MEAS = {"linear": 0, "range": 1, "bearing_linear3": 2}
+ERRNAMES = {1: "PMF_ERR_ARG", 2: "PMF_ERR_OOM", 3: "PMF_ERR_CUDA", 4: "PMF_ERR_DEGENERATE",
+            5: "PMF_ERR_TIMEOUT", 6: "PMF_ERR_ADMISSION", 7: "PMF_ERR_UNSUPPORTED"}
+
+
+class PmfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Degenerate(PmfError):
+    pass
+
+
+class Unsupported(PmfError):
+    pass
+
+
+class PmfConfig(C.Structure):
+    _fields_ = [("nx", C.c_int), ("N", C.c_int * MAX_NX), ("A", C.c_double * 9), ("Q", C.c_double * 9),
+                ("m0", C.c_double * MAX_NX), ("P0", C.c_double * 9), ("span_sigma", C.c_double),
+                ("dt_sub", C.c_double), ("realign_rho", C.c_double), ("precision", C.c_int),
+                ("psi_mode", C.c_int)]
+
+
+class PmfMeas(C.Structure):
+    _fields_ = [("kind", C.c_int), ("nz", C.c_int), ("z", C.c_double * MAX_NZ),
+                ("R", C.c_double * 9), ("H", C.c_double * 9)]
+
+
+# (name, restype, argtypes) of every entry point declared in include/pmf.h
+SIGNATURES = [
+    ("pmf_config_defaults", None, [C.POINTER(PmfConfig)]),
+    ("pmf_create", C.c_int, [C.POINTER(C.c_void_p), C.POINTER(PmfConfig), C.c_void_p]),
+    ("pmf_time_update", C.c_int, [C.c_void_p, C.c_double]),
+    ("pmf_meas_update", C.c_int, [C.c_void_p, C.POINTER(PmfMeas)]),
+    ("pmf_step", C.c_int, [C.c_void_p, C.POINTER(PmfMeas), C.c_double]),
+    ("pmf_moments", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("pmf_get_pdf", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                              C.POINTER(C.c_double)]),
+    ("pmf_sync", C.c_int, [C.c_void_p]),
+    ("pmf_num_points", C.c_longlong, [C.c_void_p]),
+    ("pmf_path", C.c_int, [C.c_void_p]),
+    ("pmf_launch_count", C.c_longlong, [C.c_void_p]),
+    ("pmf_last_error", C.c_char_p, [C.c_void_p]),
+    ("pmf_destroy", None, [C.c_void_p]),
+]
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libpmf.so (building it first if allowed); raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB) or not _build.up_to_date():
+        if not build_if_missing:
+            raise ImportError(f"libpmf.so not built at {_build.LIB}")
+        _build.build()
+    lib = C.CDLL(_build.LIB)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _fill(dst, a, n):
+    """Copy the first n values of a (flattened row-major) into the ctypes array dst."""
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64).ravel())
+    if a.size < n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    for i in range(n):
+        dst[i] = float(a[i])
+
+
+def _stream_handle(stream):
+    if stream is not None:
+        return C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # pragma: no cover - torch without CUDA
+        pass
+    return C.c_void_p(0)
+
+
+def make_config(cfg, precision="fp64", psi_mode="euler") -> PmfConfig:
+    """Marshal a filter configuration (nx, N, A, Q, m0, P0, span, dt_sub, realign_rho)."""
+    lib = load()
+    c = PmfConfig()
+    lib.pmf_config_defaults(C.byref(c))
+    n = int(cfg.nx)
+    c.nx = n
+    for a in range(n):
+        c.N[a] = int(cfg.N[a])
+    _fill(c.A, cfg.A, n * n)
+    _fill(c.Q, cfg.Q, n * n)
+    _fill(c.m0, cfg.m0, n)
+    _fill(c.P0, cfg.P0, n * n)
+    c.span_sigma = float(getattr(cfg, "span", 6.0))
+    c.dt_sub = float(getattr(cfg, "dt_sub", 0.01))
+    c.realign_rho = float(getattr(cfg, "realign_rho", 0.5))
+    c.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+    c.psi_mode = PSI[psi_mode] if isinstance(psi_mode, str) else int(psi_mode)
+    return c
+
+
+def make_meas(meas, z, nx) -> PmfMeas:
+    """Marshal a measurement (kind, R, H) and its value z."""
+    m = PmfMeas()
+    m.kind = MEAS[meas.kind]
+    R = np.asarray(meas.R, dtype=np.float64)
+    nz = R.shape[0]
+    m.nz = nz
+    _fill(m.z, z, nz)
+    _fill(m.R, R, nz * nz)
+    if meas.H is not None:
+        _fill(m.H, meas.H, nz * nx)
+    return m
+
+
+class Filter:
+    """One spectral point-mass filter resident on the GPU (a pmf_ctx)."""
+
+    def __init__(self, cfg, precision="fp64", psi_mode="euler", stream=None):
+        self._lib = load()
+        self.nx = int(cfg.nx)
+        self.N = tuple(int(v) for v in cfg.N[: self.nx])
+        self._cfg = make_config(cfg, precision, psi_mode)
+        self._stream = _stream_handle(stream)
+        h = C.c_void_p()
+        rc = self._lib.pmf_create(C.byref(h), C.byref(self._cfg), self._stream)
+        if rc != OK:
+            cls = Unsupported if rc == ERR_UNSUPPORTED else PmfError
+            raise cls(rc, "pmf_create failed")
+        self._h = h
+
+    def _check(self, rc):
+        if rc == OK:
+            return
+        msg = self._lib.pmf_last_error(self._h).decode(errors="replace")
+        if rc == ERR_DEGENERATE:
+            raise Degenerate(rc, msg)
+        raise PmfError(rc, msg)
+
+    def time_update(self, tau: float) -> None:
+        self._check(self._lib.pmf_time_update(self._h, float(tau)))
+
+    def meas_update(self, meas, z) -> None:
+        m = make_meas(meas, z, self.nx)
+        self._check(self._lib.pmf_meas_update(self._h, C.byref(m)))
+
+    def step(self, meas, z, tau: float) -> None:
+        m = make_meas(meas, z, self.nx)
+        self._check(self._lib.pmf_step(self._h, C.byref(m), float(tau)))
+
+    def sync(self) -> None:
+        self._check(self._lib.pmf_sync(self._h))
+
+    def moments(self):
+        n = self.nx
+        m = (C.c_double * n)()
+        P = (C.c_double * (n * n))()
+        self._check(self._lib.pmf_moments(self._h, m, P))
+        return np.array(m[:]), np.array(P[:]).reshape(n, n)
+
+    def pdf(self):
+        n = self.nx
+        out = np.empty(int(np.prod(self.N)), dtype=np.float64)
+        c = (C.c_double * n)()
+        M = (C.c_double * (n * n))()
+        self._check(self._lib.pmf_get_pdf(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), c, M))
+        return out.reshape(self.N), np.array(c[:]), np.array(M[:]).reshape(n, n)
+
+    @property
+    def path(self) -> int:
+        return self._lib.pmf_path(self._h)
+
+    @property
+    def num_points(self) -> int:
+        return int(self._lib.pmf_num_points(self._h))
+
+    @property
+    def launches(self) -> int:
+        return int(self._lib.pmf_launch_count(self._h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.pmf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

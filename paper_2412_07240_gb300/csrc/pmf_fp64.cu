@@ -1,0 +1,591 @@
+// Plain float64 path of the spectral point-mass filter: one small kernel per
+// step of the method, all data in global memory.  It is the reference GPU
+// implementation against which the mixed-precision tensor-core path is
+// compared, and it serves grids of any even size and n_x <= 3.
+//
+// Per time update (Sec. V-B algorithm on the moving grid, eq. gridMov):
+//   frame       regrid decision and per-sub-step diffusion coefficients
+//   realign     multilinear re-alignment (or copy) of the weights
+//   interp x n  trigonometric regrid (eq. interFreq) along each axis
+//   fwd x n     per-axis Hartley transform (real form of eq. fourtrsf)
+//   psi         diffusion multiplier and trace factor (algorithm steps 2-4),
+//               with the separable-to-n-D Hartley parity fix-up
+//   inv x n     per-axis inverse Hartley transform (step 5)
+//   moments     normalisation constant and moments (step 6)
+// Per measurement update (eq. filt): exponent minimum, likelihood multiply
+// with moment partial sums, finalisation.
+#include <cmath>
+
+#include "pmf_internal.cuh"
+#include "pmf_kernels.cuh"
+
+namespace pmf {
+
+__device__ __forceinline__ void unflatten(const Dims& d, long long p, int* j) {
+  for (int m = d.nx - 1; m >= 0; --m) {
+    j[m] = (int)(p % d.N[m]);
+    p /= d.N[m];
+  }
+}
+
+__device__ __forceinline__ double wrap_pi(double r) {
+  const double two_pi = 6.283185307179586476925286766559;
+  const double pi = 3.14159265358979323846264338327950;
+  return r - two_pi * ceil((r - pi) / two_pi);
+}
+
+// e(x) = 1/2 r^T R^{-1} r with r = z - h(x) (eq. meas).
+__device__ double meas_exponent_f64(const MeasParams& mp, const double* x) {
+  double r[PMF_MAX_NZ];
+  if (mp.kind == PMF_MEAS_LINEAR) {
+    for (int i = 0; i < mp.nz; ++i) {
+      double h = 0.0;
+      for (int a = 0; a < mp.nx; ++a) h += mp.H[i * mp.nx + a] * x[a];
+      r[i] = mp.z[i] - h;
+    }
+  } else if (mp.kind == PMF_MEAS_RANGE) {
+    r[0] = mp.z[0] - sqrt(x[0] * x[0] + x[1] * x[1]);
+  } else {
+    r[0] = wrap_pi(mp.z[0] - atan2(x[1], x[0]));
+    r[1] = mp.z[1] - x[2];
+  }
+  double e = 0.0;
+  for (int i = 0; i < mp.nz; ++i)
+    for (int k = 0; k < mp.nz; ++k) e += r[i] * mp.Rinv[i * mp.nz + k] * r[k];
+  return 0.5 * e;
+}
+
+template <int NV>
+__device__ __forceinline__ void block_sum(double* v, double* smem /* [32*NV] */, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    for (int o = 16; o; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) smem[warp * NV + i] = v[i];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double t = lane < nw ? smem[lane * NV + i] : 0.0;
+      for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) out[i] = t;
+    }
+  }
+}
+
+// Moment accumulators in frame coordinates u: S0, S1[3], S2[6] (00,01,02,11,12,22).
+__device__ __forceinline__ void acc_moments(double* acc, double p, const double* u, int nx) {
+  acc[0] += p;
+  for (int a = 0; a < nx; ++a) acc[1 + a] += p * u[a];
+  int k = 4;
+  for (int a = 0; a < 3; ++a)
+    for (int b = a; b < 3; ++b, ++k)
+      if (a < nx && b < nx) acc[k] += p * u[a] * u[b];
+}
+
+__global__ void k_meas_emin_f64(Dims d, MeasParams mp, DevState* st) {
+  double emin = INFINITY;
+  const double* c = st->c;
+  const double* M = st->M;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
+       p += (long long)gridDim.x * blockDim.x) {
+    int j[MAXN];
+    unflatten(d, p, j);
+    double x[MAXN];
+    for (int a = 0; a < d.nx; ++a) {
+      x[a] = c[a];
+      for (int b = 0; b < d.nx; ++b) x[a] += M[a * d.nx + b] * (j[b] - 0.5 * (d.N[b] - 1));
+    }
+    emin = fmin(emin, meas_exponent_f64(mp, x));
+  }
+  for (int o = 16; o; o >>= 1) emin = fmin(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+  if ((threadIdx.x & 31) == 0)
+    atomicMin(&st->emin_bits, (unsigned long long)__double_as_longlong(emin));
+}
+
+__global__ void k_meas_apply_f64(Dims d, MeasParams mp, DevState* st, double* b0, double* b1,
+                                 double* partials) {
+  __shared__ double sm[32 * 10];
+  const int cur = st->cur;
+  const double* in = cur ? b1 : b0;
+  double* out = cur ? b0 : b1;
+  const double emin = __longlong_as_double((long long)st->emin_bits);
+  const double ps = st->pscale;
+  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
+       p += (long long)gridDim.x * blockDim.x) {
+    int j[MAXN];
+    unflatten(d, p, j);
+    double u[MAXN], x[MAXN];
+    for (int a = 0; a < d.nx; ++a) u[a] = j[a] - 0.5 * (d.N[a] - 1);
+    for (int a = 0; a < d.nx; ++a) {
+      x[a] = st->c[a];
+      for (int b = 0; b < d.nx; ++b) x[a] += st->M[a * d.nx + b] * u[b];
+    }
+    const double v = in[p] * ps * exp(-(meas_exponent_f64(mp, x) - emin));
+    out[p] = v;
+    acc_moments(acc, v, u, d.nx);
+  }
+  block_sum<10>(acc, sm, partials + blockIdx.x * 10);
+}
+
+// Sum block partials, finalise moments and the normaliser.  use_pending: the
+// weights are on the frame written by k_frame (time update) and that frame is
+// committed here.  flip: buffer parity change of the update.
+__global__ void k_finalize(Dims d, DevState* st, const double* partials, int nblocks, int flip,
+                           int use_pending, const double* pend /* c, M, Minv, V */) {
+  __shared__ double sm[32 * 10];
+  __shared__ double tot[10];
+  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+    for (int i = 0; i < 10; ++i) acc[i] += partials[b * 10 + i];
+  block_sum<10>(acc, sm, tot);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const int n = d.nx;
+  const double S0 = tot[0];
+  if (!(S0 > 0.0) || !isfinite(S0)) {
+    st->status = PMF_ERR_DEGENERATE;
+    return;
+  }
+  double c[3], M[9], Minv[9], V;
+  if (use_pending) {
+    for (int i = 0; i < n; ++i) c[i] = pend[i];
+    for (int i = 0; i < n * n; ++i) { M[i] = pend[3 + i]; Minv[i] = pend[12 + i]; }
+    V = pend[21];
+  } else {
+    for (int i = 0; i < n; ++i) c[i] = st->c[i];
+    for (int i = 0; i < n * n; ++i) { M[i] = st->M[i]; Minv[i] = st->Minv[i]; }
+    V = st->V;
+  }
+  double mu[3], Cu[9];
+  for (int a = 0; a < n; ++a) mu[a] = tot[1 + a] / S0;
+  int k = 4;
+  double S2[9];
+  for (int a = 0; a < 3; ++a)
+    for (int b = a; b < 3; ++b, ++k)
+      if (a < n && b < n) S2[a * n + b] = S2[b * n + a] = tot[k];
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) Cu[a * n + b] = S2[a * n + b] / S0 - mu[a] * mu[b];
+  double cov[9];
+  congruence(n, M, Cu, cov);
+  for (int a = 0; a < n; ++a) {
+    double m = c[a];
+    for (int b = 0; b < n; ++b) m += M[a * n + b] * mu[b];
+    st->mean[a] = m;
+  }
+  for (int i = 0; i < n * n; ++i) st->cov[i] = cov[i];
+  if (use_pending) {
+    for (int i = 0; i < n; ++i) st->c[i] = c[i];
+    for (int i = 0; i < n * n; ++i) { st->M[i] = M[i]; st->Minv[i] = Minv[i]; }
+    st->V = V;
+  }
+  st->S0 = S0;
+  st->pscale = 1.0 / (V * S0);
+  st->cur ^= flip;
+}
+
+// Regrid decision and the diffusion coefficients of one time update (float64,
+// one thread).  Reads the current moments and frame, writes the regrid map,
+// the per-sub-step coefficients and the pending (advanced) frame.
+__global__ void k_frame(TimeConsts tc, DevState* st, double* pend) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int n = tc.nx;
+  double S[9], Su[9];
+  // pulled-back predicted covariance: e^{-A tau} P_pred e^{-A^T tau} = cov + Qb
+  for (int i = 0; i < n * n; ++i) S[i] = st->cov[i] + tc.Qb[i];
+  congruence(n, st->Minv, S, Su);
+  double sd[3];
+  for (int a = 0; a < n; ++a) sd[a] = sqrt(fmax(Su[a * n + a], 0.0));
+  double rho = 0.0;
+  for (int a = 0; a < n; ++a)
+    for (int b = a + 1; b < n; ++b) rho = fmax(rho, fabs(Su[a * n + b]) / (sd[a] * sd[b]));
+  double Mp[9];
+  int realign = 0;
+  if (n >= 2 && rho > tc.rho_max) {
+    double Pp[9], L[9], T[9];
+    congruence(n, tc.Phi, S, Pp);
+    if (chol(n, Pp, L)) {
+      mm(n, tc.PhiInv, L, T);
+      for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) Mp[a * n + b] = T[a * n + b] * (2.0 * tc.span / tc.N[b]);
+      realign = 1;
+    }
+  }
+  double dm[3];
+  for (int a = 0; a < n; ++a) {
+    double s = 0.0;
+    for (int b = 0; b < n; ++b) s += st->Minv[a * n + b] * (st->mean[b] - st->c[b]);
+    dm[a] = s;
+  }
+  if (realign) {
+    mm(n, st->Minv, Mp, st->B);
+    for (int a = 0; a < n; ++a) st->b[a] = dm[a];
+  } else {
+    for (int a = 0; a < n; ++a) {
+      const double D = 2.0 * tc.span * sd[a] / tc.N[a];
+      for (int r = 0; r < n; ++r) Mp[r * n + a] = st->M[r * n + a] * D;
+      st->rs[a] = dm[a];
+      st->rd[a] = D;
+    }
+  }
+  st->realign = realign;
+  double Mpi[9];
+  inv(n, Mp, Mpi);
+  // diffusion coefficients in the new frame
+  if (tc.exact) {
+    double Qu[9];
+    congruence(n, Mpi, tc.Qb, Qu);
+    for (int a = 0; a < n; ++a) st->pa[0][a] = 0.5 * Qu[a * n + a];
+    st->pb[0][0] = n > 1 ? Qu[1] : 0.0;
+    st->pb[0][1] = n > 2 ? Qu[2] : 0.0;
+    st->pb[0][2] = n > 2 ? Qu[5] : 0.0;
+    st->l = 1;
+    st->exact = 1;
+  } else {
+    double Qt[9], Qn[9], Qu[9];
+    for (int i = 0; i < n * n; ++i) Qt[i] = tc.Q[i];
+    for (int s = 0; s < tc.l; ++s) {
+      congruence(n, tc.Estep, Qt, Qn);
+      for (int i = 0; i < n * n; ++i) Qt[i] = Qn[i];
+      congruence(n, Mpi, Qt, Qu);
+      for (int a = 0; a < n; ++a) st->pa[s][a] = 0.5 * tc.dt * Qu[a * n + a];
+      st->pb[s][0] = n > 1 ? tc.dt * Qu[1] : 0.0;
+      st->pb[s][1] = n > 2 ? tc.dt * Qu[2] : 0.0;
+      st->pb[s][2] = n > 2 ? tc.dt * Qu[5] : 0.0;
+    }
+    st->l = tc.l;
+    st->exact = 0;
+  }
+  st->g = tc.g;
+  // pending frame after the move by e^{A tau}: c' = m, M' -> Phi M'
+  double nM[9], nMi[9];
+  mm(n, tc.Phi, Mp, nM);
+  mm(n, Mpi, tc.PhiInv, nMi);
+  for (int a = 0; a < n; ++a) {
+    double s = 0.0;
+    for (int b = 0; b < n; ++b) s += tc.Phi[a * n + b] * st->mean[b];
+    pend[a] = s;
+  }
+  for (int i = 0; i < n * n; ++i) { pend[3 + i] = nM[i]; pend[12 + i] = nMi[i]; }
+  pend[21] = fabs(det(n, nM));
+}
+
+// Periodic-sinc interpolation matrix of one axis (eq. interFreq evaluated at
+// the new nodes): I[q, j] = sin(pi v) / (N tan(pi v / N)), v = y_q - u_j;
+// rows of new nodes outside the old box are zero; identity when re-aligned.
+__global__ void k_build_interp_f64(Dims d, const DevState* st, int axis, double* I) {
+  const int N = d.N[axis];
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N * N) return;
+  const int q = idx / N, j = idx % N;
+  if (st->realign) {
+    I[idx] = q == j ? 1.0 : 0.0;
+    return;
+  }
+  const double y = st->rs[axis] + st->rd[axis] * (q - 0.5 * (N - 1));
+  if (fabs(y) > 0.5 * N) {
+    I[idx] = 0.0;
+    return;
+  }
+  const double v = y - (j - 0.5 * (N - 1));
+  I[idx] = v == 0.0 ? 1.0 : sinpi(v) * cospi(v / N) / (N * sinpi(v / N));
+}
+
+// Stage 0 of the time update: multilinear re-alignment when the frame was
+// re-aligned, otherwise a scaled copy (both fold the normalisation scale in).
+__global__ void k_realign_f64(Dims d, const DevState* st, double* b0, double* b1) {
+  const int cur = st->cur;
+  const double* in = cur ? b1 : b0;
+  double* out = cur ? b0 : b1;
+  const double ps = st->pscale;
+  const int n = d.nx;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
+       p += (long long)gridDim.x * blockDim.x) {
+    if (!st->realign) {
+      out[p] = ps * in[p];
+      continue;
+    }
+    int j[MAXN];
+    unflatten(d, p, j);
+    double z[MAXN];
+    int f[MAXN];
+    double w[MAXN];
+    for (int a = 0; a < n; ++a) {
+      double uo = st->b[a];
+      for (int b = 0; b < n; ++b) uo += st->B[a * n + b] * (j[b] - 0.5 * (d.N[b] - 1));
+      z[a] = uo + 0.5 * (d.N[a] - 1);
+      const double fl = floor(z[a]);
+      f[a] = (int)fmax(fmin(fl, 1e9), -1e9);
+      w[a] = z[a] - fl;
+    }
+    double s = 0.0;
+    for (int corner = 0; corner < (1 << n); ++corner) {
+      double wt = 1.0;
+      long long off = 0;
+      bool ok = true;
+      for (int a = 0; a < n; ++a) {
+        const int bit = (corner >> a) & 1;
+        const int i = f[a] + bit;
+        wt *= bit ? w[a] : 1.0 - w[a];
+        ok = ok && i >= 0 && i < d.N[a];
+        off = off * d.N[a] + (ok ? i : 0);
+      }
+      if (ok) s += wt * in[off];
+    }
+    out[p] = ps * s;
+  }
+}
+
+// Per-axis transform Y = W x_axis X (float64, 16x16 shared-memory tiles).
+// Buffers: reads bufs[(cur+stage)&1], writes the other one.
+__global__ void k_axis_gemm_f64(Dims d, int axis, const double* W, const DevState* st, int stage,
+                                double* b0, double* b1) {
+  __shared__ double Ls[16][17];
+  __shared__ double Rs[16][17];
+  const int par = (st->cur + stage) & 1;
+  const double* X = par ? b1 : b0;
+  double* Y = par ? b0 : b1;
+  const int N = d.N[axis];
+  long long inner = 1;
+  for (int m = axis + 1; m < d.nx; ++m) inner *= d.N[m];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const long long o = blockIdx.z;
+  if (inner == 1) {
+    // rows of X (one line each) times W^T: C[r][k] = sum_j X[r][j] W[k][j]
+    const long long r = blockIdx.y * 16LL + ty;
+    const int k = blockIdx.x * 16 + tx;
+    const long long rows = d.P / N;
+    double acc = 0.0;
+    for (int j0 = 0; j0 < N; j0 += 16) {
+      const long long rr = blockIdx.y * 16LL + ty;
+      Ls[ty][tx] = (rr < rows && j0 + tx < N) ? X[rr * N + j0 + tx] : 0.0;
+      const int kk = blockIdx.x * 16 + ty;
+      Rs[ty][tx] = (kk < N && j0 + tx < N) ? W[(long long)kk * N + j0 + tx] : 0.0;
+      __syncthreads();
+#pragma unroll
+      for (int t = 0; t < 16; ++t) acc += Ls[ty][t] * Rs[tx][t];
+      __syncthreads();
+    }
+    if (r < rows && k < N) Y[r * N + k] = acc;
+  } else {
+    // C[o][k][i] = sum_j W[k][j] X[o][j][i]
+    const int k = blockIdx.y * 16 + ty;
+    const long long i = blockIdx.x * 16LL + tx;
+    const double* Xo = X + o * N * inner;
+    double acc = 0.0;
+    for (int j0 = 0; j0 < N; j0 += 16) {
+      Ls[ty][tx] = (k < N && j0 + tx < N) ? W[(long long)k * N + j0 + tx] : 0.0;
+      Rs[ty][tx] = (j0 + ty < N && i < inner) ? Xo[(long long)(j0 + ty) * inner + i] : 0.0;
+      __syncthreads();
+#pragma unroll
+      for (int t = 0; t < 16; ++t) acc += Ls[ty][t] * Rs[t][tx];
+      __syncthreads();
+    }
+    if (k < N && i < inner) Y[o * N * inner + (long long)k * inner + i] = acc;
+  }
+}
+
+// Diffusion multiplier Psi and trace factor applied in the Hartley domain
+// (algorithm steps 2-4), one thread per orbit {sigma . k} of sign flips.
+// The separable Hartley coefficients S are split into parity components T_B
+// (odd in the axes of B), the multiplier into its jointly-even parity
+// components Psi_E, and the true-Fourier product is formed per component:
+//   T'_C = sum_{|E| even} (-1)^{|E|/2 + |E & C|} Psi_E T_{E ^ C}.
+__global__ void k_psi_f64(Dims d, const DevState* st, int stage, double* b0, double* b1) {
+  const int par = (st->cur + stage) & 1;
+  double* X = par ? b1 : b0;
+  const int n = d.nx;
+  long long reps = 1;
+  int H[MAXN];
+  for (int a = 0; a < n; ++a) { H[a] = d.N[a] / 2 + 1; reps *= H[a]; }
+  const int l = st->l;
+  const double g = st->g;
+  const int exact = st->exact;
+  const int ns = 1 << n;
+  const double two_pi = 6.283185307179586476925286766559;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < reps;
+       r += (long long)gridDim.x * blockDim.x) {
+    int k[MAXN];
+    long long t = r;
+    for (int a = n - 1; a >= 0; --a) { k[a] = (int)(t % H[a]); t /= H[a]; }
+    double S[8], Psi[8];
+    long long idx[8];
+    for (int s = 0; s < ns; ++s) {
+      long long off = 0;
+      double kap2[MAXN], kt[MAXN];
+      for (int a = 0; a < n; ++a) {
+        const int N = d.N[a];
+        const int ka = ((s >> a) & 1) ? (N - k[a]) % N : k[a];
+        off = off * N + ka;
+        const int w = ka < N / 2 ? ka : ka - N;      // fftshift(-N/2 : N/2-1)
+        const double kap = two_pi * w / N;
+        kap2[a] = kap * kap;
+        kt[a] = (2 * ka == N) ? 0.0 : kap;           // first-derivative: Nyquist omitted
+      }
+      idx[s] = off;
+      S[s] = X[off];
+      double den = 1.0, ex = 0.0;
+      for (int q = 0; q < l; ++q) {
+        double e = 0.0;
+        for (int a = 0; a < n; ++a) e += st->pa[q][a] * kap2[a];
+        if (n > 1) e += st->pb[q][0] * kt[0] * kt[1];
+        if (n > 2) e += st->pb[q][1] * kt[0] * kt[2] + st->pb[q][2] * kt[1] * kt[2];
+        den *= 1.0 + e;
+        ex += e;
+      }
+      Psi[s] = exact ? exp(-ex) : 1.0 / den;
+    }
+    double T[8], Pe[8], Tp[8];
+    for (int B = 0; B < ns; ++B) {
+      double tb = 0.0, pe = 0.0;
+      for (int s = 0; s < ns; ++s) {
+        const double chi = (popc((unsigned)(B & s)) & 1) ? -1.0 : 1.0;
+        tb += chi * S[s];
+        pe += chi * Psi[s];
+      }
+      T[B] = tb / ns;
+      Pe[B] = pe / ns;
+    }
+    for (int C = 0; C < ns; ++C) {
+      double acc = 0.0;
+      for (int E = 0; E < ns; ++E) {
+        const int pe = popc((unsigned)E);
+        if (pe & 1) continue;
+        const int sgn = ((pe / 2) + popc((unsigned)(E & C))) & 1;
+        acc += (sgn ? -1.0 : 1.0) * Pe[E] * T[E ^ C];
+      }
+      Tp[C] = acc * g;
+    }
+    for (int s = 0; s < ns; ++s) {
+      double v = 0.0;
+      for (int C = 0; C < ns; ++C) v += ((popc((unsigned)(C & s)) & 1) ? -1.0 : 1.0) * Tp[C];
+      X[idx[s]] = v;
+    }
+  }
+}
+
+__global__ void k_moments_f64(Dims d, const DevState* st, int stage, const double* b0,
+                              const double* b1, double* partials) {
+  __shared__ double sm[32 * 10];
+  const int par = (st->cur + stage) & 1;
+  const double* X = par ? b1 : b0;
+  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
+       p += (long long)gridDim.x * blockDim.x) {
+    int j[MAXN];
+    unflatten(d, p, j);
+    double u[MAXN];
+    for (int a = 0; a < d.nx; ++a) u[a] = j[a] - 0.5 * (d.N[a] - 1);
+    acc_moments(acc, X[p], u, d.nx);
+  }
+  block_sum<10>(acc, sm, partials + blockIdx.x * 10);
+}
+
+// Initial weights: Gaussian prior sampled on the initial frame (unnormalised).
+__global__ void k_prior_f64(Dims d, const DevState* st, const double* P0inv, const double* m0,
+                            double* X) {
+  const int n = d.nx;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
+       p += (long long)gridDim.x * blockDim.x) {
+    int j[MAXN];
+    unflatten(d, p, j);
+    double dx[MAXN];
+    for (int a = 0; a < n; ++a) {
+      double x = st->c[a];
+      for (int b = 0; b < n; ++b) x += st->M[a * n + b] * (j[b] - 0.5 * (d.N[b] - 1));
+      dx[a] = x - m0[a];
+    }
+    double q = 0.0;
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b < n; ++b) q += dx[a] * P0inv[a * n + b] * dx[b];
+    X[p] = exp(-0.5 * q);
+  }
+}
+
+// Scale the current weights by pscale into a float64 output buffer.
+__global__ void k_export_f64(Dims d, const DevState* st, const double* b0, const double* b1,
+                             double* out) {
+  const double* X = st->cur ? b1 : b0;
+  const double ps = st->pscale;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
+       p += (long long)gridDim.x * blockDim.x)
+    out[p] = ps * X[p];
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline int grid_for(long long work, int threads, int cap) {
+  long long b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+int fp64_partials_blocks(const Dims& d) { return grid_for(d.P, 256, 1024); }
+
+void launch_prior_f64(const Dims& d, const DevState* st, const double* P0inv, const double* m0,
+                      double* X, cudaStream_t s) {
+  k_prior_f64<<<grid_for(d.P, 256, 4096), 256, 0, s>>>(d, st, P0inv, m0, X);
+}
+
+void launch_moments_f64(const Dims& d, DevState* st, int stage, double* b0, double* b1,
+                        double* partials, int flip, int use_pending, const double* pend,
+                        cudaStream_t s) {
+  const int nb = fp64_partials_blocks(d);
+  k_moments_f64<<<nb, 256, 0, s>>>(d, st, stage, b0, b1, partials);
+  k_finalize<<<1, 256, 0, s>>>(d, st, partials, nb, flip, use_pending, pend);
+}
+
+void launch_meas_f64(const Dims& d, const MeasParams& mp, DevState* st, double* b0, double* b1,
+                     double* partials, cudaStream_t s) {
+  cudaMemsetAsync(&st->emin_bits, 0xff, sizeof(unsigned long long), s);
+  k_meas_emin_f64<<<grid_for(d.P, 256, 1024), 256, 0, s>>>(d, mp, st);
+  const int nb = fp64_partials_blocks(d);
+  k_meas_apply_f64<<<nb, 256, 0, s>>>(d, mp, st, b0, b1, partials);
+  k_finalize<<<1, 256, 0, s>>>(d, st, partials, nb, 1, 0, nullptr);
+}
+
+void launch_time_f64(const Dims& d, const TimeConsts& tc, DevState* st, double* b0, double* b1,
+                     double* partials, double* pend, double* const* interp,
+                     double* const* hfwd, double* const* hinv, cudaStream_t s) {
+  const int n = d.nx;
+  k_frame<<<1, 32, 0, s>>>(tc, st, pend);
+  for (int a = 0; a < n; ++a)
+    k_build_interp_f64<<<grid_for((long long)d.N[a] * d.N[a], 256, 1 << 20), 256, 0, s>>>(
+        d, st, a, interp[a]);
+  k_realign_f64<<<grid_for(d.P, 256, 4096), 256, 0, s>>>(d, st, b0, b1);
+  int stage = 1;
+  auto gemm = [&](int a, const double* W) {
+    const int N = d.N[a];
+    long long inner = 1, outer = 1;
+    for (int m = a + 1; m < n; ++m) inner *= d.N[m];
+    for (int m = 0; m < a; ++m) outer *= d.N[m];
+    dim3 blk(16, 16);
+    dim3 grd;
+    if (inner == 1) {
+      grd = dim3((N + 15) / 16, (unsigned)((d.P / N + 15) / 16), 1);
+    } else {
+      grd = dim3((unsigned)((inner + 15) / 16), (N + 15) / 16, (unsigned)outer);
+    }
+    k_axis_gemm_f64<<<grd, blk, 0, s>>>(d, a, W, st, stage, b0, b1);
+    ++stage;
+  };
+  for (int a = 0; a < n; ++a) gemm(a, interp[a]);
+  for (int a = 0; a < n; ++a) gemm(a, hfwd[a]);
+  long long reps = 1;
+  for (int a = 0; a < n; ++a) reps *= d.N[a] / 2 + 1;
+  k_psi_f64<<<grid_for(reps, 128, 4096), 128, 0, s>>>(d, st, stage, b0, b1);
+  for (int a = 0; a < n; ++a) gemm(a, hinv[a]);
+  launch_moments_f64(d, st, stage, b0, b1, partials, stage & 1, 1, pend, s);
+}
+
+void launch_export_f64(const Dims& d, const DevState* st, const double* b0, const double* b1,
+                       double* out, cudaStream_t s) {
+  k_export_f64<<<grid_for(d.P, 256, 4096), 256, 0, s>>>(d, st, b0, b1, out);
+}
+
+}  // namespace pmf

@@ -1,0 +1,157 @@
+// Internal declarations of libpmf: device state layout, per-update constants
+// and float64 small-matrix helpers shared by host and device code.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pmf.h"
+
+#define PMF_HD __host__ __device__ __forceinline__
+
+namespace pmf {
+
+constexpr int MAXN = PMF_MAX_NX;
+constexpr int MAXL = PMF_MAX_SUBSTEPS;
+
+// Grid geometry: nx axes, N[m] points along axis m, C order.
+struct Dims {
+  int nx;
+  int N[MAXN];
+  long long P;
+};
+
+// Constants of one time update that depend only on the model and tau
+// (computed on the host in float64, passed by value to the frame kernel).
+struct TimeConsts {
+  int nx, l, exact;
+  int N[MAXN];
+  double tau, dt, g, span, rho_max;
+  double Q[9];       // diffusion
+  double Phi[9];     // e^{A tau}
+  double PhiInv[9];  // e^{-A tau}
+  double Qb[9];      // int_0^tau e^{-A s} Q e^{-A^T s} ds
+  double Estep[9];   // e^{-A dt}
+};
+
+// Measurement update parameters (by value).
+struct MeasParams {
+  int kind, nz, nx;
+  double z[PMF_MAX_NZ];
+  double Rinv[9];
+  double H[9];
+};
+
+// Per-filter device state.  Frame x = c + M u; weights stored in one of two
+// buffers (cur), true weight = pscale * stored.
+struct DevState {
+  double c[3], M[9], Minv[9], V;
+  double mean[3], cov[9];
+  double S0, pscale;
+  unsigned long long emin_bits;
+  int cur, status, realign, l, exact;
+  double g;
+  // regrid of the current time update
+  double rs[3], rd[3];   // separable: u_old_m = rs_m + rd_m * u_new_m
+  double B[9], b[3];     // realigned: u_old = B u_new + b
+  // diffusion coefficients per sub-step (Euler) or integrated (exact):
+  // psi_n(k) = 1 + sum_a pa[n][a] kappa_a^2 + sum_{a<b} pb[n][ab] kt_a kt_b
+  double pa[MAXL][3];
+  double pb[MAXL][3];
+};
+
+// ---------------------------------------------------------------------------
+// float64 n x n helpers (row-major, n <= 3 on the device; <= 8 on the host)
+// ---------------------------------------------------------------------------
+PMF_HD void mm(int n, const double* A, const double* B, double* C) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < n; ++k) s += A[i * n + k] * B[k * n + j];
+      C[i * n + j] = s;
+    }
+}
+
+// C = A B^T
+PMF_HD void mmt(int n, const double* A, const double* B, double* C) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < n; ++k) s += A[i * n + k] * B[j * n + k];
+      C[i * n + j] = s;
+    }
+}
+
+// C = A S A^T (S symmetric), symmetrised
+PMF_HD void congruence(int n, const double* A, const double* S, double* C) {
+  double T[64];
+  mm(n, A, S, T);
+  mmt(n, T, A, C);
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      double v = 0.5 * (C[i * n + j] + C[j * n + i]);
+      C[i * n + j] = C[j * n + i] = v;
+    }
+}
+
+PMF_HD double det(int n, const double* A) {
+  if (n == 1) return A[0];
+  if (n == 2) return A[0] * A[3] - A[1] * A[2];
+  return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+         A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+
+// Gauss-Jordan inverse with partial pivoting; returns false if singular.
+PMF_HD bool inv(int n, const double* A, double* Ai) {
+  double W[64], I[64];
+  for (int i = 0; i < n * n; ++i) { W[i] = A[i]; I[i] = 0.0; }
+  for (int i = 0; i < n; ++i) I[i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    double best = fabs(W[c * n + c]);
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(W[r * n + c]) > best) { best = fabs(W[r * n + c]); p = r; }
+    if (!(best > 0.0)) return false;
+    if (p != c)
+      for (int k = 0; k < n; ++k) {
+        double t = W[c * n + k]; W[c * n + k] = W[p * n + k]; W[p * n + k] = t;
+        t = I[c * n + k]; I[c * n + k] = I[p * n + k]; I[p * n + k] = t;
+      }
+    double d = 1.0 / W[c * n + c];
+    for (int k = 0; k < n; ++k) { W[c * n + k] *= d; I[c * n + k] *= d; }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double f = W[r * n + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) { W[r * n + k] -= f * W[c * n + k]; I[r * n + k] -= f * I[c * n + k]; }
+    }
+  }
+  for (int i = 0; i < n * n; ++i) Ai[i] = I[i];
+  return true;
+}
+
+// Lower Cholesky factor; returns false if not positive definite.
+PMF_HD bool chol(int n, const double* A, double* L) {
+  for (int i = 0; i < n * n; ++i) L[i] = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double s = A[j * n + j];
+    for (int k = 0; k < j; ++k) s -= L[j * n + k] * L[j * n + k];
+    if (!(s > 0.0)) return false;
+    double d = sqrt(s);
+    L[j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double t = A[i * n + j];
+      for (int k = 0; k < j; ++k) t -= L[i * n + k] * L[j * n + k];
+      L[i * n + j] = t / d;
+    }
+  }
+  return true;
+}
+
+PMF_HD int popc(unsigned v) {
+  int c = 0;
+  while (v) { c += v & 1u; v >>= 1; }
+  return c;
+}
+
+}  // namespace pmf

@@ -1,0 +1,54 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path (through the C-ABI
+binding) and the float64 oracle on the same seeded inputs, update by update."""
+import numpy as np
+
+from oracle.filter import OracleFilter
+
+
+def rel_l1(p, ref):
+    return float(np.abs(p - ref).sum() / np.abs(ref).sum())
+
+
+def compare(gpu, orc):
+    """Relative L1 of the weights, frame and moment differences after one update."""
+    P, c, M = gpu.pdf()
+    out = {"l1": rel_l1(P, orc.P)}
+    out["frame"] = float(max(np.abs(c - orc.c).max() / (np.abs(orc.M).max()),
+                             np.abs(M - orc.M).max() / np.abs(orc.M).max()))
+    m, C = gpu.moments()
+    mo, Co = orc.moments()
+    out["mean"] = float(np.abs(m - mo).max() / np.sqrt(np.trace(Co)))
+    out["cov"] = float(np.abs(C - Co).max() / np.abs(Co).max())
+    return out
+
+
+def run_pair(sc, precision="fp64", epochs=None, psi_mode="euler", fused_step=False):
+    """Yield (stage, errors) after every update of both filters."""
+    from paper_2412_07240_gb300 import Filter
+    gpu = Filter(sc.cfg, precision=precision, psi_mode=psi_mode)
+    orc = OracleFilter(sc.cfg, psi_mode=psi_mode)
+    yield "prior", compare(gpu, orc)
+    for k in range(epochs or sc.epochs):
+        if fused_step:
+            gpu.step(sc.meas, sc.z[k], sc.dt)
+            orc.meas_update(sc.meas, sc.z[k])
+            orc.time_update(sc.dt)
+            yield f"step{k}", compare(gpu, orc)
+            continue
+        gpu.meas_update(sc.meas, sc.z[k])
+        orc.meas_update(sc.meas, sc.z[k])
+        yield f"meas{k}", compare(gpu, orc)
+        gpu.time_update(sc.dt)
+        info = orc.time_update(sc.dt)
+        yield f"time{k}" + ("R" if info["realigned"] else ""), compare(gpu, orc)
+    gpu.close()
+
+
+def max_errors(sc, **kw):
+    worst = {}
+    log = []
+    for stage, e in run_pair(sc, **kw):
+        log.append((stage, e))
+        for k, v in e.items():
+            worst[k] = max(worst.get(k, 0.0), v)
+    return worst, log

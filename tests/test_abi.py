@@ -1,0 +1,89 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point of include/pmf.h."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(pmf_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2412_07240_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+    assert len(_declared()) >= 13
+
+
+def test_binding_signatures_cover_header():
+    from paper_2412_07240_gb300 import _binding
+    bound = {s[0] for s in _binding.SIGNATURES}
+    assert _declared() <= bound | {"pmf_config_defaults"}, _declared() - bound
+
+
+def test_config_defaults_and_struct_layout():
+    from paper_2412_07240_gb300 import _binding
+    lib = _binding.load()
+    c = _binding.PmfConfig()
+    lib.pmf_config_defaults(ctypes.byref(c))
+    assert c.span_sigma == 6.0 and c.dt_sub == 0.01 and c.realign_rho == 0.5
+    assert c.precision == 0 and c.psi_mode == 0
+    # int nx, int N[3] | A, Q | m0 | P0 | span, dt_sub, rho | precision, psi_mode
+    assert ctypes.sizeof(_binding.PmfConfig) == 16 + 72 + 72 + 24 + 72 + 24 + 8
+
+
+def test_invalid_config_rejected_without_gpu():
+    """Validation happens on the host before any CUDA call."""
+    from paper_2412_07240_gb300 import _binding
+    lib = _binding.load()
+    c = _binding.PmfConfig()
+    lib.pmf_config_defaults(ctypes.byref(c))
+    c.nx = 2
+    c.N[0], c.N[1] = 33, 32      # odd size
+    c.P0[0] = c.P0[3] = 1.0
+    h = ctypes.c_void_p()
+    assert lib.pmf_create(ctypes.byref(h), ctypes.byref(c), None) == _binding.ERR_ARG
+    c.N[0] = 32
+    c.P0[0] = -1.0               # not positive definite
+    assert lib.pmf_create(ctypes.byref(h), ctypes.byref(c), None) == _binding.ERR_ARG
+    assert not h.value
+
+
+def test_product_path_does_not_import_oracle():
+    import subprocess
+    import sys
+    code = ("import sys, paper_2412_07240_gb300 as p; p.load(); "
+            "assert not any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules)")
+    subprocess.run([sys.executable, "-c", code], check=True, cwd=ROOT)
+
+
+def test_marshalling_of_config_and_measurement():
+    import numpy as np
+
+    import workloads as w
+    from paper_2412_07240_gb300 import _binding
+    sc = w.small_3d_scenario()
+    c = _binding.make_config(sc.cfg, "fp16x3", "exact")
+    assert c.nx == 3 and tuple(c.N) == (16, 24, 32)
+    assert np.allclose(np.array(c.A[:9]).reshape(3, 3), sc.cfg.A)
+    assert np.allclose(np.array(c.P0[:9]).reshape(3, 3), sc.cfg.P0)
+    assert c.precision == 4 and c.psi_mode == 1
+    m = _binding.make_meas(sc.meas, sc.z[0], 3)
+    assert m.kind == 2 and m.nz == 2 and np.allclose(m.z[:2], sc.z[0])
+    assert np.allclose(np.array(m.R[:4]).reshape(2, 2), sc.meas.R)
+    sc1 = w.c1_scenario()
+    c1 = _binding.make_config(sc1.cfg)
+    assert c1.nx == 1 and c1.N[0] == 64 and c1.A[0] == -0.5 and c1.Q[0] == 0.5
+    m1 = _binding.make_meas(sc1.meas, sc1.z[0], 1)
+    assert m1.kind == 0 and m1.H[0] == 1.0 and m1.R[0] == 0.01
