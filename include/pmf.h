@@ -39,7 +39,7 @@ extern "C" {
 
 #define PMF_MAX_NX 3
 #define PMF_MAX_NZ 3
-#define PMF_MAX_SUBSTEPS 256
+#define PMF_MAX_SUBSTEPS 64
 
 /* Return codes. */
 enum {

@@ -138,6 +138,20 @@ int make_time_consts(pmf_ctx* ctx, double tau, TimeConsts* tc) {
   for (int i = 0; i < n; ++i)
     for (int j = i + 1; j < n; ++j) Qd[i * n + j] = Qd[j * n + i] = 0.5 * (Qd[i * n + j] + Qd[j * n + i]);
   congruence(n, tc->PhiInv, Qd, tc->Qb);
+  // rotated diffusion at the sub-step ends: e^{-A q dt} Q e^{-A^T q dt}, q = 1..l
+  double Eq[9], mAq[9], Qq[9];
+  for (int q = 1; q <= l; ++q) {
+    for (int i = 0; i < n * n; ++i) mAq[i] = -c.A[i] * (tc->dt * q);
+    expm_host(n, mAq, Eq);
+    congruence(n, Eq, c.Q, Qq);
+    double* o = tc->Qt[q - 1];
+    o[0] = Qq[0];
+    o[1] = n > 1 ? Qq[1] : 0.0;
+    o[2] = n > 2 ? Qq[2] : 0.0;
+    o[3] = n > 1 ? Qq[n + 1] : 0.0;
+    o[4] = n > 2 ? Qq[5] : 0.0;
+    o[5] = n > 2 ? Qq[8] : 0.0;
+  }
   tc->g = tc->exact ? std::exp(-trA * tau) : std::pow(1.0 - tc->dt * trA, (double)l);
   return PMF_OK;
 }
@@ -229,10 +243,10 @@ void free_ctx(pmf_ctx* ctx) {
 int check_status(pmf_ctx* ctx) {
   int status = 0;
   PMF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  PMF_CUDA(ctx, cudaMemcpy(&status, &ctx->st->status, sizeof(int), cudaMemcpyDeviceToHost));
+  PMF_CUDA(ctx, cudaMemcpy(&status, &ctx->st->f.status, sizeof(int), cudaMemcpyDeviceToHost));
   if (status != 0) {
     const int zero = 0;
-    PMF_CUDA(ctx, cudaMemcpy(&ctx->st->status, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    PMF_CUDA(ctx, cudaMemcpy(&ctx->st->f.status, &zero, sizeof(int), cudaMemcpyHostToDevice));
     return fail(ctx, status, status == PMF_ERR_DEGENERATE
                                  ? "degenerate normaliser: density left unchanged"
                                  : "device reported an error");
@@ -322,12 +336,12 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
   DevState h{};
   double L[9];
   chol(n, cfg->P0, L);
-  for (int a = 0; a < n; ++a) h.c[a] = cfg->m0[a];
+  for (int a = 0; a < n; ++a) h.f.c[a] = cfg->m0[a];
   for (int r = 0; r < n; ++r)
-    for (int a = 0; a < n; ++a) h.M[r * n + a] = L[r * n + a] * (2.0 * cfg->span_sigma / cfg->N[a]);
-  inv(n, h.M, h.Minv);
-  h.V = std::fabs(det(n, h.M));
-  h.pscale = 1.0;
+    for (int a = 0; a < n; ++a) h.f.M[r * n + a] = L[r * n + a] * (2.0 * cfg->span_sigma / cfg->N[a]);
+  inv(n, h.f.M, h.f.Minv);
+  h.f.V = std::fabs(det(n, h.f.M));
+  h.f.pscale = 1.0;
   double aux[16] = {0};
   inv(n, cfg->P0, aux);
   for (int a = 0; a < n; ++a) aux[9 + a] = cfg->m0[a];
@@ -434,8 +448,8 @@ int pmf_moments(pmf_ctx* ctx, double* mean_out, double* cov_out) {
   const int n = ctx->cfg.nx;
   DevState h;
   PMF_CUDA(ctx, cudaMemcpy(&h, ctx->st, offsetof(DevState, pa), cudaMemcpyDeviceToHost));
-  if (mean_out) std::memcpy(mean_out, h.mean, sizeof(double) * n);
-  if (cov_out) std::memcpy(cov_out, h.cov, sizeof(double) * n * n);
+  if (mean_out) std::memcpy(mean_out, h.f.mean, sizeof(double) * n);
+  if (cov_out) std::memcpy(cov_out, h.f.cov, sizeof(double) * n * n);
   return PMF_OK;
 }
 
@@ -446,22 +460,22 @@ int pmf_get_pdf(pmf_ctx* ctx, double* host_out, double* c_out, double* M_out) {
   const int n = ctx->cfg.nx;
   DevState h;
   PMF_CUDA(ctx, cudaMemcpy(&h, ctx->st, offsetof(DevState, pa), cudaMemcpyDeviceToHost));
-  if (c_out) std::memcpy(c_out, h.c, sizeof(double) * n);
-  if (M_out) std::memcpy(M_out, h.M, sizeof(double) * n * n);
+  if (c_out) std::memcpy(c_out, h.f.c, sizeof(double) * n);
+  if (M_out) std::memcpy(M_out, h.f.M, sizeof(double) * n * n);
   if (host_out) {
     const long long P = ctx->dims.P;
     if (ctx->path == 0) {
-      PMF_CUDA(ctx, cudaMemcpy(host_out, ctx->buf[h.cur], sizeof(double) * P, cudaMemcpyDeviceToHost));
-      for (long long i = 0; i < P; ++i) host_out[i] *= h.pscale;
+      PMF_CUDA(ctx, cudaMemcpy(host_out, ctx->buf[h.f.cur], sizeof(double) * P, cudaMemcpyDeviceToHost));
+      for (long long i = 0; i < P; ++i) host_out[i] *= h.f.pscale;
     } else {
       float* tmp = new (std::nothrow) float[P];
       if (!tmp) return fail(ctx, PMF_ERR_OOM, "host buffer");
-      cudaError_t e = cudaMemcpy(tmp, ctx->buf[h.cur], sizeof(float) * P, cudaMemcpyDeviceToHost);
+      cudaError_t e = cudaMemcpy(tmp, ctx->buf[h.f.cur], sizeof(float) * P, cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) {
         delete[] tmp;
         return fail(ctx, PMF_ERR_CUDA, cudaGetErrorString(e));
       }
-      for (long long i = 0; i < P; ++i) host_out[i] = h.pscale * (double)tmp[i];
+      for (long long i = 0; i < P; ++i) host_out[i] = h.f.pscale * (double)tmp[i];
       delete[] tmp;
     }
   }

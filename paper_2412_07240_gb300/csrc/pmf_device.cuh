@@ -1,0 +1,270 @@
+// Device functions shared by the float64 kernels and the fused tensor-core
+// kernel: regrid/frame computation and moment finalisation (float64, one thread).
+#pragma once
+
+#include "pmf_internal.cuh"
+
+namespace pmf {
+
+// ---------------------------------------------------------------------------
+// Fixed-size float64 helpers (n <= 3, fully unrolled, registers only).  On
+// GB300 a dependent float64 FMA costs ~64 cycles and a division ~430, so the
+// per-epoch frame work avoids loops over local arrays and uses one reciprocal
+// per inverse.
+// ---------------------------------------------------------------------------
+template <int n>
+__device__ __forceinline__ void mm_t(const double* A, const double* B, double* C) {
+#pragma unroll
+  for (int i = 0; i < n; ++i)
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < n; ++k) s = fma(A[i * n + k], B[k * n + j], s);
+      C[i * n + j] = s;
+    }
+}
+
+// C = A S A^T for symmetric S (upper triangle computed, mirrored).
+template <int n>
+__device__ __forceinline__ void cong_t(const double* A, const double* S, double* C) {
+  double T[n * n];
+  mm_t<n>(A, S, T);
+#pragma unroll
+  for (int i = 0; i < n; ++i)
+#pragma unroll
+    for (int j = i; j < n; ++j) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < n; ++k) s = fma(T[i * n + k], A[j * n + k], s);
+      C[i * n + j] = s;
+      C[j * n + i] = s;
+    }
+}
+
+template <int n>
+__device__ __forceinline__ double det_t(const double* A) {
+  if (n == 1) return A[0];
+  if (n == 2) return A[0] * A[3] - A[1] * A[2];
+  return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+         A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+
+// Inverse by the adjugate and one reciprocal of the determinant.
+template <int n>
+__device__ __forceinline__ void inv_t(const double* A, double* Ai) {
+  const double r = 1.0 / det_t<n>(A);
+  if (n == 1) {
+    Ai[0] = r;
+  } else if (n == 2) {
+    Ai[0] = A[3] * r;
+    Ai[1] = -A[1] * r;
+    Ai[2] = -A[2] * r;
+    Ai[3] = A[0] * r;
+  } else {
+    Ai[0] = (A[4] * A[8] - A[5] * A[7]) * r;
+    Ai[1] = (A[2] * A[7] - A[1] * A[8]) * r;
+    Ai[2] = (A[1] * A[5] - A[2] * A[4]) * r;
+    Ai[3] = (A[5] * A[6] - A[3] * A[8]) * r;
+    Ai[4] = (A[0] * A[8] - A[2] * A[6]) * r;
+    Ai[5] = (A[2] * A[3] - A[0] * A[5]) * r;
+    Ai[6] = (A[3] * A[7] - A[4] * A[6]) * r;
+    Ai[7] = (A[1] * A[6] - A[0] * A[7]) * r;
+    Ai[8] = (A[0] * A[4] - A[1] * A[3]) * r;
+  }
+}
+
+template <int n>
+__device__ __forceinline__ bool chol_t(const double* A, double* L) {
+#pragma unroll
+  for (int i = 0; i < n * n; ++i) L[i] = 0.0;
+#pragma unroll
+  for (int j = 0; j < n; ++j) {
+    double s = A[j * n + j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) s -= L[j * n + k] * L[j * n + k];
+    if (!(s > 0.0)) return false;
+    const double d = sqrt(s), rd = 1.0 / d;
+    L[j * n + j] = d;
+#pragma unroll
+    for (int i = j + 1; i < n; ++i) {
+      double t = A[i * n + j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) t -= L[i * n + k] * L[j * n + k];
+      L[i * n + j] = t * rd;
+    }
+  }
+  return true;
+}
+
+// Regrid decision of one time update (float64, one thread).  From the current
+// moments and frame: the pulled-back predicted covariance
+// e^{-A tau} P_pred e^{-A^T tau} = cov + Q_b, its whitened correlation in the
+// frame, and either the separable rescale/recentre (M' = M D, c' = mean) or a
+// re-aligned frame M' = e^{-A tau} chol(P_pred) diag(2 span / N).  Writes the
+// regrid map into st, the inverse of M' into Mpi and the pending frame after
+// the move by e^{A tau} into pend = {c[3], M[9], Minv[9], V}.
+template <int n>
+__device__ inline void frame_scalar(const TimeConsts& tc, FrameState* st, double* pend, double* Mpi) {
+  double S[n * n], Su[n * n], Minv[n * n], M[n * n], Mp[n * n];
+#pragma unroll
+  for (int i = 0; i < n * n; ++i) {
+    S[i] = st->cov[i] + tc.Qb[i];
+    Minv[i] = st->Minv[i];
+    M[i] = st->M[i];
+  }
+  cong_t<n>(Minv, S, Su);
+  double sd[n];
+#pragma unroll
+  for (int a = 0; a < n; ++a) sd[a] = sqrt(fmax(Su[a * n + a], 0.0));
+  int realign = 0;
+  if (n >= 2) {
+    // max |rho_ab| > rho_max  <=>  Su_ab^2 > rho_max^2 Su_aa Su_bb (no division)
+    const double r2 = tc.rho_max * tc.rho_max;
+#pragma unroll
+    for (int a = 0; a < n; ++a)
+#pragma unroll
+      for (int b = a + 1; b < n; ++b)
+        if (Su[a * n + b] * Su[a * n + b] > r2 * Su[a * n + a] * Su[b * n + b]) realign = 1;
+  }
+  if (realign) {
+    double Pp[n * n], L[n * n], T[n * n];
+    cong_t<n>(tc.Phi, S, Pp);
+    if (chol_t<n>(Pp, L)) {
+      mm_t<n>(tc.PhiInv, L, T);
+#pragma unroll
+      for (int a = 0; a < n; ++a)
+#pragma unroll
+        for (int b = 0; b < n; ++b) Mp[a * n + b] = T[a * n + b] * (2.0 * tc.span / tc.N[b]);
+    } else {
+      realign = 0;
+    }
+  }
+  double dm[n];
+#pragma unroll
+  for (int a = 0; a < n; ++a) {
+    double s = 0.0;
+#pragma unroll
+    for (int b = 0; b < n; ++b) s = fma(Minv[a * n + b], st->mean[b] - st->c[b], s);
+    dm[a] = s;
+  }
+  if (realign) {
+    double B[n * n];
+    mm_t<n>(Minv, Mp, B);
+#pragma unroll
+    for (int i = 0; i < n * n; ++i) st->B[i] = B[i];
+#pragma unroll
+    for (int a = 0; a < n; ++a) st->b[a] = dm[a];
+    inv_t<n>(Mp, Mpi);
+  } else {
+#pragma unroll
+    for (int a = 0; a < n; ++a) {
+      const double D = 2.0 * tc.span * sd[a] / tc.N[a];
+      const double rD = 1.0 / D;
+#pragma unroll
+      for (int r = 0; r < n; ++r) {
+        Mp[r * n + a] = M[r * n + a] * D;
+        Mpi[a * n + r] = Minv[a * n + r] * rD;   // (M D)^{-1} = D^{-1} M^{-1}
+      }
+      st->rs[a] = dm[a];
+      st->rd[a] = D;
+    }
+  }
+  st->realign = realign;
+  st->exact = tc.exact;
+  st->l = tc.exact ? 1 : tc.l;
+  st->g = tc.g;
+  double nM[n * n], nMi[n * n];
+  mm_t<n>(tc.Phi, Mp, nM);
+  mm_t<n>(Mpi, tc.PhiInv, nMi);
+#pragma unroll
+  for (int a = 0; a < n; ++a) {
+    double s = 0.0;
+#pragma unroll
+    for (int b = 0; b < n; ++b) s = fma(tc.Phi[a * n + b], st->mean[b], s);
+    pend[a] = s;
+  }
+#pragma unroll
+  for (int i = 0; i < n * n; ++i) {
+    pend[3 + i] = nM[i];
+    pend[12 + i] = nMi[i];
+  }
+  pend[21] = fabs(det_t<n>(nM));
+}
+
+// Diffusion coefficients of sub-step q in the new frame (any thread):
+// Q_u(t_q) = M'^{-1} Qt_q M'^{-T}, Qt_q = e^{-A q dt} Q e^{-A^T q dt} (host),
+// pa = dt/2 Q_u,aa and pb = dt Q_u,ab (01, 02, 12); for the exact multiplier
+// the integrated Q_b takes the place of dt Qt.
+template <int n>
+__device__ inline void frame_substep(const TimeConsts& tc, const double* Mpi, int q, double* pa, double* pb) {
+  double Qt[n * n], Qu[n * n];
+  const double* src = tc.exact ? tc.Qb : nullptr;
+#pragma unroll
+  for (int a = 0; a < n; ++a)
+#pragma unroll
+    for (int b = 0; b < n; ++b) {
+      const int lo = a < b ? a : b, hi = a < b ? b : a;
+      const int k = lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);   // packed 00,01,02,11,12,22
+      Qt[a * n + b] = src ? src[a * n + b] : tc.Qt[q][k];
+    }
+  cong_t<n>(Mpi, Qt, Qu);
+  const double w = tc.exact ? 1.0 : tc.dt;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) pa[a] = a < n ? 0.5 * w * Qu[(a < n ? a : 0) * (n + 1)] : 0.0;
+  pb[0] = n > 1 ? w * Qu[1 % (n * n)] : 0.0;
+  pb[1] = n > 2 ? w * Qu[2 % (n * n)] : 0.0;
+  pb[2] = n > 2 ? w * Qu[5 % (n * n)] : 0.0;
+}
+
+// Finalise moments from the sums tot = {S0, S1[3], S2[6]} (frame coordinates u)
+// and set the normaliser pscale = 1 / (V S0).  With use_pending the weights are
+// on the pending (advanced) frame pend = {c[3], M[9], Minv[9], V}, which is
+// committed.  Returns false (status DEGENERATE, state untouched) if S0 is not
+// positive and finite.
+__device__ inline bool finalize_core(int nx, FrameState* st, const double* tot, int use_pending,
+                                     const double* pend) {
+  const int n = nx;
+  const double S0 = tot[0];
+  if (!(S0 > 0.0) || !isfinite(S0)) {
+    st->status = PMF_ERR_DEGENERATE;
+    return false;
+  }
+  double c[3], M[9], Minv[9], V;
+  if (use_pending) {
+    for (int i = 0; i < n; ++i) c[i] = pend[i];
+    for (int i = 0; i < n * n; ++i) { M[i] = pend[3 + i]; Minv[i] = pend[12 + i]; }
+    V = pend[21];
+  } else {
+    for (int i = 0; i < n; ++i) c[i] = st->c[i];
+    for (int i = 0; i < n * n; ++i) { M[i] = st->M[i]; Minv[i] = st->Minv[i]; }
+    V = st->V;
+  }
+  double mu[3], Cu[9];
+  for (int a = 0; a < n; ++a) mu[a] = tot[1 + a] / S0;
+  int k = 4;
+  double S2[9];
+  for (int a = 0; a < 3; ++a)
+    for (int b = a; b < 3; ++b, ++k)
+      if (a < n && b < n) S2[a * n + b] = S2[b * n + a] = tot[k];
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) Cu[a * n + b] = S2[a * n + b] / S0 - mu[a] * mu[b];
+  double cov[9];
+  congruence(n, M, Cu, cov);
+  for (int a = 0; a < n; ++a) {
+    double m = c[a];
+    for (int b = 0; b < n; ++b) m += M[a * n + b] * mu[b];
+    st->mean[a] = m;
+  }
+  for (int i = 0; i < n * n; ++i) st->cov[i] = cov[i];
+  if (use_pending) {
+    for (int i = 0; i < n; ++i) st->c[i] = c[i];
+    for (int i = 0; i < n * n; ++i) { st->M[i] = M[i]; st->Minv[i] = Minv[i]; }
+    st->V = V;
+  }
+  st->S0 = S0;
+  st->pscale = 1.0 / (V * S0);
+  return true;
+}
+
+}  // namespace pmf

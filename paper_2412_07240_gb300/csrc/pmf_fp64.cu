@@ -18,6 +18,7 @@
 
 #include "pmf_internal.cuh"
 #include "pmf_kernels.cuh"
+#include "pmf_device.cuh"
 
 namespace pmf {
 
@@ -87,8 +88,8 @@ __device__ __forceinline__ void acc_moments(double* acc, double p, const double*
 
 __global__ void k_meas_emin_f64(Dims d, MeasParams mp, DevState* st) {
   double emin = INFINITY;
-  const double* c = st->c;
-  const double* M = st->M;
+  const double* c = st->f.c;
+  const double* M = st->f.M;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
        p += (long long)gridDim.x * blockDim.x) {
     int j[MAXN];
@@ -108,11 +109,11 @@ __global__ void k_meas_emin_f64(Dims d, MeasParams mp, DevState* st) {
 __global__ void k_meas_apply_f64(Dims d, MeasParams mp, DevState* st, double* b0, double* b1,
                                  double* partials) {
   __shared__ double sm[32 * 10];
-  const int cur = st->cur;
+  const int cur = st->f.cur;
   const double* in = cur ? b1 : b0;
   double* out = cur ? b0 : b1;
   const double emin = __longlong_as_double((long long)st->emin_bits);
-  const double ps = st->pscale;
+  const double ps = st->f.pscale;
   double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
        p += (long long)gridDim.x * blockDim.x) {
@@ -121,8 +122,8 @@ __global__ void k_meas_apply_f64(Dims d, MeasParams mp, DevState* st, double* b0
     double u[MAXN], x[MAXN];
     for (int a = 0; a < d.nx; ++a) u[a] = j[a] - 0.5 * (d.N[a] - 1);
     for (int a = 0; a < d.nx; ++a) {
-      x[a] = st->c[a];
-      for (int b = 0; b < d.nx; ++b) x[a] += st->M[a * d.nx + b] * u[b];
+      x[a] = st->f.c[a];
+      for (int b = 0; b < d.nx; ++b) x[a] += st->f.M[a * d.nx + b] * u[b];
     }
     const double v = in[p] * ps * exp(-(meas_exponent_f64(mp, x) - emin));
     out[p] = v;
@@ -144,133 +145,31 @@ __global__ void k_finalize(Dims d, DevState* st, const double* partials, int nbl
   block_sum<10>(acc, sm, tot);
   __syncthreads();
   if (threadIdx.x != 0) return;
-  const int n = d.nx;
-  const double S0 = tot[0];
-  if (!(S0 > 0.0) || !isfinite(S0)) {
-    st->status = PMF_ERR_DEGENERATE;
-    return;
-  }
-  double c[3], M[9], Minv[9], V;
-  if (use_pending) {
-    for (int i = 0; i < n; ++i) c[i] = pend[i];
-    for (int i = 0; i < n * n; ++i) { M[i] = pend[3 + i]; Minv[i] = pend[12 + i]; }
-    V = pend[21];
-  } else {
-    for (int i = 0; i < n; ++i) c[i] = st->c[i];
-    for (int i = 0; i < n * n; ++i) { M[i] = st->M[i]; Minv[i] = st->Minv[i]; }
-    V = st->V;
-  }
-  double mu[3], Cu[9];
-  for (int a = 0; a < n; ++a) mu[a] = tot[1 + a] / S0;
-  int k = 4;
-  double S2[9];
-  for (int a = 0; a < 3; ++a)
-    for (int b = a; b < 3; ++b, ++k)
-      if (a < n && b < n) S2[a * n + b] = S2[b * n + a] = tot[k];
-  for (int a = 0; a < n; ++a)
-    for (int b = 0; b < n; ++b) Cu[a * n + b] = S2[a * n + b] / S0 - mu[a] * mu[b];
-  double cov[9];
-  congruence(n, M, Cu, cov);
-  for (int a = 0; a < n; ++a) {
-    double m = c[a];
-    for (int b = 0; b < n; ++b) m += M[a * n + b] * mu[b];
-    st->mean[a] = m;
-  }
-  for (int i = 0; i < n * n; ++i) st->cov[i] = cov[i];
-  if (use_pending) {
-    for (int i = 0; i < n; ++i) st->c[i] = c[i];
-    for (int i = 0; i < n * n; ++i) { st->M[i] = M[i]; st->Minv[i] = Minv[i]; }
-    st->V = V;
-  }
-  st->S0 = S0;
-  st->pscale = 1.0 / (V * S0);
-  st->cur ^= flip;
+  FrameState fs = st->f;   // local copy: the scalar work stays out of global memory
+  if (finalize_core(d.nx, &fs, tot, use_pending, pend)) fs.cur ^= flip;
+  st->f = fs;
 }
 
-// Regrid decision and the diffusion coefficients of one time update (float64,
-// one thread).  Reads the current moments and frame, writes the regrid map,
-// the per-sub-step coefficients and the pending (advanced) frame.
-__global__ void k_frame(TimeConsts tc, DevState* st, double* pend) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int n = tc.nx;
-  double S[9], Su[9];
-  // pulled-back predicted covariance: e^{-A tau} P_pred e^{-A^T tau} = cov + Qb
-  for (int i = 0; i < n * n; ++i) S[i] = st->cov[i] + tc.Qb[i];
-  congruence(n, st->Minv, S, Su);
-  double sd[3];
-  for (int a = 0; a < n; ++a) sd[a] = sqrt(fmax(Su[a * n + a], 0.0));
-  double rho = 0.0;
-  for (int a = 0; a < n; ++a)
-    for (int b = a + 1; b < n; ++b) rho = fmax(rho, fabs(Su[a * n + b]) / (sd[a] * sd[b]));
-  double Mp[9];
-  int realign = 0;
-  if (n >= 2 && rho > tc.rho_max) {
-    double Pp[9], L[9], T[9];
-    congruence(n, tc.Phi, S, Pp);
-    if (chol(n, Pp, L)) {
-      mm(n, tc.PhiInv, L, T);
-      for (int a = 0; a < n; ++a)
-        for (int b = 0; b < n; ++b) Mp[a * n + b] = T[a * n + b] * (2.0 * tc.span / tc.N[b]);
-      realign = 1;
-    }
+// Regrid decision (thread 0) and the diffusion coefficients of every sub-step
+// (one thread each) of one time update.
+template <int n>
+__device__ void frame_body(const TimeConsts& tc, DevState* st, double* pend) {
+  __shared__ FrameState fs;
+  __shared__ double Mpi[9];
+  if (threadIdx.x == 0) {
+    fs = st->f;
+    frame_scalar<n>(tc, &fs, pend, Mpi);
+    st->f = fs;
   }
-  double dm[3];
-  for (int a = 0; a < n; ++a) {
-    double s = 0.0;
-    for (int b = 0; b < n; ++b) s += st->Minv[a * n + b] * (st->mean[b] - st->c[b]);
-    dm[a] = s;
-  }
-  if (realign) {
-    mm(n, st->Minv, Mp, st->B);
-    for (int a = 0; a < n; ++a) st->b[a] = dm[a];
-  } else {
-    for (int a = 0; a < n; ++a) {
-      const double D = 2.0 * tc.span * sd[a] / tc.N[a];
-      for (int r = 0; r < n; ++r) Mp[r * n + a] = st->M[r * n + a] * D;
-      st->rs[a] = dm[a];
-      st->rd[a] = D;
-    }
-  }
-  st->realign = realign;
-  double Mpi[9];
-  inv(n, Mp, Mpi);
-  // diffusion coefficients in the new frame
-  if (tc.exact) {
-    double Qu[9];
-    congruence(n, Mpi, tc.Qb, Qu);
-    for (int a = 0; a < n; ++a) st->pa[0][a] = 0.5 * Qu[a * n + a];
-    st->pb[0][0] = n > 1 ? Qu[1] : 0.0;
-    st->pb[0][1] = n > 2 ? Qu[2] : 0.0;
-    st->pb[0][2] = n > 2 ? Qu[5] : 0.0;
-    st->l = 1;
-    st->exact = 1;
-  } else {
-    double Qt[9], Qn[9], Qu[9];
-    for (int i = 0; i < n * n; ++i) Qt[i] = tc.Q[i];
-    for (int s = 0; s < tc.l; ++s) {
-      congruence(n, tc.Estep, Qt, Qn);
-      for (int i = 0; i < n * n; ++i) Qt[i] = Qn[i];
-      congruence(n, Mpi, Qt, Qu);
-      for (int a = 0; a < n; ++a) st->pa[s][a] = 0.5 * tc.dt * Qu[a * n + a];
-      st->pb[s][0] = n > 1 ? tc.dt * Qu[1] : 0.0;
-      st->pb[s][1] = n > 2 ? tc.dt * Qu[2] : 0.0;
-      st->pb[s][2] = n > 2 ? tc.dt * Qu[5] : 0.0;
-    }
-    st->l = tc.l;
-    st->exact = 0;
-  }
-  st->g = tc.g;
-  // pending frame after the move by e^{A tau}: c' = m, M' -> Phi M'
-  double nM[9], nMi[9];
-  mm(n, tc.Phi, Mp, nM);
-  mm(n, Mpi, tc.PhiInv, nMi);
-  for (int a = 0; a < n; ++a) {
-    double s = 0.0;
-    for (int b = 0; b < n; ++b) s += tc.Phi[a * n + b] * st->mean[b];
-    pend[a] = s;
-  }
-  for (int i = 0; i < n * n; ++i) { pend[3 + i] = nM[i]; pend[12 + i] = nMi[i]; }
-  pend[21] = fabs(det(n, nM));
+  __syncthreads();
+  const int l = tc.exact ? 1 : tc.l;
+  for (int q = threadIdx.x; q < l; q += blockDim.x) frame_substep<n>(tc, Mpi, q, st->pa[q], st->pb[q]);
+}
+
+__global__ void k_frame(const __grid_constant__ TimeConsts tc, DevState* st, double* pend) {
+  if (tc.nx == 1) frame_body<1>(tc, st, pend);
+  else if (tc.nx == 2) frame_body<2>(tc, st, pend);
+  else frame_body<3>(tc, st, pend);
 }
 
 // Periodic-sinc interpolation matrix of one axis (eq. interFreq evaluated at
@@ -281,11 +180,11 @@ __global__ void k_build_interp_f64(Dims d, const DevState* st, int axis, double*
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= N * N) return;
   const int q = idx / N, j = idx % N;
-  if (st->realign) {
+  if (st->f.realign) {
     I[idx] = q == j ? 1.0 : 0.0;
     return;
   }
-  const double y = st->rs[axis] + st->rd[axis] * (q - 0.5 * (N - 1));
+  const double y = st->f.rs[axis] + st->f.rd[axis] * (q - 0.5 * (N - 1));
   if (fabs(y) > 0.5 * N) {
     I[idx] = 0.0;
     return;
@@ -297,14 +196,14 @@ __global__ void k_build_interp_f64(Dims d, const DevState* st, int axis, double*
 // Stage 0 of the time update: multilinear re-alignment when the frame was
 // re-aligned, otherwise a scaled copy (both fold the normalisation scale in).
 __global__ void k_realign_f64(Dims d, const DevState* st, double* b0, double* b1) {
-  const int cur = st->cur;
+  const int cur = st->f.cur;
   const double* in = cur ? b1 : b0;
   double* out = cur ? b0 : b1;
-  const double ps = st->pscale;
+  const double ps = st->f.pscale;
   const int n = d.nx;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
        p += (long long)gridDim.x * blockDim.x) {
-    if (!st->realign) {
+    if (!st->f.realign) {
       out[p] = ps * in[p];
       continue;
     }
@@ -314,8 +213,8 @@ __global__ void k_realign_f64(Dims d, const DevState* st, double* b0, double* b1
     int f[MAXN];
     double w[MAXN];
     for (int a = 0; a < n; ++a) {
-      double uo = st->b[a];
-      for (int b = 0; b < n; ++b) uo += st->B[a * n + b] * (j[b] - 0.5 * (d.N[b] - 1));
+      double uo = st->f.b[a];
+      for (int b = 0; b < n; ++b) uo += st->f.B[a * n + b] * (j[b] - 0.5 * (d.N[b] - 1));
       z[a] = uo + 0.5 * (d.N[a] - 1);
       const double fl = floor(z[a]);
       f[a] = (int)fmax(fmin(fl, 1e9), -1e9);
@@ -345,7 +244,7 @@ __global__ void k_axis_gemm_f64(Dims d, int axis, const double* W, const DevStat
                                 double* b0, double* b1) {
   __shared__ double Ls[16][17];
   __shared__ double Rs[16][17];
-  const int par = (st->cur + stage) & 1;
+  const int par = (st->f.cur + stage) & 1;
   const double* X = par ? b1 : b0;
   double* Y = par ? b0 : b1;
   const int N = d.N[axis];
@@ -395,15 +294,15 @@ __global__ void k_axis_gemm_f64(Dims d, int axis, const double* W, const DevStat
 // components Psi_E, and the true-Fourier product is formed per component:
 //   T'_C = sum_{|E| even} (-1)^{|E|/2 + |E & C|} Psi_E T_{E ^ C}.
 __global__ void k_psi_f64(Dims d, const DevState* st, int stage, double* b0, double* b1) {
-  const int par = (st->cur + stage) & 1;
+  const int par = (st->f.cur + stage) & 1;
   double* X = par ? b1 : b0;
   const int n = d.nx;
   long long reps = 1;
   int H[MAXN];
   for (int a = 0; a < n; ++a) { H[a] = d.N[a] / 2 + 1; reps *= H[a]; }
-  const int l = st->l;
-  const double g = st->g;
-  const int exact = st->exact;
+  const int l = st->f.l;
+  const double g = st->f.g;
+  const int exact = st->f.exact;
   const int ns = 1 << n;
   const double two_pi = 6.283185307179586476925286766559;
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < reps;
@@ -467,10 +366,25 @@ __global__ void k_psi_f64(Dims d, const DevState* st, int stage, double* b0, dou
   }
 }
 
+// Moment partial sums of a float32 weight array (prior of the tensor-core path).
+__global__ void k_moments_f32(Dims d, const float* X, double* partials) {
+  __shared__ double sm[32 * 10];
+  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
+       p += (long long)gridDim.x * blockDim.x) {
+    int j[MAXN];
+    unflatten(d, p, j);
+    double u[MAXN];
+    for (int a = 0; a < d.nx; ++a) u[a] = j[a] - 0.5 * (d.N[a] - 1);
+    acc_moments(acc, (double)X[p], u, d.nx);
+  }
+  block_sum<10>(acc, sm, partials + blockIdx.x * 10);
+}
+
 __global__ void k_moments_f64(Dims d, const DevState* st, int stage, const double* b0,
                               const double* b1, double* partials) {
   __shared__ double sm[32 * 10];
-  const int par = (st->cur + stage) & 1;
+  const int par = (st->f.cur + stage) & 1;
   const double* X = par ? b1 : b0;
   double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
@@ -494,8 +408,8 @@ __global__ void k_prior_f64(Dims d, const DevState* st, const double* P0inv, con
     unflatten(d, p, j);
     double dx[MAXN];
     for (int a = 0; a < n; ++a) {
-      double x = st->c[a];
-      for (int b = 0; b < n; ++b) x += st->M[a * n + b] * (j[b] - 0.5 * (d.N[b] - 1));
+      double x = st->f.c[a];
+      for (int b = 0; b < n; ++b) x += st->f.M[a * n + b] * (j[b] - 0.5 * (d.N[b] - 1));
       dx[a] = x - m0[a];
     }
     double q = 0.0;
@@ -508,8 +422,8 @@ __global__ void k_prior_f64(Dims d, const DevState* st, const double* P0inv, con
 // Scale the current weights by pscale into a float64 output buffer.
 __global__ void k_export_f64(Dims d, const DevState* st, const double* b0, const double* b1,
                              double* out) {
-  const double* X = st->cur ? b1 : b0;
-  const double ps = st->pscale;
+  const double* X = st->f.cur ? b1 : b0;
+  const double ps = st->f.pscale;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
        p += (long long)gridDim.x * blockDim.x)
     out[p] = ps * X[p];
@@ -540,6 +454,13 @@ void launch_moments_f64(const Dims& d, DevState* st, int stage, double* b0, doub
   k_finalize<<<1, 256, 0, s>>>(d, st, partials, nb, flip, use_pending, pend);
 }
 
+void launch_moments_f32(const Dims& d, DevState* st, const float* X, double* partials,
+                        cudaStream_t s) {
+  const int nb = fp64_partials_blocks(d);
+  k_moments_f32<<<nb, 256, 0, s>>>(d, X, partials);
+  k_finalize<<<1, 256, 0, s>>>(d, st, partials, nb, 0, 0, nullptr);
+}
+
 void launch_meas_f64(const Dims& d, const MeasParams& mp, DevState* st, double* b0, double* b1,
                      double* partials, cudaStream_t s) {
   cudaMemsetAsync(&st->emin_bits, 0xff, sizeof(unsigned long long), s);
@@ -553,7 +474,7 @@ void launch_time_f64(const Dims& d, const TimeConsts& tc, DevState* st, double* 
                      double* partials, double* pend, double* const* interp,
                      double* const* hfwd, double* const* hinv, cudaStream_t s) {
   const int n = d.nx;
-  k_frame<<<1, 32, 0, s>>>(tc, st, pend);
+  k_frame<<<1, MAXL, 0, s>>>(tc, st, pend);
   for (int a = 0; a < n; ++a)
     k_build_interp_f64<<<grid_for((long long)d.N[a] * d.N[a], 256, 1 << 20), 256, 0, s>>>(
         d, st, a, interp[a]);

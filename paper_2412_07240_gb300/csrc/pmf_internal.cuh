@@ -32,6 +32,7 @@ struct TimeConsts {
   double PhiInv[9];  // e^{-A tau}
   double Qb[9];      // int_0^tau e^{-A s} Q e^{-A^T s} ds
   double Estep[9];   // e^{-A dt}
+  double Qt[MAXL][6];  // e^{-A q dt} Q e^{-A^T q dt}, q = 1..l (packed 00,01,02,11,12,22)
 };
 
 // Measurement update parameters (by value).
@@ -42,20 +43,26 @@ struct MeasParams {
   double H[9];
 };
 
-// Per-filter device state.  Frame x = c + M u; weights stored in one of two
-// buffers (cur), true weight = pscale * stored.
-struct DevState {
+// Frame, moments and per-update scalars of one filter (float64).  Frame
+// x = c + M u; weights stored in one of two buffers (cur), true weight =
+// pscale * stored.  Kernels that do scalar work on it copy it to shared or
+// local memory first.
+struct FrameState {
   double c[3], M[9], Minv[9], V;
   double mean[3], cov[9];
-  double S0, pscale;
-  unsigned long long emin_bits;
-  int cur, status, realign, l, exact;
-  double g;
+  double S0, pscale, g;
   // regrid of the current time update
   double rs[3], rd[3];   // separable: u_old_m = rs_m + rd_m * u_new_m
   double B[9], b[3];     // realigned: u_old = B u_new + b
-  // diffusion coefficients per sub-step (Euler) or integrated (exact):
-  // psi_n(k) = 1 + sum_a pa[n][a] kappa_a^2 + sum_{a<b} pb[n][ab] kt_a kt_b
+  int cur, status, realign, l, exact, pad;
+};
+
+// Per-filter device state: the frame state, the exponent minimum of the
+// measurement update and the diffusion coefficients per sub-step (Euler) or
+// integrated (exact): psi_n(k) = 1 + sum_a pa[n][a] kappa_a^2 + sum_{a<b} pb[n][ab] kt_a kt_b.
+struct DevState {
+  FrameState f;
+  unsigned long long emin_bits;
   double pa[MAXL][3];
   double pb[MAXL][3];
 };

@@ -12,6 +12,8 @@ void launch_prior_f64(const Dims& d, const DevState* st, const double* P0inv, co
 void launch_moments_f64(const Dims& d, DevState* st, int stage, double* b0, double* b1,
                         double* partials, int flip, int use_pending, const double* pend,
                         cudaStream_t s);
+void launch_moments_f32(const Dims& d, DevState* st, const float* X, double* partials,
+                        cudaStream_t s);
 void launch_meas_f64(const Dims& d, const MeasParams& mp, DevState* st, double* b0, double* b1,
                      double* partials, cudaStream_t s);
 void launch_time_f64(const Dims& d, const TimeConsts& tc, DevState* st, double* b0, double* b1,

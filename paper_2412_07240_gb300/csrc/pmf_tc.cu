@@ -1,21 +1,971 @@
-// Fused tensor-core path (placeholder until the kernel lands).
+// Fused tensor-core path: one CTA carries one 2-D filter through a whole epoch
+// with its grid resident on chip.
+//
+//   measurement update (eq. filt)   registers: likelihood relative to the frame
+//                                   centre, exponent minimum, moments
+//   frame (float64, one thread)     regrid decision, diffusion coefficients
+//   R1  regrid along axis 1         tcgen05 GEMM, periodic-sinc matrix I1
+//   F1  Hartley along axis 1        tcgen05 GEMM, H1 (TMA bulk copy)
+//   R0  regrid along axis 0         tcgen05 GEMM, operand read MN-major
+//   F0  Hartley along axis 0        tcgen05 GEMM, H0
+//   Psi diffusion multiplier and trace factor with the separable-to-2-D
+//       Hartley parity fix-up (Sec. V-B algorithm steps 2-4)
+//   V0  inverse along axis 0        tcgen05 GEMM, H0 (still resident)
+//   V1  inverse along axis 1        tcgen05 GEMM, H1, operand MN-major
+//   normalisation and moments (step 6), weights written back to HBM.
+//
+// Every GEMM is D[128 lines x Nout] = A[128 x K] * W[Nout x K]^T with M = 128
+// lines (unused lines ignored), the accumulator in TMEM and both operands in
+// shared memory in the no-swizzle canonical layout of 8-row x 16-byte core
+// matrices, 16 core matrices per 8-row block.  The epilogue thread that owns
+// TMEM lane r writes row r of the next operand, so the operand of the next
+// GEMM along the other axis is the same bytes read MN-major: no transposes.
+//
+// Precisions: FP16X3 / BF16X3 split each operand into hi + lo 16-bit planes and
+// issue hi*hi + hi*lo + lo*hi (FP32 accumulate); FP16 operands carry a
+// power-of-two scale per stage (max |value| -> 2^14).  TF32 issues one
+// kind::tf32 product on float32 planes.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "pmf_device.cuh"
+#include "pmf_kernels.cuh"
 #include "pmf_tc.cuh"
 
 namespace pmf {
 
-int tc_supported(const pmf_config*, std::string* why) {
-  *why = "tensor-core path not built";
-  return PMF_ERR_UNSUPPORTED;
+namespace {
+
+constexpr int kThreads = 512;               // 16 warps: 4 TMEM lane quadrants x 4 column groups
+constexpr int kPlane = 32768;                // bytes of one 16-bit operand plane
+constexpr int kOffA = 0;                     // A operand planes [0, 64K)
+constexpr int kOffW = 65536;                 // W operand planes [64K, 128K)
+constexpr int kOffS = 131072;                // float32 staging, 128 rows x kSStr
+constexpr int kSStr = 132;                   // staging row stride (floats; conflict-free row access)
+constexpr int kSmemBytes = kOffS + 128 * kSStr * 4;
+constexpr uint32_t kTmemCols = 128;
+constexpr long long kSpin = 1LL << 22;       // bounded mbarrier polls
+
+struct FusedJob {
+  DevState* st;
+  float* buf0;
+  float* buf1;
+  const uint8_t* hart[2];   // per axis: Hartley planes (hi then lo for 16-bit formats)
+  const float* sctab[2];    // per axis: (cos, sin)(pi m / N), m = -N..N
+  int N0, N1, do_meas, do_time;
+  MeasParams mp;
+  TimeConsts tc;
+};
+
+// --- PTX wrappers ------------------------------------------------------------
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
-int tc_build_tables(const pmf_config*, TcTables*, std::string* why) {
-  *why = "tensor-core path not built";
-  return PMF_ERR_UNSUPPORTED;
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
-void tc_free_tables(TcTables*) {}
-int tc_prior(const Dims&, DevState*, const double*, float*, double*, cudaStream_t) { return 0; }
-int tc_step(const Dims&, const pmf_config&, const TcTables*, const MeasParams*, const TimeConsts*,
-            DevState*, float*, float*, cudaStream_t) {
-  return 0;
+
+// kind::f16 / kind::tf32 instruction descriptor, FP32 accumulate, M = 128.
+__device__ __forceinline__ uint32_t idesc(int fmt, int a_mn, int n) {
+  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)a_mn << 15) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+               "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+               "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+               "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  uint32_t done = 0;
+  for (long long it = 0; it < kSpin; ++it) {
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 "selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(mbar), "r"(phase));
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// Four consecutive accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ float4 tmem_ld4(uint32_t taddr) {
+  uint32_t r0, r1, r2, r3;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+               "tcgen05.wait::ld.sync.aligned;"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(taddr)
+               : "memory");
+  return make_float4(__uint_as_float(r0), __uint_as_float(r1), __uint_as_float(r2), __uint_as_float(r3));
+}
+
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// --- operand layout ------------------------------------------------------------
+// Element (r, c) of a 128-row operand plane: 8-row x 16-byte core matrices,
+// 16 (16-bit) or 32 (32-bit) core matrices per 8-row block.
+template <int P>
+struct Fmt;
+template <>
+struct Fmt<PMF_PREC_FP16X3> {
+  static constexpr int esz = 2, rowblk = 2048, planes = 2, kper = 16, code = 0;
+};
+template <>
+struct Fmt<PMF_PREC_BF16X3> {
+  static constexpr int esz = 2, rowblk = 2048, planes = 2, kper = 16, code = 1;
+};
+template <>
+struct Fmt<PMF_PREC_TF32> {
+  static constexpr int esz = 4, rowblk = 4096, planes = 1, kper = 8, code = 2;
+};
+
+template <int P>
+__device__ __forceinline__ uint32_t op_off(int r, int c) {
+  constexpr int epc = 16 / Fmt<P>::esz;
+  return (uint32_t)((r >> 3) * Fmt<P>::rowblk + (c / epc) * 128 + (r & 7) * 16 + (c % epc) * Fmt<P>::esz);
+}
+
+__device__ __forceinline__ uint32_t h2u(__half2 h) { return *(uint32_t*)&h; }
+__device__ __forceinline__ uint32_t b2u(__nv_bfloat162 h) { return *(uint32_t*)&h; }
+
+// Elements (r, c..c+3) (c a multiple of 4) of the operand planes at base, scaled
+// by s: split into hi + lo 16-bit planes, or one float32 plane for TF32.
+template <int P>
+__device__ __forceinline__ void store4(uint8_t* base, int r, int c, float4 v, float s) {
+  v.x *= s;
+  v.y *= s;
+  v.z *= s;
+  v.w *= s;
+  const uint32_t off = op_off<P>(r, c);
+  if constexpr (P == PMF_PREC_TF32) {
+    *(float4*)(base + off) = v;
+  } else if constexpr (P == PMF_PREC_FP16X3) {
+    const __half2 h0 = __floats2half2_rn(v.x, v.y), h1 = __floats2half2_rn(v.z, v.w);
+    const float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
+    const __half2 l0 = __floats2half2_rn(v.x - f0.x, v.y - f0.y), l1 = __floats2half2_rn(v.z - f1.x, v.w - f1.y);
+    *(uint2*)(base + off) = make_uint2(h2u(h0), h2u(h1));
+    *(uint2*)(base + kPlane + off) = make_uint2(h2u(l0), h2u(l1));
+  } else {
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y), h1 = __floats2bfloat162_rn(v.z, v.w);
+    const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+    const __nv_bfloat162 l0 = __floats2bfloat162_rn(v.x - f0.x, v.y - f0.y);
+    const __nv_bfloat162 l1 = __floats2bfloat162_rn(v.z - f1.x, v.w - f1.y);
+    *(uint2*)(base + off) = make_uint2(b2u(h0), b2u(h1));
+    *(uint2*)(base + kPlane + off) = make_uint2(b2u(l0), b2u(l1));
+  }
+}
+
+// TF32 operands are read K-major only: elements (c..c+3, r) of the float32 plane.
+__device__ __forceinline__ void store4_t(uint8_t* base, int r, int c, float4 v, float s) {
+  *(float*)(base + op_off<PMF_PREC_TF32>(c + 0, r)) = v.x * s;
+  *(float*)(base + op_off<PMF_PREC_TF32>(c + 1, r)) = v.y * s;
+  *(float*)(base + op_off<PMF_PREC_TF32>(c + 2, r)) = v.z * s;
+  *(float*)(base + op_off<PMF_PREC_TF32>(c + 3, r)) = v.w * s;
+}
+
+__device__ __forceinline__ float amax4(float m, float4 v) {
+  return fmaxf(fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y))), fmaxf(fabsf(v.z), fabsf(v.w)));
+}
+
+// Power-of-two scale bringing max |v| to [2^13, 2^14) for FP16 operands; 1 otherwise.
+template <int P>
+__device__ __forceinline__ float op_scale(float mx) {
+  if (P != PMF_PREC_FP16X3 || !(mx > 0.0f) || !isfinite(mx)) return 1.0f;
+  int e;
+  frexpf(mx, &e);
+  return ldexpf(1.0f, 14 - e);
+}
+
+struct Shared {
+  FrameState fs;           // working copy of the filter's frame state
+  uint64_t mbar_mma, mbar_tma;
+  uint32_t tmem;
+  int abort, degenerate;
+  float redf[2][16];
+  double redd[16][6];
+  double tot[10];
+  double pend[24];
+  double Mpi[9];
+  float pa[MAXL][2];
+  float pb[MAXL];
+  float g, ps, gsc;
+  // frame-relative measurement constants
+  float mc[2], mM[4], mr0[3], mRinv[9], mH[6], mcn;
+  // regrid rows
+  int ri[128];
+  float rf[128], rS[128], rcf[128], rsf[128];
+  unsigned char rzero[128];
+};
+
+// Block max of non-negative per-thread values (result in every thread).
+__device__ __forceinline__ float block_max(Shared& sh, float v, int slot) {
+  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) sh.redf[slot][threadIdx.x >> 5] = v;
+  __syncthreads();
+  float m = 0.0f;
+#pragma unroll
+  for (int w = 0; w < kThreads / 32; ++w) m = fmaxf(m, sh.redf[slot][w]);
+  return m;
+}
+
+__device__ __forceinline__ float block_min(Shared& sh, float v, int slot) {
+  for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) sh.redf[slot][threadIdx.x >> 5] = v;
+  __syncthreads();
+  float m = INFINITY;
+#pragma unroll
+  for (int w = 0; w < kThreads / 32; ++w) m = fminf(m, sh.redf[slot][w]);
+  return m;
+}
+
+// Compensated (Kahan) float32 accumulation of the moment sums of one thread.
+struct Moments {
+  float s[6], c[6];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) s[i] = c[i] = 0.0f;
+  }
+  __device__ __forceinline__ void add1(int i, float x) {
+    const float y = x - c[i];
+    const float t = s[i] + y;
+    c[i] = (t - s[i]) - y;
+    s[i] = t;
+  }
+  // S0, S1 (u0, u1), S2 (u0u0, u0u1, u1u1)
+  __device__ __forceinline__ void add(float x, float u0, float u1) {
+    add1(0, x);
+    add1(1, x * u0);
+    add1(2, x * u1);
+    add1(3, x * u0 * u0);
+    add1(4, x * u0 * u1);
+    add1(5, x * u1 * u1);
+  }
+};
+
+// Sum the per-thread moment sums over the block in float64 into sh.tot
+// ({S0, S1[3], S2[6]} layout); valid in thread 0 after the call.
+__device__ __forceinline__ void block_moments(Shared& sh, const Moments& m) {
+  double a[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    a[i] = (double)m.s[i] - (double)m.c[i];
+    for (int o = 16; o; o >>= 1) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
+  }
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int i = 0; i < 6; ++i) sh.redd[threadIdx.x >> 5][i] = a[i];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int l = threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      double v = l < kThreads / 32 ? sh.redd[l][i] : 0.0;
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      a[i] = v;
+    }
+    if (l == 0) {
+      sh.tot[0] = a[0];
+      sh.tot[1] = a[1];
+      sh.tot[2] = a[2];
+      sh.tot[3] = 0.0;
+      sh.tot[4] = a[3];
+      sh.tot[5] = a[4];
+      sh.tot[6] = 0.0;
+      sh.tot[7] = a[5];
+      sh.tot[8] = 0.0;
+      sh.tot[9] = 0.0;
+    }
+  }
+}
+
+// 1/2 r^T R^{-1} r with the residual formed relative to the frame centre c:
+// d = M u, and r = r0 - (change of h from c to c + d), r0 = z - h(c) in float64;
+// linear h: r = r0 - H d; range: |c + d| - |c| = (2 c.d + |d|^2) / (|c + d| + |c|).
+__device__ __forceinline__ float meas_e(const Shared& sh, int kind, int nz, float u0, float u1) {
+  const float d0 = sh.mM[0] * u0 + sh.mM[1] * u1, d1 = sh.mM[2] * u0 + sh.mM[3] * u1;
+  float r[2];
+  if (kind == PMF_MEAS_LINEAR) {
+    r[0] = sh.mr0[0] - (sh.mH[0] * d0 + sh.mH[1] * d1);
+    r[1] = nz > 1 ? sh.mr0[1] - (sh.mH[2] * d0 + sh.mH[3] * d1) : 0.0f;
+  } else {
+    const float x0 = sh.mc[0] + d0, x1 = sh.mc[1] + d1;
+    const float den = sqrtf(x0 * x0 + x1 * x1) + sh.mcn;
+    const float num = 2.0f * (sh.mc[0] * d0 + sh.mc[1] * d1) + d0 * d0 + d1 * d1;
+    r[0] = sh.mr0[0] - (den > 0.0f ? num / den : 0.0f);
+    r[1] = 0.0f;
+  }
+  float e = r[0] * sh.mRinv[0] * r[0];
+  if (nz > 1) e += 2.0f * r[0] * sh.mRinv[1] * r[1] + r[1] * sh.mRinv[3] * r[1];
+  return 0.5f * e;
+}
+
+// Issue one GEMM stage (one thread): D = A * W^T, A read K-major or MN-major.
+// For the split formats the two correction products (hi*lo, lo*hi; ~2^-11 of
+// the result) are accumulated first, while the FP32 accumulator is small, and
+// the hi*hi products last, so that only those see roundings at full magnitude.
+template <int P>
+__device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t a_base, int a_mn, uint32_t w_base,
+                                            int nout, int K, uint32_t mbar) {
+  constexpr uint32_t rb = Fmt<P>::rowblk;
+  constexpr int kp = Fmt<P>::kper;
+  const uint32_t id = idesc(Fmt<P>::code, a_mn, nout);
+  // K step of one instruction: 32 bytes = 2 core matrices along K (K-major),
+  // or kp rows = kp/8 row blocks (MN-major)
+  auto adesc = [&](uint32_t base, int ks) {
+    return a_mn ? sdesc(base + ks * (kp / 8) * rb, rb, 128) : sdesc(base + ks * 256, 128, rb);
+  };
+  if constexpr (Fmt<P>::planes == 1) {
+    for (int ks = 0; ks < K / kp; ++ks)
+      mma_tf32(tmem, adesc(a_base, ks), sdesc(w_base + ks * 256, 128, rb), id, ks > 0);
+  } else {
+    for (int ks = 0; ks < K / kp; ++ks) {
+      mma_f16(tmem, adesc(a_base, ks), sdesc(w_base + kPlane + ks * 256, 128, rb), id, ks > 0);
+      mma_f16(tmem, adesc(a_base + kPlane, ks), sdesc(w_base + ks * 256, 128, rb), id, 1);
+    }
+    for (int ks = 0; ks < K / kp; ++ks)
+      mma_f16(tmem, adesc(a_base, ks), sdesc(w_base + ks * 256, 128, rb), id, 1);
+  }
+  mma_commit(mbar);
+}
+
+// Row parameters of the separable regrid along one axis (float64 per row):
+// y_n = rs + rd u_n, z_n = y_n + (N-1)/2 = i_n + f_n with |f_n| <= 1/2.
+__device__ void regrid_rows(Shared& sh, const FrameState& fs, int axis, int N) {
+  for (int n = threadIdx.x; n < N; n += kThreads) {
+    const double y = fs.rs[axis] + fs.rd[axis] * (n - 0.5 * (N - 1));
+    const double z = y + 0.5 * (N - 1);
+    const double i = rint(fmin(fmax(z, -1.0), (double)N + 1.0));
+    const float f = (float)(z - i);
+    sh.ri[n] = (int)i;
+    sh.rf[n] = f;
+    sh.rzero[n] = !(fabs(y) <= 0.5 * N);  // also zero (and skip the table) for a non-finite y
+    sh.rS[n] = sinpif(f);
+    float s, c;
+    sincospif(f / (float)N, &s, &c);
+    sh.rsf[n] = s;
+    sh.rcf[n] = c;
+  }
+}
+
+// Periodic-sinc regrid matrix of one axis into the W planes (rows: new nodes,
+// columns: old nodes), scaled by sw:
+// I[n, j] = sin(pi v) / (N tan(pi v / N)), v = y_n - u_j = m + f_n, m = i_n - j,
+// evaluated as (-1)^m sin(pi f) cos(pi v/N) / (N sin(pi v/N)) with the angle
+// pi v / N split into the tabulated pi m / N and the per-row pi f / N.
+template <int P>
+__device__ void build_interp(const Shared& sh, uint8_t* W, int N, const float* sctab, float sw, int realign) {
+  const int q4 = N / 4;
+  for (int t = threadIdx.x; t < N * q4; t += kThreads) {
+    const int n = t / q4, c = (t % q4) * 4;
+    float k[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = c + i;
+      float v;
+      if (realign) {
+        v = n == j ? 1.0f : 0.0f;
+      } else if (sh.rzero[n]) {
+        v = 0.0f;
+      } else {
+        const int m = sh.ri[n] - j;
+        const float f = sh.rf[n];
+        if (m == 0 && f == 0.0f) {
+          v = 1.0f;
+        } else {
+          const float cm = sctab[2 * (m + N)], sm = sctab[2 * (m + N) + 1];
+          const float sv = sm * sh.rcf[n] + cm * sh.rsf[n];
+          const float cv = cm * sh.rcf[n] - sm * sh.rsf[n];
+          v = ((m & 1) ? -1.0f : 1.0f) * sh.rS[n] * cv / ((float)N * sv);
+        }
+      }
+      k[i] = v;
+    }
+    store4<P>(W, n, c, make_float4(k[0], k[1], k[2], k[3]), sw);
+  }
+}
+
+// Staging rows r < nr, columns < nc -> operand planes (scaled by s).
+template <int P>
+__device__ __forceinline__ void stage_to_operand(uint8_t* A, const float* S, int nr, int nc, float s) {
+  const int q4 = nc / 4;
+  for (int t = threadIdx.x; t < nr * q4; t += kThreads) {
+    const int r = t / q4, c = (t % q4) * 4;
+    store4<P>(A, r, c, *(const float4*)(S + r * kSStr + c), s);
+  }
+}
+
+__device__ __forceinline__ float stage_max(const float* S, int nr, int nc) {
+  const int q4 = nc / 4;
+  float m = 0.0f;
+  for (int t = threadIdx.x; t < nr * q4; t += kThreads) {
+    const int r = t / q4, c = (t % q4) * 4;
+    m = amax4(m, *(const float4*)(S + r * kSStr + c));
+  }
+  return m;
+}
+
+// Diffusion multiplier and trace factor in the Hartley domain (Sec. V-B
+// algorithm steps 2-4) on the staging tile T[k1][k0], one thread per orbit
+// {(+-k0, +-k1)}: with S_s the four separable coefficients (bit 0 of s flips
+// k0, bit 1 flips k1), T_B their parity components and Psi_E those of the
+// jointly even multiplier (E = 0 even-even, E = 3 odd-odd),
+//   T'_C = Psi_0 T_C - (-1)^{|3 & C|} Psi_3 T_{3 ^ C},
+// then back to the separable coefficients; gsc = trace factor / (N0 N1).
+__device__ void psi_stage(const Shared& sh, float* S, int N0, int N1, int l, int exact) {
+  const int H0n = N0 / 2 + 1, H1n = N1 / 2 + 1;
+  const float two_pi = 6.28318530717958647692f;
+  for (int r = threadIdx.x; r < H0n * H1n; r += kThreads) {
+    const int k0 = r % H0n, k1 = r / H0n;
+    const int i0[2] = {k0, (N0 - k0) % N0};
+    const int i1[2] = {k1, (N1 - k1) % N1};
+    float Sv[4], Ps[2];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) Sv[s] = S[i1[s >> 1] * kSStr + i0[s & 1]];
+    // Psi(k0, k1) and Psi(-k0, k1); the multiplier is jointly even
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int a0 = i0[s], a1 = i1[0];
+      const int w0 = a0 < N0 / 2 ? a0 : a0 - N0, w1 = a1 < N1 / 2 ? a1 : a1 - N1;
+      const float k0f = two_pi * w0 / N0, k1f = two_pi * w1 / N1;
+      const float t0 = (2 * a0 == N0) ? 0.0f : k0f, t1 = (2 * a1 == N1) ? 0.0f : k1f;
+      const float q0 = k0f * k0f, q1 = k1f * k1f, qx = t0 * t1;
+      float den = 1.0f, ex = 0.0f;
+      for (int qq = 0; qq < l; ++qq) {
+        const float e = sh.pa[qq][0] * q0 + sh.pa[qq][1] * q1 + sh.pb[qq] * qx;
+        den *= 1.0f + e;
+        ex += e;
+      }
+      Ps[s] = exact ? expf(-ex) : 1.0f / den;
+    }
+    const float pe0 = 0.5f * (Ps[0] + Ps[1]), pe3 = 0.5f * (Ps[0] - Ps[1]);
+    float T[4];
+#pragma unroll
+    for (int B = 0; B < 4; ++B) {
+      float tb = 0.0f;
+#pragma unroll
+      for (int s = 0; s < 4; ++s) tb += ((__popc(B & s) & 1) ? -1.0f : 1.0f) * Sv[s];
+      T[B] = 0.25f * tb;
+    }
+    float Tp[4];
+#pragma unroll
+    for (int C = 0; C < 4; ++C) {
+      const float sg3 = ((1 + __popc(3 & C)) & 1) ? -1.0f : 1.0f;
+      Tp[C] = (pe0 * T[C] + sg3 * pe3 * T[3 ^ C]) * sh.gsc;
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      float o = 0.0f;
+#pragma unroll
+      for (int C = 0; C < 4; ++C) o += ((__popc(C & s) & 1) ? -1.0f : 1.0f) * Tp[C];
+      S[i1[s >> 1] * kSStr + i0[s & 1]] = o;
+    }
+  }
+}
+
+template <int P>
+__device__ void fused2d(const FusedJob& job, uint8_t* smem) {
+  __shared__ Shared sh;
+  DevState* st = job.st;
+  FrameState& fs = sh.fs;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & 127, cg = tid >> 7;     // TMEM lane and column group of this thread
+  const int N0 = job.N0, N1 = job.N1;
+  uint8_t* A = smem + kOffA;
+  uint8_t* W = smem + kOffW;
+  float* S = (float*)(smem + kOffS);
+  const uint32_t mb_mma = su32(&sh.mbar_mma), mb_tma = su32(&sh.mbar_tma);
+  uint32_t ph_mma = 0, ph_tma = 0;
+  const float sw = P == PMF_PREC_FP16X3 ? 16384.0f : 1.0f;   // scale of the matrix operands
+  constexpr int kFsWords = sizeof(FrameState) / 8;
+
+  for (int i = tid; i < kFsWords; i += kThreads)
+    ((unsigned long long*)&fs)[i] = ((const unsigned long long*)&st->f)[i];
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_mma));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_tma));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    sh.abort = 0;
+    sh.degenerate = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&sh.tmem)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  const uint32_t tmem = sh.tmem;
+  const uint32_t tlane = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+
+  // ---- weights -> staging rows j0, columns j1 (float32, normalised) ----
+  const int cur = fs.cur;
+  const float* in = cur ? job.buf1 : job.buf0;
+  float* out = cur ? job.buf0 : job.buf1;
+  const int q1 = N1 / 4, np4 = N0 * q1;
+  {
+    const float ps = (float)fs.pscale;
+    for (int t = tid; t < np4; t += kThreads) {
+      const int r = t / q1, c = (t % q1) * 4;
+      float4 x = *(const float4*)(in + (size_t)r * N1 + c);
+      x.x *= ps;
+      x.y *= ps;
+      x.z *= ps;
+      x.w *= ps;
+      *(float4*)(S + r * kSStr + c) = x;
+    }
+  }
+  float smax = 0.0f;   // max |weight| (operand scale of the first GEMM)
+
+  // ---- measurement update (eq. filt) ----
+  if (job.do_meas) {
+    if (tid == 0) {
+      const MeasParams& mp = job.mp;
+      const double c0 = fs.c[0], c1 = fs.c[1];
+      sh.mc[0] = (float)c0;
+      sh.mc[1] = (float)c1;
+      for (int i = 0; i < 4; ++i) sh.mM[i] = (float)fs.M[i];
+      for (int i = 0; i < mp.nz * mp.nz; ++i) sh.mRinv[i] = (float)mp.Rinv[i];
+      if (mp.kind == PMF_MEAS_LINEAR) {
+        for (int i = 0; i < mp.nz; ++i) {
+          sh.mr0[i] = (float)(mp.z[i] - (mp.H[i * 2] * c0 + mp.H[i * 2 + 1] * c1));
+          for (int b = 0; b < 2; ++b) sh.mH[i * 2 + b] = (float)mp.H[i * 2 + b];
+        }
+      } else {
+        const double cn = sqrt(c0 * c0 + c1 * c1);
+        sh.mcn = (float)cn;
+        sh.mr0[0] = (float)(mp.z[0] - cn);
+      }
+    }
+    __syncthreads();
+    const int kind = job.mp.kind, nz = job.mp.nz;
+    const int npts = N0 * N1;
+    float emin = INFINITY;
+    for (int p = tid; p < npts; p += kThreads) {
+      const int r = p / N1, c = p - r * N1;
+      emin = fminf(emin, meas_e(sh, kind, nz, r - 0.5f * (N0 - 1), c - 0.5f * (N1 - 1)));
+    }
+    emin = block_min(sh, emin, 0);
+    Moments mo;
+    mo.zero();
+    for (int p = tid; p < npts; p += kThreads) {
+      const int r = p / N1, c = p - r * N1;
+      const float u0 = r - 0.5f * (N0 - 1), u1 = c - 0.5f * (N1 - 1);
+      const float x = S[r * kSStr + c] * expf(-(meas_e(sh, kind, nz, u0, u1) - emin));
+      S[r * kSStr + c] = x;
+      mo.add(x, u0, u1);
+      smax = fmaxf(smax, x);
+    }
+    block_moments(sh, mo);
+    if (tid == 0) {
+      if (!finalize_core(2, &fs, sh.tot, 0, nullptr)) {
+        sh.degenerate = 1;
+      } else {
+        sh.ps = (float)fs.pscale;   // the staged weights times ps are normalised
+        fs.pscale = 1.0;
+        fs.S0 = 1.0 / fs.V;
+      }
+    }
+    __syncthreads();
+    if (sh.degenerate) goto done;
+    if (!job.do_time) {
+      const float ps = sh.ps;
+      for (int t = tid; t < np4; t += kThreads) {
+        const int r = t / q1, c = (t % q1) * 4;
+        float4 x = *(const float4*)(S + r * kSStr + c);
+        x.x *= ps;
+        x.y *= ps;
+        x.z *= ps;
+        x.w *= ps;
+        *(float4*)(out + (size_t)r * N1 + c) = x;
+      }
+      if (tid == 0) fs.cur = cur ^ 1;
+      goto done;
+    }
+  } else {
+    smax = stage_max(S, N0, N1);
+  }
+
+  if (job.do_time) {
+    // ---- frame: regrid decision (one thread) and sub-step coefficients ----
+    if (tid == 0) {
+      frame_scalar<2>(job.tc, &fs, sh.pend, sh.Mpi);
+      sh.g = (float)fs.g;
+      sh.gsc = (float)(fs.g / ((double)N0 * (double)N1));
+    }
+    __syncthreads();
+    const int realign = fs.realign;
+    const int l = fs.l;
+    const int exact = fs.exact;
+    for (int q = tid; q < l; q += kThreads) {
+      double pa[3], pb[3];
+      frame_substep<2>(job.tc, sh.Mpi, q, pa, pb);
+      sh.pa[q][0] = (float)pa[0];
+      sh.pa[q][1] = (float)pa[1];
+      sh.pb[q] = (float)pb[0];
+    }
+    if (realign) {
+      // multilinear re-alignment: gather into the (free) W region, copy back
+      float* G = (float*)W;
+      const int npts = N0 * N1;
+      for (int p = tid; p < npts; p += kThreads) {
+        const int r = p / N1, c = p - r * N1;
+        const double u0 = r - 0.5 * (N0 - 1), u1 = c - 0.5 * (N1 - 1);
+        // old-grid index coordinates in float64 (positions span +-N/2 nodes)
+        const double z0 = fma(fs.B[0], u0, fma(fs.B[1], u1, fs.b[0] + 0.5 * (N0 - 1)));
+        const double z1 = fma(fs.B[2], u0, fma(fs.B[3], u1, fs.b[1] + 0.5 * (N1 - 1)));
+        const double f0 = floor(z0), f1 = floor(z1);
+        const float w0 = (float)(z0 - f0), w1 = (float)(z1 - f1);
+        const int i0 = (int)fmax(fmin(f0, 1e6), -1e6), i1 = (int)fmax(fmin(f1, 1e6), -1e6);
+        float s = 0.0f;
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          const int a = i0 + (cc & 1), b = i1 + (cc >> 1);
+          const float wt = ((cc & 1) ? w0 : 1.0f - w0) * ((cc >> 1) ? w1 : 1.0f - w1);
+          if (a >= 0 && a < N0 && b >= 0 && b < N1) s += wt * S[a * kSStr + b];
+        }
+        G[p] = s;
+      }
+      __syncthreads();
+      smax = 0.0f;
+      for (int p = tid; p < npts; p += kThreads) {
+        const int r = p / N1, c = p - r * N1;
+        S[r * kSStr + c] = G[p];
+        smax = fmaxf(smax, fabsf(G[p]));
+      }
+    } else {
+      regrid_rows(sh, fs, 1, N1);
+    }
+    __syncthreads();
+
+    // ---- R1 operand (rows j0, columns j1; K-major) and the matrix I1 ----
+    float sa = op_scale<P>(block_max(sh, smax, 1));
+    stage_to_operand<P>(A, S, N0, N1, sa);
+    build_interp<P>(sh, W, N1, job.sctab[1], sw, realign);
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_after_sync();
+      issue_stage<P>(tmem, su32(A), 0, su32(W), N1, N1, mb_mma);
+    }
+    float inv_scale = 1.0f / (sa * sw);
+
+    // Stages after R1: F1, R0, F0, V0, V1.  Epilogue of GEMM `stage` (0 = R1)
+    // writes the operand of GEMM stage+1.
+    for (int stage = 0; stage < 6; ++stage) {
+      const bool ok = mbar_wait(mb_mma, ph_mma);
+      ph_mma ^= 1;
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) sh.abort = 1;
+        break;
+      }
+      tc_after_sync();
+      // accumulator of GEMM `stage`: valid lanes and columns
+      const int nlane = (stage == 0 || stage == 1 || stage == 5) ? N0 : N1;
+      const int nout = (stage <= 1 || stage == 5) ? N1 : N0;
+      const int ncol = nout / 4, c0 = cg * ncol;   // this thread's columns
+      const bool lane_ok = row < nlane;
+      if (stage == 5) {
+        // final weights: rows j0, columns j1 -> staging (true scale)
+        for (int c = 0; c < ncol; c += 4) {
+          float4 v = tmem_ld4(tlane + c0 + c);
+          v.x *= inv_scale;
+          v.y *= inv_scale;
+          v.z *= inv_scale;
+          v.w *= inv_scale;
+          *(float4*)(S + row * kSStr + c0 + c) = v;
+        }
+        tc_before_sync();
+        __syncthreads();
+        break;
+      }
+      if (stage == 3) {
+        // F0 finished: spectrum T[k1][k0] -> staging, multiplier, operand of V0
+        for (int c = 0; c < ncol; c += 4) {
+          float4 v = tmem_ld4(tlane + c0 + c);
+          v.x *= inv_scale;
+          v.y *= inv_scale;
+          v.z *= inv_scale;
+          v.w *= inv_scale;
+          *(float4*)(S + row * kSStr + c0 + c) = v;
+        }
+        tc_before_sync();
+        __syncthreads();
+        psi_stage(sh, S, N0, N1, l, exact);
+        __syncthreads();
+        sa = op_scale<P>(block_max(sh, stage_max(S, N1, N0), stage & 1));
+        stage_to_operand<P>(A, S, N1, N0, sa);
+      } else {
+        float m = 0.0f;
+        for (int c = 0; c < ncol; c += 4) m = amax4(m, tmem_ld4(tlane + c0 + c));
+        sa = op_scale<P>(block_max(sh, lane_ok ? m * inv_scale : 0.0f, stage & 1));
+        // R0 and V1 read this operand MN-major; TF32 gets it written transposed
+        const bool tr = P == PMF_PREC_TF32 && (stage == 1 || stage == 4);
+        for (int c = 0; c < ncol; c += 4) {
+          float4 v = tmem_ld4(tlane + c0 + c);
+          v.x *= inv_scale;
+          v.y *= inv_scale;
+          v.z *= inv_scale;
+          v.w *= inv_scale;
+          if (tr)
+            store4_t(A, row, c0 + c, v, sa);
+          else
+            store4<P>(A, row, c0 + c, v, sa);
+        }
+        tc_before_sync();
+      }
+      // matrix of the next GEMM: F1 <- H1, R0 <- I0, F0 <- H0, V0 keeps H0, V1 <- H1
+      int mat = -1;
+      if (stage == 0 || stage == 4) mat = 1;
+      if (stage == 2) mat = 0;
+      if (stage == 1) {
+        __syncthreads();
+        regrid_rows(sh, fs, 0, N0);
+        __syncthreads();
+        build_interp<P>(sh, W, N0, job.sctab[0], sw, realign);
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc_after_sync();
+        bool ok2 = true;
+        if (mat >= 0) {
+          const int Nm = mat == 0 ? N0 : N1;
+          const uint32_t pbytes = (uint32_t)Nm * (uint32_t)(Fmt<P>::rowblk / 8);
+          expect_tx(mb_tma, pbytes * Fmt<P>::planes);
+          for (int pl = 0; pl < Fmt<P>::planes; ++pl)
+            bulk_load(su32(W) + pl * kPlane, job.hart[mat] + (size_t)pl * pbytes, pbytes, mb_tma);
+          ok2 = mbar_wait(mb_tma, ph_tma);
+        }
+        if (!ok2) {
+          sh.abort = 1;
+        } else {
+          // stage+1: F1 (K-major), R0 (MN), F0 (K), V0 (K), V1 (MN)
+          const int a_mn = (P != PMF_PREC_TF32) && (stage == 1 || stage == 4);
+          const int nn = (stage == 0 || stage == 4) ? N1 : N0;
+          issue_stage<P>(tmem, su32(A), a_mn, su32(W), nn, nn, mb_mma);
+        }
+      }
+      if (mat >= 0) ph_tma ^= 1;
+      inv_scale = 1.0f / (sa * sw);
+      __syncthreads();
+      if (sh.abort) break;
+    }
+    if (sh.abort) {
+      if (tid == 0) fs.status = PMF_ERR_TIMEOUT;
+      goto done;
+    }
+
+    // ---- normalisation, moments and write-back (rows j0, columns j1) ----
+    {
+      Moments mo;
+      mo.zero();
+      for (int t = tid; t < np4; t += kThreads) {
+        const int r = t / q1, c = (t % q1) * 4;
+        const float4 x = *(const float4*)(S + r * kSStr + c);
+        *(float4*)(out + (size_t)r * N1 + c) = x;
+        const float u0 = r - 0.5f * (N0 - 1), u1 = c - 0.5f * (N1 - 1);
+        mo.add(x.x, u0, u1);
+        mo.add(x.y, u0, u1 + 1.0f);
+        mo.add(x.z, u0, u1 + 2.0f);
+        mo.add(x.w, u0, u1 + 3.0f);
+      }
+      block_moments(sh, mo);
+      if (tid == 0 && finalize_core(2, &fs, sh.tot, 1, sh.pend)) fs.cur = cur ^ 1;
+    }
+  }
+
+done:
+  tc_before_sync();
+  __syncthreads();
+  for (int i = tid; i < kFsWords; i += kThreads)
+    ((unsigned long long*)&st->f)[i] = ((const unsigned long long*)&fs)[i];
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads, 1) k_fused2d(const __grid_constant__ FusedJob job) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  fused2d<P>(job, smem);
+}
+
+// Prior weights exp(-1/2 (x - m0)^T P0^{-1} (x - m0)) on the initial frame (float32 storage).
+__global__ void k_prior_f32(Dims d, const DevState* st, const double* aux, float* X) {
+  const int n = d.nx;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
+       p += (long long)gridDim.x * blockDim.x) {
+    int j[MAXN];
+    long long t = p;
+    for (int m = n - 1; m >= 0; --m) { j[m] = (int)(t % d.N[m]); t /= d.N[m]; }
+    double dx[MAXN];
+    for (int a = 0; a < n; ++a) {
+      double x = st->f.c[a];
+      for (int b = 0; b < n; ++b) x += st->f.M[a * n + b] * (j[b] - 0.5 * (d.N[b] - 1));
+      dx[a] = x - aux[9 + a];
+    }
+    double q = 0.0;
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b < n; ++b) q += dx[a] * aux[a * n + b] * dx[b];
+    X[p] = (float)exp(-0.5 * q);
+  }
+}
+
+// Host: split 16-bit (or float32) planes of a matrix in the operand layout.
+void split_planes(const std::vector<double>& Mt, int rows, int cols, int prec, double scale,
+                  std::vector<uint8_t>& out) {
+  const int esz = prec == PMF_PREC_TF32 ? 4 : 2;
+  const int epc = 16 / esz, rowblk = (128 / epc) * 128;
+  const size_t plane = (size_t)rows / 8 * rowblk;
+  const int np = prec == PMF_PREC_TF32 ? 1 : 2;
+  out.assign(plane * np, 0);
+  for (int r = 0; r < rows; ++r)
+    for (int c = 0; c < cols; ++c) {
+      const size_t off = (size_t)(r / 8) * rowblk + (c / epc) * 128 + (r % 8) * 16 + (c % epc) * esz;
+      const double x = Mt[(size_t)r * cols + c] * scale;
+      if (prec == PMF_PREC_TF32) {
+        float f = (float)x;
+        std::memcpy(&out[off], &f, 4);
+      } else if (prec == PMF_PREC_BF16X3) {
+        __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
+        __nv_bfloat16 lo = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
+        std::memcpy(&out[off], &hi, 2);
+        std::memcpy(&out[plane + off], &lo, 2);
+      } else {
+        __half hi = __float2half_rn((float)x);
+        __half lo = __float2half_rn((float)(x - (double)__half2float(hi)));
+        std::memcpy(&out[off], &hi, 2);
+        std::memcpy(&out[plane + off], &lo, 2);
+      }
+    }
+}
+
+}  // namespace
+
+int tc_supported(const pmf_config* cfg, std::string* why) {
+  if (cfg->nx != 2) {
+    *why = "the fused tensor-core kernel handles n_x = 2";
+    return PMF_ERR_UNSUPPORTED;
+  }
+  for (int a = 0; a < 2; ++a)
+    if (cfg->N[a] % 16 || cfg->N[a] < 16 || cfg->N[a] > 128) {
+      *why = "the fused tensor-core kernel needs N multiple of 16 in [16, 128]";
+      return PMF_ERR_UNSUPPORTED;
+    }
+  if (cfg->precision != PMF_PREC_FP16X3 && cfg->precision != PMF_PREC_BF16X3 &&
+      cfg->precision != PMF_PREC_TF32) {
+    *why = "the fused tensor-core kernel supports FP16X3, BF16X3 and TF32";
+    return PMF_ERR_UNSUPPORTED;
+  }
+  return PMF_OK;
+}
+
+int tc_build_tables(const pmf_config* cfg, TcTables* t, std::string* why) {
+  std::memset(t, 0, sizeof(*t));
+  t->prec = cfg->precision;
+  const double scale = cfg->precision == PMF_PREC_FP16X3 ? 16384.0 : 1.0;
+  for (int a = 0; a < cfg->nx; ++a) {
+    const int N = cfg->N[a];
+    std::vector<double> H((size_t)N * N);
+    const double w = 6.283185307179586476925286766559 / N;
+    for (int k = 0; k < N; ++k)
+      for (int j = 0; j < N; ++j) {
+        const long long r = ((long long)k * j) % N;
+        H[(size_t)k * N + j] = std::cos(w * r) + std::sin(w * r);
+      }
+    std::vector<uint8_t> planes;
+    split_planes(H, N, N, cfg->precision, scale, planes);
+    std::vector<float> tab(2 * (2 * N + 1));
+    for (int m = -N; m <= N; ++m) {
+      const double ang = 3.14159265358979323846 * m / N;
+      tab[2 * (m + N)] = (float)std::cos(ang);
+      tab[2 * (m + N) + 1] = (float)std::sin(ang);
+    }
+    const size_t hb = planes.size(), tb = tab.size() * sizeof(float);
+    if (cudaMalloc(&t->hart[a], hb + tb) != cudaSuccess) {
+      *why = "cudaMalloc of transform tables";
+      return PMF_ERR_OOM;
+    }
+    t->hart_bytes[a] = hb;
+    cudaMemcpy(t->hart[a], planes.data(), hb, cudaMemcpyHostToDevice);
+    cudaMemcpy((uint8_t*)t->hart[a] + hb, tab.data(), tb, cudaMemcpyHostToDevice);
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_fused2d<PMF_PREC_FP16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaFuncSetAttribute(k_fused2d<PMF_PREC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaFuncSetAttribute(k_fused2d<PMF_PREC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    attr = true;
+  }
+  return PMF_OK;
+}
+
+void tc_free_tables(TcTables* t) {
+  for (int a = 0; a < MAXN; ++a) {
+    cudaFree(t->hart[a]);
+    t->hart[a] = nullptr;
+  }
+}
+
+int tc_prior(const Dims& d, DevState* st, const double* prior_aux, float* X, double* partials,
+             cudaStream_t s) {
+  long long blocks = (d.P + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_prior_f32<<<(int)blocks, 256, 0, s>>>(d, st, prior_aux, X);
+  launch_moments_f32(d, st, X, partials, s);
+  return 3;
+}
+
+int tc_step(const Dims& d, const pmf_config& cfg, const TcTables* t, const MeasParams* mp,
+            const TimeConsts* tcs, DevState* st, float* b0, float* b1, cudaStream_t s) {
+  FusedJob job{};
+  job.st = st;
+  job.buf0 = b0;
+  job.buf1 = b1;
+  job.N0 = cfg.N[0];
+  job.N1 = cfg.N[1];
+  for (int a = 0; a < 2; ++a) {
+    job.hart[a] = (const uint8_t*)t->hart[a];
+    job.sctab[a] = (const float*)((const uint8_t*)t->hart[a] + t->hart_bytes[a]);
+  }
+  job.do_meas = mp != nullptr;
+  job.do_time = tcs != nullptr;
+  if (mp) job.mp = *mp;
+  if (tcs) job.tc = *tcs;
+  if (!job.do_meas && !job.do_time) return 0;
+  if (cfg.precision == PMF_PREC_FP16X3)
+    k_fused2d<PMF_PREC_FP16X3><<<1, kThreads, kSmemBytes, s>>>(job);
+  else if (cfg.precision == PMF_PREC_BF16X3)
+    k_fused2d<PMF_PREC_BF16X3><<<1, kThreads, kSmemBytes, s>>>(job);
+  else
+    k_fused2d<PMF_PREC_TF32><<<1, kThreads, kSmemBytes, s>>>(job);
+  return 1;
 }
 
 }  // namespace pmf

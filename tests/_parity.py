@@ -13,10 +13,11 @@ def compare(gpu, orc):
     """Relative L1 of the weights, frame and moment differences after one update."""
     P, c, M = gpu.pdf()
     out = {"l1": rel_l1(P, orc.P)}
-    out["frame"] = float(max(np.abs(c - orc.c).max() / (np.abs(orc.M).max()),
-                             np.abs(M - orc.M).max() / np.abs(orc.M).max()))
     m, C = gpu.moments()
     mo, Co = orc.moments()
+    # frame: centre shift relative to the spread, axis matrix relative to its size
+    out["frame"] = float(max(np.abs(c - orc.c).max() / np.sqrt(abs(np.trace(Co))),
+                             np.abs(M - orc.M).max() / np.abs(orc.M).max()))
     out["mean"] = float(np.abs(m - mo).max() / np.sqrt(np.trace(Co)))
     out["cov"] = float(np.abs(C - Co).max() / np.abs(Co).max())
     return out
