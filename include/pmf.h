@@ -162,6 +162,36 @@ long long pmf_launch_count(const pmf_ctx* ctx);
 const char* pmf_last_error(const pmf_ctx* ctx);
 void pmf_destroy(pmf_ctx* ctx);
 
+/* ---- moments without device allocation --------------------------------------
+ * The paper has no counterpart to this entry point: it is a service for
+ * callers that cannot allocate device memory when they need the moments --
+ * code inside CUDA graph stream capture (cudaMalloc is not capturable), hosts
+ * whose own allocator owns all device memory, real-time loops that must not
+ * allocate.  It computes S0 = sum w and the mean and covariance of the point
+ * sums of a float64 weight array on a frame x = c + M u, u_m = j_m - (N_m-1)/2,
+ * exactly like pmf_moments does for a context (mean = c + M E[u],
+ * cov = M Cov[u] M^T, weights need not be normalised).
+ *
+ *   weights : device pointer, prod N_m float64 values, C-order (caller-owned)
+ *   nx, N   : state dimension (1..PMF_MAX_NX) and points per axis (host)
+ *   c, M    : frame centre (nx) and axes (nx*nx row-major), host float64
+ *   out     : device pointer to 1 + nx + nx*nx float64: {S0, mean, cov}
+ *   stream  : cudaStream_t as void* (NULL = legacy default stream)
+ *
+ * It calls no allocating routine.  Its block partial sums live in one fixed
+ * device array of PMF_NOALLOC_MAX_POINTS / 256 * 10 float64 (320 KiB) that
+ * every GPU which loads the library holds until the process exits.  The first
+ * call on a device looks up that array's device address (once per device, with
+ * the device current); make that first call before any stream capture.  All
+ * calls share the array, so calls whose kernels overlap on the GPU (different
+ * streams, or other host threads) race: serialise them on one stream.  Each
+ * call rewrites every partial it reads, so nothing needs clearing between
+ * calls.  Asynchronous; returns PMF_ERR_ARG for null pointers, nx out of range
+ * or more than PMF_NOALLOC_MAX_POINTS points, PMF_ERR_CUDA on a launch error. */
+#define PMF_NOALLOC_MAX_POINTS (1 << 20)
+int pmf_moments_noalloc(const double* weights, int nx, const int* N, const double* c,
+                        const double* M, double* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,6 +67,8 @@ SIGNATURES = [
     ("pmf_launch_count", C.c_longlong, [C.c_void_p]),
     ("pmf_last_error", C.c_char_p, [C.c_void_p]),
     ("pmf_destroy", None, [C.c_void_p]),
+    ("pmf_moments_noalloc", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), C.c_void_p, C.c_void_p]),
 ]
 
 _lib = None
@@ -148,6 +150,22 @@ def make_meas(meas, z, nx) -> PmfMeas:
     if meas.H is not None:
         _fill(m.H, meas.H, nz * nx)
     return m
+
+
+def moments_noalloc(weights, N, c, M, out, stream=None) -> None:
+    """pmf_moments_noalloc on device tensors ``weights`` (float64, prod N) and
+    ``out`` (float64, 1 + nx + nx^2): {S0, mean, cov} without any allocation."""
+    lib = load()
+    nx = len(N)
+    Na = (C.c_int * nx)(*[int(v) for v in N])
+    ca = (C.c_double * nx)()
+    Ma = (C.c_double * (nx * nx))()
+    _fill(ca, c, nx)
+    _fill(Ma, M, nx * nx)
+    rc = lib.pmf_moments_noalloc(C.c_void_p(int(weights.data_ptr())), nx, Na, ca, Ma,
+                                 C.c_void_p(int(out.data_ptr())), _stream_handle(stream))
+    if rc != OK:
+        raise PmfError(rc, "pmf_moments_noalloc failed")
 
 
 class Filter:
