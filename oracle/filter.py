@@ -24,6 +24,12 @@ notes of the repository):
     (eq. interFreq), or, when the whitened correlation of the frame exceeds
     ``realign_rho``, a re-aligned frame filled by multilinear interpolation;
     points outside the old box get weight 0;
+  * the separable regrid is quantised: the centre moves by a multiple of 1/64
+    of a node towards the mean and each axis scale by a factor with an 8-bit
+    mantissa, so the grid geometry is exact in any precision and does not
+    random-walk with the rounding of the moments; a re-aligned frame has its
+    centre on the same 1/64-node lattice and its axis entries rounded to a
+    12-bit mantissa;
   * weights normalised so that |det M| sum P = 1 (eq. PDF_pm, c = delta sum P);
   * moments are point sums (no cell-variance term).
 """
@@ -82,6 +88,30 @@ def multilinear(P: np.ndarray, z: np.ndarray) -> np.ndarray:
             idx.append(np.clip(i, 0, P.shape[m] - 1))
         out += np.where(ok, wt * P[tuple(idx)], 0.0)
     return out
+
+
+SHIFT_QUANTUM = 1.0 / 64.0
+SCALE_MANTISSA_BITS = 8
+
+
+def quantize_shift(s: np.ndarray) -> np.ndarray:
+    """Frame-centre shift in old-node units, rounded to a multiple of 1/64 node."""
+    return np.rint(np.asarray(s) / SHIFT_QUANTUM) * SHIFT_QUANTUM
+
+
+def quantize_scale(d: float) -> float:
+    """Axis rescale factor rounded to an 8-bit mantissa (relative step 2^-8)."""
+    f, e = math.frexp(d)
+    return math.ldexp(round(math.ldexp(f, SCALE_MANTISSA_BITS)), e - SCALE_MANTISSA_BITS)
+
+
+MATRIX_MANTISSA_BITS = 12
+
+
+def quantize_matrix(M: np.ndarray) -> np.ndarray:
+    """Re-aligned frame axes, each entry rounded to a 12-bit mantissa."""
+    f, e = np.frexp(np.asarray(M, dtype=float))
+    return np.ldexp(np.rint(np.ldexp(f, MATRIX_MANTISSA_BITS)), e - MATRIX_MANTISSA_BITS)
 
 
 class OracleFilter:
@@ -175,22 +205,24 @@ class OracleFilter:
         span = self.cfg.span
         if n >= 2 and rho > self.cfg.realign_rho:
             Lp = np.linalg.cholesky(0.5 * (Ppred + Ppred.T))
-            Mnew = Phinv @ Lp @ np.diag([2.0 * span / Nm for Nm in self.N])
+            Mnew = quantize_matrix(Phinv @ Lp @ np.diag([2.0 * span / Nm for Nm in self.N]))
+            m = self.c + self.M @ quantize_shift(Minv @ (m - self.c))
             x = frame_points(m, Mnew, self.N)
             u_old = (x - self.c[None, :]) @ Minv.T
             zidx = u_old + (np.array(self.N) - 1) / 2.0
             self.P = multilinear(self.P, zidx).reshape(self.N)
             realigned = True
         else:
-            D = np.array([2.0 * span * sd[a] / self.N[a] for a in range(n)])
+            D = np.array([quantize_scale(2.0 * span * sd[a] / self.N[a]) for a in range(n)])
             Mnew = self.M @ np.diag(D)
-            s = Minv @ (m - self.c)
+            s = quantize_shift(Minv @ (m - self.c))
             P = self.P
             for a in range(n):
                 pos = s[a] + D[a] * grid_u(self.N[a]) + (self.N[a] - 1) / 2.0
                 P = _first_interp_axis(P, a, pos, self.N[a])
             self.P = P
             realigned = False
+            m = self.c + self.M @ s
         self.c = m.copy()
         self.M = Mnew
         self.normalise()

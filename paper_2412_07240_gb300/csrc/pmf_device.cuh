@@ -100,7 +100,8 @@ __device__ __forceinline__ bool chol_t(const double* A, double* L) {
 // Regrid decision of one time update (float64, one thread).  From the current
 // moments and frame: the pulled-back predicted covariance
 // e^{-A tau} P_pred e^{-A^T tau} = cov + Q_b, its whitened correlation in the
-// frame, and either the separable rescale/recentre (M' = M D, c' = mean) or a
+// frame, and either the separable rescale/recentre (M' = M D, c' = the mean,
+// both quantised as described below) or a
 // re-aligned frame M' = e^{-A tau} chol(P_pred) diag(2 span / N).  Writes the
 // regrid map into st, the inverse of M' into Mpi and the pending frame after
 // the move by e^{A tau} into pend = {c[3], M[9], Minv[9], V}.
@@ -135,7 +136,12 @@ __device__ inline void frame_scalar(const TimeConsts& tc, FrameState* st, double
 #pragma unroll
       for (int a = 0; a < n; ++a)
 #pragma unroll
-        for (int b = 0; b < n; ++b) Mp[a * n + b] = T[a * n + b] * (2.0 * tc.span / tc.N[b]);
+        for (int b = 0; b < n; ++b) {
+          // axis entries rounded to a 12-bit mantissa
+          int e;
+          const double f = frexp(T[a * n + b] * (2.0 * tc.span / tc.N[b]), &e);
+          Mp[a * n + b] = ldexp(rint(ldexp(f, 12)), e - 12);
+        }
     } else {
       realign = 0;
     }
@@ -148,6 +154,17 @@ __device__ inline void frame_scalar(const TimeConsts& tc, FrameState* st, double
     for (int b = 0; b < n; ++b) s = fma(Minv[a * n + b], st->mean[b] - st->c[b], s);
     dm[a] = s;
   }
+  double cnew[n];   // centre of the new frame
+  // the centre moves by a multiple of 1/64 node (in the old frame) towards the mean
+#pragma unroll
+  for (int a = 0; a < n; ++a) dm[a] = rint(dm[a] * 64.0) * (1.0 / 64.0);
+#pragma unroll
+  for (int a = 0; a < n; ++a) {
+    double s = st->c[a];
+#pragma unroll
+    for (int b = 0; b < n; ++b) s = fma(M[a * n + b], dm[b], s);
+    cnew[a] = s;
+  }
   if (realign) {
     double B[n * n];
     mm_t<n>(Minv, Mp, B);
@@ -157,9 +174,14 @@ __device__ inline void frame_scalar(const TimeConsts& tc, FrameState* st, double
     for (int a = 0; a < n; ++a) st->b[a] = dm[a];
     inv_t<n>(Mp, Mpi);
   } else {
+    // quantised separable regrid: scale by a factor with an 8-bit mantissa (with
+    // the 1/64-node shift the grid geometry is exact in any precision and does
+    // not random-walk with the rounding of the moments)
 #pragma unroll
     for (int a = 0; a < n; ++a) {
-      const double D = 2.0 * tc.span * sd[a] / tc.N[a];
+      int e;
+      const double f = frexp(2.0 * tc.span * sd[a] / tc.N[a], &e);
+      const double D = ldexp(rint(ldexp(f, 8)), e - 8);
       const double rD = 1.0 / D;
 #pragma unroll
       for (int r = 0; r < n; ++r) {
@@ -181,7 +203,7 @@ __device__ inline void frame_scalar(const TimeConsts& tc, FrameState* st, double
   for (int a = 0; a < n; ++a) {
     double s = 0.0;
 #pragma unroll
-    for (int b = 0; b < n; ++b) s = fma(tc.Phi[a * n + b], st->mean[b], s);
+    for (int b = 0; b < n; ++b) s = fma(tc.Phi[a * n + b], cnew[b], s);
     pend[a] = s;
   }
 #pragma unroll

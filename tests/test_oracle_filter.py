@@ -188,3 +188,22 @@ def test_mutation_trace_factor_sign(monkeypatch):
     f = of.OracleFilter(cfg)
     f.spectral_step(0.1)
     assert abs(f.last_mass_ratio - 1.0) > 5e-3
+
+
+def test_regrid_quantisation():
+    """Shift: multiple of 1/64 node, within 1/128 of the target; scale: 8-bit
+    mantissa, within 2^-8 relative; small corrections leave the grid exact."""
+    rng = np.random.default_rng(9)
+    for s in rng.uniform(-20, 20, size=50):
+        q = of.quantize_shift(np.array([s]))[0]
+        assert abs(q * 64 - round(q * 64)) == 0.0 and abs(q - s) <= 1 / 128 + 1e-15
+    for d in np.exp(rng.uniform(-5, 3, size=50)):
+        q = of.quantize_scale(d)
+        f, e = np.frexp(q)
+        assert f * 256 == round(f * 256) and abs(q / d - 1) <= 2 ** -8
+        # exact grid positions in float32: s + D u with u half-integers
+        u = np.arange(64) - 31.5
+        y = of.quantize_shift(np.array([0.3]))[0] + q * u
+        if q >= 1 / 8:
+            assert np.array_equal(y.astype(np.float32).astype(np.float64), y)
+    assert of.quantize_scale(1.0 + 1e-4) == 1.0 and of.quantize_shift(np.array([1e-3]))[0] == 0.0
