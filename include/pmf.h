@@ -162,6 +162,48 @@ long long pmf_launch_count(const pmf_ctx* ctx);
 const char* pmf_last_error(const pmf_ctx* ctx);
 void pmf_destroy(pmf_ctx* ctx);
 
+/* ---- batches of independent filters ------------------------------------------
+ * A batch holds many filters resident on the device (weights, frames, moments,
+ * model constants) and advances any subset of them with one kernel launch per
+ * epoch, one CTA per filter, larger grids scheduled first.  All filters of a
+ * batch share n_x = 2 and the precision of cfgs[0] (a tensor-core format);
+ * grid sizes may differ (multiples of 16 up to 128).  The per-filter
+ * semantics are those of pmf_step. */
+typedef struct pmf_batch pmf_batch;
+
+/* Create `count` filters from cfgs[i] with measurement models models[i] (z is
+ * ignored; the measurement of each epoch comes with pmf_batch_step).  Device
+ * memory needed: pmf_batch_bytes().  If it exceeds hbm_budget (bytes; 0 = no
+ * limit) nothing is allocated and PMF_ERR_ADMISSION is returned.  Errors:
+ * PMF_ERR_ARG, PMF_ERR_UNSUPPORTED, PMF_ERR_OOM, PMF_ERR_CUDA. */
+int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* models, int count,
+                     size_t hbm_budget, void* cuda_stream);
+
+/* One epoch for k filters ids[0..k): measurement update with
+ * z[i*PMF_MAX_NZ ...] (skipped when do_meas[i] == 0; do_meas may be NULL = all)
+ * then time update over taus[i] (skipped when taus[i] == 0).  Asynchronous;
+ * ids must be distinct within a call.  Model constants are recomputed on the
+ * host only for filters whose tau changed. */
+int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_meas,
+                   const double* taus, int k);
+
+/* Means (k*nx) and covariances (k*nx*nx) of filters ids[0..k).  Synchronous.
+ * Returns PMF_ERR_DEGENERATE if any listed filter reported a degenerate
+ * normaliser (its density is left unchanged). */
+int pmf_batch_moments(pmf_batch* b, const int* ids, int k, double* means, double* covs);
+
+/* Status words of filters ids[0..k) (PMF_OK or the PMF_ERR_* their last epoch
+ * reported, e.g. PMF_ERR_DEGENERATE), cleared after reading.  Synchronous. */
+int pmf_batch_status(pmf_batch* b, const int* ids, int k, int* status_out);
+
+/* Normalised weights of filter id (prod N_m doubles) and its frame.  Synchronous. */
+int pmf_batch_get_pdf(pmf_batch* b, int id, double* host_out, double* c_out, double* M_out);
+
+/* Device bytes held by the batch, and kernel launches issued so far. */
+long long pmf_batch_bytes(const pmf_batch* b);
+long long pmf_batch_launch_count(const pmf_batch* b);
+void pmf_batch_destroy(pmf_batch* b);
+
 /* ---- moments without device allocation --------------------------------------
  * The paper has no counterpart to this entry point: it is a service for
  * callers that cannot allocate device memory when they need the moments --

@@ -67,6 +67,18 @@ SIGNATURES = [
     ("pmf_launch_count", C.c_longlong, [C.c_void_p]),
     ("pmf_last_error", C.c_char_p, [C.c_void_p]),
     ("pmf_destroy", None, [C.c_void_p]),
+    ("pmf_batch_create", C.c_int, [C.POINTER(C.c_void_p), C.POINTER(PmfConfig), C.POINTER(PmfMeas), C.c_int,
+                                   C.c_size_t, C.c_void_p]),
+    ("pmf_batch_step", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int),
+                                 C.POINTER(C.c_double), C.c_int]),
+    ("pmf_batch_moments", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]),
+    ("pmf_batch_status", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]),
+    ("pmf_batch_get_pdf", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]),
+    ("pmf_batch_bytes", C.c_longlong, [C.c_void_p]),
+    ("pmf_batch_launch_count", C.c_longlong, [C.c_void_p]),
+    ("pmf_batch_destroy", None, [C.c_void_p]),
     ("pmf_moments_noalloc", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.c_void_p, C.c_void_p]),
 ]
@@ -236,6 +248,99 @@ class Filter:
     def close(self) -> None:
         if getattr(self, "_h", None):
             self._lib.pmf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _iptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+class Batch:
+    """Many independent 2-D filters resident on the GPU (a pmf_batch)."""
+
+    def __init__(self, cfgs, models, precision="fp16x3", psi_mode="euler", hbm_budget=0, stream=None):
+        self._lib = load()
+        n = len(cfgs)
+        self.count = n
+        self.N = [tuple(int(v) for v in c.N[:2]) for c in cfgs]
+        carr = (PmfConfig * n)()
+        marr = (PmfMeas * n)()
+        for i, (c, m) in enumerate(zip(cfgs, models)):
+            carr[i] = make_config(c, precision, psi_mode)
+            marr[i] = make_meas(m, np.zeros(np.asarray(m.R).shape[0]), 2)
+        self._stream = _stream_handle(stream)
+        h = C.c_void_p()
+        rc = self._lib.pmf_batch_create(C.byref(h), carr, marr, n, int(hbm_budget), self._stream)
+        if rc != OK:
+            cls = Unsupported if rc == ERR_UNSUPPORTED else PmfError
+            raise cls(rc, "pmf_batch_create failed")
+        self._h = h
+
+    def step(self, ids, z, taus, do_meas=None) -> None:
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        k = ids.size
+        zz = np.zeros((k, MAX_NZ))
+        if z is not None:
+            z = np.asarray(z, dtype=np.float64).reshape(k, -1)
+            zz[:, :z.shape[1]] = z
+        taus = np.ascontiguousarray(np.broadcast_to(np.asarray(taus, dtype=np.float64), (k,)))
+        dm = None if do_meas is None else np.ascontiguousarray(do_meas, dtype=np.int32)
+        rc = self._lib.pmf_batch_step(self._h, _iptr(ids), _dptr(zz), None if dm is None else _iptr(dm),
+                                      _dptr(taus), k)
+        if rc != OK:
+            raise PmfError(rc, "pmf_batch_step failed")
+
+    def moments(self, ids=None):
+        ids = np.arange(self.count, dtype=np.int32) if ids is None else np.ascontiguousarray(ids, dtype=np.int32)
+        k = ids.size
+        m = np.empty((k, 2))
+        P = np.empty((k, 2, 2))
+        rc = self._lib.pmf_batch_moments(self._h, _iptr(ids), k, _dptr(m), _dptr(P))
+        if rc == ERR_DEGENERATE:
+            raise Degenerate(rc, "degenerate normaliser in the batch")
+        if rc != OK:
+            raise PmfError(rc, "pmf_batch_moments failed")
+        return m, P
+
+    def status(self, ids=None):
+        """Per-filter status words (0 = OK), cleared after reading."""
+        ids = np.arange(self.count, dtype=np.int32) if ids is None else np.ascontiguousarray(ids, dtype=np.int32)
+        st = np.empty(ids.size, dtype=np.int32)
+        rc = self._lib.pmf_batch_status(self._h, _iptr(ids), ids.size, _iptr(st))
+        if rc != OK:
+            raise PmfError(rc, "pmf_batch_status failed")
+        return st
+
+    def pdf(self, i):
+        out = np.empty(int(np.prod(self.N[i])))
+        c = np.empty(2)
+        M = np.empty(4)
+        rc = self._lib.pmf_batch_get_pdf(self._h, int(i), _dptr(out), _dptr(c), _dptr(M))
+        if rc != OK:
+            raise PmfError(rc, "pmf_batch_get_pdf failed")
+        return out.reshape(self.N[i]), c, M.reshape(2, 2)
+
+    @property
+    def bytes(self) -> int:
+        return int(self._lib.pmf_batch_bytes(self._h))
+
+    @property
+    def launches(self) -> int:
+        return int(self._lib.pmf_batch_launch_count(self._h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.pmf_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

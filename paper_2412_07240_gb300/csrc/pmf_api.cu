@@ -1,10 +1,12 @@
 // C ABI of libpmf (declared in include/pmf.h): filter contexts, validation,
 // the float64 model constants of a time update, and dispatch to the kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "pmf_internal.cuh"
 #include "pmf_kernels.cuh"
@@ -92,15 +94,17 @@ void expm_host(int n, const double* A, double* E) {
 // Constants of a time update over tau (model only): Phi = e^{A tau},
 // Q_d = int_0^tau e^{As} Q e^{A^T s} ds (Van Loan block exponential),
 // Q_b = Phi^{-1} Q_d Phi^{-T}, E = e^{-A dt}, trace factor.
-int make_time_consts(pmf_ctx* ctx, double tau, TimeConsts* tc) {
-  const pmf_config& c = ctx->cfg;
+int time_consts(const pmf_config& c, double tau, TimeConsts* tc, std::string* why) {
   const int n = c.nx;
   *tc = TimeConsts{};
   tc->nx = n;
   for (int a = 0; a < n; ++a) tc->N[a] = c.N[a];
   int l = (int)std::ceil(tau / c.dt_sub - 1e-9);
   if (l < 1) l = 1;
-  if (l > MAXL) return fail(ctx, PMF_ERR_ARG, "tau / dt_sub exceeds PMF_MAX_SUBSTEPS");
+  if (l > MAXL) {
+    *why = "tau / dt_sub exceeds PMF_MAX_SUBSTEPS";
+    return PMF_ERR_ARG;
+  }
   tc->l = l;
   tc->tau = tau;
   tc->dt = tau / l;
@@ -156,6 +160,12 @@ int make_time_consts(pmf_ctx* ctx, double tau, TimeConsts* tc) {
   return PMF_OK;
 }
 
+int make_time_consts(pmf_ctx* ctx, double tau, TimeConsts* tc) {
+  std::string why;
+  const int rc = time_consts(ctx->cfg, tau, tc, &why);
+  return rc ? fail(ctx, rc, why) : PMF_OK;
+}
+
 int validate_config(const pmf_config* c, std::string* why) {
   if (!c) { *why = "null config"; return PMF_ERR_ARG; }
   if (c->nx < 1 || c->nx > PMF_MAX_NX) { *why = "nx out of range"; return PMF_ERR_ARG; }
@@ -195,24 +205,23 @@ void hartley_host(int N, double scale, double* H) {
     }
 }
 
-int build_meas(pmf_ctx* ctx, const pmf_meas* m, MeasParams* mp) {
-  const int n = ctx->cfg.nx;
-  if (!m) return fail(ctx, PMF_ERR_ARG, "null measurement");
-  int nz = m->nz;
+int meas_params(int n, const pmf_meas* m, MeasParams* mp, std::string* why) {
+  if (!m) { *why = "null measurement"; return PMF_ERR_ARG; }
+  const int nz = m->nz;
   if (m->kind == PMF_MEAS_RANGE) {
-    if (nz != 1 || n < 2) return fail(ctx, PMF_ERR_ARG, "range measurement needs nz = 1, nx >= 2");
+    if (nz != 1 || n < 2) { *why = "range measurement needs nz = 1, nx >= 2"; return PMF_ERR_ARG; }
   } else if (m->kind == PMF_MEAS_BEARING_LINEAR3) {
-    if (nz != 2 || n < 3) return fail(ctx, PMF_ERR_ARG, "bearing measurement needs nz = 2, nx = 3");
+    if (nz != 2 || n < 3) { *why = "bearing measurement needs nz = 2, nx = 3"; return PMF_ERR_ARG; }
   } else if (m->kind == PMF_MEAS_LINEAR) {
-    if (nz < 1 || nz > PMF_MAX_NZ) return fail(ctx, PMF_ERR_ARG, "linear measurement nz out of range");
-    if (!finite_all(m->H, nz * n)) return fail(ctx, PMF_ERR_ARG, "non-finite H");
+    if (nz < 1 || nz > PMF_MAX_NZ) { *why = "linear measurement nz out of range"; return PMF_ERR_ARG; }
+    if (!finite_all(m->H, nz * n)) { *why = "non-finite H"; return PMF_ERR_ARG; }
   } else {
-    return fail(ctx, PMF_ERR_ARG, "unknown measurement kind");
+    *why = "unknown measurement kind";
+    return PMF_ERR_ARG;
   }
-  if (!finite_all(m->z, nz) || !finite_all(m->R, nz * nz))
-    return fail(ctx, PMF_ERR_ARG, "non-finite z or R");
+  if (!finite_all(m->z, nz) || !finite_all(m->R, nz * nz)) { *why = "non-finite z or R"; return PMF_ERR_ARG; }
   double L[9];
-  if (!chol(nz, m->R, L)) return fail(ctx, PMF_ERR_ARG, "R is not positive definite");
+  if (!chol(nz, m->R, L)) { *why = "R is not positive definite"; return PMF_ERR_ARG; }
   *mp = MeasParams{};
   mp->kind = m->kind;
   mp->nz = nz;
@@ -221,6 +230,27 @@ int build_meas(pmf_ctx* ctx, const pmf_meas* m, MeasParams* mp) {
   for (int i = 0; i < nz * n; ++i) mp->H[i] = m->H[i];
   inv(nz, m->R, mp->Rinv);
   return PMF_OK;
+}
+
+int build_meas(pmf_ctx* ctx, const pmf_meas* m, MeasParams* mp) {
+  std::string why;
+  const int rc = meas_params(ctx->cfg.nx, m, mp, &why);
+  return rc ? fail(ctx, rc, why) : PMF_OK;
+}
+
+// Initial frame c = m0, M = chol(P0) diag(2 span / N) and unit normaliser.
+DevState initial_state(const pmf_config& c) {
+  DevState h{};
+  const int n = c.nx;
+  double L[9];
+  chol(n, c.P0, L);
+  for (int a = 0; a < n; ++a) h.f.c[a] = c.m0[a];
+  for (int r = 0; r < n; ++r)
+    for (int a = 0; a < n; ++a) h.f.M[r * n + a] = L[r * n + a] * (2.0 * c.span_sigma / c.N[a]);
+  inv(n, h.f.M, h.f.Minv);
+  h.f.V = std::fabs(det(n, h.f.M));
+  h.f.pscale = 1.0;
+  return h;
 }
 
 void free_ctx(pmf_ctx* ctx) {
@@ -333,15 +363,7 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
 #undef ALLOC
 
   // initial frame c = m0, M = chol(P0) diag(2 span / N)
-  DevState h{};
-  double L[9];
-  chol(n, cfg->P0, L);
-  for (int a = 0; a < n; ++a) h.f.c[a] = cfg->m0[a];
-  for (int r = 0; r < n; ++r)
-    for (int a = 0; a < n; ++a) h.f.M[r * n + a] = L[r * n + a] * (2.0 * cfg->span_sigma / cfg->N[a]);
-  inv(n, h.f.M, h.f.Minv);
-  h.f.V = std::fabs(det(n, h.f.M));
-  h.f.pscale = 1.0;
+  DevState h = initial_state(*cfg);
   double aux[16] = {0};
   inv(n, cfg->P0, aux);
   for (int a = 0; a < n; ++a) aux[9 + a] = cfg->m0[a];
@@ -487,5 +509,302 @@ int pmf_path(const pmf_ctx* ctx) { return ctx ? ctx->path : -1; }
 long long pmf_launch_count(const pmf_ctx* ctx) { return ctx ? ctx->launches : 0; }
 const char* pmf_last_error(const pmf_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 void pmf_destroy(pmf_ctx* ctx) { free_ctx(ctx); }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batches of independent 2-D filters (one fused launch per epoch)
+// ---------------------------------------------------------------------------
+struct pmf_batch {
+  int count = 0, precision = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<pmf_config> cfgs;
+  std::vector<long long> npts;
+  DevState* d_st = nullptr;
+  float* d_w = nullptr;
+  MeasParams* d_mp = nullptr;
+  TimeConsts* d_tc = nullptr;
+  FilterSlot* d_slots = nullptr;
+  StepItem* d_items = nullptr;
+  double* d_partials = nullptr;
+  double* d_aux = nullptr;
+  std::vector<void*> tables;          // per distinct N
+  std::vector<double> tau;            // tau of the constants resident for each filter
+  StepItem* h_items[2] = {nullptr, nullptr};
+  TimeConsts* h_tc[2] = {nullptr, nullptr};
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int parity = 0;
+  long long bytes = 0, launches = 0;
+  std::string err;
+};
+
+namespace {
+
+void free_batch(pmf_batch* b) {
+  if (!b) return;
+  cudaFree(b->d_st);
+  cudaFree(b->d_w);
+  cudaFree(b->d_mp);
+  cudaFree(b->d_tc);
+  cudaFree(b->d_slots);
+  cudaFree(b->d_items);
+  cudaFree(b->d_partials);
+  cudaFree(b->d_aux);
+  for (void* p : b->tables) cudaFree(p);
+  for (int i = 0; i < 2; ++i) {
+    cudaFreeHost(b->h_items[i]);
+    cudaFreeHost(b->h_tc[i]);
+    if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+  }
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* models, int count,
+                     size_t hbm_budget, void* cuda_stream) {
+  if (!out || !cfgs || !models || count < 1) return PMF_ERR_ARG;
+  *out = nullptr;
+  std::string why;
+  const int prec = cfgs[0].precision;
+  std::vector<MeasParams> mps(count);
+  std::vector<int> sizes;
+  long long wfloats = 0;
+  for (int i = 0; i < count; ++i) {
+    int rc = validate_config(&cfgs[i], &why);
+    if (rc) return rc;
+    if (cfgs[i].nx != 2 || cfgs[i].precision != prec) return PMF_ERR_UNSUPPORTED;
+    rc = tc_supported(&cfgs[i], &why);
+    if (rc) return rc;
+    rc = meas_params(2, &models[i], &mps[i], &why);
+    if (rc) return rc;
+    for (int a = 0; a < 2; ++a)
+      if (std::find(sizes.begin(), sizes.end(), cfgs[i].N[a]) == sizes.end()) sizes.push_back(cfgs[i].N[a]);
+    wfloats += 2LL * cfgs[i].N[0] * cfgs[i].N[1];
+  }
+  long long bytes = wfloats * 4 + (long long)count * (sizeof(DevState) + sizeof(MeasParams) +
+                                                       sizeof(TimeConsts) + sizeof(FilterSlot) +
+                                                       sizeof(StepItem)) +
+                    sizeof(double) * (10 * 4096 + 16 * (long long)count);
+  for (int N : sizes) bytes += (long long)tc_axis_table_bytes(N, prec);
+  if (hbm_budget && (size_t)bytes > hbm_budget) return PMF_ERR_ADMISSION;
+
+  pmf_batch* b = new (std::nothrow) pmf_batch();
+  if (!b) return PMF_ERR_OOM;
+  b->count = count;
+  b->precision = prec;
+  b->stream = (cudaStream_t)cuda_stream;
+  b->cfgs.assign(cfgs, cfgs + count);
+  b->tau.assign(count, -1.0);
+  b->bytes = bytes;
+#define BALLOC(ptr, n)                                                       \
+  do {                                                                       \
+    if (cudaMalloc((void**)&(ptr), (n)) != cudaSuccess) {                    \
+      free_batch(b);                                                         \
+      return PMF_ERR_OOM;                                                    \
+    }                                                                        \
+  } while (0)
+  BALLOC(b->d_st, sizeof(DevState) * count);
+  BALLOC(b->d_w, sizeof(float) * wfloats);
+  BALLOC(b->d_mp, sizeof(MeasParams) * count);
+  BALLOC(b->d_tc, sizeof(TimeConsts) * count);
+  BALLOC(b->d_slots, sizeof(FilterSlot) * count);
+  BALLOC(b->d_items, sizeof(StepItem) * count);
+  BALLOC(b->d_partials, sizeof(double) * 10 * 4096);
+  BALLOC(b->d_aux, sizeof(double) * 16 * count);
+#undef BALLOC
+  for (int i = 0; i < 2; ++i) {
+    if (cudaMallocHost((void**)&b->h_items[i], sizeof(StepItem) * count) != cudaSuccess ||
+        cudaMallocHost((void**)&b->h_tc[i], sizeof(TimeConsts) * count) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming) != cudaSuccess) {
+      free_batch(b);
+      return PMF_ERR_OOM;
+    }
+  }
+  std::vector<void*> tabs(sizes.size());
+  std::vector<size_t> hbytes(sizes.size());
+  for (size_t s = 0; s < sizes.size(); ++s) {
+    if (tc_build_axis_table(sizes[s], prec, &tabs[s], &hbytes[s]) != PMF_OK) {
+      b->tables = tabs;
+      free_batch(b);
+      return PMF_ERR_OOM;
+    }
+  }
+  b->tables = tabs;
+  std::vector<DevState> hst(count);
+  std::vector<FilterSlot> slots(count);
+  std::vector<double> aux(16 * (size_t)count, 0.0);
+  long long off = 0;
+  b->npts.resize(count);
+  for (int i = 0; i < count; ++i) {
+    const pmf_config& c = cfgs[i];
+    hst[i] = initial_state(c);
+    inv(2, c.P0, &aux[16 * i]);
+    aux[16 * i + 9] = c.m0[0];
+    aux[16 * i + 10] = c.m0[1];
+    const long long P = (long long)c.N[0] * c.N[1];
+    b->npts[i] = P;
+    FilterSlot& sl = slots[i];
+    sl.st = b->d_st + i;
+    sl.buf0 = b->d_w + off;
+    sl.buf1 = b->d_w + off + P;
+    off += 2 * P;
+    for (int a = 0; a < 2; ++a) {
+      const size_t s = std::find(sizes.begin(), sizes.end(), c.N[a]) - sizes.begin();
+      sl.hart[a] = (const uint8_t*)tabs[s];
+      sl.sctab[a] = (const float*)((const uint8_t*)tabs[s] + hbytes[s]);
+    }
+    sl.N0 = c.N[0];
+    sl.N1 = c.N[1];
+    sl.mp = b->d_mp + i;
+    sl.tc = b->d_tc + i;
+  }
+  cudaMemcpy(b->d_st, hst.data(), sizeof(DevState) * count, cudaMemcpyHostToDevice);
+  cudaMemcpy(b->d_mp, mps.data(), sizeof(MeasParams) * count, cudaMemcpyHostToDevice);
+  cudaMemcpy(b->d_slots, slots.data(), sizeof(FilterSlot) * count, cudaMemcpyHostToDevice);
+  cudaMemcpy(b->d_aux, aux.data(), sizeof(double) * aux.size(), cudaMemcpyHostToDevice);
+  for (int i = 0; i < count; ++i) {
+    Dims d{};
+    d.nx = 2;
+    d.N[0] = cfgs[i].N[0];
+    d.N[1] = cfgs[i].N[1];
+    d.N[2] = 1;
+    d.P = b->npts[i];
+    b->launches += tc_prior(d, b->d_st + i, b->d_aux + 16 * i, slots[i].buf0, b->d_partials, b->stream);
+  }
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    free_batch(b);
+    return PMF_ERR_CUDA;
+  }
+  *out = b;
+  return PMF_OK;
+}
+
+int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_meas,
+                   const double* taus, int k) {
+  if (!b || k < 0 || k > b->count || (k && (!ids || !taus))) return PMF_ERR_ARG;
+  if (k == 0) return PMF_OK;
+  for (int i = 0; i < k; ++i) {
+    if (ids[i] < 0 || ids[i] >= b->count || !std::isfinite(taus[i]) || taus[i] < 0) return PMF_ERR_ARG;
+    if ((!do_meas || do_meas[i]) && (!z || !finite_all(&z[(size_t)i * PMF_MAX_NZ], PMF_MAX_NZ)))
+      return PMF_ERR_ARG;
+  }
+  const int p = b->parity;
+  b->parity ^= 1;
+  // the pinned buffers of this parity were last read by the copies two steps ago
+  if (cudaEventSynchronize(b->ev[p]) != cudaSuccess) return PMF_ERR_CUDA;
+  StepItem* items = b->h_items[p];
+  TimeConsts* stage = b->h_tc[p];
+  int nchanged = 0;
+  std::vector<int> changed;
+  for (int i = 0; i < k; ++i) {
+    const int id = ids[i];
+    const double tau = taus[i];
+    const bool meas = !do_meas || do_meas[i];
+    StepItem& it = items[i];
+    it.slot = id;
+    it.flags = (meas ? 1 : 0) | (tau > 0 ? 2 : 0);
+    for (int j = 0; j < PMF_MAX_NZ; ++j) it.z[j] = meas ? z[(size_t)i * PMF_MAX_NZ + j] : 0.0;
+    if (tau > 0 && tau != b->tau[id]) {
+      std::string why;
+      const int rc = time_consts(b->cfgs[id], tau, &stage[nchanged], &why);
+      if (rc) {
+        b->err = why;
+        return rc;
+      }
+      changed.push_back(id);
+      ++nchanged;
+      b->tau[id] = tau;
+    }
+  }
+  // larger grids first: the hardware hands CTAs out in order, so the longest
+  // run first and the tail is made of small filters
+  std::vector<StepItem> sorted(items, items + k);
+  std::stable_sort(sorted.begin(), sorted.end(), [&](const StepItem& x, const StepItem& y) {
+    return b->npts[x.slot] > b->npts[y.slot];
+  });
+  std::copy(sorted.begin(), sorted.end(), items);
+  for (int j = 0; j < nchanged; ++j)
+    if (cudaMemcpyAsync(b->d_tc + changed[j], &stage[j], sizeof(TimeConsts), cudaMemcpyHostToDevice,
+                        b->stream) != cudaSuccess)
+      return PMF_ERR_CUDA;
+  if (cudaMemcpyAsync(b->d_items, items, sizeof(StepItem) * k, cudaMemcpyHostToDevice, b->stream) !=
+      cudaSuccess)
+    return PMF_ERR_CUDA;
+  cudaEventRecord(b->ev[p], b->stream);
+  b->launches += tc_batch_step(b->precision, b->d_slots, b->d_items, k, b->stream);
+  return cudaGetLastError() == cudaSuccess ? PMF_OK : PMF_ERR_CUDA;
+}
+
+int pmf_batch_moments(pmf_batch* b, const int* ids, int k, double* means, double* covs) {
+  if (!b || k < 0 || (k && !ids)) return PMF_ERR_ARG;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return PMF_ERR_CUDA;
+  std::vector<FrameState> fs(b->count);
+  if (cudaMemcpy2D(fs.data(), sizeof(FrameState), b->d_st, sizeof(DevState), sizeof(FrameState), b->count,
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+    return PMF_ERR_CUDA;
+  int rc = PMF_OK;
+  for (int i = 0; i < k; ++i) {
+    if (ids[i] < 0 || ids[i] >= b->count) return PMF_ERR_ARG;
+    const FrameState& f = fs[ids[i]];
+    if (f.status) rc = f.status;
+    if (means) std::memcpy(means + 2 * i, f.mean, sizeof(double) * 2);
+    if (covs) std::memcpy(covs + 4 * i, f.cov, sizeof(double) * 4);
+  }
+  if (rc) {
+    // report once, then clear the listed filters' status words
+    for (int i = 0; i < k; ++i) {
+      const int zero = 0;
+      cudaMemcpy(&b->d_st[ids[i]].f.status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    }
+  }
+  return rc;
+}
+
+int pmf_batch_status(pmf_batch* b, const int* ids, int k, int* status_out) {
+  if (!b || k < 0 || (k && (!ids || !status_out))) return PMF_ERR_ARG;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return PMF_ERR_CUDA;
+  std::vector<FrameState> fs(b->count);
+  if (cudaMemcpy2D(fs.data(), sizeof(FrameState), b->d_st, sizeof(DevState), sizeof(FrameState), b->count,
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+    return PMF_ERR_CUDA;
+  for (int i = 0; i < k; ++i) {
+    if (ids[i] < 0 || ids[i] >= b->count) return PMF_ERR_ARG;
+    status_out[i] = fs[ids[i]].status;
+    if (fs[ids[i]].status) {
+      const int zero = 0;
+      cudaMemcpy(&b->d_st[ids[i]].f.status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    }
+  }
+  return PMF_OK;
+}
+
+int pmf_batch_get_pdf(pmf_batch* b, int id, double* host_out, double* c_out, double* M_out) {
+  if (!b || id < 0 || id >= b->count) return PMF_ERR_ARG;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return PMF_ERR_CUDA;
+  FrameState f;
+  if (cudaMemcpy(&f, &b->d_st[id].f, sizeof(FrameState), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return PMF_ERR_CUDA;
+  if (c_out) std::memcpy(c_out, f.c, sizeof(double) * 2);
+  if (M_out) std::memcpy(M_out, f.M, sizeof(double) * 4);
+  if (host_out) {
+    FilterSlot sl;
+    if (cudaMemcpy(&sl, b->d_slots + id, sizeof(FilterSlot), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return PMF_ERR_CUDA;
+    const long long P = b->npts[id];
+    std::vector<float> tmp(P);
+    if (cudaMemcpy(tmp.data(), f.cur ? sl.buf1 : sl.buf0, sizeof(float) * P, cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return PMF_ERR_CUDA;
+    for (long long i = 0; i < P; ++i) host_out[i] = f.pscale * (double)tmp[i];
+  }
+  return PMF_OK;
+}
+
+long long pmf_batch_bytes(const pmf_batch* b) { return b ? b->bytes : 0; }
+long long pmf_batch_launch_count(const pmf_batch* b) { return b ? b->launches : 0; }
+void pmf_batch_destroy(pmf_batch* b) { free_batch(b); }
 
 }  // extern "C"

@@ -50,6 +50,7 @@ constexpr int kSmemBytes = kOffS + 128 * kSStr * 4;
 constexpr uint32_t kTmemCols = 128;
 constexpr long long kSpin = 1LL << 22;       // bounded mbarrier polls
 
+// One filter launched alone: everything by value in the kernel parameters.
 struct FusedJob {
   DevState* st;
   float* buf0;
@@ -59,6 +60,19 @@ struct FusedJob {
   int N0, N1, do_meas, do_time;
   MeasParams mp;
   TimeConsts tc;
+};
+
+// What one CTA works on: the filter's resident data and this epoch's request.
+struct FusedView {
+  DevState* st;
+  float* buf0;
+  float* buf1;
+  const uint8_t* hart[2];
+  const float* sctab[2];
+  int N0, N1, do_meas, do_time;
+  const MeasParams* mp;     // measurement model
+  const double* z;          // measurement of this epoch
+  const TimeConsts* tc;     // model constants of this time update
 };
 
 // --- PTX wrappers ------------------------------------------------------------
@@ -204,6 +218,8 @@ __device__ __forceinline__ float op_scale(float mx) {
 }
 
 struct Shared {
+  TimeConsts tc;           // copies of the update's constants and measurement model
+  MeasParams mp;
   FrameState fs;           // working copy of the filter's frame state
   uint64_t mbar_mma, mbar_tma;
   uint32_t tmem;
@@ -490,7 +506,7 @@ __device__ void psi_stage(const Shared& sh, float* S, int N0, int N1, int l, int
 }
 
 template <int P>
-__device__ void fused2d(const FusedJob& job, uint8_t* smem) {
+__device__ void fused2d(const FusedView& job, uint8_t* smem) {
   __shared__ Shared sh;
   DevState* st = job.st;
   FrameState& fs = sh.fs;
@@ -507,6 +523,15 @@ __device__ void fused2d(const FusedJob& job, uint8_t* smem) {
 
   for (int i = tid; i < kFsWords; i += kThreads)
     ((unsigned long long*)&fs)[i] = ((const unsigned long long*)&st->f)[i];
+  if (job.do_time)
+    for (int i = tid; i < (int)(sizeof(TimeConsts) / 8); i += kThreads)
+      ((unsigned long long*)&sh.tc)[i] = ((const unsigned long long*)job.tc)[i];
+  if (job.do_meas) {
+    for (int i = tid; i < (int)(sizeof(MeasParams) / 8); i += kThreads)
+      ((unsigned long long*)&sh.mp)[i] = ((const unsigned long long*)job.mp)[i];
+    __syncthreads();
+    if (tid < PMF_MAX_NZ) sh.mp.z[tid] = job.z[tid];
+  }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_mma));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_tma));
@@ -547,7 +572,7 @@ __device__ void fused2d(const FusedJob& job, uint8_t* smem) {
   // ---- measurement update (eq. filt) ----
   if (job.do_meas) {
     if (tid == 0) {
-      const MeasParams& mp = job.mp;
+      const MeasParams& mp = sh.mp;
       const double c0 = fs.c[0], c1 = fs.c[1];
       sh.mc[0] = (float)c0;
       sh.mc[1] = (float)c1;
@@ -565,7 +590,7 @@ __device__ void fused2d(const FusedJob& job, uint8_t* smem) {
       }
     }
     __syncthreads();
-    const int kind = job.mp.kind, nz = job.mp.nz;
+    const int kind = sh.mp.kind, nz = sh.mp.nz;
     const int npts = N0 * N1;
     float emin = INFINITY;
     for (int p = tid; p < npts; p += kThreads) {
@@ -616,7 +641,7 @@ __device__ void fused2d(const FusedJob& job, uint8_t* smem) {
   if (job.do_time) {
     // ---- frame: regrid decision (one thread) and sub-step coefficients ----
     if (tid == 0) {
-      frame_scalar<2>(job.tc, &fs, sh.pend, sh.Mpi);
+      frame_scalar<2>(sh.tc, &fs, sh.pend, sh.Mpi);
       sh.g = (float)fs.g;
       sh.gsc = (float)(fs.g / ((double)N0 * (double)N1));
     }
@@ -626,7 +651,7 @@ __device__ void fused2d(const FusedJob& job, uint8_t* smem) {
     const int exact = fs.exact;
     for (int q = tid; q < l; q += kThreads) {
       double pa[3], pb[3];
-      frame_substep<2>(job.tc, sh.Mpi, q, pa, pb);
+      frame_substep<2>(sh.tc, sh.Mpi, q, pa, pb);
       sh.pa[q][0] = (float)pa[0];
       sh.pa[q][1] = (float)pa[1];
       sh.pb[q] = (float)pb[0];
@@ -813,7 +838,22 @@ done:
 template <int P>
 __global__ void __launch_bounds__(kThreads, 1) k_fused2d(const __grid_constant__ FusedJob job) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  fused2d<P>(job, smem);
+  const FusedView v{job.st, job.buf0, job.buf1, {job.hart[0], job.hart[1]}, {job.sctab[0], job.sctab[1]},
+                    job.N0, job.N1, job.do_meas, job.do_time, &job.mp, job.mp.z, &job.tc};
+  fused2d<P>(v, smem);
+}
+
+// Many filters, one CTA each: items[blockIdx.x] names the filter slot, the
+// parts of the epoch to run and its measurement.
+template <int P>
+__global__ void __launch_bounds__(kThreads, 1) k_fused2d_batch(const FilterSlot* __restrict__ slots,
+                                                               const StepItem* __restrict__ items) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const StepItem& it = items[blockIdx.x];
+  const FilterSlot& sl = slots[it.slot];
+  const FusedView v{sl.st, sl.buf0, sl.buf1, {sl.hart[0], sl.hart[1]}, {sl.sctab[0], sl.sctab[1]},
+                    sl.N0, sl.N1, it.flags & 1, (it.flags >> 1) & 1, sl.mp, it.z, sl.tc};
+  fused2d<P>(v, smem);
 }
 
 // Prior weights exp(-1/2 (x - m0)^T P0^{-1} (x - m0)) on the initial frame (float32 storage).
@@ -886,42 +926,57 @@ int tc_supported(const pmf_config* cfg, std::string* why) {
   return PMF_OK;
 }
 
-int tc_build_tables(const pmf_config* cfg, TcTables* t, std::string* why) {
-  std::memset(t, 0, sizeof(*t));
-  t->prec = cfg->precision;
-  const double scale = cfg->precision == PMF_PREC_FP16X3 ? 16384.0 : 1.0;
-  for (int a = 0; a < cfg->nx; ++a) {
-    const int N = cfg->N[a];
-    std::vector<double> H((size_t)N * N);
-    const double w = 6.283185307179586476925286766559 / N;
-    for (int k = 0; k < N; ++k)
-      for (int j = 0; j < N; ++j) {
-        const long long r = ((long long)k * j) % N;
-        H[(size_t)k * N + j] = std::cos(w * r) + std::sin(w * r);
-      }
-    std::vector<uint8_t> planes;
-    split_planes(H, N, N, cfg->precision, scale, planes);
-    std::vector<float> tab(2 * (2 * N + 1));
-    for (int m = -N; m <= N; ++m) {
-      const double ang = 3.14159265358979323846 * m / N;
-      tab[2 * (m + N)] = (float)std::cos(ang);
-      tab[2 * (m + N) + 1] = (float)std::sin(ang);
+int tc_build_axis_table(int N, int precision, void** dev, size_t* hart_bytes) {
+  const double scale = precision == PMF_PREC_FP16X3 ? 16384.0 : 1.0;
+  std::vector<double> H((size_t)N * N);
+  const double w = 6.283185307179586476925286766559 / N;
+  for (int k = 0; k < N; ++k)
+    for (int j = 0; j < N; ++j) {
+      const long long r = ((long long)k * j) % N;
+      H[(size_t)k * N + j] = std::cos(w * r) + std::sin(w * r);
     }
-    const size_t hb = planes.size(), tb = tab.size() * sizeof(float);
-    if (cudaMalloc(&t->hart[a], hb + tb) != cudaSuccess) {
-      *why = "cudaMalloc of transform tables";
-      return PMF_ERR_OOM;
-    }
-    t->hart_bytes[a] = hb;
-    cudaMemcpy(t->hart[a], planes.data(), hb, cudaMemcpyHostToDevice);
-    cudaMemcpy((uint8_t*)t->hart[a] + hb, tab.data(), tb, cudaMemcpyHostToDevice);
+  std::vector<uint8_t> planes;
+  split_planes(H, N, N, precision, scale, planes);
+  std::vector<float> tab(2 * (2 * N + 1));
+  for (int m = -N; m <= N; ++m) {
+    const double ang = 3.14159265358979323846 * m / N;
+    tab[2 * (m + N)] = (float)std::cos(ang);
+    tab[2 * (m + N) + 1] = (float)std::sin(ang);
   }
+  const size_t hb = planes.size(), tb = tab.size() * sizeof(float);
+  *dev = nullptr;
+  if (cudaMalloc(dev, hb + tb) != cudaSuccess) return PMF_ERR_OOM;
+  *hart_bytes = hb;
+  if (cudaMemcpy(*dev, planes.data(), hb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy((uint8_t*)*dev + hb, tab.data(), tb, cudaMemcpyHostToDevice) != cudaSuccess)
+    return PMF_ERR_CUDA;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_fused2d<PMF_PREC_FP16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     cudaFuncSetAttribute(k_fused2d<PMF_PREC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     cudaFuncSetAttribute(k_fused2d<PMF_PREC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaFuncSetAttribute(k_fused2d_batch<PMF_PREC_FP16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaFuncSetAttribute(k_fused2d_batch<PMF_PREC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaFuncSetAttribute(k_fused2d_batch<PMF_PREC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     attr = true;
+  }
+  return PMF_OK;
+}
+
+size_t tc_axis_table_bytes(int N, int precision) {
+  const size_t plane = (size_t)N / 8 * (precision == PMF_PREC_TF32 ? 4096 : 2048);
+  return plane * (precision == PMF_PREC_TF32 ? 1 : 2) + 2 * (2 * N + 1) * sizeof(float);
+}
+
+int tc_build_tables(const pmf_config* cfg, TcTables* t, std::string* why) {
+  std::memset(t, 0, sizeof(*t));
+  t->prec = cfg->precision;
+  for (int a = 0; a < cfg->nx; ++a) {
+    const int rc = tc_build_axis_table(cfg->N[a], cfg->precision, &t->hart[a], &t->hart_bytes[a]);
+    if (rc) {
+      *why = "transform tables";
+      return rc;
+    }
   }
   return PMF_OK;
 }
@@ -965,6 +1020,17 @@ int tc_step(const Dims& d, const pmf_config& cfg, const TcTables* t, const MeasP
     k_fused2d<PMF_PREC_BF16X3><<<1, kThreads, kSmemBytes, s>>>(job);
   else
     k_fused2d<PMF_PREC_TF32><<<1, kThreads, kSmemBytes, s>>>(job);
+  return 1;
+}
+
+int tc_batch_step(int precision, const FilterSlot* slots, const StepItem* items, int k, cudaStream_t s) {
+  if (k <= 0) return 0;
+  if (precision == PMF_PREC_FP16X3)
+    k_fused2d_batch<PMF_PREC_FP16X3><<<k, kThreads, kSmemBytes, s>>>(slots, items);
+  else if (precision == PMF_PREC_BF16X3)
+    k_fused2d_batch<PMF_PREC_BF16X3><<<k, kThreads, kSmemBytes, s>>>(slots, items);
+  else
+    k_fused2d_batch<PMF_PREC_TF32><<<k, kThreads, kSmemBytes, s>>>(slots, items);
   return 1;
 }
 

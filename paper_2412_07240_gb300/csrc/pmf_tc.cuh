@@ -14,9 +14,32 @@ struct TcTables {
   int prec;
 };
 
+// Resident description of one filter of a batch (device memory).
+struct FilterSlot {
+  DevState* st;
+  float* buf0;
+  float* buf1;
+  const uint8_t* hart[2];   // split Hartley planes per axis
+  const float* sctab[2];    // (cos, sin)(pi m / N) tables per axis
+  int N0, N1;
+  const MeasParams* mp;     // measurement model of the filter
+  const TimeConsts* tc;     // constants of the filter's current tau
+};
+
+// One filter's request in a batched epoch: flags bit 0 = measurement update
+// with z, bit 1 = time update with the slot's constants.
+struct StepItem {
+  int slot;
+  int flags;
+  double z[PMF_MAX_NZ];
+};
+
 // PMF_OK if the fused kernel can hold this grid at this precision.
 int tc_supported(const pmf_config* cfg, std::string* why);
 int tc_build_tables(const pmf_config* cfg, TcTables* t, std::string* why);
+// Split Hartley planes and the (cos, sin)(pi m / N) table of one axis size (one allocation).
+int tc_build_axis_table(int N, int precision, void** dev, size_t* hart_bytes);
+size_t tc_axis_table_bytes(int N, int precision);
 void tc_free_tables(TcTables* t);
 // Prior weights and their moments; returns the number of kernel launches.
 int tc_prior(const Dims& d, DevState* st, const double* prior_aux, float* X, double* partials,
@@ -24,5 +47,8 @@ int tc_prior(const Dims& d, DevState* st, const double* prior_aux, float* X, dou
 // One fused launch: measurement update (if mp) then time update (if tc).
 int tc_step(const Dims& d, const pmf_config& cfg, const TcTables* t, const MeasParams* mp,
             const TimeConsts* tc, DevState* st, float* b0, float* b1, cudaStream_t s);
+
+// One launch, one CTA per item (items in device memory); returns launches.
+int tc_batch_step(int precision, const FilterSlot* slots, const StepItem* items, int k, cudaStream_t s);
 
 }  // namespace pmf
