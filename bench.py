@@ -245,6 +245,82 @@ def run_reference(args, ws, rank, pg):
     print(json.dumps(line))
 
 
+def bench_batch(args, ws, rank, pg):
+    """The 4096-filter batch: one fused launch per epoch over all filters."""
+    import numpy as np
+    import torch
+    import workloads as w
+    from paper_2412_07240_gb300 import Batch, Filter
+    epochs = args.warmup + args.steps + 1
+    cfgs, meas, dt, truth, z = w.c4_batch(count=args.count, epochs=epochs)
+    P = np.array([c.N[0] * c.N[1] for c in cfgs], dtype=np.int64)
+    ids = np.arange(len(cfgs))
+    b = Batch(cfgs, [meas] * len(cfgs), precision=args.precision)
+    flush = torch.empty(512 * (1 << 20) // 4, dtype=torch.float32, device="cuda")
+    for k in range(args.warmup):
+        b.step(ids, z[:, k], dt)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    l0 = b.launches
+    _barrier(pg)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record()
+            b.step(ids, z[:, args.warmup + k], dt)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+    ms = [a.elapsed_time(c) for a, c in ev]
+    t_ms = _max_over_ranks(pg, sum(ms))
+    value = ws * P.sum() * args.steps / (t_ms * 1e-3)
+    bad = int((b.status() != 0).sum())
+    # end to end: measurements from host, moments back, every epoch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ne = min(5, args.steps)
+    for k in range(ne):
+        b.step(ids, z[:, args.warmup + k], dt)
+        b.moments(strict=False)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / ne
+    # plain float64 per-filter path on a subset, scaled by points
+    sub = ids[:: max(1, len(ids) // 64)]
+    fs = [Filter(cfgs[i], precision="fp64") for i in sub]
+    for f, i in zip(fs, sub):
+        f.step(meas, z[i, 0], dt)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for f, i in zip(fs, sub):
+        f.step(meas, z[i, 1], dt)
+    e1.record()
+    torch.cuda.synchronize()
+    fp64_rate = P[sub].sum() / (e0.elapsed_time(e1) * 1e-3)
+    flops = float(sum(4.0 * c.N[0] * c.N[1] * (c.N[0] + c.N[1]) for c in cfgs))
+    kernel_ms = float(np.mean(ms))
+    peaks, src = _peaks()
+    ach = flops / (kernel_ms * 1e-3) / 1e12
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": f"f32 ({args.precision} split GEMMs)",
+            "data": "synthetic (seeded truth and measurements)",
+            "config": {"workload": f"c4_batch_{len(cfgs)}x2d_mixed", "points": int(P.sum()),
+                       "precision": args.precision, "l2": "flushed between timed steps",
+                       "parallelism": f"replicas x{ws}"},
+            "e2e": {"value": ws * P.sum() / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(len(cfgs) * 24), "d2h_bytes_per_step": int(len(cfgs) * 48),
+                    "ms_per_step": e2e_ms},
+            "gpu_launches": int(b.launches - l0 - ne),
+            "fp64_gpu": {"value": fp64_rate, "unit": UNIT, "filters_timed": int(len(sub))},
+            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+            "degenerate_filters": bad,
+            "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks.get("bf16_tflops"),
+                         "unit": "TFLOP/s", "frac": ach / peaks.get("bf16_tflops"), "traffic": None,
+                         "kernel": "k_fused2d_batch", "flops_per_launch": flops},
+            "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -254,6 +330,7 @@ def main():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--precision", default="fp16x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--count", type=int, default=4096, help="filters of the c4 batch workload")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     ws, rank, local, pg = _dist()
@@ -264,6 +341,11 @@ def main():
     import numpy as np
     import torch
     torch.cuda.set_device(local)
+    if args.workload == "c4":
+        bench_batch(args, ws, rank, pg)
+        if pg is not None:
+            pg.destroy_process_group()
+        return
     sc = _scenario(args.workload, args.warmup + args.steps + 1)
     P = 1
     for n in sc.cfg.N:

@@ -300,13 +300,17 @@ class Batch:
         if rc != OK:
             raise PmfError(rc, "pmf_batch_step failed")
 
-    def moments(self, ids=None):
+    def moments(self, ids=None, strict=True):
+        """Means and covariances; with strict=False a filter that reported a
+        degenerate normaliser does not raise (see status())."""
         ids = np.arange(self.count, dtype=np.int32) if ids is None else np.ascontiguousarray(ids, dtype=np.int32)
         k = ids.size
         m = np.empty((k, 2))
         P = np.empty((k, 2, 2))
         rc = self._lib.pmf_batch_moments(self._h, _iptr(ids), k, _dptr(m), _dptr(P))
         if rc == ERR_DEGENERATE:
+            if not strict:
+                return m, P
             raise Degenerate(rc, "degenerate normaliser in the batch")
         if rc != OK:
             raise PmfError(rc, "pmf_batch_moments failed")

@@ -289,4 +289,56 @@ __device__ inline bool finalize_core(int nx, FrameState* st, const double* tot, 
   return true;
 }
 
+// Fixed-size finalisation (n <= 3, registers, one reciprocal of S0): same
+// results as finalize_core.
+template <int n>
+__device__ inline bool finalize_t(FrameState* st, const double* tot, int use_pending, const double* pend) {
+  const double S0 = tot[0];
+  if (!(S0 > 0.0) || !isfinite(S0)) {
+    st->status = PMF_ERR_DEGENERATE;
+    return false;
+  }
+  double c[n], M[n * n], Minv[n * n], V;
+#pragma unroll
+  for (int i = 0; i < n; ++i) c[i] = use_pending ? pend[i] : st->c[i];
+#pragma unroll
+  for (int i = 0; i < n * n; ++i) {
+    M[i] = use_pending ? pend[3 + i] : st->M[i];
+    Minv[i] = use_pending ? pend[12 + i] : st->Minv[i];
+  }
+  V = use_pending ? pend[21] : st->V;
+  const double r = 1.0 / S0;
+  const int k2[3][3] = {{4, 5, 6}, {5, 7, 8}, {6, 8, 9}};
+  double mu[n], Cu[n * n], cov[n * n];
+#pragma unroll
+  for (int a = 0; a < n; ++a) mu[a] = tot[1 + a] * r;
+#pragma unroll
+  for (int a = 0; a < n; ++a)
+#pragma unroll
+    for (int b = 0; b < n; ++b) Cu[a * n + b] = fma(tot[k2[a][b]], r, -mu[a] * mu[b]);
+  cong_t<n>(M, Cu, cov);
+#pragma unroll
+  for (int a = 0; a < n; ++a) {
+    double m = c[a];
+#pragma unroll
+    for (int b = 0; b < n; ++b) m = fma(M[a * n + b], mu[b], m);
+    st->mean[a] = m;
+  }
+#pragma unroll
+  for (int i = 0; i < n * n; ++i) st->cov[i] = cov[i];
+  if (use_pending) {
+#pragma unroll
+    for (int i = 0; i < n; ++i) st->c[i] = c[i];
+#pragma unroll
+    for (int i = 0; i < n * n; ++i) {
+      st->M[i] = M[i];
+      st->Minv[i] = Minv[i];
+    }
+    st->V = V;
+  }
+  st->S0 = S0;
+  st->pscale = r / V;
+  return true;
+}
+
 }  // namespace pmf

@@ -261,63 +261,79 @@ __device__ __forceinline__ float block_min(Shared& sh, float v, int slot) {
   return m;
 }
 
-// Compensated (Kahan) float32 accumulation of the moment sums of one thread.
+// Double-float (hi + lo float32 pair) arithmetic: float64-class accuracy for
+// the moment sums at float32 throughput (GB300 issues float64 at ~1/32 of the
+// float32 rate, so block-wide float64 reductions are avoided).
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb);
+  const float t = e + a.lo + b.lo;
+  const float h = s + t;
+  return DF{h, t - (h - s)};
+}
+__device__ __forceinline__ DF df_add1(DF a, float b) { return df_add(a, DF{b, 0.0f}); }
+
+// Moment sums of one thread: S0, S1 (u0, u1), S2 (u0u0, u0u1, u1u1).  Points
+// arrive in groups (a row segment of 4); the group sums are formed in float32
+// and added in double-float.
 struct Moments {
-  float s[6], c[6];
+  DF s[6];
   __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int i = 0; i < 6; ++i) s[i] = c[i] = 0.0f;
+    for (int i = 0; i < 6; ++i) s[i] = DF{0.0f, 0.0f};
   }
-  __device__ __forceinline__ void add1(int i, float x) {
-    const float y = x - c[i];
-    const float t = s[i] + y;
-    c[i] = (t - s[i]) - y;
-    s[i] = t;
-  }
-  // S0, S1 (u0, u1), S2 (u0u0, u0u1, u1u1)
-  __device__ __forceinline__ void add(float x, float u0, float u1) {
-    add1(0, x);
-    add1(1, x * u0);
-    add1(2, x * u1);
-    add1(3, x * u0 * u0);
-    add1(4, x * u0 * u1);
-    add1(5, x * u1 * u1);
+  // four points x.x..x.w at (u0, u1 + 0..3)
+  __device__ __forceinline__ void add4(float4 x, float u0, float u1) {
+    const float a0 = x.x + x.y + x.z + x.w;
+    const float a1 = x.y + 2.0f * x.z + 3.0f * x.w;       // sum x * (u1' - u1)
+    const float a2 = x.y + 4.0f * x.z + 9.0f * x.w;       // sum x * (u1' - u1)^2
+    const float b1 = fmaf(u1, a0, a1);                      // sum x u1'
+    s[0] = df_add1(s[0], a0);
+    s[1] = df_add1(s[1], a0 * u0);
+    s[2] = df_add1(s[2], b1);
+    s[3] = df_add1(s[3], a0 * u0 * u0);
+    s[4] = df_add1(s[4], b1 * u0);
+    s[5] = df_add1(s[5], fmaf(u1, fmaf(u1, a0, 2.0f * a1), a2));   // sum x u1'^2
   }
 };
 
-// Sum the per-thread moment sums over the block in float64 into sh.tot
-// ({S0, S1[3], S2[6]} layout); valid in thread 0 after the call.
+// Sum the per-thread moment sums over the block into sh.tot ({S0, S1[3],
+// S2[6]} layout, float64); valid in thread 0 after the call.
 __device__ __forceinline__ void block_moments(Shared& sh, const Moments& m) {
-  double a[6];
+  DF a[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    a[i] = (double)m.s[i] - (double)m.c[i];
-    for (int o = 16; o; o >>= 1) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
+    a[i] = m.s[i];
+    for (int o = 16; o; o >>= 1) {
+      DF b{__shfl_xor_sync(0xffffffffu, a[i].hi, o), __shfl_xor_sync(0xffffffffu, a[i].lo, o)};
+      a[i] = df_add(a[i], b);
+    }
   }
   if ((threadIdx.x & 31) == 0)
 #pragma unroll
-    for (int i = 0; i < 6; ++i) sh.redd[threadIdx.x >> 5][i] = a[i];
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int l = threadIdx.x;
-#pragma unroll
     for (int i = 0; i < 6; ++i) {
-      double v = l < kThreads / 32 ? sh.redd[l][i] : 0.0;
-      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      a[i] = v;
+      sh.redd[threadIdx.x >> 5][i] = (double)a[i].hi + (double)a[i].lo;
     }
-    if (l == 0) {
-      sh.tot[0] = a[0];
-      sh.tot[1] = a[1];
-      sh.tot[2] = a[2];
-      sh.tot[3] = 0.0;
-      sh.tot[4] = a[3];
-      sh.tot[5] = a[4];
-      sh.tot[6] = 0.0;
-      sh.tot[7] = a[5];
-      sh.tot[8] = 0.0;
-      sh.tot[9] = 0.0;
-    }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int w = 0; w < kThreads / 32; ++w)
+#pragma unroll
+      for (int i = 0; i < 6; ++i) v[i] += sh.redd[w][i];
+    sh.tot[0] = v[0];
+    sh.tot[1] = v[1];
+    sh.tot[2] = v[2];
+    sh.tot[3] = 0.0;
+    sh.tot[4] = v[3];
+    sh.tot[5] = v[4];
+    sh.tot[6] = 0.0;
+    sh.tot[7] = v[5];
+    sh.tot[8] = 0.0;
+    sh.tot[9] = 0.0;
   }
 }
 
@@ -334,7 +350,7 @@ __device__ __forceinline__ float meas_e(const Shared& sh, int kind, int nz, floa
     const float x0 = sh.mc[0] + d0, x1 = sh.mc[1] + d1;
     const float den = sqrtf(x0 * x0 + x1 * x1) + sh.mcn;
     const float num = 2.0f * (sh.mc[0] * d0 + sh.mc[1] * d1) + d0 * d0 + d1 * d1;
-    r[0] = sh.mr0[0] - (den > 0.0f ? num / den : 0.0f);
+    r[0] = sh.mr0[0] - (den > 0.0f ? __fdividef(num, den) : 0.0f);
     r[1] = 0.0f;
   }
   float e = r[0] * sh.mRinv[0] * r[0];
@@ -399,7 +415,7 @@ template <int P>
 __device__ void build_interp(const Shared& sh, uint8_t* W, int N, const float* sctab, float sw, int realign) {
   const int q4 = N / 4;
   for (int t = threadIdx.x; t < N * q4; t += kThreads) {
-    const int n = t / q4, c = (t % q4) * 4;
+    const int n = t % N, c = (t / N) * 4;   // consecutive threads: consecutive rows
     float k[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -418,7 +434,7 @@ __device__ void build_interp(const Shared& sh, uint8_t* W, int N, const float* s
           const float cm = sctab[2 * (m + N)], sm = sctab[2 * (m + N) + 1];
           const float sv = sm * sh.rcf[n] + cm * sh.rsf[n];
           const float cv = cm * sh.rcf[n] - sm * sh.rsf[n];
-          v = ((m & 1) ? -1.0f : 1.0f) * sh.rS[n] * cv / ((float)N * sv);
+          v = __fdividef(((m & 1) ? -1.0f : 1.0f) * sh.rS[n] * cv, (float)N * sv);
         }
       }
       k[i] = v;
@@ -428,11 +444,14 @@ __device__ void build_interp(const Shared& sh, uint8_t* W, int N, const float* s
 }
 
 // Staging rows r < nr, columns < nc -> operand planes (scaled by s).
+// (consecutive threads take consecutive rows: in the core-matrix layout a row's
+// consecutive columns are 128 bytes apart, 8 consecutive rows share 128 bytes)
 template <int P>
-__device__ __forceinline__ void stage_to_operand(uint8_t* A, const float* S, int nr, int nc, float s) {
+__device__ __forceinline__ void stage_to_operand(uint8_t* A, const float* S, int nr, int nc, float s,
+                                                 int t0, int tstep) {
   const int q4 = nc / 4;
-  for (int t = threadIdx.x; t < nr * q4; t += kThreads) {
-    const int r = t / q4, c = (t % q4) * 4;
+  for (int t = t0; t < nr * q4; t += tstep) {
+    const int r = t % nr, c = (t / nr) * 4;
     store4<P>(A, r, c, *(const float4*)(S + r * kSStr + c), s);
   }
 }
@@ -567,7 +586,9 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       *(float4*)(S + r * kSStr + c) = x;
     }
   }
-  float smax = 0.0f;   // max |weight| (operand scale of the first GEMM)
+  float smax = 0.0f;      // max |weight| (operand scale of the first GEMM)
+  float sa_first = 1.0f;  // scale of the R1 operand
+  int realign = 0, l = 0, exact = 0;
 
   // ---- measurement update (eq. filt) ----
   if (job.do_meas) {
@@ -591,32 +612,56 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     }
     __syncthreads();
     const int kind = sh.mp.kind, nz = sh.mp.nz;
-    const int npts = N0 * N1;
     float emin = INFINITY;
-    for (int p = tid; p < npts; p += kThreads) {
-      const int r = p / N1, c = p - r * N1;
-      emin = fminf(emin, meas_e(sh, kind, nz, r - 0.5f * (N0 - 1), c - 0.5f * (N1 - 1)));
+    for (int t = tid; t < np4; t += kThreads) {
+      const int r = t / q1, c = (t - r * q1) * 4;
+      const float u0 = r - 0.5f * (N0 - 1), u1 = c - 0.5f * (N1 - 1);
+      emin = fminf(emin, fminf(fminf(meas_e(sh, kind, nz, u0, u1), meas_e(sh, kind, nz, u0, u1 + 1.0f)),
+                               fminf(meas_e(sh, kind, nz, u0, u1 + 2.0f), meas_e(sh, kind, nz, u0, u1 + 3.0f))));
     }
     emin = block_min(sh, emin, 0);
     Moments mo;
     mo.zero();
-    for (int p = tid; p < npts; p += kThreads) {
-      const int r = p / N1, c = p - r * N1;
+    for (int t = tid; t < np4; t += kThreads) {
+      const int r = t / q1, c = (t - r * q1) * 4;
       const float u0 = r - 0.5f * (N0 - 1), u1 = c - 0.5f * (N1 - 1);
-      const float x = S[r * kSStr + c] * expf(-(meas_e(sh, kind, nz, u0, u1) - emin));
-      S[r * kSStr + c] = x;
-      mo.add(x, u0, u1);
-      smax = fmaxf(smax, x);
+      float4 x = *(const float4*)(S + r * kSStr + c);
+      x.x *= __expf(emin - meas_e(sh, kind, nz, u0, u1));
+      x.y *= __expf(emin - meas_e(sh, kind, nz, u0, u1 + 1.0f));
+      x.z *= __expf(emin - meas_e(sh, kind, nz, u0, u1 + 2.0f));
+      x.w *= __expf(emin - meas_e(sh, kind, nz, u0, u1 + 3.0f));
+      *(float4*)(S + r * kSStr + c) = x;
+      mo.add4(x, u0, u1);
+      smax = amax4(smax, x);
     }
     block_moments(sh, mo);
+  } else {
+    smax = stage_max(S, N0, N1);
+  }
+  {
+    // Thread 0 finalises the moments and (time update) computes the frame in
+    // float64 while warps 1.. convert the staged weights into the R1 operand,
+    // which needs neither.
+    const float sa0 = op_scale<P>(block_max(sh, smax, 1));
     if (tid == 0) {
-      if (!finalize_core(2, &fs, sh.tot, 0, nullptr)) {
-        sh.degenerate = 1;
-      } else {
-        sh.ps = (float)fs.pscale;   // the staged weights times ps are normalised
-        fs.pscale = 1.0;
-        fs.S0 = 1.0 / fs.V;
+      bool ok = true;
+      if (job.do_meas) {
+        ok = finalize_t<2>(&fs, sh.tot, 0, nullptr);
+        if (!ok) {
+          sh.degenerate = 1;
+        } else {
+          sh.ps = (float)fs.pscale;   // the staged weights times ps are normalised
+          fs.pscale = 1.0;
+          fs.S0 = 1.0 / fs.V;
+        }
       }
+      if (ok && job.do_time) {
+        frame_scalar<2>(sh.tc, &fs, sh.pend, sh.Mpi);
+        sh.g = (float)fs.g;
+        sh.gsc = (float)(fs.g / ((double)N0 * (double)N1));
+      }
+    } else if (job.do_time && warp > 0) {
+      stage_to_operand<P>(A, S, N0, N1, sa0, tid - 32, kThreads - 32);
     }
     __syncthreads();
     if (sh.degenerate) goto done;
@@ -634,21 +679,14 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       if (tid == 0) fs.cur = cur ^ 1;
       goto done;
     }
-  } else {
-    smax = stage_max(S, N0, N1);
+    sa_first = sa0;
   }
 
-  if (job.do_time) {
-    // ---- frame: regrid decision (one thread) and sub-step coefficients ----
-    if (tid == 0) {
-      frame_scalar<2>(sh.tc, &fs, sh.pend, sh.Mpi);
-      sh.g = (float)fs.g;
-      sh.gsc = (float)(fs.g / ((double)N0 * (double)N1));
-    }
-    __syncthreads();
-    const int realign = fs.realign;
-    const int l = fs.l;
-    const int exact = fs.exact;
+  {
+    // ---- sub-step coefficients, regrid rows (or re-alignment) ----
+    realign = fs.realign;
+    l = fs.l;
+    exact = fs.exact;
     for (int q = tid; q < l; q += kThreads) {
       double pa[3], pb[3];
       frame_substep<2>(sh.tc, sh.Mpi, q, pa, pb);
@@ -685,14 +723,17 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         S[r * kSStr + c] = G[p];
         smax = fmaxf(smax, fabsf(G[p]));
       }
+      sa_first = op_scale<P>(block_max(sh, smax, 0));
+      stage_to_operand<P>(A, S, N0, N1, sa_first, tid, kThreads);
     } else {
       regrid_rows(sh, fs, 1, N1);
     }
     __syncthreads();
+  }
 
-    // ---- R1 operand (rows j0, columns j1; K-major) and the matrix I1 ----
-    float sa = op_scale<P>(block_max(sh, smax, 1));
-    stage_to_operand<P>(A, S, N0, N1, sa);
+  {
+    // ---- the matrix I1; the R1 operand is already written ----
+    float sa = sa_first;
     build_interp<P>(sh, W, N1, job.sctab[1], sw, realign);
     fence_async_smem();
     __syncthreads();
@@ -746,7 +787,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         psi_stage(sh, S, N0, N1, l, exact);
         __syncthreads();
         sa = op_scale<P>(block_max(sh, stage_max(S, N1, N0), stage & 1));
-        stage_to_operand<P>(A, S, N1, N0, sa);
+        stage_to_operand<P>(A, S, N1, N0, sa, tid, kThreads);
       } else {
         float m = 0.0f;
         for (int c = 0; c < ncol; c += 4) m = amax4(m, tmem_ld4(tlane + c0 + c));
@@ -817,13 +858,10 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         const float4 x = *(const float4*)(S + r * kSStr + c);
         *(float4*)(out + (size_t)r * N1 + c) = x;
         const float u0 = r - 0.5f * (N0 - 1), u1 = c - 0.5f * (N1 - 1);
-        mo.add(x.x, u0, u1);
-        mo.add(x.y, u0, u1 + 1.0f);
-        mo.add(x.z, u0, u1 + 2.0f);
-        mo.add(x.w, u0, u1 + 3.0f);
+        mo.add4(x, u0, u1);
       }
       block_moments(sh, mo);
-      if (tid == 0 && finalize_core(2, &fs, sh.tot, 1, sh.pend)) fs.cur = cur ^ 1;
+      if (tid == 0 && finalize_t<2>(&fs, sh.tot, 1, sh.pend)) fs.cur = cur ^ 1;
     }
   }
 
