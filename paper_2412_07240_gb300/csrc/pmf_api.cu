@@ -28,6 +28,7 @@ struct pmf_ctx {
   double* hinv[MAXN] = {nullptr, nullptr, nullptr};
   double* prior_aux = nullptr;  // P0^{-1} (9) and m0 (3)
   TcTables tct{};               // tensor-core path tables (pmf_tc.cu)
+  void* tc3 = nullptr;          // 3-D pipeline state (pmf_tc3.cu)
   TimeConsts tc{};
   double tc_tau = -1.0;
   long long launches = 0;
@@ -267,7 +268,17 @@ void free_ctx(pmf_ctx* ctx) {
     cudaFree(ctx->hinv[a]);
   }
   tc_free_tables(&ctx->tct);
+  tc3_free(ctx->tc3);
   delete ctx;
+}
+
+// One launch (2-D fused kernel) or the 3-D pipelines; returns kernel launches.
+int fast_step(pmf_ctx* ctx, const MeasParams* mp, const TimeConsts* tc) {
+  if (ctx->path == 2)
+    return tc3_step(ctx->tc3, ctx->dims, ctx->cfg, &ctx->tct, mp, tc, ctx->st, (float*)ctx->buf[0],
+                    (float*)ctx->buf[1], ctx->stream);
+  return tc_step(ctx->dims, ctx->cfg, &ctx->tct, mp, tc, ctx->st, (float*)ctx->buf[0], (float*)ctx->buf[1],
+                 ctx->stream);
 }
 
 int check_status(pmf_ctx* ctx) {
@@ -321,7 +332,7 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
       free_ctx(ctx);
       return rc;
     }
-    ctx->path = 1;
+    ctx->path = cfg->nx == 3 ? 2 : 1;
   }
 
 #define ALLOC(ptr, bytes)                                     \
@@ -355,6 +366,7 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
     }
   } else {
     rc = tc_build_tables(cfg, &ctx->tct, &why);
+    if (rc == PMF_OK && ctx->path == 2) rc = tc3_alloc(&ctx->tc3);
     if (rc) {
       free_ctx(ctx);
       return rc;
@@ -408,8 +420,7 @@ int pmf_time_update(pmf_ctx* ctx, double tau) {
                     ctx->partials, ctx->pend, ctx->interp, ctx->hfwd, ctx->hinv, ctx->stream);
     ctx->launches += launches_time_f64(ctx->cfg.nx);
   } else {
-    ctx->launches += tc_step(ctx->dims, ctx->cfg, &ctx->tct, nullptr, &ctx->tc, ctx->st,
-                             (float*)ctx->buf[0], (float*)ctx->buf[1], ctx->stream);
+    ctx->launches += fast_step(ctx, nullptr, &ctx->tc);
   }
   PMF_CUDA(ctx, cudaGetLastError());
   return PMF_OK;
@@ -425,8 +436,7 @@ int pmf_meas_update(pmf_ctx* ctx, const pmf_meas* meas) {
                     ctx->partials, ctx->stream);
     ctx->launches += kLaunchesMeasF64;
   } else {
-    ctx->launches += tc_step(ctx->dims, ctx->cfg, &ctx->tct, &mp, nullptr, ctx->st,
-                             (float*)ctx->buf[0], (float*)ctx->buf[1], ctx->stream);
+    ctx->launches += fast_step(ctx, &mp, nullptr);
   }
   PMF_CUDA(ctx, cudaGetLastError());
   return PMF_OK;
@@ -452,8 +462,7 @@ int pmf_step(pmf_ctx* ctx, const pmf_meas* meas, double tau) {
     }
     tcp = &ctx->tc;
   }
-  ctx->launches += tc_step(ctx->dims, ctx->cfg, &ctx->tct, &mp, tcp, ctx->st, (float*)ctx->buf[0],
-                           (float*)ctx->buf[1], ctx->stream);
+  ctx->launches += fast_step(ctx, &mp, tcp);
   PMF_CUDA(ctx, cudaGetLastError());
   return PMF_OK;
 }

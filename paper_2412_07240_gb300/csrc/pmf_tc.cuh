@@ -48,6 +48,12 @@ int tc_prior(const Dims& d, DevState* st, const double* prior_aux, float* X, dou
 int tc_step(const Dims& d, const pmf_config& cfg, const TcTables* t, const MeasParams* mp,
             const TimeConsts* tc, DevState* st, float* b0, float* b1, cudaStream_t s);
 
+// 3-D grids (pmf_tc3.cu): per-context device state, and one epoch.
+int tc3_alloc(void** handle);
+void tc3_free(void* handle);
+int tc3_step(void* handle, const Dims& d, const pmf_config& cfg, const TcTables* t, const MeasParams* mp,
+             const TimeConsts* tcs, DevState* st, float* b0, float* b1, cudaStream_t s);
+
 // One launch, one CTA per item (items in device memory); returns launches.
 int tc_batch_step(int precision, const FilterSlot* slots, const StepItem* items, int k, cudaStream_t s);
 

@@ -1,0 +1,982 @@
+// Tensor-core path for 3-D grids (N0, N1, N2 multiples of 16, at most 128):
+// the grid lives in HBM/L2 and each time update runs three on-chip pipelines.
+//
+//   meas   M1 exponent minimum, M2 likelihood multiply + moment partials,
+//          F  moments, normaliser, frame (float64), sub-step coefficients,
+//             regrid rows of the three axes
+//   time   [realign gather + copy-back when the frame is re-aligned]
+//          A  per slice j0: regrid + Hartley along axes 2 and 1 (4 GEMMs) -> T
+//          B  per tile of 128 lines along axis 0, closed under sign flips
+//             ({k1, -k1} x (C u -C)): regrid + Hartley along axis 0, the 3-D
+//             diffusion multiplier with the separable-to-3-D parity fix-up on
+//             8-point orbits (Sec. V-B steps 2-4), inverse along axis 0 -> T
+//          C  per slice: inverse along axes 2 and 1, moment partials -> weights
+//          F2 moments, normaliser, frame commit
+//
+// GEMM stages, operand layouts and split formats are those of the 2-D fused
+// kernel (pmf_tcops.cuh).  Every CTA scales its own operands.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "pmf_device.cuh"
+#include "pmf_kernels.cuh"
+#include "pmf_tc.cuh"
+#include "pmf_tcops.cuh"
+
+namespace pmf {
+
+namespace {
+
+constexpr int kT = 512;
+constexpr int kOffA = 0, kOffW = 65536, kOffS = 131072;
+constexpr int kSStr = 132;
+constexpr int kSmem = kOffS + 128 * kSStr * 4;
+constexpr uint32_t kTmemCols = 128;
+
+struct Geo3 {
+  int N[3];
+  long long P;
+};
+
+// Per-update scalars written by the frame kernel for the time-update kernels.
+struct Update3 {
+  float pa[MAXL][3];
+  float pb[MAXL][3];
+  int l, exact, realign, skip;   // skip: the measurement update was degenerate
+  float gsc;                 // trace factor / (N0 N1 N2)
+  RegridRows rows[3];        // regrid rows per axis
+};
+
+struct Job3 {
+  DevState* st;
+  float* buf0;
+  float* buf1;
+  const uint8_t* hart[3];
+  const float* sctab[3];
+  Geo3 g;
+  double* partials;          // per-CTA moment partials (10 doubles each)
+  unsigned int* emin_bits;   // float bits of the exponent minimum
+  Update3* up;               // device
+  double* pend;              // pending frame (device)
+  int precision;
+};
+
+struct Smem3 {
+  uint64_t mbar_mma, mbar_tma;
+  uint32_t tmem;
+  int abort;
+  float redf[2][16];
+  DF redd[16][6];
+};
+
+__device__ __forceinline__ float block_max3(Smem3& sh, float v, int slot) {
+  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) sh.redf[slot][threadIdx.x >> 5] = v;
+  __syncthreads();
+  float m = 0.0f;
+#pragma unroll
+  for (int w = 0; w < kT / 32; ++w) m = fmaxf(m, sh.redf[slot][w]);
+  return m;
+}
+
+// Block sum of double-float moment sums; thread 0 writes the 10 float64
+// partials {S0, S1[3], S2[6]} of this CTA.
+__device__ void block_partials3(Smem3& sh, const DF* s, double* out) {
+  DF a[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    a[i] = s[i];
+    for (int o = 16; o; o >>= 1) {
+      DF b{__shfl_xor_sync(0xffffffffu, a[i].hi, o), __shfl_xor_sync(0xffffffffu, a[i].lo, o)};
+      a[i] = df_add(a[i], b);
+    }
+  }
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int i = 0; i < 6; ++i) sh.redd[threadIdx.x >> 5][i] = a[i];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    DF v[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      v[i] = threadIdx.x < kT / 32 ? sh.redd[threadIdx.x][i] : DF{0.0f, 0.0f};
+      for (int o = 16; o; o >>= 1) {
+        DF b{__shfl_xor_sync(0xffffffffu, v[i].hi, o), __shfl_xor_sync(0xffffffffu, v[i].lo, o)};
+        v[i] = df_add(v[i], b);
+      }
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int i = 0; i < 6; ++i) out[i] = (double)v[i].hi + (double)v[i].lo;
+  }
+}
+
+// --- tensor-core plumbing shared by the three pipelines -----------------------
+struct Pipe {
+  uint32_t tmem, tlane, mb_mma, mb_tma, ph_mma, ph_tma;
+};
+
+__device__ void pipe_init(Smem3& sh, Pipe& p) {
+  const int warp = threadIdx.x >> 5;
+  p.mb_mma = su32(&sh.mbar_mma);
+  p.mb_tma = su32(&sh.mbar_tma);
+  p.ph_mma = p.ph_tma = 0;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(p.mb_mma));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(p.mb_tma));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    sh.abort = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&sh.tmem)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  p.tmem = sh.tmem;
+  p.tlane = p.tmem + ((uint32_t)((warp & 3) * 32) << 16);
+}
+
+__device__ void pipe_done(Smem3& sh, const Pipe& p) {
+  tc_before_sync();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(p.tmem), "r"(kTmemCols));
+}
+
+// After the operand and matrix of a GEMM are in shared memory (generic stores
+// fenced by the caller's __syncthreads): optionally TMA-load the Hartley planes
+// of size N into W, then issue the GEMM (thread 0).  Returns false on timeout.
+template <int P>
+__device__ bool pipe_issue(Smem3& sh, Pipe& p, uint8_t* A, uint8_t* W, const uint8_t* hart, int Nh, int a_mn,
+                           int nout, int K) {
+  if (threadIdx.x == 0) {
+    tc_after_sync();
+    bool ok = true;
+    if (hart) {
+      const uint32_t pbytes = (uint32_t)Nh * (uint32_t)(Fmt<P>::rowblk / 8);
+      expect_tx(p.mb_tma, pbytes * Fmt<P>::planes);
+      for (int pl = 0; pl < Fmt<P>::planes; ++pl)
+        bulk_load(su32(W) + pl * kPlane, hart + (size_t)pl * pbytes, pbytes, p.mb_tma);
+      ok = mbar_wait(p.mb_tma, p.ph_tma);
+    }
+    if (ok) issue_stage<P>(p.tmem, su32(A), a_mn, su32(W), nout, K, p.mb_mma);
+    else sh.abort = 1;
+  }
+  if (hart) p.ph_tma ^= 1;
+  return true;
+}
+
+// Wait for the GEMM; false (block-uniform) on timeout.
+__device__ bool pipe_wait(Smem3& sh, Pipe& p) {
+  const bool ok = mbar_wait(p.mb_mma, p.ph_mma);
+  p.ph_mma ^= 1;
+  const bool bad = __syncthreads_or(!ok || sh.abort);
+  tc_after_sync();
+  return !bad;
+}
+
+// Accumulator (lanes < nlane valid, nout columns) -> next operand with a fresh
+// scale; `tr` writes it transposed (TF32 operands read K-major only).
+// Returns the operand scale.
+template <int P>
+__device__ float acc_to_operand(Smem3& sh, const Pipe& p, uint8_t* A, int nlane, int nout, float inv_scale,
+                                bool tr, int slot) {
+  const int row = threadIdx.x & 127, cg = threadIdx.x >> 7;
+  const int ncol = nout / 4, c0 = cg * ncol;
+  float m = 0.0f;
+  for (int c = 0; c < ncol; c += 4) m = amax4(m, tmem_ld4(p.tlane + c0 + c));
+  const float sa = op_scale<P>(block_max3(sh, row < nlane ? m * inv_scale : 0.0f, slot));
+  for (int c = 0; c < ncol; c += 4) {
+    float4 v = tmem_ld4(p.tlane + c0 + c);
+    v.x *= inv_scale;
+    v.y *= inv_scale;
+    v.z *= inv_scale;
+    v.w *= inv_scale;
+    if (tr)
+      store4_t(A, row, c0 + c, v, sa);
+    else
+      store4<P>(A, row, c0 + c, v, sa);
+  }
+  tc_before_sync();
+  return sa;
+}
+
+// Accumulator -> staging tile (true scale).
+__device__ void acc_to_stage(const Pipe& p, float* S, int nout, float inv_scale) {
+  const int row = threadIdx.x & 127, cg = threadIdx.x >> 7;
+  const int ncol = nout / 4, c0 = cg * ncol;
+  for (int c = 0; c < ncol; c += 4) {
+    float4 v = tmem_ld4(p.tlane + c0 + c);
+    v.x *= inv_scale;
+    v.y *= inv_scale;
+    v.z *= inv_scale;
+    v.w *= inv_scale;
+    *(float4*)(S + row * kSStr + c0 + c) = v;
+  }
+  tc_before_sync();
+}
+
+template <int P>
+__device__ void stage_to_op(uint8_t* A, const float* S, int nr, int nc, float s) {
+  const int q4 = nc / 4;
+  for (int t = threadIdx.x; t < nr * q4; t += kT) {
+    const int r = t % nr, c = (t / nr) * 4;
+    store4<P>(A, r, c, *(const float4*)(S + r * kSStr + c), s);
+  }
+}
+
+__device__ float stage_absmax(const float* S, int nr, int nc) {
+  const int q4 = nc / 4;
+  float m = 0.0f;
+  for (int t = threadIdx.x; t < nr * q4; t += kT) {
+    const int r = t % nr, c = (t / nr) * 4;
+    m = amax4(m, *(const float4*)(S + r * kSStr + c));
+  }
+  return m;
+}
+
+// =========================== measurement update ==============================
+struct Meas3 {
+  int kind, nz;
+  float Rinv[9];
+  float M[9];
+  float r0[3];      // linear: z - H c; bearing: wrap(z1 - atan2(c2, c1)), z2 - c3
+  float H[9];
+  float c0, c1, cc; // bearing: centre components, |c_{1:2}|^2
+};
+
+__device__ __forceinline__ float wrapf(float r) {
+  const float two_pi = 6.28318530717958647692f, pi = 3.14159265358979323846f;
+  return r - two_pi * ceilf((r - pi) / two_pi);
+}
+
+// 1/2 r^T R^{-1} r, residual relative to the frame centre (d = M u):
+// linear r = r0 - H d; bearing: atan2(c + d) - atan2(c) = atan2(c x d, |c|^2 + c.d).
+__device__ __forceinline__ float meas_e3(const Meas3& m, float u0, float u1, float u2) {
+  const float d0 = m.M[0] * u0 + m.M[1] * u1 + m.M[2] * u2;
+  const float d1 = m.M[3] * u0 + m.M[4] * u1 + m.M[5] * u2;
+  const float d2 = m.M[6] * u0 + m.M[7] * u1 + m.M[8] * u2;
+  float r[3];
+  if (m.kind == PMF_MEAS_LINEAR) {
+    for (int i = 0; i < m.nz; ++i) r[i] = m.r0[i] - (m.H[i * 3] * d0 + m.H[i * 3 + 1] * d1 + m.H[i * 3 + 2] * d2);
+  } else {
+    const float dth = atan2f(m.c0 * d1 - m.c1 * d0, m.cc + m.c0 * d0 + m.c1 * d1);
+    r[0] = wrapf(m.r0[0] - dth);
+    r[1] = m.r0[1] - d2;
+  }
+  float e = 0.0f;
+  for (int i = 0; i < m.nz; ++i)
+    for (int k = 0; k < m.nz; ++k) e += r[i] * m.Rinv[i * m.nz + k] * r[k];
+  return 0.5f * e;
+}
+
+__device__ void meas_consts(const MeasParams& mp, const FrameState& fs, Meas3& m) {
+  m.kind = mp.kind;
+  m.nz = mp.nz;
+  for (int i = 0; i < 9; ++i) m.M[i] = (float)fs.M[i];
+  for (int i = 0; i < mp.nz * mp.nz; ++i) m.Rinv[i] = (float)mp.Rinv[i];
+  if (mp.kind == PMF_MEAS_LINEAR) {
+    for (int i = 0; i < mp.nz; ++i) {
+      double h = 0.0;
+      for (int b = 0; b < 3; ++b) {
+        h += mp.H[i * 3 + b] * fs.c[b];
+        m.H[i * 3 + b] = (float)mp.H[i * 3 + b];
+      }
+      m.r0[i] = (float)(mp.z[i] - h);
+    }
+  } else {
+    const double th = atan2(fs.c[1], fs.c[0]);
+    double r = mp.z[0] - th;
+    const double two_pi = 6.283185307179586476925286766559, pi = 3.14159265358979323846;
+    r -= two_pi * ceil((r - pi) / two_pi);
+    m.r0[0] = (float)r;
+    m.r0[1] = (float)(mp.z[1] - fs.c[2]);
+    m.c0 = (float)fs.c[0];
+    m.c1 = (float)fs.c[1];
+    m.cc = (float)(fs.c[0] * fs.c[0] + fs.c[1] * fs.c[1]);
+  }
+}
+
+__device__ __forceinline__ void unflat3(const Geo3& g, long long p, int* j) {
+  j[2] = (int)(p % g.N[2]);
+  p /= g.N[2];
+  j[1] = (int)(p % g.N[1]);
+  j[0] = (int)(p / g.N[1]);
+}
+
+__global__ void __launch_bounds__(kT) k_meas_min3(const __grid_constant__ Job3 job,
+                                                  const __grid_constant__ MeasParams mp) {
+  __shared__ Meas3 m;
+  __shared__ float red[kT / 32];
+  if (threadIdx.x == 0) meas_consts(mp, job.st->f, m);
+  __syncthreads();
+  const Geo3& g = job.g;
+  float e = INFINITY;
+  for (long long q = blockIdx.x * (long long)kT + threadIdx.x; q < g.P / 4; q += (long long)gridDim.x * kT) {
+    int j[3];
+    unflat3(g, q * 4, j);
+    const float u0 = j[0] - 0.5f * (g.N[0] - 1), u1 = j[1] - 0.5f * (g.N[1] - 1), u2 = j[2] - 0.5f * (g.N[2] - 1);
+    for (int k = 0; k < 4; ++k) e = fminf(e, meas_e3(m, u0, u1, u2 + k));
+  }
+  for (int o = 16; o; o >>= 1) e = fminf(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float v = INFINITY;
+    for (int w = 0; w < kT / 32; ++w) v = fminf(v, red[w]);
+    if (v < INFINITY) atomicMin(job.emin_bits, __float_as_uint(fmaxf(v, 0.0f)));
+  }
+}
+
+// Likelihood multiply (into the other buffer) and moment partials per CTA.
+__global__ void __launch_bounds__(kT) k_meas_apply3(const __grid_constant__ Job3 job,
+                                                    const __grid_constant__ MeasParams mp) {
+  __shared__ Meas3 m;
+  __shared__ Smem3 sh;
+  if (threadIdx.x == 0) meas_consts(mp, job.st->f, m);
+  __syncthreads();
+  const Geo3& g = job.g;
+  const int cur = job.st->f.cur;
+  const float* in = cur ? job.buf1 : job.buf0;
+  float* out = cur ? job.buf0 : job.buf1;
+  const float ps = (float)job.st->f.pscale;
+  const float emin = __uint_as_float(*job.emin_bits);
+  DF s[6], s2[6];
+  for (int i = 0; i < 6; ++i) s[i] = s2[i] = DF{0.0f, 0.0f};
+  for (long long q = blockIdx.x * (long long)kT + threadIdx.x; q < g.P / 4; q += (long long)gridDim.x * kT) {
+    int j[3];
+    unflat3(g, q * 4, j);
+    const float u0 = j[0] - 0.5f * (g.N[0] - 1), u1 = j[1] - 0.5f * (g.N[1] - 1), u2 = j[2] - 0.5f * (g.N[2] - 1);
+    float4 x = *(const float4*)(in + q * 4);
+    x.x *= ps * __expf(emin - meas_e3(m, u0, u1, u2));
+    x.y *= ps * __expf(emin - meas_e3(m, u0, u1, u2 + 1.0f));
+    x.z *= ps * __expf(emin - meas_e3(m, u0, u1, u2 + 2.0f));
+    x.w *= ps * __expf(emin - meas_e3(m, u0, u1, u2 + 3.0f));
+    *(float4*)(out + q * 4) = x;
+    // four points along axis 2 at (u0, u1, u2 .. u2 + 3)
+    const float a0 = x.x + x.y + x.z + x.w;
+    const float a1 = x.y + 2.0f * x.z + 3.0f * x.w;
+    const float a2 = x.y + 4.0f * x.z + 9.0f * x.w;
+    const float b2 = fmaf(u2, a0, a1);
+    s[0] = df_add1(s[0], a0);                                      // S0
+    s[1] = df_add1(s[1], a0 * u0);                                 // S1_0
+    s[2] = df_add1(s[2], a0 * u1);                                 // S1_1
+    s[3] = df_add1(s[3], b2);                                      // S1_2
+    s[4] = df_add1(s[4], a0 * u0 * u0);                            // S2_00
+    s[5] = df_add1(s[5], a0 * u0 * u1);                            // S2_01
+    s2[0] = df_add1(s2[0], b2 * u0);                               // S2_02
+    s2[1] = df_add1(s2[1], a0 * u1 * u1);                          // S2_11
+    s2[2] = df_add1(s2[2], b2 * u1);                               // S2_12
+    s2[3] = df_add1(s2[3], fmaf(u2, fmaf(u2, a0, 2.0f * a1), a2)); // S2_22
+  }
+  block_partials3(sh, s, job.partials + (size_t)blockIdx.x * 16);
+  __syncthreads();
+  block_partials3(sh, s2, job.partials + (size_t)blockIdx.x * 16 + 6);
+}
+
+// Sum the per-CTA partials (16 doubles each: S0, S1[0..2], S2_00, S2_01 | S2_02,
+// S2_11, S2_12, S2_22, ...) into the {S0, S1[3], S2[6]} layout.
+__device__ void sum_partials3(const double* part, int nb, double* tot, double* red /* smem [kT/32][10] */) {
+  double a[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nb; b += kT) {
+    const double* p = part + (size_t)b * 16;
+    a[0] += p[0];
+    a[1] += p[1];
+    a[2] += p[2];
+    a[3] += p[3];
+    a[4] += p[4];
+    a[5] += p[5];
+    a[6] += p[6];
+    a[7] += p[7];
+    a[8] += p[8];
+    a[9] += p[9];
+  }
+  for (int i = 0; i < 10; ++i)
+    for (int o = 16; o; o >>= 1) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
+  if ((threadIdx.x & 31) == 0)
+    for (int i = 0; i < 10; ++i) red[(threadIdx.x >> 5) * 10 + i] = a[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int w = 0; w < kT / 32; ++w)
+      for (int i = 0; i < 10; ++i) v[i] += red[w * 10 + i];
+    // partial layout -> {S0, S1[3], S2: 00,01,02,11,12,22}
+    tot[0] = v[0];
+    tot[1] = v[1];
+    tot[2] = v[2];
+    tot[3] = v[3];
+    tot[4] = v[4];
+    tot[5] = v[5];
+    tot[6] = v[6];
+    tot[7] = v[7];
+    tot[8] = v[8];
+    tot[9] = v[9];
+  }
+}
+
+// Moments after the measurement update; then (time update) the frame, the
+// sub-step coefficients and the regrid rows of all axes.
+__global__ void __launch_bounds__(kT) k_frame3(const __grid_constant__ Job3 job,
+                                               const __grid_constant__ TimeConsts tc, int nb, int do_meas,
+                                               int do_time) {
+  __shared__ FrameState fs;
+  __shared__ double tot[10];
+  __shared__ double red[kT / 32 * 10];
+  __shared__ double Mpi[9];
+  __shared__ int ok;
+  DevState* st = job.st;
+  constexpr int kW = sizeof(FrameState) / 8;
+  for (int i = threadIdx.x; i < kW; i += kT) ((unsigned long long*)&fs)[i] = ((const unsigned long long*)&st->f)[i];
+  __syncthreads();
+  if (do_meas) sum_partials3(job.partials, nb, tot, red);
+  if (threadIdx.x == 0) {
+    ok = 1;
+    if (do_meas) {
+      if (!finalize_t<3>(&fs, tot, 0, nullptr)) {
+        ok = 0;
+      } else {
+        fs.cur ^= 1;          // the multiplied weights are in the other buffer
+      }
+    }
+    if (ok && do_time) frame_scalar<3>(tc, &fs, job.pend, Mpi);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) job.up->skip = !(ok && do_time);
+  if (ok && do_time) {
+    Update3* up = job.up;
+    const int l = fs.l;
+    for (int q = threadIdx.x; q < l; q += kT) {
+      double pa[3], pb[3];
+      frame_substep<3>(tc, Mpi, q, pa, pb);
+      for (int a = 0; a < 3; ++a) {
+        up->pa[q][a] = (float)pa[a];
+        up->pb[q][a] = (float)pb[a];
+      }
+    }
+    if (threadIdx.x == 0) {
+      up->l = l;
+      up->exact = fs.exact;
+      up->realign = fs.realign;
+      up->gsc = (float)(fs.g / ((double)job.g.N[0] * job.g.N[1] * job.g.N[2]));
+    }
+    if (!fs.realign)
+      for (int a = 0; a < 3; ++a) regrid_rows(up->rows[a], fs.rs[a], fs.rd[a], job.g.N[a], threadIdx.x, kT);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kW; i += kT) ((unsigned long long*)&st->f)[i] = ((const unsigned long long*)&fs)[i];
+}
+
+// Multilinear re-alignment (only when the frame kernel decided it): gather
+// buf[cur] -> buf[cur^1] with pscale folded in; k_copy3 copies it back.
+__global__ void __launch_bounds__(kT) k_realign3(const __grid_constant__ Job3 job) {
+  const FrameState& f = job.st->f;
+  if (job.up->skip || !job.up->realign) return;
+  const Geo3& g = job.g;
+  const float* in = f.cur ? job.buf1 : job.buf0;
+  float* out = f.cur ? job.buf0 : job.buf1;
+  const float ps = (float)f.pscale;
+  for (long long p = blockIdx.x * (long long)kT + threadIdx.x; p < g.P; p += (long long)gridDim.x * kT) {
+    int j[3];
+    unflat3(g, p, j);
+    double z[3];
+    int fl[3];
+    float w[3];
+    for (int a = 0; a < 3; ++a) {
+      double uo = f.b[a];
+      for (int b = 0; b < 3; ++b) uo = fma(f.B[a * 3 + b], j[b] - 0.5 * (g.N[b] - 1), uo);
+      z[a] = uo + 0.5 * (g.N[a] - 1);
+      const double fz = floor(z[a]);
+      fl[a] = (int)fmax(fmin(fz, 1e6), -1e6);
+      w[a] = (float)(z[a] - fz);
+    }
+    float s = 0.0f;
+    for (int c = 0; c < 8; ++c) {
+      float wt = 1.0f;
+      long long off = 0;
+      bool ok = true;
+      for (int a = 0; a < 3; ++a) {
+        const int bit = (c >> a) & 1, i = fl[a] + bit;
+        wt *= bit ? w[a] : 1.0f - w[a];
+        ok = ok && i >= 0 && i < g.N[a];
+        off = off * g.N[a] + (ok ? i : 0);
+      }
+      if (ok) s += wt * in[off];
+    }
+    out[p] = ps * s;
+  }
+}
+
+__global__ void __launch_bounds__(kT) k_copy3(const __grid_constant__ Job3 job) {
+  const FrameState& f = job.st->f;
+  if (job.up->skip || !job.up->realign) return;
+  const float* src = f.cur ? job.buf0 : job.buf1;
+  float* dst = f.cur ? job.buf1 : job.buf0;
+  for (long long p = blockIdx.x * (long long)kT + threadIdx.x; p < job.g.P; p += (long long)gridDim.x * kT)
+    dst[p] = src[p];
+}
+
+// =========================== pipeline A (slices) =============================
+// Slice j0 of buf[cur] (rows j1, columns j2) -> regrid + Hartley along axis 2,
+// then axis 1 -> T[j0][k1][k2] in buf[cur^1].
+template <int P>
+__global__ void __launch_bounds__(kT, 1) k_slices_fwd(const __grid_constant__ Job3 job) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ Smem3 sh;
+  uint8_t* A = smem + kOffA;
+  uint8_t* W = smem + kOffW;
+  float* S = (float*)(smem + kOffS);
+  const FrameState& f = job.st->f;
+  const Update3* up = job.up;
+  const int N1 = job.g.N[1], N2 = job.g.N[2];
+  const int j0 = blockIdx.x;
+  if (up->skip) return;
+  const int realign = up->realign;
+  const float* in = f.cur ? job.buf1 : job.buf0;
+  float* out = f.cur ? job.buf0 : job.buf1;
+  const float ps = realign ? 1.0f : (float)f.pscale;   // the re-aligned copy already carries it
+  const float sw = P == PMF_PREC_FP16X3 ? 16384.0f : 1.0f;
+  Pipe p;
+  pipe_init(sh, p);
+  const float* src = in + (size_t)j0 * N1 * N2;
+  const int q2 = N2 / 4;
+  float m = 0.0f;
+  for (int t = threadIdx.x; t < N1 * q2; t += kT) {
+    const int r = t / q2, c = (t % q2) * 4;
+    float4 x = *(const float4*)(src + (size_t)r * N2 + c);
+    x.x *= ps;
+    x.y *= ps;
+    x.z *= ps;
+    x.w *= ps;
+    *(float4*)(S + r * kSStr + c) = x;
+    m = amax4(m, x);
+  }
+  float sa = op_scale<P>(block_max3(sh, m, 0));
+  stage_to_op<P>(A, S, N1, N2, sa);
+  build_interp<P>(up->rows[2], W, N2, job.sctab[2], sw, realign, threadIdx.x, kT);
+  fence_async_smem();
+  __syncthreads();
+  pipe_issue<P>(sh, p, A, W, nullptr, 0, 0, N2, N2);                        // R2
+  float inv = 1.0f / (sa * sw);
+  if (!pipe_wait(sh, p)) goto fail;
+  sa = acc_to_operand<P>(sh, p, A, N1, N2, inv, false, 1);                  // rows j1, cols j2'
+  fence_async_smem();
+  __syncthreads();
+  pipe_issue<P>(sh, p, A, W, job.hart[2], N2, 0, N2, N2);                   // F2
+  inv = 1.0f / (sa * sw);
+  if (!pipe_wait(sh, p)) goto fail;
+  sa = acc_to_operand<P>(sh, p, A, N1, N2, inv, P == PMF_PREC_TF32, 0);     // [j1][k2]: MN-major next
+  build_interp<P>(up->rows[1], W, N1, job.sctab[1], sw, realign, threadIdx.x, kT);
+  fence_async_smem();
+  __syncthreads();
+  pipe_issue<P>(sh, p, A, W, nullptr, 0, P != PMF_PREC_TF32, N1, N1);       // R1: lanes k2
+  inv = 1.0f / (sa * sw);
+  if (!pipe_wait(sh, p)) goto fail;
+  sa = acc_to_operand<P>(sh, p, A, N2, N1, inv, false, 1);                  // [k2][j1'] K-major
+  fence_async_smem();
+  __syncthreads();
+  pipe_issue<P>(sh, p, A, W, job.hart[1], N1, 0, N1, N1);                   // F1: lanes k2, cols k1
+  inv = 1.0f / (sa * sw);
+  if (!pipe_wait(sh, p)) goto fail;
+  {
+    // T[j0][k1][k2]: lane k2, column k1 (consecutive lanes: consecutive addresses)
+    const int row = threadIdx.x & 127, cg = threadIdx.x >> 7;
+    const int ncol = N1 / 4, c0 = cg * ncol;
+    float* dst = out + (size_t)j0 * N1 * N2;
+    for (int c = 0; c < ncol; c += 4) {
+      const float4 v = tmem_ld4(p.tlane + c0 + c);
+      if (row < N2) {
+        dst[(size_t)(c0 + c + 0) * N2 + row] = v.x * inv;
+        dst[(size_t)(c0 + c + 1) * N2 + row] = v.y * inv;
+        dst[(size_t)(c0 + c + 2) * N2 + row] = v.z * inv;
+        dst[(size_t)(c0 + c + 3) * N2 + row] = v.w * inv;
+      }
+    }
+  }
+  pipe_done(sh, p);
+  return;
+fail:
+  if (threadIdx.x == 0) job.st->f.status = PMF_ERR_TIMEOUT;
+  pipe_done(sh, p);
+}
+
+// ======================= pipeline B (axis-0 line tiles) ======================
+// Tile (k1, chunk): lines {k1, -k1} x (C u -C) with C = [32 chunk, 32 chunk + 32)
+// intersected with [0, N2/2]; line index s1 * 64 + i (k2 = C[i]) and
+// s1 * 64 + 32 + i (k2 = -C[i]).
+template <int P>
+__global__ void __launch_bounds__(kT, 1) k_lines_axis0(const __grid_constant__ Job3 job, int chunks) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ Smem3 sh;
+  __shared__ int lk1[128], lk2[128];
+  __shared__ float spa[MAXL][3], spb[MAXL][3];
+  uint8_t* A = smem + kOffA;
+  uint8_t* W = smem + kOffW;
+  float* S = (float*)(smem + kOffS);
+  const FrameState& f = job.st->f;
+  const Update3* up = job.up;
+  const int N0 = job.g.N[0], N1 = job.g.N[1], N2 = job.g.N[2];
+  const int k1 = blockIdx.x / chunks, chunk = blockIdx.x % chunks;
+  const int cbeg = 32 * chunk, cend = min(32 * chunk + 32, N2 / 2 + 1), nc = cend - cbeg;
+  if (up->skip) return;
+  const int realign = up->realign;
+  float* T = f.cur ? job.buf0 : job.buf1;   // written by the slice kernel
+  const size_t plane = (size_t)N1 * N2;
+  const float sw = P == PMF_PREC_FP16X3 ? 16384.0f : 1.0f;
+  for (int L = threadIdx.x; L < 128; L += kT) {
+    const int s1 = L >> 6, i = L & 31, mir = (L >> 5) & 1;
+    const int kk1 = s1 ? (N1 - k1) % N1 : k1;
+    const int c = cbeg + i;
+    lk1[L] = kk1;
+    lk2[L] = i < nc ? (mir ? (N2 - c) % N2 : c) : -1;
+  }
+  Pipe p;
+  pipe_init(sh, p);
+  // gather the lines: S[line][j0]
+  float m = 0.0f;
+  for (int t = threadIdx.x; t < 128 * (N0 / 4); t += kT) {
+    const int L = t & 127, q = t >> 7;
+    float4 x = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (lk2[L] >= 0) {
+      const float* src = T + (size_t)lk1[L] * N2 + lk2[L];
+      x.x = src[(size_t)(4 * q + 0) * plane];
+      x.y = src[(size_t)(4 * q + 1) * plane];
+      x.z = src[(size_t)(4 * q + 2) * plane];
+      x.w = src[(size_t)(4 * q + 3) * plane];
+    }
+    *(float4*)(S + L * kSStr + 4 * q) = x;
+    m = amax4(m, x);
+  }
+  float sa = op_scale<P>(block_max3(sh, m, 0));
+  stage_to_op<P>(A, S, 128, N0, sa);
+  build_interp<P>(up->rows[0], W, N0, job.sctab[0], sw, realign, threadIdx.x, kT);
+  fence_async_smem();
+  __syncthreads();
+  pipe_issue<P>(sh, p, A, W, nullptr, 0, 0, N0, N0);                        // R0
+  float inv = 1.0f / (sa * sw);
+  if (!pipe_wait(sh, p)) goto fail;
+  sa = acc_to_operand<P>(sh, p, A, 128, N0, inv, false, 1);
+  fence_async_smem();
+  __syncthreads();
+  pipe_issue<P>(sh, p, A, W, job.hart[0], N0, 0, N0, N0);                   // F0
+  inv = 1.0f / (sa * sw);
+  if (!pipe_wait(sh, p)) goto fail;
+  acc_to_stage(p, S, N0, inv);
+  __syncthreads();
+  {
+    // diffusion multiplier on 8-point orbits (+-k0, +-k1, +-k2); bit 0 of a
+    // sign pattern flips k0, bit 1 k1, bit 2 k2
+    const float two_pi = 6.28318530717958647692f;
+    const int H0 = N0 / 2 + 1;
+    const int l = up->l, exact = up->exact;
+    const float gsc = up->gsc;
+    for (int q = threadIdx.x; q < l * 3; q += kT) {
+      spa[q / 3][q % 3] = up->pa[q / 3][q % 3];
+      spb[q / 3][q % 3] = up->pb[q / 3][q % 3];
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < H0 * nc; o += kT) {
+      const int k0 = o % H0, i = o / H0;
+      const int col[2] = {k0, (N0 - k0) % N0};
+      float Sv[8], Ps[8];
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int L = ((s >> 1) & 1) * 64 + ((s >> 2) & 1) * 32 + i;
+        Sv[s] = S[L * kSStr + col[s & 1]];
+        const int a0 = col[s & 1], a1 = lk1[L], a2 = lk2[L];
+        const int w0 = a0 < N0 / 2 ? a0 : a0 - N0, w1 = a1 < N1 / 2 ? a1 : a1 - N1, w2 = a2 < N2 / 2 ? a2 : a2 - N2;
+        const float q0 = two_pi * w0 / N0, q1 = two_pi * w1 / N1, q2 = two_pi * w2 / N2;
+        const float t0 = (2 * a0 == N0) ? 0.0f : q0, t1 = (2 * a1 == N1) ? 0.0f : q1, t2 = (2 * a2 == N2) ? 0.0f : q2;
+        float den = 1.0f, ex = 0.0f;
+        for (int qq = 0; qq < l; ++qq) {
+          const float e = spa[qq][0] * q0 * q0 + spa[qq][1] * q1 * q1 + spa[qq][2] * q2 * q2 +
+                          spb[qq][0] * t0 * t1 + spb[qq][1] * t0 * t2 + spb[qq][2] * t1 * t2;
+          den *= 1.0f + e;
+          ex += e;
+        }
+        Ps[s] = exact ? expf(-ex) : __frcp_rn(den);
+      }
+      float Tb[8], Pe[8], Tp[8];
+#pragma unroll
+      for (int B = 0; B < 8; ++B) {
+        float tb = 0.0f, pe = 0.0f;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const float chi = (__popc(B & s) & 1) ? -1.0f : 1.0f;
+          tb += chi * Sv[s];
+          pe += chi * Ps[s];
+        }
+        Tb[B] = 0.125f * tb;
+        Pe[B] = 0.125f * pe;
+      }
+#pragma unroll
+      for (int C = 0; C < 8; ++C) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int E = 0; E < 8; ++E) {
+          const int pe = __popc(E);
+          if (pe & 1) continue;
+          const int sg = ((pe >> 1) + __popc(E & C)) & 1;
+          acc += (sg ? -1.0f : 1.0f) * Pe[E] * Tb[E ^ C];
+        }
+        Tp[C] = acc * gsc;
+      }
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        float v = 0.0f;
+#pragma unroll
+        for (int C = 0; C < 8; ++C) v += ((__popc(C & s) & 1) ? -1.0f : 1.0f) * Tp[C];
+        Sv[s] = v;
+      }
+      // duplicate lines/columns of self-mirrored frequencies receive equal values
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int L = ((s >> 1) & 1) * 64 + ((s >> 2) & 1) * 32 + i;
+        S[L * kSStr + col[s & 1]] = Sv[s];
+      }
+    }
+  }
+  __syncthreads();
+  sa = op_scale<P>(block_max3(sh, stage_absmax(S, 128, N0), 1));
+  stage_to_op<P>(A, S, 128, N0, sa);
+  fence_async_smem();
+  __syncthreads();
+  pipe_issue<P>(sh, p, A, W, nullptr, 0, 0, N0, N0);                        // V0 (H0 resident)
+  inv = 1.0f / (sa * sw);
+  if (!pipe_wait(sh, p)) goto fail;
+  {
+    const int row = threadIdx.x & 127, cg = threadIdx.x >> 7;
+    const int ncol = N0 / 4, c0 = cg * ncol;
+    const bool ok = lk2[row] >= 0;
+    float* dst = T + (size_t)lk1[row < 128 ? row : 0] * N2 + (ok ? lk2[row] : 0);
+    for (int c = 0; c < ncol; c += 4) {
+      const float4 v = tmem_ld4(p.tlane + c0 + c);
+      if (ok) {
+        dst[(size_t)(c0 + c + 0) * plane] = v.x * inv;
+        dst[(size_t)(c0 + c + 1) * plane] = v.y * inv;
+        dst[(size_t)(c0 + c + 2) * plane] = v.z * inv;
+        dst[(size_t)(c0 + c + 3) * plane] = v.w * inv;
+      }
+    }
+  }
+  pipe_done(sh, p);
+  return;
+fail:
+  if (threadIdx.x == 0) job.st->f.status = PMF_ERR_TIMEOUT;
+  pipe_done(sh, p);
+}
+
+// ======================= pipeline C (inverse slices) =========================
+// T[j0][k1][k2] (rows k1, columns k2) -> inverse along axis 2, then axis 1 ->
+// weights[j0][j1][j2] in buf[cur]; moment partials per CTA.
+template <int P>
+__global__ void __launch_bounds__(kT, 1) k_slices_inv(const __grid_constant__ Job3 job) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ Smem3 sh;
+  uint8_t* A = smem + kOffA;
+  uint8_t* W = smem + kOffW;
+  float* S = (float*)(smem + kOffS);
+  const FrameState& f = job.st->f;
+  const int N0 = job.g.N[0], N1 = job.g.N[1], N2 = job.g.N[2];
+  const int j0 = blockIdx.x;
+  if (job.up->skip) return;
+  const float* T = f.cur ? job.buf0 : job.buf1;
+  float* out = f.cur ? job.buf1 : job.buf0;
+  const float sw = P == PMF_PREC_FP16X3 ? 16384.0f : 1.0f;
+  Pipe p;
+  pipe_init(sh, p);
+  const float* src = T + (size_t)j0 * N1 * N2;
+  const int q2 = N2 / 4;
+  float m = 0.0f;
+  for (int t = threadIdx.x; t < N1 * q2; t += kT) {
+    const int r = t / q2, c = (t % q2) * 4;
+    const float4 x = *(const float4*)(src + (size_t)r * N2 + c);
+    *(float4*)(S + r * kSStr + c) = x;
+    m = amax4(m, x);
+  }
+  float sa = op_scale<P>(block_max3(sh, m, 0));
+  stage_to_op<P>(A, S, N1, N2, sa);
+  fence_async_smem();
+  __syncthreads();
+  pipe_issue<P>(sh, p, A, W, job.hart[2], N2, 0, N2, N2);                   // V2: lanes k1, cols j2
+  float inv = 1.0f / (sa * sw);
+  if (!pipe_wait(sh, p)) goto fail;
+  sa = acc_to_operand<P>(sh, p, A, N1, N2, inv, P == PMF_PREC_TF32, 1);     // [k1][j2]: MN-major next
+  fence_async_smem();
+  __syncthreads();
+  pipe_issue<P>(sh, p, A, W, job.hart[1], N1, P != PMF_PREC_TF32, N1, N1);  // V1: lanes j2, cols j1
+  inv = 1.0f / (sa * sw);
+  if (!pipe_wait(sh, p)) goto fail;
+  {
+    const int row = threadIdx.x & 127, cg = threadIdx.x >> 7;
+    const int ncol = N1 / 4, c0 = cg * ncol;
+    float* dst = out + (size_t)j0 * N1 * N2;
+    const float u0 = j0 - 0.5f * (N0 - 1), u2 = row - 0.5f * (N2 - 1);
+    DF s[6];
+    for (int i = 0; i < 6; ++i) s[i] = DF{0.0f, 0.0f};
+    DF s2[4];
+    for (int i = 0; i < 4; ++i) s2[i] = DF{0.0f, 0.0f};
+    for (int c = 0; c < ncol; c += 4) {
+      float4 v = tmem_ld4(p.tlane + c0 + c);
+      v.x *= inv;
+      v.y *= inv;
+      v.z *= inv;
+      v.w *= inv;
+      if (row < N2) {
+        const int j1 = c0 + c;
+        dst[(size_t)(j1 + 0) * N2 + row] = v.x;
+        dst[(size_t)(j1 + 1) * N2 + row] = v.y;
+        dst[(size_t)(j1 + 2) * N2 + row] = v.z;
+        dst[(size_t)(j1 + 3) * N2 + row] = v.w;
+        // four points along axis 1 at (u0, u1 .. u1 + 3, u2)
+        const float u1 = j1 - 0.5f * (N1 - 1);
+        const float a0 = v.x + v.y + v.z + v.w;
+        const float a1 = v.y + 2.0f * v.z + 3.0f * v.w;
+        const float a2 = v.y + 4.0f * v.z + 9.0f * v.w;
+        const float b1 = fmaf(u1, a0, a1);
+        s[0] = df_add1(s[0], a0);
+        s[1] = df_add1(s[1], a0 * u0);
+        s[2] = df_add1(s[2], b1);
+        s[3] = df_add1(s[3], a0 * u2);
+        s[4] = df_add1(s[4], a0 * u0 * u0);
+        s[5] = df_add1(s[5], b1 * u0);
+        s2[0] = df_add1(s2[0], a0 * u0 * u2);                              // S2_02
+        s2[1] = df_add1(s2[1], fmaf(u1, fmaf(u1, a0, 2.0f * a1), a2));     // S2_11
+        s2[2] = df_add1(s2[2], b1 * u2);                                   // S2_12
+        s2[3] = df_add1(s2[3], a0 * u2 * u2);                              // S2_22
+      }
+    }
+    tc_before_sync();
+    double* part = job.partials + (size_t)j0 * 16;
+    block_partials3(sh, s, part);
+    __syncthreads();
+    DF t4[6] = {s2[0], s2[1], s2[2], s2[3], DF{0.0f, 0.0f}, DF{0.0f, 0.0f}};
+    block_partials3(sh, t4, part + 6);
+  }
+  pipe_done(sh, p);
+  return;
+fail:
+  if (threadIdx.x == 0) job.st->f.status = PMF_ERR_TIMEOUT;
+  pipe_done(sh, p);
+}
+
+// Moments of the new weights, normaliser and frame commit (one CTA).
+__global__ void __launch_bounds__(kT) k_commit3(const __grid_constant__ Job3 job, int nb) {
+  __shared__ FrameState fs;
+  __shared__ double tot[10];
+  __shared__ double red[kT / 32 * 10];
+  DevState* st = job.st;
+  if (job.up->skip) return;
+  constexpr int kW = sizeof(FrameState) / 8;
+  for (int i = threadIdx.x; i < kW; i += kT) ((unsigned long long*)&fs)[i] = ((const unsigned long long*)&st->f)[i];
+  __syncthreads();
+  sum_partials3(job.partials, nb, tot, red);
+  if (threadIdx.x == 0) finalize_t<3>(&fs, tot, 1, job.pend);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kW; i += kT) ((unsigned long long*)&st->f)[i] = ((const unsigned long long*)&fs)[i];
+}
+
+}  // namespace
+
+// ------------------------------- host side ----------------------------------
+struct Tc3State {
+  Update3* up = nullptr;
+  double* pend = nullptr;
+  double* partials = nullptr;
+  unsigned int* emin = nullptr;
+};
+
+int tc3_alloc(void** handle) {
+  Tc3State* s = new (std::nothrow) Tc3State();
+  if (!s) return PMF_ERR_OOM;
+  if (cudaMalloc(&s->up, sizeof(Update3)) != cudaSuccess || cudaMalloc(&s->pend, 32 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&s->partials, 16 * 4096 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&s->emin, sizeof(unsigned int)) != cudaSuccess) {
+    tc3_free(s);
+    return PMF_ERR_OOM;
+  }
+  static bool attr = false;
+  if (!attr) {
+#define PMF_SET(k) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem)
+    PMF_SET(k_slices_fwd<PMF_PREC_FP16X3>);
+    PMF_SET(k_slices_fwd<PMF_PREC_BF16X3>);
+    PMF_SET(k_slices_fwd<PMF_PREC_TF32>);
+    PMF_SET(k_lines_axis0<PMF_PREC_FP16X3>);
+    PMF_SET(k_lines_axis0<PMF_PREC_BF16X3>);
+    PMF_SET(k_lines_axis0<PMF_PREC_TF32>);
+    PMF_SET(k_slices_inv<PMF_PREC_FP16X3>);
+    PMF_SET(k_slices_inv<PMF_PREC_BF16X3>);
+    PMF_SET(k_slices_inv<PMF_PREC_TF32>);
+#undef PMF_SET
+    attr = true;
+  }
+  *handle = s;
+  return PMF_OK;
+}
+
+void tc3_free(void* handle) {
+  Tc3State* s = (Tc3State*)handle;
+  if (!s) return;
+  cudaFree(s->up);
+  cudaFree(s->pend);
+  cudaFree(s->partials);
+  cudaFree(s->emin);
+  delete s;
+}
+
+int tc3_step(void* handle, const Dims& d, const pmf_config& cfg, const TcTables* t, const MeasParams* mp,
+             const TimeConsts* tcs, DevState* st, float* b0, float* b1, cudaStream_t s) {
+  Tc3State* h = (Tc3State*)handle;
+  Job3 job{};
+  job.st = st;
+  job.buf0 = b0;
+  job.buf1 = b1;
+  for (int a = 0; a < 3; ++a) {
+    job.hart[a] = (const uint8_t*)t->hart[a];
+    job.sctab[a] = (const float*)((const uint8_t*)t->hart[a] + t->hart_bytes[a]);
+    job.g.N[a] = d.N[a];
+  }
+  job.g.P = d.P;
+  job.partials = h->partials;
+  job.emin_bits = h->emin;
+  job.up = h->up;
+  job.pend = h->pend;
+  job.precision = cfg.precision;
+  int launches = 0;
+  const int mblocks = (int)std::min<long long>(1024, (d.P / 4 + kT - 1) / kT);
+  TimeConsts none{};
+  if (mp) {
+    cudaMemsetAsync(h->emin, 0x7f, sizeof(unsigned int), s);
+    k_meas_min3<<<mblocks, kT, 0, s>>>(job, *mp);
+    k_meas_apply3<<<mblocks, kT, 0, s>>>(job, *mp);
+    launches += 2;
+  }
+  k_frame3<<<1, kT, 0, s>>>(job, tcs ? *tcs : none, mblocks, mp != nullptr, tcs != nullptr);
+  ++launches;
+  if (!tcs) return launches;
+  const int gb = (int)std::min<long long>(2048, (d.P + kT - 1) / kT);
+  k_realign3<<<gb, kT, 0, s>>>(job);
+  k_copy3<<<gb, kT, 0, s>>>(job);
+  const int chunks = (d.N[2] / 2 + 1 + 31) / 32;
+  const int tiles = (d.N[1] / 2 + 1) * chunks;
+  if (cfg.precision == PMF_PREC_FP16X3) {
+    k_slices_fwd<PMF_PREC_FP16X3><<<d.N[0], kT, kSmem, s>>>(job);
+    k_lines_axis0<PMF_PREC_FP16X3><<<tiles, kT, kSmem, s>>>(job, chunks);
+    k_slices_inv<PMF_PREC_FP16X3><<<d.N[0], kT, kSmem, s>>>(job);
+  } else if (cfg.precision == PMF_PREC_BF16X3) {
+    k_slices_fwd<PMF_PREC_BF16X3><<<d.N[0], kT, kSmem, s>>>(job);
+    k_lines_axis0<PMF_PREC_BF16X3><<<tiles, kT, kSmem, s>>>(job, chunks);
+    k_slices_inv<PMF_PREC_BF16X3><<<d.N[0], kT, kSmem, s>>>(job);
+  } else {
+    k_slices_fwd<PMF_PREC_TF32><<<d.N[0], kT, kSmem, s>>>(job);
+    k_lines_axis0<PMF_PREC_TF32><<<tiles, kT, kSmem, s>>>(job, chunks);
+    k_slices_inv<PMF_PREC_TF32><<<d.N[0], kT, kSmem, s>>>(job);
+  }
+  k_commit3<<<1, kT, 0, s>>>(job, d.N[0]);
+  return launches + 6;
+}
+
+}  // namespace pmf

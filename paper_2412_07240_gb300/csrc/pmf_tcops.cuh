@@ -1,0 +1,296 @@
+// Building blocks of the tcgen05 kernels (included by the 2-D and 3-D
+// tensor-core translation units): PTX wrappers, the no-swizzle canonical
+// operand layout, split-precision operand stores.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "pmf_internal.cuh"
+
+namespace pmf {
+namespace {
+
+constexpr int kPlane = 32768;                // bytes of one 16-bit operand plane
+constexpr long long kSpin = 1LL << 22;       // bounded mbarrier polls
+
+// --- PTX wrappers ------------------------------------------------------------
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// kind::f16 / kind::tf32 instruction descriptor, FP32 accumulate, M = 128.
+__device__ __forceinline__ uint32_t idesc(int fmt, int a_mn, int n) {
+  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)a_mn << 15) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+               "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+               "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+               "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  uint32_t done = 0;
+  for (long long it = 0; it < kSpin; ++it) {
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 "selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(mbar), "r"(phase));
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// Four consecutive accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ float4 tmem_ld4(uint32_t taddr) {
+  uint32_t r0, r1, r2, r3;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+               "tcgen05.wait::ld.sync.aligned;"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(taddr)
+               : "memory");
+  return make_float4(__uint_as_float(r0), __uint_as_float(r1), __uint_as_float(r2), __uint_as_float(r3));
+}
+
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// --- operand layout ------------------------------------------------------------
+// Element (r, c) of a 128-row operand plane: 8-row x 16-byte core matrices,
+// 16 (16-bit) or 32 (32-bit) core matrices per 8-row block.
+template <int P>
+struct Fmt;
+template <>
+struct Fmt<PMF_PREC_FP16X3> {
+  static constexpr int esz = 2, rowblk = 2048, planes = 2, kper = 16, code = 0;
+};
+template <>
+struct Fmt<PMF_PREC_BF16X3> {
+  static constexpr int esz = 2, rowblk = 2048, planes = 2, kper = 16, code = 1;
+};
+template <>
+struct Fmt<PMF_PREC_TF32> {
+  static constexpr int esz = 4, rowblk = 4096, planes = 1, kper = 8, code = 2;
+};
+
+template <int P>
+__device__ __forceinline__ uint32_t op_off(int r, int c) {
+  constexpr int epc = 16 / Fmt<P>::esz;
+  return (uint32_t)((r >> 3) * Fmt<P>::rowblk + (c / epc) * 128 + (r & 7) * 16 + (c % epc) * Fmt<P>::esz);
+}
+
+__device__ __forceinline__ uint32_t h2u(__half2 h) { return *(uint32_t*)&h; }
+__device__ __forceinline__ uint32_t b2u(__nv_bfloat162 h) { return *(uint32_t*)&h; }
+
+// Elements (r, c..c+3) (c a multiple of 4) of the operand planes at base, scaled
+// by s: split into hi + lo 16-bit planes, or one float32 plane for TF32.
+template <int P>
+__device__ __forceinline__ void store4(uint8_t* base, int r, int c, float4 v, float s) {
+  v.x *= s;
+  v.y *= s;
+  v.z *= s;
+  v.w *= s;
+  const uint32_t off = op_off<P>(r, c);
+  if constexpr (P == PMF_PREC_TF32) {
+    *(float4*)(base + off) = v;
+  } else if constexpr (P == PMF_PREC_FP16X3) {
+    const __half2 h0 = __floats2half2_rn(v.x, v.y), h1 = __floats2half2_rn(v.z, v.w);
+    const float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
+    const __half2 l0 = __floats2half2_rn(v.x - f0.x, v.y - f0.y), l1 = __floats2half2_rn(v.z - f1.x, v.w - f1.y);
+    *(uint2*)(base + off) = make_uint2(h2u(h0), h2u(h1));
+    *(uint2*)(base + kPlane + off) = make_uint2(h2u(l0), h2u(l1));
+  } else {
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y), h1 = __floats2bfloat162_rn(v.z, v.w);
+    const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+    const __nv_bfloat162 l0 = __floats2bfloat162_rn(v.x - f0.x, v.y - f0.y);
+    const __nv_bfloat162 l1 = __floats2bfloat162_rn(v.z - f1.x, v.w - f1.y);
+    *(uint2*)(base + off) = make_uint2(b2u(h0), b2u(h1));
+    *(uint2*)(base + kPlane + off) = make_uint2(b2u(l0), b2u(l1));
+  }
+}
+
+// TF32 operands are read K-major only: elements (c..c+3, r) of the float32 plane.
+__device__ __forceinline__ void store4_t(uint8_t* base, int r, int c, float4 v, float s) {
+  *(float*)(base + op_off<PMF_PREC_TF32>(c + 0, r)) = v.x * s;
+  *(float*)(base + op_off<PMF_PREC_TF32>(c + 1, r)) = v.y * s;
+  *(float*)(base + op_off<PMF_PREC_TF32>(c + 2, r)) = v.z * s;
+  *(float*)(base + op_off<PMF_PREC_TF32>(c + 3, r)) = v.w * s;
+}
+
+__device__ __forceinline__ float amax4(float m, float4 v) {
+  return fmaxf(fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y))), fmaxf(fabsf(v.z), fabsf(v.w)));
+}
+
+// Power-of-two scale bringing max |v| to [2^13, 2^14) for FP16 operands; 1 otherwise.
+// The exponent is capped at 2^100 so that the scale and the product with the
+// matrix scale (2^14) stay finite when a tile holds only tiny or denormal
+// values (e.g. a 3-D slice far from the mass).
+template <int P>
+__device__ __forceinline__ float op_scale(float mx) {
+  if (P != PMF_PREC_FP16X3 || !(mx > 0.0f) || !isfinite(mx)) return 1.0f;
+  int e;
+  frexpf(mx, &e);
+  return ldexpf(1.0f, min(14 - e, 100));
+}
+
+
+// Double-float (hi + lo float32 pair) arithmetic: float64-class accuracy for
+// the moment sums at float32 throughput (GB300 issues float64 at ~1/32 of the
+// float32 rate, so block-wide float64 reductions are avoided).
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb);
+  const float t = e + a.lo + b.lo;
+  const float h = s + t;
+  return DF{h, t - (h - s)};
+}
+__device__ __forceinline__ DF df_add1(DF a, float b) { return df_add(a, DF{b, 0.0f}); }
+
+// Moment sums of one thread: S0, S1 (u0, u1), S2 (u0u0, u0u1, u1u1).  Points
+// arrive in groups (a row segment of 4); the group sums are formed in float32
+// and added in double-float.
+struct Moments {
+  DF s[6];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) s[i] = DF{0.0f, 0.0f};
+  }
+  // four points x.x..x.w at (u0, u1 + 0..3)
+  __device__ __forceinline__ void add4(float4 x, float u0, float u1) {
+    const float a0 = x.x + x.y + x.z + x.w;
+    const float a1 = x.y + 2.0f * x.z + 3.0f * x.w;       // sum x * (u1' - u1)
+    const float a2 = x.y + 4.0f * x.z + 9.0f * x.w;       // sum x * (u1' - u1)^2
+    const float b1 = fmaf(u1, a0, a1);                      // sum x u1'
+    s[0] = df_add1(s[0], a0);
+    s[1] = df_add1(s[1], a0 * u0);
+    s[2] = df_add1(s[2], b1);
+    s[3] = df_add1(s[3], a0 * u0 * u0);
+    s[4] = df_add1(s[4], b1 * u0);
+    s[5] = df_add1(s[5], fmaf(u1, fmaf(u1, a0, 2.0f * a1), a2));   // sum x u1'^2
+  }
+};
+
+// Issue one GEMM stage (one thread): D = A * W^T, A read K-major or MN-major.
+// For the split formats the two correction products (hi*lo, lo*hi; ~2^-11 of
+// the result) are accumulated first, while the FP32 accumulator is small, and
+// the hi*hi products last, so that only those see roundings at full magnitude.
+template <int P>
+__device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t a_base, int a_mn, uint32_t w_base,
+                                            int nout, int K, uint32_t mbar) {
+  constexpr uint32_t rb = Fmt<P>::rowblk;
+  constexpr int kp = Fmt<P>::kper;
+  const uint32_t id = idesc(Fmt<P>::code, a_mn, nout);
+  // K step of one instruction: 32 bytes = 2 core matrices along K (K-major),
+  // or kp rows = kp/8 row blocks (MN-major)
+  auto adesc = [&](uint32_t base, int ks) {
+    return a_mn ? sdesc(base + ks * (kp / 8) * rb, rb, 128) : sdesc(base + ks * 256, 128, rb);
+  };
+  if constexpr (Fmt<P>::planes == 1) {
+    for (int ks = 0; ks < K / kp; ++ks)
+      mma_tf32(tmem, adesc(a_base, ks), sdesc(w_base + ks * 256, 128, rb), id, ks > 0);
+  } else {
+    for (int ks = 0; ks < K / kp; ++ks) {
+      mma_f16(tmem, adesc(a_base, ks), sdesc(w_base + kPlane + ks * 256, 128, rb), id, ks > 0);
+      mma_f16(tmem, adesc(a_base + kPlane, ks), sdesc(w_base + ks * 256, 128, rb), id, 1);
+    }
+    for (int ks = 0; ks < K / kp; ++ks)
+      mma_f16(tmem, adesc(a_base, ks), sdesc(w_base + ks * 256, 128, rb), id, 1);
+  }
+  mma_commit(mbar);
+}
+
+// Row parameters of the separable regrid along one axis (float64 per row):
+// y_n = rs + rd u_n, z_n = y_n + (N-1)/2 = i_n + f_n with |f_n| <= 1/2.
+struct RegridRows {
+  int ri[128];
+  float rf[128], rS[128], rcf[128], rsf[128];
+  unsigned char rzero[128];
+};
+
+__device__ void regrid_rows(RegridRows& sh, double rs, double rd, int N, int t0, int tstep) {
+  for (int n = t0; n < N; n += tstep) {
+    const double y = rs + rd * (n - 0.5 * (N - 1));
+    const double z = y + 0.5 * (N - 1);
+    const double i = rint(fmin(fmax(z, -1.0), (double)N + 1.0));
+    const float f = (float)(z - i);
+    sh.ri[n] = (int)i;
+    sh.rf[n] = f;
+    sh.rzero[n] = !(fabs(y) <= 0.5 * N);  // also zero (and skip the table) for a non-finite y
+    sh.rS[n] = sinpif(f);
+    float s, c;
+    sincospif(f / (float)N, &s, &c);
+    sh.rsf[n] = s;
+    sh.rcf[n] = c;
+  }
+}
+
+// Periodic-sinc regrid matrix of one axis into the W planes (rows: new nodes,
+// columns: old nodes), scaled by sw:
+// I[n, j] = sin(pi v) / (N tan(pi v / N)), v = y_n - u_j = m + f_n, m = i_n - j,
+// evaluated as (-1)^m sin(pi f) cos(pi v/N) / (N sin(pi v/N)) with the angle
+// pi v / N split into the tabulated pi m / N and the per-row pi f / N.
+template <int P>
+__device__ void build_interp(const RegridRows& sh, uint8_t* W, int N, const float* sctab, float sw, int realign,
+                             int t0, int tstep) {
+  const int q4 = N / 4;
+  for (int t = t0; t < N * q4; t += tstep) {
+    const int n = t % N, c = (t / N) * 4;   // consecutive threads: consecutive rows
+    float k[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = c + i;
+      float v;
+      if (realign) {
+        v = n == j ? 1.0f : 0.0f;
+      } else if (sh.rzero[n]) {
+        v = 0.0f;
+      } else {
+        const int m = sh.ri[n] - j;
+        const float f = sh.rf[n];
+        if (m == 0 && f == 0.0f) {
+          v = 1.0f;
+        } else {
+          const float cm = sctab[2 * (m + N)], sm = sctab[2 * (m + N) + 1];
+          const float sv = sm * sh.rcf[n] + cm * sh.rsf[n];
+          const float cv = cm * sh.rcf[n] - sm * sh.rsf[n];
+          v = __fdividef(((m & 1) ? -1.0f : 1.0f) * sh.rS[n] * cv, (float)N * sv);
+        }
+      }
+      k[i] = v;
+    }
+    store4<P>(W, n, c, make_float4(k[0], k[1], k[2], k[3]), sw);
+  }
+}
+
+}  // namespace
+}  // namespace pmf

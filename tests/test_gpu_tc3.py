@@ -1,0 +1,59 @@
+"""GPU parity of the 3-D tensor-core pipelines against the float64 oracle.
+
+Cases: non-cubic grids whose axis-0 line tiles are ragged (N2/2 + 1 not a
+multiple of 32), the bearing + linear measurement, a linear 3-D model with a
+sheared frame, and the full 96^3 workload.  Bar: FP16X3 relative L1 <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+import workloads as w
+from tests._parity import max_errors
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(worst, bar=1e-5):
+    assert worst["l1"] <= bar, worst
+    assert worst["frame"] <= bar, worst
+    assert worst["mean"] <= bar and worst["cov"] <= 10 * bar, worst
+
+
+@pytest.mark.parametrize("N", [(16, 32, 48), (32, 48, 80)])
+def test_small_3d_bearing_fp16x3(N):
+    worst, _ = max_errors(w.small_3d_scenario(N=N, epochs=3), precision="fp16x3")
+    print(N, worst)
+    _check(worst)
+
+
+def test_3d_linear_fp16x3():
+    from workloads import FilterConfig, MeasModel, Scenario, simulate
+    rng = np.random.default_rng(21)
+    A = w.random_stable_matrix(3, rng)
+    cfg = FilterConfig(nx=3, N=(32, 32, 48), A=A, Q=np.diag([0.2, 0.1, 0.15]),
+                       m0=np.array([0.5, -0.2, 0.1]), P0=np.array([[0.3, 0.1, 0.0], [0.1, 0.25, 0.05],
+                                                                   [0.0, 0.05, 0.2]]))
+    meas = MeasModel("linear", R=0.3 ** 2 * np.eye(3), H=np.eye(3))
+    sc = Scenario("lin3", cfg, meas, dt=0.1, epochs=3)
+    sc.truth, sc.z = simulate(cfg, meas, sc.dt, sc.epochs, seed=22)
+    worst, _ = max_errors(sc, precision="fp16x3")
+    _check(worst)
+
+
+def test_c3_full_size_two_epochs():
+    worst, _ = max_errors(w.c3_scenario(epochs=2), precision="fp16x3")
+    print(worst)
+    _check(worst)
+
+
+def test_far_measurement_tiny_slices_fp16x3():
+    """A measurement ~2 sigma off the prior leaves 3-D slices with only denormal
+    weights; their per-slice operand scale must stay finite."""
+    from workloads import FilterConfig, MeasModel, Scenario
+    cfg = FilterConfig(nx=3, N=(32, 32, 32), A=np.zeros((3, 3)), Q=np.diag([0.2, 0.1, 0.15]),
+                       m0=np.array([0.5, -0.2, 0.1]), P0=0.25 * np.eye(3))
+    meas = MeasModel("linear", R=0.09 * np.eye(3), H=np.eye(3))
+    sc = Scenario("far", cfg, meas, dt=0.1, epochs=2)
+    sc.z = np.array([[-0.386, -0.368, -1.032], [-0.5, -0.4, -1.1]])
+    worst, _ = max_errors(sc, precision="fp16x3")
+    _check(worst)
