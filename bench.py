@@ -135,7 +135,13 @@ def _scenario(name, epochs=50):
         return w.c2_scenario(epochs=epochs)
     if name == "c2small":
         return w.c2_scenario(N=(64, 64), epochs=epochs)
+    if name == "c3":
+        return w.c3_scenario(epochs=epochs)
     raise SystemExit(f"unknown workload {name}")
+
+
+def _launch_names(sc):
+    return "k_fused2d" if sc.cfg.nx == 2 else "k_slices_fwd+k_lines_axis0+k_slices_inv"
 
 
 def _flops_per_step(N):
@@ -270,6 +276,7 @@ def bench_batch(args, ws, rank, pg):
             b.step(ids, z[:, args.warmup + k], dt)
             ev[k][1].record()
         torch.cuda.synchronize()
+    launches = b.launches - l0
     ms = [a.elapsed_time(c) for a, c in ev]
     t_ms = _max_over_ranks(pg, sum(ms))
     value = ws * P.sum() * args.steps / (t_ms * 1e-3)
@@ -309,7 +316,7 @@ def bench_batch(args, ws, rank, pg):
             "e2e": {"value": ws * P.sum() / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": int(len(cfgs) * 24), "d2h_bytes_per_step": int(len(cfgs) * 48),
                     "ms_per_step": e2e_ms},
-            "gpu_launches": int(b.launches - l0 - ne),
+            "gpu_launches": int(launches),
             "fp64_gpu": {"value": fp64_rate, "unit": UNIT, "filters_timed": int(len(sub))},
             "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
             "degenerate_filters": bad,
@@ -366,7 +373,7 @@ def main():
     mom_bytes = 8 * (len(sc.cfg.N) + len(sc.cfg.N) ** 2)
 
     # plain float64 GPU path on the same workload
-    f64, ms64, l64 = time_gpu(sc, "fp64", max(10, args.steps // 4), args.warmup)
+    f64, ms64, l64 = time_gpu(sc, "fp64", max(3, min(args.steps // 4, 40 if sc.cfg.nx == 2 else 5)), args.warmup)
     ms64_step = _max_over_ranks(pg, sum(ms64) / len(ms64))
 
     kernel_ms = float(np.mean(ms))
@@ -391,11 +398,11 @@ def main():
         "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
         "roofline": {"bound": "tensor", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved_tflops / peak, "traffic": None,
-                     "kernel": "k_fused2d", "peak_source": f"bf16_tflops ({peak_src})",
+                     "kernel": _launch_names(sc), "peak_source": f"bf16_tflops ({peak_src})",
                      "flops_per_launch": flops},
         "clocks": clk.summary(),
     }
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and sc.cfg.nx == 2:
         epochs = 60
         t = oracle_sample(sc, epochs)
         per = t["seconds"] / t["epochs"]

@@ -187,13 +187,15 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
 int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_meas,
                    const double* taus, int k);
 
-/* Means (k*nx) and covariances (k*nx*nx) of filters ids[0..k).  Synchronous.
- * Returns PMF_ERR_DEGENERATE if any listed filter reported a degenerate
- * normaliser (its density is left unchanged). */
+/* Means (k*nx) and covariances (k*nx*nx) of filters ids[0..k), k <= count
+ * (gathered on the device, one copy back).  Synchronous.  Returns
+ * PMF_ERR_DEGENERATE if any listed filter reported a degenerate normaliser
+ * (its density is left unchanged); the listed status words are then clear. */
 int pmf_batch_moments(pmf_batch* b, const int* ids, int k, double* means, double* covs);
 
-/* Status words of filters ids[0..k) (PMF_OK or the PMF_ERR_* their last epoch
- * reported, e.g. PMF_ERR_DEGENERATE), cleared after reading.  Synchronous. */
+/* Status words of filters ids[0..k), k <= count (PMF_OK or the PMF_ERR_*
+ * their last epoch reported, e.g. PMF_ERR_DEGENERATE), cleared after reading.
+ * Synchronous. */
 int pmf_batch_status(pmf_batch* b, const int* ids, int k, int* status_out);
 
 /* Normalised weights of filter id (prod N_m doubles) and its frame.  Synchronous. */

@@ -539,6 +539,10 @@ struct pmf_batch {
   double* d_aux = nullptr;
   std::vector<void*> tables;          // per distinct N
   std::vector<double> tau;            // tau of the constants resident for each filter
+  int* d_ids = nullptr;               // filter ids of a moments/status query
+  double* d_gather = nullptr;         // 8 doubles per queried filter
+  int* h_ids = nullptr;               // pinned staging of the query
+  double* h_gather = nullptr;
   StepItem* h_items[2] = {nullptr, nullptr};
   TimeConsts* h_tc[2] = {nullptr, nullptr};
   cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -559,6 +563,10 @@ void free_batch(pmf_batch* b) {
   cudaFree(b->d_items);
   cudaFree(b->d_partials);
   cudaFree(b->d_aux);
+  cudaFree(b->d_ids);
+  cudaFree(b->d_gather);
+  cudaFreeHost(b->h_ids);
+  cudaFreeHost(b->h_gather);
   for (void* p : b->tables) cudaFree(p);
   for (int i = 0; i < 2; ++i) {
     cudaFreeHost(b->h_items[i]);
@@ -595,7 +603,7 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
   }
   long long bytes = wfloats * 4 + (long long)count * (sizeof(DevState) + sizeof(MeasParams) +
                                                        sizeof(TimeConsts) + sizeof(FilterSlot) +
-                                                       sizeof(StepItem)) +
+                                                       sizeof(StepItem) + sizeof(int) + 8 * sizeof(double)) +
                     sizeof(double) * (10 * 4096 + 16 * (long long)count);
   for (int N : sizes) bytes += (long long)tc_axis_table_bytes(N, prec);
   if (hbm_budget && (size_t)bytes > hbm_budget) return PMF_ERR_ADMISSION;
@@ -623,7 +631,14 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
   BALLOC(b->d_items, sizeof(StepItem) * count);
   BALLOC(b->d_partials, sizeof(double) * 10 * 4096);
   BALLOC(b->d_aux, sizeof(double) * 16 * count);
+  BALLOC(b->d_ids, sizeof(int) * count);
+  BALLOC(b->d_gather, sizeof(double) * 8 * count);
 #undef BALLOC
+  if (cudaMallocHost((void**)&b->h_ids, sizeof(int) * count) != cudaSuccess ||
+      cudaMallocHost((void**)&b->h_gather, sizeof(double) * 8 * count) != cudaSuccess) {
+    free_batch(b);
+    return PMF_ERR_OOM;
+  }
   for (int i = 0; i < 2; ++i) {
     if (cudaMallocHost((void**)&b->h_items[i], sizeof(StepItem) * count) != cudaSuccess ||
         cudaMallocHost((void**)&b->h_tc[i], sizeof(TimeConsts) * count) != cudaSuccess ||
@@ -747,46 +762,47 @@ int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_
   return cudaGetLastError() == cudaSuccess ? PMF_OK : PMF_ERR_CUDA;
 }
 
-int pmf_batch_moments(pmf_batch* b, const int* ids, int k, double* means, double* covs) {
-  if (!b || k < 0 || (k && !ids)) return PMF_ERR_ARG;
+namespace {
+
+// Gather {mean, cov, status} of the listed filters on the device (clearing
+// their status words) and copy them to the pinned host buffer; synchronous.
+int batch_query(pmf_batch* b, const int* ids, int k) {
+  for (int i = 0; i < k; ++i)
+    if (ids[i] < 0 || ids[i] >= b->count) return PMF_ERR_ARG;
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return PMF_ERR_CUDA;
-  std::vector<FrameState> fs(b->count);
-  if (cudaMemcpy2D(fs.data(), sizeof(FrameState), b->d_st, sizeof(DevState), sizeof(FrameState), b->count,
-                   cudaMemcpyDeviceToHost) != cudaSuccess)
+  if (k == 0) return PMF_OK;
+  std::memcpy(b->h_ids, ids, sizeof(int) * k);
+  if (cudaMemcpyAsync(b->d_ids, b->h_ids, sizeof(int) * k, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
     return PMF_ERR_CUDA;
+  b->launches += tc_batch_gather(b->d_st, b->d_ids, k, b->d_gather, b->stream);
+  if (cudaMemcpyAsync(b->h_gather, b->d_gather, sizeof(double) * 8 * k, cudaMemcpyDeviceToHost, b->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return PMF_ERR_CUDA;
+  return PMF_OK;
+}
+
+}  // namespace
+
+int pmf_batch_moments(pmf_batch* b, const int* ids, int k, double* means, double* covs) {
+  if (!b || k < 0 || k > b->count || (k && !ids)) return PMF_ERR_ARG;
+  const int q = batch_query(b, ids, k);
+  if (q) return q;
   int rc = PMF_OK;
   for (int i = 0; i < k; ++i) {
-    if (ids[i] < 0 || ids[i] >= b->count) return PMF_ERR_ARG;
-    const FrameState& f = fs[ids[i]];
-    if (f.status) rc = f.status;
-    if (means) std::memcpy(means + 2 * i, f.mean, sizeof(double) * 2);
-    if (covs) std::memcpy(covs + 4 * i, f.cov, sizeof(double) * 4);
-  }
-  if (rc) {
-    // report once, then clear the listed filters' status words
-    for (int i = 0; i < k; ++i) {
-      const int zero = 0;
-      cudaMemcpy(&b->d_st[ids[i]].f.status, &zero, sizeof(int), cudaMemcpyHostToDevice);
-    }
+    const double* g = b->h_gather + (size_t)i * 8;
+    if (g[6] != 0.0) rc = (int)g[6];
+    if (means) std::memcpy(means + 2 * i, g, sizeof(double) * 2);
+    if (covs) std::memcpy(covs + 4 * i, g + 2, sizeof(double) * 4);
   }
   return rc;
 }
 
 int pmf_batch_status(pmf_batch* b, const int* ids, int k, int* status_out) {
-  if (!b || k < 0 || (k && (!ids || !status_out))) return PMF_ERR_ARG;
-  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return PMF_ERR_CUDA;
-  std::vector<FrameState> fs(b->count);
-  if (cudaMemcpy2D(fs.data(), sizeof(FrameState), b->d_st, sizeof(DevState), sizeof(FrameState), b->count,
-                   cudaMemcpyDeviceToHost) != cudaSuccess)
-    return PMF_ERR_CUDA;
-  for (int i = 0; i < k; ++i) {
-    if (ids[i] < 0 || ids[i] >= b->count) return PMF_ERR_ARG;
-    status_out[i] = fs[ids[i]].status;
-    if (fs[ids[i]].status) {
-      const int zero = 0;
-      cudaMemcpy(&b->d_st[ids[i]].f.status, &zero, sizeof(int), cudaMemcpyHostToDevice);
-    }
-  }
+  if (!b || k < 0 || k > b->count || (k && (!ids || !status_out))) return PMF_ERR_ARG;
+  const int q = batch_query(b, ids, k);
+  if (q) return q;
+  for (int i = 0; i < k; ++i) status_out[i] = (int)b->h_gather[(size_t)i * 8 + 6];
   return PMF_OK;
 }
 

@@ -82,7 +82,7 @@ struct Shared {
   uint32_t tmem;
   int abort, degenerate;
   float redf[2][16];
-  double redd[16][6];
+  DF redm[16][6];
   double tot[10];
   double pend[24];
   double Mpi[9];
@@ -91,7 +91,8 @@ struct Shared {
   float g, ps, gsc;
   // frame-relative measurement constants
   float mc[2], mM[4], mr0[3], mRinv[9], mH[6], mcn;
-  RegridRows rows;         // regrid rows of the axis being built
+  RegridRows rows[2];      // regrid rows per axis
+  float sct[2][2 * (2 * 128 + 1)];   // per axis (cos, sin)(pi m / N), m = -N..N
 };
 
 // Block max of non-negative per-thread values (result in every thread).
@@ -116,8 +117,12 @@ __device__ __forceinline__ float block_min(Shared& sh, float v, int slot) {
 }
 
 // Sum the per-thread moment sums over the block into sh.tot ({S0, S1[3],
-// S2[6]} layout, float64); valid in thread 0 after the call.
+// S2[6]} layout, float64); valid in warp 0 after the call.  The sums stay in
+// double-float through both the warp and the cross-warp reduction; six lanes
+// of warp 0 convert the totals to float64 (GB300 issues float64 at a small
+// fraction of the float32 rate, so no per-warp or single-thread float64 loop).
 __device__ __forceinline__ void block_moments(Shared& sh, const Moments& m) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   DF a[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
@@ -127,27 +132,30 @@ __device__ __forceinline__ void block_moments(Shared& sh, const Moments& m) {
       a[i] = df_add(a[i], b);
     }
   }
-  if ((threadIdx.x & 31) == 0)
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < 6; ++i) sh.redm[warp][i] = a[i];
+  __syncthreads();
+  if (warp == 0) {
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      sh.redd[threadIdx.x >> 5][i] = (double)a[i].hi + (double)a[i].lo;
+      a[i] = lane < kThreads / 32 ? sh.redm[lane][i] : DF{0.0f, 0.0f};
+      for (int o = kThreads / 64; o; o >>= 1) {
+        DF b{__shfl_xor_sync(0xffffffffu, a[i].hi, o), __shfl_xor_sync(0xffffffffu, a[i].lo, o)};
+        a[i] = df_add(a[i], b);
+      }
     }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double v[6] = {0, 0, 0, 0, 0, 0};
-    for (int w = 0; w < kThreads / 32; ++w)
+    // lane i < 6 converts accumulator i; {S0, S1_0, S1_1, S2_00, S2_01, S2_11}
+    // go to tot[0, 1, 2, 4, 5, 7], the n_x = 3 slots are zero
+    DF mine = a[0];
 #pragma unroll
-      for (int i = 0; i < 6; ++i) v[i] += sh.redd[w][i];
-    sh.tot[0] = v[0];
-    sh.tot[1] = v[1];
-    sh.tot[2] = v[2];
-    sh.tot[3] = 0.0;
-    sh.tot[4] = v[3];
-    sh.tot[5] = v[4];
-    sh.tot[6] = 0.0;
-    sh.tot[7] = v[5];
-    sh.tot[8] = 0.0;
-    sh.tot[9] = 0.0;
+    for (int i = 1; i < 6; ++i)
+      if (lane == i) mine = a[i];
+    const int slot = lane < 3 ? lane : lane == 3 ? 4 : lane == 4 ? 5 : lane == 5 ? 7 : lane == 6 ? 3
+                   : lane == 7 ? 6 : lane;
+    if (lane < 6) sh.tot[slot] = (double)mine.hi + (double)mine.lo;
+    else if (lane < 10) sh.tot[slot] = 0.0;
+    __syncwarp();
   }
 }
 
@@ -202,33 +210,36 @@ __device__ __forceinline__ float stage_max(const float* S, int nr, int nc) {
 // jointly even multiplier (E = 0 even-even, E = 3 odd-odd),
 //   T'_C = Psi_0 T_C - (-1)^{|3 & C|} Psi_3 T_{3 ^ C},
 // then back to the separable coefficients; gsc = trace factor / (N0 N1).
+// Psi(k0, k1) and Psi(-k0, k1) differ only in the sign of the cross term.
 __device__ void psi_stage(const Shared& sh, float* S, int N0, int N1, int l, int exact) {
   const int H0n = N0 / 2 + 1, H1n = N1 / 2 + 1;
-  const float two_pi = 6.28318530717958647692f;
+  const float w0s = 6.28318530717958647692f / (float)N0, w1s = 6.28318530717958647692f / (float)N1;
+  // r = k1 H0n + k0: (r + 1/2) / H0n is at least 1/(2 H0n) away from an integer,
+  // so the float product truncates to k1 exactly (r < 2^13)
+  const float rH0 = 1.0f / (float)H0n;
   for (int r = threadIdx.x; r < H0n * H1n; r += kThreads) {
-    const int k0 = r % H0n, k1 = r / H0n;
-    const int i0[2] = {k0, (N0 - k0) % N0};
-    const int i1[2] = {k1, (N1 - k1) % N1};
-    float Sv[4], Ps[2];
+    const int k1 = (int)(((float)r + 0.5f) * rH0);
+    const int k0 = r - k1 * H0n;
+    const int i0[2] = {k0, k0 ? N0 - k0 : 0};
+    const int i1[2] = {k1, k1 ? N1 - k1 : 0};
+    float Sv[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) Sv[s] = S[i1[s >> 1] * kSStr + i0[s & 1]];
-    // Psi(k0, k1) and Psi(-k0, k1); the multiplier is jointly even
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const int a0 = i0[s], a1 = i1[0];
-      const int w0 = a0 < N0 / 2 ? a0 : a0 - N0, w1 = a1 < N1 / 2 ? a1 : a1 - N1;
-      const float k0f = two_pi * w0 / N0, k1f = two_pi * w1 / N1;
-      const float t0 = (2 * a0 == N0) ? 0.0f : k0f, t1 = (2 * a1 == N1) ? 0.0f : k1f;
-      const float q0 = k0f * k0f, q1 = k1f * k1f, qx = t0 * t1;
-      float den = 1.0f, ex = 0.0f;
-      for (int qq = 0; qq < l; ++qq) {
-        const float e = sh.pa[qq][0] * q0 + sh.pa[qq][1] * q1 + sh.pb[qq] * qx;
-        den *= 1.0f + e;
-        ex += e;
-      }
-      Ps[s] = exact ? expf(-ex) : 1.0f / den;
+    const float k0f = w0s * (float)k0, k1f = w1s * (float)k1;
+    const float q0 = k0f * k0f, q1 = k1f * k1f;
+    // first-derivative coefficients: zero at the Nyquist index
+    const float qx = ((2 * k0 == N0) ? 0.0f : k0f) * ((2 * k1 == N1) ? 0.0f : k1f);
+    float den0 = 1.0f, den1 = 1.0f, ex0 = 0.0f, ex1 = 0.0f;
+    for (int qq = 0; qq < l; ++qq) {
+      const float b = sh.pa[qq][0] * q0 + sh.pa[qq][1] * q1;
+      const float e0 = b + sh.pb[qq] * qx, e1 = b + sh.pb[qq] * (-qx);
+      den0 *= 1.0f + e0;
+      den1 *= 1.0f + e1;
+      ex0 += e0;
+      ex1 += e1;
     }
-    const float pe0 = 0.5f * (Ps[0] + Ps[1]), pe3 = 0.5f * (Ps[0] - Ps[1]);
+    const float P0 = exact ? expf(-ex0) : __frcp_rn(den0), P1 = exact ? expf(-ex1) : __frcp_rn(den1);
+    const float pe0 = 0.5f * (P0 + P1), pe3 = 0.5f * (P0 - P1);
     float T[4];
 #pragma unroll
     for (int B = 0; B < 4; ++B) {
@@ -256,6 +267,7 @@ __device__ void psi_stage(const Shared& sh, float* S, int N0, int N1, int l, int
 template <int P>
 __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   __shared__ Shared sh;
+  if (!job.do_meas && !job.do_time) return;   // nothing requested for this filter
   DevState* st = job.st;
   FrameState& fs = sh.fs;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -271,9 +283,14 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
 
   for (int i = tid; i < kFsWords; i += kThreads)
     ((unsigned long long*)&fs)[i] = ((const unsigned long long*)&st->f)[i];
-  if (job.do_time)
+  if (job.do_time) {
     for (int i = tid; i < (int)(sizeof(TimeConsts) / 8); i += kThreads)
       ((unsigned long long*)&sh.tc)[i] = ((const unsigned long long*)job.tc)[i];
+    for (int a = 0; a < 2; ++a) {
+      const int n = 2 * (2 * (a ? N1 : N0) + 1);
+      for (int i = tid; i < n; i += kThreads) sh.sct[a][i] = job.sctab[a][i];
+    }
+  }
   if (job.do_meas) {
     for (int i = tid; i < (int)(sizeof(MeasParams) / 8); i += kThreads)
       ((unsigned long long*)&sh.mp)[i] = ((const unsigned long long*)job.mp)[i];
@@ -298,22 +315,17 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   const uint32_t tmem = sh.tmem;
   const uint32_t tlane = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 
-  // ---- weights -> staging rows j0, columns j1 (float32, normalised) ----
+  // ---- weights -> staging rows j0, columns j1 (bulk copies, one per row) ----
   const int cur = fs.cur;
   const float* in = cur ? job.buf1 : job.buf0;
   float* out = cur ? job.buf0 : job.buf1;
   const int q1 = N1 / 4, np4 = N0 * q1;
-  {
-    const float ps = (float)fs.pscale;
-    for (int t = tid; t < np4; t += kThreads) {
-      const int r = t / q1, c = (t % q1) * 4;
-      float4 x = *(const float4*)(in + (size_t)r * N1 + c);
-      x.x *= ps;
-      x.y *= ps;
-      x.z *= ps;
-      x.w *= ps;
-      *(float4*)(S + r * kSStr + c) = x;
-    }
+  if (warp == 1) {
+    // rows are N1 * 4 bytes (a multiple of 64) at 16-byte aligned addresses
+    if (tid == 32) expect_tx(mb_tma, (uint32_t)(N0 * N1 * 4));
+    __syncwarp();
+    for (int r = tid - 32; r < N0; r += 32)
+      bulk_load(su32(S + r * kSStr), in + (size_t)r * N1, (uint32_t)(N1 * 4), mb_tma);
   }
   float smax = 0.0f;      // max |weight| (operand scale of the first GEMM)
   float sa_first = 1.0f;  // scale of the R1 operand
@@ -340,32 +352,58 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       }
     }
     __syncthreads();
+    // exponents into the (still free) W region while the weights arrive
     const int kind = sh.mp.kind, nz = sh.mp.nz;
+    float4* E = (float4*)W;
     float emin = INFINITY;
     for (int t = tid; t < np4; t += kThreads) {
       const int r = t / q1, c = (t - r * q1) * 4;
       const float u0 = r - 0.5f * (N0 - 1), u1 = c - 0.5f * (N1 - 1);
-      emin = fminf(emin, fminf(fminf(meas_e(sh, kind, nz, u0, u1), meas_e(sh, kind, nz, u0, u1 + 1.0f)),
-                               fminf(meas_e(sh, kind, nz, u0, u1 + 2.0f), meas_e(sh, kind, nz, u0, u1 + 3.0f))));
+      const float4 e = make_float4(meas_e(sh, kind, nz, u0, u1), meas_e(sh, kind, nz, u0, u1 + 1.0f),
+                                   meas_e(sh, kind, nz, u0, u1 + 2.0f), meas_e(sh, kind, nz, u0, u1 + 3.0f));
+      E[t] = e;
+      emin = fminf(emin, fminf(fminf(e.x, e.y), fminf(e.z, e.w)));
     }
     emin = block_min(sh, emin, 0);
+    if (__syncthreads_or(!mbar_wait(mb_tma, ph_tma))) {
+      if (tid == 0) fs.status = PMF_ERR_TIMEOUT;
+      goto done;
+    }
+    ph_tma ^= 1;
+    const float ps = (float)fs.pscale;
     Moments mo;
     mo.zero();
     for (int t = tid; t < np4; t += kThreads) {
       const int r = t / q1, c = (t - r * q1) * 4;
       const float u0 = r - 0.5f * (N0 - 1), u1 = c - 0.5f * (N1 - 1);
       float4 x = *(const float4*)(S + r * kSStr + c);
-      x.x *= __expf(emin - meas_e(sh, kind, nz, u0, u1));
-      x.y *= __expf(emin - meas_e(sh, kind, nz, u0, u1 + 1.0f));
-      x.z *= __expf(emin - meas_e(sh, kind, nz, u0, u1 + 2.0f));
-      x.w *= __expf(emin - meas_e(sh, kind, nz, u0, u1 + 3.0f));
+      const float4 e = E[t];
+      x.x = (x.x * ps) * __expf(emin - e.x);
+      x.y = (x.y * ps) * __expf(emin - e.y);
+      x.z = (x.z * ps) * __expf(emin - e.z);
+      x.w = (x.w * ps) * __expf(emin - e.w);
       *(float4*)(S + r * kSStr + c) = x;
       mo.add4(x, u0, u1);
       smax = amax4(smax, x);
     }
     block_moments(sh, mo);
   } else {
-    smax = stage_max(S, N0, N1);
+    if (__syncthreads_or(!mbar_wait(mb_tma, ph_tma))) {
+      if (tid == 0) fs.status = PMF_ERR_TIMEOUT;
+      goto done;
+    }
+    ph_tma ^= 1;
+    const float ps = (float)fs.pscale;
+    for (int t = tid; t < np4; t += kThreads) {
+      const int r = t / q1, c = (t % q1) * 4;
+      float4 x = *(const float4*)(S + r * kSStr + c);
+      x.x *= ps;
+      x.y *= ps;
+      x.z *= ps;
+      x.w *= ps;
+      *(float4*)(S + r * kSStr + c) = x;
+      smax = amax4(smax, x);
+    }
   }
   {
     // Thread 0 finalises the moments and (time update) computes the frame in
@@ -412,7 +450,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   }
 
   {
-    // ---- sub-step coefficients, regrid rows (or re-alignment) ----
+    // ---- sub-step coefficients, regrid rows of both axes (or re-alignment) ----
     realign = fs.realign;
     l = fs.l;
     exact = fs.exact;
@@ -454,8 +492,10 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       }
       sa_first = op_scale<P>(block_max(sh, smax, 0));
       stage_to_operand<P>(A, S, N0, N1, sa_first, tid, kThreads);
+    } else if (tid < kThreads / 2) {
+      regrid_rows(sh.rows[1], fs.rs[1], fs.rd[1], N1, tid, kThreads / 2);
     } else {
-      regrid_rows(sh.rows, fs.rs[1], fs.rd[1], N1, tid, kThreads);
+      regrid_rows(sh.rows[0], fs.rs[0], fs.rd[0], N0, tid - kThreads / 2, kThreads / 2);
     }
     __syncthreads();
   }
@@ -463,7 +503,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   {
     // ---- the matrix I1; the R1 operand is already written ----
     float sa = sa_first;
-    build_interp<P>(sh.rows, W, N1, job.sctab[1], sw, realign, tid, kThreads);
+    build_interp<P>(sh.rows[1], W, N1, sh.sct[1], sw, realign, tid, kThreads);
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -487,30 +527,36 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       const int nout = (stage <= 1 || stage == 5) ? N1 : N0;
       const int ncol = nout / 4, c0 = cg * ncol;   // this thread's columns
       const bool lane_ok = row < nlane;
+      float4 v[8];
+      tmem_ld_cols(tlane + c0, ncol, v);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        v[j].x *= inv_scale;
+        v[j].y *= inv_scale;
+        v[j].z *= inv_scale;
+        v[j].w *= inv_scale;
+      }
       if (stage == 5) {
-        // final weights: rows j0, columns j1 -> staging (true scale)
-        for (int c = 0; c < ncol; c += 4) {
-          float4 v = tmem_ld4(tlane + c0 + c);
-          v.x *= inv_scale;
-          v.y *= inv_scale;
-          v.z *= inv_scale;
-          v.w *= inv_scale;
-          *(float4*)(S + row * kSStr + c0 + c) = v;
-        }
+        // final weights: rows j0, columns j1 -> staging (true scale) and moments
+        Moments mo;
+        mo.zero();
+        const float u0 = row - 0.5f * (N0 - 1);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (4 * j < ncol) {
+            *(float4*)(S + row * kSStr + c0 + 4 * j) = v[j];
+            if (lane_ok) mo.add4(v[j], u0, (c0 + 4 * j) - 0.5f * (N1 - 1));
+          }
+        fence_async_smem();
         tc_before_sync();
-        __syncthreads();
+        block_moments(sh, mo);
         break;
       }
       if (stage == 3) {
         // F0 finished: spectrum T[k1][k0] -> staging, multiplier, operand of V0
-        for (int c = 0; c < ncol; c += 4) {
-          float4 v = tmem_ld4(tlane + c0 + c);
-          v.x *= inv_scale;
-          v.y *= inv_scale;
-          v.z *= inv_scale;
-          v.w *= inv_scale;
-          *(float4*)(S + row * kSStr + c0 + c) = v;
-        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (4 * j < ncol) *(float4*)(S + row * kSStr + c0 + 4 * j) = v[j];
         tc_before_sync();
         __syncthreads();
         psi_stage(sh, S, N0, N1, l, exact);
@@ -519,21 +565,19 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         stage_to_operand<P>(A, S, N1, N0, sa, tid, kThreads);
       } else {
         float m = 0.0f;
-        for (int c = 0; c < ncol; c += 4) m = amax4(m, tmem_ld4(tlane + c0 + c));
-        sa = op_scale<P>(block_max(sh, lane_ok ? m * inv_scale : 0.0f, stage & 1));
+#pragma unroll
+        for (int j = 0; j < 8; ++j) m = amax4(m, v[j]);
+        sa = op_scale<P>(block_max(sh, lane_ok ? m : 0.0f, stage & 1));
         // R0 and V1 read this operand MN-major; TF32 gets it written transposed
         const bool tr = P == PMF_PREC_TF32 && (stage == 1 || stage == 4);
-        for (int c = 0; c < ncol; c += 4) {
-          float4 v = tmem_ld4(tlane + c0 + c);
-          v.x *= inv_scale;
-          v.y *= inv_scale;
-          v.z *= inv_scale;
-          v.w *= inv_scale;
-          if (tr)
-            store4_t(A, row, c0 + c, v, sa);
-          else
-            store4<P>(A, row, c0 + c, v, sa);
-        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (4 * j < ncol) {
+            if (tr)
+              store4_t(A, row, c0 + 4 * j, v[j], sa);
+            else
+              store4<P>(A, row, c0 + 4 * j, v[j], sa);
+          }
         tc_before_sync();
       }
       // matrix of the next GEMM: F1 <- H1, R0 <- I0, F0 <- H0, V0 keeps H0, V1 <- H1
@@ -542,9 +586,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       if (stage == 2) mat = 0;
       if (stage == 1) {
         __syncthreads();
-        regrid_rows(sh.rows, fs.rs[0], fs.rd[0], N0, tid, kThreads);
-        __syncthreads();
-        build_interp<P>(sh.rows, W, N0, job.sctab[0], sw, realign, tid, kThreads);
+        build_interp<P>(sh.rows[0], W, N0, sh.sct[0], sw, realign, tid, kThreads);
       }
       fence_async_smem();
       __syncthreads();
@@ -578,19 +620,12 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       goto done;
     }
 
-    // ---- normalisation, moments and write-back (rows j0, columns j1) ----
-    {
-      Moments mo;
-      mo.zero();
-      for (int t = tid; t < np4; t += kThreads) {
-        const int r = t / q1, c = (t % q1) * 4;
-        const float4 x = *(const float4*)(S + r * kSStr + c);
-        *(float4*)(out + (size_t)r * N1 + c) = x;
-        const float u0 = r - 0.5f * (N0 - 1), u1 = c - 0.5f * (N1 - 1);
-        mo.add4(x, u0, u1);
-      }
-      block_moments(sh, mo);
-      if (tid == 0 && finalize_t<2>(&fs, sh.tot, 1, sh.pend)) fs.cur = cur ^ 1;
+    // ---- write-back (bulk stores of the staged rows) and normalisation ----
+    if (tid == 0) {
+      for (int r = 0; r < N0; ++r) bulk_store(out + (size_t)r * N1, su32(S + r * kSStr), (uint32_t)(N1 * 4));
+      bulk_commit();
+      if (finalize_t<2>(&fs, sh.tot, 1, sh.pend)) fs.cur = cur ^ 1;
+      bulk_wait_all();
     }
   }
 
@@ -621,6 +656,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused2d_batch(const FilterSlot*
   const FusedView v{sl.st, sl.buf0, sl.buf1, {sl.hart[0], sl.hart[1]}, {sl.sctab[0], sl.sctab[1]},
                     sl.N0, sl.N1, it.flags & 1, (it.flags >> 1) & 1, sl.mp, it.z, sl.tc};
   fused2d<P>(v, smem);
+}
+
+// Moments and status words of the listed filters (read before any is cleared:
+// a filter may be listed twice).
+__global__ void k_batch_gather(const DevState* __restrict__ st, const int* __restrict__ ids, int k,
+                               double* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+    const FrameState& f = st[ids[i]].f;
+    double* o = out + (size_t)i * 8;
+    o[0] = f.mean[0];
+    o[1] = f.mean[1];
+    for (int j = 0; j < 4; ++j) o[2 + j] = f.cov[j];
+    o[6] = (double)f.status;
+    o[7] = 0.0;
+  }
+}
+
+__global__ void k_batch_clear(DevState* __restrict__ st, const int* __restrict__ ids, int k) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) st[ids[i]].f.status = 0;
 }
 
 // Prior weights exp(-1/2 (x - m0)^T P0^{-1} (x - m0)) on the initial frame (float32 storage).
@@ -799,6 +853,14 @@ int tc_batch_step(int precision, const FilterSlot* slots, const StepItem* items,
   else
     k_fused2d_batch<PMF_PREC_TF32><<<k, kThreads, kSmemBytes, s>>>(slots, items);
   return 1;
+}
+
+int tc_batch_gather(DevState* st, const int* ids, int k, double* out, cudaStream_t s) {
+  if (k <= 0) return 0;
+  const int blocks = (k + 255) / 256;
+  k_batch_gather<<<blocks, 256, 0, s>>>(st, ids, k, out);
+  k_batch_clear<<<blocks, 256, 0, s>>>(st, ids, k);
+  return 2;
 }
 
 }  // namespace pmf

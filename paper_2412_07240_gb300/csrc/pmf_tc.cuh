@@ -56,5 +56,8 @@ int tc3_step(void* handle, const Dims& d, const pmf_config& cfg, const TcTables*
 
 // One launch, one CTA per item (items in device memory); returns launches.
 int tc_batch_step(int precision, const FilterSlot* slots, const StepItem* items, int k, cudaStream_t s);
+// {mean[2], cov[4], status, 0} of filters ids[0..k) into out (8 doubles each),
+// then their status words cleared; returns the number of launches.
+int tc_batch_gather(DevState* st, const int* ids, int k, double* out, cudaStream_t s);
 
 }  // namespace pmf

@@ -77,6 +77,43 @@ __device__ __forceinline__ float4 tmem_ld4(uint32_t taddr) {
   return make_float4(__uint_as_float(r0), __uint_as_float(r1), __uint_as_float(r2), __uint_as_float(r3));
 }
 
+// Columns [0, ncol) (ncol a multiple of 4, at most 32, the same in the whole
+// warp) of this thread's TMEM lane from taddr into v[0..ncol/4); v[j] beyond
+// are zero.  All loads are in flight together; the wait names the registers
+// so that no use of them is scheduled before it.
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, int ncol, float4 (&v)[8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    if (j * 4 < ncol) {
+      uint32_t r0, r1, r2, r3;
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                   : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                   : "r"(taddr + 4 * j)
+                   : "memory");
+      v[j] = make_float4(__uint_as_float(r0), __uint_as_float(r1), __uint_as_float(r2), __uint_as_float(r3));
+    } else {
+      v[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+  }
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+f"(v[0].x), "+f"(v[0].y), "+f"(v[0].z), "+f"(v[0].w), "+f"(v[1].x), "+f"(v[1].y),
+                 "+f"(v[1].z), "+f"(v[1].w), "+f"(v[2].x), "+f"(v[2].y), "+f"(v[2].z), "+f"(v[2].w),
+                 "+f"(v[3].x), "+f"(v[3].y), "+f"(v[3].z), "+f"(v[3].w)::"memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+f"(v[4].x), "+f"(v[4].y), "+f"(v[4].z), "+f"(v[4].w), "+f"(v[5].x), "+f"(v[5].y),
+                 "+f"(v[5].z), "+f"(v[5].w), "+f"(v[6].x), "+f"(v[6].y), "+f"(v[6].z), "+f"(v[6].w),
+                 "+f"(v[7].x), "+f"(v[7].y), "+f"(v[7].z), "+f"(v[7].w)::"memory");
+}
+
+// Bulk copy shared -> global (bulk-group completion), commit, and wait for
+// all of this thread's bulk groups to complete.
+__device__ __forceinline__ void bulk_store(void* dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
