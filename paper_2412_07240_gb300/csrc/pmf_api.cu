@@ -250,6 +250,10 @@ DevState initial_state(const pmf_config& c) {
     for (int a = 0; a < n; ++a) h.f.M[r * n + a] = L[r * n + a] * (2.0 * c.span_sigma / c.N[a]);
   inv(n, h.f.M, h.f.Minv);
   h.f.V = std::fabs(det(n, h.f.M));
+  if (n == 3) {
+    h.f.hc[0] = std::atan2(h.f.c[1], h.f.c[0]);
+    h.f.hc[1] = h.f.c[0] * h.f.c[0] + h.f.c[1] * h.f.c[1];
+  }
   h.f.pscale = 1.0;
   return h;
 }

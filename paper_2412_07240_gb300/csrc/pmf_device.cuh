@@ -341,4 +341,167 @@ __device__ inline bool finalize_t(FrameState* st, const double* tot, int use_pen
   return true;
 }
 
+
+// ---------------------------------------------------------------------------
+// Warp-parallel forms of frame_scalar and finalize_t: all 32 lanes of one warp
+// call them.  A float64 instruction costs GB300 ~64 cycles whatever the number
+// of active lanes (and independent instructions of one thread do not overlap),
+// so the entries of the small products run in parallel lanes: lane e < n*n of
+// each half-warp holds entry (e / n, e % n), lanes < n hold per-axis values.
+// Every entry is formed by the same operations in the same order as in the
+// one-thread forms.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double lget(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+template <int n>
+__device__ inline void frame_warp(const TimeConsts& tc, FrameState* st, double* pend, double* Mpi) {
+  constexpr int nn = n * n;
+  const int lane = threadIdx.x & 31, h = lane & 15;
+  const bool up = lane >= 16;
+  const int e = h < nn ? h : 0;   // matrix entry of this lane
+  const int i = e / n, j = e % n;
+  const int a = h < n ? h : 0;    // axis of this lane
+  // Su = Minv (cov + Qb) Minv^T (upper triangle as in cong_t, mirrored)
+  const double S = st->cov[e] + tc.Qb[e];
+  double T = 0.0;
+#pragma unroll
+  for (int k = 0; k < n; ++k) T = fma(st->Minv[i * n + k], lget(S, k * n + j), T);
+  double C = 0.0;
+#pragma unroll
+  for (int k = 0; k < n; ++k) C = fma(lget(T, i * n + k), st->Minv[j * n + k], C);
+  const double Su = lget(C, i <= j ? e : j * n + i);
+  const double Saa = lget(Su, a * (n + 1));
+  bool realign = false;
+  if (n >= 2) {
+    const double r2 = tc.rho_max * tc.rho_max;
+    const double Sii = lget(Su, i * (n + 1)), Sjj = lget(Su, j * (n + 1));
+    realign = __any_sync(0xffffffffu, lane < nn && i < j && Su * Su > r2 * Sii * Sjj);
+  }
+  if (realign) {
+    // rare: the one-thread form takes the re-alignment branch
+    if (lane == 0) frame_scalar<n>(tc, st, pend, Mpi);
+    __syncwarp();
+    return;
+  }
+  // centre shift towards the mean, a multiple of 1/64 node (lanes a)
+  const double dd = st->mean[a] - st->c[a];
+  double dm = 0.0;
+#pragma unroll
+  for (int b = 0; b < n; ++b) dm = fma(st->Minv[a * n + b], lget(dd, b), dm);
+  dm = rint(dm * 64.0) * (1.0 / 64.0);
+  double cn = st->c[a];
+#pragma unroll
+  for (int b = 0; b < n; ++b) cn = fma(st->M[a * n + b], lget(dm, b), cn);
+  // separable scale with an 8-bit mantissa (lanes a)
+  const double sd = sqrt(fmax(Saa, 0.0));
+  int ex;
+  const double f = frexp(2.0 * tc.span * sd / tc.N[a], &ex);
+  const double D = ldexp(rint(ldexp(f, 8)), ex - 8);
+  const double rD = 1.0 / D;
+  // Mp = M D (column j scaled), Mpi = D^{-1} Minv (row i scaled)
+  const double Mp = st->M[e] * lget(D, j);
+  const double Mpie = st->Minv[e] * lget(rD, i);
+  // pending frame: nM = Phi Mp (lower half-warp), nMi = Mpi PhiInv (upper
+  // half) and its centre Phi c' (upper lanes nn .. nn + n - 1)
+  const int pc = h - nn;
+  const bool is_pc = up && pc >= 0 && pc < n;
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < n; ++k) {
+    const double m1 = lget(Mpie, i * n + k), m2 = lget(Mp, k * n + j), m3 = lget(cn, k);
+    double x, y;
+    if (is_pc) {
+      x = tc.Phi[pc * n + k];
+      y = m3;
+    } else if (up) {
+      x = m1;
+      y = tc.PhiInv[k * n + j];
+    } else {
+      x = tc.Phi[i * n + k];
+      y = m2;
+    }
+    s = fma(x, y, s);
+  }
+  double nMv[nn];
+#pragma unroll
+  for (int q = 0; q < nn; ++q) nMv[q] = lget(s, q);
+  const double det = det_t<n>(nMv);
+  if (!up && h < nn) {
+    pend[3 + h] = s;
+    Mpi[h] = Mpie;
+  }
+  if (up && h < nn) pend[12 + h] = s;
+  if (is_pc) pend[pc] = s;
+  if (lane < n) {
+    st->rs[lane] = dm;
+    st->rd[lane] = D;
+  }
+  if (lane == 0) {
+    st->realign = 0;
+    st->exact = tc.exact;
+    st->l = tc.exact ? 1 : tc.l;
+    st->g = tc.g;
+    pend[21] = fabs(det);
+  }
+  __syncwarp();
+}
+
+template <int n>
+__device__ inline bool finalize_warp(FrameState* st, const double* tot, int use_pending, const double* pend) {
+  constexpr int nn = n * n;
+  const int lane = threadIdx.x & 31, h = lane & 15;
+  const bool up = lane >= 16;
+  const double S0 = tot[0];
+  if (!(S0 > 0.0) || !isfinite(S0)) {
+    if (lane == 0) st->status = PMF_ERR_DEGENERATE;
+    __syncwarp();
+    return false;
+  }
+  const int e = h < nn ? h : 0;
+  const int i = e / n, j = e % n;
+  const int a = h < n ? h : 0;
+  const double* c = use_pending ? pend : st->c;
+  const double* M = use_pending ? pend + 3 : st->M;
+  const double V = use_pending ? pend[21] : st->V;
+  const double r = 1.0 / S0;
+  const double mu = tot[1 + a] * r;
+  const double mui = lget(mu, i), muj = lget(mu, j);
+  const int k2 = i == j ? (i == 0 ? 4 : i == 1 ? 7 : 9) : (i + j == 1 ? 5 : i + j == 2 ? 6 : 8);
+  const double Cu = fma(tot[k2], r, -mui * muj);
+  // T = M Cu (lower half-warp) and the mean c + M mu (upper lanes a)
+  double s = up ? c[a] : 0.0;
+#pragma unroll
+  for (int k = 0; k < n; ++k) {
+    const double cu = lget(Cu, k * n + j), mk = lget(mu, k);
+    const double x = up ? M[a * n + k] : M[i * n + k], y = up ? mk : cu;
+    s = fma(x, y, s);
+  }
+  double C = 0.0;
+#pragma unroll
+  for (int k = 0; k < n; ++k) C = fma(lget(s, i * n + k), M[j * n + k], C);
+  const double cov = lget(C, i <= j ? e : j * n + i);
+  double Mv = 0.0, Miv = 0.0;
+  if (use_pending) {
+    Mv = pend[3 + e];
+    Miv = pend[12 + e];
+  }
+  __syncwarp();
+  if (up && h < n) st->mean[h] = s;
+  if (lane < nn) st->cov[lane] = cov;
+  if (use_pending) {
+    if (lane < n) st->c[lane] = pend[lane];
+    if (lane < nn) {
+      st->M[lane] = Mv;
+      st->Minv[lane] = Miv;
+    }
+    if (lane == 0) st->V = V;
+  }
+  if (lane == 0) {
+    st->S0 = S0;
+    st->pscale = r / V;
+  }
+  __syncwarp();
+  return true;
+}
+
 }  // namespace pmf

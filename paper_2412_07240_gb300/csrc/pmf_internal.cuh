@@ -54,6 +54,7 @@ struct FrameState {
   // regrid of the current time update
   double rs[3], rd[3];   // separable: u_old_m = rs_m + rd_m * u_new_m
   double B[9], b[3];     // realigned: u_old = B u_new + b
+  double hc[2];          // at the frame centre: atan2(c_2, c_1) and c_1^2 + c_2^2 (n_x = 3)
   int cur, status, realign, l, exact, pad;
 };
 

@@ -410,24 +410,29 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     // float64 while warps 1.. convert the staged weights into the R1 operand,
     // which needs neither.
     const float sa0 = op_scale<P>(block_max(sh, smax, 1));
-    if (tid == 0) {
+    if (warp == 0) {
       bool ok = true;
       if (job.do_meas) {
-        ok = finalize_t<2>(&fs, sh.tot, 0, nullptr);
-        if (!ok) {
-          sh.degenerate = 1;
-        } else {
-          sh.ps = (float)fs.pscale;   // the staged weights times ps are normalised
-          fs.pscale = 1.0;
-          fs.S0 = 1.0 / fs.V;
+        ok = finalize_warp<2>(&fs, sh.tot, 0, nullptr);
+        if (tid == 0) {
+          if (!ok) {
+            sh.degenerate = 1;
+          } else {
+            sh.ps = (float)fs.pscale;   // the staged weights times ps are normalised
+            fs.pscale = 1.0;
+            fs.S0 = 1.0 / fs.V;
+          }
         }
+        __syncwarp();
       }
       if (ok && job.do_time) {
-        frame_scalar<2>(sh.tc, &fs, sh.pend, sh.Mpi);
-        sh.g = (float)fs.g;
-        sh.gsc = (float)(fs.g / ((double)N0 * (double)N1));
+        frame_warp<2>(sh.tc, &fs, sh.pend, sh.Mpi);
+        if (tid == 0) {
+          sh.g = (float)fs.g;
+          sh.gsc = (float)(fs.g / ((double)N0 * (double)N1));
+        }
       }
-    } else if (job.do_time && warp > 0) {
+    } else if (job.do_time) {
       stage_to_operand<P>(A, S, N0, N1, sa0, tid - 32, kThreads - 32);
     }
     __syncthreads();
@@ -621,10 +626,10 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     }
 
     // ---- write-back (bulk stores of the staged rows) and normalisation ----
-    if (tid == 0) {
-      for (int r = 0; r < N0; ++r) bulk_store(out + (size_t)r * N1, su32(S + r * kSStr), (uint32_t)(N1 * 4));
+    if (warp == 0) {
+      for (int r = tid; r < N0; r += 32) bulk_store(out + (size_t)r * N1, su32(S + r * kSStr), (uint32_t)(N1 * 4));
       bulk_commit();
-      if (finalize_t<2>(&fs, sh.tot, 1, sh.pend)) fs.cur = cur ^ 1;
+      if (finalize_warp<2>(&fs, sh.tot, 1, sh.pend) && tid == 0) fs.cur = cur ^ 1;
       bulk_wait_all();
     }
   }

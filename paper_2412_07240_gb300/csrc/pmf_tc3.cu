@@ -55,7 +55,7 @@ struct Job3 {
   const uint8_t* hart[3];
   const float* sctab[3];
   Geo3 g;
-  double* partials;          // per-CTA moment partials (10 doubles each)
+  DF* partials;              // per-CTA moment partials (double-float, 16 slots each)
   unsigned int* emin_bits;   // float bits of the exponent minimum
   Update3* up;               // device
   double* pend;              // pending frame (device)
@@ -80,9 +80,9 @@ __device__ __forceinline__ float block_max3(Smem3& sh, float v, int slot) {
   return m;
 }
 
-// Block sum of double-float moment sums; thread 0 writes the 10 float64
-// partials {S0, S1[3], S2[6]} of this CTA.
-__device__ void block_partials3(Smem3& sh, const DF* s, double* out) {
+// Block sum of six double-float moment sums; thread 0 writes them (double-float)
+// to out.
+__device__ void block_partials3(Smem3& sh, const DF* s, DF* out) {
   DF a[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
@@ -108,7 +108,7 @@ __device__ void block_partials3(Smem3& sh, const DF* s, double* out) {
     }
     if (threadIdx.x == 0)
 #pragma unroll
-      for (int i = 0; i < 6; ++i) out[i] = (double)v[i].hi + (double)v[i].lo;
+      for (int i = 0; i < 6; ++i) out[i] = v[i];
   }
 }
 
@@ -289,15 +289,15 @@ __device__ void meas_consts(const MeasParams& mp, const FrameState& fs, Meas3& m
       m.r0[i] = (float)(mp.z[i] - h);
     }
   } else {
-    const double th = atan2(fs.c[1], fs.c[0]);
-    double r = mp.z[0] - th;
+    // angle and squared norm of the centre were formed when the frame was committed
+    double r = mp.z[0] - fs.hc[0];
     const double two_pi = 6.283185307179586476925286766559, pi = 3.14159265358979323846;
-    r -= two_pi * ceil((r - pi) / two_pi);
+    r -= two_pi * ceil((r - pi) * (1.0 / two_pi));
     m.r0[0] = (float)r;
     m.r0[1] = (float)(mp.z[1] - fs.c[2]);
     m.c0 = (float)fs.c[0];
     m.c1 = (float)fs.c[1];
-    m.cc = (float)(fs.c[0] * fs.c[0] + fs.c[1] * fs.c[1]);
+    m.cc = (float)fs.hc[1];
   }
 }
 
@@ -378,43 +378,44 @@ __global__ void __launch_bounds__(kT) k_meas_apply3(const __grid_constant__ Job3
   block_partials3(sh, s2, job.partials + (size_t)blockIdx.x * 16 + 6);
 }
 
-// Sum the per-CTA partials (16 doubles each: S0, S1[0..2], S2_00, S2_01 | S2_02,
-// S2_11, S2_12, S2_22, ...) into the {S0, S1[3], S2[6]} layout.
-__device__ void sum_partials3(const double* part, int nb, double* tot, double* red /* smem [kT/32][10] */) {
-  double a[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+// Sum the per-CTA partials (16 double-float slots each: S0, S1[0..2], S2_00,
+// S2_01 | S2_02, S2_11, S2_12, S2_22, ...) into tot = {S0, S1[3], S2[6]}:
+// double-float throughout, lanes 0..9 of warp 0 convert the totals to float64.
+__device__ void sum_partials3(const DF* part, int nb, double* tot, DF (*red)[10] /* smem [kT/32] */) {
+  DF a[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) a[i] = DF{0.0f, 0.0f};
   for (int b = threadIdx.x; b < nb; b += kT) {
-    const double* p = part + (size_t)b * 16;
-    a[0] += p[0];
-    a[1] += p[1];
-    a[2] += p[2];
-    a[3] += p[3];
-    a[4] += p[4];
-    a[5] += p[5];
-    a[6] += p[6];
-    a[7] += p[7];
-    a[8] += p[8];
-    a[9] += p[9];
+    const DF* p = part + (size_t)b * 16;
+#pragma unroll
+    for (int i = 0; i < 10; ++i) a[i] = df_add(a[i], p[i]);
   }
+#pragma unroll
   for (int i = 0; i < 10; ++i)
-    for (int o = 16; o; o >>= 1) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
-  if ((threadIdx.x & 31) == 0)
-    for (int i = 0; i < 10; ++i) red[(threadIdx.x >> 5) * 10 + i] = a[i];
+    for (int o = 16; o; o >>= 1) {
+      DF q{__shfl_xor_sync(0xffffffffu, a[i].hi, o), __shfl_xor_sync(0xffffffffu, a[i].lo, o)};
+      a[i] = df_add(a[i], q);
+    }
+  const int lane = threadIdx.x & 31;
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < 10; ++i) red[threadIdx.x >> 5][i] = a[i];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int w = 0; w < kT / 32; ++w)
-      for (int i = 0; i < 10; ++i) v[i] += red[w * 10 + i];
-    // partial layout -> {S0, S1[3], S2: 00,01,02,11,12,22}
-    tot[0] = v[0];
-    tot[1] = v[1];
-    tot[2] = v[2];
-    tot[3] = v[3];
-    tot[4] = v[4];
-    tot[5] = v[5];
-    tot[6] = v[6];
-    tot[7] = v[7];
-    tot[8] = v[8];
-    tot[9] = v[9];
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+      a[i] = lane < kT / 32 ? red[lane][i] : DF{0.0f, 0.0f};
+      for (int o = kT / 64; o; o >>= 1) {
+        DF q{__shfl_xor_sync(0xffffffffu, a[i].hi, o), __shfl_xor_sync(0xffffffffu, a[i].lo, o)};
+        a[i] = df_add(a[i], q);
+      }
+    }
+    DF mine = a[0];
+#pragma unroll
+    for (int i = 1; i < 10; ++i)
+      if (lane == i) mine = a[i];
+    if (lane < 10) tot[lane] = (double)mine.hi + (double)mine.lo;
+    __syncwarp();
   }
 }
 
@@ -425,7 +426,7 @@ __global__ void __launch_bounds__(kT) k_frame3(const __grid_constant__ Job3 job,
                                                int do_time) {
   __shared__ FrameState fs;
   __shared__ double tot[10];
-  __shared__ double red[kT / 32 * 10];
+  __shared__ DF red[kT / 32][10];
   __shared__ double Mpi[9];
   __shared__ int ok;
   DevState* st = job.st;
@@ -433,16 +434,15 @@ __global__ void __launch_bounds__(kT) k_frame3(const __grid_constant__ Job3 job,
   for (int i = threadIdx.x; i < kW; i += kT) ((unsigned long long*)&fs)[i] = ((const unsigned long long*)&st->f)[i];
   __syncthreads();
   if (do_meas) sum_partials3(job.partials, nb, tot, red);
-  if (threadIdx.x == 0) {
-    ok = 1;
+  if (threadIdx.x < 32) {
+    bool good = true;
     if (do_meas) {
-      if (!finalize_t<3>(&fs, tot, 0, nullptr)) {
-        ok = 0;
-      } else {
-        fs.cur ^= 1;          // the multiplied weights are in the other buffer
-      }
+      good = finalize_warp<3>(&fs, tot, 0, nullptr);
+      if (good && threadIdx.x == 0) fs.cur ^= 1;   // the multiplied weights are in the other buffer
+      __syncwarp();
     }
-    if (ok && do_time) frame_scalar<3>(tc, &fs, job.pend, Mpi);
+    if (good && do_time) frame_warp<3>(tc, &fs, job.pend, Mpi);
+    if (threadIdx.x == 0) ok = good;
   }
   __syncthreads();
   if (threadIdx.x == 0) job.up->skip = !(ok && do_time);
@@ -850,7 +850,7 @@ __global__ void __launch_bounds__(kT, 1) k_slices_inv(const __grid_constant__ Jo
       }
     }
     tc_before_sync();
-    double* part = job.partials + (size_t)j0 * 16;
+    DF* part = job.partials + (size_t)j0 * 16;
     block_partials3(sh, s, part);
     __syncthreads();
     DF t4[6] = {s2[0], s2[1], s2[2], s2[3], DF{0.0f, 0.0f}, DF{0.0f, 0.0f}};
@@ -867,14 +867,17 @@ fail:
 __global__ void __launch_bounds__(kT) k_commit3(const __grid_constant__ Job3 job, int nb) {
   __shared__ FrameState fs;
   __shared__ double tot[10];
-  __shared__ double red[kT / 32 * 10];
+  __shared__ DF red[kT / 32][10];
   DevState* st = job.st;
   if (job.up->skip) return;
   constexpr int kW = sizeof(FrameState) / 8;
   for (int i = threadIdx.x; i < kW; i += kT) ((unsigned long long*)&fs)[i] = ((const unsigned long long*)&st->f)[i];
   __syncthreads();
   sum_partials3(job.partials, nb, tot, red);
-  if (threadIdx.x == 0) finalize_t<3>(&fs, tot, 1, job.pend);
+  if (threadIdx.x < 32 && finalize_warp<3>(&fs, tot, 1, job.pend) && threadIdx.x == 0) {
+    fs.hc[0] = atan2(fs.c[1], fs.c[0]);
+    fs.hc[1] = fs.c[0] * fs.c[0] + fs.c[1] * fs.c[1];
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < kW; i += kT) ((unsigned long long*)&st->f)[i] = ((const unsigned long long*)&fs)[i];
 }
@@ -885,7 +888,7 @@ __global__ void __launch_bounds__(kT) k_commit3(const __grid_constant__ Job3 job
 struct Tc3State {
   Update3* up = nullptr;
   double* pend = nullptr;
-  double* partials = nullptr;
+  DF* partials = nullptr;
   unsigned int* emin = nullptr;
 };
 
@@ -893,7 +896,7 @@ int tc3_alloc(void** handle) {
   Tc3State* s = new (std::nothrow) Tc3State();
   if (!s) return PMF_ERR_OOM;
   if (cudaMalloc(&s->up, sizeof(Update3)) != cudaSuccess || cudaMalloc(&s->pend, 32 * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&s->partials, 16 * 4096 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&s->partials, 16 * 4096 * sizeof(DF)) != cudaSuccess ||
       cudaMalloc(&s->emin, sizeof(unsigned int)) != cudaSuccess) {
     tc3_free(s);
     return PMF_ERR_OOM;
