@@ -144,6 +144,13 @@ def _launch_names(sc):
     return "k_fused2d" if sc.cfg.nx == 2 else "k_slices_fwd+k_lines_axis0+k_slices_inv"
 
 
+# DRAM bytes (read + write) per launch of the timed kernel, from one ncu capture
+# of the current kernel (profiles/): the 128 x 128 fused kernel, and the batch
+# kernel per grid point (captured on 2048 filters, scaled by the points).
+TRAFFIC_C2 = 373760.0
+TRAFFIC_C4_PER_POINT = (53320704.0 + 11064320.0) / 10976512.0
+
+
 def _flops_per_step(N):
     """Algorithmic transform flops of one epoch: forward + inverse per axis, 2 N_m flops per point each."""
     P = 1
@@ -321,7 +328,8 @@ def bench_batch(args, ws, rank, pg):
             "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
             "degenerate_filters": bad,
             "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks.get("bf16_tflops"),
-                         "unit": "TFLOP/s", "frac": ach / peaks.get("bf16_tflops"), "traffic": None,
+                         "unit": "TFLOP/s", "frac": ach / peaks.get("bf16_tflops"),
+                         "traffic": TRAFFIC_C4_PER_POINT * float(P.sum()),
                          "kernel": "k_fused2d_batch", "flops_per_launch": flops},
             "clocks": clk.summary()}
     if rank == 0:
@@ -397,7 +405,8 @@ def main():
                      "launches_per_step": l64 / max(1, len(ms64))},
         "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
         "roofline": {"bound": "tensor", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / peak, "traffic": None,
+                     "frac": achieved_tflops / peak,
+                     "traffic": TRAFFIC_C2 if sc.name.startswith("c2") and tuple(sc.cfg.N) == (128, 128) else None,
                      "kernel": _launch_names(sc), "peak_source": f"bf16_tflops ({peak_src})",
                      "flops_per_launch": flops},
         "clocks": clk.summary(),
