@@ -61,7 +61,9 @@ enum {
  *   FP16X3  : float32 grid, split FP16 with power-of-two operand scaling,
  *             (hi*hi + hi*lo + lo*hi), FP32 accumulate.
  * Everything else of a step runs in float32 on the non-FP64 paths, with the
- * frame, the normalisation constant and the moment combination in float64. */
+ * frame, the normalisation constant and the moment combination in float64.
+ * For n_x = 1 every precision other than FP64 selects the float32 CUDA-core
+ * kernel (a 1-D transform is a matrix-vector product, not a tensor-core tile). */
 enum {
   PMF_PREC_FP64 = 0,
   PMF_PREC_TF32 = 1,
@@ -88,7 +90,8 @@ enum {
 typedef struct pmf_config {
   int nx;                       /* state dimension, 1..PMF_MAX_NX */
   int N[PMF_MAX_NX];            /* grid points per axis (even; the tensor-core
-                                   path needs multiples of 16 and N <= 128) */
+                                   paths need multiples of 16 and N <= 128, the
+                                   1-D kernel a multiple of 8 in [16, 512]) */
   double A[PMF_MAX_NX * PMF_MAX_NX];   /* drift, nx x nx row-major packed (a_ij at i*nx+j) */
   double Q[PMF_MAX_NX * PMF_MAX_NX];   /* diffusion, symmetric PSD, packed like A */
   double m0[PMF_MAX_NX];        /* prior mean */
@@ -152,7 +155,8 @@ int pmf_get_pdf(pmf_ctx* ctx, double* host_out, double* c_out, double* M_out);
 int pmf_sync(pmf_ctx* ctx);
 
 /* Number of grid points (prod N_m) and the selected path:
- * 0 = plain FP64 kernels, 1 = fused tensor-core kernel, 2 = per-axis kernels. */
+ * 0 = plain FP64 kernels, 1 = fused 2-D tensor-core kernel, 2 = 3-D
+ * tensor-core pipelines, 3 = 1-D CUDA-core kernel. */
 long long pmf_num_points(const pmf_ctx* ctx);
 int pmf_path(const pmf_ctx* ctx);
 
@@ -205,6 +209,70 @@ int pmf_batch_get_pdf(pmf_batch* b, int id, double* host_out, double* c_out, dou
 long long pmf_batch_bytes(const pmf_batch* b);
 long long pmf_batch_launch_count(const pmf_batch* b);
 void pmf_batch_destroy(pmf_batch* b);
+
+/* ---------------------------------------------------------------------------
+ * Serving: resident filters of mixed dimension updated by continuous batching.
+ * (The paper runs one filter; this layer has no counterpart there.)
+ *
+ * A server owns the device memory of every admitted filter (grids, frame
+ * state, measurement model) and three CUDA streams of its own.  A request is a
+ * measurement z followed by a time update over tau, the time to the filter's
+ * next measurement (pmf_step semantics).  Requests queue per filter; whenever
+ * fewer than PMF_SERVE_INFLIGHT batches are on the device the server forms a
+ * batch from the head request of every idle filter that has one: the 1-D
+ * filters in one launch of the 1-D kernel, the 2-D filters in one launch of
+ * the fused batch kernel, the 3-D filters through their pipelines on the third
+ * stream, all three overlapping.  A filter has at most one request on the
+ * device, and each runs in its own CTAs, so its results do not depend on what
+ * else shares the batch.  A tau needing more than PMF_MAX_SUBSTEPS sub-steps
+ * runs as consecutive time updates of at most that many.
+ * ------------------------------------------------------------------------- */
+#define PMF_SERVE_INFLIGHT 4
+#define PMF_SERVE_NSTATS 6
+typedef struct pmf_server pmf_server;
+
+/* hbm_budget: device bytes the server may hold for filters and their tables
+ * (0 = no limit); max_filters: size of the id space (ids 0..max_filters-1);
+ * precision: PMF_PREC_FP16X3, _BF16X3 or _TF32 for the 2-D and 3-D filters
+ * (1-D filters use the float32 kernel).  PMF_ERR_ARG on bad arguments,
+ * PMF_ERR_OOM / PMF_ERR_CUDA if the server's own buffers cannot be made. */
+int pmf_server_create(pmf_server** out, size_t hbm_budget, int max_filters, int precision);
+
+/* Admit a filter with measurement model `model` (z is ignored); its prior is
+ * formed on the device before the call returns.  *id_out receives its id.
+ * PMF_ERR_ADMISSION if its memory would exceed the budget or no id is free,
+ * PMF_ERR_UNSUPPORTED if no fast path holds the grid (1-D: N multiple of 8 in
+ * [16, 512]; 2-D and 3-D: multiples of 16 up to 128), PMF_ERR_ARG on an
+ * invalid configuration or model. */
+int pmf_server_admit(pmf_server* s, const pmf_config* cfg, const pmf_meas* model, int* id_out);
+
+/* Release filter id and its memory (after its work on the device). */
+int pmf_server_evict(pmf_server* s, int id);
+
+/* Device bytes held for the admitted filters and shared tables (the amount
+ * the budget is checked against). */
+long long pmf_server_bytes(const pmf_server* s);
+
+/* Replay a request log in real time on the calling thread.  Request i arrives
+ * t_arrival[i] seconds after the call starts (ascending), for filter ids[i],
+ * with measurement z[i*PMF_MAX_NZ ...] and then a time update over taus[i]
+ * (finite, >= 0).  Returns when every request has completed.  latency_out[i]
+ * (may be NULL) = completion observed on the host - arrival, in seconds.
+ * stats_out (may be NULL) receives PMF_SERVE_NSTATS doubles: wall seconds,
+ * batches, kernel launches, largest batch, mean batch, requests.  All arrays
+ * are caller-owned host memory, read during the call only. */
+int pmf_server_replay(pmf_server* s, long long n, const double* t_arrival, const int* ids, const double* z,
+                      const double* taus, double* latency_out, double* stats_out);
+
+/* Mean (nx) and covariance (nx*nx) of filter id.  Synchronous; returns the
+ * filter's pending device status (e.g. PMF_ERR_DEGENERATE), then clears it. */
+int pmf_server_moments(pmf_server* s, int id, double* mean_out, double* cov_out);
+
+/* Weights (prod N), frame centre and matrix of filter id, as pmf_get_pdf. */
+int pmf_server_get_pdf(pmf_server* s, int id, double* host_out, double* c_out, double* M_out);
+
+const char* pmf_server_last_error(const pmf_server* s);
+void pmf_server_destroy(pmf_server* s);
 
 /* ---- moments without device allocation --------------------------------------
  * The paper has no counterpart to this entry point: it is a service for

@@ -79,9 +79,22 @@ SIGNATURES = [
     ("pmf_batch_bytes", C.c_longlong, [C.c_void_p]),
     ("pmf_batch_launch_count", C.c_longlong, [C.c_void_p]),
     ("pmf_batch_destroy", None, [C.c_void_p]),
+    ("pmf_server_create", C.c_int, [C.POINTER(C.c_void_p), C.c_size_t, C.c_int, C.c_int]),
+    ("pmf_server_admit", C.c_int, [C.c_void_p, C.POINTER(PmfConfig), C.POINTER(PmfMeas), C.POINTER(C.c_int)]),
+    ("pmf_server_evict", C.c_int, [C.c_void_p, C.c_int]),
+    ("pmf_server_bytes", C.c_longlong, [C.c_void_p]),
+    ("pmf_server_replay", C.c_int, [C.c_void_p, C.c_longlong, C.POINTER(C.c_double), C.POINTER(C.c_int),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]),
+    ("pmf_server_moments", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("pmf_server_get_pdf", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double)]),
+    ("pmf_server_last_error", C.c_char_p, [C.c_void_p]),
+    ("pmf_server_destroy", None, [C.c_void_p]),
     ("pmf_moments_noalloc", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.c_void_p, C.c_void_p]),
 ]
+SERVE_NSTATS = 6
 
 _lib = None
 
@@ -345,6 +358,99 @@ class Batch:
     def close(self) -> None:
         if getattr(self, "_h", None):
             self._lib.pmf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Resident filters of mixed dimension served by continuous batching (a pmf_server)."""
+
+    def __init__(self, max_filters, precision="fp16x3", hbm_budget=0):
+        self._lib = load()
+        h = C.c_void_p()
+        rc = self._lib.pmf_server_create(C.byref(h), int(hbm_budget), int(max_filters), PREC[precision])
+        if rc != OK:
+            raise PmfError(rc, "pmf_server_create failed")
+        self._h = h
+        self.nx = {}
+        self.N = {}
+
+    def _err(self, rc, what):
+        msg = self._lib.pmf_server_last_error(self._h)
+        msg = msg.decode() if msg else ""
+        cls = Degenerate if rc == ERR_DEGENERATE else Unsupported if rc == ERR_UNSUPPORTED else PmfError
+        return cls(rc, f"{what}: {msg}")
+
+    def admit(self, cfg, model) -> int:
+        """Admit a filter; returns its id (PmfError with code ERR_ADMISSION over the budget)."""
+        nx = int(cfg.nx)
+        c = make_config(cfg, "fp16x3")
+        m = make_meas(model, np.zeros(np.asarray(model.R).shape[0]), nx)
+        fid = C.c_int(-1)
+        rc = self._lib.pmf_server_admit(self._h, C.byref(c), C.byref(m), C.byref(fid))
+        if rc != OK:
+            raise self._err(rc, "pmf_server_admit")
+        self.nx[fid.value] = nx
+        self.N[fid.value] = tuple(int(v) for v in cfg.N[:nx])
+        return fid.value
+
+    def evict(self, fid) -> None:
+        rc = self._lib.pmf_server_evict(self._h, int(fid))
+        if rc != OK:
+            raise self._err(rc, "pmf_server_evict")
+        self.nx.pop(int(fid), None)
+        self.N.pop(int(fid), None)
+
+    @property
+    def bytes(self) -> int:
+        return int(self._lib.pmf_server_bytes(self._h))
+
+    def replay(self, t_arrival, ids, z, taus):
+        """Replay a request log in real time; returns (latency seconds per request, stats dict)."""
+        t = np.ascontiguousarray(t_arrival, dtype=np.float64)
+        n = t.size
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        zz = np.zeros((n, MAX_NZ))
+        z = np.asarray(z, dtype=np.float64).reshape(n, -1)
+        zz[:, :z.shape[1]] = z
+        taus = np.ascontiguousarray(taus, dtype=np.float64)
+        lat = np.zeros(n)
+        st = np.zeros(SERVE_NSTATS)
+        rc = self._lib.pmf_server_replay(self._h, n, _dptr(t), _iptr(ids), _dptr(zz), _dptr(taus), _dptr(lat),
+                                         _dptr(st))
+        if rc != OK:
+            raise self._err(rc, "pmf_server_replay")
+        keys = ["wall_s", "batches", "launches", "max_batch", "mean_batch", "requests"]
+        return lat, dict(zip(keys, st.tolist()))
+
+    def moments(self, fid):
+        n = self.nx[int(fid)]
+        m = (C.c_double * n)()
+        P = (C.c_double * (n * n))()
+        rc = self._lib.pmf_server_moments(self._h, int(fid), m, P)
+        if rc != OK:
+            raise self._err(rc, "pmf_server_moments")
+        return np.array(m[:]), np.array(P[:]).reshape(n, n)
+
+    def pdf(self, fid):
+        fid = int(fid)
+        n = self.nx[fid]
+        out = np.empty(int(np.prod(self.N[fid])))
+        c = np.empty(n)
+        M = np.empty(n * n)
+        rc = self._lib.pmf_server_get_pdf(self._h, fid, _dptr(out), _dptr(c), _dptr(M))
+        if rc != OK:
+            raise self._err(rc, "pmf_server_get_pdf")
+        return out.reshape(self.N[fid]), c, M.reshape(n, n)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.pmf_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

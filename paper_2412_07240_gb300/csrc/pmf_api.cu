@@ -10,6 +10,7 @@
 
 #include "pmf_internal.cuh"
 #include "pmf_kernels.cuh"
+#include "pmf_model.cuh"
 #include "pmf_tc.cuh"
 
 using namespace pmf;
@@ -18,7 +19,8 @@ struct pmf_ctx {
   pmf_config cfg;
   cudaStream_t stream = nullptr;
   Dims dims{};
-  int path = 0;               // 0 float64 kernels, 1 fused tensor-core kernel
+  int path = 0;               // 0 float64 kernels, 1 fused 2-D tensor-core kernel,
+                              // 2 3-D tensor-core pipelines, 3 1-D CUDA-core kernel
   DevState* st = nullptr;     // device
   void* buf[2] = {nullptr, nullptr};
   double* partials = nullptr;
@@ -28,6 +30,7 @@ struct pmf_ctx {
   double* hinv[MAXN] = {nullptr, nullptr, nullptr};
   double* prior_aux = nullptr;  // P0^{-1} (9) and m0 (3)
   TcTables tct{};               // tensor-core path tables (pmf_tc.cu)
+  void* tab1 = nullptr;         // 1-D kernel table (pmf_tc1.cu)
   void* tc3 = nullptr;          // 3-D pipeline state (pmf_tc3.cu)
   TimeConsts tc{};
   double tc_tau = -1.0;
@@ -50,187 +53,10 @@ int fail(pmf_ctx* ctx, int code, const std::string& msg) {
                   std::string(#call) + ": " + cudaGetErrorString(e_));               \
   } while (0)
 
-bool finite_all(const double* v, int n) {
-  for (int i = 0; i < n; ++i)
-    if (!std::isfinite(v[i])) return false;
-  return true;
-}
-
-// Matrix exponential by scaling and squaring of the Taylor series (float64):
-// ||X / 2^s||_1 <= 1/4, terms summed until below 1e-20 of the partial sum.
-void expm_host(int n, const double* A, double* E) {
-  double nrm = 0.0;
-  for (int j = 0; j < n; ++j) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += std::fabs(A[i * n + j]);
-    nrm = std::fmax(nrm, s);
-  }
-  int sq = 0;
-  if (nrm > 0.25) sq = (int)std::ceil(std::log2(nrm / 0.25));
-  const double sc = std::ldexp(1.0, -sq);
-  double X[64], T[64], U[64];
-  for (int i = 0; i < n * n; ++i) {
-    X[i] = A[i] * sc;
-    E[i] = 0.0;
-    T[i] = 0.0;
-  }
-  for (int i = 0; i < n; ++i) E[i * n + i] = T[i * n + i] = 1.0;
-  for (int k = 1; k < 40; ++k) {
-    mm(n, T, X, U);
-    double tn = 0.0, en = 0.0;
-    for (int i = 0; i < n * n; ++i) {
-      T[i] = U[i] / k;
-      E[i] += T[i];
-      tn = std::fmax(tn, std::fabs(T[i]));
-      en = std::fmax(en, std::fabs(E[i]));
-    }
-    if (tn < 1e-20 * en) break;
-  }
-  for (int s = 0; s < sq; ++s) {
-    mm(n, E, E, U);
-    for (int i = 0; i < n * n; ++i) E[i] = U[i];
-  }
-}
-
-// Constants of a time update over tau (model only): Phi = e^{A tau},
-// Q_d = int_0^tau e^{As} Q e^{A^T s} ds (Van Loan block exponential),
-// Q_b = Phi^{-1} Q_d Phi^{-T}, E = e^{-A dt}, trace factor.
-int time_consts(const pmf_config& c, double tau, TimeConsts* tc, std::string* why) {
-  const int n = c.nx;
-  *tc = TimeConsts{};
-  tc->nx = n;
-  for (int a = 0; a < n; ++a) tc->N[a] = c.N[a];
-  int l = (int)std::ceil(tau / c.dt_sub - 1e-9);
-  if (l < 1) l = 1;
-  if (l > MAXL) {
-    *why = "tau / dt_sub exceeds PMF_MAX_SUBSTEPS";
-    return PMF_ERR_ARG;
-  }
-  tc->l = l;
-  tc->tau = tau;
-  tc->dt = tau / l;
-  tc->exact = c.psi_mode == PMF_PSI_EXACT;
-  tc->span = c.span_sigma;
-  tc->rho_max = c.realign_rho;
-  double At[9], mAt[9], mAdt[9];
-  double trA = 0.0;
-  for (int i = 0; i < n * n; ++i) {
-    At[i] = c.A[i] * tau;
-    mAt[i] = -c.A[i] * tau;
-    mAdt[i] = -c.A[i] * tc->dt;
-    tc->Q[i] = c.Q[i];
-  }
-  for (int i = 0; i < n; ++i) trA += c.A[i * n + i];
-  expm_host(n, At, tc->Phi);
-  expm_host(n, mAt, tc->PhiInv);
-  expm_host(n, mAdt, tc->Estep);
-  const int m = 2 * n;
-  double C[36] = {0}, E[36];
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
-      C[i * m + j] = -c.A[i * n + j] * tau;
-      C[i * m + n + j] = c.Q[i * n + j] * tau;
-      C[(n + i) * m + n + j] = c.A[j * n + i] * tau;
-    }
-  expm_host(m, C, E);
-  double F12[9], Phi2[9], Qd[9];
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
-      F12[i * n + j] = E[i * m + n + j];
-      Phi2[i * n + j] = E[(n + j) * m + n + i];  // (F22)^T
-    }
-  mm(n, Phi2, F12, Qd);
-  for (int i = 0; i < n; ++i)
-    for (int j = i + 1; j < n; ++j) Qd[i * n + j] = Qd[j * n + i] = 0.5 * (Qd[i * n + j] + Qd[j * n + i]);
-  congruence(n, tc->PhiInv, Qd, tc->Qb);
-  // rotated diffusion at the sub-step ends: e^{-A q dt} Q e^{-A^T q dt}, q = 1..l
-  double Eq[9], mAq[9], Qq[9];
-  for (int q = 1; q <= l; ++q) {
-    for (int i = 0; i < n * n; ++i) mAq[i] = -c.A[i] * (tc->dt * q);
-    expm_host(n, mAq, Eq);
-    congruence(n, Eq, c.Q, Qq);
-    double* o = tc->Qt[q - 1];
-    o[0] = Qq[0];
-    o[1] = n > 1 ? Qq[1] : 0.0;
-    o[2] = n > 2 ? Qq[2] : 0.0;
-    o[3] = n > 1 ? Qq[n + 1] : 0.0;
-    o[4] = n > 2 ? Qq[5] : 0.0;
-    o[5] = n > 2 ? Qq[8] : 0.0;
-  }
-  tc->g = tc->exact ? std::exp(-trA * tau) : std::pow(1.0 - tc->dt * trA, (double)l);
-  return PMF_OK;
-}
-
 int make_time_consts(pmf_ctx* ctx, double tau, TimeConsts* tc) {
   std::string why;
   const int rc = time_consts(ctx->cfg, tau, tc, &why);
   return rc ? fail(ctx, rc, why) : PMF_OK;
-}
-
-int validate_config(const pmf_config* c, std::string* why) {
-  if (!c) { *why = "null config"; return PMF_ERR_ARG; }
-  if (c->nx < 1 || c->nx > PMF_MAX_NX) { *why = "nx out of range"; return PMF_ERR_ARG; }
-  const int n = c->nx;
-  for (int a = 0; a < n; ++a)
-    if (c->N[a] < 4 || (c->N[a] & 1) || c->N[a] > 4096) { *why = "N must be even, 4..4096"; return PMF_ERR_ARG; }
-  if (!finite_all(c->A, n * n) || !finite_all(c->Q, n * n) || !finite_all(c->m0, n) ||
-      !finite_all(c->P0, n * n)) { *why = "non-finite model value"; return PMF_ERR_ARG; }
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j)
-      if (std::fabs(c->Q[i * n + j] - c->Q[j * n + i]) > 1e-12 * (1 + std::fabs(c->Q[i * n + j])) ||
-          std::fabs(c->P0[i * n + j] - c->P0[j * n + i]) > 1e-12 * (1 + std::fabs(c->P0[i * n + j]))) {
-        *why = "Q and P0 must be symmetric";
-        return PMF_ERR_ARG;
-      }
-  double L[9], Qs[9], tr = 0.0;
-  for (int i = 0; i < n; ++i) tr += std::fabs(c->Q[i * n + i]);
-  for (int i = 0; i < n * n; ++i) Qs[i] = c->Q[i];
-  for (int i = 0; i < n; ++i) Qs[i * n + i] += 1e-12 * (tr + 1e-300);
-  if (tr > 0.0 && !chol(n, Qs, L)) { *why = "Q is not positive semidefinite"; return PMF_ERR_ARG; }
-  for (int i = 0; i < n; ++i)
-    if (c->Q[i * n + i] < 0) { *why = "Q is not positive semidefinite"; return PMF_ERR_ARG; }
-  if (!chol(n, c->P0, L)) { *why = "P0 is not positive definite"; return PMF_ERR_ARG; }
-  if (!(c->span_sigma > 0) || !(c->dt_sub > 0) || !(c->realign_rho > 0)) { *why = "span, dt_sub, rho must be > 0"; return PMF_ERR_ARG; }
-  if (c->precision < PMF_PREC_FP64 || c->precision > PMF_PREC_FP16X3) { *why = "unknown precision"; return PMF_ERR_ARG; }
-  if (c->psi_mode != PMF_PSI_EULER && c->psi_mode != PMF_PSI_EXACT) { *why = "unknown psi mode"; return PMF_ERR_ARG; }
-  return PMF_OK;
-}
-
-// Hartley matrix cas(2 pi k j / N) with exact integer reduction of k j mod N.
-void hartley_host(int N, double scale, double* H) {
-  const double w = 6.283185307179586476925286766559 / N;
-  for (int k = 0; k < N; ++k)
-    for (int j = 0; j < N; ++j) {
-      const long long r = ((long long)k * j) % N;
-      H[k * N + j] = scale * (std::cos(w * r) + std::sin(w * r));
-    }
-}
-
-int meas_params(int n, const pmf_meas* m, MeasParams* mp, std::string* why) {
-  if (!m) { *why = "null measurement"; return PMF_ERR_ARG; }
-  const int nz = m->nz;
-  if (m->kind == PMF_MEAS_RANGE) {
-    if (nz != 1 || n < 2) { *why = "range measurement needs nz = 1, nx >= 2"; return PMF_ERR_ARG; }
-  } else if (m->kind == PMF_MEAS_BEARING_LINEAR3) {
-    if (nz != 2 || n < 3) { *why = "bearing measurement needs nz = 2, nx = 3"; return PMF_ERR_ARG; }
-  } else if (m->kind == PMF_MEAS_LINEAR) {
-    if (nz < 1 || nz > PMF_MAX_NZ) { *why = "linear measurement nz out of range"; return PMF_ERR_ARG; }
-    if (!finite_all(m->H, nz * n)) { *why = "non-finite H"; return PMF_ERR_ARG; }
-  } else {
-    *why = "unknown measurement kind";
-    return PMF_ERR_ARG;
-  }
-  if (!finite_all(m->z, nz) || !finite_all(m->R, nz * nz)) { *why = "non-finite z or R"; return PMF_ERR_ARG; }
-  double L[9];
-  if (!chol(nz, m->R, L)) { *why = "R is not positive definite"; return PMF_ERR_ARG; }
-  *mp = MeasParams{};
-  mp->kind = m->kind;
-  mp->nz = nz;
-  mp->nx = n;
-  for (int i = 0; i < nz; ++i) mp->z[i] = m->z[i];
-  for (int i = 0; i < nz * n; ++i) mp->H[i] = m->H[i];
-  inv(nz, m->R, mp->Rinv);
-  return PMF_OK;
 }
 
 int build_meas(pmf_ctx* ctx, const pmf_meas* m, MeasParams* mp) {
@@ -239,24 +65,6 @@ int build_meas(pmf_ctx* ctx, const pmf_meas* m, MeasParams* mp) {
   return rc ? fail(ctx, rc, why) : PMF_OK;
 }
 
-// Initial frame c = m0, M = chol(P0) diag(2 span / N) and unit normaliser.
-DevState initial_state(const pmf_config& c) {
-  DevState h{};
-  const int n = c.nx;
-  double L[9];
-  chol(n, c.P0, L);
-  for (int a = 0; a < n; ++a) h.f.c[a] = c.m0[a];
-  for (int r = 0; r < n; ++r)
-    for (int a = 0; a < n; ++a) h.f.M[r * n + a] = L[r * n + a] * (2.0 * c.span_sigma / c.N[a]);
-  inv(n, h.f.M, h.f.Minv);
-  h.f.V = std::fabs(det(n, h.f.M));
-  if (n == 3) {
-    h.f.hc[0] = std::atan2(h.f.c[1], h.f.c[0]);
-    h.f.hc[1] = h.f.c[0] * h.f.c[0] + h.f.c[1] * h.f.c[1];
-  }
-  h.f.pscale = 1.0;
-  return h;
-}
 
 void free_ctx(pmf_ctx* ctx) {
   if (!ctx) return;
@@ -273,11 +81,15 @@ void free_ctx(pmf_ctx* ctx) {
   }
   tc_free_tables(&ctx->tct);
   tc3_free(ctx->tc3);
+  cudaFree(ctx->tab1);
   delete ctx;
 }
 
 // One launch (2-D fused kernel) or the 3-D pipelines; returns kernel launches.
 int fast_step(pmf_ctx* ctx, const MeasParams* mp, const TimeConsts* tc) {
+  if (ctx->path == 3)
+    return tc1_step(ctx->cfg.N[0], ctx->tab1, mp, tc, ctx->st, (float*)ctx->buf[0], (float*)ctx->buf[1],
+                    ctx->stream);
   if (ctx->path == 2)
     return tc3_step(ctx->tc3, ctx->dims, ctx->cfg, &ctx->tct, mp, tc, ctx->st, (float*)ctx->buf[0],
                     (float*)ctx->buf[1], ctx->stream);
@@ -331,12 +143,12 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
   const long long P = ctx->dims.P;
 
   if (cfg->precision != PMF_PREC_FP64) {
-    rc = tc_supported(cfg, &why);
+    rc = cfg->nx == 1 ? tc1_supported(cfg, &why) : tc_supported(cfg, &why);
     if (rc) {
       free_ctx(ctx);
       return rc;
     }
-    ctx->path = cfg->nx == 3 ? 2 : 1;
+    ctx->path = cfg->nx == 1 ? 3 : cfg->nx == 3 ? 2 : 1;
   }
 
 #define ALLOC(ptr, bytes)                                     \
@@ -367,6 +179,12 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
       hartley_host(N, 1.0, H);
       cudaMemcpy(ctx->hinv[a], H, sizeof(double) * N * N, cudaMemcpyHostToDevice);
       delete[] H;
+    }
+  } else if (ctx->path == 3) {
+    rc = tc1_build_table(cfg->N[0], &ctx->tab1);
+    if (rc) {
+      free_ctx(ctx);
+      return rc;
     }
   } else {
     rc = tc_build_tables(cfg, &ctx->tct, &why);

@@ -654,12 +654,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused2d(const __grid_constant__
 // parts of the epoch to run and its measurement.
 template <int P>
 __global__ void __launch_bounds__(kThreads, 1) k_fused2d_batch(const FilterSlot* __restrict__ slots,
-                                                               const StepItem* __restrict__ items) {
+                                                               const StepItem* __restrict__ items,
+                                                               const TimeConsts* __restrict__ tcs) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const StepItem& it = items[blockIdx.x];
   const FilterSlot& sl = slots[it.slot];
   const FusedView v{sl.st, sl.buf0, sl.buf1, {sl.hart[0], sl.hart[1]}, {sl.sctab[0], sl.sctab[1]},
-                    sl.N0, sl.N1, it.flags & 1, (it.flags >> 1) & 1, sl.mp, it.z, sl.tc};
+                    sl.N0, sl.N1, it.flags & 1, (it.flags >> 1) & 1, sl.mp, it.z,
+                    tcs ? tcs + blockIdx.x : sl.tc};
   fused2d<P>(v, smem);
 }
 
@@ -849,14 +851,15 @@ int tc_step(const Dims& d, const pmf_config& cfg, const TcTables* t, const MeasP
   return 1;
 }
 
-int tc_batch_step(int precision, const FilterSlot* slots, const StepItem* items, int k, cudaStream_t s) {
+int tc_batch_step(int precision, const FilterSlot* slots, const StepItem* items, int k, cudaStream_t s,
+                  const TimeConsts* tcs) {
   if (k <= 0) return 0;
   if (precision == PMF_PREC_FP16X3)
-    k_fused2d_batch<PMF_PREC_FP16X3><<<k, kThreads, kSmemBytes, s>>>(slots, items);
+    k_fused2d_batch<PMF_PREC_FP16X3><<<k, kThreads, kSmemBytes, s>>>(slots, items, tcs);
   else if (precision == PMF_PREC_BF16X3)
-    k_fused2d_batch<PMF_PREC_BF16X3><<<k, kThreads, kSmemBytes, s>>>(slots, items);
+    k_fused2d_batch<PMF_PREC_BF16X3><<<k, kThreads, kSmemBytes, s>>>(slots, items, tcs);
   else
-    k_fused2d_batch<PMF_PREC_TF32><<<k, kThreads, kSmemBytes, s>>>(slots, items);
+    k_fused2d_batch<PMF_PREC_TF32><<<k, kThreads, kSmemBytes, s>>>(slots, items, tcs);
   return 1;
 }
 

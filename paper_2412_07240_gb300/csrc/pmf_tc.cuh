@@ -34,6 +34,17 @@ struct StepItem {
   double z[PMF_MAX_NZ];
 };
 
+// Resident description of one 1-D filter (device memory).
+struct Slot1 {
+  DevState* st;
+  float* buf0;
+  float* buf1;
+  const float* tab;         // cas(2 pi r / N), r < N, then (cos, sin)(pi m / N), m = -N..N
+  int N;
+  const MeasParams* mp;
+  const TimeConsts* tc;
+};
+
 // PMF_OK if the fused kernel can hold this grid at this precision.
 int tc_supported(const pmf_config* cfg, std::string* why);
 int tc_build_tables(const pmf_config* cfg, TcTables* t, std::string* why);
@@ -50,12 +61,23 @@ int tc_step(const Dims& d, const pmf_config& cfg, const TcTables* t, const MeasP
 
 // 3-D grids (pmf_tc3.cu): per-context device state, and one epoch.
 int tc3_alloc(void** handle);
+size_t tc3_state_bytes();   // device bytes one tc3_alloc holds
 void tc3_free(void* handle);
 int tc3_step(void* handle, const Dims& d, const pmf_config& cfg, const TcTables* t, const MeasParams* mp,
              const TimeConsts* tcs, DevState* st, float* b0, float* b1, cudaStream_t s);
 
-// One launch, one CTA per item (items in device memory); returns launches.
-int tc_batch_step(int precision, const FilterSlot* slots, const StepItem* items, int k, cudaStream_t s);
+// One launch, one CTA per item (items in device memory); tcs (if not null)
+// holds each item's time-update constants in place of the slot's; returns launches.
+int tc_batch_step(int precision, const FilterSlot* slots, const StepItem* items, int k, cudaStream_t s,
+                  const TimeConsts* tcs = nullptr);
+
+// 1-D grids (pmf_tc1.cu): CUDA-core kernel, N a multiple of 8 in [16, 512].
+int tc1_supported(const pmf_config* cfg, std::string* why);
+size_t tc1_table_bytes(int N);
+int tc1_build_table(int N, void** dev);
+int tc1_step(int N, const void* table, const MeasParams* mp, const TimeConsts* tc, DevState* st, float* b0,
+             float* b1, cudaStream_t s);
+int tc1_batch_step(const Slot1* slots, const StepItem* items, const TimeConsts* tcs, int k, cudaStream_t s);
 // {mean[2], cov[4], status, 0} of filters ids[0..k) into out (8 doubles each),
 // then their status words cleared; returns the number of launches.
 int tc_batch_gather(DevState* st, const int* ids, int k, double* out, cudaStream_t s);

@@ -612,6 +612,7 @@ __global__ void __launch_bounds__(kT, 1) k_lines_axis0(const __grid_constant__ J
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ Smem3 sh;
   __shared__ int lk1[128], lk2[128];
+  __shared__ unsigned char lwr[128];   // line written back (the first copy of a self-mirrored line)
   __shared__ float spa[MAXL][3], spb[MAXL][3];
   uint8_t* A = smem + kOffA;
   uint8_t* W = smem + kOffW;
@@ -632,6 +633,9 @@ __global__ void __launch_bounds__(kT, 1) k_lines_axis0(const __grid_constant__ J
     const int c = cbeg + i;
     lk1[L] = kk1;
     lk2[L] = i < nc ? (mir ? (N2 - c) % N2 : c) : -1;
+    // k1 = -k1 (0, N1/2) or k2 = -k2 (0, N2/2): the tile holds the line twice;
+    // the two copies agree only up to rounding, so one of them is written back
+    lwr[L] = i < nc && !(s1 && kk1 == k1) && !(mir && (N2 - c) % N2 == c);
   }
   Pipe p;
   pipe_init(sh, p);
@@ -750,8 +754,8 @@ __global__ void __launch_bounds__(kT, 1) k_lines_axis0(const __grid_constant__ J
   {
     const int row = threadIdx.x & 127, cg = threadIdx.x >> 7;
     const int ncol = N0 / 4, c0 = cg * ncol;
-    const bool ok = lk2[row] >= 0;
-    float* dst = T + (size_t)lk1[row < 128 ? row : 0] * N2 + (ok ? lk2[row] : 0);
+    const bool ok = lwr[row] != 0;
+    float* dst = T + (size_t)lk1[row] * N2 + (ok ? lk2[row] : 0);
     for (int c = 0; c < ncol; c += 4) {
       const float4 v = tmem_ld4(p.tlane + c0 + c);
       if (ok) {
@@ -918,6 +922,10 @@ int tc3_alloc(void** handle) {
   }
   *handle = s;
   return PMF_OK;
+}
+
+size_t tc3_state_bytes() {
+  return sizeof(Update3) + 32 * sizeof(double) + 16 * 4096 * sizeof(DF) + sizeof(unsigned int);
 }
 
 void tc3_free(void* handle) {

@@ -268,13 +268,16 @@ __device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t a_base, int 
 
 // Row parameters of the separable regrid along one axis (float64 per row):
 // y_n = rs + rd u_n, z_n = y_n + (N-1)/2 = i_n + f_n with |f_n| <= 1/2.
-struct RegridRows {
-  int ri[128];
-  float rf[128], rS[128], rcf[128], rsf[128];
-  unsigned char rzero[128];
+template <int R>
+struct RegridRowsT {
+  int ri[R];
+  float rf[R], rS[R], rcf[R], rsf[R];
+  unsigned char rzero[R];
 };
+using RegridRows = RegridRowsT<128>;
 
-__device__ void regrid_rows(RegridRows& sh, double rs, double rd, int N, int t0, int tstep) {
+template <int R>
+__device__ void regrid_rows(RegridRowsT<R>& sh, double rs, double rd, int N, int t0, int tstep) {
   for (int n = t0; n < N; n += tstep) {
     const double y = rs + rd * (n - 0.5 * (N - 1));
     const double z = y + 0.5 * (N - 1);
@@ -291,11 +294,26 @@ __device__ void regrid_rows(RegridRows& sh, double rs, double rd, int N, int t0,
   }
 }
 
-// Periodic-sinc regrid matrix of one axis into the W planes (rows: new nodes,
-// columns: old nodes), scaled by sw:
-// I[n, j] = sin(pi v) / (N tan(pi v / N)), v = y_n - u_j = m + f_n, m = i_n - j,
-// evaluated as (-1)^m sin(pi f) cos(pi v/N) / (N sin(pi v/N)) with the angle
-// pi v / N split into the tabulated pi m / N and the per-row pi f / N.
+// Entry (n, j) of the periodic-sinc regrid matrix (rows: new nodes, columns:
+// old nodes): I[n, j] = sin(pi v) / (N tan(pi v / N)), v = y_n - u_j = m + f_n,
+// m = i_n - j, evaluated as (-1)^m sin(pi f) cos(pi v/N) / (N sin(pi v/N)) with
+// the angle pi v / N split into the tabulated pi m / N (sctab: (cos, sin) for
+// m = -N..N) and the per-row pi f / N.  Rows of new nodes outside the old box
+// are zero.
+template <int R>
+__device__ __forceinline__ float interp_entry(const RegridRowsT<R>& sh, int n, int j, int N, const float* sctab) {
+  if (sh.rzero[n]) return 0.0f;
+  const int m = sh.ri[n] - j;
+  const float f = sh.rf[n];
+  if (m == 0 && f == 0.0f) return 1.0f;
+  const float cm = sctab[2 * (m + N)], sm = sctab[2 * (m + N) + 1];
+  const float sv = sm * sh.rcf[n] + cm * sh.rsf[n];
+  const float cv = cm * sh.rcf[n] - sm * sh.rsf[n];
+  return __fdividef(((m & 1) ? -1.0f : 1.0f) * sh.rS[n] * cv, (float)N * sv);
+}
+
+// The regrid matrix of one axis into the W planes, scaled by sw (identity
+// when the frame was re-aligned: the gather already moved the weights).
 template <int P>
 __device__ void build_interp(const RegridRows& sh, uint8_t* W, int N, const float* sctab, float sw, int realign,
                              int t0, int tstep) {
@@ -306,24 +324,7 @@ __device__ void build_interp(const RegridRows& sh, uint8_t* W, int N, const floa
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int j = c + i;
-      float v;
-      if (realign) {
-        v = n == j ? 1.0f : 0.0f;
-      } else if (sh.rzero[n]) {
-        v = 0.0f;
-      } else {
-        const int m = sh.ri[n] - j;
-        const float f = sh.rf[n];
-        if (m == 0 && f == 0.0f) {
-          v = 1.0f;
-        } else {
-          const float cm = sctab[2 * (m + N)], sm = sctab[2 * (m + N) + 1];
-          const float sv = sm * sh.rcf[n] + cm * sh.rsf[n];
-          const float cv = cm * sh.rcf[n] - sm * sh.rsf[n];
-          v = __fdividef(((m & 1) ? -1.0f : 1.0f) * sh.rS[n] * cv, (float)N * sv);
-        }
-      }
-      k[i] = v;
+      k[i] = realign ? (n == j ? 1.0f : 0.0f) : interp_entry(sh, n, j, N, sctab);
     }
     store4<P>(W, n, c, make_float4(k[0], k[1], k[2], k[3]), sw);
   }

@@ -1,0 +1,48 @@
+"""1-D CUDA-core kernel (n_x = 1, float32) against the float64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import workloads as w
+from tests._parity import max_errors
+
+pytestmark = pytest.mark.gpu
+
+BAR = 1e-5   # relative L1 of the weights, float32 path
+
+
+def test_c1_all_epochs_fused_step():
+    sc = w.c1_scenario()
+    worst, log = max_errors(sc, precision="fp16x3", fused_step=True)
+    assert worst["l1"] < BAR, log
+    assert worst["mean"] < BAR and worst["cov"] < 10 * BAR, worst
+
+
+def test_c1_separate_updates_and_path():
+    from paper_2412_07240_gb300 import Filter
+    sc = w.c1_scenario()
+    f = Filter(sc.cfg, precision="fp16x3")
+    assert f.path == 3
+    f.close()
+    worst, log = max_errors(sc, precision="fp16x3", epochs=8)
+    assert worst["l1"] < BAR, log
+
+
+@pytest.mark.parametrize("N", [16, 200, 512])
+def test_grid_sizes(N):
+    # ragged (200 = 8 * 25) and the largest supported grid, a few epochs
+    sc = w.c1_scenario(N=N, epochs=6)
+    worst, log = max_errors(sc, precision="fp16x3", fused_step=True)
+    assert worst["l1"] < BAR, log
+
+
+def test_exact_multiplier():
+    sc = w.c1_scenario(epochs=6)
+    worst, log = max_errors(sc, precision="fp16x3", fused_step=True, psi_mode="exact")
+    assert worst["l1"] < BAR, log
+
+
+def test_unsupported_size_rejected():
+    from paper_2412_07240_gb300 import Filter, Unsupported
+    sc = w.c1_scenario(N=1000)
+    with pytest.raises(Unsupported):
+        Filter(sc.cfg, precision="fp16x3")

@@ -1,0 +1,120 @@
+"""The request server: continuous batching of mixed 1-D / 2-D / 3-D filters.
+
+Each filter's results through the server equal those of the same filter
+served alone and of the single-filter API, and match the float64 oracle."""
+import numpy as np
+import pytest
+
+import workloads as w
+from tests._parity import rel_l1
+
+pytestmark = pytest.mark.gpu
+
+
+def _small_workload(seed=7, duration=0.25, rate=8000.0):
+    return w.c5_serving(n_filters=40, rate=rate, duration=duration, seed=seed, n1=(16, 96), n2=(16, 48),
+                        n3=(16, 32))
+
+
+def _server(wl, ids=None, budget=0):
+    from paper_2412_07240_gb300 import Server
+    s = Server(max_filters=len(wl.cfgs), hbm_budget=budget)
+    ids = range(len(wl.cfgs)) if ids is None else ids
+    fid = {i: s.admit(wl.cfgs[i], wl.meas[i]) for i in ids}
+    return s, fid
+
+
+def test_alone_equals_in_the_mix():
+    wl = _small_workload()
+    s, fid = _server(wl)
+    lat, st = s.replay(wl.t_arrival, [fid[i] for i in wl.ids], wl.z, wl.taus)
+    assert st["requests"] == wl.ids.size and np.all(lat >= 0)
+    assert st["max_batch"] > 1   # requests shared batches
+    for nx in (1, 2, 3):
+        f = next(i for i, c in enumerate(wl.cfgs) if c.nx == nx and (wl.ids == i).sum() > 2)
+        P_mix, c_mix, M_mix = s.pdf(fid[f])
+        sel = wl.ids == f
+        alone, afid = _server(wl, ids=[f])
+        alone.replay(wl.t_arrival[sel], np.full(sel.sum(), afid[f]), wl.z[sel], wl.taus[sel])
+        P_one, c_one, M_one = alone.pdf(afid[f])
+        assert rel_l1(P_mix, P_one) <= 1e-6, nx
+        assert np.array_equal(c_mix, c_one) and np.array_equal(M_mix, M_one), nx
+        alone.close()
+    s.close()
+
+
+def test_server_matches_single_filter_api():
+    from paper_2412_07240_gb300 import Filter
+    wl = _small_workload(seed=8)
+    s, fid = _server(wl)
+    s.replay(wl.t_arrival, [fid[i] for i in wl.ids], wl.z, wl.taus)
+    for nx in (1, 2, 3):
+        f = next(i for i, c in enumerate(wl.cfgs) if c.nx == nx and (wl.ids == i).sum() > 2)
+        sel = np.nonzero(wl.ids == f)[0]
+        assert np.all(wl.taus[sel] <= 0.64)   # one time update per request
+        g = Filter(wl.cfgs[f], precision="fp16x3")
+        for r in sel:
+            g.step(wl.meas[f], wl.z[r, :nx], wl.taus[r])
+        P1, c1, M1 = g.pdf()
+        P2, c2, M2 = s.pdf(fid[f])
+        assert rel_l1(P2, P1) <= 1e-6, nx
+        g.close()
+    s.close()
+
+
+def test_server_against_oracle():
+    from oracle.filter import OracleFilter
+    wl = _small_workload(seed=9, duration=0.1)
+    s, fid = _server(wl)
+    s.replay(wl.t_arrival, [fid[i] for i in wl.ids], wl.z, wl.taus)
+    for nx in (1, 2):
+        f = next(i for i, c in enumerate(wl.cfgs) if c.nx == nx and (wl.ids == i).sum() > 1)
+        o = OracleFilter(wl.cfgs[f])
+        for r in np.nonzero(wl.ids == f)[0]:
+            o.meas_update(wl.meas[f], wl.z[r, :nx])
+            o.time_update(wl.taus[r])
+        P, c, M = s.pdf(fid[f])
+        assert rel_l1(P, o.P) < 1e-5, nx
+    s.close()
+
+
+def test_long_horizon_split_into_time_updates():
+    # tau above PMF_MAX_SUBSTEPS * dt_sub runs as consecutive time updates
+    from oracle.filter import OracleFilter
+    from paper_2412_07240_gb300 import Server
+    sc = w.c1_scenario(epochs=3)
+    s = Server(max_filters=1)
+    fid = s.admit(sc.cfg, sc.meas)
+    taus = np.array([0.9, 0.3, 1.5])
+    s.replay(np.zeros(3), [fid] * 3, sc.z[:3], taus)
+    o = OracleFilter(sc.cfg)
+    for k in range(3):
+        o.meas_update(sc.meas, sc.z[k])
+        left = taus[k]
+        while left > 0:   # the same chunks: at most 64 sub-steps of 0.01
+            t = min(left, 0.64 * (1 - 1e-12))
+            o.time_update(t)
+            left -= t
+            if left < 1e-12 * 0.64:
+                left = 0.0
+    P, c, M = s.pdf(fid)
+    assert rel_l1(P, o.P) < 1e-5
+    s.close()
+
+
+def test_admission_budget_and_eviction():
+    from paper_2412_07240_gb300 import PmfError, Server
+    from paper_2412_07240_gb300._binding import ERR_ADMISSION
+    wl = _small_workload()
+    s = Server(max_filters=len(wl.cfgs), hbm_budget=1 << 20)
+    admitted = []
+    with pytest.raises(PmfError) as e:
+        for i in range(len(wl.cfgs)):
+            admitted.append(s.admit(wl.cfgs[i], wl.meas[i]))
+    assert e.value.code == ERR_ADMISSION
+    assert admitted and s.bytes <= 1 << 20
+    before = s.bytes
+    s.evict(admitted[0])
+    assert s.bytes < before
+    s.admit(wl.cfgs[0], wl.meas[0])
+    s.close()

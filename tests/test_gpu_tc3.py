@@ -57,3 +57,20 @@ def test_far_measurement_tiny_slices_fp16x3():
     sc.z = np.array([[-0.386, -0.368, -1.032], [-0.5, -0.4, -1.1]])
     worst, _ = max_errors(sc, precision="fp16x3")
     _check(worst)
+
+
+def test_repeatable_bitwise():
+    # two filters fed the same inputs agree bit for bit (self-mirrored
+    # frequency lines are written back once, by one thread)
+    from paper_2412_07240_gb300 import Filter
+    wl = w.c5_serving(n_filters=40, rate=8000.0, duration=0.05, seed=7, n1=(16, 96), n2=(16, 48), n3=(16, 32))
+    f = next(i for i, c in enumerate(wl.cfgs) if c.nx == 3)
+    outs = []
+    for _ in range(2):
+        g = Filter(wl.cfgs[f], precision="fp16x3")
+        for k in range(3):
+            g.step(wl.meas[f], wl.z[k, :3] * 0 + wl.cfgs[f].m0, 0.1)
+        outs.append(g.pdf())
+        g.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1]) and np.array_equal(outs[0][2], outs[1][2])

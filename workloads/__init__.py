@@ -7,7 +7,7 @@ CUDA path (through the C-ABI binding) and the FP64 oracle can take their
 inputs from it without sharing any code of the method.
 """
 from .configs import (  # noqa: F401
-    FilterConfig, MeasModel, Scenario,
-    c1_scenario, c2_scenario, c3_scenario, c4_batch, small_2d_scenario,
+    FilterConfig, MeasModel, Scenario, ServingWorkload,
+    c1_scenario, c5_serving, c2_scenario, c3_scenario, c4_batch, small_2d_scenario,
     small_3d_scenario, random_stable_matrix, simulate,
 )

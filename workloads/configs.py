@@ -229,3 +229,115 @@ def c4_batch(count: int = 4096, seed: int = 4, epochs: int = 100,
         truth[:, k] = x
         z[:, k] = x + 0.1 * rng.standard_normal((count, 2))
     return cfgs, meas, dt, truth, z
+
+
+def _expm_batch(X: np.ndarray) -> np.ndarray:
+    """Matrix exponentials of a stack (k, m, m): Taylor series after scaling
+    by 2^-s (1-norm <= 1/4), then s squarings (input simulation only)."""
+    k, m, _ = X.shape
+    if k == 0:
+        return X.copy()
+    nrm = np.abs(X).sum(axis=1).max(axis=1)
+    s = np.maximum(0, np.ceil(np.log2(np.maximum(nrm, 1e-300) / 0.25))).astype(int)
+    Y = X / (2.0 ** s)[:, None, None]
+    E = np.broadcast_to(np.eye(m), X.shape).copy()
+    T = E.copy()
+    for j in range(1, 19):
+        T = T @ Y / j
+        E = E + T
+    for j in range(int(s.max())):
+        sel = s > j
+        E[sel] = E[sel] @ E[sel]
+    return E
+
+
+@dataclass
+class ServingWorkload:
+    """Resident filters and a request log replayed in real time.
+
+    Request i arrives at t_arrival[i] (seconds, ascending) for filter ids[i]:
+    measurement z[i] (nx values, zero-padded to 3) of the filter's truth at its
+    current model time, then a time update over taus[i], the time to the
+    filter's next measurement.
+    """
+    cfgs: list
+    meas: list
+    t_arrival: np.ndarray
+    ids: np.ndarray
+    z: np.ndarray
+    taus: np.ndarray
+    truth: list = field(default_factory=list)
+
+
+def c5_serving(n_filters: int = 10000, rate: float = 200e3, duration: float = 60.0, seed: int = 5,
+               frac=(0.6, 0.35, 0.05), n1=(64, 512), n2=(32, 128), n3=(32, 64),
+               tau_mean: float = 0.1) -> ServingWorkload:
+    """C5: 60% n_x = 1 filters with N in [64, 512] (multiples of 8), 35% n_x = 2
+    with each axis in [32, 128] (multiples of 16, the tensor-core tile), 5%
+    n_x = 3 with each axis in [32, 64] (multiples of 16); each with its own
+    seeded stable A, diagonal Q in [0.05, 0.5], prior N(m0 ~ N(0, I), 0.25 I)
+    and z = x + v, R = 0.1^2 I.  Requests arrive as a Poisson process of the
+    given aggregate rate for ``duration`` seconds, each for a uniformly drawn
+    filter, with the time to that filter's next measurement drawn from an
+    exponential distribution of mean ``tau_mean``.  The truth advances by the
+    exact discretisation x <- e^{A tau} x + w, w ~ N(0, Q_d(tau)).
+    """
+    rng = np.random.default_rng(seed)
+    counts = [int(round(frac[0] * n_filters)), int(round(frac[1] * n_filters))]
+    counts.append(n_filters - counts[0] - counts[1])
+    grids = {1: np.arange(n1[0], n1[1] + 1, 8), 2: np.arange(n2[0], n2[1] + 1, 16),
+             3: np.arange(n3[0], n3[1] + 1, 16)}
+    cfgs, meas = [], []
+    for nx, cnt in zip((1, 2, 3), counts):
+        for _ in range(cnt):
+            if nx == 1:
+                A = np.array([[rng.uniform(-1.0, -0.1)]])
+            else:
+                A = random_stable_matrix(nx, rng, complex_pairs=(nx == 2))
+            Q = np.diag(rng.uniform(0.05, 0.5, size=nx))
+            N = tuple(int(v) for v in rng.choice(grids[nx], size=nx))
+            cfgs.append(FilterConfig(nx=nx, N=N, A=A, Q=Q, m0=rng.standard_normal(nx), P0=0.25 * np.eye(nx)))
+            meas.append(MeasModel("linear", R=0.1 ** 2 * np.eye(nx), H=np.eye(nx)))
+    n_req = int(rng.poisson(rate * duration))
+    t_arrival = np.sort(rng.uniform(0.0, duration, size=n_req))
+    ids = rng.integers(0, n_filters, size=n_req).astype(np.int32)
+    taus = rng.exponential(tau_mean, size=n_req)
+    z = np.zeros((n_req, 3))
+    # truth per filter, advanced request by request ("round" k = k-th request of each filter)
+    order = np.argsort(ids, kind="stable")
+    first = np.searchsorted(ids[order], np.arange(n_filters))
+    rank = np.empty(n_req, dtype=np.int64)
+    rank[order] = np.arange(n_req) - first[ids[order]]
+    nxs = np.array([c.nx for c in cfgs])
+    x = [cfgs[f].m0 + 0.5 * rng.standard_normal(cfgs[f].nx) for f in range(n_filters)]
+    X = {d: np.array([x[f] for f in range(n_filters) if nxs[f] == d]).reshape(-1, d) for d in (1, 2, 3)}
+    pos = np.zeros(n_filters, dtype=np.int64)
+    for d in (1, 2, 3):
+        pos[nxs == d] = np.arange((nxs == d).sum())
+    As = {d: np.array([cfgs[f].A for f in range(n_filters) if nxs[f] == d]).reshape(-1, d, d) for d in (1, 2, 3)}
+    Qs = {d: np.array([cfgs[f].Q for f in range(n_filters) if nxs[f] == d]).reshape(-1, d, d) for d in (1, 2, 3)}
+    by_rank = np.argsort(rank, kind="stable")
+    bounds = np.searchsorted(rank[by_rank], np.arange(int(rank.max(initial=-1)) + 2))
+    for k in range(len(bounds) - 1):
+        req = by_rank[bounds[k]:bounds[k + 1]]
+        for d in (1, 2, 3):
+            r = req[nxs[ids[req]] == d]
+            if r.size == 0:
+                continue
+            p = pos[ids[r]]
+            z[r, :d] = X[d][p] + 0.1 * rng.standard_normal((r.size, d))
+            A = As[d][p]
+            tau = taus[r][:, None, None]
+            m = 2 * d
+            C = np.zeros((r.size, m, m))
+            C[:, :d, :d] = -A * tau
+            C[:, :d, d:] = Qs[d][p] * tau
+            C[:, d:, d:] = np.transpose(A, (0, 2, 1)) * tau
+            E = _expm_batch(C)
+            Phi = np.transpose(E[:, d:, d:], (0, 2, 1))
+            Qd = Phi @ E[:, :d, d:]
+            Qd = 0.5 * (Qd + np.transpose(Qd, (0, 2, 1)))
+            w, V = np.linalg.eigh(Qd)
+            L = V * np.sqrt(np.maximum(w, 0.0))[:, None, :]
+            X[d][p] = np.einsum("kij,kj->ki", Phi, X[d][p]) + np.einsum("kij,kj->ki", L, rng.standard_normal((r.size, d)))
+    return ServingWorkload(cfgs, meas, t_arrival, ids, z, taus)
