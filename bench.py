@@ -336,6 +336,76 @@ def bench_batch(args, ws, rank, pg):
         print(json.dumps(line))
 
 
+def bench_serve(args, ws, rank, pg):
+    """The serving workload: 10k resident filters of mixed dimension, a Poisson
+    request log replayed in real time through the request server."""
+    import numpy as np
+    import torch
+    import workloads as w
+    from paper_2412_07240_gb300 import Filter, Server
+    n = args.count if args.count != 4096 else 10000
+    warm = 0.5
+    wl = w.c5_serving(n_filters=n, rate=args.rate, duration=args.duration + warm, seed=5 + rank)
+    P = np.array([int(np.prod(c.N)) for c in wl.cfgs], dtype=np.int64)
+    srv = Server(max_filters=n, precision=args.precision, hbm_budget=int(120e9))
+    t0 = time.perf_counter()
+    fid = np.array([srv.admit(c, m) for c, m in zip(wl.cfgs, wl.meas)], dtype=np.int32)
+    admit_s = time.perf_counter() - t0
+    ids = fid[wl.ids]
+    k = int(np.searchsorted(wl.t_arrival, warm))
+    srv.replay(wl.t_arrival[:k], ids[:k], wl.z[:k], wl.taus[:k])          # warm-up requests
+    sel = slice(k, None)
+    _barrier(pg)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        lat, st = srv.replay(wl.t_arrival[sel] - warm, ids[sel], wl.z[sel], wl.taus[sel])
+    wall = _max_over_ranks(pg, st["wall_s"] * 1e3) * 1e-3
+    pts = float(P[wl.ids[sel]].sum())
+    value = ws * pts / wall
+    # plain float64 per-filter path on a sample of each dimension
+    rng = np.random.default_rng(0)
+    f64_pts, f64_s = 0.0, 0.0
+    for d in (1, 2, 3):
+        cand = [i for i, c in enumerate(wl.cfgs) if c.nx == d]
+        for i in rng.choice(cand, size=min(len(cand), 8 if d < 3 else 3), replace=False):
+            f = Filter(wl.cfgs[i], precision="fp64")
+            r = np.nonzero(wl.ids == i)[0][:3]
+            for q in r[:1]:
+                f.step(wl.meas[i], wl.z[q, :d], min(wl.taus[q], 0.6))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for q in r[1:]:
+                f.step(wl.meas[i], wl.z[q, :d], min(wl.taus[q], 0.6))
+            e1.record()
+            torch.cuda.synchronize()
+            f64_pts += P[i] * len(r[1:])
+            f64_s += e0.elapsed_time(e1) * 1e-3
+            f.close()
+    nreq = int(st["requests"])
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": int(st["batches"]),
+            "warmup": k, "ms_per_step": wall * 1e3 / max(1.0, st["batches"]), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": f"f32 ({args.precision} split GEMMs, 1-D float32)",
+            "data": "synthetic (seeded filters, Poisson arrivals, exact-discretisation truth)",
+            "config": {"workload": f"c5_serving_{n}_mixed", "rate_per_s": args.rate, "duration_s": args.duration,
+                       "filters": n, "resident_points": int(P.sum()), "resident_bytes": srv.bytes,
+                       "hbm_budget": int(120e9), "admission_s": admit_s, "precision": args.precision,
+                       "parallelism": f"replicas x{ws}"},
+            "requests_per_s": ws * nreq / wall,
+            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                           "max": float(lat.max() * 1e3)},
+            "batches": {"count": int(st["batches"]), "mean": st["mean_batch"], "max": int(st["max_batch"])},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(st["mean_batch"] * (32 + 3600)),
+                    "d2h_bytes_per_step": 0, "note": "the replay is end to end: requests from host arrays"},
+            "gpu_launches": int(st["launches"]),
+            "fp64_gpu": {"value": f64_pts / f64_s if f64_s > 0 else None, "unit": UNIT,
+                         "sample": "8 1-D, 8 2-D, 3 3-D filters, plain float64 path, one update each"},
+            "roofline": None,
+            "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line))
+    srv.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,7 +415,9 @@ def main():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--precision", default="fp16x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--count", type=int, default=4096, help="filters of the c4 batch workload")
+    ap.add_argument("--count", type=int, default=4096, help="filters of the c4 batch workload (c5: 10000)")
+    ap.add_argument("--rate", type=float, default=200e3, help="c5: aggregate request rate per second")
+    ap.add_argument("--duration", type=float, default=60.0, help="c5: seconds of requests replayed")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     ws, rank, local, pg = _dist()
@@ -356,8 +428,8 @@ def main():
     import numpy as np
     import torch
     torch.cuda.set_device(local)
-    if args.workload == "c4":
-        bench_batch(args, ws, rank, pg)
+    if args.workload in ("c4", "c5"):
+        (bench_batch if args.workload == "c4" else bench_serve)(args, ws, rank, pg)
         if pg is not None:
             pg.destroy_process_group()
         return

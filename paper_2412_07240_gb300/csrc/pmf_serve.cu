@@ -133,6 +133,7 @@ struct Flight {
   TimeConsts* h_tc[2] = {nullptr, nullptr};
   StepItem* d_items[2] = {nullptr, nullptr};
   TimeConsts* d_tc[2] = {nullptr, nullptr};
+  Tc3Stage stage3{};                             // 3-D descriptors of this batch
   bool inflight = false;
 };
 
@@ -306,22 +307,31 @@ int launch_batch(pmf_server* s, const double* z, const double* taus) {
     cudaEventRecord(b.ev[k], s->s[k]);
     b.used[k] = true;
   }
-  // 3-D: the pipelines, one filter after another on the third stream
-  for (size_t i = 0; i < its.size(); ++i) {
-    const Item& it = its[i];
-    if (it.kind != 2) continue;
-    SFilter& f = s->f[it.id];
-    MeasParams mp = f.mp;
-    for (int j = 0; j < PMF_MAX_NZ; ++j) mp.z[j] = z[it.req * PMF_MAX_NZ + j];
-    Dims d{};
-    d.nx = 3;
-    d.P = f.P;
-    for (int a = 0; a < 3; ++a) d.N[a] = f.cfg.N[a];
-    s->launches += tc3_step(f.tc3, d, f.cfg, &f.tct, (it.flags & 1) ? &mp : nullptr,
-                            (it.flags & 2) ? &tc3[i] : nullptr, f.st, f.buf, f.buf + f.P, s->s[2]);
+  // 3-D: every stage of the pipelines one launch over all the batch's 3-D filters
+  if (count[2]) {
+    std::vector<MeasParams> mps(count[2]);
+    std::vector<Tc3Item> t3;
+    t3.reserve(count[2]);
+    for (size_t i = 0; i < its.size(); ++i) {
+      const Item& it = its[i];
+      if (it.kind != 2) continue;
+      SFilter& f = s->f[it.id];
+      MeasParams& mp = mps[t3.size()];
+      mp = f.mp;
+      for (int j = 0; j < PMF_MAX_NZ; ++j) mp.z[j] = z[it.req * PMF_MAX_NZ + j];
+      Dims d{};
+      d.nx = 3;
+      d.P = f.P;
+      for (int a = 0; a < 3; ++a) d.N[a] = f.cfg.N[a];
+      t3.push_back(Tc3Item{f.tc3, d, &f.tct, (it.flags & 1) ? &mp : nullptr, (it.flags & 2) ? &tc3[i] : nullptr,
+                           f.st, f.buf, f.buf + f.P});
+    }
+    const int r = tc3_batch(t3.data(), (int)t3.size(), s->precision, &b.stage3, s->s[2]);
+    if (r < 0) return sfail(s, -r, "3-D batch");
+    s->launches += r;
+    cudaEventRecord(b.ev[2], s->s[2]);
     b.used[2] = true;
   }
-  if (b.used[2]) cudaEventRecord(b.ev[2], s->s[2]);
   if (cudaGetLastError() != cudaSuccess) return sfail(s, PMF_ERR_CUDA, "batch launch");
   b.inflight = true;
   s->head = (s->head + 1) % kInflight;
@@ -613,6 +623,7 @@ void pmf_server_destroy(pmf_server* s) {
   for (auto& b : s->ring) {
     for (int k = 0; k < 3; ++k)
       if (b.ev[k]) cudaEventDestroy(b.ev[k]);
+    tc3_stage_free(&b.stage3);
     for (int k = 0; k < 2; ++k) {
       cudaFreeHost(b.h_items[k]);
       cudaFreeHost(b.h_tc[k]);

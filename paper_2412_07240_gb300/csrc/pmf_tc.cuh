@@ -59,12 +59,41 @@ int tc_prior(const Dims& d, DevState* st, const double* prior_aux, float* X, dou
 int tc_step(const Dims& d, const pmf_config& cfg, const TcTables* t, const MeasParams* mp,
             const TimeConsts* tc, DevState* st, float* b0, float* b1, cudaStream_t s);
 
-// 3-D grids (pmf_tc3.cu): per-context device state, and one epoch.
+// 3-D grids (pmf_tc3.cu): per-filter device state (tc3_alloc) and epochs of
+// one or many filters, every stage one launch over all of them.
 int tc3_alloc(void** handle);
 size_t tc3_state_bytes();   // device bytes one tc3_alloc holds
 void tc3_free(void* handle);
 int tc3_step(void* handle, const Dims& d, const pmf_config& cfg, const TcTables* t, const MeasParams* mp,
              const TimeConsts* tcs, DevState* st, float* b0, float* b1, cudaStream_t s);
+
+// One filter's epoch in a batched 3-D launch sequence (mp / tc null: no
+// measurement / time update); host structs are copied at the call.
+struct Tc3Item {
+  void* handle;             // tc3_alloc state of the filter
+  Dims d;
+  const TcTables* t;
+  const MeasParams* mp;
+  const TimeConsts* tc;
+  DevState* st;
+  float* b0;
+  float* b1;
+};
+// Pinned and device staging of the per-filter descriptors of one sequence;
+// reserve waits for the previous sequence's copies from it.
+struct Tc3Stage {
+  void* h_jobs;
+  int* h_first;
+  void* d_jobs;
+  int* d_first;
+  int cap;
+  cudaEvent_t ev;
+};
+int tc3_stage_reserve(Tc3Stage* g, int n);
+void tc3_stage_free(Tc3Stage* g);
+// Launches the sequence for items[0..n) on stream s; returns the number of
+// launches, or minus a PMF_ERR_* code.
+int tc3_batch(const Tc3Item* items, int n, int precision, Tc3Stage* g, cudaStream_t s);
 
 // One launch, one CTA per item (items in device memory); tcs (if not null)
 // holds each item's time-update constants in place of the slot's; returns launches.

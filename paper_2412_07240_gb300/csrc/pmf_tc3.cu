@@ -60,7 +60,44 @@ struct Job3 {
   Update3* up;               // device
   double* pend;              // pending frame (device)
   int precision;
+  int flags;                 // this epoch: bit 0 measurement update, bit 1 time update
+  int chunks;                // axis-0 line tiles: chunks of 32 k2 per k1
+  int mblocks;               // CTAs of the measurement kernels
+  MeasParams mp;             // measurement of this epoch (z filled)
+  TimeConsts tc;             // constants of this epoch's time update
 };
+
+// One batched launch sequence: jobs and, per kernel kind, the first CTA of
+// each job (n + 1 entries per kind; a job may own no CTA of a kind).
+enum { kKindMeas = 0, kKindPoints = 1, kKindSlices = 2, kKindLines = 3, kKinds = 4 };
+struct Batch3 {
+  const Job3* jobs;
+  const int* first;          // [kind * (n + 1) + j]
+  int n;
+  Job3 one;                  // n == 1: the job itself, in the kernel parameters
+};
+
+__device__ __forceinline__ const Job3& job_at(const Batch3& b, int j) { return b.n == 1 ? b.one : b.jobs[j]; }
+
+// Job owning CTA blk of a kind (largest j with first[j] <= blk), the CTA's
+// index within the job and the job's CTA count.
+__device__ __forceinline__ int find_job(const Batch3& b, int kind, int blk, int* local, int* count) {
+  if (b.n == 1) {
+    *local = blk;
+    *count = gridDim.x;
+    return 0;
+  }
+  const int* f = b.first + kind * (b.n + 1);
+  int lo = 0, hi = b.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (f[mid] <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  *local = blk - f[lo];
+  *count = f[lo + 1] - f[lo];
+  return lo;
+}
 
 struct Smem3 {
   uint64_t mbar_mma, mbar_tma;
@@ -308,15 +345,17 @@ __device__ __forceinline__ void unflat3(const Geo3& g, long long p, int* j) {
   j[0] = (int)(p / g.N[1]);
 }
 
-__global__ void __launch_bounds__(kT) k_meas_min3(const __grid_constant__ Job3 job,
-                                                  const __grid_constant__ MeasParams mp) {
+__global__ void __launch_bounds__(kT) k_meas_min3(const __grid_constant__ Batch3 b) {
   __shared__ Meas3 m;
   __shared__ float red[kT / 32];
+  int blk, cnt;
+  const Job3& job = job_at(b, find_job(b, kKindMeas, blockIdx.x, &blk, &cnt));
+  const MeasParams& mp = job.mp;
   if (threadIdx.x == 0) meas_consts(mp, job.st->f, m);
   __syncthreads();
   const Geo3& g = job.g;
   float e = INFINITY;
-  for (long long q = blockIdx.x * (long long)kT + threadIdx.x; q < g.P / 4; q += (long long)gridDim.x * kT) {
+  for (long long q = blk * (long long)kT + threadIdx.x; q < g.P / 4; q += (long long)cnt * kT) {
     int j[3];
     unflat3(g, q * 4, j);
     const float u0 = j[0] - 0.5f * (g.N[0] - 1), u1 = j[1] - 0.5f * (g.N[1] - 1), u2 = j[2] - 0.5f * (g.N[2] - 1);
@@ -333,10 +372,12 @@ __global__ void __launch_bounds__(kT) k_meas_min3(const __grid_constant__ Job3 j
 }
 
 // Likelihood multiply (into the other buffer) and moment partials per CTA.
-__global__ void __launch_bounds__(kT) k_meas_apply3(const __grid_constant__ Job3 job,
-                                                    const __grid_constant__ MeasParams mp) {
+__global__ void __launch_bounds__(kT) k_meas_apply3(const __grid_constant__ Batch3 b) {
   __shared__ Meas3 m;
   __shared__ Smem3 sh;
+  int blk, cnt;
+  const Job3& job = job_at(b, find_job(b, kKindMeas, blockIdx.x, &blk, &cnt));
+  const MeasParams& mp = job.mp;
   if (threadIdx.x == 0) meas_consts(mp, job.st->f, m);
   __syncthreads();
   const Geo3& g = job.g;
@@ -347,7 +388,7 @@ __global__ void __launch_bounds__(kT) k_meas_apply3(const __grid_constant__ Job3
   const float emin = __uint_as_float(*job.emin_bits);
   DF s[6], s2[6];
   for (int i = 0; i < 6; ++i) s[i] = s2[i] = DF{0.0f, 0.0f};
-  for (long long q = blockIdx.x * (long long)kT + threadIdx.x; q < g.P / 4; q += (long long)gridDim.x * kT) {
+  for (long long q = blk * (long long)kT + threadIdx.x; q < g.P / 4; q += (long long)cnt * kT) {
     int j[3];
     unflat3(g, q * 4, j);
     const float u0 = j[0] - 0.5f * (g.N[0] - 1), u1 = j[1] - 0.5f * (g.N[1] - 1), u2 = j[2] - 0.5f * (g.N[2] - 1);
@@ -373,9 +414,9 @@ __global__ void __launch_bounds__(kT) k_meas_apply3(const __grid_constant__ Job3
     s2[2] = df_add1(s2[2], b2 * u1);                               // S2_12
     s2[3] = df_add1(s2[3], fmaf(u2, fmaf(u2, a0, 2.0f * a1), a2)); // S2_22
   }
-  block_partials3(sh, s, job.partials + (size_t)blockIdx.x * 16);
+  block_partials3(sh, s, job.partials + (size_t)blk * 16);
   __syncthreads();
-  block_partials3(sh, s2, job.partials + (size_t)blockIdx.x * 16 + 6);
+  block_partials3(sh, s2, job.partials + (size_t)blk * 16 + 6);
 }
 
 // Sum the per-CTA partials (16 double-float slots each: S0, S1[0..2], S2_00,
@@ -421,9 +462,11 @@ __device__ void sum_partials3(const DF* part, int nb, double* tot, DF (*red)[10]
 
 // Moments after the measurement update; then (time update) the frame, the
 // sub-step coefficients and the regrid rows of all axes.
-__global__ void __launch_bounds__(kT) k_frame3(const __grid_constant__ Job3 job,
-                                               const __grid_constant__ TimeConsts tc, int nb, int do_meas,
-                                               int do_time) {
+__global__ void __launch_bounds__(kT) k_frame3(const __grid_constant__ Batch3 b) {
+  const Job3& job = job_at(b, blockIdx.x);
+  const TimeConsts& tc = job.tc;
+  const int nb = (job.flags & 1) ? job.mblocks : 0;
+  const int do_meas = job.flags & 1, do_time = (job.flags >> 1) & 1;
   __shared__ FrameState fs;
   __shared__ double tot[10];
   __shared__ DF red[kT / 32][10];
@@ -468,18 +511,21 @@ __global__ void __launch_bounds__(kT) k_frame3(const __grid_constant__ Job3 job,
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kW; i += kT) ((unsigned long long*)&st->f)[i] = ((const unsigned long long*)&fs)[i];
+  if (threadIdx.x == 0) *job.emin_bits = 0x7f7f7f7fu;   // re-armed for the next measurement update
 }
 
 // Multilinear re-alignment (only when the frame kernel decided it): gather
 // buf[cur] -> buf[cur^1] with pscale folded in; k_copy3 copies it back.
-__global__ void __launch_bounds__(kT) k_realign3(const __grid_constant__ Job3 job) {
+__global__ void __launch_bounds__(kT) k_realign3(const __grid_constant__ Batch3 b) {
+  int blk, cnt;
+  const Job3& job = job_at(b, find_job(b, kKindPoints, blockIdx.x, &blk, &cnt));
   const FrameState& f = job.st->f;
   if (job.up->skip || !job.up->realign) return;
   const Geo3& g = job.g;
   const float* in = f.cur ? job.buf1 : job.buf0;
   float* out = f.cur ? job.buf0 : job.buf1;
   const float ps = (float)f.pscale;
-  for (long long p = blockIdx.x * (long long)kT + threadIdx.x; p < g.P; p += (long long)gridDim.x * kT) {
+  for (long long p = blk * (long long)kT + threadIdx.x; p < g.P; p += (long long)cnt * kT) {
     int j[3];
     unflat3(g, p, j);
     double z[3];
@@ -510,12 +556,14 @@ __global__ void __launch_bounds__(kT) k_realign3(const __grid_constant__ Job3 jo
   }
 }
 
-__global__ void __launch_bounds__(kT) k_copy3(const __grid_constant__ Job3 job) {
+__global__ void __launch_bounds__(kT) k_copy3(const __grid_constant__ Batch3 b) {
+  int blk, cnt;
+  const Job3& job = job_at(b, find_job(b, kKindPoints, blockIdx.x, &blk, &cnt));
   const FrameState& f = job.st->f;
   if (job.up->skip || !job.up->realign) return;
   const float* src = f.cur ? job.buf0 : job.buf1;
   float* dst = f.cur ? job.buf1 : job.buf0;
-  for (long long p = blockIdx.x * (long long)kT + threadIdx.x; p < job.g.P; p += (long long)gridDim.x * kT)
+  for (long long p = blk * (long long)kT + threadIdx.x; p < job.g.P; p += (long long)cnt * kT)
     dst[p] = src[p];
 }
 
@@ -523,16 +571,18 @@ __global__ void __launch_bounds__(kT) k_copy3(const __grid_constant__ Job3 job) 
 // Slice j0 of buf[cur] (rows j1, columns j2) -> regrid + Hartley along axis 2,
 // then axis 1 -> T[j0][k1][k2] in buf[cur^1].
 template <int P>
-__global__ void __launch_bounds__(kT, 1) k_slices_fwd(const __grid_constant__ Job3 job) {
+__global__ void __launch_bounds__(kT, 1) k_slices_fwd(const __grid_constant__ Batch3 b) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ Smem3 sh;
+  int blk, cnt;
+  const Job3& job = job_at(b, find_job(b, kKindSlices, blockIdx.x, &blk, &cnt));
   uint8_t* A = smem + kOffA;
   uint8_t* W = smem + kOffW;
   float* S = (float*)(smem + kOffS);
   const FrameState& f = job.st->f;
   const Update3* up = job.up;
   const int N1 = job.g.N[1], N2 = job.g.N[2];
-  const int j0 = blockIdx.x;
+  const int j0 = blk;
   if (up->skip) return;
   const int realign = up->realign;
   const float* in = f.cur ? job.buf1 : job.buf0;
@@ -608,9 +658,12 @@ fail:
 // intersected with [0, N2/2]; line index s1 * 64 + i (k2 = C[i]) and
 // s1 * 64 + 32 + i (k2 = -C[i]).
 template <int P>
-__global__ void __launch_bounds__(kT, 1) k_lines_axis0(const __grid_constant__ Job3 job, int chunks) {
+__global__ void __launch_bounds__(kT, 1) k_lines_axis0(const __grid_constant__ Batch3 b) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ Smem3 sh;
+  int blk, cnt;
+  const Job3& job = job_at(b, find_job(b, kKindLines, blockIdx.x, &blk, &cnt));
+  const int chunks = job.chunks;
   __shared__ int lk1[128], lk2[128];
   __shared__ unsigned char lwr[128];   // line written back (the first copy of a self-mirrored line)
   __shared__ float spa[MAXL][3], spb[MAXL][3];
@@ -620,7 +673,7 @@ __global__ void __launch_bounds__(kT, 1) k_lines_axis0(const __grid_constant__ J
   const FrameState& f = job.st->f;
   const Update3* up = job.up;
   const int N0 = job.g.N[0], N1 = job.g.N[1], N2 = job.g.N[2];
-  const int k1 = blockIdx.x / chunks, chunk = blockIdx.x % chunks;
+  const int k1 = blk / chunks, chunk = blk % chunks;
   const int cbeg = 32 * chunk, cend = min(32 * chunk + 32, N2 / 2 + 1), nc = cend - cbeg;
   if (up->skip) return;
   const int realign = up->realign;
@@ -777,15 +830,17 @@ fail:
 // T[j0][k1][k2] (rows k1, columns k2) -> inverse along axis 2, then axis 1 ->
 // weights[j0][j1][j2] in buf[cur]; moment partials per CTA.
 template <int P>
-__global__ void __launch_bounds__(kT, 1) k_slices_inv(const __grid_constant__ Job3 job) {
+__global__ void __launch_bounds__(kT, 1) k_slices_inv(const __grid_constant__ Batch3 b) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ Smem3 sh;
+  int blk, cnt;
+  const Job3& job = job_at(b, find_job(b, kKindSlices, blockIdx.x, &blk, &cnt));
   uint8_t* A = smem + kOffA;
   uint8_t* W = smem + kOffW;
   float* S = (float*)(smem + kOffS);
   const FrameState& f = job.st->f;
   const int N0 = job.g.N[0], N1 = job.g.N[1], N2 = job.g.N[2];
-  const int j0 = blockIdx.x;
+  const int j0 = blk;
   if (job.up->skip) return;
   const float* T = f.cur ? job.buf0 : job.buf1;
   float* out = f.cur ? job.buf1 : job.buf0;
@@ -868,7 +923,9 @@ fail:
 }
 
 // Moments of the new weights, normaliser and frame commit (one CTA).
-__global__ void __launch_bounds__(kT) k_commit3(const __grid_constant__ Job3 job, int nb) {
+__global__ void __launch_bounds__(kT) k_commit3(const __grid_constant__ Batch3 b) {
+  const Job3& job = job_at(b, blockIdx.x);
+  const int nb = job.g.N[0];
   __shared__ FrameState fs;
   __shared__ double tot[10];
   __shared__ DF red[kT / 32][10];
@@ -894,6 +951,8 @@ struct Tc3State {
   double* pend = nullptr;
   DF* partials = nullptr;
   unsigned int* emin = nullptr;
+  Tc3Stage stage[2];    // single-filter launches alternate between two stagings
+  int parity = 0;
 };
 
 int tc3_alloc(void** handle) {
@@ -901,7 +960,8 @@ int tc3_alloc(void** handle) {
   if (!s) return PMF_ERR_OOM;
   if (cudaMalloc(&s->up, sizeof(Update3)) != cudaSuccess || cudaMalloc(&s->pend, 32 * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&s->partials, 16 * 4096 * sizeof(DF)) != cudaSuccess ||
-      cudaMalloc(&s->emin, sizeof(unsigned int)) != cudaSuccess) {
+      cudaMalloc(&s->emin, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMemset(s->emin, 0x7f, sizeof(unsigned int)) != cudaSuccess) {
     tc3_free(s);
     return PMF_ERR_OOM;
   }
@@ -925,7 +985,8 @@ int tc3_alloc(void** handle) {
 }
 
 size_t tc3_state_bytes() {
-  return sizeof(Update3) + 32 * sizeof(double) + 16 * 4096 * sizeof(DF) + sizeof(unsigned int);
+  return sizeof(Update3) + 32 * sizeof(double) + 16 * 4096 * sizeof(DF) + sizeof(unsigned int) +
+         2 * (sizeof(Job3) + (kKinds + 1) * 2 * sizeof(int));
 }
 
 void tc3_free(void* handle) {
@@ -935,59 +996,137 @@ void tc3_free(void* handle) {
   cudaFree(s->pend);
   cudaFree(s->partials);
   cudaFree(s->emin);
+  tc3_stage_free(&s->stage[0]);
+  tc3_stage_free(&s->stage[1]);
   delete s;
+}
+
+int tc3_stage_reserve(Tc3Stage* g, int n) {
+  if (g->ev && cudaEventSynchronize(g->ev) != cudaSuccess) return PMF_ERR_CUDA;
+  if (n <= g->cap) return PMF_OK;
+  cudaFreeHost(g->h_jobs);
+  cudaFreeHost(g->h_first);
+  cudaFree(g->d_jobs);
+  cudaFree(g->d_first);
+  *g = Tc3Stage{nullptr, nullptr, nullptr, nullptr, 0, g->ev};
+  const int cap = n < 16 ? 16 : n;
+  const size_t fb = sizeof(int) * kKinds * (size_t)(cap + 1);
+  if (cudaMallocHost(&g->h_jobs, sizeof(Job3) * cap) != cudaSuccess || cudaMallocHost(&g->h_first, fb) != cudaSuccess ||
+      cudaMalloc(&g->d_jobs, sizeof(Job3) * cap) != cudaSuccess || cudaMalloc(&g->d_first, fb) != cudaSuccess)
+    return PMF_ERR_OOM;
+  if (!g->ev && cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming) != cudaSuccess) return PMF_ERR_CUDA;
+  g->cap = cap;
+  return PMF_OK;
+}
+
+void tc3_stage_free(Tc3Stage* g) {
+  cudaFreeHost(g->h_jobs);
+  cudaFreeHost(g->h_first);
+  cudaFree(g->d_jobs);
+  cudaFree(g->d_first);
+  if (g->ev) cudaEventDestroy(g->ev);
+  *g = Tc3Stage{};
+}
+
+namespace {
+
+int meas_blocks(long long P) { return (int)std::min<long long>(1024, (P / 4 + kT - 1) / kT); }
+
+template <int P>
+void launch_pipes(const Batch3& b, const int* tot, cudaStream_t s) {
+  k_slices_fwd<P><<<tot[kKindSlices], kT, kSmem, s>>>(b);
+  k_lines_axis0<P><<<tot[kKindLines], kT, kSmem, s>>>(b);
+  k_slices_inv<P><<<tot[kKindSlices], kT, kSmem, s>>>(b);
+}
+
+}  // namespace
+
+int tc3_batch(const Tc3Item* items, int n, int precision, Tc3Stage* g, cudaStream_t s) {
+  if (n <= 0) return 0;
+  static thread_local Batch3 b;      // n == 1: built here, passed by value
+  Job3* jobs = &b.one;
+  int one_first[kKinds * 2];
+  int* first = one_first;
+  if (n > 1) {
+    const int rc = tc3_stage_reserve(g, n);
+    if (rc) return -rc;
+    jobs = (Job3*)g->h_jobs;
+    first = g->h_first;
+  }
+  int tot[kKinds] = {0, 0, 0, 0};
+  for (int k = 0; k < kKinds; ++k) first[k * (n + 1)] = 0;
+  for (int i = 0; i < n; ++i) {
+    const Tc3Item& it = items[i];
+    const Tc3State* h = (const Tc3State*)it.handle;
+    Job3& job = jobs[i];
+    job.st = it.st;
+    job.buf0 = it.b0;
+    job.buf1 = it.b1;
+    for (int a = 0; a < 3; ++a) {
+      job.hart[a] = (const uint8_t*)it.t->hart[a];
+      job.sctab[a] = (const float*)((const uint8_t*)it.t->hart[a] + it.t->hart_bytes[a]);
+      job.g.N[a] = it.d.N[a];
+    }
+    job.g.P = it.d.P;
+    job.partials = h->partials;
+    job.emin_bits = h->emin;
+    job.up = h->up;
+    job.pend = h->pend;
+    job.precision = precision;
+    job.flags = (it.mp ? 1 : 0) | (it.tc ? 2 : 0);
+    job.chunks = (it.d.N[2] / 2 + 1 + 31) / 32;
+    job.mblocks = it.mp ? meas_blocks(it.d.P) : 0;
+    if (it.mp) job.mp = *it.mp;
+    if (it.tc) job.tc = *it.tc;
+    const int cnt[kKinds] = {it.mp ? meas_blocks(it.d.P) : 0,
+                             it.tc ? (int)std::min<long long>(2048, (it.d.P + kT - 1) / kT) : 0,
+                             it.tc ? it.d.N[0] : 0, it.tc ? (it.d.N[1] / 2 + 1) * job.chunks : 0};
+    for (int k = 0; k < kKinds; ++k) {
+      tot[k] += cnt[k];
+      first[k * (n + 1) + i + 1] = tot[k];
+    }
+  }
+  b.n = n;
+  b.jobs = nullptr;
+  b.first = nullptr;
+  if (n > 1) {
+    if (cudaMemcpyAsync(g->d_jobs, g->h_jobs, sizeof(Job3) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(g->d_first, g->h_first, sizeof(int) * kKinds * (n + 1), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaEventRecord(g->ev, s) != cudaSuccess)
+      return -PMF_ERR_CUDA;
+    b.jobs = (const Job3*)g->d_jobs;
+    b.first = g->d_first;
+  }
+  int launches = 0;
+  if (tot[kKindMeas]) {
+    k_meas_min3<<<tot[kKindMeas], kT, 0, s>>>(b);
+    k_meas_apply3<<<tot[kKindMeas], kT, 0, s>>>(b);
+    launches += 2;
+  }
+  k_frame3<<<n, kT, 0, s>>>(b);
+  ++launches;
+  if (tot[kKindSlices]) {
+    k_realign3<<<tot[kKindPoints], kT, 0, s>>>(b);
+    k_copy3<<<tot[kKindPoints], kT, 0, s>>>(b);
+    if (precision == PMF_PREC_FP16X3) launch_pipes<PMF_PREC_FP16X3>(b, tot, s);
+    else if (precision == PMF_PREC_BF16X3) launch_pipes<PMF_PREC_BF16X3>(b, tot, s);
+    else launch_pipes<PMF_PREC_TF32>(b, tot, s);
+    launches += 5;
+  }
+  k_commit3<<<n, kT, 0, s>>>(b);
+  return launches + 1;
 }
 
 int tc3_step(void* handle, const Dims& d, const pmf_config& cfg, const TcTables* t, const MeasParams* mp,
              const TimeConsts* tcs, DevState* st, float* b0, float* b1, cudaStream_t s) {
   Tc3State* h = (Tc3State*)handle;
-  Job3 job{};
-  job.st = st;
-  job.buf0 = b0;
-  job.buf1 = b1;
-  for (int a = 0; a < 3; ++a) {
-    job.hart[a] = (const uint8_t*)t->hart[a];
-    job.sctab[a] = (const float*)((const uint8_t*)t->hart[a] + t->hart_bytes[a]);
-    job.g.N[a] = d.N[a];
-  }
-  job.g.P = d.P;
-  job.partials = h->partials;
-  job.emin_bits = h->emin;
-  job.up = h->up;
-  job.pend = h->pend;
-  job.precision = cfg.precision;
-  int launches = 0;
-  const int mblocks = (int)std::min<long long>(1024, (d.P / 4 + kT - 1) / kT);
-  TimeConsts none{};
-  if (mp) {
-    cudaMemsetAsync(h->emin, 0x7f, sizeof(unsigned int), s);
-    k_meas_min3<<<mblocks, kT, 0, s>>>(job, *mp);
-    k_meas_apply3<<<mblocks, kT, 0, s>>>(job, *mp);
-    launches += 2;
-  }
-  k_frame3<<<1, kT, 0, s>>>(job, tcs ? *tcs : none, mblocks, mp != nullptr, tcs != nullptr);
-  ++launches;
-  if (!tcs) return launches;
-  const int gb = (int)std::min<long long>(2048, (d.P + kT - 1) / kT);
-  k_realign3<<<gb, kT, 0, s>>>(job);
-  k_copy3<<<gb, kT, 0, s>>>(job);
-  const int chunks = (d.N[2] / 2 + 1 + 31) / 32;
-  const int tiles = (d.N[1] / 2 + 1) * chunks;
-  if (cfg.precision == PMF_PREC_FP16X3) {
-    k_slices_fwd<PMF_PREC_FP16X3><<<d.N[0], kT, kSmem, s>>>(job);
-    k_lines_axis0<PMF_PREC_FP16X3><<<tiles, kT, kSmem, s>>>(job, chunks);
-    k_slices_inv<PMF_PREC_FP16X3><<<d.N[0], kT, kSmem, s>>>(job);
-  } else if (cfg.precision == PMF_PREC_BF16X3) {
-    k_slices_fwd<PMF_PREC_BF16X3><<<d.N[0], kT, kSmem, s>>>(job);
-    k_lines_axis0<PMF_PREC_BF16X3><<<tiles, kT, kSmem, s>>>(job, chunks);
-    k_slices_inv<PMF_PREC_BF16X3><<<d.N[0], kT, kSmem, s>>>(job);
-  } else {
-    k_slices_fwd<PMF_PREC_TF32><<<d.N[0], kT, kSmem, s>>>(job);
-    k_lines_axis0<PMF_PREC_TF32><<<tiles, kT, kSmem, s>>>(job, chunks);
-    k_slices_inv<PMF_PREC_TF32><<<d.N[0], kT, kSmem, s>>>(job);
-  }
-  k_commit3<<<1, kT, 0, s>>>(job, d.N[0]);
-  return launches + 6;
+  if (!mp && !tcs) return 0;
+  const Tc3Item it{handle, d, t, mp, tcs, st, b0, b1};
+  Tc3Stage* g = &h->stage[h->parity];
+  h->parity ^= 1;
+  const int r = tc3_batch(&it, 1, cfg.precision, g, s);
+  return r < 0 ? 0 : r;
 }
 
 }  // namespace pmf
