@@ -159,24 +159,34 @@ __device__ __forceinline__ void block_moments(Shared& sh, const Moments& m) {
   }
 }
 
+// Frame-relative measurement constants of one update (registers).
+struct MeasK {
+  float c0, c1, m00, m01, m10, m11, r00, r01, h00, h01, h10, h11, ri00, ri01, ri11, cn;
+  int kind, nz;
+};
+
+__device__ __forceinline__ MeasK meas_k(const Shared& sh) {
+  return MeasK{sh.mc[0], sh.mc[1], sh.mM[0], sh.mM[1], sh.mM[2], sh.mM[3], sh.mr0[0], sh.mr0[1], sh.mH[0],
+               sh.mH[1], sh.mH[2], sh.mH[3], sh.mRinv[0], sh.mRinv[1], sh.mRinv[3], sh.mcn, sh.mp.kind, sh.mp.nz};
+}
+
 // 1/2 r^T R^{-1} r with the residual formed relative to the frame centre c:
 // d = M u, and r = r0 - (change of h from c to c + d), r0 = z - h(c) in float64;
 // linear h: r = r0 - H d; range: |c + d| - |c| = (2 c.d + |d|^2) / (|c + d| + |c|).
-__device__ __forceinline__ float meas_e(const Shared& sh, int kind, int nz, float u0, float u1) {
-  const float d0 = sh.mM[0] * u0 + sh.mM[1] * u1, d1 = sh.mM[2] * u0 + sh.mM[3] * u1;
-  float r[2];
-  if (kind == PMF_MEAS_LINEAR) {
-    r[0] = sh.mr0[0] - (sh.mH[0] * d0 + sh.mH[1] * d1);
-    r[1] = nz > 1 ? sh.mr0[1] - (sh.mH[2] * d0 + sh.mH[3] * d1) : 0.0f;
+__device__ __forceinline__ float meas_e(const MeasK& k, float u0, float u1) {
+  const float d0 = k.m00 * u0 + k.m01 * u1, d1 = k.m10 * u0 + k.m11 * u1;
+  float r0, r1 = 0.0f;
+  if (k.kind == PMF_MEAS_LINEAR) {
+    r0 = k.r00 - (k.h00 * d0 + k.h01 * d1);
+    if (k.nz > 1) r1 = k.r01 - (k.h10 * d0 + k.h11 * d1);
   } else {
-    const float x0 = sh.mc[0] + d0, x1 = sh.mc[1] + d1;
-    const float den = sqrtf(x0 * x0 + x1 * x1) + sh.mcn;
-    const float num = 2.0f * (sh.mc[0] * d0 + sh.mc[1] * d1) + d0 * d0 + d1 * d1;
-    r[0] = sh.mr0[0] - (den > 0.0f ? __fdividef(num, den) : 0.0f);
-    r[1] = 0.0f;
+    const float x0 = k.c0 + d0, x1 = k.c1 + d1;
+    const float den = sqrtf(x0 * x0 + x1 * x1) + k.cn;
+    const float num = 2.0f * (k.c0 * d0 + k.c1 * d1) + d0 * d0 + d1 * d1;
+    r0 = k.r00 - (den > 0.0f ? __fdividef(num, den) : 0.0f);
   }
-  float e = r[0] * sh.mRinv[0] * r[0];
-  if (nz > 1) e += 2.0f * r[0] * sh.mRinv[1] * r[1] + r[1] * sh.mRinv[3] * r[1];
+  float e = r0 * k.ri00 * r0;
+  if (k.nz > 1) e += 2.0f * r0 * k.ri01 * r1 + r1 * k.ri11 * r1;
   return 0.5f * e;
 }
 
@@ -320,6 +330,11 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   const float* in = cur ? job.buf1 : job.buf0;
   float* out = cur ? job.buf0 : job.buf1;
   const int q1 = N1 / 4, np4 = N0 * q1;
+  if (job.do_time && warp == 2 && (tid & 31) < 2) {
+    // the Hartley planes of both axes are needed after the measurement update
+    const int a = tid & 1, Nm = a ? N1 : N0;
+    prefetch_l2(job.hart[a], (uint32_t)Nm * (uint32_t)(Fmt<P>::rowblk / 8) * Fmt<P>::planes);
+  }
   if (warp == 1) {
     // rows are N1 * 4 bytes (a multiple of 64) at 16-byte aligned addresses
     if (tid == 32) expect_tx(mb_tma, (uint32_t)(N0 * N1 * 4));
@@ -353,14 +368,17 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     }
     __syncthreads();
     // exponents into the (still free) W region while the weights arrive
-    const int kind = sh.mp.kind, nz = sh.mp.nz;
+    const MeasK mk = meas_k(sh);
+    // t = r q1 + c/4 < 2^12: (t + 1/2) / q1 is at least 1/(2 q1) from an
+    // integer, so the float product truncates to r exactly
+    const float rq1 = 1.0f / (float)q1;
     float4* E = (float4*)W;
     float emin = INFINITY;
     for (int t = tid; t < np4; t += kThreads) {
-      const int r = t / q1, c = (t - r * q1) * 4;
+      const int r = (int)(((float)t + 0.5f) * rq1), c = (t - r * q1) * 4;
       const float u0 = r - 0.5f * (N0 - 1), u1 = c - 0.5f * (N1 - 1);
-      const float4 e = make_float4(meas_e(sh, kind, nz, u0, u1), meas_e(sh, kind, nz, u0, u1 + 1.0f),
-                                   meas_e(sh, kind, nz, u0, u1 + 2.0f), meas_e(sh, kind, nz, u0, u1 + 3.0f));
+      const float4 e = make_float4(meas_e(mk, u0, u1), meas_e(mk, u0, u1 + 1.0f), meas_e(mk, u0, u1 + 2.0f),
+                                   meas_e(mk, u0, u1 + 3.0f));
       E[t] = e;
       emin = fminf(emin, fminf(fminf(e.x, e.y), fminf(e.z, e.w)));
     }
@@ -374,7 +392,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     Moments mo;
     mo.zero();
     for (int t = tid; t < np4; t += kThreads) {
-      const int r = t / q1, c = (t - r * q1) * 4;
+      const int r = (int)(((float)t + 0.5f) * rq1), c = (t - r * q1) * 4;
       const float u0 = r - 0.5f * (N0 - 1), u1 = c - 0.5f * (N1 - 1);
       float4 x = *(const float4*)(S + r * kSStr + c);
       const float4 e = E[t];
@@ -542,17 +560,18 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         v[j].w *= inv_scale;
       }
       if (stage == 5) {
-        // final weights: rows j0, columns j1 -> staging (true scale) and moments
+        // final weights: row j0 = lane, columns j1, straight to HBM (each
+        // thread writes its contiguous, 16-byte aligned row segment), and moments
         Moments mo;
         mo.zero();
         const float u0 = row - 0.5f * (N0 - 1);
+        float* orow = out + (size_t)row * N1 + c0;
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-          if (4 * j < ncol) {
-            *(float4*)(S + row * kSStr + c0 + 4 * j) = v[j];
-            if (lane_ok) mo.add4(v[j], u0, (c0 + 4 * j) - 0.5f * (N1 - 1));
+          if (4 * j < ncol && lane_ok) {
+            *(float4*)(orow + 4 * j) = v[j];
+            mo.add4(v[j], u0, (c0 + 4 * j) - 0.5f * (N1 - 1));
           }
-        fence_async_smem();
         tc_before_sync();
         block_moments(sh, mo);
         break;
@@ -625,13 +644,8 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       goto done;
     }
 
-    // ---- write-back (bulk stores of the staged rows) and normalisation ----
-    if (warp == 0) {
-      for (int r = tid; r < N0; r += 32) bulk_store(out + (size_t)r * N1, su32(S + r * kSStr), (uint32_t)(N1 * 4));
-      bulk_commit();
-      if (finalize_warp<2>(&fs, sh.tot, 1, sh.pend) && tid == 0) fs.cur = cur ^ 1;
-      bulk_wait_all();
-    }
+    // ---- normalisation on the advanced frame ----
+    if (warp == 0 && finalize_warp<2>(&fs, sh.tot, 1, sh.pend) && tid == 0) fs.cur = cur ^ 1;
   }
 
 done:

@@ -113,6 +113,12 @@ __device__ __forceinline__ void bulk_store(void* dst, uint32_t src, uint32_t byt
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// ... until the shared-memory sources of this thread's bulk groups have been read
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Warm the L2 with [src, src + bytes) (16-byte aligned, multiple of 16 bytes).
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 
 __device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -300,31 +306,50 @@ __device__ void regrid_rows(RegridRowsT<R>& sh, double rs, double rd, int N, int
 // the angle pi v / N split into the tabulated pi m / N (sctab: (cos, sin) for
 // m = -N..N) and the per-row pi f / N.  Rows of new nodes outside the old box
 // are zero.
+struct RegridRow {
+  int i;
+  float f, S, cf, sf;
+  bool zero;
+};
+
+template <int R>
+__device__ __forceinline__ RegridRow regrid_row(const RegridRowsT<R>& sh, int n) {
+  return RegridRow{sh.ri[n], sh.rf[n], sh.rS[n], sh.rcf[n], sh.rsf[n], sh.rzero[n] != 0};
+}
+
+__device__ __forceinline__ float interp_value(const RegridRow& r, int j, int N, const float* sctab) {
+  if (r.zero) return 0.0f;
+  const int m = r.i - j;
+  if (m == 0 && r.f == 0.0f) return 1.0f;
+  const float cm = sctab[2 * (m + N)], sm = sctab[2 * (m + N) + 1];
+  const float sv = sm * r.cf + cm * r.sf;
+  const float cv = cm * r.cf - sm * r.sf;
+  return __fdividef(((m & 1) ? -1.0f : 1.0f) * r.S * cv, (float)N * sv);
+}
+
 template <int R>
 __device__ __forceinline__ float interp_entry(const RegridRowsT<R>& sh, int n, int j, int N, const float* sctab) {
-  if (sh.rzero[n]) return 0.0f;
-  const int m = sh.ri[n] - j;
-  const float f = sh.rf[n];
-  if (m == 0 && f == 0.0f) return 1.0f;
-  const float cm = sctab[2 * (m + N)], sm = sctab[2 * (m + N) + 1];
-  const float sv = sm * sh.rcf[n] + cm * sh.rsf[n];
-  const float cv = cm * sh.rcf[n] - sm * sh.rsf[n];
-  return __fdividef(((m & 1) ? -1.0f : 1.0f) * sh.rS[n] * cv, (float)N * sv);
+  return interp_value(regrid_row(sh, n), j, N, sctab);
 }
 
 // The regrid matrix of one axis into the W planes, scaled by sw (identity
 // when the frame was re-aligned: the gather already moved the weights).
+// Thread t0 (of tstep >= N) keeps row t0 % N and every (tstep / N)-th group
+// of four columns, so its row parameters are read once; consecutive threads
+// take consecutive rows (8 rows share 128 bytes of the operand layout).
 template <int P>
 __device__ void build_interp(const RegridRows& sh, uint8_t* W, int N, const float* sctab, float sw, int realign,
                              int t0, int tstep) {
-  const int q4 = N / 4;
-  for (int t = t0; t < N * q4; t += tstep) {
-    const int n = t % N, c = (t / N) * 4;   // consecutive threads: consecutive rows
+  const int per = tstep / N;
+  if (t0 >= per * N) return;
+  const int n = t0 % N;
+  const RegridRow r = regrid_row(sh, n);
+  for (int c = (t0 / N) * 4; c < N; c += 4 * per) {
     float k[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int j = c + i;
-      k[i] = realign ? (n == j ? 1.0f : 0.0f) : interp_entry(sh, n, j, N, sctab);
+      k[i] = realign ? (n == j ? 1.0f : 0.0f) : interp_value(r, j, N, sctab);
     }
     store4<P>(W, n, c, make_float4(k[0], k[1], k[2], k[3]), sw);
   }
