@@ -210,6 +210,19 @@ long long pmf_batch_bytes(const pmf_batch* b);
 long long pmf_batch_launch_count(const pmf_batch* b);
 void pmf_batch_destroy(pmf_batch* b);
 
+/* Finite-difference comparator of Sec. III-B/III-C (eq. fdiff, eq. FST), as
+ * a baseline for the accuracy per grid point of the spectral method.
+ * count independent 1-D grids of N interior nodes with zero boundary values
+ * (model dx = a x dt + q dw) are advanced by l explicit sub-steps of length
+ * dt, the node spacing moving as delta_n = e^{a dt} delta_{n-1} from delta0,
+ * through the sine-transform form P' = 2/(N+1) R diag(prod lambda) R P
+ * (float64, two DST-I matrix products).  P_in, P_out: device arrays of
+ * count * N doubles (grid g at g * N), not aliased; work: device array of at
+ * least count * N + 4 * N + 2 doubles (caller-owned scratch).  Asynchronous
+ * on cuda_stream.  PMF_ERR_ARG on bad sizes or parameters. */
+int pmf_fdm_transition(const double* P_in, double* P_out, double* work, int N, int count, double q, double a,
+                       double dt, int l, double delta0, void* cuda_stream);
+
 /* ---------------------------------------------------------------------------
  * Serving: resident filters of mixed dimension updated by continuous batching.
  * (The paper runs one filter; this layer has no counterpart there.)

@@ -5,5 +5,6 @@ include/pmf.h (libpmf.so, built in-tree by ``build.build()``); this package
 is a thin ctypes binding with the same entry points.
 """
 from ._binding import (  # noqa: F401
-    Batch, Degenerate, Filter, PmfError, Server, Unsupported, load, lib_path, make_config, make_meas,
+    Batch, Degenerate, Filter, PmfError, Server, Unsupported, fdm_transition, load, lib_path, make_config,
+    make_meas,
 )

@@ -79,6 +79,8 @@ SIGNATURES = [
     ("pmf_batch_bytes", C.c_longlong, [C.c_void_p]),
     ("pmf_batch_launch_count", C.c_longlong, [C.c_void_p]),
     ("pmf_batch_destroy", None, [C.c_void_p]),
+    ("pmf_fdm_transition", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double,
+                                     C.c_double, C.c_double, C.c_int, C.c_double, C.c_void_p]),
     ("pmf_server_create", C.c_int, [C.POINTER(C.c_void_p), C.c_size_t, C.c_int, C.c_int]),
     ("pmf_server_admit", C.c_int, [C.c_void_p, C.POINTER(PmfConfig), C.POINTER(PmfMeas), C.POINTER(C.c_int)]),
     ("pmf_server_evict", C.c_int, [C.c_void_p, C.c_int]),
@@ -458,3 +460,15 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def fdm_transition(P_in, P_out, work, q, a, dt, l, delta0, stream=None) -> None:
+    """pmf_fdm_transition on device float64 tensors P_in, P_out of shape (count, N)
+    and work of at least count * N + 4 * N + 2 elements."""
+    lib = load()
+    count, N = int(P_in.shape[0]), int(P_in.shape[1])
+    rc = lib.pmf_fdm_transition(C.c_void_p(int(P_in.data_ptr())), C.c_void_p(int(P_out.data_ptr())),
+                                C.c_void_p(int(work.data_ptr())), N, count, float(q), float(a), float(dt), int(l),
+                                float(delta0), _stream_handle(stream))
+    if rc != OK:
+        raise PmfError(rc, "pmf_fdm_transition failed")
