@@ -187,7 +187,9 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
  * z[i*PMF_MAX_NZ ...] (skipped when do_meas[i] == 0; do_meas may be NULL = all)
  * then time update over taus[i] (skipped when taus[i] == 0).  Asynchronous;
  * ids must be distinct within a call.  Model constants are recomputed on the
- * host only for filters whose tau changed. */
+ * host only for filters whose tau changed.  The item upload and the single
+ * batch kernel run as a CUDA graph, captured on the first epoch of each
+ * batch size and replayed afterwards. */
 int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_meas,
                    const double* taus, int k);
 

@@ -31,6 +31,7 @@ struct pmf_ctx {
   double* prior_aux = nullptr;  // P0^{-1} (9) and m0 (3)
   TcTables tct{};               // tensor-core path tables (pmf_tc.cu)
   void* tab1 = nullptr;         // 1-D kernel table (pmf_tc1.cu)
+  int mode1 = 0;                // 1-D Hartley form (autotuned)
   void* tc3 = nullptr;          // 3-D pipeline state (pmf_tc3.cu)
   TimeConsts tc{};
   double tc_tau = -1.0;
@@ -89,7 +90,7 @@ void free_ctx(pmf_ctx* ctx) {
 int fast_step(pmf_ctx* ctx, const MeasParams* mp, const TimeConsts* tc) {
   if (ctx->path == 3)
     return tc1_step(ctx->cfg.N[0], ctx->tab1, mp, tc, ctx->st, (float*)ctx->buf[0], (float*)ctx->buf[1],
-                    ctx->stream);
+                    ctx->stream, ctx->mode1);
   if (ctx->path == 2)
     return tc3_step(ctx->tc3, ctx->dims, ctx->cfg, &ctx->tct, mp, tc, ctx->st, (float*)ctx->buf[0],
                     (float*)ctx->buf[1], ctx->stream);
@@ -186,6 +187,7 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
       free_ctx(ctx);
       return rc;
     }
+    ctx->mode1 = tc1_mode(cfg->N[0], ctx->tab1, ctx->stream);
   } else {
     rc = tc_build_tables(cfg, &ctx->tct, &why);
     if (rc == PMF_OK && ctx->path == 2) rc = tc3_alloc(&ctx->tc3);
@@ -369,6 +371,9 @@ struct pmf_batch {
   TimeConsts* h_tc[2] = {nullptr, nullptr};
   cudaEvent_t ev[2] = {nullptr, nullptr};
   int parity = 0;
+  cudaStream_t cap = nullptr;                 // capture stream of the epoch graphs
+  cudaGraphExec_t gx[2] = {nullptr, nullptr}; // item copy + batch kernel, per parity buffer
+  int gk[2] = {0, 0};                         // batch size each graph was captured for
   long long bytes = 0, launches = 0;
   std::string err;
 };
@@ -390,6 +395,9 @@ void free_batch(pmf_batch* b) {
   cudaFreeHost(b->h_ids);
   cudaFreeHost(b->h_gather);
   for (void* p : b->tables) cudaFree(p);
+  for (int i = 0; i < 2; ++i)
+    if (b->gx[i]) cudaGraphExecDestroy(b->gx[i]);
+  if (b->cap) cudaStreamDestroy(b->cap);
   for (int i = 0; i < 2; ++i) {
     cudaFreeHost(b->h_items[i]);
     cudaFreeHost(b->h_tc[i]);
@@ -576,11 +584,31 @@ int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_
     if (cudaMemcpyAsync(b->d_tc + changed[j], &stage[j], sizeof(TimeConsts), cudaMemcpyHostToDevice,
                         b->stream) != cudaSuccess)
       return PMF_ERR_CUDA;
-  if (cudaMemcpyAsync(b->d_items, items, sizeof(StepItem) * k, cudaMemcpyHostToDevice, b->stream) !=
-      cudaSuccess)
-    return PMF_ERR_CUDA;
+  // the item copy and the batch kernel replay as one CUDA graph, captured
+  // once per parity buffer and batch size (the copy reads this parity's
+  // pinned items when the graph runs)
+  if (!b->gx[p] || b->gk[p] != k) {
+    if (b->gx[p]) {
+      cudaGraphExecDestroy(b->gx[p]);
+      b->gx[p] = nullptr;
+    }
+    if (!b->cap && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return PMF_ERR_CUDA;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PMF_ERR_CUDA;
+    cudaMemcpyAsync(b->d_items, items, sizeof(StepItem) * k, cudaMemcpyHostToDevice, b->cap);
+    tc_batch_step(b->precision, b->d_slots, b->d_items, k, b->cap);
+    if (cudaStreamEndCapture(b->cap, &g) != cudaSuccess) return PMF_ERR_CUDA;
+    const cudaError_t e = cudaGraphInstantiate(&b->gx[p], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      b->gx[p] = nullptr;
+      return PMF_ERR_CUDA;
+    }
+    b->gk[p] = k;
+  }
+  if (cudaGraphLaunch(b->gx[p], b->stream) != cudaSuccess) return PMF_ERR_CUDA;
   cudaEventRecord(b->ev[p], b->stream);
-  b->launches += tc_batch_step(b->precision, b->d_slots, b->d_items, k, b->stream);
+  b->launches += 1;
   return cudaGetLastError() == cudaSuccess ? PMF_OK : PMF_ERR_CUDA;
 }
 

@@ -489,7 +489,8 @@ int pmf_server_admit(pmf_server* s, const pmf_config* cfg, const pmf_meas* model
        cudaMemcpyAsync(s->d_aux, aux, sizeof(aux), cudaMemcpyHostToDevice, st) == cudaSuccess;
   if (ok) s->launches += tc_prior(d, f.st, s->d_aux, f.buf, s->d_partials, st);
   if (ok && n == 1) {
-    const Slot1 sl{f.st, f.buf, f.buf + P, (const float*)tabs[0], cfg->N[0], f.d_mp, nullptr};
+    const Slot1 sl{f.st, f.buf, f.buf + P, (const float*)tabs[0], cfg->N[0], f.d_mp, nullptr,
+                   tc1_mode(cfg->N[0], tabs[0], st)};
     ok = cudaMemcpyAsync(s->d_slots1 + id, &sl, sizeof(sl), cudaMemcpyHostToDevice, st) == cudaSuccess;
   } else if (ok && n == 2) {
     FilterSlot sl{};

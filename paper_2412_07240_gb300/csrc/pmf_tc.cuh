@@ -43,6 +43,7 @@ struct Slot1 {
   int N;
   const MeasParams* mp;
   const TimeConsts* tc;
+  int mode;                 // Hartley transforms: 0 matrix-vector, 1 shared-memory FFT
 };
 
 // PMF_OK if the fused kernel can hold this grid at this precision.
@@ -105,7 +106,11 @@ int tc1_supported(const pmf_config* cfg, std::string* why);
 size_t tc1_table_bytes(int N);
 int tc1_build_table(int N, void** dev);
 int tc1_step(int N, const void* table, const MeasParams* mp, const TimeConsts* tc, DevState* st, float* b0,
-             float* b1, cudaStream_t s);
+             float* b1, cudaStream_t s, int mode);
+// Transform form for size N chosen by timing both on a scratch filter (once
+// per N and process; cached in autotune.json beside the library).  The
+// environment variable PMF_1D_FORM=fft|matvec overrides the choice.
+int tc1_mode(int N, const void* table, cudaStream_t s);
 int tc1_batch_step(const Slot1* slots, const StepItem* items, const TimeConsts* tcs, int k, cudaStream_t s);
 // {mean[2], cov[4], status, 0} of filters ids[0..k) into out (8 doubles each),
 // then their status words cleared; returns the number of launches.

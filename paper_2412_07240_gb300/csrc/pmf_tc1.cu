@@ -13,9 +13,23 @@
 //
 // A single 1-D filter's transform is a matrix-vector product, not a GEMM tile:
 // the products run in float32 on the CUDA cores with every operand in shared
-// memory, and the small footprint lets several filters share an SM.
+// memory, and the small footprint lets several filters share an SM.  For N a
+// power of two the two Hartley transforms can instead run as a radix-2
+// Stockham FFT in shared memory (H_k = Re Z_k - Im Z_k); an autotuner times
+// both forms once per N and caches the choice in autotune.json beside the
+// library.
+#include <dlfcn.h>
+
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
+
+#include "pmf_model.cuh"
 
 #include "pmf_device.cuh"
 #include "pmf_tc.cuh"
@@ -38,6 +52,7 @@ struct View1 {
   const MeasParams* mp;
   const double* z;
   const TimeConsts* tc;
+  int mode;                 // Hartley transforms: 0 matrix-vector, 1 Stockham FFT (N a power of two)
 };
 
 // One filter launched alone: everything by value.
@@ -49,6 +64,7 @@ struct Job1 {
   int N, do_meas, do_time;
   MeasParams mp;
   TimeConsts tc;
+  int mode;
 };
 
 struct Shared1 {
@@ -61,6 +77,7 @@ struct Shared1 {
   DF redm[kT1 / 32][3];
   float redf[kT1 / 32];
   float x[kMaxN1], y[kMaxN1];
+  float fre[2][kMaxN1], fim[2][kMaxN1];   // FFT ping-pong buffers
   float cas[kMaxN1];
   float sct[2 * (2 * kMaxN1 + 1)];
   RegridRowsT<kMaxN1> rows;
@@ -125,6 +142,41 @@ __device__ __forceinline__ void matvec1(int N, int lp, const float* src, Entry e
     for (int d = P >> 1; d; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
     if (w < total && p == 0) epi(o, s);
   }
+}
+
+// Hartley transform of src (N = 2^lg) by a radix-2 Stockham FFT of the real
+// sequence: Z = sum_j y_j e^{-2 pi i j k / N}, stage Ns pairs j and j + N/2,
+// twiddle e^{-i pi (j mod Ns) / Ns} from the (cos, sin)(pi m / N) table, and
+// writes to (j - t) 2 + t and + Ns (t = j mod Ns); then epi(k, Re Z_k - Im Z_k).
+template <class Epi>
+__device__ __forceinline__ void fht1(Shared1& sh, const float* src, int N, Epi epi) {
+  for (int j = threadIdx.x; j < N; j += kT1) {
+    sh.fre[0][j] = src[j];
+    sh.fim[0][j] = 0.0f;
+  }
+  __syncthreads();
+  int b = 0;
+  for (int Ns = 1; Ns < N; Ns <<= 1) {
+    const float* ri = sh.fre[b];
+    const float* ii = sh.fim[b];
+    float* ro = sh.fre[b ^ 1];
+    float* io = sh.fim[b ^ 1];
+    const int half = N >> 1, step = N / (2 * Ns);
+    for (int j = threadIdx.x; j < half; j += kT1) {
+      const int t = j & (Ns - 1), m = 2 * t * step;
+      const float c = sh.sct[2 * (m + N)], s = sh.sct[2 * (m + N) + 1];
+      const float ar = ri[j], ai = ii[j], br = ri[j + half], bi = ii[j + half];
+      const float tr = br * c + bi * s, ti = bi * c - br * s;
+      const int o = (j - t) * 2 + t;
+      ro[o] = ar + tr;
+      io[o] = ai + ti;
+      ro[o + Ns] = ar - tr;
+      io[o + Ns] = ai - ti;
+    }
+    b ^= 1;
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < N; k += kT1) epi(k, sh.fre[b][k] - sh.fim[b][k]);
 }
 
 __device__ void fused1d(const View1& v) {
@@ -259,7 +311,7 @@ __device__ void fused1d(const View1& v) {
       }
       return s;
     };
-    matvec1(N, lp, sh.y, hartley, [&](int k, float s) {
+    auto psi = [&](int k, float s) {
       const float kf = w2 * (float)(k < N / 2 ? k : k - N);
       const float q = kf * kf;
       float den = 1.0f, ex = 0.0f;
@@ -269,10 +321,18 @@ __device__ void fused1d(const View1& v) {
         ex += e;
       }
       sh.x[k] = s * (exact ? expf(-ex) : __frcp_rn(den)) * sh.gsc;
-    });
+    };
+    if (v.mode == 1)
+      fht1(sh, sh.y, N, psi);
+    else
+      matvec1(N, lp, sh.y, hartley, psi);
     __syncthreads();
     // inverse Hartley (its own inverse; 1/N is in gsc)
-    matvec1(N, lp, sh.x, hartley, [&](int j, float s) { sh.y[j] = s; });
+    auto keep = [&](int j, float s) { sh.y[j] = s; };
+    if (v.mode == 1)
+      fht1(sh, sh.x, N, keep);
+    else
+      matvec1(N, lp, sh.x, hartley, keep);
     __syncthreads();
     // ---- write-back, moments and normalisation on the advanced frame ----
     DF s0{0.0f, 0.0f}, s1{0.0f, 0.0f}, s2{0.0f, 0.0f};
@@ -292,7 +352,8 @@ done:
 }
 
 __global__ void __launch_bounds__(kT1) k_fused1d(const __grid_constant__ Job1 job) {
-  const View1 v{job.st, job.buf0, job.buf1, job.tab, job.N, job.do_meas, job.do_time, &job.mp, job.mp.z, &job.tc};
+  const View1 v{job.st,          job.buf0, job.buf1, job.tab, job.N, job.do_meas, job.do_time, &job.mp,
+                job.mp.z,        &job.tc,  job.mode};
   fused1d(v);
 }
 
@@ -303,7 +364,7 @@ __global__ void __launch_bounds__(kT1) k_fused1d_batch(const Slot1* __restrict__
   const StepItem& it = items[blockIdx.x];
   const Slot1& sl = slots[it.slot];
   const View1 v{sl.st, sl.buf0, sl.buf1, sl.tab, sl.N, it.flags & 1, (it.flags >> 1) & 1, sl.mp, it.z,
-                tcs ? tcs + blockIdx.x : sl.tc};
+                tcs ? tcs + blockIdx.x : sl.tc, sl.mode};
   fused1d(v);
 }
 
@@ -336,9 +397,10 @@ int tc1_build_table(int N, void** dev) {
 }
 
 int tc1_step(int N, const void* table, const MeasParams* mp, const TimeConsts* tc, DevState* st, float* b0,
-             float* b1, cudaStream_t s) {
+             float* b1, cudaStream_t s, int mode) {
   if (!mp && !tc) return 0;
   Job1 job{};
+  job.mode = mode;
   job.st = st;
   job.buf0 = b0;
   job.buf1 = b1;
@@ -356,6 +418,143 @@ int tc1_batch_step(const Slot1* slots, const StepItem* items, const TimeConsts* 
   if (k <= 0) return 0;
   k_fused1d_batch<<<k, kT1, 0, s>>>(slots, items, tcs);
   return 1;
+}
+
+}  // namespace pmf
+
+namespace pmf {
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<int, int> g_tune;      // N -> mode
+std::map<int, std::pair<double, double>> g_tune_us;   // N -> (matrix-vector, FFT) microseconds
+bool g_tune_loaded = false;
+
+std::string tune_path() {
+  Dl_info info;
+  if (!dladdr((void*)&tc1_mode, &info) || !info.dli_fname) return "";
+  std::string p = info.dli_fname;
+  const size_t slash = p.rfind('/');
+  return (slash == std::string::npos ? std::string(".") : p.substr(0, slash)) + "/autotune.json";
+}
+
+// {"1d:N": {"mode": m, ...}, ...}: read the mode of every 1-D entry.
+void tune_load() {
+  g_tune_loaded = true;
+  const std::string p = tune_path();
+  FILE* f = p.empty() ? nullptr : std::fopen(p.c_str(), "r");
+  if (!f) return;
+  char line[512];
+  while (std::fgets(line, sizeof line, f)) {
+    int N = 0, mode = -1;
+    double tm = 0.0, tf = 0.0;
+    const char* q = std::strstr(line, "\"1d:");
+    const int got = q ? std::sscanf(q, "\"1d:%d\": {\"mode\": %d, \"matvec_us\": %lf, \"fft_us\": %lf", &N, &mode, &tm,
+                                    &tf)
+                      : 0;
+    if (got >= 2 && (mode == 0 || mode == 1)) {
+      g_tune[N] = mode;
+      if (got == 4) g_tune_us[N] = {tm, tf};
+    }
+  }
+  std::fclose(f);
+}
+
+void tune_save() {
+  const auto& times = g_tune_us;
+  const std::string p = tune_path();
+  FILE* f = p.empty() ? nullptr : std::fopen(p.c_str(), "w");
+  if (!f) return;
+  std::fprintf(f, "{\n");
+  size_t i = 0;
+  for (const auto& kv : g_tune) {
+    auto t = times.find(kv.first);
+    std::fprintf(f, "  \"1d:%d\": {\"mode\": %d", kv.first, kv.second);
+    if (t != times.end()) std::fprintf(f, ", \"matvec_us\": %.3f, \"fft_us\": %.3f", t->second.first, t->second.second);
+    std::fprintf(f, "}%s\n", ++i < g_tune.size() ? "," : "");
+  }
+  std::fprintf(f, "}\n");
+  std::fclose(f);
+}
+
+// Mean time of one epoch of a scratch filter of size N in the given mode.
+double time_mode(int N, const void* table, int mode, cudaStream_t s) {
+  pmf_config c{};
+  c.nx = 1;
+  c.N[0] = N;
+  c.A[0] = -0.5;
+  c.Q[0] = 0.5;
+  c.P0[0] = 0.25;
+  c.span_sigma = 6.0;
+  c.dt_sub = 0.01;
+  c.realign_rho = 0.5;
+  c.precision = PMF_PREC_FP16X3;
+  std::string why;
+  Job1 job{};
+  pmf_meas m{};
+  m.kind = PMF_MEAS_LINEAR;
+  m.nz = 1;
+  m.z[0] = 0.1;
+  m.R[0] = 0.01;
+  m.H[0] = 1.0;
+  if (meas_params(1, &m, &job.mp, &why) || time_consts(c, 0.1, &job.tc, &why)) return -1.0;
+  DevState h = initial_state(c);
+  std::vector<float> w(2 * (size_t)N);
+  for (int j = 0; j < N; ++j) {
+    const double u = (j - 0.5 * (N - 1)) / (N / 12.0);
+    w[j] = (float)std::exp(-0.5 * u * u);
+  }
+  DevState* st = nullptr;
+  float* buf = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double us = -1.0;
+  if (cudaMalloc(&st, sizeof(DevState)) == cudaSuccess && cudaMalloc(&buf, sizeof(float) * 2 * N) == cudaSuccess &&
+      cudaMemcpy(st, &h, sizeof(DevState), cudaMemcpyHostToDevice) == cudaSuccess &&
+      cudaMemcpy(buf, w.data(), sizeof(float) * 2 * N, cudaMemcpyHostToDevice) == cudaSuccess &&
+      cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+    job.st = st;
+    job.buf0 = buf;
+    job.buf1 = buf + N;
+    job.tab = (const float*)table;
+    job.N = N;
+    job.do_meas = 1;
+    job.do_time = 1;
+    job.mode = mode;
+    for (int i = 0; i < 3; ++i) k_fused1d<<<1, kT1, 0, s>>>(job);
+    constexpr int kReps = 20;
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < kReps; ++i) k_fused1d<<<1, kT1, 0, s>>>(job);
+    cudaEventRecord(e1, s);
+    float ms = 0.0f;
+    if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+      us = 1e3 * ms / kReps;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(st);
+  cudaFree(buf);
+  return us;
+}
+
+}  // namespace
+
+int tc1_mode(int N, const void* table, cudaStream_t s) {
+  if (N < 16 || (N & (N - 1))) return 0;   // the FFT form needs a power of two
+  if (const char* form = std::getenv("PMF_1D_FORM")) {   // explicit choice, no tuning
+    if (!std::strcmp(form, "fft")) return 1;
+    if (!std::strcmp(form, "matvec")) return 0;
+  }
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  if (!g_tune_loaded) tune_load();
+  auto it = g_tune.find(N);
+  if (it != g_tune.end()) return it->second;
+  const double tm = time_mode(N, table, 0, s), tf = time_mode(N, table, 1, s);
+  const int mode = (tf > 0.0 && tm > 0.0 && tf < tm) ? 1 : 0;
+  g_tune[N] = mode;
+  g_tune_us[N] = {tm, tf};
+  tune_save();
+  return mode;
 }
 
 }  // namespace pmf

@@ -46,3 +46,27 @@ def test_unsupported_size_rejected():
     sc = w.c1_scenario(N=1000)
     with pytest.raises(Unsupported):
         Filter(sc.cfg, precision="fp16x3")
+
+
+@pytest.mark.parametrize("form", ["fft", "matvec"])
+@pytest.mark.parametrize("N", [64, 512])
+def test_transform_forms(form, N, monkeypatch):
+    # both Hartley forms (shared-memory FFT and matrix-vector) against the oracle
+    monkeypatch.setenv("PMF_1D_FORM", form)
+    sc = w.c1_scenario(N=N, epochs=6)
+    worst, log = max_errors(sc, precision="fp16x3", fused_step=True)
+    assert worst["l1"] < BAR, log
+
+
+def test_autotuner_records_its_choice(monkeypatch):
+    import json
+    import os
+    from paper_2412_07240_gb300 import Filter, lib_path
+    monkeypatch.delenv("PMF_1D_FORM", raising=False)
+    sc = w.c1_scenario(N=128, epochs=2)
+    f = Filter(sc.cfg, precision="fp16x3")
+    f.step(sc.meas, sc.z[0], sc.dt)
+    f.close()
+    path = os.path.join(os.path.dirname(lib_path()), "autotune.json")
+    entry = json.load(open(path))["1d:128"]
+    assert entry["mode"] in (0, 1)
