@@ -213,6 +213,25 @@ __device__ __forceinline__ float stage_max(const float* S, int nr, int nc) {
   return m;
 }
 
+// Out-of-line copies of the helpers called from several places of the epoch:
+// a kernel that runs once on cold caches fetches their code once (the batch
+// kernel, whose CTAs follow each other on an SM, keeps them inline).
+__device__ __noinline__ void block_moments_out(Shared& sh, const Moments& m) { block_moments(sh, m); }
+__device__ __noinline__ bool finalize_warp_out(FrameState* st, const double* tot, int use_pending,
+                                               const double* pend) {
+  return finalize_warp<2>(st, tot, use_pending, pend);
+}
+template <int P>
+__device__ __noinline__ void build_interp_out(const RegridRows& rows, uint8_t* W, int N, const float* sctab, float sw,
+                                              int realign, int t0, int tstep) {
+  build_interp<P>(rows, W, N, sctab, sw, realign, t0, tstep);
+}
+template <int P>
+__device__ __noinline__ void stage_to_operand_out(uint8_t* A, const float* S, int nr, int nc, float s, int t0,
+                                                  int tstep) {
+  stage_to_operand<P>(A, S, nr, nc, s, t0, tstep);
+}
+
 // Diffusion multiplier and trace factor in the Hartley domain (Sec. V-B
 // algorithm steps 2-4) on the staging tile T[k1][k0], one thread per orbit
 // {(+-k0, +-k1)}: with S_s the four separable coefficients (bit 0 of s flips
@@ -274,7 +293,7 @@ __device__ void psi_stage(const Shared& sh, float* S, int N0, int N1, int l, int
   }
 }
 
-template <int P>
+template <int P, bool kOut>
 __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   __shared__ Shared sh;
   if (!job.do_meas && !job.do_time) return;   // nothing requested for this filter
@@ -404,7 +423,8 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       mo.add4(x, u0, u1);
       smax = amax4(smax, x);
     }
-    block_moments(sh, mo);
+    if constexpr (kOut) block_moments_out(sh, mo);
+    else block_moments(sh, mo);
   } else {
     if (__syncthreads_or(!mbar_wait(mb_tma, ph_tma))) {
       if (tid == 0) fs.status = PMF_ERR_TIMEOUT;
@@ -431,7 +451,8 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     if (warp == 0) {
       bool ok = true;
       if (job.do_meas) {
-        ok = finalize_warp<2>(&fs, sh.tot, 0, nullptr);
+        if constexpr (kOut) ok = finalize_warp_out(&fs, sh.tot, 0, nullptr);
+        else ok = finalize_warp<2>(&fs, sh.tot, 0, nullptr);
         if (tid == 0) {
           if (!ok) {
             sh.degenerate = 1;
@@ -451,7 +472,8 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         }
       }
     } else if (job.do_time) {
-      stage_to_operand<P>(A, S, N0, N1, sa0, tid - 32, kThreads - 32);
+      if constexpr (kOut) stage_to_operand_out<P>(A, S, N0, N1, sa0, tid - 32, kThreads - 32);
+      else stage_to_operand<P>(A, S, N0, N1, sa0, tid - 32, kThreads - 32);
     }
     __syncthreads();
     if (sh.degenerate) goto done;
@@ -514,7 +536,8 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         smax = fmaxf(smax, fabsf(G[p]));
       }
       sa_first = op_scale<P>(block_max(sh, smax, 0));
-      stage_to_operand<P>(A, S, N0, N1, sa_first, tid, kThreads);
+      if constexpr (kOut) stage_to_operand_out<P>(A, S, N0, N1, sa_first, tid, kThreads);
+      else stage_to_operand<P>(A, S, N0, N1, sa_first, tid, kThreads);
     } else if (tid < kThreads / 2) {
       regrid_rows(sh.rows[1], fs.rs[1], fs.rd[1], N1, tid, kThreads / 2);
     } else {
@@ -526,7 +549,8 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   {
     // ---- the matrix I1; the R1 operand is already written ----
     float sa = sa_first;
-    build_interp<P>(sh.rows[1], W, N1, sh.sct[1], sw, realign, tid, kThreads);
+    if constexpr (kOut) build_interp_out<P>(sh.rows[1], W, N1, sh.sct[1], sw, realign, tid, kThreads);
+    else build_interp<P>(sh.rows[1], W, N1, sh.sct[1], sw, realign, tid, kThreads);
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -573,7 +597,8 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
             mo.add4(v[j], u0, (c0 + 4 * j) - 0.5f * (N1 - 1));
           }
         tc_before_sync();
-        block_moments(sh, mo);
+        if constexpr (kOut) block_moments_out(sh, mo);
+        else block_moments(sh, mo);
         break;
       }
       if (stage == 3) {
@@ -586,7 +611,8 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         psi_stage(sh, S, N0, N1, l, exact);
         __syncthreads();
         sa = op_scale<P>(block_max(sh, stage_max(S, N1, N0), stage & 1));
-        stage_to_operand<P>(A, S, N1, N0, sa, tid, kThreads);
+        if constexpr (kOut) stage_to_operand_out<P>(A, S, N1, N0, sa, tid, kThreads);
+        else stage_to_operand<P>(A, S, N1, N0, sa, tid, kThreads);
       } else {
         float m = 0.0f;
 #pragma unroll
@@ -610,7 +636,8 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       if (stage == 2) mat = 0;
       if (stage == 1) {
         __syncthreads();
-        build_interp<P>(sh.rows[0], W, N0, sh.sct[0], sw, realign, tid, kThreads);
+        if constexpr (kOut) build_interp_out<P>(sh.rows[0], W, N0, sh.sct[0], sw, realign, tid, kThreads);
+        else build_interp<P>(sh.rows[0], W, N0, sh.sct[0], sw, realign, tid, kThreads);
       }
       fence_async_smem();
       __syncthreads();
@@ -645,7 +672,12 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     }
 
     // ---- normalisation on the advanced frame ----
-    if (warp == 0 && finalize_warp<2>(&fs, sh.tot, 1, sh.pend) && tid == 0) fs.cur = cur ^ 1;
+    if (warp == 0) {
+      bool ok;
+      if constexpr (kOut) ok = finalize_warp_out(&fs, sh.tot, 1, sh.pend);
+      else ok = finalize_warp<2>(&fs, sh.tot, 1, sh.pend);
+      if (ok && tid == 0) fs.cur = cur ^ 1;
+    }
   }
 
 done:
@@ -661,7 +693,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused2d(const __grid_constant__
   extern __shared__ __align__(1024) uint8_t smem[];
   const FusedView v{job.st, job.buf0, job.buf1, {job.hart[0], job.hart[1]}, {job.sctab[0], job.sctab[1]},
                     job.N0, job.N1, job.do_meas, job.do_time, &job.mp, job.mp.z, &job.tc};
-  fused2d<P>(v, smem);
+  fused2d<P, true>(v, smem);
 }
 
 // Many filters, one CTA each: items[blockIdx.x] names the filter slot, the
@@ -676,7 +708,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused2d_batch(const FilterSlot*
   const FusedView v{sl.st, sl.buf0, sl.buf1, {sl.hart[0], sl.hart[1]}, {sl.sctab[0], sl.sctab[1]},
                     sl.N0, sl.N1, it.flags & 1, (it.flags >> 1) & 1, sl.mp, it.z,
                     tcs ? tcs + blockIdx.x : sl.tc};
-  fused2d<P>(v, smem);
+  fused2d<P, false>(v, smem);
 }
 
 // Moments and status words of the listed filters (read before any is cleared:
