@@ -298,13 +298,19 @@ int pmf_sync(pmf_ctx* ctx) {
 
 int pmf_moments(pmf_ctx* ctx, double* mean_out, double* cov_out) {
   if (!ctx) return PMF_ERR_ARG;
-  int rc = check_status(ctx);
-  if (rc) return rc;
+  // one copy brings the moments and the status word (the copy waits for the stream)
+  FrameState h;
+  PMF_CUDA(ctx, cudaMemcpyAsync(&h, &ctx->st->f, sizeof(FrameState), cudaMemcpyDeviceToHost, ctx->stream));
+  PMF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (h.status != 0) {
+    const int zero = 0;
+    PMF_CUDA(ctx, cudaMemcpy(&ctx->st->f.status, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    return fail(ctx, h.status, h.status == PMF_ERR_DEGENERATE ? "degenerate normaliser: density left unchanged"
+                                                              : "device reported an error");
+  }
   const int n = ctx->cfg.nx;
-  DevState h;
-  PMF_CUDA(ctx, cudaMemcpy(&h, ctx->st, offsetof(DevState, pa), cudaMemcpyDeviceToHost));
-  if (mean_out) std::memcpy(mean_out, h.f.mean, sizeof(double) * n);
-  if (cov_out) std::memcpy(cov_out, h.f.cov, sizeof(double) * n * n);
+  if (mean_out) std::memcpy(mean_out, h.mean, sizeof(double) * n);
+  if (cov_out) std::memcpy(cov_out, h.cov, sizeof(double) * n * n);
   return PMF_OK;
 }
 

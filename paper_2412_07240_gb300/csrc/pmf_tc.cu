@@ -226,6 +226,14 @@ __device__ __noinline__ void build_interp_out(const RegridRows& rows, uint8_t* W
                                               int realign, int t0, int tstep) {
   build_interp<P>(rows, W, N, sctab, sw, realign, t0, tstep);
 }
+__device__ __noinline__ void regrid_rows_out(RegridRows& rows, double rs, double rd, int N, int t0, int tstep) {
+  regrid_rows(rows, rs, rd, N, t0, tstep);
+}
+template <int P>
+__device__ __noinline__ void issue_stage_out(uint32_t tmem, uint32_t a_base, int a_mn, uint32_t w_base, int nout,
+                                             int K, uint32_t mbar) {
+  issue_stage<P>(tmem, a_base, a_mn, w_base, nout, K, mbar);
+}
 template <int P>
 __device__ __noinline__ void stage_to_operand_out(uint8_t* A, const float* S, int nr, int nc, float s, int t0,
                                                   int tstep) {
@@ -538,10 +546,12 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       sa_first = op_scale<P>(block_max(sh, smax, 0));
       if constexpr (kOut) stage_to_operand_out<P>(A, S, N0, N1, sa_first, tid, kThreads);
       else stage_to_operand<P>(A, S, N0, N1, sa_first, tid, kThreads);
-    } else if (tid < kThreads / 2) {
-      regrid_rows(sh.rows[1], fs.rs[1], fs.rd[1], N1, tid, kThreads / 2);
     } else {
-      regrid_rows(sh.rows[0], fs.rs[0], fs.rd[0], N0, tid - kThreads / 2, kThreads / 2);
+      // axis 1 by the first half of the block, axis 0 by the second
+      const int a = tid < kThreads / 2 ? 1 : 0;
+      const int t0 = tid - (a ? 0 : kThreads / 2);
+      if constexpr (kOut) regrid_rows_out(sh.rows[a], fs.rs[a], fs.rd[a], a ? N1 : N0, t0, kThreads / 2);
+      else regrid_rows(sh.rows[a], fs.rs[a], fs.rd[a], a ? N1 : N0, t0, kThreads / 2);
     }
     __syncthreads();
   }
@@ -555,7 +565,8 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     __syncthreads();
     if (tid == 0) {
       tc_after_sync();
-      issue_stage<P>(tmem, su32(A), 0, su32(W), N1, N1, mb_mma);
+      if constexpr (kOut) issue_stage_out<P>(tmem, su32(A), 0, su32(W), N1, N1, mb_mma);
+      else issue_stage<P>(tmem, su32(A), 0, su32(W), N1, N1, mb_mma);
     }
     float inv_scale = 1.0f / (sa * sw);
 
@@ -658,7 +669,8 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
           // stage+1: F1 (K-major), R0 (MN), F0 (K), V0 (K), V1 (MN)
           const int a_mn = (P != PMF_PREC_TF32) && (stage == 1 || stage == 4);
           const int nn = (stage == 0 || stage == 4) ? N1 : N0;
-          issue_stage<P>(tmem, su32(A), a_mn, su32(W), nn, nn, mb_mma);
+          if constexpr (kOut) issue_stage_out<P>(tmem, su32(A), a_mn, su32(W), nn, nn, mb_mma);
+          else issue_stage<P>(tmem, su32(A), a_mn, su32(W), nn, nn, mb_mma);
         }
       }
       if (mat >= 0) ph_tma ^= 1;
