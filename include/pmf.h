@@ -79,6 +79,16 @@ enum {
  *           (the alternative time stepping named as future work in Sec. VII). */
 enum { PMF_PSI_EULER = 0, PMF_PSI_EXACT = 1 };
 
+/* Fill of a re-aligned frame (the regrid when the frame's whitened
+ * correlation exceeds realign_rho; Sec. V grid reshaping).
+ *   MULTILINEAR : multilinear interpolation of the old weights (any n_x).
+ *   SHEAR       : n_x = 2 only: the trigonometric interpolant (eq. interFreq)
+ *                 of the old weights at the new nodes, as two line-wise
+ *                 passes (per line: DFT, evaluation at that line's affine
+ *                 positions); spectrally accurate for densities well inside
+ *                 the box. */
+enum { PMF_REALIGN_MULTILINEAR = 0, PMF_REALIGN_SHEAR = 1 };
+
 /* Measurement functions h of eq. meas. */
 enum {
   PMF_MEAS_LINEAR = 0,          /* h(x) = H x, nz rows of H */
@@ -101,6 +111,7 @@ typedef struct pmf_config {
   double realign_rho;           /* whitened-correlation threshold for re-alignment (0.5) */
   int precision;                /* PMF_PREC_* */
   int psi_mode;                 /* PMF_PSI_* */
+  int realign_mode;             /* PMF_REALIGN_* (default MULTILINEAR) */
 } pmf_config;
 
 typedef struct pmf_meas {

@@ -22,8 +22,10 @@ notes of the repository):
     standard deviations of the predicted covariance pulled back by
     e^{-A tau}; per-axis rescale + recentre by the trigonometric interpolant
     (eq. interFreq), or, when the whitened correlation of the frame exceeds
-    ``realign_rho``, a re-aligned frame filled by multilinear interpolation;
-    points outside the old box get weight 0;
+    ``realign_rho``, a re-aligned frame filled by multilinear interpolation
+    (default) or, in the band-limited mode (n_x = 2), by two line-wise passes
+    of the trigonometric interpolant (shear_realign); points outside the old
+    box get weight 0;
   * the separable regrid is quantised: the centre moves by a multiple of 1/64
     of a node towards the mean and each axis scale by a factor with an 8-bit
     mantissa, so the grid geometry is exact in any precision and does not
@@ -90,6 +92,46 @@ def multilinear(P: np.ndarray, z: np.ndarray) -> np.ndarray:
     return out
 
 
+def shear_realign(P: np.ndarray, B: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Band-limited re-alignment of a 2-D grid: the trigonometric interpolant
+    (eq. interFreq) of the old weights P evaluated at u_old = B u_new + b, as
+    two line-wise passes (the affine map factored into a per-line 1-D affine
+    map along one axis, then one along the other):
+
+      pass 1, along axis q for each old node i of axis p:
+        h(i, v) = f(u_p = i, u_q = c_i + d v),
+        c_i = (B_qp / B_pp) (i - b_p) + b_q,   d = det(B) / B_pp;
+      pass 2, along axis p for each new node v of axis q:
+        P'(w, v) = h(u_p = B_pp w + B_pq v + b_p, v),
+
+    with (p, q) chosen to make the line-dependent shift of pass 1 the smaller
+    one: (0, 1) when |B_10 / B_00| <= |B_01 / B_11|, else (1, 0).  Each pass is
+    the 1-D interpolant at per-line positions, so it is exact for
+    trigonometric polynomials along its axis, and the whole map is exact on
+    them when B is triangular; positions outside the old box get weight 0.
+    """
+    N = P.shape
+    p, q = (0, 1) if abs(B[1, 0]) * abs(B[1, 1]) <= abs(B[0, 1]) * abs(B[0, 0]) else (1, 0)
+    Bpp, Bpq, Bqp, Bqq = B[p, p], B[p, q], B[q, p], B[q, q]
+    d = (Bpp * Bqq - Bpq * Bqp) / Bpp
+    Pp = np.moveaxis(P, p, 0)                     # [i (axis p), j (axis q)]
+    Np, Nq = Pp.shape
+    up, uq = grid_u(Np), grid_u(Nq)
+    H = np.empty((Np, Nq))
+    for i in range(Np):
+        pos = (Bqp / Bpp) * (up[i] - b[p]) + b[q] + d * uq      # u_q positions on line i
+        E = spectral.interp_matrix(Nq, pos + (Nq - 1) / 2.0)
+        E[np.abs(pos) > Nq / 2.0, :] = 0.0
+        H[i] = E @ Pp[i]
+    out = np.empty((Np, Nq))
+    for v in range(Nq):
+        pos = Bpp * up + Bpq * uq[v] + b[p]                      # u_p positions on column v
+        E = spectral.interp_matrix(Np, pos + (Np - 1) / 2.0)
+        E[np.abs(pos) > Np / 2.0, :] = 0.0
+        out[:, v] = E @ H[:, v]
+    return np.moveaxis(out, 0, p)
+
+
 SHIFT_QUANTUM = 1.0 / 64.0
 SCALE_MANTISSA_BITS = 8
 
@@ -117,9 +159,14 @@ def quantize_matrix(M: np.ndarray) -> np.ndarray:
 class OracleFilter:
     """Float64 spectral point-mass filter for one model (one state dimension n_x <= 4)."""
 
-    def __init__(self, cfg, psi_mode: str = "euler"):
+    def __init__(self, cfg, psi_mode: str = "euler", realign_mode: str = None):
         self.cfg = cfg
         self.n = cfg.nx
+        if realign_mode is None:
+            realign_mode = getattr(cfg, "realign_mode", "multilinear")
+        if realign_mode not in ("multilinear", "shear") or (realign_mode == "shear" and cfg.nx != 2):
+            raise ValueError("realign_mode: 'multilinear', or 'shear' for n_x = 2")
+        self.realign_mode = realign_mode
         self.N = tuple(int(v) for v in cfg.N)
         self.A = np.asarray(cfg.A, dtype=float)
         self.Q = np.asarray(cfg.Q, dtype=float)
@@ -207,10 +254,14 @@ class OracleFilter:
             Lp = np.linalg.cholesky(0.5 * (Ppred + Ppred.T))
             Mnew = quantize_matrix(Phinv @ Lp @ np.diag([2.0 * span / Nm for Nm in self.N]))
             m = self.c + self.M @ quantize_shift(Minv @ (m - self.c))
-            x = frame_points(m, Mnew, self.N)
-            u_old = (x - self.c[None, :]) @ Minv.T
-            zidx = u_old + (np.array(self.N) - 1) / 2.0
-            self.P = multilinear(self.P, zidx).reshape(self.N)
+            if self.realign_mode == "shear":
+                # u_old = Minv (c' + M' u_new - c) = B u_new + b
+                self.P = shear_realign(self.P, Minv @ Mnew, Minv @ (m - self.c))
+            else:
+                x = frame_points(m, Mnew, self.N)
+                u_old = (x - self.c[None, :]) @ Minv.T
+                zidx = u_old + (np.array(self.N) - 1) / 2.0
+                self.P = multilinear(self.P, zidx).reshape(self.N)
             realigned = True
         else:
             D = np.array([quantize_scale(2.0 * span * sd[a] / self.N[a]) for a in range(n)])

@@ -20,6 +20,7 @@ MAX_NZ = 3
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_DEGENERATE, ERR_TIMEOUT, ERR_ADMISSION, ERR_UNSUPPORTED = range(8)
 PREC = {"fp64": 0, "tf32": 1, "tf32x3": 2, "bf16x3": 3, "fp16x3": 4}
 PSI = {"euler": 0, "exact": 1}
+REALIGN = {"multilinear": 0, "shear": 1}
 MEAS = {"linear": 0, "range": 1, "bearing_linear3": 2}
 ERRNAMES = {1: "PMF_ERR_ARG", 2: "PMF_ERR_OOM", 3: "PMF_ERR_CUDA", 4: "PMF_ERR_DEGENERATE",
             5: "PMF_ERR_TIMEOUT", 6: "PMF_ERR_ADMISSION", 7: "PMF_ERR_UNSUPPORTED"}
@@ -43,7 +44,7 @@ class PmfConfig(C.Structure):
     _fields_ = [("nx", C.c_int), ("N", C.c_int * MAX_NX), ("A", C.c_double * 9), ("Q", C.c_double * 9),
                 ("m0", C.c_double * MAX_NX), ("P0", C.c_double * 9), ("span_sigma", C.c_double),
                 ("dt_sub", C.c_double), ("realign_rho", C.c_double), ("precision", C.c_int),
-                ("psi_mode", C.c_int)]
+                ("psi_mode", C.c_int), ("realign_mode", C.c_int)]
 
 
 class PmfMeas(C.Structure):
@@ -162,6 +163,7 @@ def make_config(cfg, precision="fp64", psi_mode="euler") -> PmfConfig:
     c.realign_rho = float(getattr(cfg, "realign_rho", 0.5))
     c.precision = PREC[precision] if isinstance(precision, str) else int(precision)
     c.psi_mode = PSI[psi_mode] if isinstance(psi_mode, str) else int(psi_mode)
+    c.realign_mode = REALIGN[getattr(cfg, "realign_mode", "multilinear")]
     return c
 
 

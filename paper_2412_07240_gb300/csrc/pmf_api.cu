@@ -29,6 +29,7 @@ struct pmf_ctx {
   double* hfwd[MAXN] = {nullptr, nullptr, nullptr};
   double* hinv[MAXN] = {nullptr, nullptr, nullptr};
   double* prior_aux = nullptr;  // P0^{-1} (9) and m0 (3)
+  double* scratch = nullptr;    // float64 path, shear re-alignment: intermediate grid
   TcTables tct{};               // tensor-core path tables (pmf_tc.cu)
   void* tab1 = nullptr;         // 1-D kernel table (pmf_tc1.cu)
   int mode1 = 0;                // 1-D Hartley form (autotuned)
@@ -83,6 +84,7 @@ void free_ctx(pmf_ctx* ctx) {
   tc_free_tables(&ctx->tct);
   tc3_free(ctx->tc3);
   cudaFree(ctx->tab1);
+  cudaFree(ctx->scratch);
   delete ctx;
 }
 
@@ -169,6 +171,7 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
   ALLOC(ctx->pend, sizeof(double) * 32);
   ALLOC(ctx->prior_aux, sizeof(double) * 16);
   if (ctx->path == 0) {
+    if (cfg->realign_mode == PMF_REALIGN_SHEAR) ALLOC(ctx->scratch, sizeof(double) * P);
     for (int a = 0; a < n; ++a) {
       const int N = cfg->N[a];
       ALLOC(ctx->interp[a], sizeof(double) * N * N);
@@ -241,8 +244,8 @@ int pmf_time_update(pmf_ctx* ctx, double tau) {
   }
   if (ctx->path == 0) {
     launch_time_f64(ctx->dims, ctx->tc, ctx->st, (double*)ctx->buf[0], (double*)ctx->buf[1],
-                    ctx->partials, ctx->pend, ctx->interp, ctx->hfwd, ctx->hinv, ctx->stream);
-    ctx->launches += launches_time_f64(ctx->cfg.nx);
+                    ctx->partials, ctx->pend, ctx->interp, ctx->hfwd, ctx->hinv, ctx->scratch, ctx->stream);
+    ctx->launches += launches_time_f64(ctx->cfg.nx) + (ctx->scratch ? 2 : 0);
   } else {
     ctx->launches += fast_step(ctx, nullptr, &ctx->tc);
   }

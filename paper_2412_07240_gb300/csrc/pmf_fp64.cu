@@ -193,14 +193,95 @@ __global__ void k_build_interp_f64(Dims d, const DevState* st, int axis, double*
   I[idx] = v == 0.0 ? 1.0 : sinpi(v) * cospi(v / N) / (N * sinpi(v / N));
 }
 
+// Band-limited re-alignment of a 2-D grid (shear mode), one of two line-wise
+// passes, one CTA per line.  With u_old = B u_new + b and (p, q) = (0, 1) if
+// |B_10 / B_00| <= |B_01 / B_11| else (1, 0) (the smaller line-dependent shift
+// in pass 1; exact on trigonometric polynomials when B is triangular):
+//   pass 1: lines along axis q through old node i of axis p, evaluated at
+//           u_q = (B_qp / B_pp)(u_i - b_p) + b_q + (det B / B_pp) v;
+//   pass 2: lines along axis p through new node v of axis q, evaluated at
+//           u_p = B_pp w + B_pq v + b_p, times the normaliser.
+// On each line: X_s = (1/N) sum_j f_j e^{-2 pi i j s / N} (s = 0..N/2) and the
+// trigonometric interpolant (eq. interFreq)
+//   p(x) = X_0 + 2 sum_{0<s<N/2} Re(X_s e^{2 pi i s x / N}) + X_{N/2} cos(pi x)
+// at x = u + (N-1)/2; positions outside the old box give 0.  Pass 1 reads
+// buf[cur] into scratch, pass 2 writes buf[cur^1].
+__global__ void k_shear_f64(Dims d, const DevState* st, int pass, double* b0, double* b1, double* scratch) {
+  extern __shared__ double sm[];
+  const FrameState& f = st->f;
+  if (!f.realign) return;
+  // pass order making pass 1's line-dependent shift the smaller: |B_10 / B_00| <= |B_01 / B_11|
+  const int p = fabs(f.B[2]) * fabs(f.B[3]) <= fabs(f.B[1]) * fabs(f.B[0]) ? 0 : 1, q = 1 - p;
+  const double Bpp = f.B[p * 2 + p], Bpq = f.B[p * 2 + q], Bqp = f.B[q * 2 + p], Bqq = f.B[q * 2 + q];
+  const int Np = d.N[p], Nq = d.N[q];
+  const int N = pass == 1 ? Nq : Np, H = N / 2;
+  const double* in = pass == 1 ? (f.cur ? b1 : b0) : scratch;
+  double* out = pass == 1 ? scratch : (f.cur ? b0 : b1);
+  const int line = blockIdx.x;
+  if (line >= (pass == 1 ? Np : Nq)) return;
+  // element (index along p, index along q) of the C-order 2-D grid
+  auto at = [&](int ip, int iq) -> long long {
+    return p == 0 ? (long long)ip * d.N[1] + iq : (long long)iq * d.N[1] + ip;
+  };
+  double* fl = sm;
+  double* Xr = fl + N;
+  double* Xi = Xr + H + 1;
+  double* cs = Xi + H + 1;
+  double* sn = cs + N;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    fl[t] = pass == 1 ? in[at(line, t)] : in[at(t, line)];
+    sincospi(2.0 * t / N, &sn[t], &cs[t]);
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s <= H; s += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    int r = 0;
+    for (int j = 0; j < N; ++j) {
+      re = fma(fl[j], cs[r], re);
+      im = fma(-fl[j], sn[r], im);
+      r += s;
+      if (r >= N) r -= N;
+    }
+    Xr[s] = re / N;
+    Xi[s] = im / N;
+  }
+  __syncthreads();
+  const double ul = line - 0.5 * ((pass == 1 ? Np : Nq) - 1);   // the line's fixed coordinate
+  const double ps = pass == 2 ? f.pscale : 1.0;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    const double ut = t - 0.5 * (N - 1);
+    const double pos = pass == 1 ? (Bqp / Bpp) * (ul - f.b[p]) + f.b[q] + (Bpp * Bqq - Bpq * Bqp) / Bpp * ut
+                                 : Bpp * ut + Bpq * ul + f.b[p];
+    double v = 0.0;
+    if (fabs(pos) <= 0.5 * N) {
+      const double x = pos + 0.5 * (N - 1);
+      double sx, cx;
+      sincospi(2.0 * x / N, &sx, &cx);
+      double zr = 1.0, zi = 0.0;   // e^{2 pi i s x / N}
+      v = Xr[0];
+      for (int k = 1; k < H; ++k) {
+        const double nr = zr * cx - zi * sx;
+        zi = zr * sx + zi * cx;
+        zr = nr;
+        v += 2.0 * (Xr[k] * zr - Xi[k] * zi);
+      }
+      v += Xr[H] * cospi(x);
+    }
+    if (pass == 1) out[at(line, t)] = v;
+    else out[at(t, line)] = ps * v;
+  }
+}
+
 // Stage 0 of the time update: multilinear re-alignment when the frame was
 // re-aligned, otherwise a scaled copy (both fold the normalisation scale in).
-__global__ void k_realign_f64(Dims d, const DevState* st, double* b0, double* b1) {
+// In the shear mode a re-aligned frame is filled by k_shear_f64 instead.
+__global__ void k_realign_f64(Dims d, const DevState* st, double* b0, double* b1, int mode) {
   const int cur = st->f.cur;
   const double* in = cur ? b1 : b0;
   double* out = cur ? b0 : b1;
   const double ps = st->f.pscale;
   const int n = d.nx;
+  if (st->f.realign && mode == PMF_REALIGN_SHEAR) return;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
        p += (long long)gridDim.x * blockDim.x) {
     if (!st->f.realign) {
@@ -472,13 +553,22 @@ void launch_meas_f64(const Dims& d, const MeasParams& mp, DevState* st, double* 
 
 void launch_time_f64(const Dims& d, const TimeConsts& tc, DevState* st, double* b0, double* b1,
                      double* partials, double* pend, double* const* interp,
-                     double* const* hfwd, double* const* hinv, cudaStream_t s) {
+                     double* const* hfwd, double* const* hinv, double* scratch, cudaStream_t s) {
   const int n = d.nx;
   k_frame<<<1, MAXL, 0, s>>>(tc, st, pend);
   for (int a = 0; a < n; ++a)
     k_build_interp_f64<<<grid_for((long long)d.N[a] * d.N[a], 256, 1 << 20), 256, 0, s>>>(
         d, st, a, interp[a]);
-  k_realign_f64<<<grid_for(d.P, 256, 4096), 256, 0, s>>>(d, st, b0, b1);
+  k_realign_f64<<<grid_for(d.P, 256, 4096), 256, 0, s>>>(d, st, b0, b1, tc.realign_mode);
+  if (tc.realign_mode == PMF_REALIGN_SHEAR && n == 2 && scratch) {
+    const int Nmax = d.N[0] > d.N[1] ? d.N[0] : d.N[1];
+    const size_t smem = sizeof(double) * (4 * (size_t)Nmax + 2);
+    cudaFuncSetAttribute(k_shear_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // pass 1 runs over the old nodes of axis p, pass 2 over the new nodes of axis q;
+    // both axis counts are launched and surplus CTAs of the shorter axis exit
+    k_shear_f64<<<Nmax, 128, smem, s>>>(d, st, 1, b0, b1, scratch);
+    k_shear_f64<<<Nmax, 128, smem, s>>>(d, st, 2, b0, b1, scratch);
+  }
   int stage = 1;
   auto gemm = [&](int a, const double* W) {
     const int N = d.N[a];

@@ -26,6 +26,7 @@ struct Dims {
 struct TimeConsts {
   int nx, l, exact;
   int N[MAXN];
+  int realign_mode;  // PMF_REALIGN_*
   double tau, dt, g, span, rho_max;
   double Q[9];       // diffusion
   double Phi[9];     // e^{A tau}

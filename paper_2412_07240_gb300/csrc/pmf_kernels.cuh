@@ -18,7 +18,7 @@ void launch_meas_f64(const Dims& d, const MeasParams& mp, DevState* st, double* 
                      double* partials, cudaStream_t s);
 void launch_time_f64(const Dims& d, const TimeConsts& tc, DevState* st, double* b0, double* b1,
                      double* partials, double* pend, double* const* interp,
-                     double* const* hfwd, double* const* hinv, cudaStream_t s);
+                     double* const* hfwd, double* const* hinv, double* scratch, cudaStream_t s);
 void launch_export_f64(const Dims& d, const DevState* st, const double* b0, const double* b1,
                        double* out, cudaStream_t s);
 

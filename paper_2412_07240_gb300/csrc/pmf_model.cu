@@ -68,6 +68,7 @@ int time_consts(const pmf_config& c, double tau, TimeConsts* tc, std::string* wh
   tc->tau = tau;
   tc->dt = tau / l;
   tc->exact = c.psi_mode == PMF_PSI_EXACT;
+  tc->realign_mode = c.realign_mode;
   tc->span = c.span_sigma;
   tc->rho_max = c.realign_rho;
   double At[9], mAt[9], mAdt[9];
@@ -149,6 +150,14 @@ int validate_config(const pmf_config* c, std::string* why) {
   if (!(c->span_sigma > 0) || !(c->dt_sub > 0) || !(c->realign_rho > 0)) { *why = "span, dt_sub, rho must be > 0"; return PMF_ERR_ARG; }
   if (c->precision < PMF_PREC_FP64 || c->precision > PMF_PREC_FP16X3) { *why = "unknown precision"; return PMF_ERR_ARG; }
   if (c->psi_mode != PMF_PSI_EULER && c->psi_mode != PMF_PSI_EXACT) { *why = "unknown psi mode"; return PMF_ERR_ARG; }
+  if (c->realign_mode != PMF_REALIGN_MULTILINEAR && c->realign_mode != PMF_REALIGN_SHEAR) {
+    *why = "unknown re-alignment mode";
+    return PMF_ERR_ARG;
+  }
+  if (c->realign_mode == PMF_REALIGN_SHEAR && c->nx != 2) {
+    *why = "shear re-alignment is defined for n_x = 2";
+    return PMF_ERR_ARG;
+  }
   return PMF_OK;
 }
 

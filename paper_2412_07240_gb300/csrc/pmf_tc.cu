@@ -240,6 +240,80 @@ __device__ __noinline__ void stage_to_operand_out(uint8_t* A, const float* S, in
   stage_to_operand<P>(A, S, nr, nc, s, t0, tstep);
 }
 
+// Band-limited re-alignment on the staging tile (shear mode): the two
+// line-wise passes of the float64 path (k_shear_f64: the trigonometric
+// interpolant of eq. interFreq of each line, evaluated at that line's affine
+// positions) in float32, all lines of a pass at once; the lines' DFT
+// coefficients go to C ((lines) x (N + 2) floats, the free operand regions).
+// Twiddles e^{2 pi i r / N} come exactly from the (cos, sin)(pi m / N) tables;
+// an evaluation point x = m + f takes e^{2 pi i x / N} from the table entry of
+// m and sincospi of f, then powers by recurrence.  Returns this thread's
+// max |weight| of the re-aligned tile.
+__device__ __noinline__ float shear_stage(const Shared& sh, float* S, float* C, int N0, int N1) {
+  const FrameState& fs = sh.fs;
+  // pass order making pass 1's line-dependent shift the smaller: |B_10 / B_00| <= |B_01 / B_11|
+  const int p = fabs(fs.B[2]) * fabs(fs.B[3]) <= fabs(fs.B[1]) * fabs(fs.B[0]) ? 0 : 1, q = 1 - p;
+  const double Bpp = fs.B[p * 2 + p], Bpq = fs.B[p * 2 + q], Bqp = fs.B[q * 2 + p], Bqq = fs.B[q * 2 + q];
+  const float r1 = (float)(Bqp / Bpp), d1 = (float)((Bpp * Bqq - Bpq * Bqp) / Bpp);
+  const float bp = (float)fs.b[p], bq = (float)fs.b[q], fpp = (float)Bpp, fpq = (float)Bpq;
+  const int Np = p ? N1 : N0, Nq = q ? N1 : N0;
+  auto at = [&](int ip, int iq) { return p == 0 ? ip * kSStr + iq : iq * kSStr + ip; };
+  float smax = 0.0f;
+  for (int pass = 1; pass <= 2; ++pass) {
+    const int L = pass == 1 ? Np : Nq, N = pass == 1 ? Nq : Np, H = N / 2;
+    const float* sct = sh.sct[pass == 1 ? q : p];
+    const float rN = 1.0f / (float)N;
+    for (int it = threadIdx.x; it < L * (H + 1); it += kThreads) {
+      const int line = it / (H + 1), sidx = it - line * (H + 1);
+      float re = 0.0f, im = 0.0f;
+      int r = 0;
+      for (int j = 0; j < N; ++j) {
+        const float fj = pass == 1 ? S[at(line, j)] : S[at(j, line)];
+        const int m = 2 * r <= N ? 2 * r : 2 * r - 2 * N;   // 2 pi r / N = pi m / N
+        re = fmaf(fj, sct[2 * (m + N)], re);
+        im = fmaf(-fj, sct[2 * (m + N) + 1], im);
+        r += sidx;
+        if (r >= N) r -= N;
+      }
+      C[line * (N + 2) + 2 * sidx] = re * rN;
+      C[line * (N + 2) + 2 * sidx + 1] = im * rN;
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < L * N; it += kThreads) {
+      const int line = it / N, t = it - line * N;
+      const float ul = line - 0.5f * (L - 1), ut = t - 0.5f * (N - 1);
+      const float pos = pass == 1 ? fmaf(d1, ut, fmaf(r1, ul - bp, bq)) : fmaf(fpp, ut, fmaf(fpq, ul, bp));
+      float v = 0.0f;
+      if (fabsf(pos) <= 0.5f * N) {
+        const float x = pos + 0.5f * (N - 1);
+        const float mf = rintf(x), fr = x - mf;
+        int mi = (int)mf % N;
+        if (mi < 0) mi += N;
+        const int mm = 2 * mi <= N ? 2 * mi : 2 * mi - 2 * N;
+        const float cm = sct[2 * (mm + N)], sm = sct[2 * (mm + N) + 1];
+        float sf, cf;
+        sincospif(2.0f * fr * rN, &sf, &cf);
+        const float wr = cm * cf - sm * sf, wi = cm * sf + sm * cf;   // e^{2 pi i x / N}
+        const float* X = C + line * (N + 2);
+        float zr = 1.0f, zi = 0.0f;
+        v = X[0];
+        for (int k = 1; k < H; ++k) {
+          const float nr = zr * wr - zi * wi;
+          zi = zr * wi + zi * wr;
+          zr = nr;
+          v += 2.0f * (X[2 * k] * zr - X[2 * k + 1] * zi);
+        }
+        v += X[2 * H] * ((((int)mf) & 1) ? -cospif(fr) : cospif(fr));   // cos(pi x)
+      }
+      if (pass == 1) S[at(line, t)] = v;
+      else S[at(t, line)] = v;
+      if (pass == 2) smax = fmaxf(smax, fabsf(v));
+    }
+    __syncthreads();
+  }
+  return smax;
+}
+
 // Diffusion multiplier and trace factor in the Hartley domain (Sec. V-B
 // algorithm steps 2-4) on the staging tile T[k1][k0], one thread per orbit
 // {(+-k0, +-k1)}: with S_s the four separable coefficients (bit 0 of s flips
@@ -514,7 +588,13 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       sh.pa[q][1] = (float)pa[1];
       sh.pb[q] = (float)pb[0];
     }
-    if (realign) {
+    if (realign && sh.tc.realign_mode == PMF_REALIGN_SHEAR) {
+      // band-limited re-alignment in place on the staging tile
+      smax = shear_stage(sh, S, (float*)A, N0, N1);
+      sa_first = op_scale<P>(block_max(sh, smax, 0));
+      if constexpr (kOut) stage_to_operand_out<P>(A, S, N0, N1, sa_first, tid, kThreads);
+      else stage_to_operand<P>(A, S, N0, N1, sa_first, tid, kThreads);
+    } else if (realign) {
       // multilinear re-alignment: gather into the (free) W region, copy back
       float* G = (float*)W;
       const int npts = N0 * N1;

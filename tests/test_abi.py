@@ -40,7 +40,7 @@ def test_config_defaults_and_struct_layout():
     assert c.span_sigma == 6.0 and c.dt_sub == 0.01 and c.realign_rho == 0.5
     assert c.precision == 0 and c.psi_mode == 0
     # int nx, int N[3] | A, Q | m0 | P0 | span, dt_sub, rho | precision, psi_mode
-    assert ctypes.sizeof(_binding.PmfConfig) == 16 + 72 + 72 + 24 + 72 + 24 + 8
+    assert ctypes.sizeof(_binding.PmfConfig) == 16 + 72 + 72 + 24 + 72 + 24 + 8 + 8   # realign_mode + padding
 
 
 def test_invalid_config_rejected_without_gpu():

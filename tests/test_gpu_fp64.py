@@ -75,3 +75,14 @@ def test_invalid_measurement_rejected():
         f.meas_update(sc.meas, np.array([np.nan]))
     m0, _ = f.moments()
     assert np.all(np.isfinite(m0))
+
+
+def test_2d_shear_realignment_path():
+    cfg = FilterConfig(nx=2, N=(40, 48), A=np.array([[0.0, 1.0], [0.0, 0.0]]), Q=np.diag([0.01, 0.1]),
+                       m0=np.array([0.0, 1.0]), P0=np.diag([0.5, 0.5]), realign_mode="shear")
+    meas = MeasModel("linear", R=np.array([[0.3 ** 2]]), H=np.array([[1.0, 0.0]]))
+    sc = Scenario("cv", cfg, meas, dt=0.2, epochs=6)
+    sc.truth, sc.z = simulate(cfg, meas, sc.dt, sc.epochs, seed=11)
+    worst, log = max_errors(sc)
+    assert any(s.endswith("R") for s, _ in log), "re-alignment not exercised"
+    _check(worst, 1e-11)

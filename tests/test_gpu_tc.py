@@ -74,3 +74,29 @@ def test_unsupported_sizes_are_rejected():
     sc = w.small_2d_scenario(N=(40, 48))
     with pytest.raises(Unsupported):
         Filter(sc.cfg, precision="fp16x3")
+
+
+def test_shear_realignment_fp16x3():
+    cfg = FilterConfig(nx=2, N=(48, 64), A=np.array([[0.0, 1.0], [0.0, 0.0]]), Q=np.diag([0.01, 0.1]),
+                       m0=np.array([0.0, 1.0]), P0=np.diag([0.5, 0.5]), realign_mode="shear")
+    meas = MeasModel("linear", R=np.array([[0.3 ** 2]]), H=np.array([[1.0, 0.0]]))
+    sc = Scenario("cv", cfg, meas, dt=0.2, epochs=6)
+    sc.truth, sc.z = simulate(cfg, meas, sc.dt, sc.epochs, seed=11)
+    worst, log = max_errors(sc, precision="fp16x3")
+    assert any(s.endswith("R") for s, _ in log), "re-alignment not exercised"
+    _check(worst, "fp16x3")
+
+
+def test_shear_realignment_batch_equals_single():
+    from paper_2412_07240_gb300 import Batch, Filter
+    cfg = FilterConfig(nx=2, N=(48, 64), A=np.array([[0.0, 1.0], [0.0, 0.0]]), Q=np.diag([0.01, 0.1]),
+                       m0=np.array([0.0, 1.0]), P0=np.diag([0.5, 0.5]), realign_mode="shear")
+    meas = MeasModel("linear", R=0.3 ** 2 * np.eye(2), H=np.eye(2))
+    sc = Scenario("cv", cfg, meas, dt=0.2, epochs=6)
+    sc.truth, sc.z = simulate(cfg, meas, sc.dt, sc.epochs, seed=11)
+    b = Batch([cfg], [meas])
+    g = Filter(cfg, precision="fp16x3")
+    for k in range(sc.epochs):
+        b.step([0], sc.z[k][None, :], sc.dt)
+        g.step(meas, sc.z[k], sc.dt)
+    assert np.array_equal(b.pdf(0)[0], g.pdf()[0])

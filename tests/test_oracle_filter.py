@@ -207,3 +207,57 @@ def test_regrid_quantisation():
         if q >= 1 / 8:
             assert np.array_equal(y.astype(np.float32).astype(np.float64), y)
     assert of.quantize_scale(1.0 + 1e-4) == 1.0 and of.quantize_shift(np.array([1e-3]))[0] == 0.0
+
+
+def _trig_field(N):
+    u = of.grid_u(N)
+    U0, U1 = np.meshgrid(u, u, indexing="ij")
+    f = lambda a, b: (1.0 + 0.3 * np.cos(2 * np.pi * 2 * a / N + 0.4) + 0.2 * np.sin(2 * np.pi * (a + 3 * b) / N)
+                      + 0.1 * np.cos(2 * np.pi * 5 * b / N - 1.0))
+    return U0, U1, f
+
+
+@pytest.mark.parametrize("B", [[[0.7, 0.0], [0.35, 0.8]], [[0.9, 0.0], [0.35, 0.8]],
+                               [[0.8, 0.3], [0.0, 0.7]], [[0.7, 0.3], [0.0, 0.9]]])
+def test_shear_realign_exact_on_trig_polynomials(B):
+    """A triangular map is two exact 1-D resamplings of a trigonometric polynomial
+    (both pass orders are exercised); points that stay inside the old box match
+    the polynomial at the mapped positions to round-off."""
+    B = np.array(B)
+    b = np.array([0.3, -0.45])
+    U0, U1, f = _trig_field(32)
+    out = of.shear_realign(f(U0, U1), B, b)
+    Z0, Z1 = B[0, 0] * U0 + B[0, 1] * U1 + b[0], B[1, 0] * U0 + B[1, 1] * U1 + b[1]
+    inside = (np.abs(Z0) <= 16) & (np.abs(Z1) <= 16)
+    assert np.abs(out - f(Z0, Z1))[inside].max() < 1e-12
+
+
+def test_shear_realign_spectral_on_gaussians():
+    """A general (sheared) map of a correlated Gaussian inside a +-6 sigma box: the
+    band-limited fill is at the box's floor at 32 nodes, multilinear is O(h^2)."""
+    B, b = np.array([[0.9, 0.35], [-0.3, 0.8]]), np.array([0.3, -0.45])
+    for N, ml_floor in ((32, 1e-2), (64, 5e-3)):
+        u = of.grid_u(N)
+        U0, U1 = np.meshgrid(u, u, indexing="ij")
+        s = N / 12.0
+        g = lambda a, c: np.exp(-0.5 * (a ** 2 + 0.8 * a * c + c ** 2) / s ** 2)
+        Z0, Z1 = B[0, 0] * U0 + B[0, 1] * U1 + b[0], B[1, 0] * U0 + B[1, 1] * U1 + b[1]
+        ex = g(Z0, Z1)
+        sh = of.shear_realign(g(U0, U1), B, b)
+        ml = of.multilinear(g(U0, U1), np.stack([Z0.ravel(), Z1.ravel()], 1) + (N - 1) / 2).reshape(N, N)
+        assert np.abs(sh - ex).max() / ex.max() < 1e-6
+        assert np.abs(ml - ex).max() / ex.max() > ml_floor
+
+
+def test_shear_realignment_tracks_kalman():
+    """Constant-velocity model with re-alignments: the band-limited fill keeps the
+    filter at the Kalman moments (exact-in-time multiplier) where multilinear
+    interpolation loses three orders of magnitude."""
+    sc = _cv_scenario((64, 64))
+    sc.cfg.realign_mode = "shear"
+    es, rs = _kalman_errors(sc, "exact")
+    sc.cfg.realign_mode = "multilinear"
+    em, rm = _kalman_errors(sc, "exact")
+    assert rs >= 3 and rm >= 3
+    assert es[6:].max() < 1e-5
+    assert es[6:].max() < em[6:].max() / 1e3

@@ -41,7 +41,8 @@ class FilterConfig:
     half-width of the grid in standard deviations, ``dt_sub`` the Euler
     sub-step bound (l = ceil(dt / dt_sub) sub-steps per time update) and
     ``realign_rho`` the whitened-correlation threshold above which the grid
-    frame is re-aligned to the predicted covariance.
+    frame is re-aligned to the predicted covariance, ``realign_mode`` how the
+    re-aligned frame is filled ("multilinear", or "shear" for n_x = 2).
     """
     nx: int
     N: tuple
@@ -52,6 +53,7 @@ class FilterConfig:
     span: float = 6.0
     dt_sub: float = 0.01
     realign_rho: float = 0.5
+    realign_mode: str = "multilinear"
 
 
 @dataclass
