@@ -37,7 +37,8 @@
 extern "C" {
 #endif
 
-#define PMF_MAX_NX 3
+#define PMF_MAX_NX 4
+#define PMF_MEAS_NPARAM 24
 #define PMF_MAX_NZ 3
 #define PMF_MAX_SUBSTEPS 64
 
@@ -63,7 +64,8 @@ enum {
  * Everything else of a step runs in float32 on the non-FP64 paths, with the
  * frame, the normalisation constant and the moment combination in float64.
  * For n_x = 1 every precision other than FP64 selects the float32 CUDA-core
- * kernel (a 1-D transform is a matrix-vector product, not a tensor-core tile). */
+ * kernel (a 1-D transform is a matrix-vector product, not a tensor-core tile).
+ * n_x = 4 runs on the FP64 path only. */
 enum {
   PMF_PREC_FP64 = 0,
   PMF_PREC_TF32 = 1,
@@ -94,7 +96,14 @@ enum {
   PMF_MEAS_LINEAR = 0,          /* h(x) = H x, nz rows of H */
   PMF_MEAS_RANGE = 1,           /* h(x) = sqrt(x1^2 + x2^2), nz = 1 */
   PMF_MEAS_BEARING_LINEAR3 = 2  /* h(x) = [atan2(x2, x1), x3], nz = 2; the bearing
-                                   residual is wrapped to (-pi, pi] */
+                                   residual is wrapped to (-pi, pi] */,
+  PMF_MEAS_TERRAIN_GM = 3       /* n_x = 4, state [p_x, v_x, p_y, v_y], nz = 1:
+                                   h(x) = p[16] + sum_{i<4} p[4i] sin(p[4i+1] p_x
+                                          + p[4i+2] p_y + p[4i+3]) (a smooth
+                                   terrain altitude), noise a two-component
+                                   Gaussian mixture: weight p[17] (the other
+                                   1 - p[17]), means p[18], p[19], variances
+                                   p[20], p[21] (Sec. VI); R is not used */
 };
 
 typedef struct pmf_config {
@@ -120,6 +129,7 @@ typedef struct pmf_meas {
   double z[PMF_MAX_NZ];         /* measurement */
   double R[PMF_MAX_NZ * PMF_MAX_NZ];   /* noise covariance, symmetric PD, nz x nz packed */
   double H[PMF_MAX_NZ * PMF_MAX_NX];   /* LINEAR only: nz x nx row-major packed */
+  double p[PMF_MEAS_NPARAM];    /* parameters of the model kinds that need them */
 } pmf_meas;
 
 typedef struct pmf_ctx pmf_ctx;

@@ -214,13 +214,18 @@ class OracleFilter:
     def meas_update(self, meas, z) -> None:
         """Posterior weights: predictive weights times the likelihood, normalised.
 
-        The likelihood exp(-1/2 r^T R^{-1} r) is shifted by its smallest
+        The likelihood exp(-1/2 r^T R^{-1} r) (or, for the terrain measurement,
+        the Gaussian-mixture density of Sec. VI) is shifted by its smallest
         exponent over the grid (a constant factor, removed by normalisation).
         """
         x = self.points()
-        r = model.residual(meas.kind, z, x, meas.H)
-        Ri = np.linalg.inv(meas.R)
-        e = 0.5 * np.einsum("pi,ij,pj->p", r, Ri, r)
+        params = getattr(meas, "params", None)
+        r = model.residual(meas.kind, np.atleast_1d(z), x, meas.H, params)
+        if meas.kind == "terrain_gm":
+            e = model.gm_neg_log_lik(r[:, 0], params)     # -log of the mixture likelihood
+        else:
+            Ri = np.linalg.inv(meas.R)
+            e = 0.5 * np.einsum("pi,ij,pj->p", r, Ri, r)
         lik = np.exp(-(e - e.min()))
         old = self.P
         self.P = self.P * lik.reshape(self.N)

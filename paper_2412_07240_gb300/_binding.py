@@ -14,14 +14,15 @@ import numpy as np
 
 from . import build as _build
 
-MAX_NX = 3
+MAX_NX = 4
 MAX_NZ = 3
+MEAS_NPARAM = 24
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_DEGENERATE, ERR_TIMEOUT, ERR_ADMISSION, ERR_UNSUPPORTED = range(8)
 PREC = {"fp64": 0, "tf32": 1, "tf32x3": 2, "bf16x3": 3, "fp16x3": 4}
 PSI = {"euler": 0, "exact": 1}
 REALIGN = {"multilinear": 0, "shear": 1}
-MEAS = {"linear": 0, "range": 1, "bearing_linear3": 2}
+MEAS = {"linear": 0, "range": 1, "bearing_linear3": 2, "terrain_gm": 3}
 ERRNAMES = {1: "PMF_ERR_ARG", 2: "PMF_ERR_OOM", 3: "PMF_ERR_CUDA", 4: "PMF_ERR_DEGENERATE",
             5: "PMF_ERR_TIMEOUT", 6: "PMF_ERR_ADMISSION", 7: "PMF_ERR_UNSUPPORTED"}
 
@@ -41,15 +42,17 @@ class Unsupported(PmfError):
 
 
 class PmfConfig(C.Structure):
-    _fields_ = [("nx", C.c_int), ("N", C.c_int * MAX_NX), ("A", C.c_double * 9), ("Q", C.c_double * 9),
-                ("m0", C.c_double * MAX_NX), ("P0", C.c_double * 9), ("span_sigma", C.c_double),
+    _fields_ = [("nx", C.c_int), ("N", C.c_int * MAX_NX), ("A", C.c_double * (MAX_NX * MAX_NX)),
+                ("Q", C.c_double * (MAX_NX * MAX_NX)), ("m0", C.c_double * MAX_NX),
+                ("P0", C.c_double * (MAX_NX * MAX_NX)), ("span_sigma", C.c_double),
                 ("dt_sub", C.c_double), ("realign_rho", C.c_double), ("precision", C.c_int),
                 ("psi_mode", C.c_int), ("realign_mode", C.c_int)]
 
 
 class PmfMeas(C.Structure):
     _fields_ = [("kind", C.c_int), ("nz", C.c_int), ("z", C.c_double * MAX_NZ),
-                ("R", C.c_double * 9), ("H", C.c_double * 9)]
+                ("R", C.c_double * (MAX_NZ * MAX_NZ)), ("H", C.c_double * (MAX_NZ * MAX_NX)),
+                ("p", C.c_double * MEAS_NPARAM)]
 
 
 # (name, restype, argtypes) of every entry point declared in include/pmf.h
@@ -178,6 +181,9 @@ def make_meas(meas, z, nx) -> PmfMeas:
     _fill(m.R, R, nz * nz)
     if meas.H is not None:
         _fill(m.H, meas.H, nz * nx)
+    params = getattr(meas, "params", None)
+    if params is not None:
+        _fill(m.p, params, len(np.ravel(params)))
     return m
 
 

@@ -25,10 +25,10 @@ struct pmf_ctx {
   void* buf[2] = {nullptr, nullptr};
   double* partials = nullptr;
   double* pend = nullptr;
-  double* interp[MAXN] = {nullptr, nullptr, nullptr};
-  double* hfwd[MAXN] = {nullptr, nullptr, nullptr};
-  double* hinv[MAXN] = {nullptr, nullptr, nullptr};
-  double* prior_aux = nullptr;  // P0^{-1} (9) and m0 (3)
+  double* interp[MAXN] = {};
+  double* hfwd[MAXN] = {};
+  double* hinv[MAXN] = {};
+  double* prior_aux = nullptr;  // P0^{-1} (n*n) and m0 at kAuxM0
   double* scratch = nullptr;    // float64 path, shear re-alignment: intermediate grid
   TcTables tct{};               // tensor-core path tables (pmf_tc.cu)
   void* tab1 = nullptr;         // 1-D kernel table (pmf_tc1.cu)
@@ -152,6 +152,16 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
       return rc;
     }
     ctx->path = cfg->nx == 1 ? 3 : cfg->nx == 3 ? 2 : 1;
+  } else {
+    // the float64 per-axis transforms tile lines 16 x 16 with the leading axes
+    // on grid.z and the last axis' lines on grid.y (each at most 65535)
+    long long lead = 1;
+    for (int a = 0; a + 1 < n; ++a) lead *= cfg->N[a];
+    const long long lead_but_one = lead / cfg->N[n - 2 < 0 ? 0 : n - 2];
+    if ((lead + 15) / 16 > 65535 || (n > 1 && lead_but_one > 65535)) {
+      free_ctx(ctx);
+      return PMF_ERR_UNSUPPORTED;
+    }
   }
 
 #define ALLOC(ptr, bytes)                                     \
@@ -167,9 +177,9 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
   const size_t elem = ctx->path == 0 ? sizeof(double) : sizeof(float);
   ALLOC(ctx->buf[0], P * elem);
   ALLOC(ctx->buf[1], P * elem);
-  ALLOC(ctx->partials, sizeof(double) * 10 * 4096);
-  ALLOC(ctx->pend, sizeof(double) * 32);
-  ALLOC(ctx->prior_aux, sizeof(double) * 16);
+  ALLOC(ctx->partials, sizeof(double) * kMomentSlots * 4096);
+  ALLOC(ctx->pend, sizeof(double) * kPendSize);
+  ALLOC(ctx->prior_aux, sizeof(double) * kAuxSize);
   if (ctx->path == 0) {
     if (cfg->realign_mode == PMF_REALIGN_SHEAR) ALLOC(ctx->scratch, sizeof(double) * P);
     for (int a = 0; a < n; ++a) {
@@ -203,9 +213,9 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
 
   // initial frame c = m0, M = chol(P0) diag(2 span / N)
   DevState h = initial_state(*cfg);
-  double aux[16] = {0};
+  double aux[kAuxSize] = {0};
   inv(n, cfg->P0, aux);
-  for (int a = 0; a < n; ++a) aux[9 + a] = cfg->m0[a];
+  for (int a = 0; a < n; ++a) aux[kAuxM0 + a] = cfg->m0[a];
   cudaError_t e = cudaMemcpyAsync(ctx->st, &h, sizeof(DevState), cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ctx->prior_aux, aux, sizeof(aux), cudaMemcpyHostToDevice, ctx->stream);
@@ -214,7 +224,7 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
     return PMF_ERR_CUDA;
   }
   if (ctx->path == 0) {
-    launch_prior_f64(ctx->dims, ctx->st, ctx->prior_aux, ctx->prior_aux + 9, (double*)ctx->buf[0],
+    launch_prior_f64(ctx->dims, ctx->st, ctx->prior_aux, ctx->prior_aux + kAuxM0, (double*)ctx->buf[0],
                      ctx->stream);
     launch_moments_f64(ctx->dims, ctx->st, 0, (double*)ctx->buf[0], (double*)ctx->buf[1],
                        ctx->partials, 0, 0, nullptr, ctx->stream);
@@ -443,7 +453,7 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
   long long bytes = wfloats * 4 + (long long)count * (sizeof(DevState) + sizeof(MeasParams) +
                                                        sizeof(TimeConsts) + sizeof(FilterSlot) +
                                                        sizeof(StepItem) + sizeof(int) + 8 * sizeof(double)) +
-                    sizeof(double) * (10 * 4096 + 16 * (long long)count);
+                    sizeof(double) * (kMomentSlots * 4096 + 16 * (long long)count);
   for (int N : sizes) bytes += (long long)tc_axis_table_bytes(N, prec);
   if (hbm_budget && (size_t)bytes > hbm_budget) return PMF_ERR_ADMISSION;
 
@@ -468,8 +478,8 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
   BALLOC(b->d_tc, sizeof(TimeConsts) * count);
   BALLOC(b->d_slots, sizeof(FilterSlot) * count);
   BALLOC(b->d_items, sizeof(StepItem) * count);
-  BALLOC(b->d_partials, sizeof(double) * 10 * 4096);
-  BALLOC(b->d_aux, sizeof(double) * 16 * count);
+  BALLOC(b->d_partials, sizeof(double) * kMomentSlots * 4096);
+  BALLOC(b->d_aux, sizeof(double) * kAuxSize * count);
   BALLOC(b->d_ids, sizeof(int) * count);
   BALLOC(b->d_gather, sizeof(double) * 8 * count);
 #undef BALLOC
@@ -498,15 +508,15 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
   b->tables = tabs;
   std::vector<DevState> hst(count);
   std::vector<FilterSlot> slots(count);
-  std::vector<double> aux(16 * (size_t)count, 0.0);
+  std::vector<double> aux(kAuxSize * (size_t)count, 0.0);
   long long off = 0;
   b->npts.resize(count);
   for (int i = 0; i < count; ++i) {
     const pmf_config& c = cfgs[i];
     hst[i] = initial_state(c);
-    inv(2, c.P0, &aux[16 * i]);
-    aux[16 * i + 9] = c.m0[0];
-    aux[16 * i + 10] = c.m0[1];
+    inv(2, c.P0, &aux[kAuxSize * i]);
+    aux[kAuxSize * i + kAuxM0] = c.m0[0];
+    aux[kAuxSize * i + kAuxM0 + 1] = c.m0[1];
     const long long P = (long long)c.N[0] * c.N[1];
     b->npts[i] = P;
     FilterSlot& sl = slots[i];
@@ -535,7 +545,7 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
     d.N[1] = cfgs[i].N[1];
     d.N[2] = 1;
     d.P = b->npts[i];
-    b->launches += tc_prior(d, b->d_st + i, b->d_aux + 16 * i, slots[i].buf0, b->d_partials, b->stream);
+    b->launches += tc_prior(d, b->d_st + i, b->d_aux + kAuxSize * i, slots[i].buf0, b->d_partials, b->stream);
   }
   if (cudaStreamSynchronize(b->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
     free_batch(b);

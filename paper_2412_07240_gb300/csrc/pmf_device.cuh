@@ -6,6 +6,7 @@
 
 namespace pmf {
 
+
 // ---------------------------------------------------------------------------
 // Fixed-size float64 helpers (n <= 3, fully unrolled, registers only).  On
 // GB300 a dependent float64 FMA costs ~64 cycles and a division ~430, so the
@@ -44,6 +45,7 @@ __device__ __forceinline__ void cong_t(const double* A, const double* S, double*
 
 template <int n>
 __device__ __forceinline__ double det_t(const double* A) {
+  if (n == 4) return det(4, A);
   if (n == 1) return A[0];
   if (n == 2) return A[0] * A[3] - A[1] * A[2];
   return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
@@ -53,6 +55,10 @@ __device__ __forceinline__ double det_t(const double* A) {
 // Inverse by the adjugate and one reciprocal of the determinant.
 template <int n>
 __device__ __forceinline__ void inv_t(const double* A, double* Ai) {
+  if (n == 4) {
+    inv(4, A, Ai);
+    return;
+  }
   const double r = 1.0 / det_t<n>(A);
   if (n == 1) {
     Ai[0] = r;
@@ -208,10 +214,10 @@ __device__ inline void frame_scalar(const TimeConsts& tc, FrameState* st, double
   }
 #pragma unroll
   for (int i = 0; i < n * n; ++i) {
-    pend[3 + i] = nM[i];
-    pend[12 + i] = nMi[i];
+    pend[pend_M(n) + i] = nM[i];
+    pend[pend_Mi(n) + i] = nMi[i];
   }
-  pend[21] = fabs(det_t<n>(nM));
+  pend[pend_V(n)] = fabs(det_t<n>(nM));
 }
 
 // Diffusion coefficients of sub-step q in the new frame (any thread):
@@ -226,23 +232,22 @@ __device__ inline void frame_substep(const TimeConsts& tc, const double* Mpi, in
   for (int a = 0; a < n; ++a)
 #pragma unroll
     for (int b = 0; b < n; ++b) {
-      const int lo = a < b ? a : b, hi = a < b ? b : a;
-      const int k = lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);   // packed 00,01,02,11,12,22
-      Qt[a * n + b] = src ? src[a * n + b] : tc.Qt[q][k];
+      Qt[a * n + b] = src ? src[a * n + b] : tc.Qt[q][packed_sym(a, b)];
     }
   cong_t<n>(Mpi, Qt, Qu);
   const double w = tc.exact ? 1.0 : tc.dt;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) pa[a] = a < n ? 0.5 * w * Qu[(a < n ? a : 0) * (n + 1)] : 0.0;
-  pb[0] = n > 1 ? w * Qu[1 % (n * n)] : 0.0;
-  pb[1] = n > 2 ? w * Qu[2 % (n * n)] : 0.0;
-  pb[2] = n > 2 ? w * Qu[5 % (n * n)] : 0.0;
+  for (int a = 0; a < 4; ++a) pa[a] = a < n ? 0.5 * w * Qu[(a < n ? a : 0) * (n + 1)] : 0.0;
+  // cross pairs 01, 02, 12, 03, 13, 23
+  const int pi[6] = {0, 0, 1, 0, 1, 2}, pj[6] = {1, 2, 2, 3, 3, 3};
+#pragma unroll
+  for (int k = 0; k < 6; ++k) pb[k] = pj[k] < n ? w * Qu[(pj[k] < n ? pi[k] * n + pj[k] : 0)] : 0.0;
 }
 
-// Finalise moments from the sums tot = {S0, S1[3], S2[6]} (frame coordinates u)
+// Finalise moments from the sums tot (frame coordinates u; layout of tot_S2)
 // and set the normaliser pscale = 1 / (V S0).  With use_pending the weights are
-// on the pending (advanced) frame pend = {c[3], M[9], Minv[9], V}, which is
-// committed.  Returns false (status DEGENERATE, state untouched) if S0 is not
+// on the pending (advanced) frame pend = {c, M, Minv, V} (offsets pend_*), which
+// is committed.  Returns false (status DEGENERATE, state untouched) if S0 is not
 // positive and finite.
 __device__ inline bool finalize_core(int nx, FrameState* st, const double* tot, int use_pending,
                                      const double* pend) {
@@ -252,26 +257,21 @@ __device__ inline bool finalize_core(int nx, FrameState* st, const double* tot, 
     st->status = PMF_ERR_DEGENERATE;
     return false;
   }
-  double c[3], M[9], Minv[9], V;
+  double c[4], M[16], Minv[16], V;
   if (use_pending) {
     for (int i = 0; i < n; ++i) c[i] = pend[i];
-    for (int i = 0; i < n * n; ++i) { M[i] = pend[3 + i]; Minv[i] = pend[12 + i]; }
-    V = pend[21];
+    for (int i = 0; i < n * n; ++i) { M[i] = pend[pend_M(n) + i]; Minv[i] = pend[pend_Mi(n) + i]; }
+    V = pend[pend_V(n)];
   } else {
     for (int i = 0; i < n; ++i) c[i] = st->c[i];
     for (int i = 0; i < n * n; ++i) { M[i] = st->M[i]; Minv[i] = st->Minv[i]; }
     V = st->V;
   }
-  double mu[3], Cu[9];
+  double mu[4], Cu[16];
   for (int a = 0; a < n; ++a) mu[a] = tot[1 + a] / S0;
-  int k = 4;
-  double S2[9];
-  for (int a = 0; a < 3; ++a)
-    for (int b = a; b < 3; ++b, ++k)
-      if (a < n && b < n) S2[a * n + b] = S2[b * n + a] = tot[k];
   for (int a = 0; a < n; ++a)
-    for (int b = 0; b < n; ++b) Cu[a * n + b] = S2[a * n + b] / S0 - mu[a] * mu[b];
-  double cov[9];
+    for (int b = 0; b < n; ++b) Cu[a * n + b] = tot[tot_S2(n, a, b)] / S0 - mu[a] * mu[b];
+  double cov[16];
   congruence(n, M, Cu, cov);
   for (int a = 0; a < n; ++a) {
     double m = c[a];

@@ -1,7 +1,7 @@
 // Plain float64 path of the spectral point-mass filter: one small kernel per
 // step of the method, all data in global memory.  It is the reference GPU
 // implementation against which the mixed-precision tensor-core path is
-// compared, and it serves grids of any even size and n_x <= 3.
+// compared, and it serves grids of any even size and n_x <= 4.
 //
 // Per time update (Sec. V-B algorithm on the moving grid, eq. gridMov):
 //   frame       regrid decision and per-sub-step diffusion coefficients
@@ -46,6 +46,17 @@ __device__ double meas_exponent_f64(const MeasParams& mp, const double* x) {
     }
   } else if (mp.kind == PMF_MEAS_RANGE) {
     r[0] = mp.z[0] - sqrt(x[0] * x[0] + x[1] * x[1]);
+  } else if (mp.kind == PMF_MEAS_TERRAIN_GM) {
+    // terrain altitude at (p_x, p_y) = (x_0, x_2); -log of the two-component
+    // Gaussian mixture of the residual (constants from the host: gm = {1/(2 v1),
+    // 1/(2 v2), log terms c1, c2, means mu1, mu2}), in log-sum-exp form
+    double h = mp.p[16];
+    for (int i = 0; i < 4; ++i) h += mp.p[4 * i] * sin(mp.p[4 * i + 1] * x[0] + mp.p[4 * i + 2] * x[2] + mp.p[4 * i + 3]);
+    const double rr = mp.z[0] - h;
+    const double m1 = (rr - mp.gm[4]) * (rr - mp.gm[4]) * mp.gm[0] + mp.gm[2];
+    const double m2 = (rr - mp.gm[5]) * (rr - mp.gm[5]) * mp.gm[1] + mp.gm[3];
+    const double lo = fmin(m1, m2);
+    return lo - log1p(exp(-fabs(m1 - m2)));
   } else {
     r[0] = wrap_pi(mp.z[0] - atan2(x[1], x[0]));
     r[1] = mp.z[1] - x[2];
@@ -76,14 +87,12 @@ __device__ __forceinline__ void block_sum(double* v, double* smem /* [32*NV] */,
   }
 }
 
-// Moment accumulators in frame coordinates u: S0, S1[3], S2[6] (00,01,02,11,12,22).
+// Moment accumulators in frame coordinates u: S0, S1[n], S2 (layout of tot_S2).
 __device__ __forceinline__ void acc_moments(double* acc, double p, const double* u, int nx) {
   acc[0] += p;
   for (int a = 0; a < nx; ++a) acc[1 + a] += p * u[a];
-  int k = 4;
-  for (int a = 0; a < 3; ++a)
-    for (int b = a; b < 3; ++b, ++k)
-      if (a < nx && b < nx) acc[k] += p * u[a] * u[b];
+  for (int a = 0; a < nx; ++a)
+    for (int b = a; b < nx; ++b) acc[tot_S2(nx, a, b)] += p * u[a] * u[b];
 }
 
 __global__ void k_meas_emin_f64(Dims d, MeasParams mp, DevState* st) {
@@ -108,13 +117,13 @@ __global__ void k_meas_emin_f64(Dims d, MeasParams mp, DevState* st) {
 
 __global__ void k_meas_apply_f64(Dims d, MeasParams mp, DevState* st, double* b0, double* b1,
                                  double* partials) {
-  __shared__ double sm[32 * 10];
+  __shared__ double sm[32 * kMomentSlots];
   const int cur = st->f.cur;
   const double* in = cur ? b1 : b0;
   double* out = cur ? b0 : b1;
   const double emin = __longlong_as_double((long long)st->emin_bits);
   const double ps = st->f.pscale;
-  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double acc[kMomentSlots] = {};
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
        p += (long long)gridDim.x * blockDim.x) {
     int j[MAXN];
@@ -129,7 +138,7 @@ __global__ void k_meas_apply_f64(Dims d, MeasParams mp, DevState* st, double* b0
     out[p] = v;
     acc_moments(acc, v, u, d.nx);
   }
-  block_sum<10>(acc, sm, partials + blockIdx.x * 10);
+  block_sum<kMomentSlots>(acc, sm, partials + blockIdx.x * kMomentSlots);
 }
 
 // Sum block partials, finalise moments and the normaliser.  use_pending: the
@@ -137,12 +146,12 @@ __global__ void k_meas_apply_f64(Dims d, MeasParams mp, DevState* st, double* b0
 // committed here.  flip: buffer parity change of the update.
 __global__ void k_finalize(Dims d, DevState* st, const double* partials, int nblocks, int flip,
                            int use_pending, const double* pend /* c, M, Minv, V */) {
-  __shared__ double sm[32 * 10];
-  __shared__ double tot[10];
-  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  __shared__ double sm[32 * kMomentSlots];
+  __shared__ double tot[kMomentSlots];
+  double acc[kMomentSlots] = {};
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-    for (int i = 0; i < 10; ++i) acc[i] += partials[b * 10 + i];
-  block_sum<10>(acc, sm, tot);
+    for (int i = 0; i < kMomentSlots; ++i) acc[i] += partials[b * kMomentSlots + i];
+  block_sum<kMomentSlots>(acc, sm, tot);
   __syncthreads();
   if (threadIdx.x != 0) return;
   FrameState fs = st->f;   // local copy: the scalar work stays out of global memory
@@ -155,7 +164,7 @@ __global__ void k_finalize(Dims d, DevState* st, const double* partials, int nbl
 template <int n>
 __device__ void frame_body(const TimeConsts& tc, DevState* st, double* pend) {
   __shared__ FrameState fs;
-  __shared__ double Mpi[9];
+  __shared__ double Mpi[16];
   if (threadIdx.x == 0) {
     fs = st->f;
     frame_scalar<n>(tc, &fs, pend, Mpi);
@@ -169,7 +178,8 @@ __device__ void frame_body(const TimeConsts& tc, DevState* st, double* pend) {
 __global__ void k_frame(const __grid_constant__ TimeConsts tc, DevState* st, double* pend) {
   if (tc.nx == 1) frame_body<1>(tc, st, pend);
   else if (tc.nx == 2) frame_body<2>(tc, st, pend);
-  else frame_body<3>(tc, st, pend);
+  else if (tc.nx == 3) frame_body<3>(tc, st, pend);
+  else frame_body<4>(tc, st, pend);
 }
 
 // Periodic-sinc interpolation matrix of one axis (eq. interFreq evaluated at
@@ -391,8 +401,8 @@ __global__ void k_psi_f64(Dims d, const DevState* st, int stage, double* b0, dou
     int k[MAXN];
     long long t = r;
     for (int a = n - 1; a >= 0; --a) { k[a] = (int)(t % H[a]); t /= H[a]; }
-    double S[8], Psi[8];
-    long long idx[8];
+    double S[16], Psi[16];
+    long long idx[16];
     for (int s = 0; s < ns; ++s) {
       long long off = 0;
       double kap2[MAXN], kt[MAXN];
@@ -413,12 +423,13 @@ __global__ void k_psi_f64(Dims d, const DevState* st, int stage, double* b0, dou
         for (int a = 0; a < n; ++a) e += st->pa[q][a] * kap2[a];
         if (n > 1) e += st->pb[q][0] * kt[0] * kt[1];
         if (n > 2) e += st->pb[q][1] * kt[0] * kt[2] + st->pb[q][2] * kt[1] * kt[2];
+        if (n > 3) e += st->pb[q][3] * kt[0] * kt[3] + st->pb[q][4] * kt[1] * kt[3] + st->pb[q][5] * kt[2] * kt[3];
         den *= 1.0 + e;
         ex += e;
       }
       Psi[s] = exact ? exp(-ex) : 1.0 / den;
     }
-    double T[8], Pe[8], Tp[8];
+    double T[16], Pe[16], Tp[16];
     for (int B = 0; B < ns; ++B) {
       double tb = 0.0, pe = 0.0;
       for (int s = 0; s < ns; ++s) {
@@ -449,8 +460,8 @@ __global__ void k_psi_f64(Dims d, const DevState* st, int stage, double* b0, dou
 
 // Moment partial sums of a float32 weight array (prior of the tensor-core path).
 __global__ void k_moments_f32(Dims d, const float* X, double* partials) {
-  __shared__ double sm[32 * 10];
-  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  __shared__ double sm[32 * kMomentSlots];
+  double acc[kMomentSlots] = {};
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
        p += (long long)gridDim.x * blockDim.x) {
     int j[MAXN];
@@ -459,15 +470,15 @@ __global__ void k_moments_f32(Dims d, const float* X, double* partials) {
     for (int a = 0; a < d.nx; ++a) u[a] = j[a] - 0.5 * (d.N[a] - 1);
     acc_moments(acc, (double)X[p], u, d.nx);
   }
-  block_sum<10>(acc, sm, partials + blockIdx.x * 10);
+  block_sum<kMomentSlots>(acc, sm, partials + blockIdx.x * kMomentSlots);
 }
 
 __global__ void k_moments_f64(Dims d, const DevState* st, int stage, const double* b0,
                               const double* b1, double* partials) {
-  __shared__ double sm[32 * 10];
+  __shared__ double sm[32 * kMomentSlots];
   const int par = (st->f.cur + stage) & 1;
   const double* X = par ? b1 : b0;
-  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double acc[kMomentSlots] = {};
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
        p += (long long)gridDim.x * blockDim.x) {
     int j[MAXN];
@@ -476,7 +487,7 @@ __global__ void k_moments_f64(Dims d, const DevState* st, int stage, const doubl
     for (int a = 0; a < d.nx; ++a) u[a] = j[a] - 0.5 * (d.N[a] - 1);
     acc_moments(acc, X[p], u, d.nx);
   }
-  block_sum<10>(acc, sm, partials + blockIdx.x * 10);
+  block_sum<kMomentSlots>(acc, sm, partials + blockIdx.x * kMomentSlots);
 }
 
 // Initial weights: Gaussian prior sampled on the initial frame (unnormalised).

@@ -28,20 +28,48 @@ struct TimeConsts {
   int N[MAXN];
   int realign_mode;  // PMF_REALIGN_*
   double tau, dt, g, span, rho_max;
-  double Q[9];       // diffusion
-  double Phi[9];     // e^{A tau}
-  double PhiInv[9];  // e^{-A tau}
-  double Qb[9];      // int_0^tau e^{-A s} Q e^{-A^T s} ds
-  double Estep[9];   // e^{-A dt}
-  double Qt[MAXL][6];  // e^{-A q dt} Q e^{-A^T q dt}, q = 1..l (packed 00,01,02,11,12,22)
+  double Q[16];       // diffusion
+  double Phi[16];     // e^{A tau}
+  double PhiInv[16];  // e^{-A tau}
+  double Qb[16];      // int_0^tau e^{-A s} Q e^{-A^T s} ds
+  double Estep[16];   // e^{-A dt}
+  // e^{-A q dt} Q e^{-A^T q dt}, q = 1..l, packed 00,01,02,11,12,22 then 03,13,23,33
+  double Qt[MAXL][10];
 };
+
+// Index of the symmetric entry (a, b) in the packed order of TimeConsts::Qt.
+PMF_HD int packed_sym(int a, int b) {
+  const int lo = a < b ? a : b, hi = a < b ? b : a;
+  if (hi == 3) return 6 + lo;
+  return lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
+}
+
+// Pending frame {c, M, Minv, V} (written by the frame computation, committed
+// by the finalisation): fixed offsets for n <= 3, and for n = 4.
+PMF_HD int pend_M(int n) { return n == 4 ? 4 : 3; }
+PMF_HD int pend_Mi(int n) { return n == 4 ? 20 : 12; }
+PMF_HD int pend_V(int n) { return n == 4 ? 36 : 21; }
+constexpr int kPendSize = 40;
+// Prior constants handed to the initial-PDF kernels: P0^{-1} row-major with
+// row stride n at [0, n*n), m0 at [kAuxM0, kAuxM0 + n).
+constexpr int kAuxM0 = 16;
+constexpr int kAuxSize = 20;
+// Slots of the moment sums {S0, S1[n], S2}: 10 cover n <= 3, 15 cover n = 4.
+constexpr int kMomentSlots = 15;
+
+// Moment sums tot = {S0, S1[n], S2 packed as TimeConsts::Qt}: the second
+// moments start at 4 for n <= 3 (the {S0, S1[3], S2[6]} layout) and at 5 for n = 4.
+PMF_HD int tot_S2(int n, int a, int b) { return (n == 4 ? 5 : 4) + packed_sym(a, b); }
+
 
 // Measurement update parameters (by value).
 struct MeasParams {
   int kind, nz, nx;
   double z[PMF_MAX_NZ];
   double Rinv[9];
-  double H[9];
+  double H[PMF_MAX_NZ * PMF_MAX_NX];
+  double p[PMF_MEAS_NPARAM];
+  double gm[6];   // TERRAIN_GM: 1/(2 v1), 1/(2 v2), log(v1)/2 - log w1, log(v2)/2 - log w2, mu1, mu2
 };
 
 // Frame, moments and per-update scalars of one filter (float64).  Frame
@@ -49,12 +77,12 @@ struct MeasParams {
 // pscale * stored.  Kernels that do scalar work on it copy it to shared or
 // local memory first.
 struct FrameState {
-  double c[3], M[9], Minv[9], V;
-  double mean[3], cov[9];
+  double c[4], M[16], Minv[16], V;
+  double mean[4], cov[16];
   double S0, pscale, g;
   // regrid of the current time update
-  double rs[3], rd[3];   // separable: u_old_m = rs_m + rd_m * u_new_m
-  double B[9], b[3];     // realigned: u_old = B u_new + b
+  double rs[4], rd[4];   // separable: u_old_m = rs_m + rd_m * u_new_m
+  double B[16], b[4];    // realigned: u_old = B u_new + b
   double hc[2];          // at the frame centre: atan2(c_2, c_1) and c_1^2 + c_2^2 (n_x = 3)
   int cur, status, realign, l, exact, pad;
 };
@@ -65,12 +93,12 @@ struct FrameState {
 struct DevState {
   FrameState f;
   unsigned long long emin_bits;
-  double pa[MAXL][3];
-  double pb[MAXL][3];
+  double pa[MAXL][4];
+  double pb[MAXL][6];    // cross pairs 01, 02, 12, 03, 13, 23
 };
 
 // ---------------------------------------------------------------------------
-// float64 n x n helpers (row-major, n <= 3 on the device; <= 8 on the host)
+// float64 n x n helpers (row-major, n <= 4 on the device; <= 8 on the host)
 // ---------------------------------------------------------------------------
 PMF_HD void mm(int n, const double* A, const double* B, double* C) {
   for (int i = 0; i < n; ++i)
@@ -106,8 +134,21 @@ PMF_HD void congruence(int n, const double* A, const double* S, double* C) {
 PMF_HD double det(int n, const double* A) {
   if (n == 1) return A[0];
   if (n == 2) return A[0] * A[3] - A[1] * A[2];
-  return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
-         A[2] * (A[3] * A[7] - A[4] * A[6]);
+  if (n == 3)
+    return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+           A[2] * (A[3] * A[7] - A[4] * A[6]);
+  // n = 4: expansion along the first row
+  double s = 0.0;
+  for (int c = 0; c < 4; ++c) {
+    double m[9];
+    for (int r = 1, k = 0; r < 4; ++r)
+      for (int cc = 0; cc < 4; ++cc)
+        if (cc != c) m[k++] = A[r * 4 + cc];
+    const double minor = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
+                         m[2] * (m[3] * m[7] - m[4] * m[6]);
+    s += ((c & 1) ? -1.0 : 1.0) * A[c] * minor;
+  }
+  return s;
 }
 
 // Gauss-Jordan inverse with partial pivoting; returns false if singular.

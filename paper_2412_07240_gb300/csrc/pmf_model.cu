@@ -71,7 +71,7 @@ int time_consts(const pmf_config& c, double tau, TimeConsts* tc, std::string* wh
   tc->realign_mode = c.realign_mode;
   tc->span = c.span_sigma;
   tc->rho_max = c.realign_rho;
-  double At[9], mAt[9], mAdt[9];
+  double At[16], mAt[16], mAdt[16];
   double trA = 0.0;
   for (int i = 0; i < n * n; ++i) {
     At[i] = c.A[i] * tau;
@@ -84,7 +84,7 @@ int time_consts(const pmf_config& c, double tau, TimeConsts* tc, std::string* wh
   expm_host(n, mAt, tc->PhiInv);
   expm_host(n, mAdt, tc->Estep);
   const int m = 2 * n;
-  double C[36] = {0}, E[36];
+  double C[64] = {0}, E[64];
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
       C[i * m + j] = -c.A[i * n + j] * tau;
@@ -92,7 +92,7 @@ int time_consts(const pmf_config& c, double tau, TimeConsts* tc, std::string* wh
       C[(n + i) * m + n + j] = c.A[j * n + i] * tau;
     }
   expm_host(m, C, E);
-  double F12[9], Phi2[9], Qd[9];
+  double F12[16], Phi2[16], Qd[16];
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
       F12[i * n + j] = E[i * m + n + j];
@@ -104,7 +104,7 @@ int time_consts(const pmf_config& c, double tau, TimeConsts* tc, std::string* wh
   congruence(n, tc->PhiInv, Qd, tc->Qb);
   // rotated diffusion at the sub-step ends: e^{-A q dt} Q e^{-A^T q dt}, q = 1..l,
   // with e^{-A q dt} = (e^{-A dt})^q
-  double Eq[9], En[9], Qq[9];
+  double Eq[16], En[16], Qq[16];
   for (int i = 0; i < n * n; ++i) Eq[i] = tc->Estep[i];
   for (int q = 1; q <= l; ++q) {
     if (q > 1) {
@@ -113,12 +113,9 @@ int time_consts(const pmf_config& c, double tau, TimeConsts* tc, std::string* wh
     }
     congruence(n, Eq, c.Q, Qq);
     double* o = tc->Qt[q - 1];
-    o[0] = Qq[0];
-    o[1] = n > 1 ? Qq[1] : 0.0;
-    o[2] = n > 2 ? Qq[2] : 0.0;
-    o[3] = n > 1 ? Qq[n + 1] : 0.0;
-    o[4] = n > 2 ? Qq[5] : 0.0;
-    o[5] = n > 2 ? Qq[8] : 0.0;
+    for (int k = 0; k < 10; ++k) o[k] = 0.0;
+    for (int a = 0; a < n; ++a)
+      for (int b = a; b < n; ++b) o[packed_sym(a, b)] = Qq[a * n + b];
   }
   tc->g = tc->exact ? std::exp(-trA * tau) : std::pow(1.0 - tc->dt * trA, (double)l);
   return PMF_OK;
@@ -139,7 +136,7 @@ int validate_config(const pmf_config* c, std::string* why) {
         *why = "Q and P0 must be symmetric";
         return PMF_ERR_ARG;
       }
-  double L[9], Qs[9], tr = 0.0;
+  double L[16], Qs[16], tr = 0.0;
   for (int i = 0; i < n; ++i) tr += std::fabs(c->Q[i * n + i]);
   for (int i = 0; i < n * n; ++i) Qs[i] = c->Q[i];
   for (int i = 0; i < n; ++i) Qs[i * n + i] += 1e-12 * (tr + 1e-300);
@@ -181,18 +178,36 @@ int meas_params(int n, const pmf_meas* m, MeasParams* mp, std::string* why) {
   } else if (m->kind == PMF_MEAS_LINEAR) {
     if (nz < 1 || nz > PMF_MAX_NZ) { *why = "linear measurement nz out of range"; return PMF_ERR_ARG; }
     if (!finite_all(m->H, nz * n)) { *why = "non-finite H"; return PMF_ERR_ARG; }
+  } else if (m->kind == PMF_MEAS_TERRAIN_GM) {
+    if (nz != 1 || n != 4) { *why = "terrain measurement needs nz = 1, nx = 4"; return PMF_ERR_ARG; }
+    if (!finite_all(m->p, 22) || !(m->p[17] >= 0.0 && m->p[17] <= 1.0) || !(m->p[20] > 0.0) || !(m->p[21] > 0.0)) {
+      *why = "terrain measurement: invalid terrain or mixture parameters";
+      return PMF_ERR_ARG;
+    }
   } else {
     *why = "unknown measurement kind";
     return PMF_ERR_ARG;
   }
-  if (!finite_all(m->z, nz) || !finite_all(m->R, nz * nz)) { *why = "non-finite z or R"; return PMF_ERR_ARG; }
-  double L[9];
-  if (!chol(nz, m->R, L)) { *why = "R is not positive definite"; return PMF_ERR_ARG; }
+  if (!finite_all(m->z, nz)) { *why = "non-finite z"; return PMF_ERR_ARG; }
   *mp = MeasParams{};
   mp->kind = m->kind;
   mp->nz = nz;
   mp->nx = n;
   for (int i = 0; i < nz; ++i) mp->z[i] = m->z[i];
+  if (m->kind == PMF_MEAS_TERRAIN_GM) {
+    for (int i = 0; i < PMF_MEAS_NPARAM; ++i) mp->p[i] = m->p[i];
+    const double w1 = m->p[17], v1 = m->p[20], v2 = m->p[21];
+    mp->gm[0] = 0.5 / v1;
+    mp->gm[1] = 0.5 / v2;
+    mp->gm[2] = 0.5 * std::log(v1) - std::log(w1);
+    mp->gm[3] = 0.5 * std::log(v2) - std::log(1.0 - w1);
+    mp->gm[4] = m->p[18];
+    mp->gm[5] = m->p[19];
+    return PMF_OK;
+  }
+  if (!finite_all(m->R, nz * nz)) { *why = "non-finite R"; return PMF_ERR_ARG; }
+  double L[9];
+  if (!chol(nz, m->R, L)) { *why = "R is not positive definite"; return PMF_ERR_ARG; }
   for (int i = 0; i < nz * n; ++i) mp->H[i] = m->H[i];
   inv(nz, m->R, mp->Rinv);
   return PMF_OK;
@@ -202,7 +217,7 @@ int meas_params(int n, const pmf_meas* m, MeasParams* mp, std::string* why) {
 DevState initial_state(const pmf_config& c) {
   DevState h{};
   const int n = c.nx;
-  double L[9];
+  double L[16];
   chol(n, c.P0, L);
   for (int a = 0; a < n; ++a) h.f.c[a] = c.m0[a];
   for (int r = 0; r < n; ++r)

@@ -17,12 +17,15 @@
 
 namespace {
 
+using pmf::kMomentSlots;
+using pmf::tot_S2;
+
 constexpr int kThreads = 256;
 constexpr int kMaxBlocks = PMF_NOALLOC_MAX_POINTS / kThreads;   // one partial per 256 points
 
 // Shared by every call on a device, kept until the process exits; each call
 // overwrites the partials of the blocks it launches before reading them.
-__device__ __align__(256) double g_partials[kMaxBlocks * 10];
+__device__ __align__(256) double g_partials[kMaxBlocks * kMomentSlots];
 
 constexpr int kMaxDevices = 64;
 double* g_ptr[kMaxDevices] = {nullptr};
@@ -53,53 +56,50 @@ struct Geo {
   double M[PMF_MAX_NX * PMF_MAX_NX];
 };
 
-// One block per 256 consecutive points: S0, S1[3], S2[6] in frame coordinates u.
+// One block per 256 consecutive points: S0, S1[n], S2 in frame coordinates u
+// (the kMomentSlots layout of tot_S2).
 __global__ void k_partials(Geo g, const double* __restrict__ w, double* __restrict__ part) {
-  __shared__ double sm[kThreads / 32][10];
-  double a[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  __shared__ double sm[kThreads / 32][kMomentSlots];
+  double a[kMomentSlots] = {};
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (p < g.P) {
     long long t = p;
-    double u[PMF_MAX_NX] = {0, 0, 0};
+    double u[PMF_MAX_NX] = {};
     for (int m = g.nx - 1; m >= 0; --m) {
       u[m] = (double)(t % g.N[m]) - 0.5 * (g.N[m] - 1);
       t /= g.N[m];
     }
     const double x = w[p];
     a[0] = x;
-    for (int i = 0; i < 3; ++i) a[1 + i] = x * u[i];
-    a[4] = x * u[0] * u[0];
-    a[5] = x * u[0] * u[1];
-    a[6] = x * u[0] * u[2];
-    a[7] = x * u[1] * u[1];
-    a[8] = x * u[1] * u[2];
-    a[9] = x * u[2] * u[2];
+    for (int i = 0; i < g.nx; ++i) a[1 + i] = x * u[i];
+    for (int i = 0; i < g.nx; ++i)
+      for (int j = i; j < g.nx; ++j) a[tot_S2(g.nx, i, j)] = x * u[i] * u[j];
   }
-  for (int i = 0; i < 10; ++i)
+  for (int i = 0; i < kMomentSlots; ++i)
     for (int o = 16; o; o >>= 1) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
   if ((threadIdx.x & 31) == 0)
-    for (int i = 0; i < 10; ++i) sm[threadIdx.x >> 5][i] = a[i];
+    for (int i = 0; i < kMomentSlots; ++i) sm[threadIdx.x >> 5][i] = a[i];
   __syncthreads();
-  if (threadIdx.x < 10) {
+  if (threadIdx.x < kMomentSlots) {
     double s = 0.0;
     for (int k = 0; k < kThreads / 32; ++k) s += sm[k][threadIdx.x];
-    part[(size_t)blockIdx.x * 10 + threadIdx.x] = s;
+    part[(size_t)blockIdx.x * kMomentSlots + threadIdx.x] = s;
   }
 }
 
 // Sum the partials and write {S0, mean[nx], cov[nx*nx]} (x = c + M u).
 __global__ void k_finish(Geo g, const double* __restrict__ part, int nblocks, double* __restrict__ out) {
-  __shared__ double sm[kThreads / 32][10];
-  __shared__ double tot[10];
-  double a[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  __shared__ double sm[kThreads / 32][kMomentSlots];
+  __shared__ double tot[kMomentSlots];
+  double a[kMomentSlots] = {};
   for (int b = threadIdx.x; b < nblocks; b += kThreads)
-    for (int i = 0; i < 10; ++i) a[i] += part[(size_t)b * 10 + i];
-  for (int i = 0; i < 10; ++i)
+    for (int i = 0; i < kMomentSlots; ++i) a[i] += part[(size_t)b * kMomentSlots + i];
+  for (int i = 0; i < kMomentSlots; ++i)
     for (int o = 16; o; o >>= 1) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
   if ((threadIdx.x & 31) == 0)
-    for (int i = 0; i < 10; ++i) sm[threadIdx.x >> 5][i] = a[i];
+    for (int i = 0; i < kMomentSlots; ++i) sm[threadIdx.x >> 5][i] = a[i];
   __syncthreads();
-  if (threadIdx.x < 10) {
+  if (threadIdx.x < kMomentSlots) {
     double s = 0.0;
     for (int k = 0; k < kThreads / 32; ++k) s += sm[k][threadIdx.x];
     tot[threadIdx.x] = s;
@@ -109,11 +109,10 @@ __global__ void k_finish(Geo g, const double* __restrict__ part, int nblocks, do
   const int n = g.nx;
   const double S0 = tot[0];
   out[0] = S0;
-  double mu[3], S2[9], Cu[9], cov[9];
+  double mu[4], S2[16], Cu[16], cov[16];
   for (int a2 = 0; a2 < n; ++a2) mu[a2] = tot[1 + a2] / S0;
-  const int idx[3][3] = {{4, 5, 6}, {5, 7, 8}, {6, 8, 9}};
   for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) S2[i * n + j] = tot[idx[i][j]];
+    for (int j = 0; j < n; ++j) S2[i * n + j] = tot[tot_S2(n, i, j)];
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) Cu[i * n + j] = S2[i * n + j] / S0 - mu[i] * mu[j];
   pmf::congruence(n, g.M, Cu, cov);

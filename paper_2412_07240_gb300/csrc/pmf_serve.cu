@@ -390,8 +390,8 @@ int pmf_server_create(pmf_server** out, size_t hbm_budget, int max_filters, int 
   for (int k = 0; k < 3; ++k) ok = ok && cudaStreamCreateWithFlags(&s->s[k], cudaStreamNonBlocking) == cudaSuccess;
   ok = ok && cudaMalloc(&s->d_slots1, sizeof(Slot1) * max_filters) == cudaSuccess;
   ok = ok && cudaMalloc(&s->d_slots2, sizeof(FilterSlot) * max_filters) == cudaSuccess;
-  ok = ok && cudaMalloc(&s->d_partials, sizeof(double) * 10 * 4096) == cudaSuccess;
-  ok = ok && cudaMalloc(&s->d_aux, sizeof(double) * 16) == cudaSuccess;
+  ok = ok && cudaMalloc(&s->d_partials, sizeof(double) * kMomentSlots * 4096) == cudaSuccess;
+  ok = ok && cudaMalloc(&s->d_aux, sizeof(double) * kAuxSize) == cudaSuccess;
   for (int r = 0; r < kInflight && ok; ++r) {
     Flight& b = s->ring[r];
     for (int k = 0; k < 3 && ok; ++k) ok = cudaEventCreateWithFlags(&b.ev[k], cudaEventDisableTiming) == cudaSuccess;
@@ -476,9 +476,9 @@ int pmf_server_admit(pmf_server* s, const pmf_config* cfg, const pmf_meas* model
   }
   // initial state and prior on the device (stream 0), then the slot entry
   DevState h = initial_state(f.cfg);
-  double aux[16] = {0};
+  double aux[kAuxSize] = {0};
   inv(n, cfg->P0, aux);
-  for (int a = 0; a < n; ++a) aux[9 + a] = cfg->m0[a];
+  for (int a = 0; a < n; ++a) aux[kAuxM0 + a] = cfg->m0[a];
   Dims d{};
   d.nx = n;
   d.P = P;

@@ -582,7 +582,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     l = fs.l;
     exact = fs.exact;
     for (int q = tid; q < l; q += kThreads) {
-      double pa[3], pb[3];
+      double pa[4], pb[6];
       frame_substep<2>(sh.tc, sh.Mpi, q, pa, pb);
       sh.pa[q][0] = (float)pa[0];
       sh.pa[q][1] = (float)pa[1];
@@ -834,7 +834,7 @@ __global__ void k_prior_f32(Dims d, const DevState* st, const double* aux, float
     for (int a = 0; a < n; ++a) {
       double x = st->f.c[a];
       for (int b = 0; b < n; ++b) x += st->f.M[a * n + b] * (j[b] - 0.5 * (d.N[b] - 1));
-      dx[a] = x - aux[9 + a];
+      dx[a] = x - aux[kAuxM0 + a];
     }
     double q = 0.0;
     for (int a = 0; a < n; ++a)

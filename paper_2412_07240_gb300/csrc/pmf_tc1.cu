@@ -280,7 +280,7 @@ __device__ void fused1d(const View1& v) {
     l = fs.l;
     exact = fs.exact;
     for (int q = tid; q < l; q += kT1) {
-      double pa[3], pb[3];
+      double pa[4], pb[6];
       frame_substep<1>(sh.tc, sh.Mpi, q, pa, pb);
       sh.pa[q] = (float)pa[0];
     }

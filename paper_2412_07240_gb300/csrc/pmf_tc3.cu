@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(kT) k_frame3(const __grid_constant__ Batch3 b)
     Update3* up = job.up;
     const int l = fs.l;
     for (int q = threadIdx.x; q < l; q += kT) {
-      double pa[3], pb[3];
+      double pa[4], pb[6];
       frame_substep<3>(tc, Mpi, q, pa, pb);
       for (int a = 0; a < 3; ++a) {
         up->pa[q][a] = (float)pa[a];

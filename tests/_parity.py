@@ -18,7 +18,7 @@ def compare(gpu, orc):
     # frame: centre shift relative to the spread, axis matrix relative to its size
     out["frame"] = float(max(np.abs(c - orc.c).max() / np.sqrt(abs(np.trace(Co))),
                              np.abs(M - orc.M).max() / np.abs(orc.M).max()))
-    out["mean"] = float(np.abs(m - mo).max() / np.sqrt(np.trace(Co)))
+    out["mean"] = float(np.abs(m - mo).max() / np.sqrt(abs(np.trace(Co))))
     out["cov"] = float(np.abs(C - Co).max() / np.abs(Co).max())
     return out
 

@@ -67,6 +67,53 @@ def test_2d_linear_exact_time_matches_kalman():
     assert errs.max() < 1e-7, errs.max(axis=0)
 
 
+def _turn_4d(N, epochs, R=25.0):
+    """Coordinated turn with position measurements (linear h), no re-alignment."""
+    a = np.deg2rad(30.0)
+    A = np.array([[0.0, 1.0, 0.0, 0.0], [0.0, 0.0, 0.0, -a], [0.0, 0.0, 0.0, 1.0], [0.0, a, 0.0, 0.0]])
+    P0 = np.diag([9.0, 4.0, 9.0, 4.0])
+    P0[0, 1] = P0[1, 0] = 2.0
+    cfg = FilterConfig(nx=4, N=N, A=A, Q=np.diag([0.0, 1.0, 0.0, 1.0]), m0=np.array([0.0, 5.0, 0.0, 5.0]),
+                       P0=P0, span=6.0, dt_sub=0.05, realign_rho=10.0)
+    meas = MeasModel("linear", R=R * np.eye(2), H=np.array([[1.0, 0.0, 0.0, 0.0], [0.0, 0.0, 1.0, 0.0]]))
+    sc = w.Scenario("turn4", cfg, meas, dt=0.5, epochs=epochs)
+    sc.truth, sc.z = simulate(cfg, meas, sc.dt, sc.epochs, seed=4)
+    return sc
+
+
+def test_4d_linear_exact_time_matches_kalman():
+    """n_x = 4 with singular Q: the Kalman filter is exact; the grid (+-6 sigma,
+    about 2 nodes per posterior sigma) sets a few-1e-6 floor on the moments."""
+    errs, realigns = _kalman_errors(_turn_4d((24, 22, 24, 20), 4), "exact")
+    assert realigns == 0
+    assert errs[:, 0].max() < 2e-6 and errs[:, 1].max() < 1e-5, errs.max(axis=0)
+
+
+def test_multilinear_exact_on_multilinear_4d():
+    """Multilinear interpolation reproduces any polynomial of degree <= 1 per axis
+    inside the box and gives 0 outside it (the re-alignment of Sec. V, n_x = 4)."""
+    rng = np.random.default_rng(5)
+    N = (7, 6, 5, 8)
+    coef = rng.standard_normal(16)
+
+    def f(z):
+        out = np.zeros(z.shape[0])
+        for S in range(16):
+            t = np.full(z.shape[0], coef[S])
+            for m in range(4):
+                if (S >> m) & 1:
+                    t = t * z[:, m]
+            out += t
+        return out
+    grid = np.stack(np.meshgrid(*[np.arange(n, dtype=float) for n in N], indexing="ij"), axis=-1)
+    P = f(grid.reshape(-1, 4)).reshape(N)
+    z = rng.uniform(0.0, 1.0, size=(500, 4)) * (np.array(N) - 1)
+    np.testing.assert_allclose(of.multilinear(P, z), f(z), rtol=0, atol=1e-12 * np.abs(P).max())
+    far = z.copy()
+    far[:, 2] = N[2] + 0.5
+    assert np.all(of.multilinear(P, far) == 0.0)
+
+
 def _cv_scenario(N):
     cfg = FilterConfig(nx=2, N=N, A=np.array([[0.0, 1.0], [0.0, 0.0]]), Q=np.diag([0.01, 0.1]),
                        m0=np.array([0.0, 1.0]), P0=np.diag([0.5, 0.5]))
@@ -173,6 +220,31 @@ def test_mutation_transposed_frame(monkeypatch):
     sc.cfg.A = np.array([[0.0, 1.0], [-1.0, -0.2]])
     errs, _ = _kalman_errors(sc, "exact")
     assert errs.max() > 1e-6
+
+
+def test_mutation_4d_last_axis_cross_terms(monkeypatch):
+    """Dropping the Q_u terms that couple the fourth axis breaks the 4-D Gaussian pin."""
+    from oracle import model
+    from tests.test_oracle_time_update import test_gaussian_fpe_exact_time_4d_degenerate_q
+    orig = model.backward_diffusion_integral
+    frame = {}
+
+    def bad(A, Q, tau):
+        Qb = orig(A, Q, tau)
+        M = frame["M"]
+        Mi = np.linalg.inv(M)
+        Qu = Mi @ Qb @ Mi.T
+        Qu[3, :3] = Qu[:3, 3] = 0.0
+        return M @ Qu @ M.T
+    orig_mult = of.OracleFilter.diffusion_multiplier
+
+    def spy(self, tau):
+        frame["M"] = self.M
+        return orig_mult(self, tau)
+    monkeypatch.setattr(model, "backward_diffusion_integral", bad)
+    monkeypatch.setattr(of.OracleFilter, "diffusion_multiplier", spy)
+    with pytest.raises(AssertionError):
+        test_gaussian_fpe_exact_time_4d_degenerate_q()
 
 
 def test_mutation_trace_factor_sign(monkeypatch):

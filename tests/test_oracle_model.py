@@ -1,5 +1,6 @@
 """Pins of the oracle's model arithmetic: discretisation of eq. dynam and measurement functions."""
 import numpy as np
+import pytest
 
 from oracle import fdm, model
 
@@ -70,6 +71,35 @@ def test_measurement_functions():
     np.testing.assert_allclose(model.h("linear", x, H), [[11.0], [-1.0]])
     r = model.residual("bearing_linear3", np.array([-np.pi + 0.01, 0.0]), x[1:])
     assert abs(r[0, 0] - 0.01) < 1e-12
+
+
+def test_gm_likelihood_is_the_mixture_density():
+    """Sec. VI noise: exp(-gm_neg_log_lik) is w N(r; m1, v1) + (1 - w) N(r; m2, v2)."""
+    from scipy.stats import norm
+    p = np.zeros(24)
+    p[17:22] = [0.3, -1.0, 20.0, 0.5, 4.0]
+    r = np.linspace(-5.0, 30.0, 71)
+    ref = 0.3 * norm.pdf(r, -1.0, np.sqrt(0.5)) + 0.7 * norm.pdf(r, 20.0, 2.0)
+    np.testing.assert_allclose(np.exp(-model.gm_neg_log_lik(r, p)), ref, rtol=1e-13)
+    # far tails stay finite in log form where the density itself underflows
+    far = model.gm_neg_log_lik(np.array([1e4]), p)
+    assert np.isfinite(far[0]) and far[0] > 700
+    # weight 1 is a single Gaussian: -log N(r; m1, v1)
+    p[17] = 1.0
+    np.testing.assert_allclose(model.gm_neg_log_lik(r, p),
+                               0.5 * np.log(2 * np.pi * 0.5) + 0.5 * (r + 1.0) ** 2 / 0.5, rtol=1e-13)
+
+
+def test_terrain_measurement_special_values():
+    """Terrain of four plane waves on a base; h reads positions from state axes 0 and 2."""
+    p = np.zeros(24)
+    p[16] = 500.0
+    p[0:4] = [10.0, np.pi / 100.0, 0.0, 0.0]           # 10 sin(pi p_x / 100)
+    p[4:8] = [3.0, 0.0, np.pi / 20.0, np.pi / 2.0]     # 3 cos(pi p_y / 20)
+    x = np.array([[50.0, 7.0, 0.0, -2.0], [100.0, -1.0, 10.0, 5.0], [-50.0, 0.0, 20.0, 0.0]])
+    np.testing.assert_allclose(model.h("terrain_gm", x, params=p)[:, 0], [513.0, 500.0, 487.0],
+                               atol=1e-12)
+    assert model.residual("terrain_gm", np.array([520.0]), x[:1], params=p)[0, 0] == pytest.approx(7.0)
 
 
 def test_fst_inverse_and_eigenpairs():

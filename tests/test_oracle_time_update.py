@@ -62,6 +62,24 @@ def test_gaussian_fpe_exact_time_3d():
     assert _closed_form_error(f, 0.1) < 1e-8
 
 
+def test_gaussian_fpe_exact_time_4d_degenerate_q():
+    """Coordinated turn (Sec. VI): rotating velocity, diffusion on the velocity axes
+    only (singular Q) and a correlated prior, so Q_u has cross terms and the
+    4-D sign-flip orbits of the parity fix-up are all exercised."""
+    a = np.deg2rad(30.0)
+    A = [[0, 1, 0, 0], [0, 0, 0, -a], [0, 0, 0, 1], [0, a, 0, 0]]
+    Q = np.diag([0.0, 1.0, 0.0, 1.0])
+    sd = np.sqrt([9.0, 4.0, 9.0, 4.0])
+    R = np.array([[1.0, 0.3, -0.2, 0.1], [0.3, 1.0, 0.25, -0.3], [-0.2, 0.25, 1.0, 0.2], [0.1, -0.3, 0.2, 1.0]])
+    P0 = sd[:, None] * R * sd[None, :]
+    f = of.OracleFilter(_cfg(A, Q, [0.0, 5.0, 0.0, 5.0], P0, [32, 30, 34, 28], span=7.0), psi_mode="exact")
+    Mi = np.linalg.inv(f.M)
+    Qu = Mi @ Q @ Mi.T
+    # the first frame axis sees no diffusion (rank-2 Q); the other three pairs couple
+    assert np.count_nonzero(np.abs(Qu[np.triu_indices(4, 1)]) > 0.1) == 3
+    assert _closed_form_error(f, 0.5) < 3e-9
+
+
 def test_euler_first_order_in_substep():
     A = [[0.0, 1.0], [-1.0, -0.2]]
     Q = [[0.1, 0.0], [0.0, 0.3]]

@@ -46,3 +46,17 @@ def test_c5_truth_is_the_exact_discretisation():
         var.append(q * (np.exp(2 * a * wl.taus[r[:-1]]) - 1) / (2 * a) + (1 + e ** 2) * 0.01)
     res, var = np.concatenate(res), np.concatenate(var)
     assert abs(np.mean(res ** 2 / var) - 1.0) < 0.05
+
+
+def test_c6_local_coordinates_state_the_same_problem():
+    """The local form shifts positions by the prior mean and moves the offset into
+    the terrain phases: same altitudes at the same physical points, same z."""
+    from oracle import model
+    a = w.c6_scenario(epochs=5)
+    b = w.c6_scenario(epochs=5, local=True)
+    np.testing.assert_array_equal(a.z, b.z)
+    ha = model.h("terrain_gm", a.truth, params=a.meas.params)
+    hb = model.h("terrain_gm", b.truth, params=b.meas.params)
+    np.testing.assert_allclose(hb, ha, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(b.truth + np.array([36569.0, 0, 55581.0, 0]), a.truth, rtol=1e-15)
+    assert np.allclose(b.cfg.m0, [0.0, 50.0, 0.0, 50.0])

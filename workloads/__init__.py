@@ -8,6 +8,6 @@ inputs from it without sharing any code of the method.
 """
 from .configs import (  # noqa: F401
     FilterConfig, MeasModel, Scenario, ServingWorkload,
-    c1_scenario, c5_serving, c2_scenario, c3_scenario, c4_batch, small_2d_scenario,
+    c1_scenario, c5_serving, c6_scenario, terrain_params, c2_scenario, c3_scenario, c4_batch, small_2d_scenario,
     small_3d_scenario, random_stable_matrix, simulate,
 )

@@ -60,12 +60,16 @@ class FilterConfig:
 class MeasModel:
     """Measurement model z = h(x) + v, v ~ N(0, R).
 
-    kind: 'linear' (h = H x), 'range' (h = |x_{1:2}|) or 'bearing_linear3'
-    (h = [atan2(x2, x1), x3]).
+    kind: 'linear' (h = H x), 'range' (h = |x_{1:2}|), 'bearing_linear3'
+    (h = [atan2(x2, x1), x3]) or 'terrain_gm' (n_x = 4, state [p_x, v_x, p_y,
+    v_y]: a smooth terrain altitude under the position, two-component Gaussian
+    mixture noise; ``params`` holds the terrain and mixture constants in the
+    layout of pmf_meas.p, and R is the mixture's covariance for reference).
     """
     kind: str
     R: np.ndarray
     H: Optional[np.ndarray] = None
+    params: Optional[np.ndarray] = None
 
     @property
     def nz(self) -> int:
@@ -343,3 +347,77 @@ def c5_serving(n_filters: int = 10000, rate: float = 200e3, duration: float = 60
             L = V * np.sqrt(np.maximum(w, 0.0))[:, None, :]
             X[d][p] = np.einsum("kij,kj->ki", Phi, X[d][p]) + np.einsum("kij,kj->ki", L, rng.standard_normal((r.size, d)))
     return ServingWorkload(cfgs, meas, t_arrival, ids, z, taus)
+
+
+def terrain_params(seed: int = 6) -> np.ndarray:
+    """Seeded smooth terrain and the Sec. VI noise mixture, in the pmf_meas.p
+    layout: four plane waves (amplitude 20-60 m, wavelength 300-1500 m, random
+    direction and phase) on a 500 m base; mixture weights 1/2, 1/2, means 0 and
+    20 m, unit variances.  Stands in for the paper's terrain map, which is not
+    available."""
+    rng = np.random.default_rng(1000 + seed)
+    p = np.zeros(24)
+    for i in range(4):
+        amp, lam, th = rng.uniform(20.0, 60.0), rng.uniform(300.0, 1500.0), rng.uniform(0.0, 2 * np.pi)
+        k = 2 * np.pi / lam
+        p[4 * i:4 * i + 4] = [amp, k * np.cos(th), k * np.sin(th), rng.uniform(0.0, 2 * np.pi)]
+    p[16] = 500.0
+    p[17:22] = [0.5, 0.0, 20.0, 1.0, 1.0]
+    return p
+
+
+def c6_scenario(seed: int = 6, epochs: int = 20, N=34, dt_sub: float = 0.05,
+                terrain_seed: int = 6, local: bool = False) -> Scenario:
+    """The paper's numerical illustration (Sec. VI): coordinated turn with known
+    turn rate alpha = 30 deg/s, state [p_x, v_x, p_y, v_y], diffusion on the
+    velocity axes only (Q = diag(0, 1, 0, 1)), prior N([36569, 50, 55581, 50],
+    diag(90, 160, 5, 5)), sampling period 1 s, N_pa = 34 points per axis;
+    terrain-altitude measurement with two-component Gaussian-mixture noise
+    (synthetic terrain, see terrain_params; one terrain shared by every seed
+    of the trajectory).  The truth advances by the exact discretisation
+    x <- e^{A T} x + w, w ~ N(0, Q_d(T)).
+
+    local=True states the same problem in positions relative to the prior mean
+    (the terrain's wave phases absorb the offset), so that grid coordinates are
+    O(100) m instead of O(50 km)."""
+    rng = np.random.default_rng(600 + seed)
+    a = np.deg2rad(30.0)
+    A = np.array([[0.0, 1.0, 0.0, 0.0], [0.0, 0.0, 0.0, -a], [0.0, 0.0, 0.0, 1.0], [0.0, a, 0.0, 0.0]])
+    Q = np.diag([0.0, 1.0, 0.0, 1.0])
+    m0 = np.array([36569.0, 50.0, 55581.0, 50.0])
+    P0 = np.diag([90.0, 160.0, 5.0, 5.0])
+    Ns = tuple(int(v) for v in (N if np.ndim(N) else (N,) * 4))
+    cfg = FilterConfig(nx=4, N=Ns, A=A, Q=Q, m0=m0, P0=P0, dt_sub=dt_sub)
+    params = terrain_params(terrain_seed)
+    meas = MeasModel("terrain_gm", R=np.array([[1.0]]), params=params)
+    sc = Scenario("c6_4d_coordinated_turn", cfg, meas, dt=1.0, epochs=epochs)
+    C = np.zeros((1, 8, 8))
+    C[0, :4, :4] = -A * sc.dt
+    C[0, :4, 4:] = Q * sc.dt
+    C[0, 4:, 4:] = A.T * sc.dt
+    E = _expm_batch(C)[0]
+    Phi = E[4:, 4:].T
+    Qd = Phi @ E[:4, 4:]
+    w_, V_ = np.linalg.eigh(0.5 * (Qd + Qd.T))
+    Lq = V_ * np.sqrt(np.maximum(w_, 0.0))[None, :]
+    x = m0 + np.linalg.cholesky(P0) @ rng.standard_normal(4)
+    truth, z = [], []
+    for _ in range(epochs):
+        comp = rng.uniform() >= params[17]
+        v = params[19 if comp else 18] + np.sqrt(params[21 if comp else 20]) * rng.standard_normal()
+        alt = params[16] + sum(params[4 * i] * np.sin(params[4 * i + 1] * x[0] + params[4 * i + 2] * x[2]
+                                                      + params[4 * i + 3]) for i in range(4))
+        truth.append(x.copy())
+        z.append(np.array([alt + v]))
+        x = Phi @ x + Lq @ rng.standard_normal(4)
+    sc.truth, sc.z = np.array(truth), np.array(z)
+    if local:
+        o = np.array([m0[0], 0.0, m0[2], 0.0])
+        p = params.copy()
+        for i in range(4):
+            p[4 * i + 3] = np.mod(p[4 * i + 3] + p[4 * i + 1] * o[0] + p[4 * i + 2] * o[2], 2 * np.pi)
+        sc.cfg.m0 = m0 - o
+        sc.meas = MeasModel("terrain_gm", R=np.array([[1.0]]), params=p)
+        sc.truth = sc.truth - o[None, :]
+        sc.name = "c6_4d_coordinated_turn_local"
+    return sc
