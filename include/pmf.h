@@ -65,7 +65,9 @@ enum {
  * frame, the normalisation constant and the moment combination in float64.
  * For n_x = 1 every precision other than FP64 selects the float32 CUDA-core
  * kernel (a 1-D transform is a matrix-vector product, not a tensor-core tile).
- * n_x = 4 runs on the FP64 path only. */
+ * For n_x = 4 every precision other than FP64 selects the float32 4-D kernels
+ * (float32 contractions on the CUDA cores, N <= 64 per axis; the measurement
+ * exponents and moment sums keep float64-class accuracy). */
 enum {
   PMF_PREC_FP64 = 0,
   PMF_PREC_TF32 = 1,
@@ -177,7 +179,7 @@ int pmf_sync(pmf_ctx* ctx);
 
 /* Number of grid points (prod N_m) and the selected path:
  * 0 = plain FP64 kernels, 1 = fused 2-D tensor-core kernel, 2 = 3-D
- * tensor-core pipelines, 3 = 1-D CUDA-core kernel. */
+ * tensor-core pipelines, 3 = 1-D CUDA-core kernel, 4 = float32 4-D kernels. */
 long long pmf_num_points(const pmf_ctx* ctx);
 int pmf_path(const pmf_ctx* ctx);
 

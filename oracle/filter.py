@@ -239,8 +239,11 @@ class OracleFilter:
     def substeps(self, tau: float) -> int:
         return max(1, int(math.ceil(tau / self.cfg.dt_sub - 1e-9)))
 
-    def regrid(self, tau: float) -> dict:
-        """Re-centre and re-size the grid for the prediction over tau (head of the time update)."""
+    def choose_frame(self, tau: float) -> dict:
+        """The regrid decision of the time update over tau (reading of Sec. V):
+        re-aligned frame (Mnew, centre m) when the whitened correlation of the
+        pulled-back predicted covariance exceeds realign_rho, otherwise the
+        per-axis scales D and the centre shift s (both quantised)."""
         n = self.n
         m, C = self.moments()
         Phi, Qd = model.van_loan(self.A, self.Q, tau)
@@ -258,7 +261,38 @@ class OracleFilter:
         if n >= 2 and rho > self.cfg.realign_rho:
             Lp = np.linalg.cholesky(0.5 * (Ppred + Ppred.T))
             Mnew = quantize_matrix(Phinv @ Lp @ np.diag([2.0 * span / Nm for Nm in self.N]))
-            m = self.c + self.M @ quantize_shift(Minv @ (m - self.c))
+            s = quantize_shift(Minv @ (m - self.c))
+            return {"realigned": True, "rho": rho, "M": Mnew, "s": s}
+        D = np.array([quantize_scale(2.0 * span * sd[a] / self.N[a]) for a in range(n)])
+        s = quantize_shift(Minv @ (m - self.c))
+        return {"realigned": False, "rho": rho, "D": D, "s": s}
+
+    def frame_from_target(self, tau: float, c_after, M_after) -> dict:
+        """Test helper: the regrid decision whose frame, moved over tau, is the
+        given (c_after, M_after) (a frame chosen by another implementation from
+        its own moments).  The decision is read back onto the quantisation
+        lattices, so it is exact when the target lies on them."""
+        Phi = model.expm(self.A * tau)
+        Mt = np.linalg.solve(Phi, np.asarray(M_after, dtype=float))
+        ct = np.linalg.solve(Phi, np.asarray(c_after, dtype=float))
+        Minv = np.linalg.inv(self.M)
+        s = quantize_shift(Minv @ (ct - self.c))
+        R = Minv @ Mt                       # diagonal iff the frame was only rescaled
+        off = np.abs(R - np.diag(np.diag(R))).max()
+        if off <= 1e-9 * np.abs(np.diag(R)).max():
+            D = np.array([quantize_scale(d) for d in np.diag(R)])
+            return {"realigned": False, "rho": None, "D": D, "s": s}
+        return {"realigned": True, "rho": None, "M": quantize_matrix(Mt), "s": s}
+
+    def regrid(self, tau: float, choice: dict = None) -> dict:
+        """Re-centre and re-size the grid for the prediction over tau (head of the
+        time update), with the decision of choose_frame (or the one given)."""
+        n = self.n
+        ch = self.choose_frame(tau) if choice is None else choice
+        Minv = np.linalg.inv(self.M)
+        m = self.c + self.M @ ch["s"]
+        if ch["realigned"]:
+            Mnew = ch["M"]
             if self.realign_mode == "shear":
                 # u_old = Minv (c' + M' u_new - c) = B u_new + b
                 self.P = shear_realign(self.P, Minv @ Mnew, Minv @ (m - self.c))
@@ -267,22 +301,18 @@ class OracleFilter:
                 u_old = (x - self.c[None, :]) @ Minv.T
                 zidx = u_old + (np.array(self.N) - 1) / 2.0
                 self.P = multilinear(self.P, zidx).reshape(self.N)
-            realigned = True
         else:
-            D = np.array([quantize_scale(2.0 * span * sd[a] / self.N[a]) for a in range(n)])
+            D = ch["D"]
             Mnew = self.M @ np.diag(D)
-            s = quantize_shift(Minv @ (m - self.c))
             P = self.P
             for a in range(n):
-                pos = s[a] + D[a] * grid_u(self.N[a]) + (self.N[a] - 1) / 2.0
+                pos = ch["s"][a] + D[a] * grid_u(self.N[a]) + (self.N[a] - 1) / 2.0
                 P = _first_interp_axis(P, a, pos, self.N[a])
             self.P = P
-            realigned = False
-            m = self.c + self.M @ s
         self.c = m.copy()
         self.M = Mnew
         self.normalise()
-        self.last_regrid = {"realigned": realigned, "rho": rho}
+        self.last_regrid = {"realigned": ch["realigned"], "rho": ch["rho"]}
         return self.last_regrid
 
     def diffusion_multiplier(self, tau: float):
@@ -338,7 +368,7 @@ class OracleFilter:
         self.last_mass_ratio = self.cell_volume * self.P.sum() / mass0
         self.normalise()                             # step 6
 
-    def time_update(self, tau: float) -> dict:
-        info = self.regrid(tau)
+    def time_update(self, tau: float, choice: dict = None) -> dict:
+        info = self.regrid(tau, choice)
         self.spectral_step(tau)
         return info

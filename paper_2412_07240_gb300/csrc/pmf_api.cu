@@ -11,6 +11,7 @@
 #include "pmf_internal.cuh"
 #include "pmf_kernels.cuh"
 #include "pmf_model.cuh"
+#include "pmf_f4.cuh"
 #include "pmf_tc.cuh"
 
 using namespace pmf;
@@ -20,7 +21,8 @@ struct pmf_ctx {
   cudaStream_t stream = nullptr;
   Dims dims{};
   int path = 0;               // 0 float64 kernels, 1 fused 2-D tensor-core kernel,
-                              // 2 3-D tensor-core pipelines, 3 1-D CUDA-core kernel
+                              // 2 3-D tensor-core pipelines, 3 1-D CUDA-core kernel,
+                              // 4 float32 4-D kernels
   DevState* st = nullptr;     // device
   void* buf[2] = {nullptr, nullptr};
   double* partials = nullptr;
@@ -31,6 +33,7 @@ struct pmf_ctx {
   double* prior_aux = nullptr;  // P0^{-1} (n*n) and m0 at kAuxM0
   double* scratch = nullptr;    // float64 path, shear re-alignment: intermediate grid
   TcTables tct{};               // tensor-core path tables (pmf_tc.cu)
+  F4Tables f4{};                // float32 4-D path tables and scratch (pmf_f4.cu)
   void* tab1 = nullptr;         // 1-D kernel table (pmf_tc1.cu)
   int mode1 = 0;                // 1-D Hartley form (autotuned)
   void* tc3 = nullptr;          // 3-D pipeline state (pmf_tc3.cu)
@@ -83,13 +86,23 @@ void free_ctx(pmf_ctx* ctx) {
   }
   tc_free_tables(&ctx->tct);
   tc3_free(ctx->tc3);
+  f4_free(&ctx->f4);
   cudaFree(ctx->tab1);
   cudaFree(ctx->scratch);
   delete ctx;
 }
 
-// One launch (2-D fused kernel) or the 3-D pipelines; returns kernel launches.
+// The fast paths (fused 2-D kernel, 3-D pipelines, 1-D kernel, 4-D kernels);
+// returns the kernel launches.
 int fast_step(pmf_ctx* ctx, const MeasParams* mp, const TimeConsts* tc) {
+  if (ctx->path == 4) {
+    int n = 0;
+    if (mp) n += f4_meas(ctx->dims, *mp, ctx->st, ctx->f4, (float*)ctx->buf[0], (float*)ctx->buf[1],
+                         ctx->partials, ctx->stream);
+    if (tc) n += f4_time(ctx->dims, *tc, ctx->st, ctx->f4, (float*)ctx->buf[0], (float*)ctx->buf[1],
+                         ctx->partials, ctx->pend, ctx->stream);
+    return n;
+  }
   if (ctx->path == 3)
     return tc1_step(ctx->cfg.N[0], ctx->tab1, mp, tc, ctx->st, (float*)ctx->buf[0], (float*)ctx->buf[1],
                     ctx->stream, ctx->mode1);
@@ -146,12 +159,14 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
   const long long P = ctx->dims.P;
 
   if (cfg->precision != PMF_PREC_FP64) {
-    rc = cfg->nx == 1 ? tc1_supported(cfg, &why) : tc_supported(cfg, &why);
+    rc = cfg->nx == 1   ? tc1_supported(cfg, &why)
+         : cfg->nx == 4 ? f4_supported(cfg, &why)
+                        : tc_supported(cfg, &why);
     if (rc) {
       free_ctx(ctx);
       return rc;
     }
-    ctx->path = cfg->nx == 1 ? 3 : cfg->nx == 3 ? 2 : 1;
+    ctx->path = cfg->nx == 1 ? 3 : cfg->nx == 4 ? 4 : cfg->nx == 3 ? 2 : 1;
   } else {
     // the float64 per-axis transforms tile lines 16 x 16 with the leading axes
     // on grid.z and the last axis' lines on grid.y (each at most 65535)
@@ -193,6 +208,12 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
       hartley_host(N, 1.0, H);
       cudaMemcpy(ctx->hinv[a], H, sizeof(double) * N * N, cudaMemcpyHostToDevice);
       delete[] H;
+    }
+  } else if (ctx->path == 4) {
+    rc = f4_alloc(cfg, &ctx->f4);
+    if (rc) {
+      free_ctx(ctx);
+      return rc;
     }
   } else if (ctx->path == 3) {
     rc = tc1_build_table(cfg->N[0], &ctx->tab1);

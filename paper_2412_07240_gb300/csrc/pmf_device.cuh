@@ -353,8 +353,152 @@ __device__ inline bool finalize_t(FrameState* st, const double* tot, int use_pen
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double lget(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
+// Regrid decision in lanes for any n <= 4 (both branches): lane e < n*n holds
+// matrix entry (e / n, e % n), lanes < n per-axis values; the products, the
+// Cholesky factor (column by column) and the inverse (adjugate) of the new
+// axes run in parallel lanes.  Same quantities as frame_scalar; used for the
+// re-alignment branch and for n = 4.
+template <int n>
+__device__ inline void frame_warp_full(const TimeConsts& tc, FrameState* st, double* pend, double* Mpi) {
+  constexpr int nn = n * n;
+  const int lane = threadIdx.x & 31;
+  const int e = lane < nn ? lane : 0;
+  const int i = e / n, j = e % n;
+  const int a = lane < n ? lane : 0;
+  // Su = Minv (cov + Qb) Minv^T (upper triangle mirrored)
+  const double S = st->cov[e] + tc.Qb[e];
+  double T = 0.0;
+#pragma unroll
+  for (int k = 0; k < n; ++k) T = fma(st->Minv[i * n + k], lget(S, k * n + j), T);
+  double C = 0.0;
+#pragma unroll
+  for (int k = 0; k < n; ++k) C = fma(lget(T, i * n + k), st->Minv[j * n + k], C);
+  const double Su = lget(C, i <= j ? e : j * n + i);
+  const double Saa = lget(Su, a * (n + 1));
+  bool realign = false;
+  if (n >= 2) {
+    const double r2 = tc.rho_max * tc.rho_max;
+    const double Sii = lget(Su, i * (n + 1)), Sjj = lget(Su, j * (n + 1));
+    realign = __any_sync(0xffffffffu, lane < nn && i < j && Su * Su > r2 * Sii * Sjj);
+  }
+  double Mp = 0.0, Mpie = 0.0;
+  if (realign) {
+    // Pp = Phi S Phi^T, its Cholesky factor L (lane (i, k) holds L_ik, i >= k)
+    double U = 0.0;
+#pragma unroll
+    for (int k = 0; k < n; ++k) U = fma(tc.Phi[i * n + k], lget(S, k * n + j), U);
+    double W = 0.0;
+#pragma unroll
+    for (int k = 0; k < n; ++k) W = fma(lget(U, i * n + k), tc.Phi[j * n + k], W);
+    const double Pp = lget(W, i <= j ? e : j * n + i);
+    double L = 0.0;
+    bool pd = true;
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+      double t = Pp;
+#pragma unroll
+      for (int m = 0; m < k; ++m) t -= lget(L, i * n + m) * lget(L, k * n + m);
+      const double dkk = lget(t, k * n + k);
+      pd = pd && dkk > 0.0;
+      const double d = sqrt(fmax(dkk, 0.0)), rd = 1.0 / d;
+      if (lane < nn && j == k && i >= k) L = i == k ? d : t * rd;
+    }
+    if (pd) {
+      // Mp = e^{-A tau} L diag(2 span / N), entries rounded to a 12-bit mantissa
+      double T2 = 0.0;
+#pragma unroll
+      for (int k = 0; k < n; ++k) T2 = fma(tc.PhiInv[i * n + k], lget(L, k * n + j), T2);
+      int ex;
+      const double f = frexp(T2 * (2.0 * tc.span / tc.N[j]), &ex);
+      Mp = ldexp(rint(ldexp(f, 12)), ex - 12);
+      // Mpi = adj(Mp) / det(Mp): lane (i, j) forms the cofactor of entry (i, j)
+      double cof;
+      if constexpr (n == 1) {
+        cof = 1.0;
+      } else {
+        constexpr int m = n - 1;
+        double mv[m * m];
+#pragma unroll
+        for (int rr = 0; rr < m; ++rr)
+#pragma unroll
+          for (int cc = 0; cc < m; ++cc)
+            mv[rr * m + cc] = lget(Mp, (rr + (rr >= i)) * n + cc + (cc >= j));
+        cof = ((i + j) & 1 ? -1.0 : 1.0) * det_t<m>(mv);
+      }
+      double dt = 0.0;
+#pragma unroll
+      for (int k = 0; k < n; ++k) dt = fma(lget(Mp, k), lget(cof, k), dt);
+      Mpie = lget(cof, j * n + i) * (1.0 / dt);
+    } else {
+      realign = false;   // not positive definite: keep the separable regrid
+    }
+  }
+  // centre shift towards the mean, a multiple of 1/64 node (lanes a)
+  const double dd = st->mean[a] - st->c[a];
+  double dm = 0.0;
+#pragma unroll
+  for (int b = 0; b < n; ++b) dm = fma(st->Minv[a * n + b], lget(dd, b), dm);
+  dm = rint(dm * 64.0) * (1.0 / 64.0);
+  double cn = st->c[a];
+#pragma unroll
+  for (int b = 0; b < n; ++b) cn = fma(st->M[a * n + b], lget(dm, b), cn);
+  if (realign) {
+    // regrid map u_old = B u_new + b with B = Minv Mp, b = the shift
+    double Bv = 0.0;
+#pragma unroll
+    for (int k = 0; k < n; ++k) Bv = fma(st->Minv[i * n + k], lget(Mp, k * n + j), Bv);
+    __syncwarp();
+    if (lane < nn) st->B[lane] = Bv;
+    if (lane < n) st->b[lane] = dm;
+  } else {
+    // separable scale with an 8-bit mantissa (lanes a)
+    const double sd = sqrt(fmax(Saa, 0.0));
+    int ex;
+    const double f = frexp(2.0 * tc.span * sd / tc.N[a], &ex);
+    const double D = ldexp(rint(ldexp(f, 8)), ex - 8);
+    const double rD = 1.0 / D;
+    Mp = st->M[e] * lget(D, j);
+    Mpie = st->Minv[e] * lget(rD, i);
+    __syncwarp();
+    if (lane < n) {
+      st->rs[lane] = dm;
+      st->rd[lane] = D;
+    }
+  }
+  // pending frame after the move: Phi Mp, Mpi PhiInv, centre Phi c'
+  double nM = 0.0, nMi = 0.0, pc = 0.0;
+#pragma unroll
+  for (int k = 0; k < n; ++k) {
+    nM = fma(tc.Phi[i * n + k], lget(Mp, k * n + j), nM);
+    nMi = fma(lget(Mpie, i * n + k), tc.PhiInv[k * n + j], nMi);
+    pc = fma(tc.Phi[a * n + k], lget(cn, k), pc);
+  }
+  double nMv[nn];
+#pragma unroll
+  for (int q = 0; q < nn; ++q) nMv[q] = lget(nM, q);
+  const double det = det_t<n>(nMv);
+  if (lane < nn) {
+    pend[pend_M(n) + lane] = nM;
+    pend[pend_Mi(n) + lane] = nMi;
+    Mpi[lane] = Mpie;
+  }
+  if (lane < n) pend[lane] = pc;
+  if (lane == 0) {
+    st->realign = realign ? 1 : 0;
+    st->exact = tc.exact;
+    st->l = tc.exact ? 1 : tc.l;
+    st->g = tc.g;
+    pend[pend_V(n)] = fabs(det);
+  }
+  __syncwarp();
+}
+
 template <int n>
 __device__ inline void frame_warp(const TimeConsts& tc, FrameState* st, double* pend, double* Mpi) {
+  if constexpr (n == 4) {
+    frame_warp_full<4>(tc, st, pend, Mpi);
+    return;
+  }
   constexpr int nn = n * n;
   const int lane = threadIdx.x & 31, h = lane & 15;
   const bool up = lane >= 16;
@@ -378,9 +522,7 @@ __device__ inline void frame_warp(const TimeConsts& tc, FrameState* st, double* 
     realign = __any_sync(0xffffffffu, lane < nn && i < j && Su * Su > r2 * Sii * Sjj);
   }
   if (realign) {
-    // rare: the one-thread form takes the re-alignment branch
-    if (lane == 0) frame_scalar<n>(tc, st, pend, Mpi);
-    __syncwarp();
+    frame_warp_full<n>(tc, st, pend, Mpi);
     return;
   }
   // centre shift towards the mean, a multiple of 1/64 node (lanes a)
@@ -461,13 +603,12 @@ __device__ inline bool finalize_warp(FrameState* st, const double* tot, int use_
   const int i = e / n, j = e % n;
   const int a = h < n ? h : 0;
   const double* c = use_pending ? pend : st->c;
-  const double* M = use_pending ? pend + 3 : st->M;
-  const double V = use_pending ? pend[21] : st->V;
+  const double* M = use_pending ? pend + pend_M(n) : st->M;
+  const double V = use_pending ? pend[pend_V(n)] : st->V;
   const double r = 1.0 / S0;
   const double mu = tot[1 + a] * r;
   const double mui = lget(mu, i), muj = lget(mu, j);
-  const int k2 = i == j ? (i == 0 ? 4 : i == 1 ? 7 : 9) : (i + j == 1 ? 5 : i + j == 2 ? 6 : 8);
-  const double Cu = fma(tot[k2], r, -mui * muj);
+  const double Cu = fma(tot[tot_S2(n, i, j)], r, -mui * muj);
   // T = M Cu (lower half-warp) and the mean c + M mu (upper lanes a)
   double s = up ? c[a] : 0.0;
 #pragma unroll
@@ -482,8 +623,8 @@ __device__ inline bool finalize_warp(FrameState* st, const double* tot, int use_
   const double cov = lget(C, i <= j ? e : j * n + i);
   double Mv = 0.0, Miv = 0.0;
   if (use_pending) {
-    Mv = pend[3 + e];
-    Miv = pend[12 + e];
+    Mv = pend[pend_M(n) + e];
+    Miv = pend[pend_Mi(n) + e];
   }
   __syncwarp();
   if (up && h < n) st->mean[h] = s;

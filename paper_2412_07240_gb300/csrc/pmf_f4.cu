@@ -1,0 +1,631 @@
+// Float32 path for n_x = 4 grids (the coordinated-turn workload of Sec. VI and
+// any other four-dimensional filter).  The weights live in float32; the
+// per-axis transforms are float32 contractions on the CUDA cores; the frame
+// arithmetic, the regrid matrices, the measurement exponents and the moment
+// sums keep float64-class accuracy.
+//
+// Per time update (Sec. V-B algorithm on the moving grid, eq. gridMov):
+//   frame        regrid decision and sub-step coefficients (float64, shared
+//                with the float64 path)
+//   interp x 4   trigonometric regrid matrix of each axis (eq. interFreq,
+//                float64, shared with the float64 path)
+//   fuse         W_a = H_a I_a per axis (regrid folded into the forward
+//                Hartley transform), rounded to float32
+//   realign      multilinear re-alignment (or scaled copy) of the weights
+//   fwd x 4      W_a along axis a
+//   psi          diffusion multiplier and trace factor over 16-point sign-flip
+//                orbits (the separable-to-4-D Hartley parity fix-up)
+//   inv x 4      inverse Hartley transform along each axis (step 5)
+//   moments      normaliser and moments in double-float, finalised in float64
+// Per measurement update (eq. filt): exponent parts and their minimum, then
+// the likelihood multiply with the moment sums, then the finalisation.
+#include <cmath>
+#include <vector>
+
+#include "pmf_f4.cuh"
+#include "pmf_grid.cuh"
+#include "pmf_kernels.cuh"
+#include "pmf_model.cuh"
+#include "pmf_tcops.cuh"
+
+namespace pmf {
+namespace {
+
+constexpr int kMaxN4 = 64;
+constexpr int kCols = 64;               // lines per block of the axis transform
+constexpr int kAxisThreads = 256;       // four threads per line (output groups q, q + 4)
+constexpr int kColStr = kCols + 1;      // shared stride of a tile row (conflict-free column reads)
+constexpr int kMomBlocks = 304;         // moment partial blocks (2 per SM)
+
+__host__ __device__ inline int kpad(int N) { return (N + 7) & ~7; }
+
+size_t axis_smem(int N) { return sizeof(float) * (2 * (size_t)N * kColStr + (size_t)N * kpad(N)); }
+
+// ---- measurement update, pass 1 -------------------------------------------
+// Terrain altitude (Sec. VI): base + sum_i amp_i sin(phi_i), phi_i = kx_i x_0 +
+// ky_i x_2 + ph_i with x = c + M u, so phi_i = theta_i + sum_a g_ia u_a with
+// theta_i = kx_i c_0 + ky_i c_2 + ph_i and g_ia = kx_i M_0a + ky_i M_2a.  One
+// block per (j0, j1) slab: e^{i(theta + g_0 u_0 + g_1 u_1)} once per block,
+// times e^{i g_2 u_2} and the amplitude as a shared table over j2, e^{i g_3 u_3}
+// as a table over j3, and the sine of every point by angle addition in float64
+// (two fused multiply-adds per wave).  The mixture exponent is kept as its
+// smaller component m_lo and the gap |m_1 - m_2| (e = m_lo - log(1 + e^-gap));
+// other measurement kinds store e itself with an infinite gap.
+__global__ void k_f4_meas_e(Dims d, MeasParams mp, DevState* st, double* lo_out, float* gap_out) {
+  __shared__ double2 t2[4][kMaxN4], t3[4][kMaxN4];
+  __shared__ double2 base[4];
+  __shared__ double gg[4][4];
+  __shared__ double wmin[32];
+  const int N2 = d.N[2], N3 = d.N[3];
+  const int j0 = blockIdx.x / d.N[1], j1 = blockIdx.x % d.N[1];
+  const double u0 = j0 - 0.5 * (d.N[0] - 1), u1 = j1 - 0.5 * (d.N[1] - 1);
+  const double* c = st->f.c;
+  const double* M = st->f.M;
+  const bool terrain = mp.kind == PMF_MEAS_TERRAIN_GM;
+  if (terrain) {
+    if (threadIdx.x < 4) {
+      const int i = threadIdx.x;
+      const double kx = mp.p[4 * i + 1], ky = mp.p[4 * i + 2];
+      for (int a = 0; a < 4; ++a) gg[i][a] = kx * M[a] + ky * M[8 + a];
+      const double ph = kx * c[0] + ky * c[2] + mp.p[4 * i + 3] + gg[i][0] * u0 + gg[i][1] * u1;
+      double sn, cs;
+      sincos(ph, &sn, &cs);
+      base[i] = make_double2(cs, sn);
+    }
+    __syncthreads();
+    // t2 holds amp_i e^{i(theta + g_0 u_0 + g_1 u_1 + g_2 u_2)}, t3 e^{i g_3 u_3}
+    for (int t = threadIdx.x; t < 4 * (N2 + N3); t += blockDim.x) {
+      const int i = t / (N2 + N3), r = t % (N2 + N3);
+      const bool ax2 = r < N2;
+      const int j = ax2 ? r : r - N2;
+      const double u = j - 0.5 * ((ax2 ? N2 : N3) - 1);
+      double sn, cs;
+      sincos(gg[i][ax2 ? 2 : 3] * u, &sn, &cs);
+      if (ax2) {
+        const double2 q = base[i];
+        const double amp = mp.p[4 * i];
+        t2[i][j] = make_double2(amp * (q.x * cs - q.y * sn), amp * (q.x * sn + q.y * cs));
+      } else {
+        t3[i][j] = make_double2(cs, sn);
+      }
+    }
+    __syncthreads();
+  }
+  const long long p0 = (long long)blockIdx.x * N2 * N3;
+  double emin = INFINITY;
+  for (int t = threadIdx.x; t < N2 * N3; t += blockDim.x) {
+    const int j2 = t / N3, j3 = t % N3;
+    double lo;
+    float gap;
+    if (terrain) {
+      double h = mp.p[16];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const double2 a = t2[i][j2], b = t3[i][j3];
+        h = fma(a.x, b.y, fma(a.y, b.x, h));    // amp_i sin(phi_i) = Im(a b)
+      }
+      const double rr = mp.z[0] - h;
+      const double m1 = (rr - mp.gm[4]) * (rr - mp.gm[4]) * mp.gm[0] + mp.gm[2];
+      const double m2 = (rr - mp.gm[5]) * (rr - mp.gm[5]) * mp.gm[1] + mp.gm[3];
+      lo = fmin(m1, m2);
+      gap = (float)fabs(m1 - m2);
+    } else {
+      const double u[4] = {u0, u1, j2 - 0.5 * (N2 - 1), j3 - 0.5 * (N3 - 1)};
+      double x[4];
+      for (int a = 0; a < 4; ++a) {
+        x[a] = c[a];
+        for (int b = 0; b < 4; ++b) x[a] += M[a * 4 + b] * u[b];
+      }
+      lo = meas_exponent_f64(mp, x);
+      gap = INFINITY;
+    }
+    lo_out[p0 + t] = lo;
+    gap_out[p0 + t] = gap;
+    emin = fmin(emin, lo);
+  }
+  for (int o = 16; o; o >>= 1) emin = fmin(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+  if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = emin;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) emin = fmin(emin, wmin[w]);
+    // every exponent is >= 0 (Gaussian forms; mixture constants shifted on the
+    // host), so the bit patterns order like the values
+    atomicMin(&st->emin_bits, (unsigned long long)__double_as_longlong(emin));
+  }
+}
+
+// Double-float moment sums of one thread in the tot_S2 layout for n_x = 4:
+// {S0, S1[4], S2[10]}.
+struct Mom4 {
+  DF s[kMomentSlots];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < kMomentSlots; ++i) s[i] = DF{0.0f, 0.0f};
+  }
+  __device__ __forceinline__ void add(float v, const float* u) {
+    s[0] = df_add1(s[0], v);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const float vu = v * u[a];
+      s[1 + a] = df_add1(s[1 + a], vu);
+#pragma unroll
+      for (int b = a; b < 4; ++b) s[tot_S2(4, a, b)] = df_add1(s[tot_S2(4, a, b)], vu * u[b]);
+    }
+  }
+};
+
+// Block sum of the double-float moment sums into float64 partials.
+__device__ void mom4_block(Mom4& m, double* out) {
+  __shared__ DF red[32][kMomentSlots];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < kMomentSlots; ++i)
+    for (int o = 16; o; o >>= 1) {
+      DF b{__shfl_xor_sync(0xffffffffu, m.s[i].hi, o), __shfl_xor_sync(0xffffffffu, m.s[i].lo, o)};
+      m.s[i] = df_add(m.s[i], b);
+    }
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < kMomentSlots; ++i) red[warp][i] = m.s[i];
+  __syncthreads();
+  if (warp == 0 && lane < kMomentSlots) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += (double)red[w][lane].hi + (double)red[w][lane].lo;
+    out[lane] = t;
+  }
+}
+
+// Node indices of flat point p (C order, four axes; constant indexing keeps
+// them in registers).
+__device__ __forceinline__ void unflatten4(const Dims& d, long long p, int* j) {
+#pragma unroll
+  for (int m = 3; m >= 0; --m) {
+    j[m] = (int)(p % d.N[m]);
+    p /= d.N[m];
+  }
+}
+
+__device__ __forceinline__ void frame_u4(const Dims& d, long long p, float* u) {
+  int j[4];
+  unflatten4(d, p, j);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) u[a] = j[a] - 0.5f * (d.N[a] - 1);
+}
+
+// ---- measurement update, pass 2: likelihood multiply and moment sums ----
+__global__ void k_f4_meas_apply(Dims d, DevState* st, const double* lo, const float* gap, float* b0,
+                                float* b1, double* partials) {
+  const int cur = st->f.cur;
+  const float* in = cur ? b1 : b0;
+  float* out = cur ? b0 : b1;
+  const double emin = __longlong_as_double((long long)st->emin_bits);
+  const float ps = (float)st->f.pscale;
+  Mom4 m;
+  m.zero();
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
+       p += (long long)gridDim.x * blockDim.x) {
+    const float f = expf((float)(emin - lo[p])) * (1.0f + expf(-gap[p]));
+    const float v = (in[p] * ps) * f;
+    out[p] = v;
+    float u[4];
+    frame_u4(d, p, u);
+    m.add(v, u);
+  }
+  mom4_block(m, partials + blockIdx.x * kMomentSlots);
+}
+
+// ---- time update ------------------------------------------------------------
+// W_a^T (row j, column k, k padded to a multiple of 8 with zeros) of the fused
+// regrid + forward transform W_a = H_a I_a, formed in float64: one block per
+// (axis, j), one thread per k.
+__global__ void k_f4_fuse(Dims d, const F4Tables t) {
+  const int a = blockIdx.y, N = d.N[a], j = blockIdx.x;
+  if (j >= N) return;
+  const int Kp = kpad(N);
+  for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
+    double s = 0.0;
+    if (k < N)
+      for (int q = 0; q < N; ++q) s += t.hfwd[a][(size_t)k * N + q] * t.interp[a][(size_t)q * N + j];
+    t.wfwd[a][(size_t)j * Kp + k] = (float)s;
+  }
+}
+
+// Multilinear re-alignment of the weights onto the new frame (u_old = B u_new
+// + b, 16 corners; nodes outside the old box contribute 0), or the scaled copy
+// when the frame was not re-aligned.  Reads buf[cur], writes buf[cur ^ 1].
+// A block takes kLinesR lines along axis 3: the old-index position of each
+// line's first node is formed once in float64 (split into an integer and a
+// fraction), and a node adds B_a3 j3 in float64; the corner weights and sums
+// are float32.
+constexpr int kLinesR = 8;
+
+__global__ void __launch_bounds__(256) k_f4_realign(Dims d, const DevState* st, float* b0, float* b1) {
+  __shared__ double zl[kLinesR][4];
+  const int cur = st->f.cur;
+  const float* in = cur ? b1 : b0;
+  float* out = cur ? b0 : b1;
+  const float ps = (float)st->f.pscale;
+  const int P = (int)d.P, N3 = d.N[3];
+  if (!st->f.realign) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) out[p] = ps * in[p];
+    return;
+  }
+  const int lines = P / N3;
+  const int N0 = d.N[0], N1 = d.N[1], N2 = d.N[2];
+  for (int l0 = blockIdx.x * kLinesR; l0 < lines; l0 += gridDim.x * kLinesR) {
+    if (threadIdx.x < kLinesR * 4) {
+      const int li = threadIdx.x >> 2, a = threadIdx.x & 3, ln = l0 + li;
+      if (ln < lines) {
+        const int j2 = ln % N2, j1 = (ln / N2) % N1, j0 = ln / (N2 * N1);
+        const double u[4] = {j0 - 0.5 * (N0 - 1), j1 - 0.5 * (N1 - 1), j2 - 0.5 * (N2 - 1), -0.5 * (N3 - 1)};
+        double z = st->f.b[a] + 0.5 * (d.N[a] - 1);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) z = fma(st->f.B[a * 4 + b], u[b], z);
+        zl[li][a] = z;
+      }
+    }
+    __syncthreads();
+    const int cnt = min(kLinesR, lines - l0) * N3;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      const int li = t / N3, j3 = t - li * N3;
+      int f[4];
+      float w[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const double z = fma(st->f.B[a * 4 + 3], (double)j3, zl[li][a]);
+        const double fl = floor(z);
+        f[a] = (int)fmax(fmin(fl, 1e6), -1e6);
+        w[a] = (float)(z - fl);
+      }
+      float sum = 0.0f;
+#pragma unroll
+      for (int corner = 0; corner < 16; ++corner) {
+        float wt = 1.0f;
+        int off = 0;
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int bit = (corner >> a) & 1;
+          const int i = f[a] + bit;
+          wt *= bit ? w[a] : 1.0f - w[a];
+          ok = ok && i >= 0 && i < d.N[a];
+          off = off * d.N[a] + (ok ? i : 0);
+        }
+        if (ok) sum = fmaf(wt, in[off], sum);
+      }
+      out[(l0 + li) * N3 + j3] = ps * sum;
+    }
+    __syncthreads();
+  }
+}
+
+// Y = W x_axis X on the float32 grid viewed as [outer][N][inner] (C order):
+// a block takes kCols consecutive lines along the axis (line = (outer, inner)
+// pair) and stages them as a [N][kCols] tile; thread (line c, quarter q)
+// forms the outputs k of groups q, q + 4 (8 accumulators per group), the 8
+// weights of a group being two float4 broadcasts of W^T.  Reads
+// bufs[(cur+stage)&1], writes the other one.  Indices fit 32 bits (N <= 64).
+__global__ void __launch_bounds__(kAxisThreads) k_f4_axis(Dims d, int axis, const float* WT,
+                                                          const DevState* st, int stage, float* b0,
+                                                          float* b1) {
+  extern __shared__ __align__(16) float sm[];
+  const int N = d.N[axis], Kp = kpad(N);
+  int inner = 1;
+#pragma unroll
+  for (int m = 1; m < 4; ++m)
+    if (m > axis) inner *= d.N[m];
+  const int lines = (int)d.P / N;
+  const int l0 = blockIdx.x * kCols;
+  const int nl = min(kCols, lines - l0);
+  float* Xs = sm;
+  float* Ys = sm + N * kColStr;
+  float* Ws = Ys + N * kColStr;
+  const int par = (st->f.cur + stage) & 1;
+  const float* X = par ? b1 : b0;
+  float* Y = par ? b0 : b1;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < N * Kp; i += kAxisThreads) Ws[i] = WT[i];
+  if (inner == 1) {
+    const float* src = X + l0 * N;
+    for (int t = tid; t < nl * N; t += kAxisThreads) {
+      const int c = t / N, j = t - c * N;
+      Xs[j * kColStr + c] = src[t];
+    }
+  } else {
+    for (int t = tid; t < N * kCols; t += kAxisThreads) {
+      const int j = t / kCols, c = t - j * kCols;
+      if (c < nl) {
+        const int ln = l0 + c, o = ln / inner, i = ln - o * inner;
+        Xs[j * kColStr + c] = X[(o * N + j) * inner + i];
+      }
+    }
+  }
+  __syncthreads();
+  const int c = tid % kCols, q = tid / kCols;
+  if (c < nl) {
+    for (int k0 = 8 * q; k0 < N; k0 += 8 * (kAxisThreads / kCols)) {
+      float acc[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) acc[r] = 0.0f;
+#pragma unroll 2
+      for (int j = 0; j < N; ++j) {
+        const float x = Xs[j * kColStr + c];
+        const float4 w0 = *(const float4*)(Ws + j * Kp + k0);
+        const float4 w1 = *(const float4*)(Ws + j * Kp + k0 + 4);
+        acc[0] = fmaf(w0.x, x, acc[0]);
+        acc[1] = fmaf(w0.y, x, acc[1]);
+        acc[2] = fmaf(w0.z, x, acc[2]);
+        acc[3] = fmaf(w0.w, x, acc[3]);
+        acc[4] = fmaf(w1.x, x, acc[4]);
+        acc[5] = fmaf(w1.y, x, acc[5]);
+        acc[6] = fmaf(w1.z, x, acc[6]);
+        acc[7] = fmaf(w1.w, x, acc[7]);
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        if (k0 + r < N) Ys[(k0 + r) * kColStr + c] = acc[r];
+    }
+  }
+  __syncthreads();
+  if (inner == 1) {
+    float* dst = Y + l0 * N;
+    for (int t = tid; t < nl * N; t += kAxisThreads) {
+      const int cc = t / N, j = t - cc * N;
+      dst[t] = Ys[j * kColStr + cc];
+    }
+  } else {
+    for (int t = tid; t < N * kCols; t += kAxisThreads) {
+      const int j = t / kCols, cc = t - j * kCols;
+      if (cc < nl) {
+        const int ln = l0 + cc, o = ln / inner, i = ln - o * inner;
+        Y[(o * N + j) * inner + i] = Ys[j * kColStr + cc];
+      }
+    }
+  }
+}
+
+// Diffusion multiplier and trace factor in the Hartley domain (algorithm
+// steps 2-4) for n_x = 4: one thread per orbit {sigma . k} of the 16 sign
+// flips.  The separable coefficients S split into parity components T_B (odd
+// in the axes of B), the multiplier into its jointly-even components Psi_E,
+// and T'_C = sum_{|E| even} (-1)^{|E|/2 + |E & C|} Psi_E T_{E ^ C}.
+// Over an orbit |kappa_a| is fixed and the first-derivative coefficients flip
+// sign with sigma_a, so a sub-step exponent is E_q + sum_{a<b} sigma_a sigma_b
+// X_q,ab: eight distinct values (sigma and -sigma agree), formed from one
+// read of the sub-step coefficients.  float32 arithmetic; the coefficients are
+// rounded from float64 once per block.
+__global__ void __launch_bounds__(128) k_f4_psi(Dims d, const DevState* st, int stage, float* b0,
+                                                float* b1) {
+  __shared__ float spa[MAXL][4], spb[MAXL][6];
+  const int par = (st->f.cur + stage) & 1;
+  float* X = par ? b1 : b0;
+  const int l = st->f.l, exact = st->f.exact;
+  const float g = (float)st->f.g;
+  for (int q = threadIdx.x; q < l; q += blockDim.x) {
+    for (int a = 0; a < 4; ++a) spa[q][a] = (float)st->pa[q][a];
+    for (int a = 0; a < 6; ++a) spb[q][a] = (float)st->pb[q][a];
+  }
+  __syncthreads();
+  int H[4], N[4];
+  int reps = 1;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    N[a] = d.N[a];
+    H[a] = N[a] / 2 + 1;
+    reps *= H[a];
+  }
+  const float two_pi = 6.28318530717958647692f;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < reps; r += gridDim.x * blockDim.x) {
+    int k[4];
+    int t = r;
+#pragma unroll
+    for (int a = 3; a >= 0; --a) {
+      k[a] = t % H[a];
+      t /= H[a];
+    }
+    float kap2[4], kt[4];
+    int kp[4], km[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      kp[a] = k[a];
+      km[a] = (N[a] - k[a]) % N[a];
+      const int w = k[a] < N[a] / 2 ? k[a] : k[a] - N[a];     // fftshift(-N/2 : N/2-1)
+      const float kap = two_pi * (float)w / (float)N[a];
+      kap2[a] = kap * kap;
+      kt[a] = (2 * k[a] == N[a]) ? 0.0f : kap;                // first derivative: Nyquist omitted
+    }
+    // eight sign patterns sigma (sigma_3 = +1); pattern s and s ^ 15 share Psi
+    float den[8], ex[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      den[s] = 1.0f;
+      ex[s] = 0.0f;
+    }
+    const float c01 = kt[0] * kt[1], c02 = kt[0] * kt[2], c12 = kt[1] * kt[2];
+    const float c03 = kt[0] * kt[3], c13 = kt[1] * kt[3], c23 = kt[2] * kt[3];
+    for (int q = 0; q < l; ++q) {
+      const float E = spa[q][0] * kap2[0] + spa[q][1] * kap2[1] + spa[q][2] * kap2[2] + spa[q][3] * kap2[3];
+      const float x01 = spb[q][0] * c01, x02 = spb[q][1] * c02, x12 = spb[q][2] * c12;
+      const float x03 = spb[q][3] * c03, x13 = spb[q][4] * c13, x23 = spb[q][5] * c23;
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const float s0 = (s & 1) ? -1.0f : 1.0f, s1 = (s & 2) ? -1.0f : 1.0f, s2 = (s & 4) ? -1.0f : 1.0f;
+        const float e = E + s0 * s1 * x01 + s0 * s2 * x02 + s1 * s2 * x12 + s0 * x03 + s1 * x13 + s2 * x23;
+        den[s] *= 1.0f + e;
+        ex[s] += e;
+      }
+    }
+    float Psi[16], S[16];
+    int idx[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+      const int h = s < 8 ? s : s ^ 15;
+      Psi[s] = exact ? expf(-ex[h]) : 1.0f / den[h];
+      int off = 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) off = off * N[a] + (((s >> a) & 1) ? km[a] : kp[a]);
+      idx[s] = off;
+      S[s] = X[off];
+    }
+    float T[16], Pe[16];
+#pragma unroll
+    for (int B = 0; B < 16; ++B) {
+      float tb = 0.0f, pe = 0.0f;
+#pragma unroll
+      for (int s = 0; s < 16; ++s) {
+        const bool odd = popc((unsigned)(B & s)) & 1;
+        tb += odd ? -S[s] : S[s];
+        pe += odd ? -Psi[s] : Psi[s];
+      }
+      T[B] = tb * (1.0f / 16.0f);
+      Pe[B] = pe * (1.0f / 16.0f);
+    }
+    float Tp[16];
+#pragma unroll
+    for (int C = 0; C < 16; ++C) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int E = 0; E < 16; ++E) {
+        const int pe = popc((unsigned)E);
+        if (pe & 1) continue;
+        const int sgn = ((pe / 2) + popc((unsigned)(E & C))) & 1;
+        acc += sgn ? -Pe[E] * T[E ^ C] : Pe[E] * T[E ^ C];
+      }
+      Tp[C] = acc * g;
+    }
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+      float v = 0.0f;
+#pragma unroll
+      for (int C = 0; C < 16; ++C) v += (popc((unsigned)(C & s)) & 1) ? -Tp[C] : Tp[C];
+      X[idx[s]] = v;
+    }
+  }
+}
+
+// Moment sums of the weights after the time update (buffer of the stage).
+__global__ void k_f4_moments(Dims d, const DevState* st, int stage, const float* b0, const float* b1,
+                             double* partials) {
+  const int par = (st->f.cur + stage) & 1;
+  const float* X = par ? b1 : b0;
+  Mom4 m;
+  m.zero();
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
+       p += (long long)gridDim.x * blockDim.x) {
+    float u[4];
+    frame_u4(d, p, u);
+    m.add(X[p], u);
+  }
+  mom4_block(m, partials + blockIdx.x * kMomentSlots);
+}
+
+inline int grid_cap(long long work, int threads, int cap) {
+  long long b = (work + threads - 1) / threads;
+  return (int)(b < 1 ? 1 : b > cap ? cap : b);
+}
+
+}  // namespace
+
+int f4_supported(const pmf_config* cfg, std::string* why) {
+  if (cfg->nx != 4) {
+    *why = "the float32 4-D kernels handle n_x = 4";
+    return PMF_ERR_UNSUPPORTED;
+  }
+  long long P = 1;
+  for (int a = 0; a < 4; ++a) {
+    if (cfg->N[a] > kMaxN4) {
+      *why = "the float32 4-D kernels need N <= 64 per axis";
+      return PMF_ERR_UNSUPPORTED;
+    }
+    P *= cfg->N[a];
+  }
+  if (P / ((long long)cfg->N[0] * cfg->N[1]) > (1 << 20)) {
+    *why = "grid too large for the 4-D kernels";
+    return PMF_ERR_UNSUPPORTED;
+  }
+  return PMF_OK;
+}
+
+int f4_alloc(const pmf_config* cfg, F4Tables* t) {
+  *t = F4Tables{};
+  long long P = 1;
+  for (int a = 0; a < 4; ++a) P *= cfg->N[a];
+  bool ok = cudaMalloc(&t->lo, sizeof(double) * P) == cudaSuccess &&
+            cudaMalloc(&t->gap, sizeof(float) * P) == cudaSuccess;
+  for (int a = 0; ok && a < 4; ++a) {
+    const int N = cfg->N[a], Kp = kpad(N);
+    ok = cudaMalloc(&t->interp[a], sizeof(double) * N * N) == cudaSuccess &&
+         cudaMalloc(&t->hfwd[a], sizeof(double) * N * N) == cudaSuccess &&
+         cudaMalloc(&t->wfwd[a], sizeof(float) * N * Kp) == cudaSuccess &&
+         cudaMalloc(&t->winv[a], sizeof(float) * N * Kp) == cudaSuccess;
+    if (!ok) break;
+    std::vector<double> H((size_t)N * N);
+    hartley_host(N, 1.0 / N, H.data());
+    ok = cudaMemcpy(t->hfwd[a], H.data(), sizeof(double) * N * N, cudaMemcpyHostToDevice) == cudaSuccess;
+    // inverse transform (the Hartley matrix is symmetric): W^T = H, k padded
+    hartley_host(N, 1.0, H.data());
+    std::vector<float> WT((size_t)N * Kp, 0.0f);
+    for (int j = 0; j < N; ++j)
+      for (int k = 0; k < N; ++k) WT[(size_t)j * Kp + k] = (float)H[(size_t)k * N + j];
+    ok = ok && cudaMemcpy(t->winv[a], WT.data(), sizeof(float) * N * Kp, cudaMemcpyHostToDevice) == cudaSuccess;
+  }
+  if (ok) {
+    const int smem = (int)axis_smem(kMaxN4);
+    ok = cudaFuncSetAttribute(k_f4_axis, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
+  }
+  if (!ok) {
+    f4_free(t);
+    return PMF_ERR_OOM;
+  }
+  return PMF_OK;
+}
+
+void f4_free(F4Tables* t) {
+  cudaFree(t->lo);
+  cudaFree(t->gap);
+  for (int a = 0; a < 4; ++a) {
+    cudaFree(t->interp[a]);
+    cudaFree(t->hfwd[a]);
+    cudaFree(t->wfwd[a]);
+    cudaFree(t->winv[a]);
+  }
+  *t = F4Tables{};
+}
+
+int f4_meas(const Dims& d, const MeasParams& mp, DevState* st, const F4Tables& t, float* b0, float* b1,
+            double* partials, cudaStream_t s) {
+  cudaMemsetAsync(&st->emin_bits, 0xff, sizeof(unsigned long long), s);
+  k_f4_meas_e<<<d.N[0] * d.N[1], 256, 0, s>>>(d, mp, st, t.lo, t.gap);
+  const int nb = grid_cap(d.P, 256, kMomBlocks);
+  k_f4_meas_apply<<<nb, 256, 0, s>>>(d, st, t.lo, t.gap, b0, b1, partials);
+  launch_finalize(d, st, partials, nb, 1, 0, nullptr, s);
+  return 3;
+}
+
+int f4_time(const Dims& d, const TimeConsts& tc, DevState* st, const F4Tables& t, float* b0, float* b1,
+            double* partials, double* pend, cudaStream_t s) {
+  launch_frame(tc, st, pend, s);
+  launch_build_interp(d, st, t.interp, s);
+  int maxN = 0;
+  for (int a = 0; a < 4; ++a) maxN = d.N[a] > maxN ? d.N[a] : maxN;
+  k_f4_fuse<<<dim3(maxN, 4), 64, 0, s>>>(d, t);
+  k_f4_realign<<<grid_cap(d.P, 256, 4096), 256, 0, s>>>(d, st, b0, b1);
+  int stage = 1;
+  auto axis = [&](int a, const float* WT) {
+    const long long lines = d.P / d.N[a];
+    k_f4_axis<<<(unsigned)((lines + kCols - 1) / kCols), kAxisThreads, axis_smem(d.N[a]), s>>>(d, a, WT, st,
+                                                                                              stage, b0, b1);
+    ++stage;
+  };
+  for (int a = 0; a < 4; ++a) axis(a, t.wfwd[a]);
+  long long reps = 1;
+  for (int a = 0; a < 4; ++a) reps *= d.N[a] / 2 + 1;
+  k_f4_psi<<<grid_cap(reps, 128, 4096), 128, 0, s>>>(d, st, stage, b0, b1);
+  for (int a = 0; a < 4; ++a) axis(a, t.winv[a]);
+  const int nb = grid_cap(d.P, 256, kMomBlocks);
+  k_f4_moments<<<nb, 256, 0, s>>>(d, st, stage, b0, b1, partials);
+  launch_finalize(d, st, partials, nb, stage & 1, 1, pend, s);
+  return 1 + 4 + 1 + 1 + 8 + 1 + 2;
+}
+
+}  // namespace pmf

@@ -18,82 +18,10 @@
 
 #include "pmf_internal.cuh"
 #include "pmf_kernels.cuh"
+#include "pmf_grid.cuh"
 #include "pmf_device.cuh"
 
 namespace pmf {
-
-__device__ __forceinline__ void unflatten(const Dims& d, long long p, int* j) {
-  for (int m = d.nx - 1; m >= 0; --m) {
-    j[m] = (int)(p % d.N[m]);
-    p /= d.N[m];
-  }
-}
-
-__device__ __forceinline__ double wrap_pi(double r) {
-  const double two_pi = 6.283185307179586476925286766559;
-  const double pi = 3.14159265358979323846264338327950;
-  return r - two_pi * ceil((r - pi) / two_pi);
-}
-
-// e(x) = 1/2 r^T R^{-1} r with r = z - h(x) (eq. meas).
-__device__ double meas_exponent_f64(const MeasParams& mp, const double* x) {
-  double r[PMF_MAX_NZ];
-  if (mp.kind == PMF_MEAS_LINEAR) {
-    for (int i = 0; i < mp.nz; ++i) {
-      double h = 0.0;
-      for (int a = 0; a < mp.nx; ++a) h += mp.H[i * mp.nx + a] * x[a];
-      r[i] = mp.z[i] - h;
-    }
-  } else if (mp.kind == PMF_MEAS_RANGE) {
-    r[0] = mp.z[0] - sqrt(x[0] * x[0] + x[1] * x[1]);
-  } else if (mp.kind == PMF_MEAS_TERRAIN_GM) {
-    // terrain altitude at (p_x, p_y) = (x_0, x_2); -log of the two-component
-    // Gaussian mixture of the residual (constants from the host: gm = {1/(2 v1),
-    // 1/(2 v2), log terms c1, c2, means mu1, mu2}), in log-sum-exp form
-    double h = mp.p[16];
-    for (int i = 0; i < 4; ++i) h += mp.p[4 * i] * sin(mp.p[4 * i + 1] * x[0] + mp.p[4 * i + 2] * x[2] + mp.p[4 * i + 3]);
-    const double rr = mp.z[0] - h;
-    const double m1 = (rr - mp.gm[4]) * (rr - mp.gm[4]) * mp.gm[0] + mp.gm[2];
-    const double m2 = (rr - mp.gm[5]) * (rr - mp.gm[5]) * mp.gm[1] + mp.gm[3];
-    const double lo = fmin(m1, m2);
-    return lo - log1p(exp(-fabs(m1 - m2)));
-  } else {
-    r[0] = wrap_pi(mp.z[0] - atan2(x[1], x[0]));
-    r[1] = mp.z[1] - x[2];
-  }
-  double e = 0.0;
-  for (int i = 0; i < mp.nz; ++i)
-    for (int k = 0; k < mp.nz; ++k) e += r[i] * mp.Rinv[i * mp.nz + k] * r[k];
-  return 0.5 * e;
-}
-
-template <int NV>
-__device__ __forceinline__ void block_sum(double* v, double* smem /* [32*NV] */, double* out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NV; ++i)
-    for (int o = 16; o; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
-  if (lane == 0)
-#pragma unroll
-    for (int i = 0; i < NV; ++i) smem[warp * NV + i] = v[i];
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      double t = lane < nw ? smem[lane * NV + i] : 0.0;
-      for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) out[i] = t;
-    }
-  }
-}
-
-// Moment accumulators in frame coordinates u: S0, S1[n], S2 (layout of tot_S2).
-__device__ __forceinline__ void acc_moments(double* acc, double p, const double* u, int nx) {
-  acc[0] += p;
-  for (int a = 0; a < nx; ++a) acc[1 + a] += p * u[a];
-  for (int a = 0; a < nx; ++a)
-    for (int b = a; b < nx; ++b) acc[tot_S2(nx, a, b)] += p * u[a] * u[b];
-}
 
 __global__ void k_meas_emin_f64(Dims d, MeasParams mp, DevState* st) {
   double emin = INFINITY;
@@ -144,33 +72,48 @@ __global__ void k_meas_apply_f64(Dims d, MeasParams mp, DevState* st, double* b0
 // Sum block partials, finalise moments and the normaliser.  use_pending: the
 // weights are on the frame written by k_frame (time update) and that frame is
 // committed here.  flip: buffer parity change of the update.
+// The moments are formed by warp 0 in parallel lanes (finalize_warp: one
+// matrix entry per lane) on a shared copy of the frame state.
 __global__ void k_finalize(Dims d, DevState* st, const double* partials, int nblocks, int flip,
                            int use_pending, const double* pend /* c, M, Minv, V */) {
   __shared__ double sm[32 * kMomentSlots];
   __shared__ double tot[kMomentSlots];
+  __shared__ FrameState fs;
+  constexpr int kWords = sizeof(FrameState) / 8;
   double acc[kMomentSlots] = {};
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
     for (int i = 0; i < kMomentSlots; ++i) acc[i] += partials[b * kMomentSlots + i];
   block_sum<kMomentSlots>(acc, sm, tot);
+  for (int i = threadIdx.x; i < kWords; i += blockDim.x)
+    ((unsigned long long*)&fs)[i] = ((const unsigned long long*)&st->f)[i];
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  FrameState fs = st->f;   // local copy: the scalar work stays out of global memory
-  if (finalize_core(d.nx, &fs, tot, use_pending, pend)) fs.cur ^= flip;
-  st->f = fs;
+  if (threadIdx.x >= 32) return;
+  bool ok;
+  if (d.nx == 1) ok = finalize_warp<1>(&fs, tot, use_pending, pend);
+  else if (d.nx == 2) ok = finalize_warp<2>(&fs, tot, use_pending, pend);
+  else if (d.nx == 3) ok = finalize_warp<3>(&fs, tot, use_pending, pend);
+  else ok = finalize_warp<4>(&fs, tot, use_pending, pend);
+  if (ok && threadIdx.x == 0) fs.cur ^= flip;
+  __syncwarp();
+  for (int i = threadIdx.x; i < kWords; i += 32)
+    ((unsigned long long*)&st->f)[i] = ((const unsigned long long*)&fs)[i];
 }
 
-// Regrid decision (thread 0) and the diffusion coefficients of every sub-step
-// (one thread each) of one time update.
+// Regrid decision (warp 0, lane-parallel, on a shared copy of the frame
+// state) and the diffusion coefficients of every sub-step (one thread each)
+// of one time update.
 template <int n>
 __device__ void frame_body(const TimeConsts& tc, DevState* st, double* pend) {
   __shared__ FrameState fs;
   __shared__ double Mpi[16];
-  if (threadIdx.x == 0) {
-    fs = st->f;
-    frame_scalar<n>(tc, &fs, pend, Mpi);
-    st->f = fs;
-  }
+  constexpr int kWords = sizeof(FrameState) / 8;
+  for (int i = threadIdx.x; i < kWords; i += blockDim.x)
+    ((unsigned long long*)&fs)[i] = ((const unsigned long long*)&st->f)[i];
   __syncthreads();
+  if (threadIdx.x < 32) frame_warp<n>(tc, &fs, pend, Mpi);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kWords; i += blockDim.x)
+    ((unsigned long long*)&st->f)[i] = ((const unsigned long long*)&fs)[i];
   const int l = tc.exact ? 1 : tc.l;
   for (int q = threadIdx.x; q < l; q += blockDim.x) frame_substep<n>(tc, Mpi, q, st->pa[q], st->pb[q]);
 }
@@ -603,6 +546,21 @@ void launch_time_f64(const Dims& d, const TimeConsts& tc, DevState* st, double* 
   k_psi_f64<<<grid_for(reps, 128, 4096), 128, 0, s>>>(d, st, stage, b0, b1);
   for (int a = 0; a < n; ++a) gemm(a, hinv[a]);
   launch_moments_f64(d, st, stage, b0, b1, partials, stage & 1, 1, pend, s);
+}
+
+void launch_frame(const TimeConsts& tc, DevState* st, double* pend, cudaStream_t s) {
+  k_frame<<<1, MAXL, 0, s>>>(tc, st, pend);
+}
+
+void launch_build_interp(const Dims& d, const DevState* st, double* const* interp, cudaStream_t s) {
+  for (int a = 0; a < d.nx; ++a)
+    k_build_interp_f64<<<grid_for((long long)d.N[a] * d.N[a], 256, 1 << 20), 256, 0, s>>>(
+        d, st, a, interp[a]);
+}
+
+void launch_finalize(const Dims& d, DevState* st, const double* partials, int nblocks, int flip,
+                     int use_pending, const double* pend, cudaStream_t s) {
+  k_finalize<<<1, 256, 0, s>>>(d, st, partials, nblocks, flip, use_pending, pend);
 }
 
 void launch_export_f64(const Dims& d, const DevState* st, const double* b0, const double* b1,

@@ -69,7 +69,7 @@ struct MeasParams {
   double Rinv[9];
   double H[PMF_MAX_NZ * PMF_MAX_NX];
   double p[PMF_MEAS_NPARAM];
-  double gm[6];   // TERRAIN_GM: 1/(2 v1), 1/(2 v2), log(v1)/2 - log w1, log(v2)/2 - log w2, mu1, mu2
+  double gm[6];   // TERRAIN_GM: 1/(2 v1), 1/(2 v2), log(v_g)/2 - log w_g (g = 1, 2; common shift, min log 2), mu1, mu2
 };
 
 // Frame, moments and per-update scalars of one filter (float64).  Frame

@@ -199,8 +199,17 @@ int meas_params(int n, const pmf_meas* m, MeasParams* mp, std::string* why) {
     const double w1 = m->p[17], v1 = m->p[20], v2 = m->p[21];
     mp->gm[0] = 0.5 / v1;
     mp->gm[1] = 0.5 / v2;
-    mp->gm[2] = 0.5 * std::log(v1) - std::log(w1);
-    mp->gm[3] = 0.5 * std::log(v2) - std::log(1.0 - w1);
+    // component constants 1/2 log v_g - log w_g, shifted by a common amount
+    // (a constant factor of the likelihood, removed by the normalisation) so
+    // that the smaller is log 2: every exponent is then >= 0, which the
+    // bitwise minimum over the grid relies on
+    double c1 = 0.5 * std::log(v1) - std::log(w1);
+    double c2 = 0.5 * std::log(v2) - std::log(1.0 - w1);
+    const double lo = std::fmin(c1, c2) - 0.69314718055994530942;
+    c1 -= lo;
+    c2 -= lo;
+    mp->gm[2] = c1;
+    mp->gm[3] = c2;
     mp->gm[4] = m->p[18];
     mp->gm[5] = m->p[19];
     return PMF_OK;

@@ -23,8 +23,27 @@ def compare(gpu, orc):
     return out
 
 
-def run_pair(sc, precision="fp64", epochs=None, psi_mode="euler", fused_step=False):
-    """Yield (stage, errors) after every update of both filters."""
+def frame_choice_error(orc, tau, choice):
+    """Distance of a regrid decision from the oracle's own one: the branch
+    (0 if equal, inf if not) or the relative difference of the new axes/scales."""
+    own = orc.choose_frame(tau)
+    if own["realigned"] != choice["realigned"]:
+        return float("inf")
+    if own["realigned"]:
+        return float(np.abs(own["M"] - choice["M"]).max() / np.abs(own["M"]).max())
+    return float(np.abs(own["D"] - choice["D"]).max() / np.abs(own["D"]).max())
+
+
+def run_pair(sc, precision="fp64", epochs=None, psi_mode="euler", fused_step=False, follow_frame=False):
+    """Yield (stage, errors) after every update of both filters.
+
+    follow_frame: the oracle takes each regrid decision (centre shift, scales
+    or re-aligned axes, all on their quantisation lattices) from the CUDA path
+    instead of from its own moments, and the distance between the two
+    decisions is reported as "choice".  The decision is a discrete function of
+    the moments; on a float32 path whose moments differ from the oracle's in
+    the sixth digit it can land on a neighbouring lattice point, and both
+    frames are then valid grids for the method."""
     from paper_2412_07240_gb300 import Filter
     gpu = Filter(sc.cfg, precision=precision, psi_mode=psi_mode)
     orc = OracleFilter(sc.cfg, psi_mode=psi_mode)
@@ -40,8 +59,13 @@ def run_pair(sc, precision="fp64", epochs=None, psi_mode="euler", fused_step=Fal
         orc.meas_update(sc.meas, sc.z[k])
         yield f"meas{k}", compare(gpu, orc)
         gpu.time_update(sc.dt)
-        info = orc.time_update(sc.dt)
-        yield f"time{k}" + ("R" if info["realigned"] else ""), compare(gpu, orc)
+        choice, extra = None, {}
+        if follow_frame:
+            _, c, M = gpu.pdf()
+            choice = orc.frame_from_target(sc.dt, c, M)
+            extra["choice"] = frame_choice_error(orc, sc.dt, choice)
+        info = orc.time_update(sc.dt, choice)
+        yield f"time{k}" + ("R" if info["realigned"] else ""), {**compare(gpu, orc), **extra}
     gpu.close()
 
 
