@@ -7,10 +7,9 @@
 // Per time update (Sec. V-B algorithm on the moving grid, eq. gridMov):
 //   frame        regrid decision and sub-step coefficients (float64, shared
 //                with the float64 path)
-//   interp x 4   trigonometric regrid matrix of each axis (eq. interFreq,
-//                float64, shared with the float64 path)
-//   fuse         W_a = H_a I_a per axis (regrid folded into the forward
-//                Hartley transform), rounded to float32
+//   tables       W_a = H_a I_a per axis: the trigonometric regrid (eq.
+//                interFreq) folded into the forward Hartley transform, float64,
+//                rounded to float32
 //   realign      multilinear re-alignment (or scaled copy) of the weights
 //   fwd x 4      W_a along axis a
 //   psi          diffusion multiplier and trace factor over 16-point sign-flip
@@ -35,27 +34,68 @@ constexpr int kMaxN4 = 64;
 constexpr int kCols = 64;               // lines per block of the axis transform
 constexpr int kAxisThreads = 256;       // four threads per line (output groups q, q + 4)
 constexpr int kColStr = kCols + 1;      // shared stride of a tile row (conflict-free column reads)
-constexpr int kMomBlocks = 304;         // moment partial blocks (2 per SM)
 
 __host__ __device__ inline int kpad(int N) { return (N + 7) & ~7; }
 
 size_t axis_smem(int N) { return sizeof(float) * (2 * (size_t)N * kColStr + (size_t)N * kpad(N)); }
 
+// ---- double-float helpers ---------------------------------------------------
+__device__ __forceinline__ DF df_of(double x) {
+  const float h = (float)x;
+  return DF{h, (float)(x - (double)h)};
+}
+// a b, with the product of the high parts exact (fma) and the cross terms rounded
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  const float h = p + e;
+  return DF{h, e - (h - p)};
+}
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+
 // ---- measurement update, pass 1 -------------------------------------------
 // Terrain altitude (Sec. VI): base + sum_i amp_i sin(phi_i), phi_i = kx_i x_0 +
 // ky_i x_2 + ph_i with x = c + M u, so phi_i = theta_i + sum_a g_ia u_a with
-// theta_i = kx_i c_0 + ky_i c_2 + ph_i and g_ia = kx_i M_0a + ky_i M_2a.  One
-// block per (j0, j1) slab: e^{i(theta + g_0 u_0 + g_1 u_1)} once per block,
-// times e^{i g_2 u_2} and the amplitude as a shared table over j2, e^{i g_3 u_3}
-// as a table over j3, and the sine of every point by angle addition in float64
-// (two fused multiply-adds per wave).  The mixture exponent is kept as its
-// smaller component m_lo and the gap |m_1 - m_2| (e = m_lo - log(1 + e^-gap));
-// other measurement kinds store e itself with an infinite gap.
-__global__ void k_f4_meas_e(Dims d, MeasParams mp, DevState* st, double* lo_out, float* gap_out) {
-  __shared__ double2 t2[4][kMaxN4], t3[4][kMaxN4];
-  __shared__ double2 base[4];
-  __shared__ double gg[4][4];
-  __shared__ double wmin[32];
+// theta_i = kx_i c_0 + ky_i c_2 + ph_i and g_ia = kx_i M_0a + ky_i M_2a, and
+// e^{i phi_i} is a product of per-axis factors.  k_f4_meas_tab forms the
+// factors (float64); k_f4_meas_e takes one block per (j0, j1) slab, multiplies
+// the factors of axes 0-2 into a table over j2 (float64, then double-float),
+// holds the axis-3 factors as double-float, and forms a point's altitude
+// residual r = (z - base) - sum_i Im(t2_i t3_i) in double-float (~2^-44
+// relative); the mixture exponents follow from r - mu_g in float32.  The
+// exponent is kept as its smaller component m_lo and the gap |m_1 - m_2|
+// (e = m_lo - log(1 + e^-gap)); other measurement kinds store e itself
+// (float64, rounded) with an infinite gap.
+//
+// Phase tables (one block per wave i): tab[i][a][j] = e^{i g_ia u_j}, with
+// amp_i e^{i theta_i} folded into axis 0.
+__global__ void k_f4_meas_tab(Dims d, MeasParams mp, const DevState* st, double2* tab) {
+  const int i = blockIdx.x;
+  const double* c = st->f.c;
+  const double* M = st->f.M;
+  const double kx = mp.p[4 * i + 1], ky = mp.p[4 * i + 2];
+  const double theta = kx * c[0] + ky * c[2] + mp.p[4 * i + 3];
+  for (int t = threadIdx.x; t < 4 * kMaxN4; t += blockDim.x) {
+    const int a = t / kMaxN4, j = t % kMaxN4;
+    if (j >= d.N[a]) continue;
+    const double g = kx * M[a] + ky * M[8 + a];
+    const double ph = g * (j - 0.5 * (d.N[a] - 1)) + (a == 0 ? theta : 0.0);
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    const double amp = a == 0 ? mp.p[4 * i] : 1.0;
+    tab[(i * 4 + a) * kMaxN4 + j] = make_double2(amp * cs, amp * sn);
+  }
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__global__ void k_f4_meas_e(Dims d, MeasParams mp, DevState* st, const double2* tab, float* lo_out,
+                            float* gap_out) {
+  __shared__ float4 t2[4][kMaxN4], t3[4][kMaxN4];   // (re.hi, re.lo, im.hi, im.lo)
+  __shared__ float wmin[32];
   const int N2 = d.N[2], N3 = d.N[3];
   const int j0 = blockIdx.x / d.N[1], j1 = blockIdx.x % d.N[1];
   const double u0 = j0 - 0.5 * (d.N[0] - 1), u1 = j1 - 0.5 * (d.N[1] - 1);
@@ -63,52 +103,40 @@ __global__ void k_f4_meas_e(Dims d, MeasParams mp, DevState* st, double* lo_out,
   const double* M = st->f.M;
   const bool terrain = mp.kind == PMF_MEAS_TERRAIN_GM;
   if (terrain) {
-    if (threadIdx.x < 4) {
-      const int i = threadIdx.x;
-      const double kx = mp.p[4 * i + 1], ky = mp.p[4 * i + 2];
-      for (int a = 0; a < 4; ++a) gg[i][a] = kx * M[a] + ky * M[8 + a];
-      const double ph = kx * c[0] + ky * c[2] + mp.p[4 * i + 3] + gg[i][0] * u0 + gg[i][1] * u1;
-      double sn, cs;
-      sincos(ph, &sn, &cs);
-      base[i] = make_double2(cs, sn);
-    }
-    __syncthreads();
-    // t2 holds amp_i e^{i(theta + g_0 u_0 + g_1 u_1 + g_2 u_2)}, t3 e^{i g_3 u_3}
+    // t2: amp_i e^{i(theta + g_0 u_0 + g_1 u_1 + g_2 u_2)} over j2, t3: e^{i g_3 u_3}
     for (int t = threadIdx.x; t < 4 * (N2 + N3); t += blockDim.x) {
       const int i = t / (N2 + N3), r = t % (N2 + N3);
-      const bool ax2 = r < N2;
-      const int j = ax2 ? r : r - N2;
-      const double u = j - 0.5 * ((ax2 ? N2 : N3) - 1);
-      double sn, cs;
-      sincos(gg[i][ax2 ? 2 : 3] * u, &sn, &cs);
-      if (ax2) {
-        const double2 q = base[i];
-        const double amp = mp.p[4 * i];
-        t2[i][j] = make_double2(amp * (q.x * cs - q.y * sn), amp * (q.x * sn + q.y * cs));
-      } else {
-        t3[i][j] = make_double2(cs, sn);
-      }
+      const double2* ti = tab + i * 4 * kMaxN4;
+      double2 v;
+      if (r < N2) v = cmul(cmul(ti[j0], ti[kMaxN4 + j1]), ti[2 * kMaxN4 + r]);
+      else v = ti[3 * kMaxN4 + r - N2];
+      const DF re = df_of(v.x), im = df_of(v.y);
+      (r < N2 ? t2[i][r] : t3[i][r - N2]) = make_float4(re.hi, re.lo, im.hi, im.lo);
     }
     __syncthreads();
   }
-  const long long p0 = (long long)blockIdx.x * N2 * N3;
-  double emin = INFINITY;
+  const DF zb = df_of(mp.z[0] - mp.p[16]);
+  const DF mu1 = df_of(mp.gm[4]), mu2 = df_of(mp.gm[5]);
+  const float g0 = (float)mp.gm[0], g1 = (float)mp.gm[1], g2 = (float)mp.gm[2], g3 = (float)mp.gm[3];
+  const int p0 = blockIdx.x * N2 * N3;
+  float emin = INFINITY;
   for (int t = threadIdx.x; t < N2 * N3; t += blockDim.x) {
     const int j2 = t / N3, j3 = t % N3;
-    double lo;
-    float gap;
+    float lo, gap;
     if (terrain) {
-      double h = mp.p[16];
+      DF h{0.0f, 0.0f};
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const double2 a = t2[i][j2], b = t3[i][j3];
-        h = fma(a.x, b.y, fma(a.y, b.x, h));    // amp_i sin(phi_i) = Im(a b)
+        const float4 a = t2[i][j2], b = t3[i][j3];
+        // amp_i sin(phi_i) = Im(a b) = a.re b.im + a.im b.re
+        h = df_add(h, df_add(df_mul(DF{a.x, a.y}, DF{b.z, b.w}), df_mul(DF{a.z, a.w}, DF{b.x, b.y})));
       }
-      const double rr = mp.z[0] - h;
-      const double m1 = (rr - mp.gm[4]) * (rr - mp.gm[4]) * mp.gm[0] + mp.gm[2];
-      const double m2 = (rr - mp.gm[5]) * (rr - mp.gm[5]) * mp.gm[1] + mp.gm[3];
-      lo = fmin(m1, m2);
-      gap = (float)fabs(m1 - m2);
+      const DF rr = df_add(zb, df_neg(h));
+      const DF e1 = df_add(rr, df_neg(mu1)), e2 = df_add(rr, df_neg(mu2));
+      const float d1 = e1.hi + e1.lo, d2 = e2.hi + e2.lo;
+      const float m1 = fmaf(d1 * d1, g0, g2), m2 = fmaf(d2 * d2, g1, g3);
+      lo = fminf(m1, m2);
+      gap = fabsf(m1 - m2);
     } else {
       const double u[4] = {u0, u1, j2 - 0.5 * (N2 - 1), j3 - 0.5 * (N3 - 1)};
       double x[4];
@@ -116,41 +144,47 @@ __global__ void k_f4_meas_e(Dims d, MeasParams mp, DevState* st, double* lo_out,
         x[a] = c[a];
         for (int b = 0; b < 4; ++b) x[a] += M[a * 4 + b] * u[b];
       }
-      lo = meas_exponent_f64(mp, x);
+      lo = (float)meas_exponent_f64(mp, x);
       gap = INFINITY;
     }
     lo_out[p0 + t] = lo;
     gap_out[p0 + t] = gap;
-    emin = fmin(emin, lo);
+    emin = fminf(emin, lo);
   }
-  for (int o = 16; o; o >>= 1) emin = fmin(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+  for (int o = 16; o; o >>= 1) emin = fminf(emin, __shfl_xor_sync(0xffffffffu, emin, o));
   if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = emin;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) emin = fmin(emin, wmin[w]);
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) emin = fminf(emin, wmin[w]);
     // every exponent is >= 0 (Gaussian forms; mixture constants shifted on the
     // host), so the bit patterns order like the values
-    atomicMin(&st->emin_bits, (unsigned long long)__double_as_longlong(emin));
+    atomicMin(&st->emin_bits, (unsigned long long)__double_as_longlong((double)emin));
   }
 }
 
 // Double-float moment sums of one thread in the tot_S2 layout for n_x = 4:
-// {S0, S1[4], S2[10]}.
+// {S0, S1[4], S2[10]}, accumulated line by line.
 struct Mom4 {
   DF s[kMomentSlots];
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int i = 0; i < kMomentSlots; ++i) s[i] = DF{0.0f, 0.0f};
   }
-  __device__ __forceinline__ void add(float v, const float* u) {
-    s[0] = df_add1(s[0], v);
+  // One line along axis 3 at (u0, u1, u2): its float32 sums s0 = sum v,
+  // s1 = sum v u3, s2 = sum v u3^2 spread over the 15 slots.
+  __device__ __forceinline__ void add_line(float s0, float s1, float s2, float u0, float u1, float u2) {
+    const float u[3] = {u0, u1, u2};
+    s[0] = df_add1(s[0], s0);
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const float vu = v * u[a];
-      s[1 + a] = df_add1(s[1 + a], vu);
+    for (int a = 0; a < 3; ++a) {
+      const float su = s0 * u[a];
+      s[1 + a] = df_add1(s[1 + a], su);
 #pragma unroll
-      for (int b = a; b < 4; ++b) s[tot_S2(4, a, b)] = df_add1(s[tot_S2(4, a, b)], vu * u[b]);
+      for (int b = a; b < 3; ++b) s[tot_S2(4, a, b)] = df_add1(s[tot_S2(4, a, b)], su * u[b]);
+      s[tot_S2(4, a, 3)] = df_add1(s[tot_S2(4, a, 3)], s1 * u[a]);
     }
+    s[4] = df_add1(s[4], s1);
+    s[tot_S2(4, 3, 3)] = df_add1(s[tot_S2(4, 3, 3)], s2);
   }
 };
 
@@ -175,58 +209,86 @@ __device__ void mom4_block(Mom4& m, double* out) {
   }
 }
 
-// Node indices of flat point p (C order, four axes; constant indexing keeps
-// them in registers).
-__device__ __forceinline__ void unflatten4(const Dims& d, long long p, int* j) {
-#pragma unroll
-  for (int m = 3; m >= 0; --m) {
-    j[m] = (int)(p % d.N[m]);
-    p /= d.N[m];
-  }
-}
+// Moment kernels: a block takes kLinesM lines along axis 3, four threads per
+// line (points j3 = q, q + 4, ...); a thread sums its points in float32 and adds
+// the 15 slot contributions of its part of the line in double-float.
+constexpr int kLinesM = 64;
+constexpr int kMomThreads = 4 * kLinesM;
 
-__device__ __forceinline__ void frame_u4(const Dims& d, long long p, float* u) {
-  int j[4];
-  unflatten4(d, p, j);
-#pragma unroll
-  for (int a = 0; a < 4; ++a) u[a] = j[a] - 0.5f * (d.N[a] - 1);
+__device__ __forceinline__ void line_u(const Dims& d, int ln, float* u) {
+  const int j2 = ln % d.N[2], r = ln / d.N[2];
+  u[0] = (r / d.N[1]) - 0.5f * (d.N[0] - 1);
+  u[1] = (r % d.N[1]) - 0.5f * (d.N[1] - 1);
+  u[2] = j2 - 0.5f * (d.N[2] - 1);
 }
 
 // ---- measurement update, pass 2: likelihood multiply and moment sums ----
-__global__ void k_f4_meas_apply(Dims d, DevState* st, const double* lo, const float* gap, float* b0,
-                                float* b1, double* partials) {
+__global__ void __launch_bounds__(kMomThreads) k_f4_meas_apply(Dims d, DevState* st, const float* lo,
+                                                               const float* gap, float* b0, float* b1,
+                                                               double* partials) {
   const int cur = st->f.cur;
   const float* in = cur ? b1 : b0;
   float* out = cur ? b0 : b1;
   const double emin = __longlong_as_double((long long)st->emin_bits);
   const float ps = (float)st->f.pscale;
+  const int N3 = d.N[3], lines = (int)d.P / N3;
+  const float h3 = 0.5f * (N3 - 1);
+  const int ln = blockIdx.x * kLinesM + threadIdx.x / 4, q = threadIdx.x % 4;
   Mom4 m;
   m.zero();
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
-       p += (long long)gridDim.x * blockDim.x) {
-    const float f = expf((float)(emin - lo[p])) * (1.0f + expf(-gap[p]));
-    const float v = (in[p] * ps) * f;
-    out[p] = v;
-    float u[4];
-    frame_u4(d, p, u);
-    m.add(v, u);
+  if (ln < lines) {
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+    for (int j = q; j < N3; j += 4) {
+      const int p = ln * N3 + j;
+      const float f = expf((float)(emin - (double)lo[p])) * (1.0f + expf(-gap[p]));
+      const float v = (in[p] * ps) * f;
+      out[p] = v;
+      const float u3 = j - h3, vu = v * u3;
+      s0 += v;
+      s1 += vu;
+      s2 = fmaf(vu, u3, s2);
+    }
+    float u[3];
+    line_u(d, ln, u);
+    m.add_line(s0, s1, s2, u[0], u[1], u[2]);
   }
   mom4_block(m, partials + blockIdx.x * kMomentSlots);
 }
 
 // ---- time update ------------------------------------------------------------
 // W_a^T (row j, column k, k padded to a multiple of 8 with zeros) of the fused
-// regrid + forward transform W_a = H_a I_a, formed in float64: one block per
-// (axis, j), one thread per k.
-__global__ void k_f4_fuse(Dims d, const F4Tables t) {
+// regrid + forward transform W_a = H_a I_a, formed in float64.  I_a is the
+// periodic-sinc regrid matrix of eq. interFreq (identity when the frame was
+// re-aligned): I[q, j] = sin(pi v) cos(pi v / N) / (N sin(pi v / N)), v = y_q -
+// u_j, y_q = rs_a + rd_a u_q, zero rows where |y_q| > N / 2.  One block per
+// (j, axis): the column I[., j] in shared memory, then one thread per k.
+__global__ void k_f4_tables(Dims d, const DevState* st, const F4Tables t) {
+  __shared__ double col[kMaxN4];
   const int a = blockIdx.y, N = d.N[a], j = blockIdx.x;
   if (j >= N) return;
+  const double half = 0.5 * (N - 1);
+  for (int q = threadIdx.x; q < N; q += blockDim.x) {
+    double v;
+    if (st->f.realign) {
+      v = q == j ? 1.0 : 0.0;
+    } else {
+      const double y = st->f.rs[a] + st->f.rd[a] * (q - half);
+      if (fabs(y) > 0.5 * N) {
+        v = 0.0;
+      } else {
+        const double x = y - (j - half);
+        v = x == 0.0 ? 1.0 : sinpi(x) * cospi(x / N) / (N * sinpi(x / N));
+      }
+    }
+    col[q] = v;
+  }
+  __syncthreads();
   const int Kp = kpad(N);
   for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
-    double s = 0.0;
+    double sum = 0.0;
     if (k < N)
-      for (int q = 0; q < N; ++q) s += t.hfwd[a][(size_t)k * N + q] * t.interp[a][(size_t)q * N + j];
-    t.wfwd[a][(size_t)j * Kp + k] = (float)s;
+      for (int q = 0; q < N; ++q) sum = fma(t.hfwd[a][k * N + q], col[q], sum);
+    t.wfwd[a][j * Kp + k] = (float)sum;
   }
 }
 
@@ -234,13 +296,14 @@ __global__ void k_f4_fuse(Dims d, const F4Tables t) {
 // + b, 16 corners; nodes outside the old box contribute 0), or the scaled copy
 // when the frame was not re-aligned.  Reads buf[cur], writes buf[cur ^ 1].
 // A block takes kLinesR lines along axis 3: the old-index position of each
-// line's first node is formed once in float64 (split into an integer and a
-// fraction), and a node adds B_a3 j3 in float64; the corner weights and sums
-// are float32.
+// line's first node is formed once in float64 and held as double-float, a
+// node adds B_a3 j3 in double-float (exact product of the high part), and the
+// integer part and the fraction of the position come from that sum (~1e-12
+// node); the corner weights and sums are float32.
 constexpr int kLinesR = 8;
 
 __global__ void __launch_bounds__(256) k_f4_realign(Dims d, const DevState* st, float* b0, float* b1) {
-  __shared__ double zl[kLinesR][4];
+  __shared__ DF zl[kLinesR][4];
   const int cur = st->f.cur;
   const float* in = cur ? b1 : b0;
   float* out = cur ? b0 : b1;
@@ -252,6 +315,9 @@ __global__ void __launch_bounds__(256) k_f4_realign(Dims d, const DevState* st, 
   }
   const int lines = P / N3;
   const int N0 = d.N[0], N1 = d.N[1], N2 = d.N[2];
+  DF B3[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) B3[a] = df_of(st->f.B[a * 4 + 3]);
   for (int l0 = blockIdx.x * kLinesR; l0 < lines; l0 += gridDim.x * kLinesR) {
     if (threadIdx.x < kLinesR * 4) {
       const int li = threadIdx.x >> 2, a = threadIdx.x & 3, ln = l0 + li;
@@ -261,7 +327,7 @@ __global__ void __launch_bounds__(256) k_f4_realign(Dims d, const DevState* st, 
         double z = st->f.b[a] + 0.5 * (d.N[a] - 1);
 #pragma unroll
         for (int b = 0; b < 4; ++b) z = fma(st->f.B[a * 4 + b], u[b], z);
-        zl[li][a] = z;
+        zl[li][a] = df_of(z);
       }
     }
     __syncthreads();
@@ -272,10 +338,21 @@ __global__ void __launch_bounds__(256) k_f4_realign(Dims d, const DevState* st, 
       float w[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        const double z = fma(st->f.B[a * 4 + 3], (double)j3, zl[li][a]);
-        const double fl = floor(z);
-        f[a] = (int)fmax(fmin(fl, 1e6), -1e6);
-        w[a] = (float)(z - fl);
+        const DF b3 = B3[a];
+        const float jf = (float)j3;
+        const float p = b3.hi * jf;
+        const DF z = df_add(zl[li][a], DF{p, fmaf(b3.lo, jf, fmaf(b3.hi, jf, -p))});
+        float fl = floorf(z.hi);
+        float wa = (z.hi - fl) + z.lo;
+        if (wa < 0.0f) {
+          wa += 1.0f;
+          fl -= 1.0f;
+        } else if (wa >= 1.0f) {
+          wa -= 1.0f;
+          fl += 1.0f;
+        }
+        f[a] = (int)fmaxf(fminf(fl, 1e6f), -1e6f);
+        w[a] = wa;
       }
       float sum = 0.0f;
 #pragma unroll
@@ -325,25 +402,27 @@ __global__ void __launch_bounds__(kAxisThreads) k_f4_axis(Dims d, int axis, cons
   float* Y = par ? b0 : b1;
   const int tid = threadIdx.x;
   for (int i = tid; i < N * Kp; i += kAxisThreads) Ws[i] = WT[i];
+  // line c of the tile starts at element base(c) and steps by inner; one
+  // division per thread (each thread keeps its column in both copy loops)
+  const int cc = tid % kCols, jq = tid / kCols;
+  constexpr int kJStep = kAxisThreads / kCols;
+  int cbase = 0;
+  if (inner > 1 && cc < nl) {
+    const int ln = l0 + cc, o = ln / inner;
+    cbase = o * N * inner + (ln - o * inner);
+  }
   if (inner == 1) {
+    // contiguous lines: one warp per line, lanes along it
     const float* src = X + l0 * N;
-    for (int t = tid; t < nl * N; t += kAxisThreads) {
-      const int c = t / N, j = t - c * N;
-      Xs[j * kColStr + c] = src[t];
-    }
-  } else {
-    for (int t = tid; t < N * kCols; t += kAxisThreads) {
-      const int j = t / kCols, c = t - j * kCols;
-      if (c < nl) {
-        const int ln = l0 + c, o = ln / inner, i = ln - o * inner;
-        Xs[j * kColStr + c] = X[(o * N + j) * inner + i];
-      }
-    }
+    for (int c = tid >> 5; c < nl; c += kAxisThreads / 32)
+      for (int j = tid & 31; j < N; j += 32) Xs[j * kColStr + c] = src[c * N + j];
+  } else if (cc < nl) {
+    for (int j = jq; j < N; j += kJStep) Xs[j * kColStr + cc] = X[cbase + j * inner];
   }
   __syncthreads();
-  const int c = tid % kCols, q = tid / kCols;
+  const int c = cc, q = jq;
   if (c < nl) {
-    for (int k0 = 8 * q; k0 < N; k0 += 8 * (kAxisThreads / kCols)) {
+    for (int k0 = 8 * q; k0 < N; k0 += 8 * kJStep) {
       float acc[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) acc[r] = 0.0f;
@@ -369,18 +448,10 @@ __global__ void __launch_bounds__(kAxisThreads) k_f4_axis(Dims d, int axis, cons
   __syncthreads();
   if (inner == 1) {
     float* dst = Y + l0 * N;
-    for (int t = tid; t < nl * N; t += kAxisThreads) {
-      const int cc = t / N, j = t - cc * N;
-      dst[t] = Ys[j * kColStr + cc];
-    }
-  } else {
-    for (int t = tid; t < N * kCols; t += kAxisThreads) {
-      const int j = t / kCols, cc = t - j * kCols;
-      if (cc < nl) {
-        const int ln = l0 + cc, o = ln / inner, i = ln - o * inner;
-        Y[(o * N + j) * inner + i] = Ys[j * kColStr + cc];
-      }
-    }
+    for (int c = tid >> 5; c < nl; c += kAxisThreads / 32)
+      for (int j = tid & 31; j < N; j += 32) dst[c * N + j] = Ys[j * kColStr + c];
+  } else if (cc < nl) {
+    for (int j = jq; j < N; j += kJStep) Y[cbase + j * inner] = Ys[j * kColStr + cc];
   }
 }
 
@@ -504,17 +575,27 @@ __global__ void __launch_bounds__(128) k_f4_psi(Dims d, const DevState* st, int 
 }
 
 // Moment sums of the weights after the time update (buffer of the stage).
-__global__ void k_f4_moments(Dims d, const DevState* st, int stage, const float* b0, const float* b1,
-                             double* partials) {
+__global__ void __launch_bounds__(kMomThreads) k_f4_moments(Dims d, const DevState* st, int stage,
+                                                            const float* b0, const float* b1,
+                                                            double* partials) {
   const int par = (st->f.cur + stage) & 1;
   const float* X = par ? b1 : b0;
+  const int N3 = d.N[3], lines = (int)d.P / N3;
+  const float h3 = 0.5f * (N3 - 1);
+  const int ln = blockIdx.x * kLinesM + threadIdx.x / 4, q = threadIdx.x % 4;
   Mom4 m;
   m.zero();
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < d.P;
-       p += (long long)gridDim.x * blockDim.x) {
-    float u[4];
-    frame_u4(d, p, u);
-    m.add(X[p], u);
+  if (ln < lines) {
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+    for (int j = q; j < N3; j += 4) {
+      const float v = X[ln * N3 + j], u3 = j - h3, vu = v * u3;
+      s0 += v;
+      s1 += vu;
+      s2 = fmaf(vu, u3, s2);
+    }
+    float u[3];
+    line_u(d, ln, u);
+    m.add_line(s0, s1, s2, u[0], u[1], u[2]);
   }
   mom4_block(m, partials + blockIdx.x * kMomentSlots);
 }
@@ -550,12 +631,12 @@ int f4_alloc(const pmf_config* cfg, F4Tables* t) {
   *t = F4Tables{};
   long long P = 1;
   for (int a = 0; a < 4; ++a) P *= cfg->N[a];
-  bool ok = cudaMalloc(&t->lo, sizeof(double) * P) == cudaSuccess &&
+  bool ok = cudaMalloc(&t->mtab, sizeof(double2) * 16 * kMaxN4) == cudaSuccess &&
+            cudaMalloc(&t->lo, sizeof(float) * P) == cudaSuccess &&
             cudaMalloc(&t->gap, sizeof(float) * P) == cudaSuccess;
   for (int a = 0; ok && a < 4; ++a) {
     const int N = cfg->N[a], Kp = kpad(N);
-    ok = cudaMalloc(&t->interp[a], sizeof(double) * N * N) == cudaSuccess &&
-         cudaMalloc(&t->hfwd[a], sizeof(double) * N * N) == cudaSuccess &&
+    ok = cudaMalloc(&t->hfwd[a], sizeof(double) * N * N) == cudaSuccess &&
          cudaMalloc(&t->wfwd[a], sizeof(float) * N * Kp) == cudaSuccess &&
          cudaMalloc(&t->winv[a], sizeof(float) * N * Kp) == cudaSuccess;
     if (!ok) break;
@@ -581,10 +662,10 @@ int f4_alloc(const pmf_config* cfg, F4Tables* t) {
 }
 
 void f4_free(F4Tables* t) {
+  cudaFree(t->mtab);
   cudaFree(t->lo);
   cudaFree(t->gap);
   for (int a = 0; a < 4; ++a) {
-    cudaFree(t->interp[a]);
     cudaFree(t->hfwd[a]);
     cudaFree(t->wfwd[a]);
     cudaFree(t->winv[a]);
@@ -595,20 +676,24 @@ void f4_free(F4Tables* t) {
 int f4_meas(const Dims& d, const MeasParams& mp, DevState* st, const F4Tables& t, float* b0, float* b1,
             double* partials, cudaStream_t s) {
   cudaMemsetAsync(&st->emin_bits, 0xff, sizeof(unsigned long long), s);
-  k_f4_meas_e<<<d.N[0] * d.N[1], 256, 0, s>>>(d, mp, st, t.lo, t.gap);
-  const int nb = grid_cap(d.P, 256, kMomBlocks);
-  k_f4_meas_apply<<<nb, 256, 0, s>>>(d, st, t.lo, t.gap, b0, b1, partials);
+  int n = 3;
+  if (mp.kind == PMF_MEAS_TERRAIN_GM) {
+    k_f4_meas_tab<<<4, 128, 0, s>>>(d, mp, st, t.mtab);
+    ++n;
+  }
+  k_f4_meas_e<<<d.N[0] * d.N[1], 256, 0, s>>>(d, mp, st, t.mtab, t.lo, t.gap);
+  const int nb = (int)((d.P / d.N[3] + kLinesM - 1) / kLinesM);
+  k_f4_meas_apply<<<nb, kMomThreads, 0, s>>>(d, st, t.lo, t.gap, b0, b1, partials);
   launch_finalize(d, st, partials, nb, 1, 0, nullptr, s);
-  return 3;
+  return n;
 }
 
 int f4_time(const Dims& d, const TimeConsts& tc, DevState* st, const F4Tables& t, float* b0, float* b1,
             double* partials, double* pend, cudaStream_t s) {
   launch_frame(tc, st, pend, s);
-  launch_build_interp(d, st, t.interp, s);
   int maxN = 0;
   for (int a = 0; a < 4; ++a) maxN = d.N[a] > maxN ? d.N[a] : maxN;
-  k_f4_fuse<<<dim3(maxN, 4), 64, 0, s>>>(d, t);
+  k_f4_tables<<<dim3(maxN, 4), 64, 0, s>>>(d, st, t);
   k_f4_realign<<<grid_cap(d.P, 256, 4096), 256, 0, s>>>(d, st, b0, b1);
   int stage = 1;
   auto axis = [&](int a, const float* WT) {
@@ -622,10 +707,10 @@ int f4_time(const Dims& d, const TimeConsts& tc, DevState* st, const F4Tables& t
   for (int a = 0; a < 4; ++a) reps *= d.N[a] / 2 + 1;
   k_f4_psi<<<grid_cap(reps, 128, 4096), 128, 0, s>>>(d, st, stage, b0, b1);
   for (int a = 0; a < 4; ++a) axis(a, t.winv[a]);
-  const int nb = grid_cap(d.P, 256, kMomBlocks);
-  k_f4_moments<<<nb, 256, 0, s>>>(d, st, stage, b0, b1, partials);
+  const int nb = (int)((d.P / d.N[3] + kLinesM - 1) / kLinesM);
+  k_f4_moments<<<nb, kMomThreads, 0, s>>>(d, st, stage, b0, b1, partials);
   launch_finalize(d, st, partials, nb, stage & 1, 1, pend, s);
-  return 1 + 4 + 1 + 1 + 8 + 1 + 2;
+  return 1 + 1 + 1 + 8 + 1 + 2;
 }
 
 }  // namespace pmf

@@ -8,9 +8,9 @@
 namespace pmf {
 
 struct F4Tables {
-  double* lo = nullptr;        // per point: smaller mixture exponent (or the exponent)
+  double2* mtab = nullptr;     // terrain waves: per-axis phase tables (4 waves x 4 axes x 64)
+  float* lo = nullptr;         // per point: smaller mixture exponent (or the exponent)
   float* gap = nullptr;        // per point: gap to the other mixture exponent
-  double* interp[4] = {};      // per axis: regrid matrix (float64, N x N)
   double* hfwd[4] = {};        // per axis: forward Hartley matrix / N (float64)
   float* wfwd[4] = {};         // per axis: (H I)^T, columns padded to a multiple of 8
   float* winv[4] = {};         // per axis: H^T (inverse transform), padded likewise

@@ -552,12 +552,6 @@ void launch_frame(const TimeConsts& tc, DevState* st, double* pend, cudaStream_t
   k_frame<<<1, MAXL, 0, s>>>(tc, st, pend);
 }
 
-void launch_build_interp(const Dims& d, const DevState* st, double* const* interp, cudaStream_t s) {
-  for (int a = 0; a < d.nx; ++a)
-    k_build_interp_f64<<<grid_for((long long)d.N[a] * d.N[a], 256, 1 << 20), 256, 0, s>>>(
-        d, st, a, interp[a]);
-}
-
 void launch_finalize(const Dims& d, DevState* st, const double* partials, int nblocks, int flip,
                      int use_pending, const double* pend, cudaStream_t s) {
   k_finalize<<<1, 256, 0, s>>>(d, st, partials, nblocks, flip, use_pending, pend);

@@ -23,10 +23,8 @@ void launch_export_f64(const Dims& d, const DevState* st, const double* b0, cons
                        double* out, cudaStream_t s);
 
 // Pieces shared with the float32 n_x = 4 path: the frame kernel (regrid
-// decision, sub-step coefficients), the per-axis regrid matrices (float64)
-// and the moment finalisation.
+// decision, sub-step coefficients) and the moment finalisation.
 void launch_frame(const TimeConsts& tc, DevState* st, double* pend, cudaStream_t s);
-void launch_build_interp(const Dims& d, const DevState* st, double* const* interp, cudaStream_t s);
 void launch_finalize(const Dims& d, DevState* st, const double* partials, int nblocks, int flip,
                      int use_pending, const double* pend, cudaStream_t s);
 
