@@ -156,8 +156,8 @@ def _launch_names(sc):
 # DRAM bytes (read + write) per launch of the timed kernel, from one ncu capture
 # of the current kernel (profiles/): the 128 x 128 fused kernel, and the batch
 # kernel per grid point (captured on 2048 filters, scaled by the points).
-TRAFFIC_C2 = 373760.0
-TRAFFIC_C4_PER_POINT = (53320704.0 + 11064320.0) / 10976512.0
+TRAFFIC_C2 = 346880.0
+TRAFFIC_C4_PER_POINT = (59654912.0 + 9783296.0) / 10976512.0
 
 
 def _flops_per_step(N):
