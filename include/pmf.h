@@ -93,6 +93,16 @@ enum { PMF_PSI_EULER = 0, PMF_PSI_EXACT = 1 };
  *                 the box. */
 enum { PMF_REALIGN_MULTILINEAR = 0, PMF_REALIGN_SHEAR = 1 };
 
+/* Form of the per-axis Hartley transforms (step 1 and step 5 of the Sec. V-B
+ * algorithm).
+ *   AUTO : per grid size the faster form, measured on first use (n_x = 1;
+ *          the environment variable PMF_1D_FORM=matvec|fft overrides it);
+ *          the contraction everywhere else.
+ *   GEMM : the dense contraction with the N x N transform matrix (every path).
+ *   FFT  : the shared-memory radix-2 FFT (n_x = 1, non-FP64 precision, N a
+ *          power of two); PMF_ERR_UNSUPPORTED elsewhere. */
+enum { PMF_TRANSFORM_AUTO = 0, PMF_TRANSFORM_GEMM = 1, PMF_TRANSFORM_FFT = 2 };
+
 /* Measurement functions h of eq. meas. */
 enum {
   PMF_MEAS_LINEAR = 0,          /* h(x) = H x, nz rows of H */
@@ -123,6 +133,7 @@ typedef struct pmf_config {
   int precision;                /* PMF_PREC_* */
   int psi_mode;                 /* PMF_PSI_* */
   int realign_mode;             /* PMF_REALIGN_* (default MULTILINEAR) */
+  int transform;                /* PMF_TRANSFORM_* (default AUTO) */
 } pmf_config;
 
 typedef struct pmf_meas {

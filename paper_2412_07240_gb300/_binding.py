@@ -22,6 +22,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_DEGENERATE, ERR_TIMEOUT, ERR_ADMISSION, ERR_
 PREC = {"fp64": 0, "tf32": 1, "tf32x3": 2, "bf16x3": 3, "fp16x3": 4}
 PSI = {"euler": 0, "exact": 1}
 REALIGN = {"multilinear": 0, "shear": 1}
+TRANSFORM = {"auto": 0, "gemm": 1, "fft": 2}
 MEAS = {"linear": 0, "range": 1, "bearing_linear3": 2, "terrain_gm": 3}
 ERRNAMES = {1: "PMF_ERR_ARG", 2: "PMF_ERR_OOM", 3: "PMF_ERR_CUDA", 4: "PMF_ERR_DEGENERATE",
             5: "PMF_ERR_TIMEOUT", 6: "PMF_ERR_ADMISSION", 7: "PMF_ERR_UNSUPPORTED"}
@@ -46,7 +47,7 @@ class PmfConfig(C.Structure):
                 ("Q", C.c_double * (MAX_NX * MAX_NX)), ("m0", C.c_double * MAX_NX),
                 ("P0", C.c_double * (MAX_NX * MAX_NX)), ("span_sigma", C.c_double),
                 ("dt_sub", C.c_double), ("realign_rho", C.c_double), ("precision", C.c_int),
-                ("psi_mode", C.c_int), ("realign_mode", C.c_int)]
+                ("psi_mode", C.c_int), ("realign_mode", C.c_int), ("transform", C.c_int)]
 
 
 class PmfMeas(C.Structure):
@@ -148,7 +149,7 @@ def _stream_handle(stream):
     return C.c_void_p(0)
 
 
-def make_config(cfg, precision="fp64", psi_mode="euler") -> PmfConfig:
+def make_config(cfg, precision="fp64", psi_mode="euler", transform="auto") -> PmfConfig:
     """Marshal a filter configuration (nx, N, A, Q, m0, P0, span, dt_sub, realign_rho)."""
     lib = load()
     c = PmfConfig()
@@ -167,6 +168,7 @@ def make_config(cfg, precision="fp64", psi_mode="euler") -> PmfConfig:
     c.precision = PREC[precision] if isinstance(precision, str) else int(precision)
     c.psi_mode = PSI[psi_mode] if isinstance(psi_mode, str) else int(psi_mode)
     c.realign_mode = REALIGN[getattr(cfg, "realign_mode", "multilinear")]
+    c.transform = TRANSFORM[transform] if isinstance(transform, str) else int(transform)
     return c
 
 
@@ -206,11 +208,11 @@ def moments_noalloc(weights, N, c, M, out, stream=None) -> None:
 class Filter:
     """One spectral point-mass filter resident on the GPU (a pmf_ctx)."""
 
-    def __init__(self, cfg, precision="fp64", psi_mode="euler", stream=None):
+    def __init__(self, cfg, precision="fp64", psi_mode="euler", stream=None, transform="auto"):
         self._lib = load()
         self.nx = int(cfg.nx)
         self.N = tuple(int(v) for v in cfg.N[: self.nx])
-        self._cfg = make_config(cfg, precision, psi_mode)
+        self._cfg = make_config(cfg, precision, psi_mode, transform)
         self._stream = _stream_handle(stream)
         h = C.c_void_p()
         rc = self._lib.pmf_create(C.byref(h), C.byref(self._cfg), self._stream)

@@ -158,6 +158,10 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
   for (int a = 0; a < n; ++a) ctx->dims.P *= cfg->N[a];
   const long long P = ctx->dims.P;
 
+  if (cfg->transform == PMF_TRANSFORM_FFT && (cfg->nx != 1 || cfg->precision == PMF_PREC_FP64)) {
+    free_ctx(ctx);
+    return PMF_ERR_UNSUPPORTED;   // the FFT form exists in the 1-D kernel only
+  }
   if (cfg->precision != PMF_PREC_FP64) {
     rc = cfg->nx == 1   ? tc1_supported(cfg, &why)
          : cfg->nx == 4 ? f4_supported(cfg, &why)
@@ -221,7 +225,7 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
       free_ctx(ctx);
       return rc;
     }
-    ctx->mode1 = tc1_mode(cfg->N[0], ctx->tab1, ctx->stream);
+    ctx->mode1 = tc1_form(cfg, ctx->tab1, ctx->stream);
   } else {
     rc = tc_build_tables(cfg, &ctx->tct, &why);
     if (rc == PMF_OK && ctx->path == 2) rc = tc3_alloc(&ctx->tc3);
@@ -462,7 +466,8 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
   for (int i = 0; i < count; ++i) {
     int rc = validate_config(&cfgs[i], &why);
     if (rc) return rc;
-    if (cfgs[i].nx != 2 || cfgs[i].precision != prec) return PMF_ERR_UNSUPPORTED;
+    if (cfgs[i].nx != 2 || cfgs[i].precision != prec || cfgs[i].transform == PMF_TRANSFORM_FFT)
+      return PMF_ERR_UNSUPPORTED;
     rc = tc_supported(&cfgs[i], &why);
     if (rc) return rc;
     rc = meas_params(2, &models[i], &mps[i], &why);

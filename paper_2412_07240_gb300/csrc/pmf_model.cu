@@ -151,6 +151,10 @@ int validate_config(const pmf_config* c, std::string* why) {
     *why = "unknown re-alignment mode";
     return PMF_ERR_ARG;
   }
+  if (c->transform < PMF_TRANSFORM_AUTO || c->transform > PMF_TRANSFORM_FFT) {
+    *why = "unknown transform form";
+    return PMF_ERR_ARG;
+  }
   if (c->realign_mode == PMF_REALIGN_SHEAR && c->nx != 2) {
     *why = "shear re-alignment is defined for n_x = 2";
     return PMF_ERR_ARG;

@@ -418,7 +418,10 @@ int pmf_server_admit(pmf_server* s, const pmf_config* cfg, const pmf_meas* model
   int rc = validate_config(cfg, &why);
   if (rc) return sfail(s, rc, why);
   const int n = cfg->nx;
-  if (n == 1) {
+  if (cfg->transform == PMF_TRANSFORM_FFT && n != 1) {
+    rc = PMF_ERR_UNSUPPORTED;
+    why = "the FFT form exists in the 1-D kernel only";
+  } else if (n == 1) {
     rc = tc1_supported(cfg, &why);
   } else {
     pmf_config c2 = *cfg;
@@ -490,7 +493,7 @@ int pmf_server_admit(pmf_server* s, const pmf_config* cfg, const pmf_meas* model
   if (ok) s->launches += tc_prior(d, f.st, s->d_aux, f.buf, s->d_partials, st);
   if (ok && n == 1) {
     const Slot1 sl{f.st, f.buf, f.buf + P, (const float*)tabs[0], cfg->N[0], f.d_mp, nullptr,
-                   tc1_mode(cfg->N[0], tabs[0], st)};
+                   tc1_form(cfg, tabs[0], st)};
     ok = cudaMemcpyAsync(s->d_slots1 + id, &sl, sizeof(sl), cudaMemcpyHostToDevice, st) == cudaSuccess;
   } else if (ok && n == 2) {
     FilterSlot sl{};

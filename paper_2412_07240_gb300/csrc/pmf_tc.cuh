@@ -110,6 +110,8 @@ int tc1_step(int N, const void* table, const MeasParams* mp, const TimeConsts* t
 // Transform form for size N chosen by timing both on a scratch filter (once
 // per N and process; cached in autotune.json beside the library).  The
 // environment variable PMF_1D_FORM=fft|matvec overrides the choice.
+// Transform form of a 1-D filter: the config's choice, or tc1_mode for AUTO.
+int tc1_form(const pmf_config* cfg, const void* table, cudaStream_t s);
 int tc1_mode(int N, const void* table, cudaStream_t s);
 int tc1_batch_step(const Slot1* slots, const StepItem* items, const TimeConsts* tcs, int k, cudaStream_t s);
 // {mean[2], cov[4], status, 0} of filters ids[0..k) into out (8 doubles each),

@@ -375,6 +375,10 @@ int tc1_supported(const pmf_config* cfg, std::string* why) {
     *why = "the 1-D kernel needs n_x = 1 and N a multiple of 8 in [16, 512]";
     return PMF_ERR_UNSUPPORTED;
   }
+  if (cfg->transform == PMF_TRANSFORM_FFT && (cfg->N[0] & (cfg->N[0] - 1))) {
+    *why = "the FFT form needs N a power of two";
+    return PMF_ERR_UNSUPPORTED;
+  }
   return PMF_OK;
 }
 
@@ -538,6 +542,12 @@ double time_mode(int N, const void* table, int mode, cudaStream_t s) {
 }
 
 }  // namespace
+
+int tc1_form(const pmf_config* cfg, const void* table, cudaStream_t s) {
+  if (cfg->transform == PMF_TRANSFORM_GEMM) return 0;
+  if (cfg->transform == PMF_TRANSFORM_FFT) return 1;
+  return tc1_mode(cfg->N[0], table, s);
+}
 
 int tc1_mode(int N, const void* table, cudaStream_t s) {
   if (N < 16 || (N & (N - 1))) return 0;   // the FFT form needs a power of two

@@ -34,7 +34,8 @@ def frame_choice_error(orc, tau, choice):
     return float(np.abs(own["D"] - choice["D"]).max() / np.abs(own["D"]).max())
 
 
-def run_pair(sc, precision="fp64", epochs=None, psi_mode="euler", fused_step=False, follow_frame=False):
+def run_pair(sc, precision="fp64", epochs=None, psi_mode="euler", fused_step=False, follow_frame=False,
+             transform="auto"):
     """Yield (stage, errors) after every update of both filters.
 
     follow_frame: the oracle takes each regrid decision (centre shift, scales
@@ -45,7 +46,7 @@ def run_pair(sc, precision="fp64", epochs=None, psi_mode="euler", fused_step=Fal
     the sixth digit it can land on a neighbouring lattice point, and both
     frames are then valid grids for the method."""
     from paper_2412_07240_gb300 import Filter
-    gpu = Filter(sc.cfg, precision=precision, psi_mode=psi_mode)
+    gpu = Filter(sc.cfg, precision=precision, psi_mode=psi_mode, transform=transform)
     orc = OracleFilter(sc.cfg, psi_mode=psi_mode)
     yield "prior", compare(gpu, orc)
     for k in range(epochs or sc.epochs):

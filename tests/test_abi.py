@@ -42,6 +42,7 @@ def test_config_defaults_and_struct_layout():
     # int nx, int N[4] (+4 padding) | A, Q | m0 | P0 | span, dt_sub, rho | precision, psi_mode,
     # realign_mode (+4 padding)
     assert ctypes.sizeof(_binding.PmfConfig) == 24 + 128 + 128 + 32 + 128 + 24 + 16
+    assert _binding.PmfConfig.transform.offset == 476
     # int kind, nz | z[3] | R[9] | H[12] | p[24]
     assert ctypes.sizeof(_binding.PmfMeas) == 8 + 24 + 72 + 96 + 192
 

@@ -58,6 +58,24 @@ def test_transform_forms(form, N, monkeypatch):
     assert worst["l1"] < BAR, log
 
 
+@pytest.mark.parametrize("form", ["fft", "gemm"])
+def test_transform_form_from_the_config(form, monkeypatch):
+    monkeypatch.delenv("PMF_1D_FORM", raising=False)
+    sc = w.c1_scenario(N=128, epochs=6)
+    worst, log = max_errors(sc, precision="fp16x3", fused_step=True, transform=form)
+    assert worst["l1"] < BAR, log
+
+
+def test_fft_form_only_where_it_exists():
+    from paper_2412_07240_gb300 import Filter, Unsupported
+    with pytest.raises(Unsupported):                         # not a power of two
+        Filter(w.c1_scenario(N=200).cfg, precision="fp16x3", transform="fft")
+    with pytest.raises(Unsupported):                         # float64 path
+        Filter(w.c1_scenario(N=64).cfg, precision="fp64", transform="fft")
+    with pytest.raises(Unsupported):                         # 2-D tensor-core path
+        Filter(w.small_2d_scenario(N=(48, 32), epochs=1).cfg, precision="fp16x3", transform="fft")
+
+
 def test_autotuner_records_its_choice(monkeypatch):
     import json
     import os
