@@ -11,11 +11,13 @@
 //                interFreq) folded into the forward Hartley transform, float64,
 //                rounded to float32
 //   realign      multilinear re-alignment (or scaled copy) of the weights
-//   fwd x 4      W_a along axis a
+//   slab23       W_3 and W_2 on (j0, j1) slabs in shared memory (one pass)
+//   fwd 1, fwd 0 W_a along axis a
 //   psi          diffusion multiplier and trace factor over 16-point sign-flip
 //                orbits (the separable-to-4-D Hartley parity fix-up)
-//   inv x 4      inverse Hartley transform along each axis (step 5)
-//   moments      normaliser and moments in double-float, finalised in float64
+//   inv 0, inv 1 inverse Hartley transform along axes 0 and 1 (step 5)
+//   slab23       inverse along axes 2 and 3, with the moment sums of the result
+//   finalize     normaliser and moments (float64, step 6)
 // Per measurement update (eq. filt): exponent parts and their minimum, then
 // the likelihood multiply with the moment sums, then the finalisation.
 #include <cmath>
@@ -455,6 +457,113 @@ __global__ void __launch_bounds__(kAxisThreads) k_f4_axis(Dims d, int axis, cons
   }
 }
 
+// Both inner axes at once: a block takes kSlabs slabs (j0, j1) of N2 x N3
+// contiguous points, applies W3 along axis 3 (rows of a slab) and then W2
+// along axis 2 (its columns) in shared memory, and writes the slabs back: one
+// pass over the grid for two contractions.  With kMom the moment sums of the
+// result (the weights after the inverse transform) are formed from the slabs
+// in shared memory (line sums along axis 3, double-float slot totals).
+// Reads bufs[(cur+stage)&1], writes the other one.
+constexpr int kSlabs = 4;
+constexpr int kSlabThreads = 256;
+
+__device__ __forceinline__ void contract_lines(const float* X, float* Y, const float* Ws, int lines, int per,
+                                               int sstride, int N, int Kp, int xl, int xj, int yl, int yk) {
+  // Y[line][k] = sum_j W[k][j] X[line][j] over lines = (slab, c), line = slab *
+  // per + c: element (line, j) of X at slab * sstride + c * xl + j * xj, of Y
+  // at slab * sstride + c * yl + k * yk; W^T rows j in Ws (k contiguous, Kp)
+  const int groups = (N + 7) / 8;
+  for (int it = threadIdx.x; it < lines * groups; it += blockDim.x) {
+    const int line = it % lines, k0 = (it / lines) * 8;
+    const int sb = line / per, c = line - sb * per;
+    float acc[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) acc[r] = 0.0f;
+    const float* xr = X + sb * sstride + c * xl;
+#pragma unroll 2
+    for (int j = 0; j < N; ++j) {
+      const float x = xr[j * xj];
+      const float4 w0 = *(const float4*)(Ws + j * Kp + k0);
+      const float4 w1 = *(const float4*)(Ws + j * Kp + k0 + 4);
+      acc[0] = fmaf(w0.x, x, acc[0]);
+      acc[1] = fmaf(w0.y, x, acc[1]);
+      acc[2] = fmaf(w0.z, x, acc[2]);
+      acc[3] = fmaf(w0.w, x, acc[3]);
+      acc[4] = fmaf(w1.x, x, acc[4]);
+      acc[5] = fmaf(w1.y, x, acc[5]);
+      acc[6] = fmaf(w1.z, x, acc[6]);
+      acc[7] = fmaf(w1.w, x, acc[7]);
+    }
+    float* yr = Y + sb * sstride + c * yl;
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+      if (k0 + r < N) yr[(k0 + r) * yk] = acc[r];
+  }
+}
+
+size_t slab_smem(int N2, int N3) {
+  return sizeof(float) * (2 * (size_t)kSlabs * N2 * (N3 + 1) + (size_t)N3 * kpad(N3) + (size_t)N2 * kpad(N2));
+}
+
+template <bool kMom>
+__global__ void __launch_bounds__(kSlabThreads) k_f4_slab23(Dims d, const float* W3T, const float* W2T,
+                                                            const DevState* st, int stage, float* b0, float* b1,
+                                                            double* partials) {
+  extern __shared__ __align__(16) float sm[];
+  const int N1 = d.N[1], N2 = d.N[2], N3 = d.N[3];
+  const int str = N3 + 1, slab = N2 * str, K3 = kpad(N3), K2 = kpad(N2);
+  float* Xs = sm;                               // [kSlabs][N2][N3 + 1]
+  float* Ys = Xs + kSlabs * slab;               // [kSlabs][N2][N3 + 1]
+  float* W3 = Ys + kSlabs * slab;               // [N3][K3]
+  float* W2 = W3 + N3 * K3;                     // [N2][K2]
+  const int par = (st->f.cur + stage) & 1;
+  const float* X = par ? b1 : b0;
+  float* Y = par ? b0 : b1;
+  const int nslab = d.N[0] * N1, s0 = blockIdx.x * kSlabs, ns = min(kSlabs, nslab - s0);
+  const int tid = threadIdx.x, pts = N2 * N3;
+  for (int i = tid; i < N3 * K3; i += kSlabThreads) W3[i] = W3T[i];
+  for (int i = tid; i < N2 * K2; i += kSlabThreads) W2[i] = W2T[i];
+  for (int sl = 0; sl < ns; ++sl) {
+    const float* src = X + (size_t)(s0 + sl) * pts;
+    for (int t = tid; t < pts; t += kSlabThreads) {
+      const int r = t / N3, c = t - r * N3;
+      Xs[sl * slab + r * str + c] = src[t];
+    }
+  }
+  __syncthreads();
+  // axis 3: rows (sl, j2) of every slab, X -> Y
+  contract_lines(Xs, Ys, W3, ns * N2, N2, slab, N3, K3, str, 1, str, 1);
+  __syncthreads();
+  // axis 2: columns (sl, k3) of every slab, Y -> X
+  contract_lines(Ys, Xs, W2, ns * N3, N3, slab, N2, K2, 1, str, 1, str);
+  __syncthreads();
+  for (int sl = 0; sl < ns; ++sl) {
+    float* dst = Y + (size_t)(s0 + sl) * pts;
+    for (int t = tid; t < pts; t += kSlabThreads) {
+      const int r = t / N3, c = t - r * N3;
+      dst[t] = Xs[sl * slab + r * str + c];
+    }
+  }
+  if constexpr (kMom) {
+    Mom4 m;
+    m.zero();
+    const float h3 = 0.5f * (N3 - 1);
+    for (int ln = tid; ln < ns * N2; ln += kSlabThreads) {
+      const int sl = ln / N2, r = ln - sl * N2, sg = s0 + sl;
+      const float* row = Xs + sl * slab + r * str;
+      float a = 0.0f, b = 0.0f, c = 0.0f;
+      for (int j = 0; j < N3; ++j) {
+        const float v = row[j], u3 = j - h3, vu = v * u3;
+        a += v;
+        b += vu;
+        c = fmaf(vu, u3, c);
+      }
+      m.add_line(a, b, c, (sg / N1) - 0.5f * (d.N[0] - 1), (sg % N1) - 0.5f * (N1 - 1), r - 0.5f * (N2 - 1));
+    }
+    mom4_block(m, partials + blockIdx.x * kMomentSlots);
+  }
+}
+
 // Diffusion multiplier and trace factor in the Hartley domain (algorithm
 // steps 2-4) for n_x = 4: one thread per orbit {sigma . k} of the 16 sign
 // flips.  The separable coefficients S split into parity components T_B (odd
@@ -574,32 +683,6 @@ __global__ void __launch_bounds__(128) k_f4_psi(Dims d, const DevState* st, int 
   }
 }
 
-// Moment sums of the weights after the time update (buffer of the stage).
-__global__ void __launch_bounds__(kMomThreads) k_f4_moments(Dims d, const DevState* st, int stage,
-                                                            const float* b0, const float* b1,
-                                                            double* partials) {
-  const int par = (st->f.cur + stage) & 1;
-  const float* X = par ? b1 : b0;
-  const int N3 = d.N[3], lines = (int)d.P / N3;
-  const float h3 = 0.5f * (N3 - 1);
-  const int ln = blockIdx.x * kLinesM + threadIdx.x / 4, q = threadIdx.x % 4;
-  Mom4 m;
-  m.zero();
-  if (ln < lines) {
-    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
-    for (int j = q; j < N3; j += 4) {
-      const float v = X[ln * N3 + j], u3 = j - h3, vu = v * u3;
-      s0 += v;
-      s1 += vu;
-      s2 = fmaf(vu, u3, s2);
-    }
-    float u[3];
-    line_u(d, ln, u);
-    m.add_line(s0, s1, s2, u[0], u[1], u[2]);
-  }
-  mom4_block(m, partials + blockIdx.x * kMomentSlots);
-}
-
 inline int grid_cap(long long work, int threads, int cap) {
   long long b = (work + threads - 1) / threads;
   return (int)(b < 1 ? 1 : b > cap ? cap : b);
@@ -651,8 +734,11 @@ int f4_alloc(const pmf_config* cfg, F4Tables* t) {
     ok = ok && cudaMemcpy(t->winv[a], WT.data(), sizeof(float) * N * Kp, cudaMemcpyHostToDevice) == cudaSuccess;
   }
   if (ok) {
-    const int smem = (int)axis_smem(kMaxN4);
-    ok = cudaFuncSetAttribute(k_f4_axis, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
+    const int smem = (int)axis_smem(kMaxN4), ssm = (int)slab_smem(kMaxN4, kMaxN4);
+    ok = cudaFuncSetAttribute(k_f4_axis, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
+         cudaFuncSetAttribute(k_f4_slab23<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(k_f4_slab23<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm) == cudaSuccess;
   }
   if (!ok) {
     f4_free(t);
@@ -702,15 +788,19 @@ int f4_time(const Dims& d, const TimeConsts& tc, DevState* st, const F4Tables& t
                                                                                               stage, b0, b1);
     ++stage;
   };
-  for (int a = 0; a < 4; ++a) axis(a, t.wfwd[a]);
+  const int nslab = (d.N[0] * d.N[1] + kSlabs - 1) / kSlabs;
+  const size_t ssm = slab_smem(d.N[2], d.N[3]);
+  k_f4_slab23<false><<<nslab, kSlabThreads, ssm, s>>>(d, t.wfwd[3], t.wfwd[2], st, stage++, b0, b1, nullptr);
+  axis(1, t.wfwd[1]);
+  axis(0, t.wfwd[0]);
   long long reps = 1;
   for (int a = 0; a < 4; ++a) reps *= d.N[a] / 2 + 1;
   k_f4_psi<<<grid_cap(reps, 128, 4096), 128, 0, s>>>(d, st, stage, b0, b1);
-  for (int a = 0; a < 4; ++a) axis(a, t.winv[a]);
-  const int nb = (int)((d.P / d.N[3] + kLinesM - 1) / kLinesM);
-  k_f4_moments<<<nb, kMomThreads, 0, s>>>(d, st, stage, b0, b1, partials);
-  launch_finalize(d, st, partials, nb, stage & 1, 1, pend, s);
-  return 1 + 1 + 1 + 8 + 1 + 2;
+  axis(0, t.winv[0]);
+  axis(1, t.winv[1]);
+  k_f4_slab23<true><<<nslab, kSlabThreads, ssm, s>>>(d, t.winv[3], t.winv[2], st, stage++, b0, b1, partials);
+  launch_finalize(d, st, partials, nslab, stage & 1, 1, pend, s);
+  return 1 + 1 + 1 + 6 + 1 + 1;
 }
 
 }  // namespace pmf
