@@ -302,10 +302,10 @@ __global__ void k_f4_tables(Dims d, const DevState* st, const F4Tables t) {
 // node adds B_a3 j3 in double-float (exact product of the high part), and the
 // integer part and the fraction of the position come from that sum (~1e-12
 // node); the corner weights and sums are float32.
-constexpr int kLinesR = 8;
+constexpr int kLinesRMax = 128;   // lines per block iteration: 512 / N3 (two passes of 256 threads)
 
 __global__ void __launch_bounds__(256) k_f4_realign(Dims d, const DevState* st, float* b0, float* b1) {
-  __shared__ DF zl[kLinesR][4];
+  __shared__ DF zl[kLinesRMax][4];
   const int cur = st->f.cur;
   const float* in = cur ? b1 : b0;
   float* out = cur ? b0 : b1;
@@ -315,20 +315,21 @@ __global__ void __launch_bounds__(256) k_f4_realign(Dims d, const DevState* st, 
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) out[p] = ps * in[p];
     return;
   }
-  const int lines = P / N3;
+  const int lines = P / N3, kLinesR = min(kLinesRMax, 512 / N3);
   const int N0 = d.N[0], N1 = d.N[1], N2 = d.N[2];
   DF B3[4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) B3[a] = df_of(st->f.B[a * 4 + 3]);
   for (int l0 = blockIdx.x * kLinesR; l0 < lines; l0 += gridDim.x * kLinesR) {
-    if (threadIdx.x < kLinesR * 4) {
-      const int li = threadIdx.x >> 2, a = threadIdx.x & 3, ln = l0 + li;
+    for (int it = threadIdx.x; it < kLinesR * 4; it += blockDim.x) {
+      const int li = it >> 2, a = it & 3, ln = l0 + li;
       if (ln < lines) {
         const int j2 = ln % N2, j1 = (ln / N2) % N1, j0 = ln / (N2 * N1);
-        const double u[4] = {j0 - 0.5 * (N0 - 1), j1 - 0.5 * (N1 - 1), j2 - 0.5 * (N2 - 1), -0.5 * (N3 - 1)};
-        double z = st->f.b[a] + 0.5 * (d.N[a] - 1);
-#pragma unroll
-        for (int b = 0; b < 4; ++b) z = fma(st->f.B[a * 4 + b], u[b], z);
+        double z = st->f.b[a] + 0.5 * ((a == 0 ? N0 : a == 1 ? N1 : a == 2 ? N2 : N3) - 1);
+        z = fma(st->f.B[a * 4 + 0], j0 - 0.5 * (N0 - 1), z);
+        z = fma(st->f.B[a * 4 + 1], j1 - 0.5 * (N1 - 1), z);
+        z = fma(st->f.B[a * 4 + 2], j2 - 0.5 * (N2 - 1), z);
+        z = fma(st->f.B[a * 4 + 3], -0.5 * (N3 - 1), z);
         zl[li][a] = df_of(z);
       }
     }
@@ -780,7 +781,7 @@ int f4_time(const Dims& d, const TimeConsts& tc, DevState* st, const F4Tables& t
   int maxN = 0;
   for (int a = 0; a < 4; ++a) maxN = d.N[a] > maxN ? d.N[a] : maxN;
   k_f4_tables<<<dim3(maxN, 4), 64, 0, s>>>(d, st, t);
-  k_f4_realign<<<grid_cap(d.P, 256, 4096), 256, 0, s>>>(d, st, b0, b1);
+  k_f4_realign<<<grid_cap(d.P / d.N[3], 512 / d.N[3], 4096), 256, 0, s>>>(d, st, b0, b1);
   int stage = 1;
   auto axis = [&](int a, const float* WT) {
     const long long lines = d.P / d.N[a];
