@@ -17,13 +17,14 @@
 //                orbits (the separable-to-4-D Hartley parity fix-up)
 //   inv 0, inv 1 inverse Hartley transform along axes 0 and 1 (step 5)
 //   slab23       inverse along axes 2 and 3, with the moment sums of the result
-//   finalize     normaliser and moments (float64, step 6)
+//   finalize     normaliser and moments (double-float sums, float64 frame; step 6)
 // Per measurement update (eq. filt): exponent parts and their minimum, then
 // the likelihood multiply with the moment sums, then the finalisation.
 #include <cmath>
 #include <vector>
 
 #include "pmf_f4.cuh"
+#include "pmf_device.cuh"
 #include "pmf_grid.cuh"
 #include "pmf_kernels.cuh"
 #include "pmf_model.cuh"
@@ -190,8 +191,9 @@ struct Mom4 {
   }
 };
 
-// Block sum of the double-float moment sums into float64 partials.
-__device__ void mom4_block(Mom4& m, double* out) {
+// Block sum of the double-float moment sums into double-float partials
+// (float2 {hi, lo} per slot), summed again in double-float by k_f4_finalize.
+__device__ void mom4_block(Mom4& m, float2* out) {
   __shared__ DF red[32][kMomentSlots];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -205,10 +207,55 @@ __device__ void mom4_block(Mom4& m, double* out) {
     for (int i = 0; i < kMomentSlots; ++i) red[warp][i] = m.s[i];
   __syncthreads();
   if (warp == 0 && lane < kMomentSlots) {
-    double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += (double)red[w][lane].hi + (double)red[w][lane].lo;
-    out[lane] = t;
+    DF t = red[0][lane];
+    for (int w = 1; w < nw; ++w) t = df_add(t, red[w][lane]);
+    out[lane] = make_float2(t.hi, t.lo);
   }
+}
+
+// Normaliser and moments of the n_x = 4 weights from the blocks' double-float
+// partials: the cross-block sums stay in double-float (float32 arithmetic;
+// GB300 issues float64 at 1/64 of the float32 rate and this runs on one SM),
+// the 15 totals become float64, and warp 0 finalises (finalize_warp, one
+// matrix entry per lane) on a shared copy of the frame state.
+__global__ void __launch_bounds__(256) k_f4_finalize(DevState* st, const float2* partials, int nblocks, int flip,
+                                                     int use_pending, const double* pend) {
+  __shared__ DF red[8][kMomentSlots];
+  __shared__ double tot[kMomentSlots];
+  __shared__ FrameState fs;
+  constexpr int kWords = sizeof(FrameState) / 8;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  DF acc[kMomentSlots];
+#pragma unroll
+  for (int i = 0; i < kMomentSlots; ++i) acc[i] = DF{0.0f, 0.0f};
+  for (int b = tid; b < nblocks; b += 256)
+#pragma unroll
+    for (int i = 0; i < kMomentSlots; ++i) {
+      const float2 v = partials[b * kMomentSlots + i];
+      acc[i] = df_add(acc[i], DF{v.x, v.y});
+    }
+#pragma unroll
+  for (int i = 0; i < kMomentSlots; ++i)
+    for (int o = 16; o; o >>= 1) {
+      DF b{__shfl_xor_sync(0xffffffffu, acc[i].hi, o), __shfl_xor_sync(0xffffffffu, acc[i].lo, o)};
+      acc[i] = df_add(acc[i], b);
+    }
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < kMomentSlots; ++i) red[warp][i] = acc[i];
+  for (int i = tid; i < kWords; i += 256) ((unsigned long long*)&fs)[i] = ((const unsigned long long*)&st->f)[i];
+  __syncthreads();
+  if (warp == 0 && lane < kMomentSlots) {
+    DF t = red[0][lane];
+    for (int w = 1; w < 8; ++w) t = df_add(t, red[w][lane]);
+    tot[lane] = (double)t.hi + (double)t.lo;
+  }
+  __syncthreads();
+  if (warp != 0) return;
+  const bool ok = finalize_warp<4>(&fs, tot, use_pending, pend);
+  if (ok && lane == 0) fs.cur ^= flip;
+  __syncwarp();
+  for (int i = lane; i < kWords; i += 32) ((unsigned long long*)&st->f)[i] = ((const unsigned long long*)&fs)[i];
 }
 
 // Moment kernels: a block takes kLinesM lines along axis 3, four threads per
@@ -254,7 +301,7 @@ __global__ void __launch_bounds__(kMomThreads) k_f4_meas_apply(Dims d, DevState*
     line_u(d, ln, u);
     m.add_line(s0, s1, s2, u[0], u[1], u[2]);
   }
-  mom4_block(m, partials + blockIdx.x * kMomentSlots);
+  mom4_block(m, (float2*)partials + blockIdx.x * kMomentSlots);
 }
 
 // ---- time update ------------------------------------------------------------
@@ -561,7 +608,7 @@ __global__ void __launch_bounds__(kSlabThreads) k_f4_slab23(Dims d, const float*
       }
       m.add_line(a, b, c, (sg / N1) - 0.5f * (d.N[0] - 1), (sg % N1) - 0.5f * (N1 - 1), r - 0.5f * (N2 - 1));
     }
-    mom4_block(m, partials + blockIdx.x * kMomentSlots);
+    mom4_block(m, (float2*)partials + blockIdx.x * kMomentSlots);
   }
 }
 
@@ -771,7 +818,7 @@ int f4_meas(const Dims& d, const MeasParams& mp, DevState* st, const F4Tables& t
   k_f4_meas_e<<<d.N[0] * d.N[1], 256, 0, s>>>(d, mp, st, t.mtab, t.lo, t.gap);
   const int nb = (int)((d.P / d.N[3] + kLinesM - 1) / kLinesM);
   k_f4_meas_apply<<<nb, kMomThreads, 0, s>>>(d, st, t.lo, t.gap, b0, b1, partials);
-  launch_finalize(d, st, partials, nb, 1, 0, nullptr, s);
+  k_f4_finalize<<<1, 256, 0, s>>>(st, (const float2*)partials, nb, 1, 0, nullptr);
   return n;
 }
 
@@ -800,7 +847,7 @@ int f4_time(const Dims& d, const TimeConsts& tc, DevState* st, const F4Tables& t
   axis(0, t.winv[0]);
   axis(1, t.winv[1]);
   k_f4_slab23<true><<<nslab, kSlabThreads, ssm, s>>>(d, t.winv[3], t.winv[2], st, stage++, b0, b1, partials);
-  launch_finalize(d, st, partials, nslab, stage & 1, 1, pend, s);
+  k_f4_finalize<<<1, 256, 0, s>>>(st, (const float2*)partials, nslab, stage & 1, 1, pend);
   return 1 + 1 + 1 + 6 + 1 + 1;
 }
 

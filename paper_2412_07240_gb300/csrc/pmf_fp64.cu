@@ -102,13 +102,18 @@ __global__ void k_finalize(Dims d, DevState* st, const double* partials, int nbl
 // Regrid decision (warp 0, lane-parallel, on a shared copy of the frame
 // state) and the diffusion coefficients of every sub-step (one thread each)
 // of one time update.
+// The constants are staged in shared memory first: the lanes read different
+// entries, which the parameter (constant) bank would serialise.
 template <int n>
-__device__ void frame_body(const TimeConsts& tc, DevState* st, double* pend) {
+__device__ void frame_body(const TimeConsts& tcp, DevState* st, double* pend) {
   __shared__ FrameState fs;
   __shared__ double Mpi[16];
-  constexpr int kWords = sizeof(FrameState) / 8;
+  __shared__ TimeConsts tc;
+  constexpr int kWords = sizeof(FrameState) / 8, kTcWords = sizeof(TimeConsts) / 8;
   for (int i = threadIdx.x; i < kWords; i += blockDim.x)
     ((unsigned long long*)&fs)[i] = ((const unsigned long long*)&st->f)[i];
+  for (int i = threadIdx.x; i < kTcWords; i += blockDim.x)
+    ((unsigned long long*)&tc)[i] = ((const unsigned long long*)&tcp)[i];
   __syncthreads();
   if (threadIdx.x < 32) frame_warp<n>(tc, &fs, pend, Mpi);
   __syncthreads();
@@ -550,11 +555,6 @@ void launch_time_f64(const Dims& d, const TimeConsts& tc, DevState* st, double* 
 
 void launch_frame(const TimeConsts& tc, DevState* st, double* pend, cudaStream_t s) {
   k_frame<<<1, MAXL, 0, s>>>(tc, st, pend);
-}
-
-void launch_finalize(const Dims& d, DevState* st, const double* partials, int nblocks, int flip,
-                     int use_pending, const double* pend, cudaStream_t s) {
-  k_finalize<<<1, 256, 0, s>>>(d, st, partials, nblocks, flip, use_pending, pend);
 }
 
 void launch_export_f64(const Dims& d, const DevState* st, const double* b0, const double* b1,

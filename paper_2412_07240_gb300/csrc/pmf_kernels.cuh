@@ -22,11 +22,9 @@ void launch_time_f64(const Dims& d, const TimeConsts& tc, DevState* st, double* 
 void launch_export_f64(const Dims& d, const DevState* st, const double* b0, const double* b1,
                        double* out, cudaStream_t s);
 
-// Pieces shared with the float32 n_x = 4 path: the frame kernel (regrid
-// decision, sub-step coefficients) and the moment finalisation.
+// Shared with the float32 n_x = 4 path: the frame kernel (regrid decision,
+// sub-step coefficients).
 void launch_frame(const TimeConsts& tc, DevState* st, double* pend, cudaStream_t s);
-void launch_finalize(const Dims& d, DevState* st, const double* partials, int nblocks, int flip,
-                     int use_pending, const double* pend, cudaStream_t s);
 
 // Launch counts of the launchers above (per call).
 constexpr int kLaunchesMeasF64 = 3;   // emin, apply, finalize (+1 memset)
