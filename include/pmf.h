@@ -340,7 +340,7 @@ void pmf_server_destroy(pmf_server* s);
  *   stream  : cudaStream_t as void* (NULL = legacy default stream)
  *
  * It calls no allocating routine.  Its block partial sums live in one fixed
- * device array of PMF_NOALLOC_MAX_POINTS / 256 * 10 float64 (320 KiB) that
+ * device array of PMF_NOALLOC_MAX_POINTS / 256 * 15 float64 (480 KiB) that
  * every GPU which loads the library holds until the process exits.  The first
  * call on a device looks up that array's device address (once per device, with
  * the device current); make that first call before any stream capture.  All
@@ -352,6 +352,20 @@ void pmf_server_destroy(pmf_server* s);
 #define PMF_NOALLOC_MAX_POINTS (1 << 20)
 int pmf_moments_noalloc(const double* weights, int nx, const int* N, const double* c,
                         const double* M, double* out, void* cuda_stream);
+
+/* Self-test of the bounded device waits (no counterpart in the paper).  Every
+ * wait of the tensor-core kernels on an mbarrier (bulk copies, MMA completion)
+ * polls at most a fixed number of times and then records PMF_ERR_TIMEOUT in
+ * the filter's status and returns, so a lost completion ends the kernel with
+ * an error the host reads instead of a hung GPU.  This call runs that wait in
+ * a one-warp kernel on a barrier that expects one arrival:
+ *   arrive = 1 : the arrival happens before the wait; expected PMF_OK.
+ *   arrive = 0 : nothing arrives; the wait gives up after `polls` polls
+ *                (>= 1) and the call returns PMF_ERR_TIMEOUT.
+ * Synchronous on `cuda_stream` (NULL = legacy default stream); PMF_ERR_ARG
+ * for polls < 1, PMF_ERR_CUDA if the launch or the synchronisation fails (the
+ * context stays usable after a timeout). */
+int pmf_selftest_bounded_wait(long long polls, int arrive, void* cuda_stream);
 
 #ifdef __cplusplus
 }

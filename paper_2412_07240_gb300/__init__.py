@@ -6,5 +6,5 @@ is a thin ctypes binding with the same entry points.
 """
 from ._binding import (  # noqa: F401
     Batch, Degenerate, Filter, PmfError, Server, Unsupported, fdm_transition, load, lib_path, make_config,
-    make_meas,
+    make_meas, selftest_bounded_wait,
 )

@@ -100,6 +100,7 @@ SIGNATURES = [
     ("pmf_server_destroy", None, [C.c_void_p]),
     ("pmf_moments_noalloc", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.c_void_p, C.c_void_p]),
+    ("pmf_selftest_bounded_wait", C.c_int, [C.c_longlong, C.c_int, C.c_void_p]),
 ]
 SERVE_NSTATS = 6
 
@@ -203,6 +204,12 @@ def moments_noalloc(weights, N, c, M, out, stream=None) -> None:
                                  C.c_void_p(int(out.data_ptr())), _stream_handle(stream))
     if rc != OK:
         raise PmfError(rc, "pmf_moments_noalloc failed")
+
+
+def selftest_bounded_wait(polls: int, arrive: bool, stream=None) -> int:
+    """pmf_selftest_bounded_wait: the return code of a bounded mbarrier wait
+    (OK when the arrival happened, ERR_TIMEOUT when it gave up)."""
+    return int(load().pmf_selftest_bounded_wait(int(polls), 1 if arrive else 0, _stream_handle(stream)))
 
 
 class Filter:

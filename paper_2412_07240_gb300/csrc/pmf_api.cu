@@ -381,6 +381,11 @@ int pmf_get_pdf(pmf_ctx* ctx, double* host_out, double* c_out, double* M_out) {
   return PMF_OK;
 }
 
+int pmf_selftest_bounded_wait(long long polls, int arrive, void* cuda_stream) {
+  if (polls < 1) return PMF_ERR_ARG;
+  return tc_wait_probe(polls, arrive ? 1 : 0, (cudaStream_t)cuda_stream);
+}
+
 long long pmf_num_points(const pmf_ctx* ctx) { return ctx ? ctx->dims.P : 0; }
 int pmf_path(const pmf_ctx* ctx) { return ctx ? ctx->path : -1; }
 long long pmf_launch_count(const pmf_ctx* ctx) { return ctx ? ctx->launches : 0; }

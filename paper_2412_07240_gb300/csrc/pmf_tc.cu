@@ -954,6 +954,34 @@ void tc_free_tables(TcTables* t) {
   }
 }
 
+// One warp waits (bounded) on a shared-memory mbarrier expecting one arrival;
+// with arrive the arrival precedes the wait.  out: PMF_OK or PMF_ERR_TIMEOUT.
+__global__ void k_wait_probe(long long polls, int arrive, int* out) {
+  __shared__ uint64_t bar;
+  const uint32_t mb = su32(&bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncwarp();
+  if (arrive && threadIdx.x == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb) : "memory");
+  __syncwarp();
+  const bool ok = mbar_wait(mb, 0, polls);
+  if (threadIdx.x == 0) *out = ok ? PMF_OK : PMF_ERR_TIMEOUT;
+}
+
+int tc_wait_probe(long long polls, int arrive, cudaStream_t s) {
+  int* d = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return PMF_ERR_CUDA;
+  int h = -1;
+  k_wait_probe<<<1, 32, 0, s>>>(polls, arrive, d);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  return e == cudaSuccess ? h : PMF_ERR_CUDA;
+}
+
 int tc_prior(const Dims& d, DevState* st, const double* prior_aux, float* X, double* partials,
              cudaStream_t s) {
   long long blocks = (d.P + 255) / 256;

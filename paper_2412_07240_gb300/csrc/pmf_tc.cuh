@@ -53,6 +53,8 @@ int tc_build_tables(const pmf_config* cfg, TcTables* t, std::string* why);
 int tc_build_axis_table(int N, int precision, void** dev, size_t* hart_bytes);
 size_t tc_axis_table_bytes(int N, int precision);
 void tc_free_tables(TcTables* t);
+// Bounded mbarrier wait in a one-warp kernel (see pmf_selftest_bounded_wait).
+int tc_wait_probe(long long polls, int arrive, cudaStream_t s);
 // Prior weights and their moments; returns the number of kernel launches.
 int tc_prior(const Dims& d, DevState* st, const double* prior_aux, float* X, double* partials,
              cudaStream_t s);

@@ -46,9 +46,9 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, long long polls = kSpin) {
   uint32_t done = 0;
-  for (long long it = 0; it < kSpin; ++it) {
+  for (long long it = 0; it < polls; ++it) {
     asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                  "selp.u32 %0, 1, 0, p;\n}"
                  : "=r"(done) : "r"(mbar), "r"(phase));
