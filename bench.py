@@ -156,6 +156,10 @@ def _launch_names(sc):
 # DRAM bytes (read + write) per launch of the timed kernel, from one ncu capture
 # of the current kernel (profiles/): the 128 x 128 fused kernel, and the batch
 # kernel per grid point (captured on 2048 filters, scaled by the points).
+# Bytes a served request uploads: its StepItem (slot, flags, z[3]) and the
+# TimeConsts of its time update (32 + 5 x 16 x 8 + 64 x 10 x 8 + 5 x 8 bytes).
+STEP_ITEM_BYTES = 32
+TIME_CONSTS_BYTES = 5832
 TRAFFIC_C2 = 346880.0
 TRAFFIC_C4_PER_POINT = (59654912.0 + 9783296.0) / 10976512.0
 
@@ -245,9 +249,98 @@ print(json.dumps({{"seconds": dt, "epochs": {epochs}}}))
     return res
 
 
+def _oracle_proc(code, timeout=900):
+    """Run oracle code in a single-threaded subprocess; its last stdout line is JSON."""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=timeout)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr)
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_c4_sample(count, epochs=8, nsample=128):
+    """The float64 oracle on `nsample` filters spread over the batch (all sizes),
+    `epochs` epochs each, single thread: grid-point updates and seconds."""
+    code = f"""
+import json, sys, time
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+import workloads as w
+from oracle.filter import OracleFilter
+cfgs, meas, dt, truth, z = w.c4_batch(count={count}, epochs={epochs})
+idx = np.linspace(0, len(cfgs) - 1, {nsample}).astype(int)
+pts, sec = 0, 0.0
+for i in idx:
+    f = OracleFilter(cfgs[i])
+    t = time.perf_counter()
+    for k in range({epochs}):
+        f.meas_update(meas, z[i, k])
+        f.time_update(dt)
+    sec += time.perf_counter() - t
+    pts += int(np.prod(cfgs[i].N)) * {epochs}
+print(json.dumps({{"seconds": sec, "points": pts, "filters": len(idx), "epochs": {epochs}}}))
+"""
+    return _oracle_proc(code)
+
+
+def oracle_c5_sample(n_filters, per_dim=(30, 20, 5), reqs=5):
+    """The float64 oracle on the first requests of a few serving filters of each
+    dimension (same filter population as the served one), single thread."""
+    code = f"""
+import json, sys, time
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+import workloads as w
+from oracle.filter import OracleFilter
+wl = w.c5_serving(n_filters={n_filters}, duration=0.3, seed=5)
+pts, sec, used = 0, 0.0, []
+for d, want in zip((1, 2, 3), {per_dim!r}):
+    got = 0
+    for i, c in enumerate(wl.cfgs):
+        if c.nx != d or got == want:
+            continue
+        r = np.nonzero(wl.ids == i)[0][:{reqs}]
+        if len(r) < {reqs}:
+            continue
+        f = OracleFilter(c)
+        t = time.perf_counter()
+        for q in r:
+            f.meas_update(wl.meas[i], wl.z[q, :d])
+            f.time_update(min(float(wl.taus[q]), 0.6))
+        sec += time.perf_counter() - t
+        pts += int(np.prod(c.N)) * len(r)
+        got += 1
+    used.append(got)
+print(json.dumps({{"seconds": sec, "points": pts, "filters": used, "requests_each": {reqs}}}))
+"""
+    return _oracle_proc(code)
+
+
 def run_reference(args, ws, rank, pg):
     """The oracle arm: float64 oracle on the host cores, bounded sample per step."""
     if rank != 0:
+        return
+    if args.workload in ("c4", "c5"):
+        if args.workload == "c4":
+            t = oracle_c4_sample(args.count)
+            name, sample = f"c4_batch_{args.count}x2d_mixed", (f"{t['filters']} filters spread over the batch, "
+                                                                f"{t['epochs']} epochs each, single thread")
+        else:
+            n = args.count if args.count != 4096 else 10000
+            t = oracle_c5_sample(n)
+            name, sample = f"c5_serving_{n}_mixed", (f"first {t['requests_each']} requests of "
+                                                     f"{t['filters']} 1-D/2-D/3-D filters, single thread")
+        value = t["points"] / t["seconds"]
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded filters and measurements)",
+                "config": {"workload": name, "parallelism": "replicas"},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
         return
     sc = _scenario(args.workload, args.warmup + args.steps)
     P = 1
@@ -342,6 +435,11 @@ def bench_batch(args, ws, rank, pg):
                          "traffic": TRAFFIC_C4_PER_POINT * float(P.sum()),
                          "kernel": "k_fused2d_batch", "flops_per_launch": flops},
             "clocks": clk.summary()}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        t = oracle_c4_sample(len(cfgs))
+        line["cpu_baseline"] = {"value": t["points"] / t["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{t['filters']} filters spread over the batch, {t['epochs']} epochs "
+                                          "each, single thread"}
     if rank == 0:
         print(json.dumps(line))
 
@@ -392,6 +490,12 @@ def bench_serve(args, ws, rank, pg):
             f64_s += e0.elapsed_time(e1) * 1e-3
             f.close()
     nreq = int(st["requests"])
+    # algorithmic transform flops of the served requests: forward + inverse per axis
+    served = wl.ids[sel]
+    per_filter = np.array([4.0 * np.prod(c.N) * sum(c.N) for c in wl.cfgs])
+    flops = float(per_filter[served].sum())
+    peaks, peak_src = _peaks()
+    peak = peaks.get("bf16_tflops", 1900.0)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": int(st["batches"]),
             "warmup": k, "ms_per_step": wall * 1e3 / max(1.0, st["batches"]), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": f"f32 ({args.precision} split GEMMs, 1-D float32)",
@@ -404,13 +508,23 @@ def bench_serve(args, ws, rank, pg):
             "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
                            "max": float(lat.max() * 1e3)},
             "batches": {"count": int(st["batches"]), "mean": st["mean_batch"], "max": int(st["max_batch"])},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(st["mean_batch"] * (32 + 3600)),
+            "e2e": {"value": value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(st["mean_batch"] * (STEP_ITEM_BYTES + TIME_CONSTS_BYTES)),
                     "d2h_bytes_per_step": 0, "note": "the replay is end to end: requests from host arrays"},
             "gpu_launches": int(st["launches"]),
             "fp64_gpu": {"value": f64_pts / f64_s if f64_s > 0 else None, "unit": UNIT,
                          "sample": "8 1-D, 8 2-D, 3 3-D filters, plain float64 path, one update each"},
-            "roofline": None,
+            "roofline": {"bound": "tensor", "achieved": flops / wall / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / wall / 1e12 / peak, "traffic": None,
+                         "kernel": "all serving launches (1-D CUDA-core, 2-D fused, 3-D pipelines)",
+                         "peak_source": f"bf16_tflops ({peak_src})",
+                         "flops": flops, "note": "algorithmic transform flops of the served requests / wall"},
             "clocks": clk.summary()}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        t = oracle_c5_sample(n)
+        line["cpu_baseline"] = {"value": t["points"] / t["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {t['requests_each']} requests of {t['filters']} 1-D/2-D/3-D "
+                                          "filters, single thread"}
     if rank == 0:
         print(json.dumps(line))
     srv.close()
