@@ -356,3 +356,32 @@ def test_frame_from_target_recovers_the_decision():
             b.time_update(sc.dt, got)
             np.testing.assert_array_equal(b.P, a.P)
         assert kinds == {True, False} or sc.cfg.nx == 4
+
+
+def test_4d_terrain_cycle_self_converges():
+    """The Sec. VI terrain measurement has no closed form (parity unpinned beyond
+    this): unit mass and PSD covariance after every update, the moments of the
+    first update converge spectrally in N, and later ones (multilinear
+    re-alignment in between) at least halve their distance to N = 32 from
+    N = 16 to N = 24."""
+    res = {}
+    for N in (16, 24, 32):
+        sc = w.c6_scenario(N=N, epochs=2, local=True)
+        f = of.OracleFilter(sc.cfg)
+        out = []
+        for k in range(sc.epochs):
+            f.meas_update(sc.meas, sc.z[k])
+            assert abs(f.cell_volume * f.P.sum() - 1.0) < 1e-12
+            m, C = f.moments()
+            assert np.all(np.linalg.eigvalsh(C) > 0)
+            out.append((m, C))
+            f.time_update(sc.dt)
+        res[N] = out
+    for k in range(2):
+        (m16, _), (m24, _), (m32, C32) = res[16][k], res[24][k], res[32][k]
+        s = np.sqrt(np.diag(C32)).max()
+        e16, e24 = np.abs(m16 - m32).max() / s, np.abs(m24 - m32).max() / s
+        if k == 0:
+            assert e24 < 1e-4 and e24 < e16 / 50, (e16, e24)
+        else:
+            assert e24 < e16 / 2, (e16, e24)
