@@ -723,8 +723,8 @@ def main():
                      "flops_per_launch": flops},
         "clocks": clk.summary(),
     }
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline and sc.cfg.nx == 2:
-        epochs = 60
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and sc.cfg.nx in (2, 3):
+        epochs = 60 if sc.cfg.nx == 2 else 10
         t = oracle_sample(args.workload, epochs)
         per = t["seconds"] / t["epochs"]
         # parity of the sample: same epochs on the GPU path from the prior
