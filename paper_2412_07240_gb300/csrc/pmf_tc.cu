@@ -660,6 +660,19 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         break;
       }
       tc_after_sync();
+      // matrix of the next GEMM: F1 <- H1, R0 <- I0 (built below), F0 <- H0,
+      // V0 keeps H0, V1 <- H1.  The MMA that read W has completed, and the
+      // epilogue does not touch W, so the copy runs behind the epilogue.
+      int mat = -1;
+      if (stage == 0 || stage == 4) mat = 1;
+      if (stage == 2) mat = 0;
+      if (tid == 0 && mat >= 0) {
+        const int Nm = mat == 0 ? N0 : N1;
+        const uint32_t pbytes = (uint32_t)Nm * (uint32_t)(Fmt<P>::rowblk / 8);
+        expect_tx(mb_tma, pbytes * Fmt<P>::planes);
+        for (int pl = 0; pl < Fmt<P>::planes; ++pl)
+          bulk_load(su32(W) + pl * kPlane, job.hart[mat] + (size_t)pl * pbytes, pbytes, mb_tma);
+      }
       // accumulator of GEMM `stage`: valid lanes and columns
       const int nlane = (stage == 0 || stage == 1 || stage == 5) ? N0 : N1;
       const int nout = (stage <= 1 || stage == 5) ? N1 : N0;
@@ -721,10 +734,6 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
           }
         tc_before_sync();
       }
-      // matrix of the next GEMM: F1 <- H1, R0 <- I0, F0 <- H0, V0 keeps H0, V1 <- H1
-      int mat = -1;
-      if (stage == 0 || stage == 4) mat = 1;
-      if (stage == 2) mat = 0;
       if (stage == 1) {
         __syncthreads();
         if constexpr (kOut) build_interp_out<P>(sh.rows[0], W, N0, sh.sct[0], sw, realign, tid, kThreads);
@@ -735,14 +744,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       if (tid == 0) {
         tc_after_sync();
         bool ok2 = true;
-        if (mat >= 0) {
-          const int Nm = mat == 0 ? N0 : N1;
-          const uint32_t pbytes = (uint32_t)Nm * (uint32_t)(Fmt<P>::rowblk / 8);
-          expect_tx(mb_tma, pbytes * Fmt<P>::planes);
-          for (int pl = 0; pl < Fmt<P>::planes; ++pl)
-            bulk_load(su32(W) + pl * kPlane, job.hart[mat] + (size_t)pl * pbytes, pbytes, mb_tma);
-          ok2 = mbar_wait(mb_tma, ph_tma);
-        }
+        if (mat >= 0) ok2 = mbar_wait(mb_tma, ph_tma);
         if (!ok2) {
           sh.abort = 1;
         } else {
