@@ -1,5 +1,6 @@
-// Device functions shared by the float64 kernels and the fused tensor-core
-// kernel: regrid/frame computation and moment finalisation (float64, one thread).
+// Device functions shared by the float64 kernels and the tensor-core and
+// float32 kernels: regrid/frame decision, sub-step diffusion coefficients and
+// moment finalisation (float64, in the lanes of one warp).
 #pragma once
 
 #include "pmf_internal.cuh"
@@ -8,10 +9,9 @@ namespace pmf {
 
 
 // ---------------------------------------------------------------------------
-// Fixed-size float64 helpers (n <= 3, fully unrolled, registers only).  On
-// GB300 a dependent float64 FMA costs ~64 cycles and a division ~430, so the
-// per-epoch frame work avoids loops over local arrays and uses one reciprocal
-// per inverse.
+// Fixed-size float64 helpers (fully unrolled, registers only).  On GB300 a
+// dependent float64 FMA costs ~64 cycles and a division ~430, so the per-epoch
+// frame work avoids loops over local arrays and divides once per inverse.
 // ---------------------------------------------------------------------------
 template <int n>
 __device__ __forceinline__ void mm_t(const double* A, const double* B, double* C) {
@@ -52,174 +52,6 @@ __device__ __forceinline__ double det_t(const double* A) {
          A[2] * (A[3] * A[7] - A[4] * A[6]);
 }
 
-// Inverse by the adjugate and one reciprocal of the determinant.
-template <int n>
-__device__ __forceinline__ void inv_t(const double* A, double* Ai) {
-  if (n == 4) {
-    inv(4, A, Ai);
-    return;
-  }
-  const double r = 1.0 / det_t<n>(A);
-  if (n == 1) {
-    Ai[0] = r;
-  } else if (n == 2) {
-    Ai[0] = A[3] * r;
-    Ai[1] = -A[1] * r;
-    Ai[2] = -A[2] * r;
-    Ai[3] = A[0] * r;
-  } else {
-    Ai[0] = (A[4] * A[8] - A[5] * A[7]) * r;
-    Ai[1] = (A[2] * A[7] - A[1] * A[8]) * r;
-    Ai[2] = (A[1] * A[5] - A[2] * A[4]) * r;
-    Ai[3] = (A[5] * A[6] - A[3] * A[8]) * r;
-    Ai[4] = (A[0] * A[8] - A[2] * A[6]) * r;
-    Ai[5] = (A[2] * A[3] - A[0] * A[5]) * r;
-    Ai[6] = (A[3] * A[7] - A[4] * A[6]) * r;
-    Ai[7] = (A[1] * A[6] - A[0] * A[7]) * r;
-    Ai[8] = (A[0] * A[4] - A[1] * A[3]) * r;
-  }
-}
-
-template <int n>
-__device__ __forceinline__ bool chol_t(const double* A, double* L) {
-#pragma unroll
-  for (int i = 0; i < n * n; ++i) L[i] = 0.0;
-#pragma unroll
-  for (int j = 0; j < n; ++j) {
-    double s = A[j * n + j];
-#pragma unroll
-    for (int k = 0; k < j; ++k) s -= L[j * n + k] * L[j * n + k];
-    if (!(s > 0.0)) return false;
-    const double d = sqrt(s), rd = 1.0 / d;
-    L[j * n + j] = d;
-#pragma unroll
-    for (int i = j + 1; i < n; ++i) {
-      double t = A[i * n + j];
-#pragma unroll
-      for (int k = 0; k < j; ++k) t -= L[i * n + k] * L[j * n + k];
-      L[i * n + j] = t * rd;
-    }
-  }
-  return true;
-}
-
-// Regrid decision of one time update (float64, one thread).  From the current
-// moments and frame: the pulled-back predicted covariance
-// e^{-A tau} P_pred e^{-A^T tau} = cov + Q_b, its whitened correlation in the
-// frame, and either the separable rescale/recentre (M' = M D, c' = the mean,
-// both quantised as described below) or a
-// re-aligned frame M' = e^{-A tau} chol(P_pred) diag(2 span / N).  Writes the
-// regrid map into st, the inverse of M' into Mpi and the pending frame after
-// the move by e^{A tau} into pend = {c[3], M[9], Minv[9], V}.
-template <int n>
-__device__ inline void frame_scalar(const TimeConsts& tc, FrameState* st, double* pend, double* Mpi) {
-  double S[n * n], Su[n * n], Minv[n * n], M[n * n], Mp[n * n];
-#pragma unroll
-  for (int i = 0; i < n * n; ++i) {
-    S[i] = st->cov[i] + tc.Qb[i];
-    Minv[i] = st->Minv[i];
-    M[i] = st->M[i];
-  }
-  cong_t<n>(Minv, S, Su);
-  double sd[n];
-#pragma unroll
-  for (int a = 0; a < n; ++a) sd[a] = sqrt(fmax(Su[a * n + a], 0.0));
-  int realign = 0;
-  if (n >= 2) {
-    // max |rho_ab| > rho_max  <=>  Su_ab^2 > rho_max^2 Su_aa Su_bb (no division)
-    const double r2 = tc.rho_max * tc.rho_max;
-#pragma unroll
-    for (int a = 0; a < n; ++a)
-#pragma unroll
-      for (int b = a + 1; b < n; ++b)
-        if (Su[a * n + b] * Su[a * n + b] > r2 * Su[a * n + a] * Su[b * n + b]) realign = 1;
-  }
-  if (realign) {
-    double Pp[n * n], L[n * n], T[n * n];
-    cong_t<n>(tc.Phi, S, Pp);
-    if (chol_t<n>(Pp, L)) {
-      mm_t<n>(tc.PhiInv, L, T);
-#pragma unroll
-      for (int a = 0; a < n; ++a)
-#pragma unroll
-        for (int b = 0; b < n; ++b) {
-          // axis entries rounded to a 12-bit mantissa
-          int e;
-          const double f = frexp(T[a * n + b] * (2.0 * tc.span / tc.N[b]), &e);
-          Mp[a * n + b] = ldexp(rint(ldexp(f, 12)), e - 12);
-        }
-    } else {
-      realign = 0;
-    }
-  }
-  double dm[n];
-#pragma unroll
-  for (int a = 0; a < n; ++a) {
-    double s = 0.0;
-#pragma unroll
-    for (int b = 0; b < n; ++b) s = fma(Minv[a * n + b], st->mean[b] - st->c[b], s);
-    dm[a] = s;
-  }
-  double cnew[n];   // centre of the new frame
-  // the centre moves by a multiple of 1/64 node (in the old frame) towards the mean
-#pragma unroll
-  for (int a = 0; a < n; ++a) dm[a] = rint(dm[a] * 64.0) * (1.0 / 64.0);
-#pragma unroll
-  for (int a = 0; a < n; ++a) {
-    double s = st->c[a];
-#pragma unroll
-    for (int b = 0; b < n; ++b) s = fma(M[a * n + b], dm[b], s);
-    cnew[a] = s;
-  }
-  if (realign) {
-    double B[n * n];
-    mm_t<n>(Minv, Mp, B);
-#pragma unroll
-    for (int i = 0; i < n * n; ++i) st->B[i] = B[i];
-#pragma unroll
-    for (int a = 0; a < n; ++a) st->b[a] = dm[a];
-    inv_t<n>(Mp, Mpi);
-  } else {
-    // quantised separable regrid: scale by a factor with an 8-bit mantissa (with
-    // the 1/64-node shift the grid geometry is exact in any precision and does
-    // not random-walk with the rounding of the moments)
-#pragma unroll
-    for (int a = 0; a < n; ++a) {
-      int e;
-      const double f = frexp(2.0 * tc.span * sd[a] / tc.N[a], &e);
-      const double D = ldexp(rint(ldexp(f, 8)), e - 8);
-      const double rD = 1.0 / D;
-#pragma unroll
-      for (int r = 0; r < n; ++r) {
-        Mp[r * n + a] = M[r * n + a] * D;
-        Mpi[a * n + r] = Minv[a * n + r] * rD;   // (M D)^{-1} = D^{-1} M^{-1}
-      }
-      st->rs[a] = dm[a];
-      st->rd[a] = D;
-    }
-  }
-  st->realign = realign;
-  st->exact = tc.exact;
-  st->l = tc.exact ? 1 : tc.l;
-  st->g = tc.g;
-  double nM[n * n], nMi[n * n];
-  mm_t<n>(tc.Phi, Mp, nM);
-  mm_t<n>(Mpi, tc.PhiInv, nMi);
-#pragma unroll
-  for (int a = 0; a < n; ++a) {
-    double s = 0.0;
-#pragma unroll
-    for (int b = 0; b < n; ++b) s = fma(tc.Phi[a * n + b], cnew[b], s);
-    pend[a] = s;
-  }
-#pragma unroll
-  for (int i = 0; i < n * n; ++i) {
-    pend[pend_M(n) + i] = nM[i];
-    pend[pend_Mi(n) + i] = nMi[i];
-  }
-  pend[pend_V(n)] = fabs(det_t<n>(nM));
-}
-
 // Diffusion coefficients of sub-step q in the new frame (any thread):
 // Q_u(t_q) = M'^{-1} Qt_q M'^{-T}, Qt_q = e^{-A q dt} Q e^{-A^T q dt} (host),
 // pa = dt/2 Q_u,aa and pb = dt Q_u,ab (01, 02, 12); for the exact multiplier
@@ -244,112 +76,13 @@ __device__ inline void frame_substep(const TimeConsts& tc, const double* Mpi, in
   for (int k = 0; k < 6; ++k) pb[k] = pj[k] < n ? w * Qu[(pj[k] < n ? pi[k] * n + pj[k] : 0)] : 0.0;
 }
 
-// Finalise moments from the sums tot (frame coordinates u; layout of tot_S2)
-// and set the normaliser pscale = 1 / (V S0).  With use_pending the weights are
-// on the pending (advanced) frame pend = {c, M, Minv, V} (offsets pend_*), which
-// is committed.  Returns false (status DEGENERATE, state untouched) if S0 is not
-// positive and finite.
-__device__ inline bool finalize_core(int nx, FrameState* st, const double* tot, int use_pending,
-                                     const double* pend) {
-  const int n = nx;
-  const double S0 = tot[0];
-  if (!(S0 > 0.0) || !isfinite(S0)) {
-    st->status = PMF_ERR_DEGENERATE;
-    return false;
-  }
-  double c[4], M[16], Minv[16], V;
-  if (use_pending) {
-    for (int i = 0; i < n; ++i) c[i] = pend[i];
-    for (int i = 0; i < n * n; ++i) { M[i] = pend[pend_M(n) + i]; Minv[i] = pend[pend_Mi(n) + i]; }
-    V = pend[pend_V(n)];
-  } else {
-    for (int i = 0; i < n; ++i) c[i] = st->c[i];
-    for (int i = 0; i < n * n; ++i) { M[i] = st->M[i]; Minv[i] = st->Minv[i]; }
-    V = st->V;
-  }
-  double mu[4], Cu[16];
-  for (int a = 0; a < n; ++a) mu[a] = tot[1 + a] / S0;
-  for (int a = 0; a < n; ++a)
-    for (int b = 0; b < n; ++b) Cu[a * n + b] = tot[tot_S2(n, a, b)] / S0 - mu[a] * mu[b];
-  double cov[16];
-  congruence(n, M, Cu, cov);
-  for (int a = 0; a < n; ++a) {
-    double m = c[a];
-    for (int b = 0; b < n; ++b) m += M[a * n + b] * mu[b];
-    st->mean[a] = m;
-  }
-  for (int i = 0; i < n * n; ++i) st->cov[i] = cov[i];
-  if (use_pending) {
-    for (int i = 0; i < n; ++i) st->c[i] = c[i];
-    for (int i = 0; i < n * n; ++i) { st->M[i] = M[i]; st->Minv[i] = Minv[i]; }
-    st->V = V;
-  }
-  st->S0 = S0;
-  st->pscale = 1.0 / (V * S0);
-  return true;
-}
-
-// Fixed-size finalisation (n <= 3, registers, one reciprocal of S0): same
-// results as finalize_core.
-template <int n>
-__device__ inline bool finalize_t(FrameState* st, const double* tot, int use_pending, const double* pend) {
-  const double S0 = tot[0];
-  if (!(S0 > 0.0) || !isfinite(S0)) {
-    st->status = PMF_ERR_DEGENERATE;
-    return false;
-  }
-  double c[n], M[n * n], Minv[n * n], V;
-#pragma unroll
-  for (int i = 0; i < n; ++i) c[i] = use_pending ? pend[i] : st->c[i];
-#pragma unroll
-  for (int i = 0; i < n * n; ++i) {
-    M[i] = use_pending ? pend[3 + i] : st->M[i];
-    Minv[i] = use_pending ? pend[12 + i] : st->Minv[i];
-  }
-  V = use_pending ? pend[21] : st->V;
-  const double r = 1.0 / S0;
-  const int k2[3][3] = {{4, 5, 6}, {5, 7, 8}, {6, 8, 9}};
-  double mu[n], Cu[n * n], cov[n * n];
-#pragma unroll
-  for (int a = 0; a < n; ++a) mu[a] = tot[1 + a] * r;
-#pragma unroll
-  for (int a = 0; a < n; ++a)
-#pragma unroll
-    for (int b = 0; b < n; ++b) Cu[a * n + b] = fma(tot[k2[a][b]], r, -mu[a] * mu[b]);
-  cong_t<n>(M, Cu, cov);
-#pragma unroll
-  for (int a = 0; a < n; ++a) {
-    double m = c[a];
-#pragma unroll
-    for (int b = 0; b < n; ++b) m = fma(M[a * n + b], mu[b], m);
-    st->mean[a] = m;
-  }
-#pragma unroll
-  for (int i = 0; i < n * n; ++i) st->cov[i] = cov[i];
-  if (use_pending) {
-#pragma unroll
-    for (int i = 0; i < n; ++i) st->c[i] = c[i];
-#pragma unroll
-    for (int i = 0; i < n * n; ++i) {
-      st->M[i] = M[i];
-      st->Minv[i] = Minv[i];
-    }
-    st->V = V;
-  }
-  st->S0 = S0;
-  st->pscale = r / V;
-  return true;
-}
-
-
 // ---------------------------------------------------------------------------
-// Warp-parallel forms of frame_scalar and finalize_t: all 32 lanes of one warp
-// call them.  A float64 instruction costs GB300 ~64 cycles whatever the number
-// of active lanes (and independent instructions of one thread do not overlap),
-// so the entries of the small products run in parallel lanes: lane e < n*n of
-// each half-warp holds entry (e / n, e % n), lanes < n hold per-axis values.
-// Every entry is formed by the same operations in the same order as in the
-// one-thread forms.
+// Regrid decision and moment finalisation in warp lanes: all 32 lanes of one
+// warp call them.  A float64 instruction costs GB300 ~64 cycles whatever the
+// number of active lanes (and independent instructions of one thread do not
+// overlap), so the entries of the small products run in parallel lanes: lane
+// e < n*n (of each half-warp where both halves work) holds entry
+// (e / n, e % n), lanes < n hold per-axis values.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double lget(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
