@@ -74,3 +74,12 @@ def test_repeatable_bitwise():
         g.close()
     assert np.array_equal(outs[0][0], outs[1][0])
     assert np.array_equal(outs[0][1], outs[1][1]) and np.array_equal(outs[0][2], outs[1][2])
+
+
+@pytest.mark.parametrize("prec,bar", [("bf16x3", 1e-4), ("tf32", 3e-2)])
+def test_small_3d_bearing_other_precisions(prec, bar):
+    """The 3-D pipelines in the other operand formats (bars as for 2-D: BF16X3
+    keeps ~16 bits of each operand, TF32 ~11)."""
+    worst, _ = max_errors(w.small_3d_scenario(N=(16, 32, 48), epochs=3), precision=prec)
+    assert worst["l1"] <= bar, worst
+    assert worst["mean"] <= bar, worst
