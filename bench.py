@@ -172,11 +172,22 @@ def _flops_per_step(N):
     return 4.0 * P * sum(N)
 
 
+# Method variants of the single-filter workloads (--psi, --realign): the
+# diffusion multiplier (Euler product or exact-in-time) and the fill of a
+# re-aligned frame (multilinear or band-limited shear passes, n_x = 2).
+MODES = {"psi": "euler", "realign": "multilinear"}
+
+
+def _apply_modes(sc):
+    sc.cfg.realign_mode = MODES["realign"]
+    return sc
+
+
 def time_gpu(sc, precision, steps, warmup, flush_mb=512):
     """Device time of `steps` epochs (CUDA events around each pmf_step, L2 flushed between)."""
     import torch
     from paper_2412_07240_gb300 import Filter
-    f = Filter(sc.cfg, precision=precision)
+    f = Filter(sc.cfg, precision=precision, psi_mode=MODES["psi"])
     assert len(sc.z) >= warmup + steps
     flush = torch.empty(flush_mb * (1 << 20) // 4, dtype=torch.float32, device="cuda")
     K = len(sc.z)
@@ -201,7 +212,7 @@ def time_e2e(sc, precision, steps):
     """Wall time of steps through the public API: measurement from host, moments read back."""
     import torch
     from paper_2412_07240_gb300 import Filter
-    f = Filter(sc.cfg, precision=precision)
+    f = Filter(sc.cfg, precision=precision, psi_mode=MODES["psi"])
     for k in range(3):
         f.step(sc.meas, sc.z[k], sc.dt)
         f.moments()
@@ -227,7 +238,8 @@ import numpy as np
 import workloads as w
 from oracle.filter import OracleFilter
 sc = {_scenario_expr(name, epochs)}
-f = OracleFilter(sc.cfg)
+sc.cfg.realign_mode = {MODES["realign"]!r}
+f = OracleFilter(sc.cfg, psi_mode={MODES["psi"]!r})
 t = time.perf_counter()
 for k in range({epochs}):
     f.meas_update(sc.meas, sc.z[k])
@@ -342,7 +354,7 @@ def run_reference(args, ws, rank, pg):
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
-    sc = _scenario(args.workload, args.warmup + args.steps)
+    sc = _apply_modes(_scenario(args.workload, args.warmup + args.steps))
     P = 1
     for n in sc.cfg.N:
         P *= n
@@ -560,7 +572,7 @@ def bench_4d(args, ws, rank, pg, local):
     se, var, used, lost = np.zeros(4), np.zeros(4), 0, 0
     for m in range(rank, M, ws):
         run = w.c6_scenario(seed=100 + m, epochs=T + 1)
-        g = Filter(run.cfg, precision=prec)
+        g = Filter(run.cfg, precision=prec, psi_mode=MODES["psi"])
         try:
             for k in range(T + 1):
                 g.meas_update(run.meas, run.z[k])
@@ -624,8 +636,8 @@ def bench_4d(args, ws, rank, pg, local):
         # parity of a sample: the oracle follows the kernels' regrid decisions
         # (on their quantisation lattices) and compares weights after each update
         from oracle.filter import OracleFilter
-        g = Filter(sc.cfg, precision=prec)
-        o = OracleFilter(sc.cfg)
+        g = Filter(sc.cfg, precision=prec, psi_mode=MODES["psi"])
+        o = OracleFilter(sc.cfg, psi_mode=MODES["psi"])
         worst = 0.0
         for k in range(epochs):
             g.meas_update(sc.meas, sc.z[k])
@@ -655,8 +667,13 @@ def main():
     ap.add_argument("--rate", type=float, default=200e3, help="c5: aggregate request rate per second")
     ap.add_argument("--duration", type=float, default=60.0, help="c5: seconds of requests replayed")
     ap.add_argument("--mc", type=int, default=50, help="c6: Monte Carlo runs for RMSE/ASTD")
+    ap.add_argument("--psi", default="euler", choices=["euler", "exact"],
+                    help="c2/c3/c6: diffusion multiplier (Euler product or exact in time)")
+    ap.add_argument("--realign", default="multilinear", choices=["multilinear", "shear"],
+                    help="c2: fill of a re-aligned frame (shear: band-limited, n_x = 2)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    MODES["psi"], MODES["realign"] = args.psi, args.realign
     ws, rank, local, pg = _dist()
     if args.impl == "reference":
         run_reference(args, ws, rank, pg)
@@ -673,7 +690,7 @@ def main():
         if pg is not None:
             pg.destroy_process_group()
         return
-    sc = _scenario(args.workload, args.warmup + args.steps + 1)
+    sc = _apply_modes(_scenario(args.workload, args.warmup + args.steps + 1))
     P = 1
     for n in sc.cfg.N:
         P *= n
@@ -708,6 +725,7 @@ def main():
         if args.precision == "fp16x3" else args.precision,
         "data": "synthetic (seeded truth and measurements)",
         "config": {"workload": sc.name, "grid": list(sc.cfg.N), "precision": args.precision,
+                   "psi": MODES["psi"], "realign": MODES["realign"],
                    "step": "one epoch: Bayes measurement update + spectral time update",
                    "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{ws}"},
         "e2e": {"value": ws * P / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": meas_bytes,
@@ -728,7 +746,7 @@ def main():
         t = oracle_sample(args.workload, epochs)
         per = t["seconds"] / t["epochs"]
         # parity of the sample: same epochs on the GPU path from the prior
-        g = type(f)(sc.cfg, precision=args.precision)
+        g = type(f)(sc.cfg, precision=args.precision, psi_mode=MODES["psi"])
         for k in range(epochs):
             g.step(sc.meas, sc.z[k], sc.dt)
         Pg = g.pdf()[0]
