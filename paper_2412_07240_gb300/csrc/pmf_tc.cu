@@ -395,7 +395,10 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   for (int i = tid; i < kFsWords; i += kThreads)
     ((unsigned long long*)&fs)[i] = ((const unsigned long long*)&st->f)[i];
   if (job.do_time) {
-    for (int i = tid; i < (int)(sizeof(TimeConsts) / 8); i += kThreads)
+    // the constants up to the sub-step rows this update uses
+    const int nq = job.tc->exact ? 1 : job.tc->l;
+    const int words = (int)((offsetof(TimeConsts, Qt) + sizeof(job.tc->Qt[0]) * (size_t)nq) / 8);
+    for (int i = tid; i < words; i += kThreads)
       ((unsigned long long*)&sh.tc)[i] = ((const unsigned long long*)job.tc)[i];
     for (int a = 0; a < 2; ++a) {
       const int n = 2 * (2 * (a ? N1 : N0) + 1);
@@ -492,18 +495,32 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     const float ps = (float)fs.pscale;
     Moments mo;
     mo.zero();
-    for (int t = tid; t < np4; t += kThreads) {
-      const int r = (int)(((float)t + 0.5f) * rq1), c = (t - r * q1) * 4;
-      const float u0 = r - 0.5f * (N0 - 1), u1 = c - 0.5f * (N1 - 1);
-      float4 x = *(const float4*)(S + r * kSStr + c);
-      const float4 e = E[t];
-      x.x = (x.x * ps) * __expf(emin - e.x);
-      x.y = (x.y * ps) * __expf(emin - e.y);
-      x.z = (x.z * ps) * __expf(emin - e.z);
-      x.w = (x.w * ps) * __expf(emin - e.w);
-      *(float4*)(S + r * kSStr + c) = x;
-      mo.add4(x, u0, u1);
-      smax = amax4(smax, x);
+    // a thread keeps one group of four columns (the step is a multiple of q1)
+    // and sums its rows in float32 per column; one double-float add per slot
+    const int tmax = (kThreads / q1) * q1;
+    if (tid < tmax) {
+      float ca[4] = {0.0f, 0.0f, 0.0f, 0.0f}, cb[4] = {0.0f, 0.0f, 0.0f, 0.0f}, cc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      for (int t = tid; t < np4; t += tmax) {
+        const int r = (int)(((float)t + 0.5f) * rq1), c = (t - r * q1) * 4;
+        const float u0 = r - 0.5f * (N0 - 1);
+        float4 x = *(const float4*)(S + r * kSStr + c);
+        const float4 e = E[t];
+        x.x = (x.x * ps) * __expf(emin - e.x);
+        x.y = (x.y * ps) * __expf(emin - e.y);
+        x.z = (x.z * ps) * __expf(emin - e.z);
+        x.w = (x.w * ps) * __expf(emin - e.w);
+        *(float4*)(S + r * kSStr + c) = x;
+        const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float xu = xs[i] * u0;
+          ca[i] += xs[i];
+          cb[i] += xu;
+          cc[i] = fmaf(xu, u0, cc[i]);
+        }
+        smax = amax4(smax, x);
+      }
+      mo.add_cols4(ca, cb, cc, (tid % q1) * 4 - 0.5f * (N1 - 1));
     }
     if constexpr (kOut) block_moments_out(sh, mo);
     else block_moments(sh, mo);
@@ -694,12 +711,21 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         mo.zero();
         const float u0 = row - 0.5f * (N0 - 1);
         float* orow = out + (size_t)row * N1 + c0;
+        float ra = 0.0f, rb = 0.0f, rc = 0.0f;   // this row segment: sum x, x u1, x u1^2
 #pragma unroll
         for (int j = 0; j < 8; ++j)
           if (4 * j < ncol && lane_ok) {
             *(float4*)(orow + 4 * j) = v[j];
-            mo.add4(v[j], u0, (c0 + 4 * j) - 0.5f * (N1 - 1));
+            const float4 x = v[j];
+            const float u1 = (c0 + 4 * j) - 0.5f * (N1 - 1);
+            const float a0 = x.x + x.y + x.z + x.w;
+            const float a1 = x.y + 2.0f * x.z + 3.0f * x.w;
+            const float a2 = x.y + 4.0f * x.z + 9.0f * x.w;
+            ra += a0;
+            rb += fmaf(u1, a0, a1);
+            rc += fmaf(u1, fmaf(u1, a0, 2.0f * a1), a2);
           }
+        mo.add_row(ra, rb, rc, u0);
         tc_before_sync();
         if constexpr (kOut) block_moments_out(sh, mo);
         else block_moments(sh, mo);

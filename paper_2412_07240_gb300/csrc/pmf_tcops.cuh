@@ -220,26 +220,44 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
 __device__ __forceinline__ DF df_add1(DF a, float b) { return df_add(a, DF{b, 0.0f}); }
 
 // Moment sums of one thread: S0, S1 (u0, u1), S2 (u0u0, u0u1, u1u1).  Points
-// arrive in groups (a row segment of 4); the group sums are formed in float32
-// and added in double-float.
+// arrive in groups (a thread's row segment, or a thread's four columns); the
+// group sums are formed in float32 (at most ~40 terms) and added in
+// double-float.
 struct Moments {
   DF s[6];
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int i = 0; i < 6; ++i) s[i] = DF{0.0f, 0.0f};
   }
-  // four points x.x..x.w at (u0, u1 + 0..3)
-  __device__ __forceinline__ void add4(float4 x, float u0, float u1) {
-    const float a0 = x.x + x.y + x.z + x.w;
-    const float a1 = x.y + 2.0f * x.z + 3.0f * x.w;       // sum x * (u1' - u1)
-    const float a2 = x.y + 4.0f * x.z + 9.0f * x.w;       // sum x * (u1' - u1)^2
-    const float b1 = fmaf(u1, a0, a1);                      // sum x u1'
-    s[0] = df_add1(s[0], a0);
-    s[1] = df_add1(s[1], a0 * u0);
-    s[2] = df_add1(s[2], b1);
-    s[3] = df_add1(s[3], a0 * u0 * u0);
-    s[4] = df_add1(s[4], b1 * u0);
-    s[5] = df_add1(s[5], fmaf(u1, fmaf(u1, a0, 2.0f * a1), a2));   // sum x u1'^2
+  // float32 sums of a row segment at u0: a = sum x, b = sum x u1, c = sum x u1^2
+  __device__ __forceinline__ void add_row(float a, float b, float c, float u0) {
+    s[0] = df_add1(s[0], a);
+    s[1] = df_add1(s[1], a * u0);
+    s[2] = df_add1(s[2], b);
+    s[3] = df_add1(s[3], a * u0 * u0);
+    s[4] = df_add1(s[4], b * u0);
+    s[5] = df_add1(s[5], c);
+  }
+  // float32 sums of four columns u1 + 0..3: a[i] = sum x, b[i] = sum x u0,
+  // c[i] = sum x u0^2 over the rows of column i
+  __device__ __forceinline__ void add_cols4(const float* a, const float* b, const float* c, float u1) {
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f, s4 = 0.0f, s5 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float v = u1 + (float)i;
+      s0 += a[i];
+      s1 += b[i];
+      s2 = fmaf(a[i], v, s2);
+      s3 += c[i];
+      s4 = fmaf(b[i], v, s4);
+      s5 = fmaf(a[i] * v, v, s5);
+    }
+    s[0] = df_add1(s[0], s0);
+    s[1] = df_add1(s[1], s1);
+    s[2] = df_add1(s[2], s2);
+    s[3] = df_add1(s[3], s3);
+    s[4] = df_add1(s[4], s4);
+    s[5] = df_add1(s[5], s5);
   }
 };
 
