@@ -109,10 +109,11 @@ __device__ void frame_body(const TimeConsts& tcp, DevState* st, double* pend) {
   __shared__ FrameState fs;
   __shared__ double Mpi[16];
   __shared__ TimeConsts tc;
-  constexpr int kWords = sizeof(FrameState) / 8, kTcWords = sizeof(TimeConsts) / 8;
+  constexpr int kWords = sizeof(FrameState) / 8;
+  const int tc_w = tc_words(&tcp);
   for (int i = threadIdx.x; i < kWords; i += blockDim.x)
     ((unsigned long long*)&fs)[i] = ((const unsigned long long*)&st->f)[i];
-  for (int i = threadIdx.x; i < kTcWords; i += blockDim.x)
+  for (int i = threadIdx.x; i < tc_w; i += blockDim.x)
     ((unsigned long long*)&tc)[i] = ((const unsigned long long*)&tcp)[i];
   __syncthreads();
   if (threadIdx.x < 32) frame_warp<n>(tc, &fs, pend, Mpi);

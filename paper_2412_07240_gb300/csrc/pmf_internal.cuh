@@ -37,6 +37,14 @@ struct TimeConsts {
   double Qt[MAXL][10];
 };
 
+// 8-byte words of a TimeConsts that a time update reads: everything up to the
+// sub-step rows it uses (Qt is the last member; the exact multiplier reads none
+// of them but one row is kept).
+PMF_HD int tc_words(const TimeConsts* tc) {
+  const int rows = tc->exact ? 1 : tc->l;
+  return (int)((sizeof(TimeConsts) - sizeof(tc->Qt) + sizeof(tc->Qt[0]) * rows) / 8);
+}
+
 // Index of the symmetric entry (a, b) in the packed order of TimeConsts::Qt.
 PMF_HD int packed_sym(int a, int b) {
   const int lo = a < b ? a : b, hi = a < b ? b : a;

@@ -395,9 +395,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   for (int i = tid; i < kFsWords; i += kThreads)
     ((unsigned long long*)&fs)[i] = ((const unsigned long long*)&st->f)[i];
   if (job.do_time) {
-    // the constants up to the sub-step rows this update uses
-    const int nq = job.tc->exact ? 1 : job.tc->l;
-    const int words = (int)((offsetof(TimeConsts, Qt) + sizeof(job.tc->Qt[0]) * (size_t)nq) / 8);
+    const int words = tc_words(job.tc);   // up to the sub-step rows this update uses
     for (int i = tid; i < words; i += kThreads)
       ((unsigned long long*)&sh.tc)[i] = ((const unsigned long long*)job.tc)[i];
     for (int a = 0; a < 2; ++a) {

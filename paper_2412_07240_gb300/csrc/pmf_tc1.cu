@@ -189,7 +189,8 @@ __device__ void fused1d(const View1& v) {
   constexpr int kFsWords = sizeof(FrameState) / 8;
   for (int i = tid; i < kFsWords; i += kT1) ((unsigned long long*)&fs)[i] = ((const unsigned long long*)&st->f)[i];
   if (v.do_time) {
-    for (int i = tid; i < (int)(sizeof(TimeConsts) / 8); i += kT1)
+    const int words = tc_words(v.tc);   // up to the sub-step rows this update uses
+    for (int i = tid; i < words; i += kT1)
       ((unsigned long long*)&sh.tc)[i] = ((const unsigned long long*)v.tc)[i];
     for (int i = tid; i < N; i += kT1) sh.cas[i] = v.tab[i];
     for (int i = tid; i < 2 * (2 * N + 1); i += kT1) sh.sct[i] = v.tab[N + i];
