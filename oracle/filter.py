@@ -132,6 +132,77 @@ def shear_realign(P: np.ndarray, B: np.ndarray, b: np.ndarray) -> np.ndarray:
     return np.moveaxis(out, 0, p)
 
 
+SHEAR_ORDERS_3D = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+
+
+def shear_passes(B: np.ndarray, b: np.ndarray):
+    """Factor u_old = B w + b into n line-wise passes (n = 2 or 3).
+
+    With an axis order (a_1, ..., a_n), pass k (applied to the data in the
+    order k = n, ..., 1) resamples along axis a_k; on its array the axes
+    S = {a_1..a_{k-1}} still carry old coordinates u_S and T = {a_k..a_n} new
+    ones w_T, and the old coordinate a_k sits at
+        u_{a_k} = alpha . u_S + beta . w_T + gamma,
+        alpha = B[a_k, S] B[S, S]^{-1},  beta = B[a_k, T] - alpha B[S, T],
+        gamma = b[a_k] - alpha b[S]
+    (eliminating w_S from the rows S of the map).  The order minimises the
+    largest |alpha| (the line-dependent shifts), first in SHEAR_ORDERS_3D on
+    ties; for n = 2 this is the rule of shear_realign.  Returns
+    [(axis, coefficient per axis (3-vector over all axes), gamma)] in data
+    order (k = n first)."""
+    n = B.shape[0]
+    orders = ((0, 1), (1, 0)) if n == 2 else SHEAR_ORDERS_3D
+    best, best_val = None, np.inf
+    for order in orders:
+        val, ok, passes = 0.0, True, []
+        for k in range(n, 0, -1):
+            a, S, T = order[k - 1], list(order[:k - 1]), list(order[k - 1:])
+            if S:
+                BSS = B[np.ix_(S, S)]
+                if abs(np.linalg.det(BSS)) <= 1e-12 * max(1.0, np.abs(BSS).max()) ** len(S):
+                    ok = False
+                    break
+                alpha = B[a, S] @ np.linalg.inv(BSS)
+                val = max(val, np.abs(alpha).max())
+            else:
+                alpha = np.zeros(0)
+            beta = B[a, T] - (alpha @ B[np.ix_(S, T)] if S else 0.0)
+            gamma = b[a] - (alpha @ b[S] if S else 0.0)
+            coef = np.zeros(n)
+            coef[S] = alpha
+            coef[T] = beta
+            passes.append((a, coef, float(gamma)))
+        if ok and val < best_val:
+            best, best_val = passes, val
+    if best is None:
+        raise Degenerate("re-alignment map has a singular leading block in every order")
+    return best
+
+
+def shear_realign_nd(P: np.ndarray, B: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Band-limited re-alignment in n = 2 or 3 dimensions: the passes of
+    shear_passes, each the 1-D trigonometric interpolant (eq. interFreq) of
+    every line along its axis at that line's positions (coordinate value of
+    the other axes times their coefficients, plus gamma, plus the running
+    coefficient times the new node); positions outside the old box get 0."""
+    G = np.array(P, dtype=float)
+    N = G.shape
+    for a, coef, gamma in shear_passes(np.asarray(B, float), np.asarray(b, float)):
+        Ga = np.moveaxis(G, a, -1)                    # lines along a, other axes in order
+        others = [m for m in range(G.ndim) if m != a]
+        grids = np.meshgrid(*[grid_u(N[m]) for m in others], indexing="ij")
+        offset = gamma + sum(coef[m] * g for m, g in zip(others, grids))
+        ua = grid_u(N[a])
+        out = np.empty_like(Ga)
+        for idx in np.ndindex(*Ga.shape[:-1]):
+            pos = offset[idx] + coef[a] * ua
+            E = spectral.interp_matrix(N[a], pos + (N[a] - 1) / 2.0)
+            E[np.abs(pos) > N[a] / 2.0, :] = 0.0
+            out[idx] = E @ Ga[idx]
+        G = np.moveaxis(out, -1, a)
+    return G
+
+
 SHIFT_QUANTUM = 1.0 / 64.0
 SCALE_MANTISSA_BITS = 8
 
@@ -164,8 +235,8 @@ class OracleFilter:
         self.n = cfg.nx
         if realign_mode is None:
             realign_mode = getattr(cfg, "realign_mode", "multilinear")
-        if realign_mode not in ("multilinear", "shear") or (realign_mode == "shear" and cfg.nx != 2):
-            raise ValueError("realign_mode: 'multilinear', or 'shear' for n_x = 2")
+        if realign_mode not in ("multilinear", "shear") or (realign_mode == "shear" and cfg.nx not in (2, 3)):
+            raise ValueError("realign_mode: 'multilinear', or 'shear' for n_x = 2 or 3")
         self.realign_mode = realign_mode
         self.N = tuple(int(v) for v in cfg.N)
         self.A = np.asarray(cfg.A, dtype=float)
@@ -295,7 +366,8 @@ class OracleFilter:
             Mnew = ch["M"]
             if self.realign_mode == "shear":
                 # u_old = Minv (c' + M' u_new - c) = B u_new + b
-                self.P = shear_realign(self.P, Minv @ Mnew, Minv @ (m - self.c))
+                shear = shear_realign if n == 2 else shear_realign_nd
+                self.P = shear(self.P, Minv @ Mnew, Minv @ (m - self.c))
             else:
                 x = frame_points(m, Mnew, self.N)
                 u_old = (x - self.c[None, :]) @ Minv.T

@@ -385,3 +385,58 @@ def test_4d_terrain_cycle_self_converges():
             assert e24 < 1e-4 and e24 < e16 / 50, (e16, e24)
         else:
             assert e24 < e16 / 2, (e16, e24)
+
+
+def test_shear_nd_reduces_to_the_2d_passes():
+    """The n-dimensional factorisation chooses the same pass order as the 2-D
+    rule and gives the same values (to the association order of the sums)."""
+    rng = np.random.default_rng(1)
+    for B in ([[0.9, 0.35], [-0.3, 0.8]], [[0.7, 0.0], [0.35, 0.8]], [[0.8, 0.3], [0.0, 0.7]],
+              [[1.1, -0.4], [0.5, 0.6]]):
+        B, b = np.array(B), np.array([0.3, -0.45])
+        P = rng.uniform(size=(24, 28))
+        assert np.abs(of.shear_realign(P, B, b) - of.shear_realign_nd(P, B, b)).max() < 1e-13
+
+
+def _trig_field3(N):
+    u = of.grid_u(N)
+    U = np.meshgrid(u, u, u, indexing="ij")
+    f = lambda a, b, c: (1.0 + 0.3 * np.cos(2 * np.pi * 2 * a / N + 0.4) + 0.2 * np.sin(2 * np.pi * (a + 2 * b) / N)
+                         + 0.1 * np.cos(2 * np.pi * (3 * c - b) / N - 1.0))
+    return U, f
+
+
+@pytest.mark.parametrize("B", [
+    [[0.8, 0.0, 0.0], [0.3, 0.9, 0.0], [-0.2, 0.25, 0.7]],      # lower triangular
+    [[0.7, 0.3, -0.2], [0.0, 0.9, 0.25], [0.0, 0.0, 0.8]],      # upper triangular
+    [[0.9, 0.0, 0.2], [0.0, 0.8, 0.0], [0.0, 0.3, 0.75]],       # triangular after a permutation
+])
+def test_shear3_exact_on_trig_polynomials(B):
+    """A map that is triangular in some axis order is three exact 1-D
+    resamplings of a trigonometric polynomial (the order selection finds it:
+    no line-dependent shift before an axis is resampled)."""
+    B, b = np.array(B), np.array([0.3, -0.45, 0.2])
+    N = 16
+    U, f = _trig_field3(N)
+    out = of.shear_realign_nd(f(*U), B, b)
+    Z = [sum(B[i, j] * U[j] for j in range(3)) + b[i] for i in range(3)]
+    inside = np.all([np.abs(z) <= N / 2 for z in Z], axis=0)
+    assert np.abs(out - f(*Z))[inside].max() < 1e-12
+
+
+def test_shear3_spectral_on_gaussians():
+    """A general map of a correlated 3-D Gaussian inside a +-6 sigma box: the
+    band-limited fill is far below the multilinear one."""
+    B = np.array([[0.9, 0.3, -0.1], [-0.25, 0.85, 0.2], [0.15, -0.2, 0.8]])
+    b = np.array([0.3, -0.45, 0.2])
+    N = 24
+    u = of.grid_u(N)
+    U = np.meshgrid(u, u, u, indexing="ij")
+    s = N / 12.0
+    g = lambda a, c, e: np.exp(-0.5 * (a ** 2 + 0.6 * a * c + c ** 2 - 0.4 * c * e + e ** 2) / s ** 2)
+    Z = [sum(B[i, j] * U[j] for j in range(3)) + b[i] for i in range(3)]
+    ex = g(*Z)
+    sh = of.shear_realign_nd(g(*U), B, b)
+    ml = of.multilinear(g(*U), np.stack([z.ravel() for z in Z], 1) + (N - 1) / 2).reshape(N, N, N)
+    e_sh, e_ml = np.abs(sh - ex).max() / ex.max(), np.abs(ml - ex).max() / ex.max()
+    assert e_sh < 1e-4 and e_sh < e_ml / 100, (e_sh, e_ml)
