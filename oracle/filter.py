@@ -146,13 +146,16 @@ def shear_passes(B: np.ndarray, b: np.ndarray):
         alpha = B[a_k, S] B[S, S]^{-1},  beta = B[a_k, T] - alpha B[S, T],
         gamma = b[a_k] - alpha b[S]
     (eliminating w_S from the rows S of the map).  The order minimises the
-    largest |alpha| (the line-dependent shifts), first in SHEAR_ORDERS_3D on
-    ties; for n = 2 this is the rule of shear_realign.  Returns
+    largest |alpha| (the line-dependent shifts); orders within a relative
+    1e-9 of the minimum count as tied (orders that share their alpha sets tie
+    exactly in real arithmetic, so the choice must not depend on rounding)
+    and the first tied one in SHEAR_ORDERS_3D is taken; for n = 2 this is the
+    rule of shear_realign.  Returns
     [(axis, coefficient per axis (3-vector over all axes), gamma)] in data
     order (k = n first)."""
     n = B.shape[0]
     orders = ((0, 1), (1, 0)) if n == 2 else SHEAR_ORDERS_3D
-    best, best_val = None, np.inf
+    cands = []
     for order in orders:
         val, ok, passes = 0.0, True, []
         for k in range(n, 0, -1):
@@ -172,11 +175,12 @@ def shear_passes(B: np.ndarray, b: np.ndarray):
             coef[S] = alpha
             coef[T] = beta
             passes.append((a, coef, float(gamma)))
-        if ok and val < best_val:
-            best, best_val = passes, val
-    if best is None:
+        if ok:
+            cands.append((val, passes))
+    if not cands:
         raise Degenerate("re-alignment map has a singular leading block in every order")
-    return best
+    vmin = min(v for v, _ in cands)
+    return next(p for v, p in cands if v <= vmin * (1.0 + 1e-9))
 
 
 def shear_realign_nd(P: np.ndarray, B: np.ndarray, b: np.ndarray) -> np.ndarray:

@@ -234,6 +234,159 @@ __global__ void k_shear_f64(Dims d, const DevState* st, int pass, double* b0, do
 // Stage 0 of the time update: multilinear re-alignment when the frame was
 // re-aligned, otherwise a scaled copy (both fold the normalisation scale in).
 // In the shear mode a re-aligned frame is filled by k_shear_f64 instead.
+// Band-limited re-alignment of a 3-D grid (shear mode): the map u_old = B w + b
+// factored into three line-wise passes.  With an axis order (a_1, a_2, a_3),
+// pass k (applied in the order k = 3, 2, 1) resamples along a_k; the axes
+// S = {a_1..a_{k-1}} still carry old coordinates and T = {a_k..a_3} new ones,
+// and the old coordinate a_k of a node is
+//   alpha . u_S + beta . w_T + gamma,  alpha = B[a_k, S] B[S, S]^{-1},
+//   beta = B[a_k, T] - alpha B[S, T],  gamma = b[a_k] - alpha b[S].
+// The order minimises the largest |alpha| (first of the six in lexicographic
+// order on ties).  k_shear3_setup (one thread) writes, per pass in data order,
+// pc[8 i] = axis, pc[8 i + 1..3] = coefficient of each axis, pc[8 i + 4] =
+// gamma, and pc[24] = 1 (0 and status DEGENERATE if every order has a
+// singular leading block).
+// Passes of one axis order (false if a leading block is singular); val = the
+// largest |alpha|.
+__device__ bool shear3_order(const double* B, const double* bb, const int* a, double* cand, double* val) {
+  *val = 0.0;
+  for (int i = 0; i < 24; ++i) cand[i] = 0.0;
+  for (int k = 3; k >= 1; --k) {
+    const int ax = a[k - 1], i = 3 - k;   // data order index
+    double coef[3] = {0.0, 0.0, 0.0}, alpha[2] = {0.0, 0.0};
+    const int ns = k - 1;
+    if (ns == 1) {
+      const double d = B[a[0] * 3 + a[0]];
+      if (fabs(d) <= 1e-12 * fmax(1.0, fabs(d))) return false;
+      alpha[0] = B[ax * 3 + a[0]] / d;
+    } else if (ns == 2) {
+      const double s00 = B[a[0] * 3 + a[0]], s01 = B[a[0] * 3 + a[1]];
+      const double s10 = B[a[1] * 3 + a[0]], s11 = B[a[1] * 3 + a[1]];
+      const double det = s00 * s11 - s01 * s10;
+      const double mx = fmax(fmax(fabs(s00), fabs(s01)), fmax(fabs(s10), fabs(s11)));
+      if (fabs(det) <= 1e-12 * fmax(1.0, mx) * fmax(1.0, mx)) return false;
+      // alpha = B[ax, S] inv(B_SS), inv = [s11 -s01; -s10 s00] / det
+      const double r0 = B[ax * 3 + a[0]], r1 = B[ax * 3 + a[1]];
+      alpha[0] = (r0 * s11 - r1 * s10) / det;
+      alpha[1] = (-r0 * s01 + r1 * s00) / det;
+    }
+    for (int m = 0; m < ns; ++m) *val = fmax(*val, fabs(alpha[m]));
+    double gamma = bb[ax];
+    for (int m = 0; m < ns; ++m) {
+      coef[a[m]] = alpha[m];
+      gamma -= alpha[m] * bb[a[m]];
+    }
+    for (int t = ns; t < 3; ++t) {          // T = {a_k..a_3}
+      double v = B[ax * 3 + a[t]];
+      for (int m = 0; m < ns; ++m) v -= alpha[m] * B[a[m] * 3 + a[t]];
+      coef[a[t]] = v;
+    }
+    cand[8 * i] = ax;
+    for (int m = 0; m < 3; ++m) cand[8 * i + 1 + m] = coef[m];
+    cand[8 * i + 4] = gamma;
+  }
+  return true;
+}
+
+__global__ void k_shear3_setup(DevState* st, double* pc) {
+  const FrameState& f = st->f;
+  if (!f.realign) return;
+  const int orders[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  double vals[6], cand[24], vmin = INFINITY;
+  for (int o = 0; o < 6; ++o) {
+    vals[o] = INFINITY;
+    double v;
+    if (shear3_order(f.B, f.b, orders[o], cand, &v)) vals[o] = v;
+    vmin = fmin(vmin, vals[o]);
+  }
+  for (int i = 0; i < 25; ++i) pc[i] = 0.0;
+  for (int o = 0; o < 6 && isfinite(vmin); ++o)
+    if (vals[o] <= vmin * (1.0 + 1e-9)) {   // first tied order
+      double v;
+      shear3_order(f.B, f.b, orders[o], cand, &v);
+      for (int i = 0; i < 24; ++i) pc[i] = cand[i];
+      pc[24] = 1.0;
+      return;
+    }
+  st->f.status = PMF_ERR_DEGENERATE;
+}
+
+// One pass of the 3-D band-limited re-alignment: one CTA per line along the
+// pass's axis (surplus CTAs exit); per line the DFT coefficients from an exact
+// twiddle table, then the trigonometric interpolant (eq. interFreq) at the
+// line's positions by a recurrence from an exactly formed e^{2 pi i x / N};
+// positions outside the old box give 0.  Buffers: pass 0 buf[cur] -> scratch,
+// pass 1 scratch -> buf[cur] (the old grid is no longer needed), pass 2
+// buf[cur] -> buf[cur ^ 1] with pscale.
+__global__ void k_shear3_f64(Dims d, const DevState* st, const double* pc, int pass, double* b0, double* b1,
+                             double* scratch) {
+  extern __shared__ double sm[];
+  const FrameState& f = st->f;
+  if (!f.realign || pc[24] == 0.0) return;
+  double* bc = f.cur ? b1 : b0;
+  double* bn = f.cur ? b0 : b1;
+  const double* in = pass == 1 ? scratch : bc;
+  double* out = pass == 0 ? scratch : pass == 1 ? bc : bn;
+  const int last = pass == 2;
+  const int a = (int)pc[8 * pass];
+  const double* coef = pc + 8 * pass + 1;
+  const double gamma = pc[8 * pass + 4];
+  const int o1 = a == 0 ? 1 : 0, o2 = a == 2 ? 1 : 2;
+  const int N = d.N[a], H = N / 2, N1 = d.N[o1], N2 = d.N[o2];
+  const int line = blockIdx.x;
+  if (line >= N1 * N2) return;
+  const int i1 = line / N2, i2 = line % N2;
+  long long stride[3];
+  stride[2] = 1;
+  stride[1] = d.N[2];
+  stride[0] = (long long)d.N[1] * d.N[2];
+  const long long base = i1 * stride[o1] + i2 * stride[o2], sa = stride[a];
+  double* fl = sm;
+  double* Xr = fl + N;
+  double* Xi = Xr + H + 1;
+  double* cs = Xi + H + 1;
+  double* sn = cs + N;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    fl[t] = in[base + t * sa];
+    sincospi(2.0 * t / N, &sn[t], &cs[t]);
+  }
+  __syncthreads();
+  for (int sidx = threadIdx.x; sidx <= H; sidx += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    int r = 0;
+    for (int j = 0; j < N; ++j) {
+      re = fma(fl[j], cs[r], re);
+      im = fma(-fl[j], sn[r], im);
+      r += sidx;
+      if (r >= N) r -= N;
+    }
+    Xr[sidx] = re / N;
+    Xi[sidx] = im / N;
+  }
+  __syncthreads();
+  const double offset = gamma + coef[o1] * (i1 - 0.5 * (N1 - 1)) + coef[o2] * (i2 - 0.5 * (N2 - 1));
+  const double ps = last ? f.pscale : 1.0;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    const double pos = offset + coef[a] * (t - 0.5 * (N - 1));
+    double v = 0.0;
+    if (fabs(pos) <= 0.5 * N) {
+      const double x = pos + 0.5 * (N - 1);
+      double sx, cx;
+      sincospi(2.0 * x / N, &sx, &cx);
+      double zr = 1.0, zi = 0.0;   // e^{2 pi i s x / N}
+      v = Xr[0];
+      for (int k = 1; k < H; ++k) {
+        const double nr = zr * cx - zi * sx;
+        zi = zr * sx + zi * cx;
+        zr = nr;
+        v += 2.0 * (Xr[k] * zr - Xi[k] * zi);
+      }
+      v += Xr[H] * cospi(x);
+    }
+    out[base + t * sa] = ps * v;
+  }
+}
+
 __global__ void k_realign_f64(Dims d, const DevState* st, double* b0, double* b1, int mode) {
   const int cur = st->f.cur;
   const double* in = cur ? b1 : b0;
@@ -520,6 +673,20 @@ void launch_time_f64(const Dims& d, const TimeConsts& tc, DevState* st, double* 
     k_build_interp_f64<<<grid_for((long long)d.N[a] * d.N[a], 256, 1 << 20), 256, 0, s>>>(
         d, st, a, interp[a]);
   k_realign_f64<<<grid_for(d.P, 256, 4096), 256, 0, s>>>(d, st, b0, b1, tc.realign_mode);
+  if (tc.realign_mode == PMF_REALIGN_SHEAR && n == 3 && scratch) {
+    int Nmax = 0, Nmin = 1 << 30;
+    for (int a = 0; a < 3; ++a) {
+      Nmax = d.N[a] > Nmax ? d.N[a] : Nmax;
+      Nmin = d.N[a] < Nmin ? d.N[a] : Nmin;
+    }
+    const size_t smem = sizeof(double) * (4 * (size_t)Nmax + 2);
+    cudaFuncSetAttribute(k_shear3_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    double* pc = scratch + d.P;   // pass coefficients after the intermediate grid
+    const unsigned lines = (unsigned)(d.P / Nmin);   // enough for the pass with the most lines
+    k_shear3_setup<<<1, 1, 0, s>>>(st, pc);
+    for (int pass = 0; pass < 3; ++pass)
+      k_shear3_f64<<<lines, 128, smem, s>>>(d, st, pc, pass, b0, b1, scratch);
+  }
   if (tc.realign_mode == PMF_REALIGN_SHEAR && n == 2 && scratch) {
     const int Nmax = d.N[0] > d.N[1] ? d.N[0] : d.N[1];
     const size_t smem = sizeof(double) * (4 * (size_t)Nmax + 2);

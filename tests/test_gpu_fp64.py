@@ -86,3 +86,26 @@ def test_2d_shear_realignment_path():
     worst, log = max_errors(sc)
     assert any(s.endswith("R") for s, _ in log), "re-alignment not exercised"
     _check(worst, 1e-11)
+
+
+def _cv3(mode, N=(20, 24, 16), epochs=6):
+    A = np.array([[0.0, 1.0, 0.0], [0.0, 0.0, 0.0], [0.0, 0.3, -0.5]])
+    cfg = FilterConfig(nx=3, N=N, A=A, Q=np.diag([0.01, 0.1, 0.05]), m0=np.array([0.0, 1.0, 0.5]),
+                       P0=np.diag([0.5, 0.5, 0.3]), realign_mode=mode)
+    meas = MeasModel("linear", R=np.diag([0.3 ** 2, 0.4 ** 2]), H=np.array([[1.0, 0.0, 0.0], [0.0, 0.0, 1.0]]))
+    sc = Scenario("cv3", cfg, meas, dt=0.2, epochs=epochs)
+    sc.truth, sc.z = simulate(cfg, meas, sc.dt, sc.epochs, seed=12)
+    return sc
+
+
+def test_3d_shear_realignment_path():
+    """Band-limited re-alignment in 3-D: three line-wise passes on the float64 path."""
+    worst, log = max_errors(_cv3("shear"))
+    assert sum(s.endswith("R") for s, _ in log) >= 2, "re-alignment not exercised"
+    _check(worst, 1e-11)
+
+
+def test_3d_shear_only_on_the_float64_path():
+    from paper_2412_07240_gb300 import Filter, Unsupported
+    with pytest.raises(Unsupported):
+        Filter(_cv3("shear", N=(32, 32, 16)).cfg, precision="fp16x3")
