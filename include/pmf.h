@@ -86,11 +86,12 @@ enum { PMF_PSI_EULER = 0, PMF_PSI_EXACT = 1 };
 /* Fill of a re-aligned frame (the regrid when the frame's whitened
  * correlation exceeds realign_rho; Sec. V grid reshaping).
  *   MULTILINEAR : multilinear interpolation of the old weights (any n_x).
- *   SHEAR       : n_x = 2 only: the trigonometric interpolant (eq. interFreq)
- *                 of the old weights at the new nodes, as two line-wise
+ *   SHEAR       : n_x = 2 or 3: the trigonometric interpolant (eq. interFreq)
+ *                 of the old weights at the new nodes, as n line-wise
  *                 passes (per line: DFT, evaluation at that line's affine
  *                 positions); spectrally accurate for densities well inside
- *                 the box. */
+ *                 the box.  n_x = 3 runs on the FP64 path only (the 3-D
+ *                 tensor-core pipelines return PMF_ERR_UNSUPPORTED). */
 enum { PMF_REALIGN_MULTILINEAR = 0, PMF_REALIGN_SHEAR = 1 };
 
 /* Form of the per-axis Hartley transforms (step 1 and step 5 of the Sec. V-B
