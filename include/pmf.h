@@ -90,8 +90,7 @@ enum { PMF_PSI_EULER = 0, PMF_PSI_EXACT = 1 };
  *                 of the old weights at the new nodes, as n line-wise
  *                 passes (per line: DFT, evaluation at that line's affine
  *                 positions); spectrally accurate for densities well inside
- *                 the box.  n_x = 3 runs on the FP64 path only (the 3-D
- *                 tensor-core pipelines return PMF_ERR_UNSUPPORTED). */
+ *                 the box. */
 enum { PMF_REALIGN_MULTILINEAR = 0, PMF_REALIGN_SHEAR = 1 };
 
 /* Form of the per-axis Hartley transforms (step 1 and step 5 of the Sec. V-B

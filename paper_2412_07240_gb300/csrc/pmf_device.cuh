@@ -52,6 +52,76 @@ __device__ __forceinline__ double det_t(const double* A) {
          A[2] * (A[3] * A[7] - A[4] * A[6]);
 }
 
+// Passes of one axis order (false if a leading block is singular); val = the
+// largest |alpha|.
+__device__ inline bool shear3_order(const double* B, const double* bb, const int* a, double* cand, double* val) {
+  *val = 0.0;
+  for (int i = 0; i < 24; ++i) cand[i] = 0.0;
+  for (int k = 3; k >= 1; --k) {
+    const int ax = a[k - 1], i = 3 - k;   // data order index
+    double coef[3] = {0.0, 0.0, 0.0}, alpha[2] = {0.0, 0.0};
+    const int ns = k - 1;
+    if (ns == 1) {
+      const double d = B[a[0] * 3 + a[0]];
+      if (fabs(d) <= 1e-12 * fmax(1.0, fabs(d))) return false;
+      alpha[0] = B[ax * 3 + a[0]] / d;
+    } else if (ns == 2) {
+      const double s00 = B[a[0] * 3 + a[0]], s01 = B[a[0] * 3 + a[1]];
+      const double s10 = B[a[1] * 3 + a[0]], s11 = B[a[1] * 3 + a[1]];
+      const double det = s00 * s11 - s01 * s10;
+      const double mx = fmax(fmax(fabs(s00), fabs(s01)), fmax(fabs(s10), fabs(s11)));
+      if (fabs(det) <= 1e-12 * fmax(1.0, mx) * fmax(1.0, mx)) return false;
+      // alpha = B[ax, S] inv(B_SS), inv = [s11 -s01; -s10 s00] / det
+      const double r0 = B[ax * 3 + a[0]], r1 = B[ax * 3 + a[1]];
+      alpha[0] = (r0 * s11 - r1 * s10) / det;
+      alpha[1] = (-r0 * s01 + r1 * s00) / det;
+    }
+    for (int m = 0; m < ns; ++m) *val = fmax(*val, fabs(alpha[m]));
+    double gamma = bb[ax];
+    for (int m = 0; m < ns; ++m) {
+      coef[a[m]] = alpha[m];
+      gamma -= alpha[m] * bb[a[m]];
+    }
+    for (int t = ns; t < 3; ++t) {          // T = {a_k..a_3}
+      double v = B[ax * 3 + a[t]];
+      for (int m = 0; m < ns; ++m) v -= alpha[m] * B[a[m] * 3 + a[t]];
+      coef[a[t]] = v;
+    }
+    cand[8 * i] = ax;
+    for (int m = 0; m < 3; ++m) cand[8 * i + 1 + m] = coef[m];
+    cand[8 * i + 4] = gamma;
+  }
+  return true;
+}
+
+// Pass coefficients of the 3-D band-limited re-alignment for the frame's map
+// u_old = B w + b: per pass in data order pc[8 i] = axis, pc[8 i + 1..3] =
+// coefficient of each axis, pc[8 i + 4] = gamma; pc[24] = 1, or 0 (and false)
+// when every order has a singular leading block.  The order minimises the
+// largest |alpha|; orders within a relative 1e-9 of the minimum are tied
+// (orders sharing their alpha sets tie exactly in real arithmetic) and the
+// first tied one in lexicographic order is taken.
+__device__ inline bool shear3_setup(const FrameState& f, double* pc) {
+  const int orders[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  double vals[6], cand[24], vmin = INFINITY;
+  for (int o = 0; o < 6; ++o) {
+    vals[o] = INFINITY;
+    double v;
+    if (shear3_order(f.B, f.b, orders[o], cand, &v)) vals[o] = v;
+    vmin = fmin(vmin, vals[o]);
+  }
+  for (int i = 0; i < 25; ++i) pc[i] = 0.0;
+  for (int o = 0; o < 6 && isfinite(vmin); ++o)
+    if (vals[o] <= vmin * (1.0 + 1e-9)) {   // first tied order
+      double v;
+      shear3_order(f.B, f.b, orders[o], cand, &v);
+      for (int i = 0; i < 24; ++i) pc[i] = cand[i];
+      pc[24] = 1.0;
+      return true;
+    }
+  return false;
+}
+
 // Diffusion coefficients of sub-step q in the new frame (any thread):
 // Q_u(t_q) = M'^{-1} Qt_q M'^{-T}, Qt_q = e^{-A q dt} Q e^{-A^T q dt} (host),
 // pa = dt/2 Q_u,aa and pb = dt Q_u,ab (01, 02, 12); for the exact multiplier

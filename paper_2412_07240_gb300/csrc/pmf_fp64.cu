@@ -231,9 +231,6 @@ __global__ void k_shear_f64(Dims d, const DevState* st, int pass, double* b0, do
   }
 }
 
-// Stage 0 of the time update: multilinear re-alignment when the frame was
-// re-aligned, otherwise a scaled copy (both fold the normalisation scale in).
-// In the shear mode a re-aligned frame is filled by k_shear_f64 instead.
 // Band-limited re-alignment of a 3-D grid (shear mode): the map u_old = B w + b
 // factored into three line-wise passes.  With an axis order (a_1, a_2, a_3),
 // pass k (applied in the order k = 3, 2, 1) resamples along a_k; the axes
@@ -241,74 +238,14 @@ __global__ void k_shear_f64(Dims d, const DevState* st, int pass, double* b0, do
 // and the old coordinate a_k of a node is
 //   alpha . u_S + beta . w_T + gamma,  alpha = B[a_k, S] B[S, S]^{-1},
 //   beta = B[a_k, T] - alpha B[S, T],  gamma = b[a_k] - alpha b[S].
-// The order minimises the largest |alpha| (first of the six in lexicographic
-// order on ties).  k_shear3_setup (one thread) writes, per pass in data order,
+// The order and coefficients come from shear3_setup (pmf_device.cuh);
+// k_shear3_setup (one thread) writes them, per pass in data order, as
 // pc[8 i] = axis, pc[8 i + 1..3] = coefficient of each axis, pc[8 i + 4] =
 // gamma, and pc[24] = 1 (0 and status DEGENERATE if every order has a
 // singular leading block).
-// Passes of one axis order (false if a leading block is singular); val = the
-// largest |alpha|.
-__device__ bool shear3_order(const double* B, const double* bb, const int* a, double* cand, double* val) {
-  *val = 0.0;
-  for (int i = 0; i < 24; ++i) cand[i] = 0.0;
-  for (int k = 3; k >= 1; --k) {
-    const int ax = a[k - 1], i = 3 - k;   // data order index
-    double coef[3] = {0.0, 0.0, 0.0}, alpha[2] = {0.0, 0.0};
-    const int ns = k - 1;
-    if (ns == 1) {
-      const double d = B[a[0] * 3 + a[0]];
-      if (fabs(d) <= 1e-12 * fmax(1.0, fabs(d))) return false;
-      alpha[0] = B[ax * 3 + a[0]] / d;
-    } else if (ns == 2) {
-      const double s00 = B[a[0] * 3 + a[0]], s01 = B[a[0] * 3 + a[1]];
-      const double s10 = B[a[1] * 3 + a[0]], s11 = B[a[1] * 3 + a[1]];
-      const double det = s00 * s11 - s01 * s10;
-      const double mx = fmax(fmax(fabs(s00), fabs(s01)), fmax(fabs(s10), fabs(s11)));
-      if (fabs(det) <= 1e-12 * fmax(1.0, mx) * fmax(1.0, mx)) return false;
-      // alpha = B[ax, S] inv(B_SS), inv = [s11 -s01; -s10 s00] / det
-      const double r0 = B[ax * 3 + a[0]], r1 = B[ax * 3 + a[1]];
-      alpha[0] = (r0 * s11 - r1 * s10) / det;
-      alpha[1] = (-r0 * s01 + r1 * s00) / det;
-    }
-    for (int m = 0; m < ns; ++m) *val = fmax(*val, fabs(alpha[m]));
-    double gamma = bb[ax];
-    for (int m = 0; m < ns; ++m) {
-      coef[a[m]] = alpha[m];
-      gamma -= alpha[m] * bb[a[m]];
-    }
-    for (int t = ns; t < 3; ++t) {          // T = {a_k..a_3}
-      double v = B[ax * 3 + a[t]];
-      for (int m = 0; m < ns; ++m) v -= alpha[m] * B[a[m] * 3 + a[t]];
-      coef[a[t]] = v;
-    }
-    cand[8 * i] = ax;
-    for (int m = 0; m < 3; ++m) cand[8 * i + 1 + m] = coef[m];
-    cand[8 * i + 4] = gamma;
-  }
-  return true;
-}
-
 __global__ void k_shear3_setup(DevState* st, double* pc) {
-  const FrameState& f = st->f;
-  if (!f.realign) return;
-  const int orders[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-  double vals[6], cand[24], vmin = INFINITY;
-  for (int o = 0; o < 6; ++o) {
-    vals[o] = INFINITY;
-    double v;
-    if (shear3_order(f.B, f.b, orders[o], cand, &v)) vals[o] = v;
-    vmin = fmin(vmin, vals[o]);
-  }
-  for (int i = 0; i < 25; ++i) pc[i] = 0.0;
-  for (int o = 0; o < 6 && isfinite(vmin); ++o)
-    if (vals[o] <= vmin * (1.0 + 1e-9)) {   // first tied order
-      double v;
-      shear3_order(f.B, f.b, orders[o], cand, &v);
-      for (int i = 0; i < 24; ++i) pc[i] = cand[i];
-      pc[24] = 1.0;
-      return;
-    }
-  st->f.status = PMF_ERR_DEGENERATE;
+  if (!st->f.realign) return;
+  if (!shear3_setup(st->f, pc)) st->f.status = PMF_ERR_DEGENERATE;
 }
 
 // One pass of the 3-D band-limited re-alignment: one CTA per line along the
@@ -387,6 +324,10 @@ __global__ void k_shear3_f64(Dims d, const DevState* st, const double* pc, int p
   }
 }
 
+// Stage 0 of the time update: multilinear re-alignment when the frame was
+// re-aligned, otherwise a scaled copy (both fold the normalisation scale in).
+// In the shear mode a re-aligned frame is filled by k_shear_f64 (2-D) or
+// k_shear3_f64 (3-D) instead.
 __global__ void k_realign_f64(Dims d, const DevState* st, double* b0, double* b1, int mode) {
   const int cur = st->f.cur;
   const double* in = cur ? b1 : b0;

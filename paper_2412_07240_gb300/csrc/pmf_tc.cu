@@ -905,10 +905,6 @@ int tc_supported(const pmf_config* cfg, std::string* why) {
     *why = "the tensor-core path handles n_x = 2 (fused) and n_x = 3 (per-axis pipelines)";
     return PMF_ERR_UNSUPPORTED;
   }
-  if (cfg->nx == 3 && cfg->realign_mode == PMF_REALIGN_SHEAR) {
-    *why = "the 3-D pipelines fill re-aligned frames multilinearly (shear: float64 path)";
-    return PMF_ERR_UNSUPPORTED;
-  }
   for (int a = 0; a < cfg->nx; ++a)
     if (cfg->N[a] % 16 || cfg->N[a] < 16 || cfg->N[a] > 128) {
       *why = "the fused tensor-core kernel needs N multiple of 16 in [16, 128]";

@@ -46,6 +46,7 @@ struct Update3 {
   int l, exact, realign, skip;   // skip: the measurement update was degenerate
   float gsc;                 // trace factor / (N0 N1 N2)
   RegridRows rows[3];        // regrid rows per axis
+  double shear[25];          // band-limited re-alignment passes (shear3_setup layout)
 };
 
 struct Job3 {
@@ -69,7 +70,7 @@ struct Job3 {
 
 // One batched launch sequence: jobs and, per kernel kind, the first CTA of
 // each job (n + 1 entries per kind; a job may own no CTA of a kind).
-enum { kKindMeas = 0, kKindPoints = 1, kKindSlices = 2, kKindLines = 3, kKinds = 4 };
+enum { kKindMeas = 0, kKindPoints = 1, kKindSlices = 2, kKindLines = 3, kKindShear = 4, kKinds = 5 };
 struct Batch3 {
   const Job3* jobs;
   const int* first;          // [kind * (n + 1) + j]
@@ -505,6 +506,9 @@ __global__ void __launch_bounds__(kT) k_frame3(const __grid_constant__ Batch3 b)
       up->exact = fs.exact;
       up->realign = fs.realign;
       up->gsc = (float)(fs.g / ((double)job.g.N[0] * job.g.N[1] * job.g.N[2]));
+      up->shear[24] = 0.0;
+      if (fs.realign && tc.realign_mode == PMF_REALIGN_SHEAR && !shear3_setup(fs, up->shear))
+        fs.status = PMF_ERR_DEGENERATE;
     }
     if (!fs.realign)
       for (int a = 0; a < 3; ++a) regrid_rows(up->rows[a], fs.rs[a], fs.rd[a], job.g.N[a], threadIdx.x, kT);
@@ -520,7 +524,7 @@ __global__ void __launch_bounds__(kT) k_realign3(const __grid_constant__ Batch3 
   int blk, cnt;
   const Job3& job = job_at(b, find_job(b, kKindPoints, blockIdx.x, &blk, &cnt));
   const FrameState& f = job.st->f;
-  if (job.up->skip || !job.up->realign) return;
+  if (job.up->skip || !job.up->realign || job.tc.realign_mode == PMF_REALIGN_SHEAR) return;
   const Geo3& g = job.g;
   const float* in = f.cur ? job.buf1 : job.buf0;
   float* out = f.cur ? job.buf0 : job.buf1;
@@ -565,6 +569,76 @@ __global__ void __launch_bounds__(kT) k_copy3(const __grid_constant__ Batch3 b) 
   float* dst = f.cur ? job.buf1 : job.buf0;
   for (long long p = blk * (long long)kT + threadIdx.x; p < job.g.P; p += (long long)cnt * kT)
     dst[p] = src[p];
+}
+
+// Band-limited re-alignment (shear mode), one of three line-wise passes: one
+// CTA per line along the pass's axis (the job owns N0 N1 N2 / min N CTAs; the
+// surplus exits).  Per line the DFT coefficients (float32, exact twiddle
+// indices), then the trigonometric interpolant (eq. interFreq) at the line's
+// positions alpha . u_S + beta . w_T + gamma (float64 positions, float32
+// evaluation by a recurrence from e^{2 pi i x / N}); positions outside the old
+// box give 0.  Buffers: pass 0 buf[cur] -> buf[cur ^ 1], pass 1 back, pass 2
+// buf[cur] -> buf[cur ^ 1] with pscale (k_copy3 then copies it back).
+constexpr int kShearT = 128;   // threads per line CTA (N <= 128)
+
+__global__ void __launch_bounds__(kShearT) k_shear3p(const __grid_constant__ Batch3 b, int pass) {
+  __shared__ float fl[128], cs[128], sn[128], Xr[65], Xi[65];
+  int blk, cnt;
+  const Job3& job = job_at(b, find_job(b, kKindShear, blockIdx.x, &blk, &cnt));
+  const Update3* up = job.up;
+  if (up->skip || !up->realign || up->shear[24] == 0.0) return;
+  const FrameState& f = job.st->f;
+  const double* pc = up->shear + 8 * pass;
+  const int a = (int)pc[0];
+  const int o1 = a == 0 ? 1 : 0, o2 = a == 2 ? 1 : 2;
+  const int N = job.g.N[a], H = N / 2, N1 = job.g.N[o1], N2 = job.g.N[o2];
+  if (blk >= N1 * N2) return;
+  const int i1 = blk / N2, i2 = blk % N2;
+  const long long stride[3] = {(long long)job.g.N[1] * job.g.N[2], job.g.N[2], 1};
+  const long long base = i1 * stride[o1] + i2 * stride[o2], sa = stride[a];
+  float* bc = f.cur ? job.buf1 : job.buf0;
+  float* bn = f.cur ? job.buf0 : job.buf1;
+  const float* in = pass == 1 ? bn : bc;
+  float* out = pass == 1 ? bc : bn;
+  for (int t = threadIdx.x; t < N; t += kShearT) {
+    fl[t] = in[base + t * sa];
+    sincospif(2.0f * (float)t / (float)N, &sn[t], &cs[t]);
+  }
+  __syncthreads();
+  for (int sidx = threadIdx.x; sidx <= H; sidx += kShearT) {
+    float re = 0.0f, im = 0.0f;
+    int r = 0;
+    for (int j = 0; j < N; ++j) {
+      re = fmaf(fl[j], cs[r], re);
+      im = fmaf(-fl[j], sn[r], im);
+      r += sidx;
+      if (r >= N) r -= N;
+    }
+    Xr[sidx] = re / (float)N;
+    Xi[sidx] = im / (float)N;
+  }
+  __syncthreads();
+  const double offset = pc[4] + pc[1 + o1] * (i1 - 0.5 * (N1 - 1)) + pc[1 + o2] * (i2 - 0.5 * (N2 - 1));
+  const float ps = pass == 2 ? (float)f.pscale : 1.0f;
+  for (int t = threadIdx.x; t < N; t += kShearT) {
+    const double pos = offset + pc[1 + a] * (t - 0.5 * (N - 1));
+    float v = 0.0f;
+    if (fabs(pos) <= 0.5 * N) {
+      const double x = pos + 0.5 * (N - 1);
+      float sx, cx;
+      sincospif((float)(2.0 * x / N), &sx, &cx);
+      float zr = 1.0f, zi = 0.0f;   // e^{2 pi i s x / N}
+      v = Xr[0];
+      for (int k = 1; k < H; ++k) {
+        const float nr = zr * cx - zi * sx;
+        zi = zr * sx + zi * cx;
+        zr = nr;
+        v += 2.0f * (Xr[k] * zr - Xi[k] * zi);
+      }
+      v += Xr[H] * cospif((float)x);
+    }
+    out[base + t * sa] = ps * v;
+  }
 }
 
 // =========================== pipeline A (slices) =============================
@@ -1053,7 +1127,7 @@ int tc3_batch(const Tc3Item* items, int n, int precision, Tc3Stage* g, cudaStrea
     jobs = (Job3*)g->h_jobs;
     first = g->h_first;
   }
-  int tot[kKinds] = {0, 0, 0, 0};
+  int tot[kKinds] = {0, 0, 0, 0, 0};
   for (int k = 0; k < kKinds; ++k) first[k * (n + 1)] = 0;
   for (int i = 0; i < n; ++i) {
     const Tc3Item& it = items[i];
@@ -1078,9 +1152,12 @@ int tc3_batch(const Tc3Item* items, int n, int precision, Tc3Stage* g, cudaStrea
     job.mblocks = it.mp ? meas_blocks(it.d.P) : 0;
     if (it.mp) job.mp = *it.mp;
     if (it.tc) job.tc = *it.tc;
+    const int nmin = std::min(it.d.N[0], std::min(it.d.N[1], it.d.N[2]));
+    const bool shear = it.tc && it.tc->realign_mode == PMF_REALIGN_SHEAR;
     const int cnt[kKinds] = {it.mp ? meas_blocks(it.d.P) : 0,
                              it.tc ? (int)std::min<long long>(2048, (it.d.P + kT - 1) / kT) : 0,
-                             it.tc ? it.d.N[0] : 0, it.tc ? (it.d.N[1] / 2 + 1) * job.chunks : 0};
+                             it.tc ? it.d.N[0] : 0, it.tc ? (it.d.N[1] / 2 + 1) * job.chunks : 0,
+                             shear ? (int)(it.d.P / nmin) : 0};
     for (int k = 0; k < kKinds; ++k) {
       tot[k] += cnt[k];
       first[k * (n + 1) + i + 1] = tot[k];
@@ -1108,6 +1185,10 @@ int tc3_batch(const Tc3Item* items, int n, int precision, Tc3Stage* g, cudaStrea
   ++launches;
   if (tot[kKindSlices]) {
     k_realign3<<<tot[kKindPoints], kT, 0, s>>>(b);
+    if (tot[kKindShear]) {
+      for (int pass = 0; pass < 3; ++pass) k_shear3p<<<tot[kKindShear], kShearT, 0, s>>>(b, pass);
+      launches += 3;
+    }
     k_copy3<<<tot[kKindPoints], kT, 0, s>>>(b);
     if (precision == PMF_PREC_FP16X3) launch_pipes<PMF_PREC_FP16X3>(b, tot, s);
     else if (precision == PMF_PREC_BF16X3) launch_pipes<PMF_PREC_BF16X3>(b, tot, s);

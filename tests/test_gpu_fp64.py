@@ -104,8 +104,3 @@ def test_3d_shear_realignment_path():
     assert sum(s.endswith("R") for s, _ in log) >= 2, "re-alignment not exercised"
     _check(worst, 1e-11)
 
-
-def test_3d_shear_only_on_the_float64_path():
-    from paper_2412_07240_gb300 import Filter, Unsupported
-    with pytest.raises(Unsupported):
-        Filter(_cv3("shear", N=(32, 32, 16)).cfg, precision="fp16x3")

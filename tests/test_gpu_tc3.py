@@ -83,3 +83,12 @@ def test_small_3d_bearing_other_precisions(prec, bar):
     worst, _ = max_errors(w.small_3d_scenario(N=(16, 32, 48), epochs=3), precision=prec)
     assert worst["l1"] <= bar, worst
     assert worst["mean"] <= bar, worst
+
+
+def test_3d_shear_realignment_fp16x3():
+    """Band-limited re-alignment in the 3-D pipelines (three batched line-wise
+    passes in float32) against the oracle's passes."""
+    from tests.test_gpu_fp64 import _cv3
+    worst, log = max_errors(_cv3("shear", N=(32, 32, 16)), precision="fp16x3")
+    assert sum(s.endswith("R") for s, _ in log) >= 2, "re-alignment not exercised"
+    _check(worst)
