@@ -1155,7 +1155,7 @@ int tc3_batch(const Tc3Item* items, int n, int precision, Tc3Stage* g, cudaStrea
     const int nmin = std::min(it.d.N[0], std::min(it.d.N[1], it.d.N[2]));
     const bool shear = it.tc && it.tc->realign_mode == PMF_REALIGN_SHEAR;
     const int cnt[kKinds] = {it.mp ? meas_blocks(it.d.P) : 0,
-                             it.tc ? (int)std::min<long long>(2048, (it.d.P + kT - 1) / kT) : 0,
+                             it.tc ? (int)std::min<long long>(304, (it.d.P + kT - 1) / kT) : 0,
                              it.tc ? it.d.N[0] : 0, it.tc ? (it.d.N[1] / 2 + 1) * job.chunks : 0,
                              shear ? (int)(it.d.P / nmin) : 0};
     for (int k = 0; k < kKinds; ++k) {
