@@ -156,10 +156,17 @@ __device__ inline void frame_substep(const TimeConsts& tc, const double* Mpi, in
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double lget(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
-// Regrid decision in lanes for any n <= 4 (both branches): lane e < n*n holds
-// matrix entry (e / n, e % n), lanes < n per-axis values; the products, the
-// Cholesky factor (column by column) and the inverse (adjugate) of the new
-// axes run in parallel lanes.  Same quantities as frame_scalar; used for the
+// Regrid decision of one time update in lanes, for any n <= 4 (both
+// branches).  From the current moments and frame: the pulled-back predicted
+// covariance e^{-A tau} P_pred e^{-A^T tau} = cov + Q_b, its whitened
+// correlation in the frame, and either the separable rescale/recentre
+// (M' = M D, centre moved towards the mean by a multiple of 1/64 node, D with
+// an 8-bit mantissa) or a re-aligned frame M' = e^{-A tau} chol(P_pred)
+// diag(2 span / N) with 12-bit entries.  Writes the regrid map into st, the
+// inverse of M' into Mpi and the pending frame after the move by e^{A tau}
+// into pend (offsets pend_*).  Lane e < n*n holds matrix entry (e / n, e % n),
+// lanes < n per-axis values; the products, the Cholesky factor (column by
+// column) and the inverse (adjugate) run in parallel lanes.  Used for the
 // re-alignment branch and for n = 4.
 template <int n>
 __device__ inline void frame_warp_full(const TimeConsts& tc, FrameState* st, double* pend, double* Mpi) {
