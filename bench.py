@@ -160,8 +160,8 @@ def _launch_names(sc):
 # TimeConsts of its time update (32 + 5 x 16 x 8 + 64 x 10 x 8 + 5 x 8 bytes).
 STEP_ITEM_BYTES = 32
 TIME_CONSTS_BYTES = 5832
-TRAFFIC_C2 = 346880.0
-TRAFFIC_C4_PER_POINT = (59654912.0 + 9783296.0) / 10976512.0
+TRAFFIC_C2 = 345344.0
+TRAFFIC_C4_PER_POINT = (50111744.0 + 7359488.0) / 10976512.0
 
 
 def _flops_per_step(N):
