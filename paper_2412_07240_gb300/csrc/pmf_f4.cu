@@ -35,12 +35,11 @@ namespace {
 
 constexpr int kMaxN4 = 64;
 constexpr int kCols = 64;               // lines per block of the axis transform
-constexpr int kAxisThreads = 256;       // four threads per line (output groups q, q + 4)
 constexpr int kColStr = kCols + 1;      // shared stride of a tile row (conflict-free column reads)
 
 __host__ __device__ inline int kpad(int N) { return (N + 7) & ~7; }
 
-size_t axis_smem(int N) { return sizeof(float) * (2 * (size_t)N * kColStr + (size_t)N * kpad(N)); }
+size_t axis_smem(int N) { return sizeof(float) * (size_t)kpad(N) * (kColStr + kpad(N)); }
 
 // ---- double-float helpers ---------------------------------------------------
 __device__ __forceinline__ DF df_of(double x) {
@@ -428,15 +427,21 @@ __global__ void __launch_bounds__(256) k_f4_realign(Dims d, const DevState* st, 
 
 // Y = W x_axis X on the float32 grid viewed as [outer][N][inner] (C order):
 // a block takes kCols consecutive lines along the axis (line = (outer, inner)
-// pair) and stages them as a [N][kCols] tile; thread (line c, quarter q)
-// forms the outputs k of groups q, q + 4 (8 accumulators per group), the 8
-// weights of a group being two float4 broadcasts of W^T.  Reads
-// bufs[(cur+stage)&1], writes the other one.  Indices fit 32 bits (N <= 64).
-__global__ void __launch_bounds__(kAxisThreads) k_f4_axis(Dims d, int axis, const float* WT,
-                                                          const DevState* st, int stage, float* b0,
-                                                          float* b1) {
+// pair) and stages them as a [Kp][kCols] tile; the block has G = Kp / 8
+// threads per line, thread (line c, group q) forming the outputs k = 8 q ..
+// 8 q + 7 (the 8 weights of a step two float4 broadcasts of W^T), so every
+// thread does the same work.  Kp = 8 G is a template parameter: the loop over
+// j is unrolled with constant shared-memory offsets, rows N .. Kp - 1 of the
+// tile and of W^T are zero (their terms add exact zeros).  Tile loads and the
+// stores of y_k from registers are runs of consecutive floats when inner >=
+// kCols (axes 0 and 1).  Reads bufs[(cur+stage)&1], writes the other one.
+// Indices fit 32 bits (N <= 64).
+template <int G>
+__global__ void __launch_bounds__(kCols * G) k_f4_axis(Dims d, int axis, const float* WT, const DevState* st,
+                                                       int stage, float* b0, float* b1) {
+  constexpr int Kp = 8 * G, kThreads = kCols * G;
   extern __shared__ __align__(16) float sm[];
-  const int N = d.N[axis], Kp = kpad(N);
+  const int N = d.N[axis];
   int inner = 1;
 #pragma unroll
   for (int m = 1; m < 4; ++m)
@@ -444,64 +449,61 @@ __global__ void __launch_bounds__(kAxisThreads) k_f4_axis(Dims d, int axis, cons
   const int lines = (int)d.P / N;
   const int l0 = blockIdx.x * kCols;
   const int nl = min(kCols, lines - l0);
-  float* Xs = sm;
-  float* Ys = sm + N * kColStr;
-  float* Ws = Ys + N * kColStr;
+  float* Ws = sm;                 // [Kp][Kp]: float4 rows stay 16-byte aligned
+  float* Xs = sm + Kp * Kp;       // [Kp][kColStr]
   const int par = (st->f.cur + stage) & 1;
   const float* X = par ? b1 : b0;
   float* Y = par ? b0 : b1;
   const int tid = threadIdx.x;
-  for (int i = tid; i < N * Kp; i += kAxisThreads) Ws[i] = WT[i];
-  // line c of the tile starts at element base(c) and steps by inner; one
-  // division per thread (each thread keeps its column in both copy loops)
-  const int cc = tid % kCols, jq = tid / kCols;
-  constexpr int kJStep = kAxisThreads / kCols;
+  for (int i = tid; i < Kp * Kp; i += kThreads) Ws[i] = i < N * Kp ? WT[i] : 0.0f;
+  const int c = tid % kCols, q = tid / kCols;
   int cbase = 0;
-  if (inner > 1 && cc < nl) {
-    const int ln = l0 + cc, o = ln / inner;
+  if (c < nl) {
+    const int ln = l0 + c, o = ln / inner;
     cbase = o * N * inner + (ln - o * inner);
   }
-  if (inner == 1) {
-    // contiguous lines: one warp per line, lanes along it
-    const float* src = X + l0 * N;
-    for (int c = tid >> 5; c < nl; c += kAxisThreads / 32)
-      for (int j = tid & 31; j < N; j += 32) Xs[j * kColStr + c] = src[c * N + j];
-  } else if (cc < nl) {
-    for (int j = jq; j < N; j += kJStep) Xs[j * kColStr + cc] = X[cbase + j * inner];
-  }
-  __syncthreads();
-  const int c = cc, q = jq;
-  if (c < nl) {
-    for (int k0 = 8 * q; k0 < N; k0 += 8 * kJStep) {
-      float acc[8];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) acc[r] = 0.0f;
-#pragma unroll 2
-      for (int j = 0; j < N; ++j) {
-        const float x = Xs[j * kColStr + c];
-        const float4 w0 = *(const float4*)(Ws + j * Kp + k0);
-        const float4 w1 = *(const float4*)(Ws + j * Kp + k0 + 4);
-        acc[0] = fmaf(w0.x, x, acc[0]);
-        acc[1] = fmaf(w0.y, x, acc[1]);
-        acc[2] = fmaf(w0.z, x, acc[2]);
-        acc[3] = fmaf(w0.w, x, acc[3]);
-        acc[4] = fmaf(w1.x, x, acc[4]);
-        acc[5] = fmaf(w1.y, x, acc[5]);
-        acc[6] = fmaf(w1.z, x, acc[6]);
-        acc[7] = fmaf(w1.w, x, acc[7]);
-      }
-#pragma unroll
-      for (int r = 0; r < 8; ++r)
-        if (k0 + r < N) Ys[(k0 + r) * kColStr + c] = acc[r];
-    }
-  }
+  for (int j = q; j < Kp; j += G) Xs[j * kColStr + c] = (c < nl && j < N) ? X[cbase + j * inner] : 0.0f;
   __syncthreads();
-  if (inner == 1) {
-    float* dst = Y + l0 * N;
-    for (int c = tid >> 5; c < nl; c += kAxisThreads / 32)
-      for (int j = tid & 31; j < N; j += 32) dst[c * N + j] = Ys[j * kColStr + c];
-  } else if (cc < nl) {
-    for (int j = jq; j < N; j += kJStep) Y[cbase + j * inner] = Ys[j * kColStr + cc];
+  if (c >= nl) return;
+  const float* xs = Xs + c;
+  const float* ws = Ws + 8 * q;
+  float acc[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) acc[r] = 0.0f;
+#pragma unroll
+  for (int j = 0; j < Kp; ++j) {
+    const float x = xs[j * kColStr];
+    const float4 w0 = *(const float4*)(ws + j * Kp);
+    const float4 w1 = *(const float4*)(ws + j * Kp + 4);
+    acc[0] = fmaf(w0.x, x, acc[0]);
+    acc[1] = fmaf(w0.y, x, acc[1]);
+    acc[2] = fmaf(w0.z, x, acc[2]);
+    acc[3] = fmaf(w0.w, x, acc[3]);
+    acc[4] = fmaf(w1.x, x, acc[4]);
+    acc[5] = fmaf(w1.y, x, acc[5]);
+    acc[6] = fmaf(w1.z, x, acc[6]);
+    acc[7] = fmaf(w1.w, x, acc[7]);
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+    if (8 * q + r < N) Y[cbase + (8 * q + r) * inner] = acc[r];
+}
+
+void launch_axis(const Dims& d, int a, const float* WT, const DevState* st, int stage, float* b0, float* b1,
+                 cudaStream_t s) {
+  const int lines = (int)(d.P / d.N[a]), G = kpad(d.N[a]) / 8;
+  const unsigned blocks = (unsigned)((lines + kCols - 1) / kCols);
+  const size_t smem = axis_smem(d.N[a]);
+  switch (G) {
+    case 1: k_f4_axis<1><<<blocks, kCols * 1, smem, s>>>(d, a, WT, st, stage, b0, b1); break;
+    case 2: k_f4_axis<2><<<blocks, kCols * 2, smem, s>>>(d, a, WT, st, stage, b0, b1); break;
+    case 3: k_f4_axis<3><<<blocks, kCols * 3, smem, s>>>(d, a, WT, st, stage, b0, b1); break;
+    case 4: k_f4_axis<4><<<blocks, kCols * 4, smem, s>>>(d, a, WT, st, stage, b0, b1); break;
+    case 5: k_f4_axis<5><<<blocks, kCols * 5, smem, s>>>(d, a, WT, st, stage, b0, b1); break;
+    case 6: k_f4_axis<6><<<blocks, kCols * 6, smem, s>>>(d, a, WT, st, stage, b0, b1); break;
+    case 7: k_f4_axis<7><<<blocks, kCols * 7, smem, s>>>(d, a, WT, st, stage, b0, b1); break;
+    default: k_f4_axis<8><<<blocks, kCols * 8, smem, s>>>(d, a, WT, st, stage, b0, b1); break;
   }
 }
 
@@ -782,9 +784,9 @@ int f4_alloc(const pmf_config* cfg, F4Tables* t) {
     ok = ok && cudaMemcpy(t->winv[a], WT.data(), sizeof(float) * N * Kp, cudaMemcpyHostToDevice) == cudaSuccess;
   }
   if (ok) {
-    const int smem = (int)axis_smem(kMaxN4), ssm = (int)slab_smem(kMaxN4, kMaxN4);
-    ok = cudaFuncSetAttribute(k_f4_axis, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
-         cudaFuncSetAttribute(k_f4_slab23<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm) ==
+    // the axis tiles need at most 64 x (65 + 64) floats = 33 KB (no opt-in)
+    const int ssm = (int)slab_smem(kMaxN4, kMaxN4);
+    ok = cudaFuncSetAttribute(k_f4_slab23<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm) ==
              cudaSuccess &&
          cudaFuncSetAttribute(k_f4_slab23<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm) == cudaSuccess;
   }
@@ -830,12 +832,7 @@ int f4_time(const Dims& d, const TimeConsts& tc, DevState* st, const F4Tables& t
   k_f4_tables<<<dim3(maxN, 4), 64, 0, s>>>(d, st, t);
   k_f4_realign<<<grid_cap(d.P / d.N[3], 512 / d.N[3], 4096), 256, 0, s>>>(d, st, b0, b1);
   int stage = 1;
-  auto axis = [&](int a, const float* WT) {
-    const long long lines = d.P / d.N[a];
-    k_f4_axis<<<(unsigned)((lines + kCols - 1) / kCols), kAxisThreads, axis_smem(d.N[a]), s>>>(d, a, WT, st,
-                                                                                              stage, b0, b1);
-    ++stage;
-  };
+  auto axis = [&](int a, const float* WT) { launch_axis(d, a, WT, st, stage++, b0, b1, s); };
   const int nslab = (d.N[0] * d.N[1] + kSlabs - 1) / kSlabs;
   const size_t ssm = slab_smem(d.N[2], d.N[3]);
   k_f4_slab23<false><<<nslab, kSlabThreads, ssm, s>>>(d, t.wfwd[3], t.wfwd[2], st, stage++, b0, b1, nullptr);
