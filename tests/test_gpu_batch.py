@@ -1,6 +1,7 @@
 """Batched filters: one launch per epoch, one CTA per filter, mixed grid sizes.
 
-* every filter of a batch equals the same filter run alone (same kernel body);
+* every filter of a batch equals the same filter run alone (same kernel body),
+  in FP16X3, BF16X3 and TF32 and with the exact-in-time multiplier;
 * sampled filters equal the float64 oracle within the FP16X3 bar (1e-5);
 * the full 4096-filter workload in the benchmarked launch configuration keeps
   unit mass, finite weights and PSD covariances, and its sampled filters match
@@ -21,11 +22,15 @@ def _c4(count, epochs, seed=4):
     return cfgs, meas, dt, z
 
 
-def test_batch_equals_single_filters():
+@pytest.mark.parametrize("prec,psi", [("fp16x3", "euler"), ("bf16x3", "euler"), ("tf32", "euler"),
+                                      ("fp16x3", "exact")])
+def test_batch_equals_single_filters(prec, psi):
+    """Bit-identical to the same filters run alone, in every precision and both
+    multipliers (the single-filter path meets the oracle at those bars)."""
     from paper_2412_07240_gb300 import Batch, Filter
     cfgs, meas, dt, z = _c4(10, 4)
-    b = Batch(cfgs, [meas] * len(cfgs))
-    singles = [Filter(c, precision="fp16x3") for c in cfgs]
+    b = Batch(cfgs, [meas] * len(cfgs), precision=prec, psi_mode=psi)
+    singles = [Filter(c, precision=prec, psi_mode=psi) for c in cfgs]
     ids = np.arange(len(cfgs))
     for k in range(4):
         b.step(ids, z[:, k], dt)
