@@ -817,18 +817,35 @@ __global__ void __launch_bounds__(kT, 1) k_lines_axis0(const __grid_constant__ B
       for (int s = 0; s < 8; ++s) {
         const int L = ((s >> 1) & 1) * 64 + ((s >> 2) & 1) * 32 + i;
         Sv[s] = S[L * kSStr + col[s & 1]];
-        const int a0 = col[s & 1], a1 = lk1[L], a2 = lk2[L];
+      }
+      // Over the orbit the squared wavenumbers are fixed and a flipped index
+      // negates the first-derivative coefficient (zero at 0 and N/2), so the
+      // sub-step exponent of pattern s is E + s01 X01 + s02 X02 + s12 X12 with
+      // s_ab = sigma_a sigma_b: four distinct values (s and s ^ 7 agree), formed
+      // from one read of the sub-step coefficients.  Magnitudes from pattern 0.
+      {
+        const int a0 = k0, a1 = lk1[i], a2 = lk2[i];
         const int w0 = a0 < N0 / 2 ? a0 : a0 - N0, w1 = a1 < N1 / 2 ? a1 : a1 - N1, w2 = a2 < N2 / 2 ? a2 : a2 - N2;
         const float q0 = two_pi * w0 / N0, q1 = two_pi * w1 / N1, q2 = two_pi * w2 / N2;
         const float t0 = (2 * a0 == N0) ? 0.0f : q0, t1 = (2 * a1 == N1) ? 0.0f : q1, t2 = (2 * a2 == N2) ? 0.0f : q2;
-        float den = 1.0f, ex = 0.0f;
+        const float q00 = q0 * q0, q11 = q1 * q1, q22 = q2 * q2, c01 = t0 * t1, c02 = t0 * t2, c12 = t1 * t2;
+        float den[4] = {1.0f, 1.0f, 1.0f, 1.0f}, ex[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         for (int qq = 0; qq < l; ++qq) {
-          const float e = spa[qq][0] * q0 * q0 + spa[qq][1] * q1 * q1 + spa[qq][2] * q2 * q2 +
-                          spb[qq][0] * t0 * t1 + spb[qq][1] * t0 * t2 + spb[qq][2] * t1 * t2;
-          den *= 1.0f + e;
-          ex += e;
+          const float E = spa[qq][0] * q00 + spa[qq][1] * q11 + spa[qq][2] * q22;
+          const float x01 = spb[qq][0] * c01, x02 = spb[qq][1] * c02, x12 = spb[qq][2] * c12;
+          // patterns 0 (no flip), 1 (k0), 2 (k1), 3 (k0 and k1)
+          const float e[4] = {E + x01 + x02 + x12, E - x01 - x02 + x12, E - x01 + x02 - x12, E + x01 - x02 - x12};
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            den[h] *= 1.0f + e[h];
+            ex[h] += e[h];
+          }
         }
-        Ps[s] = exact ? expf(-ex) : __frcp_rn(den);
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const int h = s < 4 ? s : s ^ 7;
+          Ps[s] = exact ? expf(-ex[h]) : __frcp_rn(den[h]);
+        }
       }
       float Tb[8], Pe[8], Tp[8];
 #pragma unroll

@@ -2,7 +2,7 @@
 
 Cases: non-cubic grids whose axis-0 line tiles are ragged (N2/2 + 1 not a
 multiple of 32), the bearing + linear measurement, a linear 3-D model with a
-sheared frame, and the full 96^3 workload.  Bar: FP16X3 relative L1 <= 1e-5.
+sheared frame, the exact-in-time multiplier, and the full 96^3 workload.  Bar: FP16X3 relative L1 <= 1e-5.
 """
 import numpy as np
 import pytest
@@ -37,6 +37,12 @@ def test_3d_linear_fp16x3():
     sc = Scenario("lin3", cfg, meas, dt=0.1, epochs=3)
     sc.truth, sc.z = simulate(cfg, meas, sc.dt, sc.epochs, seed=22)
     worst, _ = max_errors(sc, precision="fp16x3")
+    _check(worst)
+
+
+def test_3d_exact_multiplier_fp16x3():
+    # the exact-in-time multiplier on the 8-point orbits (cross terms of both signs)
+    worst, _ = max_errors(w.small_3d_scenario(N=(32, 48, 80), epochs=3), precision="fp16x3", psi_mode="exact")
     _check(worst)
 
 
