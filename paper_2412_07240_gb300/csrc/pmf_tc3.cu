@@ -288,8 +288,10 @@ struct Meas3 {
 };
 
 __device__ __forceinline__ float wrapf(float r) {
+  // at an exact +-pi boundary either branch gives the same squared residual
   const float two_pi = 6.28318530717958647692f, pi = 3.14159265358979323846f;
-  return r - two_pi * ceilf((r - pi) / two_pi);
+  const float inv_two_pi = 0.15915494309189533577f;
+  return r - two_pi * ceilf((r - pi) * inv_two_pi);
 }
 
 // 1/2 r^T R^{-1} r, residual relative to the frame centre (d = M u):
@@ -339,11 +341,12 @@ __device__ void meas_consts(const MeasParams& mp, const FrameState& fs, Meas3& m
   }
 }
 
+// Point index -> (j0, j1, j2); 32-bit arithmetic (P <= 128^3 < 2^31).
 __device__ __forceinline__ void unflat3(const Geo3& g, long long p, int* j) {
-  j[2] = (int)(p % g.N[2]);
-  p /= g.N[2];
-  j[1] = (int)(p % g.N[1]);
-  j[0] = (int)(p / g.N[1]);
+  const int i = (int)p, t = i / g.N[2];
+  j[2] = i - t * g.N[2];
+  j[1] = t % g.N[1];
+  j[0] = t / g.N[1];
 }
 
 __global__ void __launch_bounds__(kT) k_meas_min3(const __grid_constant__ Batch3 b) {
