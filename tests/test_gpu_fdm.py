@@ -1,6 +1,6 @@
 """Finite-difference comparator on the GPU (eq. fdiff / eq. FST): parity with
 the oracle, second-order convergence, and the spectral method's accuracy per
-grid point against it (the Gaussian FPE closed form as the judge)."""
+grid point against it (the Gaussian FPE closed form as the arbiter)."""
 import numpy as np
 import pytest
 
