@@ -4,8 +4,10 @@
 //   meas   M1 exponent minimum, M2 likelihood multiply + moment partials,
 //          F  moments, normaliser, frame (float64), sub-step coefficients,
 //             regrid rows of the three axes
-//   time   [realign gather + copy-back when the frame is re-aligned]
-//          A  per slice j0: regrid + Hartley along axes 2 and 1 (4 GEMMs) -> T
+//   time   [realign gather + copy-back when the frame is re-aligned; when it
+//             is kept, the folded forward matrices W_a = H_a I_a instead]
+//          A  per slice j0: regrid + Hartley along axes 2 and 1, one GEMM per
+//             axis with W_a (H_a after a re-alignment) -> T
 //          B  per tile of 128 lines along axis 0, closed under sign flips
 //             ({k1, -k1} x (C u -C)): regrid + Hartley along axis 0, the 3-D
 //             diffusion multiplier with the separable-to-3-D parity fix-up on
@@ -47,6 +49,7 @@ struct Update3 {
   float gsc;                 // trace factor / (N0 N1 N2)
   RegridRows rows[3];        // regrid rows per axis
   double shear[25];          // band-limited re-alignment passes (shear3_setup layout)
+  unsigned int wmax[3];      // float bits of max |W_a| of the folded forward matrices
 };
 
 struct Job3 {
@@ -60,6 +63,7 @@ struct Job3 {
   unsigned int* emin_bits;   // float bits of the exponent minimum
   Update3* up;               // device
   double* pend;              // pending frame (device)
+  float* fold;               // folded forward matrices W_a = H_a I_a: [3][128][128], rows k, columns j
   int precision;
   int flags;                 // this epoch: bit 0 measurement update, bit 1 time update
   int chunks;                // axis-0 line tiles: chunks of 32 k2 per k1
@@ -510,6 +514,7 @@ __global__ void __launch_bounds__(kT) k_frame3(const __grid_constant__ Batch3 b)
       up->realign = fs.realign;
       up->gsc = (float)(fs.g / ((double)job.g.N[0] * job.g.N[1] * job.g.N[2]));
       up->shear[24] = 0.0;
+      for (int a = 0; a < 3; ++a) up->wmax[a] = 0u;
       if (fs.realign && tc.realign_mode == PMF_REALIGN_SHEAR && !shear3_setup(fs, up->shear))
         fs.status = PMF_ERR_DEGENERATE;
     }
@@ -521,13 +526,122 @@ __global__ void __launch_bounds__(kT) k_frame3(const __grid_constant__ Batch3 b)
   if (threadIdx.x == 0) *job.emin_bits = 0x7f7f7f7fu;   // re-armed for the next measurement update
 }
 
+// Folded forward matrices of a kept frame: W_a[k][j] = sum_n H_a[k][n] I_a[n][j]
+// with H_a the unnormalised Hartley matrix cas(2 pi k n / N) and I_a the
+// periodic-sinc regrid matrix of eq. interFreq (rows: new nodes n, columns:
+// old nodes j), so the slice and tile kernels apply the regrid and the
+// forward transform of an axis as one GEMM.  A unit is (axis, 8 rows k); the
+// four 128-thread groups of the CTA sum quarters of n for column j (float32),
+// and the unit's max |W| goes to wmax[a] (the operand scale of the consumers).
+constexpr int kFoldRows = 8;
+
+__device__ __forceinline__ int fold_units(const Geo3& g) {
+  return (g.N[0] + kFoldRows - 1) / kFoldRows + (g.N[1] + kFoldRows - 1) / kFoldRows +
+         (g.N[2] + kFoldRows - 1) / kFoldRows;
+}
+
+__device__ void fold_unit(const Job3& job, int u) {
+  __shared__ float hs[kFoldRows][128];
+  __shared__ float part[4][kFoldRows][128];
+  __shared__ float bmax[kT / 32];
+  __shared__ RegridRows rows;
+  int a = 0;
+  while (a < 2 && u >= (job.g.N[a] + kFoldRows - 1) / kFoldRows) {
+    u -= (job.g.N[a] + kFoldRows - 1) / kFoldRows;
+    ++a;
+  }
+  const int N = job.g.N[a], k0 = u * kFoldRows;
+  const float* sct = job.sctab[a];
+  {
+    // the axis' regrid row parameters, read by every thread for every n
+    const unsigned int* src = (const unsigned int*)&job.up->rows[a];
+    unsigned int* dst = (unsigned int*)&rows;
+    for (int i = threadIdx.x; i < (int)(sizeof(RegridRows) / 4); i += kT) dst[i] = src[i];
+  }
+  // H rows k0 .. k0 + kFoldRows - 1 from the (cos, sin)(pi m / N) table: cas(2 pi r / N), r = k n mod N
+  for (int t = threadIdx.x; t < kFoldRows * N; t += kT) {
+    const int kr = t / N, n = t - kr * N, k = k0 + kr;
+    float h = 0.0f;
+    if (k < N) {
+      const int r = (k * n) % N, m = 2 * r <= N ? 2 * r : 2 * r - 2 * N;
+      h = sct[2 * (m + N)] + sct[2 * (m + N) + 1];
+    }
+    hs[kr][n] = h;
+  }
+  __syncthreads();
+  const int grp = threadIdx.x >> 7, j = threadIdx.x & 127;
+  const int q = (N + 3) / 4, nb = grp * q, ne = min(N, nb + q);
+  float acc[kFoldRows];
+#pragma unroll
+  for (int r = 0; r < kFoldRows; ++r) acc[r] = 0.0f;
+  if (j < N)
+    for (int n = nb; n < ne; ++n) {
+      const float x = interp_value(regrid_row(rows, n), j, N, sct);
+#pragma unroll
+      for (int r = 0; r < kFoldRows; ++r) acc[r] = fmaf(hs[r][n], x, acc[r]);
+    }
+#pragma unroll
+  for (int r = 0; r < kFoldRows; ++r) part[grp][r][j] = acc[r];
+  __syncthreads();
+  float m = 0.0f;
+  float* dst = job.fold + (size_t)a * 128 * 128;
+  for (int t = threadIdx.x; t < kFoldRows * 128; t += kT) {
+    const int kr = t >> 7, jj = t & 127, k = k0 + kr;
+    if (k < N && jj < N) {
+      const float w = (part[0][kr][jj] + part[1][kr][jj]) + (part[2][kr][jj] + part[3][kr][jj]);
+      dst[k * 128 + jj] = w;
+      m = fmaxf(m, fabsf(w));
+    }
+  }
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) bmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float v = 0.0f;
+    for (int w = 0; w < kT / 32; ++w) v = fmaxf(v, bmax[w]);
+    atomicMax(&job.up->wmax[a], __float_as_uint(v));
+  }
+  __syncthreads();   // the shared arrays are reused by the CTA's next unit
+}
+
+// Folded matrix of axis a into the W planes, scaled by a power of two (16-bit
+// float: max |W| into [2^14, 2^15), the exponent capped as for the data
+// operands); returns the scale.  Consecutive threads take consecutive rows.
+template <int P>
+__device__ float load_fold(const Job3& job, int a, uint8_t* W) {
+  const int N = job.g.N[a];
+  float sc = 1.0f;
+  if (P == PMF_PREC_FP16X3) {
+    const float wmax = __uint_as_float(job.up->wmax[a]);
+    if (wmax > 0.0f && wmax < INFINITY) {
+      int e;
+      frexpf(wmax, &e);
+      sc = ldexpf(1.0f, min(15 - e, 100));
+    }
+  }
+  const float* src = job.fold + (size_t)a * 128 * 128;
+  const int q4 = N / 4;
+  for (int t = threadIdx.x; t < N * q4; t += kT) {
+    const int n = t % N, c = (t / N) * 4;
+    store4<P>(W, n, c, *(const float4*)(src + n * 128 + c), sc);
+  }
+  return sc;
+}
+
 // Multilinear re-alignment (only when the frame kernel decided it): gather
-// buf[cur] -> buf[cur^1] with pscale folded in; k_copy3 copies it back.
+// buf[cur] -> buf[cur^1] with pscale folded in; k_copy3 copies it back.  When
+// the frame was kept, the CTAs form the folded forward matrices instead.
 __global__ void __launch_bounds__(kT) k_realign3(const __grid_constant__ Batch3 b) {
   int blk, cnt;
   const Job3& job = job_at(b, find_job(b, kKindPoints, blockIdx.x, &blk, &cnt));
   const FrameState& f = job.st->f;
-  if (job.up->skip || !job.up->realign || job.tc.realign_mode == PMF_REALIGN_SHEAR) return;
+  if (job.up->skip) return;
+  if (!job.up->realign) {
+    const int units = fold_units(job.g);
+    for (int u = blk; u < units; u += cnt) fold_unit(job, u);
+    return;
+  }
+  if (job.tc.realign_mode == PMF_REALIGN_SHEAR) return;
   const Geo3& g = job.g;
   const float* in = f.cur ? job.buf1 : job.buf0;
   float* out = f.cur ? job.buf0 : job.buf1;
@@ -646,7 +760,7 @@ __global__ void __launch_bounds__(kShearT) k_shear3p(const __grid_constant__ Bat
 
 // =========================== pipeline A (slices) =============================
 // Slice j0 of buf[cur] (rows j1, columns j2) -> regrid + Hartley along axis 2,
-// then axis 1 -> T[j0][k1][k2] in buf[cur^1].
+// then axis 1 (one GEMM each) -> T[j0][k1][k2] in buf[cur^1].
 template <int P>
 __global__ void __launch_bounds__(kT, 1) k_slices_fwd(const __grid_constant__ Batch3 b) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -683,30 +797,20 @@ __global__ void __launch_bounds__(kT, 1) k_slices_fwd(const __grid_constant__ Ba
   }
   float sa = op_scale<P>(block_max3(sh, m, 0));
   stage_to_op<P>(A, S, N1, N2, sa);
-  build_interp<P>(up->rows[2], W, N2, job.sctab[2], sw, realign, threadIdx.x, kT);
+  // regrid and transform of an axis in one GEMM: the folded matrix of a kept
+  // frame, the Hartley matrix after a re-alignment (the gather moved the weights)
+  float wsc = realign ? sw : load_fold<P>(job, 2, W);
   fence_async_smem();
   __syncthreads();
-  pipe_issue<P>(sh, p, A, W, nullptr, 0, 0, N2, N2);                        // R2
-  float inv = 1.0f / (sa * sw);
-  if (!pipe_wait(sh, p)) goto fail;
-  sa = acc_to_operand<P>(sh, p, A, N1, N2, inv, false, 1);                  // rows j1, cols j2'
-  fence_async_smem();
-  __syncthreads();
-  pipe_issue<P>(sh, p, A, W, job.hart[2], N2, 0, N2, N2);                   // F2
-  inv = 1.0f / (sa * sw);
+  pipe_issue<P>(sh, p, A, W, realign ? job.hart[2] : nullptr, N2, 0, N2, N2);   // F2 (regrid folded in)
+  float inv = 1.0f / (sa * wsc);
   if (!pipe_wait(sh, p)) goto fail;
   sa = acc_to_operand<P>(sh, p, A, N1, N2, inv, P == PMF_PREC_TF32, 0);     // [j1][k2]: MN-major next
-  build_interp<P>(up->rows[1], W, N1, job.sctab[1], sw, realign, threadIdx.x, kT);
+  wsc = realign ? sw : load_fold<P>(job, 1, W);
   fence_async_smem();
   __syncthreads();
-  pipe_issue<P>(sh, p, A, W, nullptr, 0, P != PMF_PREC_TF32, N1, N1);       // R1: lanes k2
-  inv = 1.0f / (sa * sw);
-  if (!pipe_wait(sh, p)) goto fail;
-  sa = acc_to_operand<P>(sh, p, A, N2, N1, inv, false, 1);                  // [k2][j1'] K-major
-  fence_async_smem();
-  __syncthreads();
-  pipe_issue<P>(sh, p, A, W, job.hart[1], N1, 0, N1, N1);                   // F1: lanes k2, cols k1
-  inv = 1.0f / (sa * sw);
+  pipe_issue<P>(sh, p, A, W, realign ? job.hart[1] : nullptr, N1, P != PMF_PREC_TF32, N1, N1);   // F1: lanes k2
+  inv = 1.0f / (sa * wsc);
   if (!pipe_wait(sh, p)) goto fail;
   {
     // T[j0][k1][k2]: lane k2, column k1 (consecutive lanes: consecutive addresses)
@@ -786,17 +890,11 @@ __global__ void __launch_bounds__(kT, 1) k_lines_axis0(const __grid_constant__ B
   }
   float sa = op_scale<P>(block_max3(sh, m, 0));
   stage_to_op<P>(A, S, 128, N0, sa);
-  build_interp<P>(up->rows[0], W, N0, job.sctab[0], sw, realign, threadIdx.x, kT);
+  const float wsc = realign ? sw : load_fold<P>(job, 0, W);
   fence_async_smem();
   __syncthreads();
-  pipe_issue<P>(sh, p, A, W, nullptr, 0, 0, N0, N0);                        // R0
-  float inv = 1.0f / (sa * sw);
-  if (!pipe_wait(sh, p)) goto fail;
-  sa = acc_to_operand<P>(sh, p, A, 128, N0, inv, false, 1);
-  fence_async_smem();
-  __syncthreads();
-  pipe_issue<P>(sh, p, A, W, job.hart[0], N0, 0, N0, N0);                   // F0
-  inv = 1.0f / (sa * sw);
+  pipe_issue<P>(sh, p, A, W, realign ? job.hart[0] : nullptr, N0, 0, N0, N0);   // F0 (regrid folded in)
+  float inv = 1.0f / (sa * wsc);
   if (!pipe_wait(sh, p)) goto fail;
   acc_to_stage(p, S, N0, inv);
   __syncthreads();
@@ -895,7 +993,7 @@ __global__ void __launch_bounds__(kT, 1) k_lines_axis0(const __grid_constant__ B
   stage_to_op<P>(A, S, 128, N0, sa);
   fence_async_smem();
   __syncthreads();
-  pipe_issue<P>(sh, p, A, W, nullptr, 0, 0, N0, N0);                        // V0 (H0 resident)
+  pipe_issue<P>(sh, p, A, W, realign ? nullptr : job.hart[0], N0, 0, N0, N0);   // V0 (H0 resident if re-aligned)
   inv = 1.0f / (sa * sw);
   if (!pipe_wait(sh, p)) goto fail;
   {
@@ -1045,6 +1143,7 @@ struct Tc3State {
   double* pend = nullptr;
   DF* partials = nullptr;
   unsigned int* emin = nullptr;
+  float* fold = nullptr;  // folded forward matrices, 3 x 128 x 128
   Tc3Stage stage[2];    // single-filter launches alternate between two stagings
   int parity = 0;
 };
@@ -1055,6 +1154,7 @@ int tc3_alloc(void** handle) {
   if (cudaMalloc(&s->up, sizeof(Update3)) != cudaSuccess || cudaMalloc(&s->pend, 32 * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&s->partials, 16 * 4096 * sizeof(DF)) != cudaSuccess ||
       cudaMalloc(&s->emin, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMalloc(&s->fold, 3 * 128 * 128 * sizeof(float)) != cudaSuccess ||
       cudaMemset(s->emin, 0x7f, sizeof(unsigned int)) != cudaSuccess) {
     tc3_free(s);
     return PMF_ERR_OOM;
@@ -1080,7 +1180,7 @@ int tc3_alloc(void** handle) {
 
 size_t tc3_state_bytes() {
   return sizeof(Update3) + 32 * sizeof(double) + 16 * 4096 * sizeof(DF) + sizeof(unsigned int) +
-         2 * (sizeof(Job3) + (kKinds + 1) * 2 * sizeof(int));
+         3 * 128 * 128 * sizeof(float) + 2 * (sizeof(Job3) + (kKinds + 1) * 2 * sizeof(int));
 }
 
 void tc3_free(void* handle) {
@@ -1090,6 +1190,7 @@ void tc3_free(void* handle) {
   cudaFree(s->pend);
   cudaFree(s->partials);
   cudaFree(s->emin);
+  cudaFree(s->fold);
   tc3_stage_free(&s->stage[0]);
   tc3_stage_free(&s->stage[1]);
   delete s;
@@ -1166,6 +1267,7 @@ int tc3_batch(const Tc3Item* items, int n, int precision, Tc3Stage* g, cudaStrea
     job.emin_bits = h->emin;
     job.up = h->up;
     job.pend = h->pend;
+    job.fold = h->fold;
     job.precision = precision;
     job.flags = (it.mp ? 1 : 0) | (it.tc ? 2 : 0);
     job.chunks = (it.d.N[2] / 2 + 1 + 31) / 32;
