@@ -86,11 +86,12 @@ enum { PMF_PSI_EULER = 0, PMF_PSI_EXACT = 1 };
 /* Fill of a re-aligned frame (the regrid when the frame's whitened
  * correlation exceeds realign_rho; Sec. V grid reshaping).
  *   MULTILINEAR : multilinear interpolation of the old weights (any n_x).
- *   SHEAR       : n_x = 2 or 3: the trigonometric interpolant (eq. interFreq)
- *                 of the old weights at the new nodes, as n line-wise
- *                 passes (per line: DFT, evaluation at that line's affine
- *                 positions); spectrally accurate for densities well inside
- *                 the box. */
+ *   SHEAR       : n_x = 2, 3 or 4: the trigonometric interpolant (eq.
+ *                 interFreq) of the old weights at the new nodes, as n
+ *                 line-wise passes (per line: DFT, evaluation at that line's
+ *                 affine positions); spectrally accurate for densities well
+ *                 inside the box.  For n_x = 4 the float64 path only (the
+ *                 float32 4-D kernels return PMF_ERR_UNSUPPORTED). */
 enum { PMF_REALIGN_MULTILINEAR = 0, PMF_REALIGN_SHEAR = 1 };
 
 /* Form of the per-axis Hartley transforms (step 1 and step 5 of the Sec. V-B

@@ -23,9 +23,9 @@ notes of the repository):
     e^{-A tau}; per-axis rescale + recentre by the trigonometric interpolant
     (eq. interFreq), or, when the whitened correlation of the frame exceeds
     ``realign_rho``, a re-aligned frame filled by multilinear interpolation
-    (default) or, in the band-limited mode (n_x = 2), by two line-wise passes
-    of the trigonometric interpolant (shear_realign); points outside the old
-    box get weight 0;
+    (default) or, in the band-limited mode, by n_x line-wise passes of the
+    trigonometric interpolant (shear_realign, shear_realign_nd); points
+    outside the old box get weight 0;
   * the separable regrid is quantised: the centre moves by a multiple of 1/64
     of a node towards the mean and each axis scale by a factor with an 8-bit
     mantissa, so the grid geometry is exact in any precision and does not
@@ -37,6 +37,7 @@ notes of the repository):
 """
 from __future__ import annotations
 
+import itertools
 import math
 
 import numpy as np
@@ -132,11 +133,17 @@ def shear_realign(P: np.ndarray, B: np.ndarray, b: np.ndarray) -> np.ndarray:
     return np.moveaxis(out, 0, p)
 
 
-SHEAR_ORDERS_3D = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+def shear_orders(n: int) -> tuple:
+    """Axis orders of the n-pass factorisation, in lexicographic order (the
+    order in which ties are broken)."""
+    return tuple(itertools.permutations(range(n)))
+
+
+SHEAR_ORDERS_3D = shear_orders(3)
 
 
 def shear_passes(B: np.ndarray, b: np.ndarray):
-    """Factor u_old = B w + b into n line-wise passes (n = 2 or 3).
+    """Factor u_old = B w + b into n line-wise passes (n = 2, 3 or 4).
 
     With an axis order (a_1, ..., a_n), pass k (applied to the data in the
     order k = n, ..., 1) resamples along axis a_k; on its array the axes
@@ -149,12 +156,12 @@ def shear_passes(B: np.ndarray, b: np.ndarray):
     largest |alpha| (the line-dependent shifts); orders within a relative
     1e-9 of the minimum count as tied (orders that share their alpha sets tie
     exactly in real arithmetic, so the choice must not depend on rounding)
-    and the first tied one in SHEAR_ORDERS_3D is taken; for n = 2 this is the
-    rule of shear_realign.  Returns
-    [(axis, coefficient per axis (3-vector over all axes), gamma)] in data
+    and the first tied one in lexicographic order (shear_orders) is taken; for
+    n = 2 this is the rule of shear_realign.  Returns
+    [(axis, coefficient per axis (n-vector over all axes), gamma)] in data
     order (k = n first)."""
     n = B.shape[0]
-    orders = ((0, 1), (1, 0)) if n == 2 else SHEAR_ORDERS_3D
+    orders = shear_orders(n)
     cands = []
     for order in orders:
         val, ok, passes = 0.0, True, []
@@ -184,7 +191,7 @@ def shear_passes(B: np.ndarray, b: np.ndarray):
 
 
 def shear_realign_nd(P: np.ndarray, B: np.ndarray, b: np.ndarray) -> np.ndarray:
-    """Band-limited re-alignment in n = 2 or 3 dimensions: the passes of
+    """Band-limited re-alignment in n = 2, 3 or 4 dimensions: the passes of
     shear_passes, each the 1-D trigonometric interpolant (eq. interFreq) of
     every line along its axis at that line's positions (coordinate value of
     the other axes times their coefficients, plus gamma, plus the running
@@ -239,8 +246,8 @@ class OracleFilter:
         self.n = cfg.nx
         if realign_mode is None:
             realign_mode = getattr(cfg, "realign_mode", "multilinear")
-        if realign_mode not in ("multilinear", "shear") or (realign_mode == "shear" and cfg.nx not in (2, 3)):
-            raise ValueError("realign_mode: 'multilinear', or 'shear' for n_x = 2 or 3")
+        if realign_mode not in ("multilinear", "shear") or (realign_mode == "shear" and cfg.nx == 1):
+            raise ValueError("realign_mode: 'multilinear', or 'shear' for n_x = 2, 3 or 4")
         self.realign_mode = realign_mode
         self.N = tuple(int(v) for v in cfg.N)
         self.A = np.asarray(cfg.A, dtype=float)

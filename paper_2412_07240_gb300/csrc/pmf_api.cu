@@ -200,7 +200,7 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
   ALLOC(ctx->pend, sizeof(double) * kPendSize);
   ALLOC(ctx->prior_aux, sizeof(double) * kAuxSize);
   if (ctx->path == 0) {
-    if (cfg->realign_mode == PMF_REALIGN_SHEAR) ALLOC(ctx->scratch, sizeof(double) * (P + 32));
+    if (cfg->realign_mode == PMF_REALIGN_SHEAR) ALLOC(ctx->scratch, sizeof(double) * (P + 64));
     for (int a = 0; a < n; ++a) {
       const int N = cfg->N[a];
       ALLOC(ctx->interp[a], sizeof(double) * N * N);
@@ -280,7 +280,7 @@ int pmf_time_update(pmf_ctx* ctx, double tau) {
   if (ctx->path == 0) {
     launch_time_f64(ctx->dims, ctx->tc, ctx->st, (double*)ctx->buf[0], (double*)ctx->buf[1],
                     ctx->partials, ctx->pend, ctx->interp, ctx->hfwd, ctx->hinv, ctx->scratch, ctx->stream);
-    ctx->launches += launches_time_f64(ctx->cfg.nx) + (ctx->scratch ? (ctx->cfg.nx == 3 ? 4 : 2) : 0);
+    ctx->launches += launches_time_f64(ctx->cfg.nx) + (ctx->scratch ? ctx->cfg.nx + (ctx->cfg.nx > 2 ? 1 : 0) : 0);
   } else {
     ctx->launches += fast_step(ctx, nullptr, &ctx->tc);
   }

@@ -122,6 +122,122 @@ __device__ inline bool shear3_setup(const FrameState& f, double* pc) {
   return false;
 }
 
+// The same factorisation for n = 4: pass k (applied for k = 4, .., 1) along
+// a_k with S = {a_1..a_{k-1}} on old and T = {a_k..a_4} on new coordinates,
+// alpha = B[a_k, S] B[S, S]^{-1} (leading blocks up to 3 x 3, inverted by the
+// adjugate), beta = B[a_k, T] - alpha B[S, T], gamma = b[a_k] - alpha b[S];
+// a leading block is singular when |det| <= 1e-12 max(1, max |entry|)^|S|.
+// Candidate layout per pass in data order: cand[10 i] = axis, cand[10 i + 1..4]
+// = coefficient of each axis, cand[10 i + 5] = gamma.
+__device__ inline bool shear4_order(const double* B, const double* bb, const int* a, double* cand, double* val) {
+  *val = 0.0;
+  for (int i = 0; i < 40; ++i) cand[i] = 0.0;
+  for (int k = 4; k >= 1; --k) {
+    const int ax = a[k - 1], i = 4 - k, ns = k - 1;
+    double S[9], inv[9], alpha[3] = {0.0, 0.0, 0.0}, coef[4] = {0.0, 0.0, 0.0, 0.0};
+    double mx = 0.0;
+    for (int r = 0; r < ns; ++r)
+      for (int c = 0; c < ns; ++c) {
+        S[r * 3 + c] = B[a[r] * 4 + a[c]];
+        mx = fmax(mx, fabs(S[r * 3 + c]));
+      }
+    double det = 1.0;
+    if (ns == 1) {
+      det = S[0];
+      inv[0] = 1.0 / det;
+    } else if (ns == 2) {
+      det = S[0] * S[4] - S[1] * S[3];
+      inv[0] = S[4] / det;
+      inv[1] = -S[1] / det;
+      inv[3] = -S[3] / det;
+      inv[4] = S[0] / det;
+    } else if (ns == 3) {
+      const double c00 = S[4] * S[8] - S[5] * S[7], c01 = S[5] * S[6] - S[3] * S[8], c02 = S[3] * S[7] - S[4] * S[6];
+      det = S[0] * c00 + S[1] * c01 + S[2] * c02;
+      inv[0] = c00 / det;
+      inv[3] = c01 / det;
+      inv[6] = c02 / det;
+      inv[1] = (S[2] * S[7] - S[1] * S[8]) / det;
+      inv[4] = (S[0] * S[8] - S[2] * S[6]) / det;
+      inv[7] = (S[1] * S[6] - S[0] * S[7]) / det;
+      inv[2] = (S[1] * S[5] - S[2] * S[4]) / det;
+      inv[5] = (S[2] * S[3] - S[0] * S[5]) / det;
+      inv[8] = (S[0] * S[4] - S[1] * S[3]) / det;
+    }
+    if (ns > 0) {
+      double lim = 1e-12;
+      for (int r = 0; r < ns; ++r) lim *= fmax(1.0, mx);
+      if (!(fabs(det) > lim)) return false;
+    }
+    for (int c = 0; c < ns; ++c) {
+      double v = 0.0;
+      for (int r = 0; r < ns; ++r) v += B[ax * 4 + a[r]] * inv[r * 3 + c];
+      alpha[c] = v;
+      *val = fmax(*val, fabs(v));
+    }
+    double gamma = bb[ax];
+    for (int m = 0; m < ns; ++m) {
+      coef[a[m]] = alpha[m];
+      gamma -= alpha[m] * bb[a[m]];
+    }
+    for (int t = ns; t < 4; ++t) {
+      double v = B[ax * 4 + a[t]];
+      for (int m = 0; m < ns; ++m) v -= alpha[m] * B[a[m] * 4 + a[t]];
+      coef[a[t]] = v;
+    }
+    cand[10 * i] = ax;
+    for (int m = 0; m < 4; ++m) cand[10 * i + 1 + m] = coef[m];
+    cand[10 * i + 5] = gamma;
+  }
+  return true;
+}
+
+// Pass coefficients of the 4-D band-limited re-alignment (layout of
+// shear4_order, pc[40] = 1), or false (pc[40] = 0) when every order has a
+// singular leading block.  The 24 axis orders are visited in lexicographic
+// order; the order minimising the largest |alpha| is taken, orders within a
+// relative 1e-9 of the minimum being tied and the first tied one chosen.
+__device__ inline bool shear4_setup(const FrameState& f, double* pc) {
+  int ord[24][4];
+  {
+    int p[4] = {0, 1, 2, 3};
+    for (int o = 0; o < 24; ++o) {
+      for (int m = 0; m < 4; ++m) ord[o][m] = p[m];
+      // next permutation in lexicographic order
+      int i = 2;
+      while (i >= 0 && p[i] > p[i + 1]) --i;
+      if (i < 0) break;
+      int j = 3;
+      while (p[j] < p[i]) --j;
+      const int t = p[i];
+      p[i] = p[j];
+      p[j] = t;
+      for (int l = i + 1, r = 3; l < r; ++l, --r) {
+        const int u = p[l];
+        p[l] = p[r];
+        p[r] = u;
+      }
+    }
+  }
+  double vals[24], cand[40], vmin = INFINITY;
+  for (int o = 0; o < 24; ++o) {
+    vals[o] = INFINITY;
+    double v;
+    if (shear4_order(f.B, f.b, ord[o], cand, &v)) vals[o] = v;
+    vmin = fmin(vmin, vals[o]);
+  }
+  for (int i = 0; i < 41; ++i) pc[i] = 0.0;
+  for (int o = 0; o < 24 && isfinite(vmin); ++o)
+    if (vals[o] <= vmin * (1.0 + 1e-9)) {
+      double v;
+      shear4_order(f.B, f.b, ord[o], cand, &v);
+      for (int i = 0; i < 40; ++i) pc[i] = cand[i];
+      pc[40] = 1.0;
+      return true;
+    }
+  return false;
+}
+
 // Diffusion coefficients of sub-step q in the new frame (any thread):
 // Q_u(t_q) = M'^{-1} Qt_q M'^{-T}, Qt_q = e^{-A q dt} Q e^{-A^T q dt} (host),
 // pa = dt/2 Q_u,aa and pb = dt Q_u,ab (01, 02, 12); for the exact multiplier

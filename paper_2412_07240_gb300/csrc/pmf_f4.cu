@@ -745,6 +745,10 @@ int f4_supported(const pmf_config* cfg, std::string* why) {
     *why = "the float32 4-D kernels handle n_x = 4";
     return PMF_ERR_UNSUPPORTED;
   }
+  if (cfg->realign_mode == PMF_REALIGN_SHEAR) {
+    *why = "the float32 4-D kernels re-align by multilinear interpolation (shear mode: float64 path)";
+    return PMF_ERR_UNSUPPORTED;
+  }
   long long P = 1;
   for (int a = 0; a < 4; ++a) {
     if (cfg->N[a] > kMaxN4) {

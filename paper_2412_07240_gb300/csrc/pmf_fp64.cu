@@ -231,6 +231,98 @@ __global__ void k_shear_f64(Dims d, const DevState* st, int pass, double* b0, do
   }
 }
 
+// Band-limited re-alignment of a 4-D grid: the four line-wise passes of
+// shear4_setup (pmf_device.cuh), written by k_shear4_setup as pc[10 i] = axis,
+// pc[10 i + 1..4] = coefficient of each axis, pc[10 i + 5] = gamma (data
+// order), pc[40] = 1 (0 and status DEGENERATE if every order is singular).
+__global__ void k_shear4_setup(DevState* st, double* pc) {
+  if (!st->f.realign) return;
+  if (!shear4_setup(st->f, pc)) st->f.status = PMF_ERR_DEGENERATE;
+}
+
+// One pass of the 4-D band-limited re-alignment: one CTA per line along the
+// pass's axis (surplus CTAs exit), the line's DFT coefficients from an exact
+// twiddle table and the trigonometric interpolant (eq. interFreq) at its
+// positions, as in k_shear3_f64.  Buffers: pass 0 buf[cur] -> scratch, pass 1
+// scratch -> buf[cur], pass 2 buf[cur] -> scratch, pass 3 scratch ->
+// buf[cur ^ 1] with pscale.
+__global__ void k_shear4_f64(Dims d, const DevState* st, const double* pc, int pass, double* b0, double* b1,
+                             double* scratch) {
+  extern __shared__ double sm[];
+  const FrameState& f = st->f;
+  if (!f.realign || pc[40] == 0.0) return;
+  double* bc = f.cur ? b1 : b0;
+  double* bn = f.cur ? b0 : b1;
+  const double* in = (pass & 1) ? scratch : bc;
+  double* out = pass == 3 ? bn : (pass & 1) ? bc : scratch;
+  const int a = (int)pc[10 * pass];
+  const double* coef = pc + 10 * pass + 1;
+  const double gamma = pc[10 * pass + 5];
+  int o[3], no = 0;
+  for (int m = 0; m < 4; ++m)
+    if (m != a) o[no++] = m;
+  const int N = d.N[a], H = N / 2;
+  const long long lines = d.P / N;
+  const long long line = blockIdx.x;
+  if (line >= lines) return;
+  long long stride[4];
+  stride[3] = 1;
+  for (int m = 2; m >= 0; --m) stride[m] = stride[m + 1] * d.N[m + 1];
+  long long rest = line, base = 0;
+  double offset = gamma;
+  for (int q = 2; q >= 0; --q) {
+    const int m = o[q];
+    const int i = (int)(rest % d.N[m]);
+    rest /= d.N[m];
+    base += i * stride[m];
+    offset += coef[m] * (i - 0.5 * (d.N[m] - 1));
+  }
+  const long long sa = stride[a];
+  double* fl = sm;
+  double* Xr = fl + N;
+  double* Xi = Xr + H + 1;
+  double* cs = Xi + H + 1;
+  double* sn = cs + N;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    fl[t] = in[base + t * sa];
+    sincospi(2.0 * t / N, &sn[t], &cs[t]);
+  }
+  __syncthreads();
+  for (int sidx = threadIdx.x; sidx <= H; sidx += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    int r = 0;
+    for (int j = 0; j < N; ++j) {
+      re = fma(fl[j], cs[r], re);
+      im = fma(-fl[j], sn[r], im);
+      r += sidx;
+      if (r >= N) r -= N;
+    }
+    Xr[sidx] = re / N;
+    Xi[sidx] = im / N;
+  }
+  __syncthreads();
+  const double ps = pass == 3 ? f.pscale : 1.0;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    const double pos = offset + coef[a] * (t - 0.5 * (N - 1));
+    double v = 0.0;
+    if (fabs(pos) <= 0.5 * N) {
+      const double x = pos + 0.5 * (N - 1);
+      double sx, cx;
+      sincospi(2.0 * x / N, &sx, &cx);
+      double zr = 1.0, zi = 0.0;   // e^{2 pi i s x / N}
+      v = Xr[0];
+      for (int k = 1; k < H; ++k) {
+        const double nr = zr * cx - zi * sx;
+        zi = zr * sx + zi * cx;
+        zr = nr;
+        v += 2.0 * (Xr[k] * zr - Xi[k] * zi);
+      }
+      v += Xr[H] * cospi(x);
+    }
+    out[base + t * sa] = ps * v;
+  }
+}
+
 // Band-limited re-alignment of a 3-D grid (shear mode): the map u_old = B w + b
 // factored into three line-wise passes.  With an axis order (a_1, a_2, a_3),
 // pass k (applied in the order k = 3, 2, 1) resamples along a_k; the axes
@@ -627,6 +719,20 @@ void launch_time_f64(const Dims& d, const TimeConsts& tc, DevState* st, double* 
     k_shear3_setup<<<1, 1, 0, s>>>(st, pc);
     for (int pass = 0; pass < 3; ++pass)
       k_shear3_f64<<<lines, 128, smem, s>>>(d, st, pc, pass, b0, b1, scratch);
+  }
+  if (tc.realign_mode == PMF_REALIGN_SHEAR && n == 4 && scratch) {
+    int Nmax = 0, Nmin = 1 << 30;
+    for (int a = 0; a < 4; ++a) {
+      Nmax = d.N[a] > Nmax ? d.N[a] : Nmax;
+      Nmin = d.N[a] < Nmin ? d.N[a] : Nmin;
+    }
+    const size_t smem = sizeof(double) * (4 * (size_t)Nmax + 2);
+    cudaFuncSetAttribute(k_shear4_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    double* pc = scratch + d.P;   // pass coefficients after the intermediate grid
+    const unsigned lines = (unsigned)(d.P / Nmin);
+    k_shear4_setup<<<1, 1, 0, s>>>(st, pc);
+    for (int pass = 0; pass < 4; ++pass)
+      k_shear4_f64<<<lines, 128, smem, s>>>(d, st, pc, pass, b0, b1, scratch);
   }
   if (tc.realign_mode == PMF_REALIGN_SHEAR && n == 2 && scratch) {
     const int Nmax = d.N[0] > d.N[1] ? d.N[0] : d.N[1];

@@ -155,8 +155,8 @@ int validate_config(const pmf_config* c, std::string* why) {
     *why = "unknown transform form";
     return PMF_ERR_ARG;
   }
-  if (c->realign_mode == PMF_REALIGN_SHEAR && c->nx != 2 && c->nx != 3) {
-    *why = "shear re-alignment is defined for n_x = 2 and 3";
+  if (c->realign_mode == PMF_REALIGN_SHEAR && c->nx < 2) {
+    *why = "shear re-alignment is defined for n_x = 2, 3 and 4";
     return PMF_ERR_ARG;
   }
   return PMF_OK;

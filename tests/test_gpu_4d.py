@@ -160,3 +160,31 @@ def test_4d_path_selection():
             s.admit(sc.cfg, sc.meas)
     finally:
         s.close()
+
+
+def test_4d_shear_realignment_fp64():
+    """Band-limited re-alignment in 4-D: four line-wise passes on the float64
+    path.  Two constant-velocity axes with position measurements (a density
+    the grid resolves; on the under-resolved terrain posterior the
+    trigonometric fill rings into negative lobes, which multilinear
+    interpolation cannot)."""
+    A = np.zeros((4, 4))
+    A[0, 1] = 1.0
+    A[2, 3] = 1.0
+    A[3, 2] = -0.2
+    cfg = FilterConfig(nx=4, N=(16, 14, 12, 18), A=A, Q=np.diag([0.01, 0.1, 0.01, 0.1]),
+                       m0=np.array([0.0, 1.0, 0.0, -0.5]), P0=np.diag([0.5, 0.5, 0.4, 0.3]), realign_mode="shear")
+    meas = MeasModel("linear", R=np.eye(2), H=np.array([[1.0, 0.0, 0.0, 0.0], [0.0, 0.0, 1.0, 0.0]]))
+    sc = Scenario("cv4", cfg, meas, dt=0.3, epochs=6)
+    sc.truth, sc.z = simulate(cfg, meas, sc.dt, sc.epochs, seed=12)
+    worst, log = max_errors(sc)
+    assert sum(s.endswith("R") for s, _ in log) >= 1, "re-alignment not exercised"
+    _check(worst, 1e-11)
+
+
+def test_f32_4d_rejects_shear_mode():
+    from paper_2412_07240_gb300 import Filter, Unsupported
+    sc = w.c6_scenario(N=16, epochs=1)
+    sc.cfg.realign_mode = "shear"
+    with pytest.raises(Unsupported):
+        Filter(sc.cfg, precision="fp16x3")

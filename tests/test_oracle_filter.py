@@ -440,3 +440,73 @@ def test_shear3_spectral_on_gaussians():
     ml = of.multilinear(g(*U), np.stack([z.ravel() for z in Z], 1) + (N - 1) / 2).reshape(N, N, N)
     e_sh, e_ml = np.abs(sh - ex).max() / ex.max(), np.abs(ml - ex).max() / ex.max()
     assert e_sh < 1e-4 and e_sh < e_ml / 100, (e_sh, e_ml)
+
+
+def _trig_field4(N):
+    u = of.grid_u(N)
+    U = np.meshgrid(u, u, u, u, indexing="ij")
+    f = lambda a, b, c, d: (1.0 + 0.3 * np.cos(2 * np.pi * 2 * a / N + 0.4)
+                            + 0.2 * np.sin(2 * np.pi * (a + 2 * b) / N)
+                            + 0.1 * np.cos(2 * np.pi * (3 * c - b) / N - 1.0)
+                            + 0.15 * np.sin(2 * np.pi * (2 * d + c - a) / N + 0.7))
+    return U, f
+
+
+def test_shear_orders_are_lexicographic_permutations():
+    assert of.shear_orders(2) == ((0, 1), (1, 0))
+    assert of.SHEAR_ORDERS_3D == ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+    o4 = of.shear_orders(4)
+    assert len(o4) == 24 and len(set(o4)) == 24 and list(o4) == sorted(o4)
+
+
+@pytest.mark.parametrize("B", [
+    [[0.8, 0.0, 0.0, 0.0], [0.3, 0.9, 0.0, 0.0], [-0.2, 0.25, 0.7, 0.0], [0.1, -0.15, 0.2, 0.85]],   # lower
+    [[0.85, 0.0, 0.2, 0.0], [0.1, 0.9, -0.15, 0.25], [0.0, 0.0, 0.8, 0.0], [0.0, 0.0, 0.3, 0.75]],  # permuted
+])
+def test_shear4_exact_on_trig_polynomials(B):
+    """A 4-D map triangular in some axis order is four exact 1-D resamplings
+    of a trigonometric polynomial (the order selection finds the order)."""
+    B, b = np.array(B), np.array([0.3, -0.45, 0.2, 0.1])
+    N = 10
+    U, f = _trig_field4(N)
+    out = of.shear_realign_nd(f(*U), B, b)
+    Z = [sum(B[i, j] * U[j] for j in range(4)) + b[i] for i in range(4)]
+    inside = np.all([np.abs(z) <= N / 2 for z in Z], axis=0)
+    assert inside.sum() > 0.3 * N ** 4
+    assert np.abs(out - f(*Z))[inside].max() < 1e-11
+
+
+def test_shear4_passes_reproduce_the_map():
+    """Composing the four passes' affine maps gives back u_old = B w + b:
+    traced back from the new coordinates (passes in reverse data order), each
+    pass replaces the new coordinate of its axis by the old one, from the old
+    coordinates of the axes resampled after it and the new ones of the rest."""
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        B = np.eye(4) + 0.3 * rng.standard_normal((4, 4))
+        b = rng.standard_normal(4)
+        w = rng.standard_normal(4)
+        coords = w.copy()                 # current coordinate of each axis (new until resampled)
+        for a, coef, gamma in reversed(of.shear_passes(B, b)):
+            coords[a] = coef @ coords + gamma
+        assert np.allclose(coords, B @ w + b, atol=1e-12)
+
+
+def test_shear4_spectral_on_gaussians():
+    """A general 4-D map of a correlated Gaussian inside its box: the
+    band-limited fill is far below the multilinear one."""
+    B = np.array([[0.9, 0.3, -0.1, 0.05], [-0.25, 0.85, 0.2, 0.0], [0.15, -0.2, 0.8, 0.1],
+                  [0.0, 0.1, -0.15, 0.9]])
+    b = np.array([0.3, -0.45, 0.2, -0.1])
+    N = 16
+    u = of.grid_u(N)
+    U = np.meshgrid(u, u, u, u, indexing="ij")
+    s = N / 10.0
+    g = lambda a, c, e, h: np.exp(-0.5 * (a ** 2 + 0.6 * a * c + c ** 2 - 0.4 * c * e + e ** 2 + h ** 2
+                                          + 0.3 * e * h) / s ** 2)
+    Z = [sum(B[i, j] * U[j] for j in range(4)) + b[i] for i in range(4)]
+    ex = g(*Z)
+    sh = of.shear_realign_nd(g(*U), B, b)
+    ml = of.multilinear(g(*U), np.stack([z.ravel() for z in Z], 1) + (N - 1) / 2).reshape((N,) * 4)
+    e_sh, e_ml = np.abs(sh - ex).max() / ex.max(), np.abs(ml - ex).max() / ex.max()
+    assert e_sh < 1e-4 and e_sh < e_ml / 1000, (e_sh, e_ml)
