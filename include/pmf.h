@@ -90,8 +90,7 @@ enum { PMF_PSI_EULER = 0, PMF_PSI_EXACT = 1 };
  *                 interFreq) of the old weights at the new nodes, as n
  *                 line-wise passes (per line: DFT, evaluation at that line's
  *                 affine positions); spectrally accurate for densities well
- *                 inside the box.  For n_x = 4 the float64 path only (the
- *                 float32 4-D kernels return PMF_ERR_UNSUPPORTED). */
+ *                 inside the box. */
 enum { PMF_REALIGN_MULTILINEAR = 0, PMF_REALIGN_SHEAR = 1 };
 
 /* Form of the per-axis Hartley transforms (step 1 and step 5 of the Sec. V-B

@@ -350,13 +350,15 @@ __global__ void k_f4_tables(Dims d, const DevState* st, const F4Tables t) {
 // node); the corner weights and sums are float32.
 constexpr int kLinesRMax = 128;   // lines per block iteration: 512 / N3 (two passes of 256 threads)
 
-__global__ void __launch_bounds__(256) k_f4_realign(Dims d, const DevState* st, float* b0, float* b1) {
+__global__ void __launch_bounds__(256) k_f4_realign(Dims d, const DevState* st, float* b0, float* b1,
+                                                    int shear) {
   __shared__ DF zl[kLinesRMax][4];
   const int cur = st->f.cur;
   const float* in = cur ? b1 : b0;
   float* out = cur ? b0 : b1;
   const float ps = (float)st->f.pscale;
   const int P = (int)d.P, N3 = d.N[3];
+  if (st->f.realign && shear) return;   // the band-limited passes fill the re-aligned frame
   if (!st->f.realign) {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) out[p] = ps * in[p];
     return;
@@ -422,6 +424,98 @@ __global__ void __launch_bounds__(256) k_f4_realign(Dims d, const DevState* st, 
       out[(l0 + li) * N3 + j3] = ps * sum;
     }
     __syncthreads();
+  }
+}
+
+// Band-limited re-alignment (shear mode): the four line-wise passes of
+// shear4_setup (pmf_device.cuh; pass coefficients in float64, written by
+// k_f4_shear_setup), each the trigonometric interpolant (eq. interFreq) of
+// every line along the pass's axis at that line's positions: one CTA per line,
+// the line's DFT coefficients in float32 from a twiddle table, the positions
+// in float64, each power e^{2 pi i k x / N} from the table and a small-angle
+// factor.  Buffers:
+// pass 0 buf[cur] -> buf[cur ^ 1], pass 1 back to buf[cur], pass 2 buf[cur] ->
+// scratch (the measurement exponents, free during a time update), pass 3
+// scratch -> buf[cur ^ 1] with pscale.
+__global__ void k_f4_shear_setup(DevState* st, double* pc) {
+  if (!st->f.realign) return;
+  if (!shear4_setup(st->f, pc)) st->f.status = PMF_ERR_DEGENERATE;
+}
+
+constexpr int kShearT4 = 64;
+
+__global__ void __launch_bounds__(kShearT4) k_f4_shear(Dims d, const DevState* st, const double* pc, int pass,
+                                                       float* b0, float* b1, float* scratch) {
+  __shared__ float fl[kMaxN4], cs[kMaxN4], sn[kMaxN4], Xr[kMaxN4 / 2 + 1], Xi[kMaxN4 / 2 + 1];
+  const FrameState& f = st->f;
+  if (!f.realign || pc[40] == 0.0) return;
+  float* bc = f.cur ? b1 : b0;
+  float* bn = f.cur ? b0 : b1;
+  const float* in = pass == 0 ? bc : pass == 1 ? bn : pass == 2 ? bc : scratch;
+  float* out = pass == 0 ? bn : pass == 1 ? bc : pass == 2 ? scratch : bn;
+  const double* q = pc + 10 * pass;
+  const int a = (int)q[0];
+  int o[3], no = 0;
+  for (int m = 0; m < 4; ++m)
+    if (m != a) o[no++] = m;
+  const int N = d.N[a], H = N / 2;
+  const int lines = (int)(d.P / N);
+  if ((int)blockIdx.x >= lines) return;
+  int stride[4];
+  stride[3] = 1;
+  for (int m = 2; m >= 0; --m) stride[m] = stride[m + 1] * d.N[m + 1];
+  int rest = blockIdx.x, base = 0;
+  double offset = q[5];
+  for (int k = 2; k >= 0; --k) {
+    const int m = o[k], i = rest % d.N[m];
+    rest /= d.N[m];
+    base += i * stride[m];
+    offset += q[1 + m] * (i - 0.5 * (d.N[m] - 1));
+  }
+  const int sa = stride[a];
+  for (int t = threadIdx.x; t < N; t += kShearT4) {
+    fl[t] = in[base + t * sa];
+    sincospif(2.0f * (float)t / (float)N, &sn[t], &cs[t]);
+  }
+  __syncthreads();
+  for (int sidx = threadIdx.x; sidx <= H; sidx += kShearT4) {
+    float re = 0.0f, im = 0.0f;
+    int r = 0;
+    for (int j = 0; j < N; ++j) {
+      re = fmaf(fl[j], cs[r], re);
+      im = fmaf(-fl[j], sn[r], im);
+      r += sidx;
+      if (r >= N) r -= N;
+    }
+    Xr[sidx] = re / (float)N;
+    Xi[sidx] = im / (float)N;
+  }
+  __syncthreads();
+  const float ps = pass == 3 ? (float)f.pscale : 1.0f;
+  for (int t = threadIdx.x; t < N; t += kShearT4) {
+    const double pos = offset + q[1 + a] * (t - 0.5 * (N - 1));
+    float v = 0.0f;
+    if (fabs(pos) <= 0.5 * N) {
+      // x = m + fr (m integer, |fr| <= 1/2): e^{2 pi i k x / N} is the table
+      // entry of k m mod N times e^{2 pi i k fr / N}, each power formed
+      // directly (no recurrence, no rounded large argument)
+      const double x = pos + 0.5 * (N - 1);
+      const double mf = rint(x);
+      const float fr = (float)(x - mf);
+      int m = (int)mf % N;
+      if (m < 0) m += N;
+      v = Xr[0];
+      for (int k = 1; k < H; ++k) {
+        const int idx = (k * m) % N;
+        float s2, c2;
+        sincospif(2.0f * (float)k * fr / (float)N, &s2, &c2);
+        const float zr = cs[idx] * c2 - sn[idx] * s2, zi = sn[idx] * c2 + cs[idx] * s2;
+        v += 2.0f * (Xr[k] * zr - Xi[k] * zi);
+      }
+      const float cn = cospif(fr);
+      v += Xr[H] * ((((int)mf) & 1) ? -cn : cn);   // cos(pi x)
+    }
+    out[base + t * sa] = ps * v;
   }
 }
 
@@ -745,10 +839,6 @@ int f4_supported(const pmf_config* cfg, std::string* why) {
     *why = "the float32 4-D kernels handle n_x = 4";
     return PMF_ERR_UNSUPPORTED;
   }
-  if (cfg->realign_mode == PMF_REALIGN_SHEAR) {
-    *why = "the float32 4-D kernels re-align by multilinear interpolation (shear mode: float64 path)";
-    return PMF_ERR_UNSUPPORTED;
-  }
   long long P = 1;
   for (int a = 0; a < 4; ++a) {
     if (cfg->N[a] > kMaxN4) {
@@ -769,6 +859,7 @@ int f4_alloc(const pmf_config* cfg, F4Tables* t) {
   long long P = 1;
   for (int a = 0; a < 4; ++a) P *= cfg->N[a];
   bool ok = cudaMalloc(&t->mtab, sizeof(double2) * 16 * kMaxN4) == cudaSuccess &&
+            cudaMalloc(&t->shear, sizeof(double) * 48) == cudaSuccess &&
             cudaMalloc(&t->lo, sizeof(float) * P) == cudaSuccess &&
             cudaMalloc(&t->gap, sizeof(float) * P) == cudaSuccess;
   for (int a = 0; ok && a < 4; ++a) {
@@ -803,6 +894,7 @@ int f4_alloc(const pmf_config* cfg, F4Tables* t) {
 
 void f4_free(F4Tables* t) {
   cudaFree(t->mtab);
+  cudaFree(t->shear);
   cudaFree(t->lo);
   cudaFree(t->gap);
   for (int a = 0; a < 4; ++a) {
@@ -834,7 +926,15 @@ int f4_time(const Dims& d, const TimeConsts& tc, DevState* st, const F4Tables& t
   int maxN = 0;
   for (int a = 0; a < 4; ++a) maxN = d.N[a] > maxN ? d.N[a] : maxN;
   k_f4_tables<<<dim3(maxN, 4), 64, 0, s>>>(d, st, t);
-  k_f4_realign<<<grid_cap(d.P / d.N[3], 512 / d.N[3], 4096), 256, 0, s>>>(d, st, b0, b1);
+  const int shear = tc.realign_mode == PMF_REALIGN_SHEAR;
+  k_f4_realign<<<grid_cap(d.P / d.N[3], 512 / d.N[3], 4096), 256, 0, s>>>(d, st, b0, b1, shear);
+  if (shear) {
+    int Nmin = d.N[0];
+    for (int a = 1; a < 4; ++a) Nmin = d.N[a] < Nmin ? d.N[a] : Nmin;
+    k_f4_shear_setup<<<1, 1, 0, s>>>(st, t.shear);
+    for (int pass = 0; pass < 4; ++pass)
+      k_f4_shear<<<(unsigned)(d.P / Nmin), kShearT4, 0, s>>>(d, st, t.shear, pass, b0, b1, t.lo);
+  }
   int stage = 1;
   auto axis = [&](int a, const float* WT) { launch_axis(d, a, WT, st, stage++, b0, b1, s); };
   const int nslab = (d.N[0] * d.N[1] + kSlabs - 1) / kSlabs;
@@ -849,7 +949,7 @@ int f4_time(const Dims& d, const TimeConsts& tc, DevState* st, const F4Tables& t
   axis(1, t.winv[1]);
   k_f4_slab23<true><<<nslab, kSlabThreads, ssm, s>>>(d, t.winv[3], t.winv[2], st, stage++, b0, b1, partials);
   k_f4_finalize<<<1, 256, 0, s>>>(st, (const float2*)partials, nslab, stage & 1, 1, pend);
-  return 1 + 1 + 1 + 6 + 1 + 1;
+  return 1 + 1 + 1 + 6 + 1 + 1 + (shear ? 5 : 0);
 }
 
 }  // namespace pmf

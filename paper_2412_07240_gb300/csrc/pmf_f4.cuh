@@ -14,6 +14,7 @@ struct F4Tables {
   double* hfwd[4] = {};        // per axis: forward Hartley matrix / N (float64)
   float* wfwd[4] = {};         // per axis: (H I)^T, columns padded to a multiple of 8
   float* winv[4] = {};         // per axis: H^T (inverse transform), padded likewise
+  double* shear = nullptr;     // band-limited re-alignment: pass coefficients (shear4_setup layout)
 };
 
 // PMF_OK if the float32 4-D kernels can hold this grid.
