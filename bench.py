@@ -626,7 +626,7 @@ def bench_4d(args, ws, rank, pg, local):
     import torch
     import workloads as w
     from paper_2412_07240_gb300 import Degenerate, Filter
-    sc = _scenario("c6", args.warmup + args.steps + 1)
+    sc = _apply_modes(_scenario("c6", args.warmup + args.steps + 1))
     P = 1
     for n in sc.cfg.N:
         P *= n
@@ -647,7 +647,7 @@ def bench_4d(args, ws, rank, pg, local):
     T, M = 20, args.mc
     se, var, used, lost = np.zeros(4), np.zeros(4), 0, 0
     for m in range(rank, M, ws):
-        run = w.c6_scenario(seed=100 + m, epochs=T + 1)
+        run = _apply_modes(w.c6_scenario(seed=100 + m, epochs=T + 1))
         g = Filter(run.cfg, precision=prec, psi_mode=MODES["psi"])
         try:
             for k in range(T + 1):
