@@ -432,8 +432,8 @@ __global__ void __launch_bounds__(256) k_f4_realign(Dims d, const DevState* st, 
 // k_f4_shear_setup), each the trigonometric interpolant (eq. interFreq) of
 // every line along the pass's axis at that line's positions: one CTA per line,
 // the line's DFT coefficients in float32 from a twiddle table, the positions
-// in float64, each power e^{2 pi i k x / N} from the table and a small-angle
-// factor.  Buffers:
+// in float64, each power e^{2 pi i k x / N} from the table (k m mod N) and the
+// power of a small-angle factor.  Buffers:
 // pass 0 buf[cur] -> buf[cur ^ 1], pass 1 back to buf[cur], pass 2 buf[cur] ->
 // scratch (the measurement exponents, free during a time update), pass 3
 // scratch -> buf[cur ^ 1] with pscale.
@@ -497,19 +497,25 @@ __global__ void __launch_bounds__(kShearT4) k_f4_shear(Dims d, const DevState* s
     float v = 0.0f;
     if (fabs(pos) <= 0.5 * N) {
       // x = m + fr (m integer, |fr| <= 1/2): e^{2 pi i k x / N} is the table
-      // entry of k m mod N times e^{2 pi i k fr / N}, each power formed
-      // directly (no recurrence, no rounded large argument)
+      // entry of k m mod N times e^{2 pi i k fr / N}; the small-angle factor's
+      // powers by recurrence from one sincospi (no rounded large argument)
       const double x = pos + 0.5 * (N - 1);
       const double mf = rint(x);
       const float fr = (float)(x - mf);
       int m = (int)mf % N;
       if (m < 0) m += N;
+      float s1, c1;
+      sincospif(2.0f * fr / (float)N, &s1, &c1);
+      float wr = 1.0f, wi = 0.0f;   // e^{2 pi i k fr / N}
+      int idx = 0;
       v = Xr[0];
       for (int k = 1; k < H; ++k) {
-        const int idx = (k * m) % N;
-        float s2, c2;
-        sincospif(2.0f * (float)k * fr / (float)N, &s2, &c2);
-        const float zr = cs[idx] * c2 - sn[idx] * s2, zi = sn[idx] * c2 + cs[idx] * s2;
+        const float nr = wr * c1 - wi * s1;
+        wi = wr * s1 + wi * c1;
+        wr = nr;
+        idx += m;
+        if (idx >= N) idx -= N;
+        const float zr = cs[idx] * wr - sn[idx] * wi, zi = sn[idx] * wr + cs[idx] * wi;
         v += 2.0f * (Xr[k] * zr - Xi[k] * zi);
       }
       const float cn = cospif(fr);
