@@ -61,6 +61,10 @@ def test_invalid_config_rejected_without_gpu():
     c.N[0] = 32
     c.P0[0] = -1.0               # not positive definite
     assert lib.pmf_create(ctypes.byref(h), ctypes.byref(c), None) == _binding.ERR_ARG
+    c.nx = 1
+    c.P0[0] = 1.0
+    c.realign_mode = _binding.REALIGN["shear"]   # band-limited re-alignment needs n_x >= 2
+    assert lib.pmf_create(ctypes.byref(h), ctypes.byref(c), None) == _binding.ERR_ARG
     assert not h.value
 
 
