@@ -1,17 +1,21 @@
 """Benchmark of the spectral point-mass filter hot path on GB300.
 
-Workload (default): the 2-D damped oscillator, A = [[0, 1], [-1, -0.2]],
-Q = diag(0.1, 0.3), 128 x 128 grid, range measurement with sigma_v = 0.05,
-dt = 0.05 (seeded synthetic truth and measurements).  One step = one filter
-epoch = Bayes measurement update + spectral time update of the whole grid.
+Workload (default, --workload c4): 4096 independent 2-D filters, each with its
+own seeded stable A and diagonal Q, axis sizes drawn from {32, 48, 64, 96,
+128}, linear measurement z = x + v (R = 0.1^2 I), dt = 0.05.  One step = one
+epoch of every filter (Bayes measurement update + spectral time update), one
+graph-replayed launch of the batched fused kernel.  --workload c2 | c3 | c5 |
+c6 select the 128 x 128 oscillator, the 96^3 bearing filter, the serving
+population and the 4-D coordinated turn.
 
 metric : grid-point updates per second (points x epochs / device time)
-value  : the fused tensor-core kernel at the chosen precision (default
-         FP16X3), inputs resident in HBM, L2 flushed between timed steps
-e2e    : the same through the public C-ABI call with the measurement taken
+value  : the tensor-core path at the chosen precision (default FP16X3),
+         inputs resident in HBM, L2 flushed between timed steps
+e2e    : the same through the public C-ABI call with the measurements taken
          from host memory and the moments read back every step
 fp64_gpu : the plain float64 GPU path on the same workload (comparator)
-cpu_baseline : the float64 oracle on a bounded sample, on the host cores
+cpu_baseline : the float64 oracle on a bounded sample, on the host cores,
+         with the parity of the same sample on the GPU
 
 Multi-GPU: filters are independent, so N ranks run N replicas ("replicas
 only"), barriers and a max-over-ranks timing, no data-path collective.
@@ -149,6 +153,17 @@ def _scenario(name, epochs=50):
     return eval(_scenario_expr(name, epochs))
 
 
+def leg_epochs(workload, steps, warmup):
+    """Epochs of the seeded scenario that each leg of a single-filter bench
+    run consumes (timed steps after the warm-up, the end-to-end loop, the
+    float64 comparator, the oracle parity sample); the scenario is built with
+    the largest of them, so every leg indexes inside it."""
+    nx = {"c2": 2, "c2small": 2, "c3": 3, "c6": 4}[workload]
+    f64 = max(3, min(steps // 4, {2: 40, 3: 5, 4: 10}[nx]))
+    return {"timed": warmup + steps, "e2e": 3 + steps, "fp64": warmup + f64,
+            "parity": {2: 60, 3: 10, 4: 2}[nx]}
+
+
 def _launch_names(sc):
     return "k_fused2d" if sc.cfg.nx == 2 else "k_slices_fwd+k_lines_axis0+k_slices_inv"
 
@@ -162,6 +177,7 @@ STEP_ITEM_BYTES = 32
 TIME_CONSTS_BYTES = 5832
 TRAFFIC_C2 = 345344.0
 TRAFFIC_C4_PER_POINT = (50111744.0 + 7359488.0) / 10976512.0
+BATCH_KERNEL = "k_fused2d_batch"
 
 
 def _flops_per_step(N):
@@ -225,9 +241,10 @@ def time_e2e(sc, precision, steps):
     return (t1 - t0) * 1e3 / steps
 
 
-def oracle_sample(name, epochs, threads=1):
-    """Run the float64 oracle on `epochs` epochs of workload `name` in a
-    single-threaded subprocess."""
+def oracle_sample(name, epochs, threads=1, total=None):
+    """Run the float64 oracle on the first `epochs` epochs of workload `name`
+    (a scenario of `total` epochs, default `epochs`) in a single-threaded
+    subprocess."""
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = str(threads)
@@ -237,7 +254,7 @@ sys.path.insert(0, {ROOT!r})
 import numpy as np
 import workloads as w
 from oracle.filter import OracleFilter
-sc = {_scenario_expr(name, epochs)}
+sc = {_scenario_expr(name, max(epochs, total or 0))}
 sc.cfg.realign_mode = {MODES["realign"]!r}
 f = OracleFilter(sc.cfg, psi_mode={MODES["psi"]!r})
 t = time.perf_counter()
@@ -325,10 +342,18 @@ def _oracle_cores(n_units):
     return max(1, min(os.cpu_count() or 1, n_units))
 
 
-def oracle_c4_sample(count, epochs=8, nsample=256):
+def c4_sample_ids(count, nsample=256):
+    """Indices of the filters the oracle samples from the batch (all sizes)."""
+    import numpy as np
+    return np.linspace(0, count - 1, min(nsample, count)).astype(int)
+
+
+def oracle_c4_sample(count, epochs=8, nsample=256, outdir=None):
     """The float64 oracle on `nsample` filters spread over the batch (all sizes),
     `epochs` epochs each, the filters dealt round-robin to one single-threaded
-    process per host core: grid-point updates and the wall span."""
+    process per host core: grid-point updates and the wall span.  With
+    `outdir`, each child also saves the final weights of its filters there
+    (outside the timed span) for the parity comparison."""
     code = f"""
 import json, sys, time
 sys.path.insert(0, {ROOT!r})
@@ -337,23 +362,28 @@ import workloads as w
 from oracle.filter import OracleFilter
 rank, nproc = int(sys.argv[1]), int(sys.argv[2])
 {_SHARE_SRC}cfgs, meas, dt, truth, z = w.c4_batch(count={count}, epochs={epochs})
-idx = np.linspace(0, len(cfgs) - 1, {nsample}).astype(int)
+idx = np.linspace(0, len(cfgs) - 1, min({nsample}, len(cfgs))).astype(int)
 owner = _share([int(np.prod(cfgs[i].N)) * sum(cfgs[i].N) for i in idx], nproc)
 idx = [i for i, o in zip(idx, owner) if o == rank]
 print("ready", flush=True)
 sys.stdin.readline()
-pts, t0 = 0, time.time()
+pts, t0, done = 0, time.time(), []
 for i in idx:
     f = OracleFilter(cfgs[i])
     for k in range({epochs}):
         f.meas_update(meas, z[i, k])
         f.time_update(dt)
     pts += int(np.prod(cfgs[i].N)) * {epochs}
-print(json.dumps({{"points": pts, "t0": t0, "t1": time.time(), "filters": len(idx)}}))
+    done.append((i, f.P))
+t1 = time.time()
+if {outdir!r} is not None:
+    for i, P in done:
+        np.save(f"{outdir}/{{i}}.npy", P)
+print(json.dumps({{"points": pts, "t0": t0, "t1": t1, "filters": len(idx)}}))
 """
     cores = _oracle_cores(nsample)
     t = _oracle_par(code, cores)
-    t.update(filters=nsample, epochs=epochs, cores=cores)
+    t.update(filters=min(nsample, count), epochs=epochs, cores=cores)
     return t
 
 
@@ -502,6 +532,10 @@ def bench_batch(args, ws, rank, pg):
     kernel_ms = float(np.mean(ms))
     peaks, src = _peaks()
     ach = flops / (kernel_ms * 1e-3) / 1e12
+    # the epoch's algorithmic intensity (flops / 8 B per point) is below the
+    # bf16 ridge, so the HBM roofline binds: float32 weights in and out
+    alg_bytes = 8.0 * float(P.sum())
+    gbs = alg_bytes / (kernel_ms * 1e-3) / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": f"f32 ({args.precision} split GEMMs)",
@@ -516,17 +550,40 @@ def bench_batch(args, ws, rank, pg):
             "fp64_gpu": {"value": fp64_rate, "unit": UNIT, "filters_timed": int(len(sub))},
             "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
             "degenerate_filters": bad,
-            "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks.get("bf16_tflops"),
-                         "unit": "TFLOP/s", "frac": ach / peaks.get("bf16_tflops"),
-                         "traffic": TRAFFIC_C4_PER_POINT * float(P.sum()),
-                         "kernel": "k_fused2d_batch", "flops_per_launch": flops},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                         "frac": gbs / peaks.get("hbm_gbs"),
+                         "traffic": None if TRAFFIC_C4_PER_POINT is None else TRAFFIC_C4_PER_POINT * float(P.sum()),
+                         "kernel": BATCH_KERNEL, "bytes_per_launch": alg_bytes,
+                         "peak_source": f"hbm_gbs ({src})",
+                         "tensor": {"achieved": ach, "peak": peaks.get("bf16_tflops"), "unit": "TFLOP/s",
+                                    "frac": ach / peaks.get("bf16_tflops"), "flops_per_launch": flops,
+                                    "note": "algorithmic transform flops (forward + inverse per axis)"}},
             "clocks": clk.summary()}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        t = oracle_c4_sample(len(cfgs))
+        import tempfile
+        with tempfile.TemporaryDirectory() as td:
+            t = oracle_c4_sample(len(cfgs), outdir=td)
+            # parity of the sample: the same filters in a batch of their own,
+            # the same epochs from their priors, weights against the oracle's
+            sid = c4_sample_ids(len(cfgs))
+            g = Batch([cfgs[i] for i in sid], [meas] * len(sid), precision=args.precision)
+            for k in range(t["epochs"]):
+                g.step(np.arange(len(sid)), z[sid, k], dt)
+            gst = g.status()
+            errs = []
+            for j, i in enumerate(sid):
+                Po = np.load(os.path.join(td, f"{i}.npy"))
+                if gst[j] == 0:
+                    errs.append(float(np.abs(g.pdf(j)[0] - Po).sum() / np.abs(Po).sum()))
+            g.close()
         line["cpu_baseline"] = {"value": t["points"] / t["seconds"], "unit": UNIT, "cores": t["cores"],
                                 "kind": "oracle",
                                 "sample": f"{t['filters']} filters spread over the batch, {t['epochs']} epochs "
                                           "each, one single-threaded process per core"}
+        line["rel_l1_vs_oracle"] = max(errs) if errs else None
+        line["rel_l1_sample"] = (f"max over {len(errs)} of the {t['filters']} sampled filters "
+                                 f"({int((gst != 0).sum())} degenerate on the GPU) after {t['epochs']} epochs, "
+                                 "same filters in a batch of their own")
     if rank == 0:
         print(json.dumps(line))
 
@@ -626,7 +683,8 @@ def bench_4d(args, ws, rank, pg, local):
     import torch
     import workloads as w
     from paper_2412_07240_gb300 import Degenerate, Filter
-    sc = _apply_modes(_scenario("c6", args.warmup + args.steps + 1))
+    legs = leg_epochs("c6", args.steps, args.warmup)
+    sc = _apply_modes(_scenario("c6", max(legs.values()) + 1))
     P = 1
     for n in sc.cfg.N:
         P *= n
@@ -638,7 +696,7 @@ def bench_4d(args, ws, rank, pg, local):
     value = ws * P * args.steps / (t_ms * 1e-3)
     e2e_ms = _max_over_ranks(pg, time_e2e(sc, prec, min(args.steps, len(sc.z) - 3)))
     f.close()
-    f64, ms64, l64 = time_gpu(sc, "fp64", max(3, min(args.steps // 4, 10)), args.warmup)
+    f64, ms64, l64 = time_gpu(sc, "fp64", legs["fp64"] - args.warmup, args.warmup)
     ms64_step = _max_over_ranks(pg, sum(ms64) / len(ms64))
     f64.close()
 
@@ -704,8 +762,8 @@ def bench_4d(args, ws, rank, pg, local):
         "clocks": clk.summary(),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        epochs = 2
-        t = oracle_sample("c6", epochs)
+        epochs = legs["parity"]
+        t = oracle_sample("c6", epochs, total=len(sc.z))
         per = t["seconds"] / t["epochs"]
         line["cpu_baseline"] = {"value": P / per, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{epochs} epochs of the {sc.name} filter, single thread"}
@@ -730,13 +788,13 @@ def bench_4d(args, ws, rank, pg, local):
         print(json.dumps(line))
 
 
-def main():
+def make_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--workload", default="c4")
     ap.add_argument("--precision", default="fp16x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--count", type=int, default=4096, help="filters of the c4 batch workload (c5: 10000)")
@@ -747,7 +805,11 @@ def main():
                     help="c2/c3/c6: diffusion multiplier (Euler product or exact in time)")
     ap.add_argument("--realign", default="multilinear", choices=["multilinear", "shear"],
                     help="c2: fill of a re-aligned frame (shear: band-limited, n_x = 2)")
-    args = ap.parse_args()
+    return ap
+
+
+def main(argv=None):
+    args = make_parser().parse_args(argv)
     args.warmup = max(3, args.warmup)
     MODES["psi"], MODES["realign"] = args.psi, args.realign
     ws, rank, local, pg = _dist()
@@ -766,7 +828,8 @@ def main():
         if pg is not None:
             pg.destroy_process_group()
         return
-    sc = _apply_modes(_scenario(args.workload, args.warmup + args.steps + 1))
+    legs = leg_epochs(args.workload, args.steps, args.warmup)
+    sc = _apply_modes(_scenario(args.workload, max(legs.values()) + 1))
     P = 1
     for n in sc.cfg.N:
         P *= n
@@ -786,7 +849,7 @@ def main():
     mom_bytes = 8 * (len(sc.cfg.N) + len(sc.cfg.N) ** 2)
 
     # plain float64 GPU path on the same workload
-    f64, ms64, l64 = time_gpu(sc, "fp64", max(3, min(args.steps // 4, 40 if sc.cfg.nx == 2 else 5)), args.warmup)
+    f64, ms64, l64 = time_gpu(sc, "fp64", legs["fp64"] - args.warmup, args.warmup)
     ms64_step = _max_over_ranks(pg, sum(ms64) / len(ms64))
 
     kernel_ms = float(np.mean(ms))
@@ -818,8 +881,8 @@ def main():
         "clocks": clk.summary(),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and sc.cfg.nx in (2, 3):
-        epochs = 60 if sc.cfg.nx == 2 else 10
-        t = oracle_sample(args.workload, epochs)
+        epochs = legs["parity"]
+        t = oracle_sample(args.workload, epochs, total=len(sc.z))
         per = t["seconds"] / t["epochs"]
         # parity of the sample: same epochs on the GPU path from the prior
         g = type(f)(sc.cfg, precision=args.precision, psi_mode=MODES["psi"])

@@ -1,0 +1,50 @@
+"""The benchmark's argument and scenario plumbing, without a GPU.
+
+Every leg of a bench run (warm-up and timed steps, the end-to-end loop, the
+float64 comparator, the oracle parity sample) indexes into a seeded scenario;
+these tests build the scenarios the way bench.py does, for the driver's
+arguments and for edge cases, and check that each leg stays inside.
+"""
+import numpy as np
+import pytest
+
+import bench
+import workloads as w
+
+
+def test_default_workload_is_the_batch():
+    args = bench.make_parser().parse_args([])
+    assert args.workload == "c4"
+    assert args.gpus == 1 and args.impl == "native"
+
+
+@pytest.mark.parametrize("workload", ["c2", "c3", "c6"])
+@pytest.mark.parametrize("steps,warmup", [(20, 5), (1, 3), (200, 10), (3, 100)])
+def test_single_filter_legs_fit_their_scenario(workload, steps, warmup):
+    warmup = max(3, warmup)
+    legs = bench.leg_epochs(workload, steps, warmup)
+    sc = bench._scenario(workload, max(legs.values()) + 1)
+    for name, n in legs.items():
+        assert len(sc.z) >= n, (name, n, len(sc.z))
+    # the oracle subprocess builds the same scenario (same expression, same length)
+    expr = bench._scenario_expr(workload, max(legs["parity"], len(sc.z)))
+    sc2 = eval(expr, {"w": w})
+    assert len(sc2.z) == len(sc.z)
+    np.testing.assert_array_equal(sc2.z, sc.z)
+
+
+@pytest.mark.parametrize("steps,warmup", [(20, 5), (1, 3), (200, 10)])
+def test_batch_legs_fit(steps, warmup):
+    warmup = max(3, warmup)
+    epochs = warmup + steps + 1
+    cfgs, meas, dt, truth, z = w.c4_batch(count=8, epochs=epochs)
+    # timed steps and the end-to-end loop read z[:, warmup + k]
+    assert warmup + steps - 1 < z.shape[1]
+    assert warmup + min(5, steps) - 1 < z.shape[1]
+    # the oracle sample (8 epochs of its own c4_batch call) sees the same
+    # measurements as the batch's first epochs: draws are made epoch by epoch
+    _, _, _, _, z8 = w.c4_batch(count=8, epochs=8)
+    np.testing.assert_array_equal(z8[:, :min(8, epochs)], z[:, :min(8, epochs)])
+    ids = bench.c4_sample_ids(4096)
+    assert len(ids) == 256 and ids[0] == 0 and ids[-1] == 4095 and len(set(ids)) == 256
+    assert len(bench.c4_sample_ids(100)) == 100
