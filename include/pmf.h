@@ -326,12 +326,14 @@ void pmf_server_destroy(pmf_server* s);
 /* ---- moments without device allocation --------------------------------------
  * The paper has no counterpart to this entry point: it is a service for
  * callers that cannot allocate device memory when they need the moments --
- * code inside CUDA graph stream capture (cudaMalloc is not capturable), hosts
- * whose own allocator owns all device memory, real-time loops that must not
- * allocate.  It computes S0 = sum w and the mean and covariance of the point
- * sums of a float64 weight array on a frame x = c + M u, u_m = j_m - (N_m-1)/2,
- * exactly like pmf_moments does for a context (mean = c + M E[u],
- * cov = M Cov[u] M^T, weights need not be normalised).
+ * hosts whose own allocator owns all device memory and forbids libraries to
+ * allocate, and real-time loops that must not pay the latency or risk the
+ * failure of a cudaMalloc.  It computes S0 = sum w and the mean and covariance
+ * of the point sums of a float64 weight array on a frame x = c + M u,
+ * u_m = j_m - (N_m-1)/2, exactly like pmf_moments does for a context
+ * (mean = c + M E[u], cov = M Cov[u] M^T, weights need not be normalised).
+ * If S0 is zero or not finite, out[0] = S0 and the mean and covariance are
+ * written as NaN.
  *
  *   weights : device pointer, prod N_m float64 values, C-order (caller-owned)
  *   nx, N   : state dimension (1..PMF_MAX_NX) and points per axis (host)

@@ -1,13 +1,13 @@
 // Moments of a float64 weight array without any device allocation.
 //
 // Some callers cannot call cudaMalloc at the moment they need the moments:
-// code running while a stream is being captured into a CUDA graph (allocation
-// is not a capturable operation), hosts that own every byte of device memory
-// through their own allocator and forbid libraries from allocating, and
-// real-time loops that must not pay the latency or the failure mode of an
-// allocation.  pmf_moments_noalloc serves them: it is the block-partial-sum
-// moment reduction of the float64 path with its partial sums in a fixed
-// file-scope device array instead of a context's scratch buffer.
+// hosts that own every byte of device memory through their own allocator and
+// forbid libraries from allocating, and real-time loops that must not pay the
+// latency or the failure mode of an allocation (cudaMalloc may synchronise
+// the device and may fail under memory pressure).  pmf_moments_noalloc serves
+// them: it is the block-partial-sum moment reduction of the float64 path with
+// its partial sums in a fixed file-scope device array instead of a context's
+// scratch buffer.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -109,6 +109,11 @@ __global__ void k_finish(Geo g, const double* __restrict__ part, int nblocks, do
   const int n = g.nx;
   const double S0 = tot[0];
   out[0] = S0;
+  if (S0 == 0.0 || !isfinite(S0)) {
+    // no mass (or a non-finite sum): the moments are undefined
+    for (int i = 0; i < n + n * n; ++i) out[1 + i] = nan("");
+    return;
+  }
   double mu[4], S2[16], Cu[16], cov[16];
   for (int a2 = 0; a2 < n; ++a2) mu[a2] = tot[1 + a2] / S0;
   for (int i = 0; i < n; ++i)
@@ -135,11 +140,11 @@ extern "C" int pmf_moments_noalloc(const double* weights, int nx, const int* N, 
   for (int m = 0; m < nx; ++m) {
     if (N[m] < 1) return PMF_ERR_ARG;
     g.N[m] = N[m];
-    g.P *= N[m];
+    g.P *= N[m];   // at most 2^20 * (2^31 - 1): no overflow before the check below
+    if (g.P > PMF_NOALLOC_MAX_POINTS) return PMF_ERR_ARG;
     g.c[m] = c[m];
   }
   for (int i = 0; i < nx * nx; ++i) g.M[i] = M[i];
-  if (g.P > PMF_NOALLOC_MAX_POINTS) return PMF_ERR_ARG;
   double* part = nullptr;
   if (scratch_for_current_device(&part) != cudaSuccess) return PMF_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)cuda_stream;

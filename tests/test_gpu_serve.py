@@ -39,7 +39,7 @@ def test_alone_equals_in_the_mix():
         alone, afid = _server(wl, ids=[f])
         alone.replay(wl.t_arrival[sel], np.full(sel.sum(), afid[f]), wl.z[sel], wl.taus[sel])
         P_one, c_one, M_one = alone.pdf(afid[f])
-        assert rel_l1(P_mix, P_one) <= 1e-6, nx
+        assert np.array_equal(P_mix, P_one), (nx, rel_l1(P_mix, P_one))
         assert np.array_equal(c_mix, c_one) and np.array_equal(M_mix, M_one), nx
         alone.close()
     s.close()
@@ -59,7 +59,8 @@ def test_server_matches_single_filter_api():
             g.step(wl.meas[f], wl.z[r, :nx], wl.taus[r])
         P1, c1, M1 = g.pdf()
         P2, c2, M2 = s.pdf(fid[f])
-        assert rel_l1(P2, P1) <= 1e-6, nx
+        assert np.array_equal(P2, P1), (nx, rel_l1(P2, P1))
+        assert np.array_equal(c2, c1) and np.array_equal(M2, M1), nx
         g.close()
     s.close()
 
