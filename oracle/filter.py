@@ -349,23 +349,6 @@ class OracleFilter:
         s = quantize_shift(Minv @ (m - self.c))
         return {"realigned": False, "rho": rho, "D": D, "s": s}
 
-    def frame_from_target(self, tau: float, c_after, M_after) -> dict:
-        """Test helper: the regrid decision whose frame, moved over tau, is the
-        given (c_after, M_after) (a frame chosen by another implementation from
-        its own moments).  The decision is read back onto the quantisation
-        lattices, so it is exact when the target lies on them."""
-        Phi = model.expm(self.A * tau)
-        Mt = np.linalg.solve(Phi, np.asarray(M_after, dtype=float))
-        ct = np.linalg.solve(Phi, np.asarray(c_after, dtype=float))
-        Minv = np.linalg.inv(self.M)
-        s = quantize_shift(Minv @ (ct - self.c))
-        R = Minv @ Mt                       # diagonal iff the frame was only rescaled
-        off = np.abs(R - np.diag(np.diag(R))).max()
-        if off <= 1e-9 * np.abs(np.diag(R)).max():
-            D = np.array([quantize_scale(d) for d in np.diag(R)])
-            return {"realigned": False, "rho": None, "D": D, "s": s}
-        return {"realigned": True, "rho": None, "M": quantize_matrix(Mt), "s": s}
-
     def regrid(self, tau: float, choice: dict = None) -> dict:
         """Re-centre and re-size the grid for the prediction over tau (head of the
         time update), with the decision of choose_frame (or the one given)."""

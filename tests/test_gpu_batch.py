@@ -79,6 +79,21 @@ def test_admission_by_budget():
     assert e.value.code == ERR_ADMISSION
 
 
+def _oracle_fails(cfg, meas, zs, dt, epochs):
+    from oracle.filter import Degenerate, OracleFilter
+    o = OracleFilter(cfg)
+    try:
+        for k in range(epochs):
+            o.meas_update(meas, zs[k])
+            m, C = o.moments()
+            if not (np.all(np.isfinite(C)) and np.all(np.linalg.eigvalsh(C) > 0)):
+                return True
+            o.time_update(dt)
+    except (Degenerate, np.linalg.LinAlgError, FloatingPointError, ValueError):
+        return True
+    return False
+
+
 def test_full_c4_workload_sampled():
     """4096 filters, sizes from {32..128}^2, in the benchmarked launch configuration.
 
@@ -97,6 +112,11 @@ def test_full_c4_workload_sampled():
         b.step(ids, z[:, k], dt)
         bad |= b.status() != 0
     assert bad.sum() <= 0.01 * len(cfgs), bad.sum()
+    # a filter the GPU reports as degenerate is one the oracle cannot carry
+    # either: its normaliser fails, its covariance stops being positive
+    # definite, or its frame decision has no Cholesky factor
+    for i in np.nonzero(bad)[0]:
+        assert _oracle_fails(cfgs[i], meas, z[i], dt, epochs), i
     rng = np.random.default_rng(0)
     checked = 0
     for i in rng.permutation(len(cfgs)):

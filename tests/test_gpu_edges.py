@@ -6,7 +6,7 @@ import pytest
 
 import workloads as w
 from oracle.filter import OracleFilter
-from tests._parity import compare, max_errors
+from tests._parity import check_own_decisions, compare, displacement_bound, max_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -54,13 +54,12 @@ def test_horizon_of_one_substep(make, prec, bar):
     gpu.meas_update(sc.meas, sc.z[0])
     orc.meas_update(sc.meas, sc.z[0])
     gpu.time_update(tau)
-    if sc.cfg.nx == 4 and prec != "fp64":
-        _, c, M = gpu.pdf()
-        orc.time_update(tau, orc.frame_from_target(tau, c, M))
-    else:
-        orc.time_update(tau)
+    orc.time_update(tau)
     e = compare(gpu, orc)
-    assert e["l1"] <= bar and e["frame"] <= bar, e
+    _, c, M = gpu.pdf()
+    # both on their own regrid decisions (see check_own_decisions)
+    shift = displacement_bound(orc, c, M) if prec != "fp64" else 0.0
+    assert e["l1"] <= bar + 2.0 * shift and e["frame"] <= max(bar, 1e-3 if shift else 0.0), e
     gpu.close()
 
 
@@ -70,7 +69,7 @@ def test_largest_grids_per_axis():
     cases = [(w.c1_scenario(N=512, epochs=2), "fp16x3", {}),
              (w.small_2d_scenario(N=(128, 16), epochs=2), "fp16x3", {}),
              (w.small_3d_scenario(N=(128, 16, 32), epochs=2), "fp16x3", {}),
-             (w.c6_scenario(N=(64, 6, 8, 6), epochs=2, local=True), "fp16x3", {"follow_frame": True})]
+             (w.c6_scenario(N=(64, 6, 8, 6), epochs=2, local=True), "fp16x3", {})]
     for sc, prec, kw in cases:
-        worst, _ = max_errors(sc, precision=prec, **kw)
-        assert worst["l1"] <= 1e-5 and worst["frame"] <= 1e-5, (sc.cfg.N, worst)
+        worst, log = max_errors(sc, precision=prec, **kw)
+        check_own_decisions(log, 1e-5)

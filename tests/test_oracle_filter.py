@@ -335,29 +335,6 @@ def test_shear_realignment_tracks_kalman():
     assert es[6:].max() < em[6:].max() / 1e3
 
 
-def test_frame_from_target_recovers_the_decision():
-    """Reading a regrid decision back from the moved frame it produced gives the
-    same decision (lattice values exactly), in both branches and in 4-D."""
-    for sc in (w.c6_scenario(N=(10, 8, 12, 8), epochs=3, local=True), _cv_scenario((32, 32))):
-        a = of.OracleFilter(sc.cfg)
-        b = of.OracleFilter(sc.cfg)
-        kinds = set()
-        for k in range(sc.epochs):
-            a.meas_update(sc.meas, sc.z[k])
-            b.meas_update(sc.meas, sc.z[k])
-            own = a.choose_frame(sc.dt)
-            a.time_update(sc.dt)
-            got = b.frame_from_target(sc.dt, a.c, a.M)
-            assert got["realigned"] == own["realigned"]
-            kinds.add(own["realigned"])
-            np.testing.assert_array_equal(got["s"], own["s"])
-            key = "M" if own["realigned"] else "D"
-            np.testing.assert_array_equal(got[key], own[key])
-            b.time_update(sc.dt, got)
-            np.testing.assert_array_equal(b.P, a.P)
-        assert kinds == {True, False} or sc.cfg.nx == 4
-
-
 def test_4d_terrain_cycle_self_converges():
     """The Sec. VI terrain measurement has no closed form (parity unpinned beyond
     this): unit mass and PSD covariance after every update, the moments of the
