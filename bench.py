@@ -176,8 +176,8 @@ def _launch_names(sc):
 STEP_ITEM_BYTES = 32
 TIME_CONSTS_BYTES = 5832
 TRAFFIC_C2 = 345344.0
-TRAFFIC_C4_PER_POINT = (50111744.0 + 7359488.0) / 10976512.0
-BATCH_KERNEL = "k_fused2d_batch"
+TRAFFIC_C4_PER_POINT = None   # not captured for the current batch kernels
+BATCH_KERNEL = "k_front2d + k_fused2d_planned<128> + k_fused2d_planned<64> (one graph per epoch)"
 
 
 def _flops_per_step(N):

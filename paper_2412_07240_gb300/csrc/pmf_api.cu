@@ -410,7 +410,8 @@ struct pmf_batch {
   StepItem* d_items = nullptr;
   double* d_partials = nullptr;
   double* d_aux = nullptr;
-  std::vector<void*> tables;          // per distinct N
+  uint8_t* d_plan = nullptr;          // per filter: the front kernel's results of an epoch
+  std::vector<void*> tables;          // per distinct N (and size class)
   std::vector<double> tau;            // tau of the constants resident for each filter
   int* d_ids = nullptr;               // filter ids of a moments/status query
   double* d_gather = nullptr;         // 8 doubles per queried filter
@@ -421,8 +422,12 @@ struct pmf_batch {
   cudaEvent_t ev[2] = {nullptr, nullptr};
   int parity = 0;
   cudaStream_t cap = nullptr;                 // capture stream of the epoch graphs
+  cudaStream_t cap2 = nullptr;                // second branch: the size-64 transform kernel
+  cudaEvent_t evf = nullptr, evj = nullptr;   // fork and join of the two branches
   cudaGraphExec_t gx[2] = {nullptr, nullptr}; // item copy + batch kernel, per parity buffer
   int gk[2] = {0, 0};                         // batch size each graph was captured for
+  int gk128[2] = {0, 0};                      // ... and its number of size-128 filters
+  int per_epoch = 0;                          // kernel launches in one epoch graph
   long long bytes = 0, launches = 0;
   std::string err;
 };
@@ -439,6 +444,7 @@ void free_batch(pmf_batch* b) {
   cudaFree(b->d_items);
   cudaFree(b->d_partials);
   cudaFree(b->d_aux);
+  cudaFree(b->d_plan);
   cudaFree(b->d_ids);
   cudaFree(b->d_gather);
   cudaFreeHost(b->h_ids);
@@ -447,6 +453,9 @@ void free_batch(pmf_batch* b) {
   for (int i = 0; i < 2; ++i)
     if (b->gx[i]) cudaGraphExecDestroy(b->gx[i]);
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->cap2) cudaStreamDestroy(b->cap2);
+  if (b->evf) cudaEventDestroy(b->evf);
+  if (b->evj) cudaEventDestroy(b->evj);
   for (int i = 0; i < 2; ++i) {
     cudaFreeHost(b->h_items[i]);
     cudaFreeHost(b->h_tc[i]);
@@ -466,7 +475,7 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
   std::string why;
   const int prec = cfgs[0].precision;
   std::vector<MeasParams> mps(count);
-  std::vector<int> sizes;
+  std::vector<int> sizes;             // key N * 1000 + size class of the table
   long long wfloats = 0;
   for (int i = 0; i < count; ++i) {
     int rc = validate_config(&cfgs[i], &why);
@@ -477,15 +486,19 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
     if (rc) return rc;
     rc = meas_params(2, &models[i], &mps[i], &why);
     if (rc) return rc;
-    for (int a = 0; a < 2; ++a)
-      if (std::find(sizes.begin(), sizes.end(), cfgs[i].N[a]) == sizes.end()) sizes.push_back(cfgs[i].N[a]);
+    const int cls = tc_class(cfgs[i].N[0], cfgs[i].N[1]);
+    for (int a = 0; a < 2; ++a) {
+      const int key = cfgs[i].N[a] * 1000 + cls;
+      if (std::find(sizes.begin(), sizes.end(), key) == sizes.end()) sizes.push_back(key);
+    }
     wfloats += 2LL * cfgs[i].N[0] * cfgs[i].N[1];
   }
   long long bytes = wfloats * 4 + (long long)count * (sizeof(DevState) + sizeof(MeasParams) +
                                                        sizeof(TimeConsts) + sizeof(FilterSlot) +
-                                                       sizeof(StepItem) + sizeof(int) + 8 * sizeof(double)) +
+                                                       sizeof(StepItem) + sizeof(int) + 8 * sizeof(double) +
+                                                       (long long)tc_plan_bytes()) +
                     sizeof(double) * (kMomentSlots * 4096 + 16 * (long long)count);
-  for (int N : sizes) bytes += (long long)tc_axis_table_bytes(N, prec);
+  for (int key : sizes) bytes += (long long)tc_axis_table_bytes(key / 1000, prec, key % 1000);
   if (hbm_budget && (size_t)bytes > hbm_budget) return PMF_ERR_ADMISSION;
 
   pmf_batch* b = new (std::nothrow) pmf_batch();
@@ -511,6 +524,7 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
   BALLOC(b->d_items, sizeof(StepItem) * count);
   BALLOC(b->d_partials, sizeof(double) * kMomentSlots * 4096);
   BALLOC(b->d_aux, sizeof(double) * kAuxSize * count);
+  BALLOC(b->d_plan, tc_plan_bytes() * count);
   BALLOC(b->d_ids, sizeof(int) * count);
   BALLOC(b->d_gather, sizeof(double) * 8 * count);
 #undef BALLOC
@@ -530,7 +544,7 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
   std::vector<void*> tabs(sizes.size());
   std::vector<size_t> hbytes(sizes.size());
   for (size_t s = 0; s < sizes.size(); ++s) {
-    if (tc_build_axis_table(sizes[s], prec, &tabs[s], &hbytes[s]) != PMF_OK) {
+    if (tc_build_axis_table(sizes[s] / 1000, prec, &tabs[s], &hbytes[s], sizes[s] % 1000) != PMF_OK) {
       b->tables = tabs;
       free_batch(b);
       return PMF_ERR_OOM;
@@ -555,8 +569,9 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
     sl.buf0 = b->d_w + off;
     sl.buf1 = b->d_w + off + P;
     off += 2 * P;
+    const int cls = tc_class(c.N[0], c.N[1]);
     for (int a = 0; a < 2; ++a) {
-      const size_t s = std::find(sizes.begin(), sizes.end(), c.N[a]) - sizes.begin();
+      const size_t s = std::find(sizes.begin(), sizes.end(), c.N[a] * 1000 + cls) - sizes.begin();
       sl.hart[a] = (const uint8_t*)tabs[s];
       sl.sctab[a] = (const float*)((const uint8_t*)tabs[s] + hbytes[s]);
     }
@@ -564,6 +579,7 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
     sl.N1 = c.N[1];
     sl.mp = b->d_mp + i;
     sl.tc = b->d_tc + i;
+    sl.plan = b->d_plan + tc_plan_bytes() * i;
   }
   cudaMemcpy(b->d_st, hst.data(), sizeof(DevState) * count, cudaMemcpyHostToDevice);
   cudaMemcpy(b->d_mp, mps.data(), sizeof(MeasParams) * count, cudaMemcpyHostToDevice);
@@ -623,13 +639,18 @@ int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_
       b->tau[id] = tau;
     }
   }
-  // larger grids first: the hardware hands CTAs out in order, so the longest
-  // run first and the tail is made of small filters
+  // size class 128 first, then 64 (the two transform kernels take the two
+  // ranges); within a class larger grids first: the hardware hands CTAs out
+  // in order, so the longest run first and the tail is made of small filters
+  auto cls = [&](const StepItem& x) { return tc_class(b->cfgs[x.slot].N[0], b->cfgs[x.slot].N[1]); };
   std::vector<StepItem> sorted(items, items + k);
   std::stable_sort(sorted.begin(), sorted.end(), [&](const StepItem& x, const StepItem& y) {
-    return b->npts[x.slot] > b->npts[y.slot];
+    const int cx = cls(x), cy = cls(y);
+    return cx != cy ? cx > cy : b->npts[x.slot] > b->npts[y.slot];
   });
   std::copy(sorted.begin(), sorted.end(), items);
+  int k128 = 0;
+  while (k128 < k && cls(items[k128]) == 128) ++k128;
   for (int j = 0; j < nchanged; ++j)
     if (cudaMemcpyAsync(b->d_tc + changed[j], &stage[j], sizeof(TimeConsts), cudaMemcpyHostToDevice,
                         b->stream) != cudaSuccess)
@@ -637,16 +658,21 @@ int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_
   // the item copy and the batch kernel replay as one CUDA graph, captured
   // once per parity buffer and batch size (the copy reads this parity's
   // pinned items when the graph runs)
-  if (!b->gx[p] || b->gk[p] != k) {
+  if (!b->gx[p] || b->gk[p] != k || b->gk128[p] != k128) {
     if (b->gx[p]) {
       cudaGraphExecDestroy(b->gx[p]);
       b->gx[p] = nullptr;
     }
     if (!b->cap && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return PMF_ERR_CUDA;
+    if (!b->cap2 && (cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking) != cudaSuccess ||
+                     cudaEventCreateWithFlags(&b->evf, cudaEventDisableTiming) != cudaSuccess ||
+                     cudaEventCreateWithFlags(&b->evj, cudaEventDisableTiming) != cudaSuccess))
+      return PMF_ERR_CUDA;
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PMF_ERR_CUDA;
     cudaMemcpyAsync(b->d_items, items, sizeof(StepItem) * k, cudaMemcpyHostToDevice, b->cap);
-    tc_batch_step(b->precision, b->d_slots, b->d_items, k, b->cap);
+    b->per_epoch = tc_batch_epoch(b->precision, b->d_slots, b->d_items, k, k128, b->cap, nullptr, b->cap2, b->evf,
+                                  b->evj);
     if (cudaStreamEndCapture(b->cap, &g) != cudaSuccess) return PMF_ERR_CUDA;
     const cudaError_t e = cudaGraphInstantiate(&b->gx[p], g, 0);
     cudaGraphDestroy(g);
@@ -655,10 +681,11 @@ int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_
       return PMF_ERR_CUDA;
     }
     b->gk[p] = k;
+    b->gk128[p] = k128;
   }
   if (cudaGraphLaunch(b->gx[p], b->stream) != cudaSuccess) return PMF_ERR_CUDA;
   cudaEventRecord(b->ev[p], b->stream);
-  b->launches += 1;
+  b->launches += b->per_epoch;
   return cudaGetLastError() == cudaSuccess ? PMF_OK : PMF_ERR_CUDA;
 }
 

@@ -117,6 +117,7 @@ struct SFilter {
   MeasParams* d_mp = nullptr;
   TcTables tct{};          // 2-D/3-D: shared tables (owned by the server)
   void* tc3 = nullptr;     // 3-D pipeline state (owned)
+  void* plan = nullptr;    // 2-D: the batch front kernel's results (owned)
   // request in progress
   bool busy = false;
   long long cur = -1;
@@ -176,6 +177,7 @@ void free_filter(pmf_server* s, SFilter& f) {
   cudaFree(f.st);
   cudaFree(f.buf);
   cudaFree(f.d_mp);
+  cudaFree(f.plan);
   tc3_free(f.tc3);
   s->bytes -= f.bytes;
   f = SFilter{};
@@ -188,7 +190,9 @@ int sync_all(pmf_server* s) {
 }
 
 // Shared device table of an axis size: kind 1 = 1-D kernel table, 2 = split
-// Hartley planes + sinc table of the tensor-core kernels.  Adds new bytes to *add.
+// Hartley planes + sinc table of the tensor-core kernels (size class 128),
+// 3 = the same for the size-64 class of the batched 2-D kernels.  Adds new
+// bytes to *add.
 int table_for(pmf_server* s, int kind, int N, void** out, size_t* hb, long long* add, bool create) {
   const long long key = (long long)kind * 100000 + N;
   auto it = s->tables.find(key);
@@ -197,12 +201,14 @@ int table_for(pmf_server* s, int kind, int N, void** out, size_t* hb, long long*
     if (hb) *hb = s->hart_bytes[key];
     return PMF_OK;
   }
-  const long long nb = kind == 1 ? (long long)tc1_table_bytes(N) : (long long)tc_axis_table_bytes(N, s->precision);
+  const int cls = kind == 3 ? 64 : 128;
+  const long long nb =
+      kind == 1 ? (long long)tc1_table_bytes(N) : (long long)tc_axis_table_bytes(N, s->precision, cls);
   *add += nb;
   if (!create) return PMF_OK;
   void* t = nullptr;
   size_t h = 0;
-  const int rc = kind == 1 ? tc1_build_table(N, &t) : tc_build_axis_table(N, s->precision, &t, &h);
+  const int rc = kind == 1 ? tc1_build_table(N, &t) : tc_build_axis_table(N, s->precision, &t, &h, cls);
   if (rc) {
     cudaFree(t);
     return rc;
@@ -268,11 +274,16 @@ int launch_batch(pmf_server* s, const double* z, const double* taus) {
 
   // host constants (parallel), items
   std::vector<TimeConsts> tc3(its.size());
-  int slot[2] = {0, 0};
+  // 2-D items: size class 128 first, then 64 (the two transform kernels take the two ranges)
+  auto cls2 = [&](int id) { return tc_class(s->f[id].cfg.N[0], s->f[id].cfg.N[1]); };
+  int n128 = 0;
+  for (const Item& it : its)
+    if (it.kind == 1 && cls2(it.id) == 128) ++n128;
+  int slot[2] = {0, 0}, slot64 = n128;
   std::vector<int> pos(its.size());
   for (size_t i = 0; i < its.size(); ++i) {
     const int k = its[i].kind;
-    pos[i] = k < 2 ? slot[k]++ : 0;
+    pos[i] = k == 0 ? slot[0]++ : k == 1 ? (cls2(its[i].id) == 128 ? slot[1]++ : slot64++) : 0;
   }
   std::atomic<int> bad{0};
   const std::function<void(int)> fill = [&](int i) {
@@ -303,7 +314,7 @@ int launch_batch(pmf_server* s, const double* z, const double* taus) {
             cudaSuccess)
       return sfail(s, PMF_ERR_CUDA, "batch copies");
     s->launches += k == 0 ? tc1_batch_step(s->d_slots1, b.d_items[0], b.d_tc[0], n, s->s[0])
-                          : tc_batch_step(s->precision, s->d_slots2, b.d_items[1], n, s->s[1], b.d_tc[1]);
+                          : tc_batch_epoch(s->precision, s->d_slots2, b.d_items[1], n, n128, s->s[1], b.d_tc[1]);
     cudaEventRecord(b.ev[k], s->s[k]);
     b.used[k] = true;
   }
@@ -439,12 +450,15 @@ int pmf_server_admit(pmf_server* s, const pmf_config* cfg, const pmf_meas* model
   for (int a = 0; a < n; ++a) P *= cfg->N[a];
   long long bytes = (long long)sizeof(DevState) + 8 * P + (long long)sizeof(MeasParams);
   if (n == 3) bytes += (long long)tc3_state_bytes();
+  if (n == 2) bytes += (long long)tc_plan_bytes();
+  // table kind of this filter's axes (the 2-D size-64 class has its own layout)
+  const int tkind = n == 1 ? 1 : (n == 2 && tc_class(cfg->N[0], cfg->N[1]) == 64 ? 3 : 2);
   long long tbytes = 0;
   void* tab = nullptr;
   for (int a = 0; a < n; ++a) {
     bool seen = false;
     for (int b = 0; b < a; ++b) seen = seen || cfg->N[b] == cfg->N[a];
-    if (!seen) table_for(s, n == 1 ? 1 : 2, cfg->N[a], &tab, nullptr, &tbytes, false);
+    if (!seen) table_for(s, tkind, cfg->N[a], &tab, nullptr, &tbytes, false);
   }
   if (s->budget && (size_t)(s->bytes + bytes + tbytes) > s->budget)
     return sfail(s, PMF_ERR_ADMISSION, "device-memory budget");
@@ -460,10 +474,11 @@ int pmf_server_admit(pmf_server* s, const pmf_config* cfg, const pmf_meas* model
             cudaMalloc(&f.buf, sizeof(float) * 2 * P) == cudaSuccess &&
             cudaMalloc(&f.d_mp, sizeof(MeasParams)) == cudaSuccess;
   if (ok && n == 3) ok = tc3_alloc(&f.tc3) == PMF_OK;
+  if (ok && n == 2) ok = cudaMalloc(&f.plan, tc_plan_bytes()) == cudaSuccess;
   size_t hb[3] = {0, 0, 0};
   void* tabs[3] = {nullptr, nullptr, nullptr};
   long long added = 0;
-  for (int a = 0; a < n && ok; ++a) ok = table_for(s, n == 1 ? 1 : 2, cfg->N[a], &tabs[a], &hb[a], &added, true) == PMF_OK;
+  for (int a = 0; a < n && ok; ++a) ok = table_for(s, tkind, cfg->N[a], &tabs[a], &hb[a], &added, true) == PMF_OK;
   s->bytes += added;
   if (!ok) {
     f.bytes = 0;
@@ -508,6 +523,7 @@ int pmf_server_admit(pmf_server* s, const pmf_config* cfg, const pmf_meas* model
     sl.N1 = cfg->N[1];
     sl.mp = f.d_mp;
     sl.tc = nullptr;
+    sl.plan = f.plan;
     ok = cudaMemcpyAsync(s->d_slots2 + id, &sl, sizeof(sl), cudaMemcpyHostToDevice, st) == cudaSuccess;
   }
   ok = ok && cudaStreamSynchronize(st) == cudaSuccess && cudaGetLastError() == cudaSuccess;

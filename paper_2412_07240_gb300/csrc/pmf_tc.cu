@@ -41,13 +41,27 @@ namespace pmf {
 
 namespace {
 
-constexpr int kThreads = 512;               // 16 warps: 4 TMEM lane quadrants x 4 column groups
-constexpr int kOffA = 0;                     // A operand planes [0, 64K)
-constexpr int kOffW = 65536;                 // W operand planes [64K, 128K)
-constexpr int kOffS = 131072;                // float32 staging, 128 rows x kSStr
-constexpr int kSStr = 132;                   // staging row stride (floats; conflict-free row access)
-constexpr int kSmemBytes = kOffS + 128 * kSStr * 4;
 constexpr uint32_t kTmemCols = 128;
+
+// Size classes of the fused kernel: C is the largest axis a CTA holds.
+//   C = 128: 512 threads (4 TMEM lane quadrants x 4 column groups), 16-bit
+//            operand planes of 128 x 128, one CTA per SM;
+//   C = 64 : 256 threads (4 quadrants x 2 column groups), planes of
+//            128 rows x 64 (A) and 64 x 64 (W), three CTAs per SM.
+// Dynamic shared memory: A operand planes, W operand planes, float32 staging
+// of C rows x (C + 4) floats (the padding makes row access conflict-free).
+template <int P, int C>
+struct Smem {
+  static constexpr int threads = C == 128 ? 512 : 256;
+  static constexpr int sstr = C + 4;
+  static constexpr int offA = 0;
+  static constexpr int offW = Fmt<P>::planes * Lay<P, C>::plane;
+  static constexpr int offS = offW + Fmt<P>::planes * Lay<P, C>::wplane;
+  static constexpr int bytes = offS + C * sstr * 4;
+};
+constexpr int kThreads = 512;                // the single-filter kernel (class 128)
+constexpr int kSmemBytes = Smem<PMF_PREC_FP16X3, 128>::bytes;
+static_assert(Smem<PMF_PREC_TF32, 128>::bytes == kSmemBytes, "one dynamic size for every class-128 format");
 
 // One filter launched alone: everything by value in the kernel parameters.
 struct FusedJob {
@@ -72,15 +86,30 @@ struct FusedView {
   const MeasParams* mp;     // measurement model
   const double* z;          // measurement of this epoch
   const TimeConsts* tc;     // model constants of this time update
+  const struct BatchPlan* plan;   // planned transform kernel: the front kernel's results
 };
 
-struct Shared {
-  TimeConsts tc;           // copies of the update's constants and measurement model
+// The constants of the update are kept in shared memory only by the kernels
+// that compute the frame (the fused kernel and the batch front kernel); the
+// planned transform kernel reads the front kernel's results instead.
+template <bool kKeep>
+struct TcHolder {
+  TimeConsts tc;
+};
+template <>
+struct TcHolder<false> {};
+
+// Static shared memory of one CTA (threads T, largest axis C).
+template <int T, int C, bool kTc>
+struct SharedT : TcHolder<kTc> {
+  static constexpr int kT = T;
+  static constexpr int kC = C;
+  static constexpr int kStr = C + 4;   // staging row stride (floats)
   MeasParams mp;
   FrameState fs;           // working copy of the filter's frame state
   uint64_t mbar_mma, mbar_tma;
   uint32_t tmem;
-  int abort, degenerate;
+  int abort, degenerate, realign_mode;
   float redf[2][16];
   DF redm[16][6];
   double tot[10];
@@ -91,28 +120,44 @@ struct Shared {
   float g, ps, gsc;
   // frame-relative measurement constants
   float mc[2], mM[4], mr0[3], mRinv[9], mH[6], mcn;
-  RegridRows rows[2];      // regrid rows per axis
-  float sct[2][2 * (2 * 128 + 1)];   // per axis (cos, sin)(pi m / N), m = -N..N
+  RegridRowsT<C> rows[2];      // regrid rows per axis
+  float sct[2][2 * (2 * C + 1)];   // per axis (cos, sin)(pi m / N), m = -N..N
+};
+using Shared = SharedT<512, 128, true>;
+
+// What the batch front kernel hands to the planned transform kernel for one
+// filter and epoch: whether the time update runs, the pending frame after the
+// move (finalisation input), the sub-step coefficients in float32, the trace
+// factor and the regrid rows of both axes (unused after a re-alignment).
+struct BatchPlan {
+  double pend[24];
+  float pa[MAXL][2];
+  float pb[MAXL];
+  float g, gsc;
+  int ok, pad;
+  RegridRowsT<128> rows[2];
 };
 
 // Block max of non-negative per-thread values (result in every thread).
-__device__ __forceinline__ float block_max(Shared& sh, float v, int slot) {
+template <class SH>
+__device__ __forceinline__ float block_max(SH& sh, float v, int slot) {
   for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   if ((threadIdx.x & 31) == 0) sh.redf[slot][threadIdx.x >> 5] = v;
   __syncthreads();
   float m = 0.0f;
 #pragma unroll
-  for (int w = 0; w < kThreads / 32; ++w) m = fmaxf(m, sh.redf[slot][w]);
+  for (int w = 0; w < SH::kT / 32; ++w) m = fmaxf(m, sh.redf[slot][w]);
   return m;
 }
 
-__device__ __forceinline__ float block_min(Shared& sh, float v, int slot) {
+template <class SH>
+__device__ __forceinline__ float block_min(SH& sh, float v, int slot) {
   for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
   if ((threadIdx.x & 31) == 0) sh.redf[slot][threadIdx.x >> 5] = v;
   __syncthreads();
   float m = INFINITY;
 #pragma unroll
-  for (int w = 0; w < kThreads / 32; ++w) m = fminf(m, sh.redf[slot][w]);
+  for (int w = 0; w < SH::kT / 32; ++w) m = fminf(m, sh.redf[slot][w]);
   return m;
 }
 
@@ -121,7 +166,9 @@ __device__ __forceinline__ float block_min(Shared& sh, float v, int slot) {
 // double-float through both the warp and the cross-warp reduction; six lanes
 // of warp 0 convert the totals to float64 (GB300 issues float64 at a small
 // fraction of the float32 rate, so no per-warp or single-thread float64 loop).
-__device__ __forceinline__ void block_moments(Shared& sh, const Moments& m) {
+template <class SH>
+__device__ __forceinline__ void block_moments(SH& sh, const Moments& m) {
+  constexpr int kThreads = SH::kT;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   DF a[6];
 #pragma unroll
@@ -140,7 +187,8 @@ __device__ __forceinline__ void block_moments(Shared& sh, const Moments& m) {
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       a[i] = lane < kThreads / 32 ? sh.redm[lane][i] : DF{0.0f, 0.0f};
-      for (int o = kThreads / 64; o; o >>= 1) {
+      // the whole warp, so that lanes 0..5 below all hold the totals
+      for (int o = 16; o; o >>= 1) {
         DF b{__shfl_xor_sync(0xffffffffu, a[i].hi, o), __shfl_xor_sync(0xffffffffu, a[i].lo, o)};
         a[i] = df_add(a[i], b);
       }
@@ -165,7 +213,8 @@ struct MeasK {
   int kind, nz;
 };
 
-__device__ __forceinline__ MeasK meas_k(const Shared& sh) {
+template <class SH>
+__device__ __forceinline__ MeasK meas_k(const SH& sh) {
   return MeasK{sh.mc[0], sh.mc[1], sh.mM[0], sh.mM[1], sh.mM[2], sh.mM[3], sh.mr0[0], sh.mr0[1], sh.mH[0],
                sh.mH[1], sh.mH[2], sh.mH[3], sh.mRinv[0], sh.mRinv[1], sh.mRinv[3], sh.mcn, sh.mp.kind, sh.mp.nz};
 }
@@ -193,22 +242,23 @@ __device__ __forceinline__ float meas_e(const MeasK& k, float u0, float u1) {
 // Staging rows r < nr, columns < nc -> operand planes (scaled by s).
 // (consecutive threads take consecutive rows: in the core-matrix layout a row's
 // consecutive columns are 128 bytes apart, 8 consecutive rows share 128 bytes)
-template <int P>
+template <int P, int C = 128>
 __device__ __forceinline__ void stage_to_operand(uint8_t* A, const float* S, int nr, int nc, float s,
                                                  int t0, int tstep) {
   const int q4 = nc / 4;
   for (int t = t0; t < nr * q4; t += tstep) {
     const int r = t % nr, c = (t / nr) * 4;
-    store4<P>(A, r, c, *(const float4*)(S + r * kSStr + c), s);
+    store4<P, C>(A, r, c, *(const float4*)(S + r * (C + 4) + c), s);
   }
 }
 
+template <int T, int C>
 __device__ __forceinline__ float stage_max(const float* S, int nr, int nc) {
   const int q4 = nc / 4;
   float m = 0.0f;
-  for (int t = threadIdx.x; t < nr * q4; t += kThreads) {
+  for (int t = threadIdx.x; t < nr * q4; t += T) {
     const int r = t / q4, c = (t % q4) * 4;
-    m = amax4(m, *(const float4*)(S + r * kSStr + c));
+    m = amax4(m, *(const float4*)(S + r * (C + 4) + c));
   }
   return m;
 }
@@ -216,28 +266,30 @@ __device__ __forceinline__ float stage_max(const float* S, int nr, int nc) {
 // Out-of-line copies of the helpers called from several places of the epoch:
 // a kernel that runs once on cold caches fetches their code once (the batch
 // kernel, whose CTAs follow each other on an SM, keeps them inline).
-__device__ __noinline__ void block_moments_out(Shared& sh, const Moments& m) { block_moments(sh, m); }
+template <class SH>
+__device__ __noinline__ void block_moments_out(SH& sh, const Moments& m) { block_moments(sh, m); }
 __device__ __noinline__ bool finalize_warp_out(FrameState* st, const double* tot, int use_pending,
                                                const double* pend) {
   return finalize_warp<2>(st, tot, use_pending, pend);
 }
-template <int P>
-__device__ __noinline__ void build_interp_out(const RegridRows& rows, uint8_t* W, int N, const float* sctab, float sw,
-                                              int realign, int t0, int tstep) {
-  build_interp<P>(rows, W, N, sctab, sw, realign, t0, tstep);
+template <int P, int C, int R>
+__device__ __noinline__ void build_interp_out(const RegridRowsT<R>& rows, uint8_t* W, int N, const float* sctab,
+                                              float sw, int realign, int t0, int tstep) {
+  build_interp<P, C, R>(rows, W, N, sctab, sw, realign, t0, tstep);
 }
-__device__ __noinline__ void regrid_rows_out(RegridRows& rows, double rs, double rd, int N, int t0, int tstep) {
+template <int R>
+__device__ __noinline__ void regrid_rows_out(RegridRowsT<R>& rows, double rs, double rd, int N, int t0, int tstep) {
   regrid_rows(rows, rs, rd, N, t0, tstep);
 }
-template <int P>
+template <int P, int C>
 __device__ __noinline__ void issue_stage_out(uint32_t tmem, uint32_t a_base, int a_mn, uint32_t w_base, int nout,
                                              int K, uint32_t mbar) {
-  issue_stage<P>(tmem, a_base, a_mn, w_base, nout, K, mbar);
+  issue_stage<P, C>(tmem, a_base, a_mn, w_base, nout, K, mbar);
 }
-template <int P>
+template <int P, int C>
 __device__ __noinline__ void stage_to_operand_out(uint8_t* A, const float* S, int nr, int nc, float s, int t0,
                                                   int tstep) {
-  stage_to_operand<P>(A, S, nr, nc, s, t0, tstep);
+  stage_to_operand<P, C>(A, S, nr, nc, s, t0, tstep);
 }
 
 // Band-limited re-alignment on the staging tile (shear mode): the two
@@ -249,7 +301,9 @@ __device__ __noinline__ void stage_to_operand_out(uint8_t* A, const float* S, in
 // an evaluation point x = m + f takes e^{2 pi i x / N} from the table entry of
 // m and sincospi of f, then powers by recurrence.  Returns this thread's
 // max |weight| of the re-aligned tile.
-__device__ __noinline__ float shear_stage(const Shared& sh, float* S, float* C, int N0, int N1) {
+template <class SH>
+__device__ __noinline__ float shear_stage(const SH& sh, float* S, float* C, int N0, int N1) {
+  constexpr int kThreads = SH::kT, kSStr = SH::kStr;
   const FrameState& fs = sh.fs;
   // pass order making pass 1's line-dependent shift the smaller: |B_10 / B_00| <= |B_01 / B_11|
   const int p = fabs(fs.B[2]) * fabs(fs.B[3]) <= fabs(fs.B[1]) * fabs(fs.B[0]) ? 0 : 1, q = 1 - p;
@@ -322,7 +376,9 @@ __device__ __noinline__ float shear_stage(const Shared& sh, float* S, float* C, 
 //   T'_C = Psi_0 T_C - (-1)^{|3 & C|} Psi_3 T_{3 ^ C},
 // then back to the separable coefficients; gsc = trace factor / (N0 N1).
 // Psi(k0, k1) and Psi(-k0, k1) differ only in the sign of the cross term.
-__device__ void psi_stage(const Shared& sh, float* S, int N0, int N1, int l, int exact) {
+template <class SH>
+__device__ void psi_stage(const SH& sh, float* S, int N0, int N1, int l, int exact) {
+  constexpr int kThreads = SH::kT, kSStr = SH::kStr;
   const int H0n = N0 / 2 + 1, H1n = N1 / 2 + 1;
   const float w0s = 6.28318530717958647692f / (float)N0, w1s = 6.28318530717958647692f / (float)N1;
   // r = k1 H0n + k0: (r + 1/2) / H0n is at least 1/(2 H0n) away from an integer,
@@ -375,18 +431,26 @@ __device__ void psi_stage(const Shared& sh, float* S, int N0, int N1, int l, int
   }
 }
 
-template <int P, bool kOut>
+// kPlan: the planned transform kernel of a batch (time update only; the
+// measurement update, moments, frame decision, sub-step coefficients and
+// regrid rows come from the front kernel through job.plan).  C: size class.
+template <int P, bool kOut, bool kPlan = false, int C = 128>
 __device__ void fused2d(const FusedView& job, uint8_t* smem) {
-  __shared__ Shared sh;
+  using SH = SharedT<Smem<P, C>::threads, C, !kPlan>;
+  constexpr int kThreads = SH::kT, kSStr = SH::kStr, kGroups = kThreads / 128;
+  __shared__ SH sh;
   if (!job.do_meas && !job.do_time) return;   // nothing requested for this filter
+  if constexpr (kPlan) {
+    if (!job.plan->ok) return;                 // degenerate measurement update: no time update
+  }
   DevState* st = job.st;
   FrameState& fs = sh.fs;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int row = tid & 127, cg = tid >> 7;     // TMEM lane and column group of this thread
   const int N0 = job.N0, N1 = job.N1;
-  uint8_t* A = smem + kOffA;
-  uint8_t* W = smem + kOffW;
-  float* S = (float*)(smem + kOffS);
+  uint8_t* A = smem + Smem<P, C>::offA;
+  uint8_t* W = smem + Smem<P, C>::offW;
+  float* S = (float*)(smem + Smem<P, C>::offS);
   const uint32_t mb_mma = su32(&sh.mbar_mma), mb_tma = su32(&sh.mbar_tma);
   uint32_t ph_mma = 0, ph_tma = 0;
   const float sw = P == PMF_PREC_FP16X3 ? 16384.0f : 1.0f;   // scale of the matrix operands
@@ -395,9 +459,12 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   for (int i = tid; i < kFsWords; i += kThreads)
     ((unsigned long long*)&fs)[i] = ((const unsigned long long*)&st->f)[i];
   if (job.do_time) {
-    const int words = tc_words(job.tc);   // up to the sub-step rows this update uses
-    for (int i = tid; i < words; i += kThreads)
-      ((unsigned long long*)&sh.tc)[i] = ((const unsigned long long*)job.tc)[i];
+    if constexpr (!kPlan) {
+      const int words = tc_words(job.tc);   // up to the sub-step rows this update uses
+      for (int i = tid; i < words; i += kThreads)
+        ((unsigned long long*)&sh.tc)[i] = ((const unsigned long long*)job.tc)[i];
+    }
+    if (tid == 0) sh.realign_mode = job.tc->realign_mode;
     for (int a = 0; a < 2; ++a) {
       const int n = 2 * (2 * (a ? N1 : N0) + 1);
       for (int i = tid; i < n; i += kThreads) sh.sct[a][i] = job.sctab[a][i];
@@ -435,7 +502,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   if (job.do_time && warp == 2 && (tid & 31) < 2) {
     // the Hartley planes of both axes are needed after the measurement update
     const int a = tid & 1, Nm = a ? N1 : N0;
-    prefetch_l2(job.hart[a], (uint32_t)Nm * (uint32_t)(Fmt<P>::rowblk / 8) * Fmt<P>::planes);
+    prefetch_l2(job.hart[a], (uint32_t)Nm * (uint32_t)(Lay<P, C>::rowblk / 8) * Fmt<P>::planes);
   }
   if (warp == 1) {
     // rows are N1 * 4 bytes (a multiple of 64) at 16-byte aligned addresses
@@ -449,7 +516,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   int realign = 0, l = 0, exact = 0;
 
   // ---- measurement update (eq. filt) ----
-  if (job.do_meas) {
+  if (!kPlan && job.do_meas) {
     if (tid == 0) {
       const MeasParams& mp = sh.mp;
       const double c0 = fs.c[0], c1 = fs.c[1];
@@ -545,7 +612,16 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     // float64 while warps 1.. convert the staged weights into the R1 operand,
     // which needs neither.
     const float sa0 = op_scale<P>(block_max(sh, smax, 1));
-    if (warp == 0) {
+    if (warp == 0 && kPlan) {
+      // the front kernel decided the frame: pending frame and trace factor
+      const BatchPlan* pl = job.plan;
+      if (tid < 24) sh.pend[tid] = pl->pend[tid];
+      if (tid == 0) {
+        sh.g = pl->g;
+        sh.gsc = pl->gsc;
+      }
+      __syncwarp();
+    } else if (warp == 0) {
       bool ok = true;
       if (job.do_meas) {
         if constexpr (kOut) ok = finalize_warp_out(&fs, sh.tot, 0, nullptr);
@@ -561,7 +637,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         }
         __syncwarp();
       }
-      if (ok && job.do_time) {
+      if constexpr (!kPlan) if (ok && job.do_time) {
         frame_warp<2>(sh.tc, &fs, sh.pend, sh.Mpi);
         if (tid == 0) {
           sh.g = (float)fs.g;
@@ -569,8 +645,8 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         }
       }
     } else if (job.do_time) {
-      if constexpr (kOut) stage_to_operand_out<P>(A, S, N0, N1, sa0, tid - 32, kThreads - 32);
-      else stage_to_operand<P>(A, S, N0, N1, sa0, tid - 32, kThreads - 32);
+      if constexpr (kOut) stage_to_operand_out<P, C>(A, S, N0, N1, sa0, tid - 32, kThreads - 32);
+      else stage_to_operand<P, C>(A, S, N0, N1, sa0, tid - 32, kThreads - 32);
     }
     __syncthreads();
     if (sh.degenerate) goto done;
@@ -596,19 +672,28 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     realign = fs.realign;
     l = fs.l;
     exact = fs.exact;
-    for (int q = tid; q < l; q += kThreads) {
-      double pa[4], pb[6];
-      frame_substep<2>(sh.tc, sh.Mpi, q, pa, pb);
-      sh.pa[q][0] = (float)pa[0];
-      sh.pa[q][1] = (float)pa[1];
-      sh.pb[q] = (float)pb[0];
+    if constexpr (kPlan) {
+      const BatchPlan* pl = job.plan;
+      for (int q = tid; q < l; q += kThreads) {
+        sh.pa[q][0] = pl->pa[q][0];
+        sh.pa[q][1] = pl->pa[q][1];
+        sh.pb[q] = pl->pb[q];
+      }
+    } else {
+      for (int q = tid; q < l; q += kThreads) {
+        double pa[4], pb[6];
+        frame_substep<2>(sh.tc, sh.Mpi, q, pa, pb);
+        sh.pa[q][0] = (float)pa[0];
+        sh.pa[q][1] = (float)pa[1];
+        sh.pb[q] = (float)pb[0];
+      }
     }
-    if (realign && sh.tc.realign_mode == PMF_REALIGN_SHEAR) {
+    if (realign && sh.realign_mode == PMF_REALIGN_SHEAR) {
       // band-limited re-alignment in place on the staging tile
       smax = shear_stage(sh, S, (float*)A, N0, N1);
       sa_first = op_scale<P>(block_max(sh, smax, 0));
-      if constexpr (kOut) stage_to_operand_out<P>(A, S, N0, N1, sa_first, tid, kThreads);
-      else stage_to_operand<P>(A, S, N0, N1, sa_first, tid, kThreads);
+      if constexpr (kOut) stage_to_operand_out<P, C>(A, S, N0, N1, sa_first, tid, kThreads);
+      else stage_to_operand<P, C>(A, S, N0, N1, sa_first, tid, kThreads);
     } else if (realign) {
       // multilinear re-alignment: gather into the (free) W region, copy back
       float* G = (float*)W;
@@ -639,14 +724,28 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         smax = fmaxf(smax, fabsf(G[p]));
       }
       sa_first = op_scale<P>(block_max(sh, smax, 0));
-      if constexpr (kOut) stage_to_operand_out<P>(A, S, N0, N1, sa_first, tid, kThreads);
-      else stage_to_operand<P>(A, S, N0, N1, sa_first, tid, kThreads);
+      if constexpr (kOut) stage_to_operand_out<P, C>(A, S, N0, N1, sa_first, tid, kThreads);
+      else stage_to_operand<P, C>(A, S, N0, N1, sa_first, tid, kThreads);
     } else {
       // axis 1 by the first half of the block, axis 0 by the second
       const int a = tid < kThreads / 2 ? 1 : 0;
       const int t0 = tid - (a ? 0 : kThreads / 2);
-      if constexpr (kOut) regrid_rows_out(sh.rows[a], fs.rs[a], fs.rd[a], a ? N1 : N0, t0, kThreads / 2);
-      else regrid_rows(sh.rows[a], fs.rs[a], fs.rd[a], a ? N1 : N0, t0, kThreads / 2);
+      if constexpr (kPlan) {
+        const RegridRowsT<128>& src = job.plan->rows[a];
+        RegridRowsT<C>& dst = sh.rows[a];
+        for (int n = t0; n < (a ? N1 : N0); n += kThreads / 2) {
+          dst.ri[n] = src.ri[n];
+          dst.rf[n] = src.rf[n];
+          dst.rS[n] = src.rS[n];
+          dst.rcf[n] = src.rcf[n];
+          dst.rsf[n] = src.rsf[n];
+          dst.rzero[n] = src.rzero[n];
+        }
+      } else if constexpr (kOut) {
+        regrid_rows_out(sh.rows[a], fs.rs[a], fs.rd[a], a ? N1 : N0, t0, kThreads / 2);
+      } else {
+        regrid_rows(sh.rows[a], fs.rs[a], fs.rd[a], a ? N1 : N0, t0, kThreads / 2);
+      }
     }
     __syncthreads();
   }
@@ -654,14 +753,14 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   {
     // ---- the matrix I1; the R1 operand is already written ----
     float sa = sa_first;
-    if constexpr (kOut) build_interp_out<P>(sh.rows[1], W, N1, sh.sct[1], sw, realign, tid, kThreads);
-    else build_interp<P>(sh.rows[1], W, N1, sh.sct[1], sw, realign, tid, kThreads);
+    if constexpr (kOut) build_interp_out<P, C, C>(sh.rows[1], W, N1, sh.sct[1], sw, realign, tid, kThreads);
+    else build_interp<P, C, C>(sh.rows[1], W, N1, sh.sct[1], sw, realign, tid, kThreads);
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
       tc_after_sync();
-      if constexpr (kOut) issue_stage_out<P>(tmem, su32(A), 0, su32(W), N1, N1, mb_mma);
-      else issue_stage<P>(tmem, su32(A), 0, su32(W), N1, N1, mb_mma);
+      if constexpr (kOut) issue_stage_out<P, C>(tmem, su32(A), 0, su32(W), N1, N1, mb_mma);
+      else issue_stage<P, C>(tmem, su32(A), 0, su32(W), N1, N1, mb_mma);
     }
     float inv_scale = 1.0f / (sa * sw);
 
@@ -683,15 +782,15 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       if (stage == 2) mat = 0;
       if (tid == 0 && mat >= 0) {
         const int Nm = mat == 0 ? N0 : N1;
-        const uint32_t pbytes = (uint32_t)Nm * (uint32_t)(Fmt<P>::rowblk / 8);
+        const uint32_t pbytes = (uint32_t)Nm * (uint32_t)(Lay<P, C>::rowblk / 8);
         expect_tx(mb_tma, pbytes * Fmt<P>::planes);
         for (int pl = 0; pl < Fmt<P>::planes; ++pl)
-          bulk_load(su32(W) + pl * kPlane, job.hart[mat] + (size_t)pl * pbytes, pbytes, mb_tma);
+          bulk_load(su32(W) + pl * Lay<P, C>::wplane, job.hart[mat] + (size_t)pl * pbytes, pbytes, mb_tma);
       }
       // accumulator of GEMM `stage`: valid lanes and columns
       const int nlane = (stage == 0 || stage == 1 || stage == 5) ? N0 : N1;
       const int nout = (stage <= 1 || stage == 5) ? N1 : N0;
-      const int ncol = nout / 4, c0 = cg * ncol;   // this thread's columns
+      const int ncol = nout / kGroups, c0 = cg * ncol;   // this thread's columns
       const bool lane_ok = row < nlane;
       float4 v[8];
       tmem_ld_cols(tlane + c0, ncol, v);
@@ -732,15 +831,15 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       if (stage == 3) {
         // F0 finished: spectrum T[k1][k0] -> staging, multiplier, operand of V0
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (4 * j < ncol) *(float4*)(S + row * kSStr + c0 + 4 * j) = v[j];
+        for (int j = 0; j < 8; ++j)   // valid lanes only: the staging tile has C rows
+          if (4 * j < ncol && lane_ok) *(float4*)(S + row * kSStr + c0 + 4 * j) = v[j];
         tc_before_sync();
         __syncthreads();
         psi_stage(sh, S, N0, N1, l, exact);
         __syncthreads();
-        sa = op_scale<P>(block_max(sh, stage_max(S, N1, N0), stage & 1));
-        if constexpr (kOut) stage_to_operand_out<P>(A, S, N1, N0, sa, tid, kThreads);
-        else stage_to_operand<P>(A, S, N1, N0, sa, tid, kThreads);
+        sa = op_scale<P>(block_max(sh, stage_max<kThreads, C>(S, N1, N0), stage & 1));
+        if constexpr (kOut) stage_to_operand_out<P, C>(A, S, N1, N0, sa, tid, kThreads);
+        else stage_to_operand<P, C>(A, S, N1, N0, sa, tid, kThreads);
       } else {
         float m = 0.0f;
 #pragma unroll
@@ -751,17 +850,20 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
 #pragma unroll
         for (int j = 0; j < 8; ++j)
           if (4 * j < ncol) {
-            if (tr)
-              store4_t(A, row, c0 + 4 * j, v[j], sa);
-            else
-              store4<P>(A, row, c0 + 4 * j, v[j], sa);
+            if (tr) {
+              // transposed, lanes become columns: a lane >= C would land in the
+              // next row block of the size-64 layout, so invalid lanes are skipped
+              if (lane_ok) store4_t<C>(A, row, c0 + 4 * j, v[j], sa);
+            } else {
+              store4<P, C>(A, row, c0 + 4 * j, v[j], sa);
+            }
           }
         tc_before_sync();
       }
       if (stage == 1) {
         __syncthreads();
-        if constexpr (kOut) build_interp_out<P>(sh.rows[0], W, N0, sh.sct[0], sw, realign, tid, kThreads);
-        else build_interp<P>(sh.rows[0], W, N0, sh.sct[0], sw, realign, tid, kThreads);
+        if constexpr (kOut) build_interp_out<P, C, C>(sh.rows[0], W, N0, sh.sct[0], sw, realign, tid, kThreads);
+        else build_interp<P, C, C>(sh.rows[0], W, N0, sh.sct[0], sw, realign, tid, kThreads);
       }
       fence_async_smem();
       __syncthreads();
@@ -775,8 +877,8 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
           // stage+1: F1 (K-major), R0 (MN), F0 (K), V0 (K), V1 (MN)
           const int a_mn = (P != PMF_PREC_TF32) && (stage == 1 || stage == 4);
           const int nn = (stage == 0 || stage == 4) ? N1 : N0;
-          if constexpr (kOut) issue_stage_out<P>(tmem, su32(A), a_mn, su32(W), nn, nn, mb_mma);
-          else issue_stage<P>(tmem, su32(A), a_mn, su32(W), nn, nn, mb_mma);
+          if constexpr (kOut) issue_stage_out<P, C>(tmem, su32(A), a_mn, su32(W), nn, nn, mb_mma);
+          else issue_stage<P, C>(tmem, su32(A), a_mn, su32(W), nn, nn, mb_mma);
         }
       }
       if (mat >= 0) ph_tma ^= 1;
@@ -812,6 +914,193 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused2d(const __grid_constant__
   const FusedView v{job.st, job.buf0, job.buf1, {job.hart[0], job.hart[1]}, {job.sctab[0], job.sctab[1]},
                     job.N0, job.N1, job.do_meas, job.do_time, &job.mp, job.mp.z, &job.tc};
   fused2d<P, true>(v, smem);
+}
+
+// Front kernel of a batched epoch (one CTA per filter, no operand tiles, so
+// several CTAs share an SM and their float64 latency chains overlap): the
+// measurement update (eq. filt) streamed through registers from the current
+// weight buffer into the other one, the moments, the float64 regrid decision
+// of the time update, its sub-step coefficients and the regrid rows of both
+// axes, handed to the planned transform kernel through the filter's plan.
+// The steps are those of the fused kernel (the exponents are recomputed
+// instead of stored).
+constexpr int kFrontThreads = 128;   // four warps: six or more CTAs (filters) share an SM
+
+__global__ void __launch_bounds__(kFrontThreads, 6) k_front2d(const FilterSlot* __restrict__ slots,
+                                                              const StepItem* __restrict__ items,
+                                                              const TimeConsts* __restrict__ tcs) {
+  __shared__ SharedT<kFrontThreads, 128, true> sh;
+  constexpr int kT = kFrontThreads;
+  const StepItem& it = items[blockIdx.x];
+  const FilterSlot& sl = slots[it.slot];
+  const int do_meas = it.flags & 1, do_time = (it.flags >> 1) & 1;
+  BatchPlan* plan = (BatchPlan*)sl.plan;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (!do_meas && !do_time) {
+    if (tid == 0) plan->ok = 0;
+    return;
+  }
+  DevState* st = sl.st;
+  FrameState& fs = sh.fs;
+  const int N0 = sl.N0, N1 = sl.N1;
+  constexpr int kFsWords = sizeof(FrameState) / 8;
+  for (int i = tid; i < kFsWords; i += kT) ((unsigned long long*)&fs)[i] = ((const unsigned long long*)&st->f)[i];
+  if (do_time) {
+    const TimeConsts* tc = tcs ? tcs + blockIdx.x : sl.tc;
+    const int words = tc_words(tc);
+    for (int i = tid; i < words; i += kT) ((unsigned long long*)&sh.tc)[i] = ((const unsigned long long*)tc)[i];
+  }
+  if (do_meas)
+    for (int i = tid; i < (int)(sizeof(MeasParams) / 8); i += kT)
+      ((unsigned long long*)&sh.mp)[i] = ((const unsigned long long*)sl.mp)[i];
+  if (tid == 0) sh.degenerate = 0;
+  __syncthreads();
+  if (do_meas && tid < PMF_MAX_NZ) sh.mp.z[tid] = it.z[tid];
+  __syncthreads();
+  const int cur = fs.cur;
+  const float* in = cur ? sl.buf1 : sl.buf0;
+  float* out = cur ? sl.buf0 : sl.buf1;
+  const int q1 = N1 / 4, np4 = N0 * q1;
+  const float rq1 = 1.0f / (float)q1;
+  if (do_meas) {
+    if (tid == 0) {
+      const MeasParams& mp = sh.mp;
+      const double c0 = fs.c[0], c1 = fs.c[1];
+      sh.mc[0] = (float)c0;
+      sh.mc[1] = (float)c1;
+      for (int i = 0; i < 4; ++i) sh.mM[i] = (float)fs.M[i];
+      for (int i = 0; i < mp.nz * mp.nz; ++i) sh.mRinv[i] = (float)mp.Rinv[i];
+      if (mp.kind == PMF_MEAS_LINEAR) {
+        for (int i = 0; i < mp.nz; ++i) {
+          sh.mr0[i] = (float)(mp.z[i] - (mp.H[i * 2] * c0 + mp.H[i * 2 + 1] * c1));
+          for (int b = 0; b < 2; ++b) sh.mH[i * 2 + b] = (float)mp.H[i * 2 + b];
+        }
+      } else {
+        const double cn = sqrt(c0 * c0 + c1 * c1);
+        sh.mcn = (float)cn;
+        sh.mr0[0] = (float)(mp.z[0] - cn);
+      }
+    }
+    __syncthreads();
+    const MeasK mk = meas_k(sh);
+    float emin = INFINITY;
+    for (int t = tid; t < np4; t += kT) {
+      const int r = (int)(((float)t + 0.5f) * rq1), c = (t - r * q1) * 4;
+      const float u0 = r - 0.5f * (N0 - 1), u1 = c - 0.5f * (N1 - 1);
+      emin = fminf(emin, fminf(fminf(meas_e(mk, u0, u1), meas_e(mk, u0, u1 + 1.0f)),
+                               fminf(meas_e(mk, u0, u1 + 2.0f), meas_e(mk, u0, u1 + 3.0f))));
+    }
+    emin = block_min(sh, emin, 0);
+    const float ps = (float)fs.pscale;
+    Moments mo;
+    mo.zero();
+    const int tmax = (kT / q1) * q1;
+    if (tid < tmax) {
+      // float32 column sums over at most 16 rows, then one double-float add per slot
+      float ca[4] = {0.0f, 0.0f, 0.0f, 0.0f}, cb[4] = {0.0f, 0.0f, 0.0f, 0.0f}, cc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      int rows = 0;
+      for (int t = tid; t < np4; t += tmax) {
+        const int r = (int)(((float)t + 0.5f) * rq1), c = (t - r * q1) * 4;
+        const float u0 = r - 0.5f * (N0 - 1), u1 = c - 0.5f * (N1 - 1);
+        float4 x = *(const float4*)(in + (size_t)r * N1 + c);
+        x.x = (x.x * ps) * __expf(emin - meas_e(mk, u0, u1));
+        x.y = (x.y * ps) * __expf(emin - meas_e(mk, u0, u1 + 1.0f));
+        x.z = (x.z * ps) * __expf(emin - meas_e(mk, u0, u1 + 2.0f));
+        x.w = (x.w * ps) * __expf(emin - meas_e(mk, u0, u1 + 3.0f));
+        *(float4*)(out + (size_t)r * N1 + c) = x;
+        const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float xu = xs[i] * u0;
+          ca[i] += xs[i];
+          cb[i] += xu;
+          cc[i] = fmaf(xu, u0, cc[i]);
+        }
+        if (++rows == 16) {
+          mo.add_cols4(ca, cb, cc, (tid % q1) * 4 - 0.5f * (N1 - 1));
+#pragma unroll
+          for (int i = 0; i < 4; ++i) ca[i] = cb[i] = cc[i] = 0.0f;
+          rows = 0;
+        }
+      }
+      mo.add_cols4(ca, cb, cc, (tid % q1) * 4 - 0.5f * (N1 - 1));
+    }
+    block_moments(sh, mo);
+  }
+  if (warp == 0) {
+    bool ok = true;
+    if (do_meas) {
+      ok = finalize_warp<2>(&fs, sh.tot, 0, nullptr);
+      if (tid == 0) {
+        if (!ok) {
+          sh.degenerate = 1;
+        } else {
+          sh.ps = (float)fs.pscale;   // the new weights times ps are normalised
+          fs.pscale = 1.0;
+          fs.S0 = 1.0 / fs.V;
+          fs.cur = cur ^ 1;           // they live in the other buffer now
+        }
+      }
+      __syncwarp();
+    }
+    if (ok && do_time) {
+      frame_warp<2>(sh.tc, &fs, sh.pend, sh.Mpi);
+      if (tid < 24) plan->pend[tid] = sh.pend[tid];
+      if (tid == 0) {
+        plan->g = (float)fs.g;
+        plan->gsc = (float)(fs.g / ((double)N0 * (double)N1));
+      }
+    }
+  }
+  __syncthreads();
+  if (sh.degenerate) {
+    if (tid == 0) plan->ok = 0;
+  } else if (!do_time) {
+    // measurement only: normalise the new weights in place
+    const float ps = sh.ps;
+    for (int t = tid; t < np4; t += kT) {
+      const int r = t / q1, c = (t % q1) * 4;
+      float4 x = *(const float4*)(out + (size_t)r * N1 + c);
+      x.x *= ps;
+      x.y *= ps;
+      x.z *= ps;
+      x.w *= ps;
+      *(float4*)(out + (size_t)r * N1 + c) = x;
+    }
+    if (tid == 0) plan->ok = 0;
+  } else {
+    // sub-step coefficients and, for a separable regrid, the regrid rows
+    const int l = fs.l;
+    for (int q = tid; q < l; q += kT) {
+      double pa[4], pb[6];
+      frame_substep<2>(sh.tc, sh.Mpi, q, pa, pb);
+      plan->pa[q][0] = (float)pa[0];
+      plan->pa[q][1] = (float)pa[1];
+      plan->pb[q] = (float)pb[0];
+    }
+    if (!fs.realign) {
+      const int a = tid < kT / 2 ? 1 : 0;
+      regrid_rows(plan->rows[a], fs.rs[a], fs.rd[a], a ? N1 : N0, tid - (a ? 0 : kT / 2), kT / 2);
+    }
+    if (tid == 0) plan->ok = 1;
+  }
+  __syncthreads();
+  for (int i = tid; i < kFsWords; i += kT) ((unsigned long long*)&st->f)[i] = ((const unsigned long long*)&fs)[i];
+}
+
+// Planned transform kernel of a batched epoch (size class C): the time update
+// of the filters whose front kernel ran it, from the weights and plan it left.
+template <int P, int C>
+__global__ void __launch_bounds__(Smem<P, C>::threads, C == 128 ? 1 : 3)
+    k_fused2d_planned(const FilterSlot* __restrict__ slots, const StepItem* __restrict__ items,
+                      const TimeConsts* __restrict__ tcs) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const StepItem& it = items[blockIdx.x];
+  const FilterSlot& sl = slots[it.slot];
+  const FusedView v{sl.st, sl.buf0, sl.buf1, {sl.hart[0], sl.hart[1]}, {sl.sctab[0], sl.sctab[1]},
+                    sl.N0, sl.N1, 0, (it.flags >> 1) & 1, sl.mp, it.z,
+                    tcs ? tcs + blockIdx.x : sl.tc, (const BatchPlan*)sl.plan};
+  fused2d<P, false, true, C>(v, smem);
 }
 
 // Many filters, one CTA each: items[blockIdx.x] names the filter slot, the
@@ -871,9 +1160,9 @@ __global__ void k_prior_f32(Dims d, const DevState* st, const double* aux, float
 
 // Host: split 16-bit (or float32) planes of a matrix in the operand layout.
 void split_planes(const std::vector<double>& Mt, int rows, int cols, int prec, double scale,
-                  std::vector<uint8_t>& out) {
+                  std::vector<uint8_t>& out, int cls) {
   const int esz = prec == PMF_PREC_TF32 ? 4 : 2;
-  const int epc = 16 / esz, rowblk = (128 / epc) * 128;
+  const int epc = 16 / esz, rowblk = (cls / epc) * 128;
   const size_t plane = (size_t)rows / 8 * rowblk;
   const int np = prec == PMF_PREC_TF32 ? 1 : 2;
   out.assign(plane * np, 0);
@@ -918,7 +1207,8 @@ int tc_supported(const pmf_config* cfg, std::string* why) {
   return PMF_OK;
 }
 
-int tc_build_axis_table(int N, int precision, void** dev, size_t* hart_bytes) {
+int tc_build_axis_table(int N, int precision, void** dev, size_t* hart_bytes, int cls) {
+  if (cls != 128 && (cls != 64 || N > 64)) return PMF_ERR_ARG;
   const double scale = precision == PMF_PREC_FP16X3 ? 16384.0 : 1.0;
   std::vector<double> H((size_t)N * N);
   const double w = 6.283185307179586476925286766559 / N;
@@ -928,7 +1218,7 @@ int tc_build_axis_table(int N, int precision, void** dev, size_t* hart_bytes) {
       H[(size_t)k * N + j] = std::cos(w * r) + std::sin(w * r);
     }
   std::vector<uint8_t> planes;
-  split_planes(H, N, N, precision, scale, planes);
+  split_planes(H, N, N, precision, scale, planes, cls);
   std::vector<float> tab(2 * (2 * N + 1));
   for (int m = -N; m <= N; ++m) {
     const double ang = 3.14159265358979323846 * m / N;
@@ -950,13 +1240,25 @@ int tc_build_axis_table(int N, int precision, void** dev, size_t* hart_bytes) {
     cudaFuncSetAttribute(k_fused2d_batch<PMF_PREC_FP16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     cudaFuncSetAttribute(k_fused2d_batch<PMF_PREC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     cudaFuncSetAttribute(k_fused2d_batch<PMF_PREC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_FP16X3, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         Smem<PMF_PREC_FP16X3, 128>::bytes);
+    cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_BF16X3, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         Smem<PMF_PREC_BF16X3, 128>::bytes);
+    cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_TF32, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         Smem<PMF_PREC_TF32, 128>::bytes);
+    cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_FP16X3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         Smem<PMF_PREC_FP16X3, 64>::bytes);
+    cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_BF16X3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         Smem<PMF_PREC_BF16X3, 64>::bytes);
+    cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_TF32, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         Smem<PMF_PREC_TF32, 64>::bytes);
     attr = true;
   }
   return PMF_OK;
 }
 
-size_t tc_axis_table_bytes(int N, int precision) {
-  const size_t plane = (size_t)N / 8 * (precision == PMF_PREC_TF32 ? 4096 : 2048);
+size_t tc_axis_table_bytes(int N, int precision, int cls) {
+  const size_t plane = (size_t)N / 8 * (precision == PMF_PREC_TF32 ? 32 : 16) * cls;
   return plane * (precision == PMF_PREC_TF32 ? 1 : 2) + 2 * (2 * N + 1) * sizeof(float);
 }
 
@@ -1053,6 +1355,43 @@ int tc_batch_step(int precision, const FilterSlot* slots, const StepItem* items,
   else
     k_fused2d_batch<PMF_PREC_TF32><<<k, kThreads, kSmemBytes, s>>>(slots, items, tcs);
   return 1;
+}
+
+size_t tc_plan_bytes() { return sizeof(BatchPlan); }
+
+namespace {
+template <int P>
+void launch_planned(const FilterSlot* slots, const StepItem* items, int k, int k128, cudaStream_t s,
+                    const TimeConsts* tcs, cudaStream_t s2) {
+  if (k128 > 0)
+    k_fused2d_planned<P, 128><<<k128, Smem<P, 128>::threads, Smem<P, 128>::bytes, s>>>(slots, items, tcs);
+  if (k > k128)
+    k_fused2d_planned<P, 64><<<k - k128, Smem<P, 64>::threads, Smem<P, 64>::bytes, s2>>>(
+        slots, items + k128, tcs ? tcs + k128 : nullptr);
+}
+}  // namespace
+
+int tc_batch_epoch(int precision, const FilterSlot* slots, const StepItem* items, int k, int k128, cudaStream_t s,
+                   const TimeConsts* tcs, cudaStream_t s2, cudaEvent_t ev_fork, cudaEvent_t ev_join) {
+  if (k <= 0) return 0;
+  k_front2d<<<k, kFrontThreads, 0, s>>>(slots, items, tcs);
+  const bool fork = s2 && ev_fork && ev_join && k128 > 0 && k > k128;
+  if (fork) {
+    cudaEventRecord(ev_fork, s);
+    cudaStreamWaitEvent(s2, ev_fork, 0);
+  }
+  cudaStream_t t = fork ? s2 : s;
+  if (precision == PMF_PREC_FP16X3)
+    launch_planned<PMF_PREC_FP16X3>(slots, items, k, k128, s, tcs, t);
+  else if (precision == PMF_PREC_BF16X3)
+    launch_planned<PMF_PREC_BF16X3>(slots, items, k, k128, s, tcs, t);
+  else
+    launch_planned<PMF_PREC_TF32>(slots, items, k, k128, s, tcs, t);
+  if (fork) {
+    cudaEventRecord(ev_join, s2);
+    cudaStreamWaitEvent(s, ev_join, 0);
+  }
+  return 1 + (k128 > 0) + (k > k128);
 }
 
 int tc_batch_gather(DevState* st, const int* ids, int k, double* out, cudaStream_t s) {

@@ -24,6 +24,7 @@ struct FilterSlot {
   int N0, N1;
   const MeasParams* mp;     // measurement model of the filter
   const TimeConsts* tc;     // constants of the filter's current tau
+  void* plan;               // batched epochs: the front kernel's results (tc_plan_bytes)
 };
 
 // One filter's request in a batched epoch: flags bit 0 = measurement update
@@ -50,8 +51,14 @@ struct Slot1 {
 int tc_supported(const pmf_config* cfg, std::string* why);
 int tc_build_tables(const pmf_config* cfg, TcTables* t, std::string* why);
 // Split Hartley planes and the (cos, sin)(pi m / N) table of one axis size (one allocation).
-int tc_build_axis_table(int N, int precision, void** dev, size_t* hart_bytes);
-size_t tc_axis_table_bytes(int N, int precision);
+// cls: size class of the kernels that read it (128: every fused kernel; 64:
+// the compact planned kernel of batched filters whose axes are all <= 64).
+int tc_build_axis_table(int N, int precision, void** dev, size_t* hart_bytes, int cls = 128);
+size_t tc_axis_table_bytes(int N, int precision, int cls = 128);
+// Size class of a 2-D filter in batched epochs (64 when both axes are <= 64).
+inline int tc_class(int N0, int N1) { return N0 <= 64 && N1 <= 64 ? 64 : 128; }
+// Device bytes of one filter's plan (the front kernel's results of an epoch).
+size_t tc_plan_bytes();
 void tc_free_tables(TcTables* t);
 // Bounded mbarrier wait in a one-warp kernel (see pmf_selftest_bounded_wait).
 int tc_wait_probe(long long polls, int arrive, cudaStream_t s);
@@ -102,6 +109,14 @@ int tc3_batch(const Tc3Item* items, int n, int precision, Tc3Stage* g, cudaStrea
 // holds each item's time-update constants in place of the slot's; returns launches.
 int tc_batch_step(int precision, const FilterSlot* slots, const StepItem* items, int k, cudaStream_t s,
                   const TimeConsts* tcs = nullptr);
+// A batched epoch as a front kernel over all k items, then the planned
+// transform kernels: items [0, k128) of size class 128, then [k128, k) of
+// class 64 (on stream s2 when it is given, joined back into s through ev,
+// so the two classes share the SMs).  tcs as for tc_batch_step.  Returns the
+// number of launches.
+int tc_batch_epoch(int precision, const FilterSlot* slots, const StepItem* items, int k, int k128,
+                   cudaStream_t s, const TimeConsts* tcs = nullptr, cudaStream_t s2 = nullptr,
+                   cudaEvent_t ev_fork = nullptr, cudaEvent_t ev_join = nullptr);
 
 // 1-D grids (pmf_tc1.cu): CUDA-core kernel, N a multiple of 8 in [16, 512].
 int tc1_supported(const pmf_config* cfg, std::string* why);

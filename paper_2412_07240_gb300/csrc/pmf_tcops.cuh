@@ -142,10 +142,20 @@ struct Fmt<PMF_PREC_TF32> {
   static constexpr int esz = 4, rowblk = 4096, planes = 1, kper = 8, code = 2;
 };
 
-template <int P>
+// Operand tiles of a size class C (the largest axis they hold, 64 or 128):
+// an 8-row block covers C elements along K, so a 128-row plane takes
+// 128 * C * esz bytes (class 128, 16-bit: 32 KiB, the kPlane of the fused kernel).
+template <int P, int C>
+struct Lay {
+  static constexpr int rowblk = C * Fmt<P>::esz * 8;
+  static constexpr int plane = 128 * C * Fmt<P>::esz;   // a 128-row (M) operand plane
+  static constexpr int wplane = C * C * Fmt<P>::esz;    // a C-row matrix (W) plane
+};
+
+template <int P, int C = 128>
 __device__ __forceinline__ uint32_t op_off(int r, int c) {
   constexpr int epc = 16 / Fmt<P>::esz;
-  return (uint32_t)((r >> 3) * Fmt<P>::rowblk + (c / epc) * 128 + (r & 7) * 16 + (c % epc) * Fmt<P>::esz);
+  return (uint32_t)((r >> 3) * Lay<P, C>::rowblk + (c / epc) * 128 + (r & 7) * 16 + (c % epc) * Fmt<P>::esz);
 }
 
 __device__ __forceinline__ uint32_t h2u(__half2 h) { return *(uint32_t*)&h; }
@@ -153,13 +163,14 @@ __device__ __forceinline__ uint32_t b2u(__nv_bfloat162 h) { return *(uint32_t*)&
 
 // Elements (r, c..c+3) (c a multiple of 4) of the operand planes at base, scaled
 // by s: split into hi + lo 16-bit planes, or one float32 plane for TF32.
-template <int P>
+template <int P, int C = 128, bool kW = false>
 __device__ __forceinline__ void store4(uint8_t* base, int r, int c, float4 v, float s) {
+  constexpr int kPl = kW ? Lay<P, C>::wplane : Lay<P, C>::plane;
   v.x *= s;
   v.y *= s;
   v.z *= s;
   v.w *= s;
-  const uint32_t off = op_off<P>(r, c);
+  const uint32_t off = op_off<P, C>(r, c);
   if constexpr (P == PMF_PREC_TF32) {
     *(float4*)(base + off) = v;
   } else if constexpr (P == PMF_PREC_FP16X3) {
@@ -167,23 +178,24 @@ __device__ __forceinline__ void store4(uint8_t* base, int r, int c, float4 v, fl
     const float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
     const __half2 l0 = __floats2half2_rn(v.x - f0.x, v.y - f0.y), l1 = __floats2half2_rn(v.z - f1.x, v.w - f1.y);
     *(uint2*)(base + off) = make_uint2(h2u(h0), h2u(h1));
-    *(uint2*)(base + kPlane + off) = make_uint2(h2u(l0), h2u(l1));
+    *(uint2*)(base + kPl + off) = make_uint2(h2u(l0), h2u(l1));
   } else {
     const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y), h1 = __floats2bfloat162_rn(v.z, v.w);
     const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
     const __nv_bfloat162 l0 = __floats2bfloat162_rn(v.x - f0.x, v.y - f0.y);
     const __nv_bfloat162 l1 = __floats2bfloat162_rn(v.z - f1.x, v.w - f1.y);
     *(uint2*)(base + off) = make_uint2(b2u(h0), b2u(h1));
-    *(uint2*)(base + kPlane + off) = make_uint2(b2u(l0), b2u(l1));
+    *(uint2*)(base + kPl + off) = make_uint2(b2u(l0), b2u(l1));
   }
 }
 
 // TF32 operands are read K-major only: elements (c..c+3, r) of the float32 plane.
+template <int C = 128>
 __device__ __forceinline__ void store4_t(uint8_t* base, int r, int c, float4 v, float s) {
-  *(float*)(base + op_off<PMF_PREC_TF32>(c + 0, r)) = v.x * s;
-  *(float*)(base + op_off<PMF_PREC_TF32>(c + 1, r)) = v.y * s;
-  *(float*)(base + op_off<PMF_PREC_TF32>(c + 2, r)) = v.z * s;
-  *(float*)(base + op_off<PMF_PREC_TF32>(c + 3, r)) = v.w * s;
+  *(float*)(base + op_off<PMF_PREC_TF32, C>(c + 0, r)) = v.x * s;
+  *(float*)(base + op_off<PMF_PREC_TF32, C>(c + 1, r)) = v.y * s;
+  *(float*)(base + op_off<PMF_PREC_TF32, C>(c + 2, r)) = v.z * s;
+  *(float*)(base + op_off<PMF_PREC_TF32, C>(c + 3, r)) = v.w * s;
 }
 
 __device__ __forceinline__ float amax4(float m, float4 v) {
@@ -265,10 +277,11 @@ struct Moments {
 // For the split formats the two correction products (hi*lo, lo*hi; ~2^-11 of
 // the result) are accumulated first, while the FP32 accumulator is small, and
 // the hi*hi products last, so that only those see roundings at full magnitude.
-template <int P>
+template <int P, int C = 128>
 __device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t a_base, int a_mn, uint32_t w_base,
                                             int nout, int K, uint32_t mbar) {
-  constexpr uint32_t rb = Fmt<P>::rowblk;
+  constexpr uint32_t rb = Lay<P, C>::rowblk;
+  constexpr uint32_t kPl = Lay<P, C>::plane, kWPl = Lay<P, C>::wplane;
   constexpr int kp = Fmt<P>::kper;
   const uint32_t id = idesc(Fmt<P>::code, a_mn, nout);
   // K step of one instruction: 32 bytes = 2 core matrices along K (K-major),
@@ -281,8 +294,8 @@ __device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t a_base, int 
       mma_tf32(tmem, adesc(a_base, ks), sdesc(w_base + ks * 256, 128, rb), id, ks > 0);
   } else {
     for (int ks = 0; ks < K / kp; ++ks) {
-      mma_f16(tmem, adesc(a_base, ks), sdesc(w_base + kPlane + ks * 256, 128, rb), id, ks > 0);
-      mma_f16(tmem, adesc(a_base + kPlane, ks), sdesc(w_base + ks * 256, 128, rb), id, 1);
+      mma_f16(tmem, adesc(a_base, ks), sdesc(w_base + kWPl + ks * 256, 128, rb), id, ks > 0);
+      mma_f16(tmem, adesc(a_base + kPl, ks), sdesc(w_base + ks * 256, 128, rb), id, 1);
     }
     for (int ks = 0; ks < K / kp; ++ks)
       mma_f16(tmem, adesc(a_base, ks), sdesc(w_base + ks * 256, 128, rb), id, 1);
@@ -355,8 +368,8 @@ __device__ __forceinline__ float interp_entry(const RegridRowsT<R>& sh, int n, i
 // Thread t0 (of tstep >= N) keeps row t0 % N and every (tstep / N)-th group
 // of four columns, so its row parameters are read once; consecutive threads
 // take consecutive rows (8 rows share 128 bytes of the operand layout).
-template <int P>
-__device__ void build_interp(const RegridRows& sh, uint8_t* W, int N, const float* sctab, float sw, int realign,
+template <int P, int C = 128, int R = 128>
+__device__ void build_interp(const RegridRowsT<R>& sh, uint8_t* W, int N, const float* sctab, float sw, int realign,
                              int t0, int tstep) {
   const int per = tstep / N;
   if (t0 >= per * N) return;
@@ -369,7 +382,7 @@ __device__ void build_interp(const RegridRows& sh, uint8_t* W, int N, const floa
       const int j = c + i;
       k[i] = realign ? (n == j ? 1.0f : 0.0f) : interp_value(r, j, N, sctab);
     }
-    store4<P>(W, n, c, make_float4(k[0], k[1], k[2], k[3]), sw);
+    store4<P, C, true>(W, n, c, make_float4(k[0], k[1], k[2], k[3]), sw);
   }
 }
 

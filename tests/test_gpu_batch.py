@@ -22,11 +22,23 @@ def _c4(count, epochs, seed=4):
     return cfgs, meas, dt, z
 
 
+# a last-bit difference of the inputs re-rounds the 16-bit (or TF32) operand
+# splits: the two agree to the precision's own resolution
+AGREE = {"fp16x3": 1e-6, "bf16x3": 1e-4, "tf32": 3e-2}
+
+
 @pytest.mark.parametrize("prec,psi", [("fp16x3", "euler"), ("bf16x3", "euler"), ("tf32", "euler"),
                                       ("fp16x3", "exact")])
 def test_batch_equals_single_filters(prec, psi):
-    """Bit-identical to the same filters run alone, in every precision and both
-    multipliers (the single-filter path meets the oracle at those bars)."""
+    """The same filters run alone, in every precision and both multipliers (the
+    single-filter path meets the oracle at those bars).  The batch splits the
+    epoch into a front kernel (measurement update, moments, frame decision)
+    and a transform kernel of the filter's size class, with the steps of the
+    fused kernel; the front kernel recomputes the likelihood exponents instead
+    of storing them (the compiler may contract their float32 products
+    differently) and the size-64 class sums the final moments over fewer
+    threads, so the two agree to the rounding of the format, on the same
+    frames."""
     from paper_2412_07240_gb300 import Batch, Filter
     cfgs, meas, dt, z = _c4(10, 4)
     b = Batch(cfgs, [meas] * len(cfgs), precision=prec, psi_mode=psi)
@@ -36,10 +48,14 @@ def test_batch_equals_single_filters(prec, psi):
         b.step(ids, z[:, k], dt)
         for i, f in enumerate(singles):
             f.step(meas, z[i, k], dt)
+    classes = set()
     for i, f in enumerate(singles):
         Pb, cb, Mb = b.pdf(i)
         Ps, cs, Ms = f.pdf()
-        assert np.array_equal(Pb, Ps) and np.array_equal(cb, cs) and np.array_equal(Mb, Ms)
+        assert np.array_equal(cb, cs) and np.array_equal(Mb, Ms), i
+        assert rel_l1(Pb, Ps) <= AGREE[prec], (i, rel_l1(Pb, Ps))
+        classes.add(max(cfgs[i].N) > 64)
+    assert classes == {True, False}
 
 
 def test_batch_matches_oracle():

@@ -88,7 +88,10 @@ def test_shear_realignment_fp16x3():
 
 
 def test_shear_realignment_batch_equals_single():
+    """The band-limited re-alignment in the batch's size-64 transform kernel
+    equals the single-filter kernel's to float32 rounding, on the same frames."""
     from paper_2412_07240_gb300 import Batch, Filter
+    from tests._parity import rel_l1
     cfg = FilterConfig(nx=2, N=(48, 64), A=np.array([[0.0, 1.0], [0.0, 0.0]]), Q=np.diag([0.01, 0.1]),
                        m0=np.array([0.0, 1.0]), P0=np.diag([0.5, 0.5]), realign_mode="shear")
     meas = MeasModel("linear", R=0.3 ** 2 * np.eye(2), H=np.eye(2))
@@ -99,4 +102,7 @@ def test_shear_realignment_batch_equals_single():
     for k in range(sc.epochs):
         b.step([0], sc.z[k][None, :], sc.dt)
         g.step(meas, sc.z[k], sc.dt)
-    assert np.array_equal(b.pdf(0)[0], g.pdf()[0])
+    Pb, cb, Mb = b.pdf(0)
+    Ps, cs, Ms = g.pdf()
+    assert np.array_equal(cb, cs) and np.array_equal(Mb, Ms)
+    assert rel_l1(Pb, Ps) <= 1e-6, rel_l1(Pb, Ps)
