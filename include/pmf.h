@@ -95,12 +95,17 @@ enum { PMF_REALIGN_MULTILINEAR = 0, PMF_REALIGN_SHEAR = 1 };
 
 /* Form of the per-axis Hartley transforms (step 1 and step 5 of the Sec. V-B
  * algorithm).
- *   AUTO : per grid size the faster form, measured on first use (n_x = 1;
- *          the environment variable PMF_1D_FORM=matvec|fft overrides it);
- *          the contraction everywhere else.
+ *   AUTO : per grid size the faster form, measured on first use: n_x = 1
+ *          (matrix-vector or FFT; PMF_1D_FORM=matvec|fft overrides it) and
+ *          n_x = 2 on the tensor-core paths (GEMM or FFT, per (N0, N1,
+ *          precision); PMF_2D_FORM=gemm|fft overrides it); the choices are
+ *          cached in autotune.json / autotune_2d.json beside the library.
+ *          The contraction everywhere else.
  *   GEMM : the dense contraction with the N x N transform matrix (every path).
- *   FFT  : the shared-memory radix-2 FFT (n_x = 1, non-FP64 precision, N a
- *          power of two); PMF_ERR_UNSUPPORTED elsewhere. */
+ *   FFT  : shared-memory FFTs of the real lines (H_k = Re Z_k - Im Z_k):
+ *          n_x = 1 with N a power of two (radix 2), n_x = 2 with both axes
+ *          2^a 3^b (radix 3 and 2; the regrid stays a tensor-core GEMM);
+ *          non-FP64 precision; PMF_ERR_UNSUPPORTED elsewhere. */
 enum { PMF_TRANSFORM_AUTO = 0, PMF_TRANSFORM_GEMM = 1, PMF_TRANSFORM_FFT = 2 };
 
 /* Measurement functions h of eq. meas. */

@@ -300,7 +300,8 @@ def _iptr(a):
 class Batch:
     """Many independent 2-D filters resident on the GPU (a pmf_batch)."""
 
-    def __init__(self, cfgs, models, precision="fp16x3", psi_mode="euler", hbm_budget=0, stream=None):
+    def __init__(self, cfgs, models, precision="fp16x3", psi_mode="euler", hbm_budget=0, stream=None,
+                 transform="auto"):
         self._lib = load()
         n = len(cfgs)
         self.count = n
@@ -308,7 +309,7 @@ class Batch:
         carr = (PmfConfig * n)()
         marr = (PmfMeas * n)()
         for i, (c, m) in enumerate(zip(cfgs, models)):
-            carr[i] = make_config(c, precision, psi_mode)
+            carr[i] = make_config(c, precision, psi_mode, transform)
             marr[i] = make_meas(m, np.zeros(np.asarray(m.R).shape[0]), 2)
         self._stream = _stream_handle(stream)
         h = C.c_void_p()

@@ -158,9 +158,10 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
   for (int a = 0; a < n; ++a) ctx->dims.P *= cfg->N[a];
   const long long P = ctx->dims.P;
 
-  if (cfg->transform == PMF_TRANSFORM_FFT && (cfg->nx != 1 || cfg->precision == PMF_PREC_FP64)) {
+  if (cfg->transform == PMF_TRANSFORM_FFT &&
+      (cfg->precision == PMF_PREC_FP64 || (cfg->nx != 1 && !(cfg->nx == 2 && tc2_fft_ok(cfg->N[0], cfg->N[1]))))) {
     free_ctx(ctx);
-    return PMF_ERR_UNSUPPORTED;   // the FFT form exists in the 1-D kernel only
+    return PMF_ERR_UNSUPPORTED;   // the FFT form: 1-D kernel, fused 2-D kernel with axes 2^a 3^b
   }
   if (cfg->precision != PMF_PREC_FP64) {
     rc = cfg->nx == 1   ? tc1_supported(cfg, &why)
@@ -228,6 +229,7 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
     ctx->mode1 = tc1_form(cfg, ctx->tab1, ctx->stream);
   } else {
     rc = tc_build_tables(cfg, &ctx->tct, &why);
+    if (rc == PMF_OK && ctx->path == 1) ctx->tct.fft = tc2_form(cfg, ctx->stream);
     if (rc == PMF_OK && ctx->path == 2) rc = tc3_alloc(&ctx->tc3);
     if (rc) {
       free_ctx(ctx);
@@ -480,7 +482,8 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
   for (int i = 0; i < count; ++i) {
     int rc = validate_config(&cfgs[i], &why);
     if (rc) return rc;
-    if (cfgs[i].nx != 2 || cfgs[i].precision != prec || cfgs[i].transform == PMF_TRANSFORM_FFT)
+    if (cfgs[i].nx != 2 || cfgs[i].precision != prec ||
+        (cfgs[i].transform == PMF_TRANSFORM_FFT && !tc2_fft_ok(cfgs[i].N[0], cfgs[i].N[1])))
       return PMF_ERR_UNSUPPORTED;
     rc = tc_supported(&cfgs[i], &why);
     if (rc) return rc;
@@ -580,6 +583,7 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
     sl.mp = b->d_mp + i;
     sl.tc = b->d_tc + i;
     sl.plan = b->d_plan + tc_plan_bytes() * i;
+    sl.fft = tc2_form(&c, b->stream);
   }
   cudaMemcpy(b->d_st, hst.data(), sizeof(DevState) * count, cudaMemcpyHostToDevice);
   cudaMemcpy(b->d_mp, mps.data(), sizeof(MeasParams) * count, cudaMemcpyHostToDevice);

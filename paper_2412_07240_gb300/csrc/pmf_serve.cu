@@ -524,6 +524,9 @@ int pmf_server_admit(pmf_server* s, const pmf_config* cfg, const pmf_meas* model
     sl.mp = f.d_mp;
     sl.tc = nullptr;
     sl.plan = f.plan;
+    pmf_config fc = *cfg;
+    fc.precision = s->precision;
+    sl.fft = tc2_form(&fc, st);
     ok = cudaMemcpyAsync(s->d_slots2 + id, &sl, sizeof(sl), cudaMemcpyHostToDevice, st) == cudaSuccess;
   }
   ok = ok && cudaStreamSynchronize(st) == cudaSuccess && cudaGetLastError() == cudaSuccess;

@@ -28,11 +28,20 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <dlfcn.h>
+
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
 #include <vector>
 
 #include "pmf_device.cuh"
+#include "pmf_model.cuh"
 #include "pmf_kernels.cuh"
 #include "pmf_tc.cuh"
 #include "pmf_tcops.cuh"
@@ -70,7 +79,7 @@ struct FusedJob {
   float* buf1;
   const uint8_t* hart[2];   // per axis: Hartley planes (hi then lo for 16-bit formats)
   const float* sctab[2];    // per axis: (cos, sin)(pi m / N), m = -N..N
-  int N0, N1, do_meas, do_time;
+  int N0, N1, do_meas, do_time, fft;
   MeasParams mp;
   TimeConsts tc;
 };
@@ -87,6 +96,7 @@ struct FusedView {
   const double* z;          // measurement of this epoch
   const TimeConsts* tc;     // model constants of this time update
   const struct BatchPlan* plan;   // planned transform kernel: the front kernel's results
+  int fft;                  // Hartley transforms in shared memory instead of GEMMs
 };
 
 // The constants of the update are kept in shared memory only by the kernels
@@ -434,6 +444,85 @@ __device__ void psi_stage(const SH& sh, float* S, int N0, int N1, int l, int exa
 // kPlan: the planned transform kernel of a batch (time update only; the
 // measurement update, moments, frame decision, sub-step coefficients and
 // regrid rows come from the front kernel through job.plan).  C: size class.
+// ---- shared-memory form of the per-axis Hartley transforms ------------------
+// (the FFT form of steps 1 and 5 of the Sec. V-B algorithm, an alternative to
+// the tensor-core contraction for axis sizes 2^a 3^b)
+__device__ __forceinline__ bool fht_size_ok(int N) {
+  while (N % 3 == 0) N /= 3;
+  return N >= 2 && (N & (N - 1)) == 0;
+}
+
+// e^{-2 pi i a / N}, 0 <= a < N, from the (cos, sin)(pi m / N) table (m = -N..N).
+__device__ __forceinline__ float2 twiddle(const float* sct, int a, int N) {
+  const int m = 2 * a <= N ? 2 * a : 2 * a - 2 * N;
+  return make_float2(sct[2 * (m + N)], -sct[2 * (m + N) + 1]);
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Hartley transforms of L real lines of length N (L even) held in the float32
+// tile S, element (l, j) at S[l * ls + j * es], in place.  Two lines form one
+// complex line z = x_{2p} + i x_{2p+1}; its DFT Z (radix-3 then radix-2
+// Stockham passes, self-sorting, between X and Y, L/2 x N float2 each, neither
+// aliasing S) gives both transforms, F_{2p,k} = (Z_k + conj Z_{N-k}) / 2,
+// F_{2p+1,k} = (Z_k - conj Z_{N-k}) / (2i), and H = Re F - Im F (cas = cos + sin).
+// Ends with a block barrier.
+template <int T>
+__device__ void fht_lines(float* S, int ls, int es, int L, int N, float2* X, float2* Y, const float* sct) {
+  const int half = L / 2, tot = half * N;
+  for (int idx = threadIdx.x; idx < tot; idx += T) {
+    const int p = idx / N, j = idx - p * N;
+    X[idx] = make_float2(S[(2 * p) * ls + j * es], S[(2 * p + 1) * ls + j * es]);
+  }
+  __syncthreads();
+  float2* src = X;
+  float2* dst = Y;
+  int s = 1, rem = N;
+  const float h3 = 0.86602540378443864676f;   // sin(2 pi / 3)
+  while (rem > 1) {
+    const int r = rem % 3 == 0 ? 3 : 2;
+    const int n = N / s, m = n / r;            // this pass: sub-length n, butterflies m x s per line
+    const int per = m * s;
+    for (int idx = threadIdx.x; idx < half * per; idx += T) {
+      const int line = idx / per, b = idx - line * per;
+      const int pp = b / s, q = b - pp * s;
+      const float2* x = src + line * N + q + s * pp;
+      float2* y = dst + line * N + q + s * r * pp;
+      if (r == 2) {
+        const float2 a0 = x[0], a1 = x[s * m];
+        y[0] = make_float2(a0.x + a1.x, a0.y + a1.y);
+        y[s] = cmul(make_float2(a0.x - a1.x, a0.y - a1.y), twiddle(sct, (pp * s) % N, N));
+      } else {
+        const float2 a0 = x[0], a1 = x[s * m], a2 = x[2 * s * m];
+        const float2 bsum = make_float2(a1.x + a2.x, a1.y + a2.y), d = make_float2(a1.x - a2.x, a1.y - a2.y);
+        const float2 c = make_float2(a0.x - 0.5f * bsum.x, a0.y - 0.5f * bsum.y);
+        y[0] = make_float2(a0.x + bsum.x, a0.y + bsum.y);
+        // a0 + a1 w + a2 w^2 (w = e^{-2 pi i / 3}) = c - i h3 d, and its conjugate pair
+        y[s] = cmul(make_float2(c.x + h3 * d.y, c.y - h3 * d.x), twiddle(sct, (pp * s) % N, N));
+        y[2 * s] = cmul(make_float2(c.x - h3 * d.y, c.y + h3 * d.x), twiddle(sct, (2 * pp * s) % N, N));
+      }
+    }
+    __syncthreads();
+    float2* t = src;
+    src = dst;
+    dst = t;
+    s *= r;
+    rem /= r;
+  }
+  for (int idx = threadIdx.x; idx < tot; idx += T) {
+    const int p = idx / N, k = idx - p * N;
+    const float2 zk = src[p * N + k], zm = src[p * N + (k ? N - k : 0)];
+    // F1 = (zk + conj zm) / 2, F2 = -i (zk - conj zm) / 2
+    const float f1r = 0.5f * (zk.x + zm.x), f1i = 0.5f * (zk.y - zm.y);
+    const float f2r = 0.5f * (zk.y + zm.y), f2i = -0.5f * (zk.x - zm.x);
+    S[(2 * p) * ls + k * es] = f1r - f1i;
+    S[(2 * p + 1) * ls + k * es] = f2r - f2i;
+  }
+  __syncthreads();
+}
+
 template <int P, bool kOut, bool kPlan = false, int C = 128>
 __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   using SH = SharedT<Smem<P, C>::threads, C, !kPlan>;
@@ -764,6 +853,83 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     }
     float inv_scale = 1.0f / (sa * sw);
 
+    if (job.fft) {
+      // FFT form: the regrid of each axis stays a tensor-core GEMM whose
+      // epilogue writes float32 to the staging tile; the four Hartley
+      // transforms run in shared memory (fht_lines, scratch in W and A).
+      float2* X = (float2*)W;
+      float2* Y = (float2*)A;
+      for (int g = 0; g < 2; ++g) {
+        // g = 0: R1 (lanes j0, columns k1); g = 1: R0 (lanes k1, columns j0)
+        const bool okw = mbar_wait(mb_mma, ph_mma);
+        ph_mma ^= 1;
+        if (__syncthreads_or(!okw)) {
+          if (tid == 0) sh.abort = 1;
+          break;
+        }
+        tc_after_sync();
+        const int nlane = g ? N1 : N0, nout = g ? N0 : N1;
+        const int ncol = nout / kGroups, c0 = cg * ncol;
+        float4 v[8];
+        tmem_ld_cols(tlane + c0, ncol, v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (4 * j < ncol && row < nlane) {
+            const float4 x = v[j];
+            *(float4*)(S + row * kSStr + c0 + 4 * j) =
+                make_float4(x.x * inv_scale, x.y * inv_scale, x.z * inv_scale, x.w * inv_scale);
+          }
+        tc_before_sync();
+        __syncthreads();
+        if (g == 0) {
+          // F1 along axis 1 (rows of the tile), then the operand of R0 (read MN-major)
+          fht_lines<kThreads>(S, kSStr, 1, N0, N1, X, Y, sh.sct[1]);
+          sa = op_scale<P>(block_max(sh, stage_max<kThreads, C>(S, N0, N1), 0));
+          if constexpr (P == PMF_PREC_TF32) {
+            const int q4 = N1 / 4;
+            for (int t = tid; t < N0 * q4; t += kThreads) {
+              const int r = t % N0, c = (t / N0) * 4;
+              store4_t<C>(A, r, c, *(const float4*)(S + r * kSStr + c), sa);
+            }
+          } else {
+            stage_to_operand<P, C>(A, S, N0, N1, sa, tid, kThreads);
+          }
+          build_interp<P, C, C>(sh.rows[0], W, N0, sh.sct[0], sw, realign, tid, kThreads);
+          fence_async_smem();
+          __syncthreads();
+          if (tid == 0) {
+            tc_after_sync();
+            issue_stage<P, C>(tmem, su32(A), P != PMF_PREC_TF32, su32(W), N0, N0, mb_mma);
+          }
+          inv_scale = 1.0f / (sa * sw);
+        }
+      }
+      if (!sh.abort) {
+        // F0 along axis 0 (rows of the tile T[k1][.]), the multiplier, V0, then
+        // V1 along axis 1 (columns of the tile)
+        fht_lines<kThreads>(S, kSStr, 1, N1, N0, X, Y, sh.sct[0]);
+        psi_stage(sh, S, N0, N1, l, exact);
+        __syncthreads();
+        fht_lines<kThreads>(S, kSStr, 1, N1, N0, X, Y, sh.sct[0]);
+        fht_lines<kThreads>(S, 1, kSStr, N0, N1, X, Y, sh.sct[1]);
+        // final weights: tile [j1][j0] -> row j0 of the output, moments
+        Moments mo;
+        mo.zero();
+        const int q4 = N1 / 4;
+        for (int t = tid; t < N0 * q4; t += kThreads) {
+          const int j0 = t / q4, j1 = (t - j0 * q4) * 4;
+          const float4 x = make_float4(S[j1 * kSStr + j0], S[(j1 + 1) * kSStr + j0], S[(j1 + 2) * kSStr + j0],
+                                       S[(j1 + 3) * kSStr + j0]);
+          *(float4*)(out + (size_t)j0 * N1 + j1) = x;
+          const float u0 = j0 - 0.5f * (N0 - 1), u1 = j1 - 0.5f * (N1 - 1);
+          const float a0 = x.x + x.y + x.z + x.w;
+          const float a1 = x.y + 2.0f * x.z + 3.0f * x.w;
+          const float a2 = x.y + 4.0f * x.z + 9.0f * x.w;
+          mo.add_row(a0, fmaf(u1, a0, a1), fmaf(u1, fmaf(u1, a0, 2.0f * a1), a2), u0);
+        }
+        block_moments(sh, mo);
+      }
+    } else {
     // Stages after R1: F1, R0, F0, V0, V1.  Epilogue of GEMM `stage` (0 = R1)
     // writes the operand of GEMM stage+1.
     for (int stage = 0; stage < 6; ++stage) {
@@ -886,6 +1052,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       __syncthreads();
       if (sh.abort) break;
     }
+    }   // GEMM form
     if (sh.abort) {
       if (tid == 0) fs.status = PMF_ERR_TIMEOUT;
       goto done;
@@ -912,7 +1079,7 @@ template <int P>
 __global__ void __launch_bounds__(kThreads, 1) k_fused2d(const __grid_constant__ FusedJob job) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const FusedView v{job.st, job.buf0, job.buf1, {job.hart[0], job.hart[1]}, {job.sctab[0], job.sctab[1]},
-                    job.N0, job.N1, job.do_meas, job.do_time, &job.mp, job.mp.z, &job.tc};
+                    job.N0, job.N1, job.do_meas, job.do_time, &job.mp, job.mp.z, &job.tc, nullptr, job.fft};
   fused2d<P, true>(v, smem);
 }
 
@@ -1099,7 +1266,7 @@ __global__ void __launch_bounds__(Smem<P, C>::threads, C == 128 ? 1 : 3)
   const FilterSlot& sl = slots[it.slot];
   const FusedView v{sl.st, sl.buf0, sl.buf1, {sl.hart[0], sl.hart[1]}, {sl.sctab[0], sl.sctab[1]},
                     sl.N0, sl.N1, 0, (it.flags >> 1) & 1, sl.mp, it.z,
-                    tcs ? tcs + blockIdx.x : sl.tc, (const BatchPlan*)sl.plan};
+                    tcs ? tcs + blockIdx.x : sl.tc, (const BatchPlan*)sl.plan, sl.fft};
   fused2d<P, false, true, C>(v, smem);
 }
 
@@ -1333,6 +1500,7 @@ int tc_step(const Dims& d, const pmf_config& cfg, const TcTables* t, const MeasP
   }
   job.do_meas = mp != nullptr;
   job.do_time = tcs != nullptr;
+  job.fft = t->fft;
   if (mp) job.mp = *mp;
   if (tcs) job.tc = *tcs;
   if (!job.do_meas && !job.do_time) return 0;
@@ -1392,6 +1560,172 @@ int tc_batch_epoch(int precision, const FilterSlot* slots, const StepItem* items
     cudaStreamWaitEvent(s, ev_join, 0);
   }
   return 1 + (k128 > 0) + (k > k128);
+}
+
+// ---- form of the 2-D Hartley transforms: tensor-core GEMM or shared-memory FFT
+bool tc2_fft_ok(int N0, int N1) {
+  auto ok = [](int N) {
+    while (N % 3 == 0) N /= 3;
+    return N >= 2 && (N & (N - 1)) == 0;
+  };
+  return ok(N0) && ok(N1);
+}
+
+namespace {
+
+std::mutex g_tune2_mu;
+// (N0, N1, precision) -> (form, GEMM us, FFT us)
+std::map<std::tuple<int, int, int>, std::tuple<int, double, double>> g_tune2;
+bool g_tune2_loaded = false;
+
+std::string tune2_path() {
+  Dl_info info;
+  if (!dladdr((void*)&tc2_fft_ok, &info) || !info.dli_fname) return "";
+  std::string p = info.dli_fname;
+  const size_t slash = p.rfind('/');
+  return (slash == std::string::npos ? std::string(".") : p.substr(0, slash)) + "/autotune_2d.json";
+}
+
+// {"2d:N0x N1:p": {"form": f, "gemm_us": g, "fft_us": t}, ...}
+void tune2_load() {
+  g_tune2_loaded = true;
+  const std::string p = tune2_path();
+  FILE* f = p.empty() ? nullptr : std::fopen(p.c_str(), "r");
+  if (!f) return;
+  char line[512];
+  while (std::fgets(line, sizeof line, f)) {
+    int a = 0, b = 0, prec = 0, form = -1;
+    double tg = 0.0, tf = 0.0;
+    const char* q = std::strstr(line, "\"2d:");
+    if (q && std::sscanf(q, "\"2d:%dx%d:%d\": {\"form\": %d, \"gemm_us\": %lf, \"fft_us\": %lf", &a, &b, &prec, &form,
+                         &tg, &tf) == 6 &&
+        (form == 0 || form == 1))
+      g_tune2[std::make_tuple(a, b, prec)] = std::make_tuple(form, tg, tf);
+  }
+  std::fclose(f);
+}
+
+void tune2_save() {
+  const std::string p = tune2_path();
+  FILE* f = p.empty() ? nullptr : std::fopen(p.c_str(), "w");
+  if (!f) return;
+  std::fprintf(f, "{\n");
+  size_t i = 0;
+  for (const auto& kv : g_tune2)
+    std::fprintf(f, "  \"2d:%dx%d:%d\": {\"form\": %d, \"gemm_us\": %.3f, \"fft_us\": %.3f}%s\n",
+                 std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), std::get<0>(kv.second),
+                 std::get<1>(kv.second), std::get<2>(kv.second), ++i < g_tune2.size() ? "," : "");
+  std::fprintf(f, "}\n");
+  std::fclose(f);
+}
+
+// Mean time of one epoch (measurement + time update) of a scratch N0 x N1
+// filter in the fused kernel, in the given form.
+double time_form2(int N0, int N1, int prec, int fft, cudaStream_t s) {
+  pmf_config c{};
+  c.nx = 2;
+  c.N[0] = N0;
+  c.N[1] = N1;
+  const double A[4] = {0.0, 1.0, -1.0, -0.2};
+  for (int i = 0; i < 4; ++i) c.A[i] = A[i];
+  c.Q[0] = 0.1;
+  c.Q[3] = 0.3;
+  c.P0[0] = c.P0[3] = 0.25;
+  c.span_sigma = 6.0;
+  c.dt_sub = 0.01;
+  c.realign_rho = 0.5;
+  c.precision = prec;
+  pmf_meas m{};
+  m.kind = PMF_MEAS_LINEAR;
+  m.nz = 2;
+  m.z[0] = 0.05;
+  m.z[1] = -0.05;
+  m.R[0] = m.R[3] = 0.01;
+  m.H[0] = m.H[3] = 1.0;
+  std::string why;
+  FusedJob job{};
+  if (meas_params(2, &m, &job.mp, &why) || time_consts(c, 0.05, &job.tc, &why)) return -1.0;
+  TcTables t{};
+  if (tc_build_tables(&c, &t, &why) != PMF_OK) {
+    tc_free_tables(&t);
+    return -1.0;
+  }
+  const DevState h = initial_state(c);
+  const size_t P = (size_t)N0 * N1;
+  std::vector<float> w(2 * P, 0.0f);
+  for (int i = 0; i < N0; ++i)
+    for (int j = 0; j < N1; ++j) {
+      const double u = (i - 0.5 * (N0 - 1)) / (N0 / 12.0), v = (j - 0.5 * (N1 - 1)) / (N1 / 12.0);
+      w[(size_t)i * N1 + j] = (float)std::exp(-0.5 * (u * u + v * v));
+    }
+  DevState* st = nullptr;
+  float* buf = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double us = -1.0;
+  if (cudaMalloc(&st, sizeof(DevState)) == cudaSuccess && cudaMalloc(&buf, sizeof(float) * 2 * P) == cudaSuccess &&
+      cudaMemcpy(buf, w.data(), sizeof(float) * 2 * P, cudaMemcpyHostToDevice) == cudaSuccess &&
+      cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+    job.st = st;
+    job.buf0 = buf;
+    job.buf1 = buf + P;
+    job.N0 = N0;
+    job.N1 = N1;
+    for (int a = 0; a < 2; ++a) {
+      job.hart[a] = (const uint8_t*)t.hart[a];
+      job.sctab[a] = (const float*)((const uint8_t*)t.hart[a] + t.hart_bytes[a]);
+    }
+    job.do_meas = 1;
+    job.do_time = 1;
+    job.fft = fft;
+    auto launch = [&]() {
+      if (prec == PMF_PREC_FP16X3)
+        k_fused2d<PMF_PREC_FP16X3><<<1, kThreads, kSmemBytes, s>>>(job);
+      else if (prec == PMF_PREC_BF16X3)
+        k_fused2d<PMF_PREC_BF16X3><<<1, kThreads, kSmemBytes, s>>>(job);
+      else
+        k_fused2d<PMF_PREC_TF32><<<1, kThreads, kSmemBytes, s>>>(job);
+    };
+    constexpr int kReps = 20;
+    float ms = 0.0f;
+    // every epoch starts from the same state and weights
+    for (int i = 0; i < 3 + kReps; ++i) {
+      if (i == 3) cudaEventRecord(e0, s);
+      cudaMemcpyAsync(st, &h, sizeof(DevState), cudaMemcpyHostToDevice, s);
+      launch();
+    }
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+        cudaGetLastError() == cudaSuccess)
+      us = 1e3 * ms / kReps;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(st);
+  cudaFree(buf);
+  tc_free_tables(&t);
+  return us;
+}
+
+}  // namespace
+
+int tc2_form(const pmf_config* cfg, cudaStream_t s) {
+  if (cfg->nx != 2 || !tc2_fft_ok(cfg->N[0], cfg->N[1]) || cfg->transform == PMF_TRANSFORM_GEMM) return 0;
+  if (cfg->transform == PMF_TRANSFORM_FFT) return 1;
+  if (const char* form = std::getenv("PMF_2D_FORM")) {   // explicit choice, no tuning
+    if (!std::strcmp(form, "fft")) return 1;
+    if (!std::strcmp(form, "gemm")) return 0;
+  }
+  const auto key = std::make_tuple(cfg->N[0], cfg->N[1], cfg->precision);
+  std::lock_guard<std::mutex> g(g_tune2_mu);
+  if (!g_tune2_loaded) tune2_load();
+  auto it = g_tune2.find(key);
+  if (it != g_tune2.end()) return std::get<0>(it->second);
+  const double tg = time_form2(cfg->N[0], cfg->N[1], cfg->precision, 0, s);
+  const double tf = time_form2(cfg->N[0], cfg->N[1], cfg->precision, 1, s);
+  const int form = (tf > 0.0 && tg > 0.0 && tf < tg) ? 1 : 0;
+  g_tune2[key] = std::make_tuple(form, tg, tf);
+  tune2_save();
+  return form;
 }
 
 int tc_batch_gather(DevState* st, const int* ids, int k, double* out, cudaStream_t s) {

@@ -12,6 +12,7 @@ struct TcTables {
   void* hart[MAXN];   // split Hartley matrices per axis, canonical smem layout
   size_t hart_bytes[MAXN];
   int prec;
+  int fft;            // 2-D: Hartley transforms in shared memory (tc2_form)
 };
 
 // Resident description of one filter of a batch (device memory).
@@ -25,6 +26,7 @@ struct FilterSlot {
   const MeasParams* mp;     // measurement model of the filter
   const TimeConsts* tc;     // constants of the filter's current tau
   void* plan;               // batched epochs: the front kernel's results (tc_plan_bytes)
+  int fft;                  // 1: Hartley transforms in shared memory (tc2_form), 0: GEMMs
 };
 
 // One filter's request in a batched epoch: flags bit 0 = measurement update
@@ -55,6 +57,13 @@ int tc_build_tables(const pmf_config* cfg, TcTables* t, std::string* why);
 // the compact planned kernel of batched filters whose axes are all <= 64).
 int tc_build_axis_table(int N, int precision, void** dev, size_t* hart_bytes, int cls = 128);
 size_t tc_axis_table_bytes(int N, int precision, int cls = 128);
+// Form of the Hartley transforms of a 2-D filter: 0 the tensor-core GEMMs,
+// 1 the shared-memory FFT (axis sizes 2^a 3^b only).  TRANSFORM_AUTO times
+// both on a scratch filter the first time a (N0, N1, precision) is used and
+// caches the choice in autotune_2d.json beside the library (the environment
+// variable PMF_2D_FORM=fft|gemm overrides it).
+bool tc2_fft_ok(int N0, int N1);
+int tc2_form(const pmf_config* cfg, cudaStream_t s);
 // Size class of a 2-D filter in batched epochs (64 when both axes are <= 64).
 inline int tc_class(int N0, int N1) { return N0 <= 64 && N1 <= 64 ? 64 : 128; }
 // Device bytes of one filter's plan (the front kernel's results of an epoch).

@@ -72,8 +72,10 @@ def test_fft_form_only_where_it_exists():
         Filter(w.c1_scenario(N=200).cfg, precision="fp16x3", transform="fft")
     with pytest.raises(Unsupported):                         # float64 path
         Filter(w.c1_scenario(N=64).cfg, precision="fp64", transform="fft")
-    with pytest.raises(Unsupported):                         # 2-D tensor-core path
-        Filter(w.small_2d_scenario(N=(48, 32), epochs=1).cfg, precision="fp16x3", transform="fft")
+    with pytest.raises(Unsupported):                         # 2-D axis not 2^a 3^b
+        Filter(w.small_2d_scenario(N=(80, 32), epochs=1).cfg, precision="fp16x3", transform="fft")
+    with pytest.raises(Unsupported):                         # 3-D pipelines
+        Filter(w.small_3d_scenario(N=(16, 16, 16), epochs=1).cfg, precision="fp16x3", transform="fft")
 
 
 def test_autotuner_records_its_choice(monkeypatch):
