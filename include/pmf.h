@@ -57,7 +57,6 @@ enum {
 /* Arithmetic of the per-axis transforms (the differentiation GEMMs).
  *   FP64    : float64 grid and float64 transforms (the plain reference path).
  *   TF32    : float32 grid, one TF32 tensor-core product per transform.
- *   TF32X3  : float32 grid, split TF32 (hi*hi + hi*lo + lo*hi), FP32 accumulate.
  *   BF16X3  : float32 grid, split BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulate.
  *   FP16X3  : float32 grid, split FP16 with power-of-two operand scaling,
  *             (hi*hi + hi*lo + lo*hi), FP32 accumulate.
@@ -71,7 +70,7 @@ enum {
 enum {
   PMF_PREC_FP64 = 0,
   PMF_PREC_TF32 = 1,
-  PMF_PREC_TF32X3 = 2,
+  /* 2 is not assigned */
   PMF_PREC_BF16X3 = 3,
   PMF_PREC_FP16X3 = 4
 };

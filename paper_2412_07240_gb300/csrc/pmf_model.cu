@@ -145,7 +145,10 @@ int validate_config(const pmf_config* c, std::string* why) {
     if (c->Q[i * n + i] < 0) { *why = "Q is not positive semidefinite"; return PMF_ERR_ARG; }
   if (!chol(n, c->P0, L)) { *why = "P0 is not positive definite"; return PMF_ERR_ARG; }
   if (!(c->span_sigma > 0) || !(c->dt_sub > 0) || !(c->realign_rho > 0)) { *why = "span, dt_sub, rho must be > 0"; return PMF_ERR_ARG; }
-  if (c->precision < PMF_PREC_FP64 || c->precision > PMF_PREC_FP16X3) { *why = "unknown precision"; return PMF_ERR_ARG; }
+  if (c->precision < PMF_PREC_FP64 || c->precision > PMF_PREC_FP16X3 || c->precision == 2) {
+    *why = "unknown precision";
+    return PMF_ERR_ARG;
+  }
   if (c->psi_mode != PMF_PSI_EULER && c->psi_mode != PMF_PSI_EXACT) { *why = "unknown psi mode"; return PMF_ERR_ARG; }
   if (c->realign_mode != PMF_REALIGN_MULTILINEAR && c->realign_mode != PMF_REALIGN_SHEAR) {
     *why = "unknown re-alignment mode";

@@ -95,3 +95,18 @@ def test_marshalling_of_config_and_measurement():
     assert c1.nx == 1 and c1.N[0] == 64 and c1.A[0] == -0.5 and c1.Q[0] == 0.5
     m1 = _binding.make_meas(sc1.meas, sc1.z[0], 1)
     assert m1.kind == 0 and m1.H[0] == 1.0 and m1.R[0] == 0.01
+
+
+def test_unassigned_precision_rejected_without_gpu():
+    """Precision code 2 is not assigned (no split-TF32 path is built)."""
+    from paper_2412_07240_gb300 import _binding
+    lib = _binding.load()
+    c = _binding.PmfConfig()
+    lib.pmf_config_defaults(ctypes.byref(c))
+    c.nx = 2
+    c.N[0], c.N[1] = 32, 32
+    c.P0[0] = c.P0[3] = 1.0
+    c.precision = 2
+    h = ctypes.c_void_p()
+    assert lib.pmf_create(ctypes.byref(h), ctypes.byref(c), None) == _binding.ERR_ARG
+    assert "tf32x3" not in _binding.PREC
