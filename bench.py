@@ -477,6 +477,27 @@ def run_reference(args, ws, rank, pg):
     print(json.dumps(line))
 
 
+def transform_forms(cfgs, precision):
+    """Filters per Hartley form (tensor-core GEMM or shared-memory FFT), from the
+    2-D autotuner's record beside the library, and the record's entries."""
+    from paper_2412_07240_gb300 import _binding, lib_path
+    path = os.path.join(os.path.dirname(lib_path()), "autotune_2d.json")
+    rec = json.load(open(path)) if os.path.exists(path) else {}
+    code = _binding.PREC[precision]
+    counts, used = {"gemm": 0, "fft": 0}, {}
+    for c in cfgs:
+        key = f"2d:{c.N[0]}x{c.N[1]}:{code}"
+        e = rec.get(key)
+        if os.environ.get("PMF_2D_FORM") in ("gemm", "fft"):
+            counts[os.environ["PMF_2D_FORM"]] += 1
+        elif e is None:
+            counts["gemm"] += 1           # sizes without an FFT form
+        else:
+            counts["fft" if e["form"] else "gemm"] += 1
+            used[key] = e
+    return {"filters": counts, "autotune": used}
+
+
 def bench_batch(args, ws, rank, pg):
     """The 4096-filter batch: one fused launch per epoch over all filters."""
     import numpy as np
@@ -550,6 +571,7 @@ def bench_batch(args, ws, rank, pg):
             "fp64_gpu": {"value": fp64_rate, "unit": UNIT, "filters_timed": int(len(sub))},
             "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
             "degenerate_filters": bad,
+            "transform_forms": transform_forms(cfgs, args.precision),
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                          "frac": gbs / peaks.get("hbm_gbs"),
                          "traffic": None if TRAFFIC_C4_PER_POINT is None else TRAFFIC_C4_PER_POINT * float(P.sum()),
@@ -605,7 +627,8 @@ def bench_serve(args, ws, rank, pg):
     from paper_2412_07240_gb300 import Filter, Server
     n = args.count if args.count != 4096 else 10000
     warm = 0.5
-    wl = w.c5_serving(n_filters=n, rate=args.rate, duration=args.duration + warm, seed=5 + rank)
+    cap_s = args.capacity_log      # log seconds after the timed window, replayed all at once
+    wl = w.c5_serving(n_filters=n, rate=args.rate, duration=args.duration + warm + cap_s, seed=5 + rank)
     P = np.array([int(np.prod(c.N)) for c in wl.cfgs], dtype=np.int64)
     srv = Server(max_filters=n, precision=args.precision, hbm_budget=int(120e9))
     t0 = time.perf_counter()
@@ -613,14 +636,28 @@ def bench_serve(args, ws, rank, pg):
     admit_s = time.perf_counter() - t0
     ids = fid[wl.ids]
     k = int(np.searchsorted(wl.t_arrival, warm))
+    kend = int(np.searchsorted(wl.t_arrival, warm + args.duration))
     srv.replay(wl.t_arrival[:k], ids[:k], wl.z[:k], wl.taus[:k])          # warm-up requests
-    sel = slice(k, None)
+    sel = slice(k, kend)
     _barrier(pg)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         lat, st = srv.replay(wl.t_arrival[sel] - warm, ids[sel], wl.z[sel], wl.taus[sel])
     wall = _max_over_ranks(pg, st["wall_s"] * 1e3) * 1e-3
     pts = float(P[wl.ids[sel]].sum())
     value = ws * pts / wall
+    # capacity: the continuation of the log (each filter's next requests, so
+    # the measurements stay consistent with its state), every request queued
+    # at once: the rate the server sustains when it never waits for arrivals
+    capacity = None
+    if kend < len(wl.t_arrival):
+        csel = slice(kend, None)
+        clat, cst = srv.replay(np.zeros(len(wl.t_arrival) - kend), ids[csel], wl.z[csel], wl.taus[csel])
+        cwall = _max_over_ranks(pg, cst["wall_s"] * 1e3) * 1e-3
+        capacity = {"requests_per_s": ws * float(cst["requests"]) / cwall,
+                    "grid_pt_updates_per_s": ws * float(P[wl.ids[csel]].sum()) / cwall,
+                    "requests": int(cst["requests"]), "wall_s": cwall,
+                    "mean_batch": cst["mean_batch"], "max_batch": int(cst["max_batch"]),
+                    "note": "next requests of every filter, all queued at t = 0 (no arrival waits)"}
     # plain float64 per-filter path on a sample of each dimension
     rng = np.random.default_rng(0)
     f64_pts, f64_s = 0.0, 0.0
@@ -660,6 +697,7 @@ def bench_serve(args, ws, rank, pg):
             "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
                            "max": float(lat.max() * 1e3)},
             "batches": {"count": int(st["batches"]), "mean": st["mean_batch"], "max": int(st["max_batch"])},
+            "capacity": capacity,
             "e2e": {"value": value, "unit": UNIT,
                     "h2d_bytes_per_step": int(st["mean_batch"] * (STEP_ITEM_BYTES + TIME_CONSTS_BYTES)),
                     "d2h_bytes_per_step": 0, "note": "the replay is end to end: requests from host arrays"},
@@ -818,6 +856,8 @@ def make_parser():
     ap.add_argument("--count", type=int, default=4096, help="filters of the c4 batch workload (c5: 10000)")
     ap.add_argument("--rate", type=float, default=200e3, help="c5: aggregate request rate per second")
     ap.add_argument("--duration", type=float, default=60.0, help="c5: seconds of requests replayed")
+    ap.add_argument("--capacity-log", type=float, default=2.0,
+                    help="c5: seconds of further log replayed all at once for the capacity figure")
     ap.add_argument("--mc", type=int, default=50, help="c6: Monte Carlo runs for RMSE/ASTD")
     ap.add_argument("--psi", default="euler", choices=["euler", "exact"],
                     help="c2/c3/c6: diffusion multiplier (Euler product or exact in time)")
