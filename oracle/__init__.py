@@ -22,8 +22,8 @@ Modules
             its sine-transform form (eq. FST).
   kalman    the continuous-discrete Kalman filter (closed form for linear h).
 
-Parity status: every function is pinned by tests in tests/test_oracle_*.py
-except the nonlinear-measurement filter cycles (range, bearing), which are
-pinned only by self-convergence and invariants ("parity unpinned" beyond
-those).
+Parity status: every function is pinned by tests in tests/test_oracle_*.py;
+the range and bearing measurement updates and the predictions that follow
+them are pinned against quadratures and exact moment propagation
+(tests/test_oracle_nonlinear.py), the 4-D terrain measurement likewise.
 """

@@ -219,3 +219,86 @@ def test_bearing_pin_trips_on_planted_mistakes(monkeypatch, mistake):
         return
     em, ec = _rel(*f.moments(), mq, Cq)
     assert max(em, ec) > 1e-2, (em, ec)
+
+
+# --- terrain altitude with Gaussian-mixture noise (n_x = 4, Sec. VI) ---------------
+
+def _terrain_problem(N=(128, 16, 32, 16)):
+    """The coordinated turn in prior-relative coordinates with a position-velocity
+    correlated prior; the grid resolves the likelihood's bands along the two
+    position axes (the velocities enter the likelihood only through the prior)."""
+    sc = w.c6_scenario(N=N, epochs=2, local=True)
+    P0 = np.array(sc.cfg.P0, dtype=float)
+    P0[0, 1] = P0[1, 0] = 60.0
+    sc.cfg.P0 = P0
+    return sc
+
+
+def _terrain_lik(params, z, px, py):
+    """Mixture density of z - h(p), h restated from the model's definition."""
+    p = np.asarray(params, dtype=float)
+    h = p[16] + sum(p[4 * i] * np.sin(p[4 * i + 1] * px + p[4 * i + 2] * py + p[4 * i + 3]) for i in range(4))
+    r = z - h
+    g = lambda mu, v: np.exp(-0.5 * (r - mu) ** 2 / v) / np.sqrt(2 * np.pi * v)
+    return p[17] * g(p[18], p[20]) + (1.0 - p[17]) * g(p[19], p[21])
+
+
+def _terrain_moments(sc, z, n=(900, 500)):
+    """Posterior moments: a Gauss-Legendre quadrature over the positions (x0, x2)
+    with their Gaussian prior marginal, and the velocities by Gaussian
+    conditioning on the positions (exact, the likelihood depends on p only)."""
+    m0, P0 = np.asarray(sc.cfg.m0, float), np.asarray(sc.cfg.P0, float)
+    ip, iv = [0, 2], [1, 3]
+    Cpp, Cvp, Cvv = P0[np.ix_(ip, ip)], P0[np.ix_(iv, ip)], P0[np.ix_(iv, iv)]
+    sd = np.sqrt(np.diag(Cpp))
+    a, wa = _gl(m0[0] - 8 * sd[0], m0[0] + 8 * sd[0], n[0])
+    b, wb = _gl(m0[2] - 8 * sd[1], m0[2] + 8 * sd[1], n[1])
+    PX, PY = np.meshgrid(a, b, indexing="ij")
+    pts = np.stack([PX.ravel(), PY.ravel()], axis=1)
+    wq = np.outer(wa, wb).ravel() * _gauss(pts, m0[ip], Cpp) * _terrain_lik(sc.meas.params, z, pts[:, 0], pts[:, 1])
+    mp, Cp = _moments(pts, wq)
+    K = Cvp @ np.linalg.inv(Cpp)
+    mv = m0[iv] + K @ (mp - m0[ip])
+    Cv = Cvv - K @ Cvp.T + K @ Cp @ K.T
+    m = np.zeros(4)
+    C = np.zeros((4, 4))
+    m[ip], m[iv] = mp, mv
+    C[np.ix_(ip, ip)], C[np.ix_(iv, iv)] = Cp, Cv
+    C[np.ix_(iv, ip)] = K @ Cp
+    C[np.ix_(ip, iv)] = (K @ Cp).T
+    return m, C
+
+
+def test_terrain_update_matches_quadrature():
+    """The Sec. VI measurement (terrain altitude, two-component mixture noise)
+    on a position-velocity correlated Gaussian prior: every moment to the
+    truncation of the prior by the +-6 sigma box.  The grid resolves the
+    likelihood's bands along the positions (16 nodes per velocity axis keep
+    the velocities' trapezoid sums exact)."""
+    sc = _terrain_problem(N=(128, 16, 32, 16))
+    mq, Cq = _terrain_moments(sc, float(sc.z[0][0]))
+    f = of.OracleFilter(sc.cfg, psi_mode="exact")
+    f.meas_update(sc.meas, sc.z[0])
+    em, ec = _rel(*f.moments(), mq, Cq)
+    assert em < 1e-8 and ec < 1e-6, (em, ec)
+
+
+def test_terrain_pin_trips_on_a_planted_mistake(monkeypatch):
+    """The terrain read at (p_x, v_x) instead of (p_x, p_y)."""
+    sc = _terrain_problem(N=(96, 16, 24, 16))
+    z = float(sc.z[0][0])
+    mq, Cq = _terrain_moments(sc, z, n=(500, 300))
+    good = model.h
+
+    def bad(kind, x, H=None, params=None):
+        if kind == "terrain_gm":
+            return model.terrain(params, x[:, 0], x[:, 1])[:, None]
+        return good(kind, x, H, params)
+    monkeypatch.setattr(model, "h", bad)
+    f = of.OracleFilter(sc.cfg, psi_mode="exact")
+    try:
+        f.meas_update(sc.meas, sc.z[0])
+    except of.Degenerate:
+        return
+    em, ec = _rel(*f.moments(), mq, Cq)
+    assert max(em, ec) > 1e-2, (em, ec)
