@@ -65,8 +65,10 @@ enum {
  * For n_x = 1 every precision other than FP64 selects the float32 CUDA-core
  * kernel (a 1-D transform is a matrix-vector product, not a tensor-core tile).
  * For n_x = 4 every precision other than FP64 selects the float32 4-D kernels
- * (float32 contractions on the CUDA cores, N <= 64 per axis; the measurement
- * exponents and moment sums keep float64-class accuracy). */
+ * (float32 weights, split-FP16 tensor-core contractions along axes 0 and 1
+ * and float32 shared-memory contractions along axes 2 and 3, N <= 64 per
+ * axis; the measurement exponents and moment sums keep float64-class
+ * accuracy). */
 enum {
   PMF_PREC_FP64 = 0,
   PMF_PREC_TF32 = 1,

@@ -1,8 +1,9 @@
 // Float32 path for n_x = 4 grids (the coordinated-turn workload of Sec. VI and
 // any other four-dimensional filter).  The weights live in float32; the
-// per-axis transforms are float32 contractions on the CUDA cores; the frame
-// arithmetic, the regrid matrices, the measurement exponents and the moment
-// sums keep float64-class accuracy.
+// per-axis transforms along axes 0 and 1 are tensor-core contractions (split
+// FP16, FP32 accumulation), those along axes 2 and 3 float32 contractions of
+// shared-memory slabs; the frame arithmetic, the regrid matrices, the
+// measurement exponents and the moment sums keep float64-class accuracy.
 //
 // Per time update (Sec. V-B algorithm on the moving grid, eq. gridMov):
 //   frame        regrid decision and sub-step coefficients (float64, shared
@@ -12,7 +13,7 @@
 //                rounded to float32
 //   realign      multilinear re-alignment (or scaled copy) of the weights
 //   slab23       W_3 and W_2 on (j0, j1) slabs in shared memory (one pass)
-//   fwd 1, fwd 0 W_a along axis a
+//   fwd 1, fwd 0 W_a along axis a (k_f4_axis_tc)
 //   psi          diffusion multiplier and trace factor over 16-point sign-flip
 //                orbits (the separable-to-4-D Hartley parity fix-up)
 //   inv 0, inv 1 inverse Hartley transform along axes 0 and 1 (step 5)
@@ -34,12 +35,9 @@ namespace pmf {
 namespace {
 
 constexpr int kMaxN4 = 64;
-constexpr int kCols = 64;               // lines per block of the axis transform
-constexpr int kColStr = kCols + 1;      // shared stride of a tile row (conflict-free column reads)
 
 __host__ __device__ inline int kpad(int N) { return (N + 7) & ~7; }
 
-size_t axis_smem(int N) { return sizeof(float) * (size_t)kpad(N) * (kColStr + kpad(N)); }
 
 // ---- double-float helpers ---------------------------------------------------
 __device__ __forceinline__ DF df_of(double x) {
@@ -525,86 +523,137 @@ __global__ void __launch_bounds__(kShearT4) k_f4_shear(Dims d, const DevState* s
   }
 }
 
-// Y = W x_axis X on the float32 grid viewed as [outer][N][inner] (C order):
-// a block takes kCols consecutive lines along the axis (line = (outer, inner)
-// pair) and stages them as a [Kp][kCols] tile; the block has G = Kp / 8
-// threads per line, thread (line c, group q) forming the outputs k = 8 q ..
-// 8 q + 7 (the 8 weights of a step two float4 broadcasts of W^T), so every
-// thread does the same work.  Kp = 8 G is a template parameter: the loop over
-// j is unrolled with constant shared-memory offsets, rows N .. Kp - 1 of the
-// tile and of W^T are zero (their terms add exact zeros).  Tile loads and the
-// stores of y_k from registers are runs of consecutive floats when inner >=
-// kCols (axes 0 and 1).  Reads bufs[(cur+stage)&1], writes the other one.
-// Indices fit 32 bits (N <= 64).
-template <int G>
-__global__ void __launch_bounds__(kCols * G) k_f4_axis(Dims d, int axis, const float* WT, const DevState* st,
-                                                       int stage, float* b0, float* b1) {
-  constexpr int Kp = 8 * G, kThreads = kCols * G;
-  extern __shared__ __align__(16) float sm[];
-  const int N = d.N[axis];
+// Y = W x_axis X on the float32 grid viewed as [outer][N][inner] (C order),
+// on the tensor cores (tcgen05, split FP16, three products per K step): a CTA of 128 threads takes 128 consecutive lines, one
+// per thread and TMEM lane.  Each thread loads its line (the loads of a warp
+// are runs of consecutive floats for axes 0 and 1), and the tile becomes the A
+// operand [128 lines x K] in hi + lo 16-bit planes under a power-of-two tile
+// scale; W^T becomes the B operand [Nout x K] likewise (K and Nout padded to
+// a multiple of 16 with zeros).  The accumulator goes from TMEM straight to
+// the output lines.  The layout is the size-64 operand layout of the fused
+// kernels (N <= 64).  Every wait is bounded; a lost completion records
+// PMF_ERR_TIMEOUT in the filter's status and skips the stores.
+constexpr int kTcLines = 128;
+constexpr int kTcSmem = 2 * Lay<PMF_PREC_FP16X3, 64>::plane + 2 * Lay<PMF_PREC_FP16X3, 64>::wplane;
+
+__global__ void __launch_bounds__(kTcLines) k_f4_axis_tc(Dims d, int axis, const float* __restrict__ WT,
+                                                         DevState* st, int stage, float* b0, float* b1) {
+  constexpr int P = PMF_PREC_FP16X3, C = 64;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ float red[2][kTcLines / 32];
+  uint8_t* A = smem;
+  uint8_t* W = smem + 2 * Lay<P, C>::plane;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int N = d.N[axis], Kw = kpad(N), K = (N + 15) & ~15;
   int inner = 1;
 #pragma unroll
   for (int m = 1; m < 4; ++m)
     if (m > axis) inner *= d.N[m];
   const int lines = (int)d.P / N;
-  const int l0 = blockIdx.x * kCols;
-  const int nl = min(kCols, lines - l0);
-  float* Ws = sm;                 // [Kp][Kp]: float4 rows stay 16-byte aligned
-  float* Xs = sm + Kp * Kp;       // [Kp][kColStr]
+  const int ln = blockIdx.x * kTcLines + tid;
+  const bool mine = ln < lines;
+  int cbase = 0;
+  if (mine) {
+    const int o = ln / inner;
+    cbase = o * N * inner + (ln - o * inner);
+  }
   const int par = (st->f.cur + stage) & 1;
   const float* X = par ? b1 : b0;
   float* Y = par ? b0 : b1;
-  const int tid = threadIdx.x;
-  for (int i = tid; i < Kp * Kp; i += kThreads) Ws[i] = i < N * Kp ? WT[i] : 0.0f;
-  const int c = tid % kCols, q = tid / kCols;
-  int cbase = 0;
-  if (c < nl) {
-    const int ln = l0 + c, o = ln / inner;
-    cbase = o * N * inner + (ln - o * inner);
+  const uint32_t mb = su32(&mbar);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+    asm volatile("fence.mbarrier_init.release.cluster;");
   }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                 "r"(64));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // this thread's line, and the largest |x| of the tile and |W^T| of the matrix
+  float x[64];
+  float mx = 0.0f, mw = 0.0f;
 #pragma unroll
-  for (int j = q; j < Kp; j += G) Xs[j * kColStr + c] = (c < nl && j < N) ? X[cbase + j * inner] : 0.0f;
+  for (int j = 0; j < 64; ++j) {
+    x[j] = (mine && j < N) ? X[cbase + j * inner] : 0.0f;
+    mx = fmaxf(mx, fabsf(x[j]));
+  }
+  for (int i = tid; i < N * Kw; i += kTcLines) mw = fmaxf(mw, fabsf(WT[i]));
+  for (int o = 16; o; o >>= 1) {
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
+  }
+  if ((tid & 31) == 0) {
+    red[0][warp] = mx;
+    red[1][warp] = mw;
+  }
+  tc_before_sync();
   __syncthreads();
-  if (c >= nl) return;
-  const float* xs = Xs + c;
-  const float* ws = Ws + 8 * q;
-  float acc[8];
+  tc_after_sync();
+  mx = fmaxf(fmaxf(red[0][0], red[0][1]), fmaxf(red[0][2], red[0][3]));
+  mw = fmaxf(fmaxf(red[1][0], red[1][1]), fmaxf(red[1][2], red[1][3]));
+  const float sa = op_scale<P>(mx), sw = op_scale<P>(mw);
+  // A: row = this line, K columns; B: row k (output), column j: W^T[j][k]
 #pragma unroll
-  for (int r = 0; r < 8; ++r) acc[r] = 0.0f;
+  for (int q = 0; q < 16; ++q)
+    if (4 * q < K) store4<P, C>(A, tid, 4 * q, make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]), sa);
+  for (int i = tid; i < K * (K / 4); i += kTcLines) {
+    const int k = i / (K / 4), j = (i - k * (K / 4)) * 4;
+    float v[4];
 #pragma unroll
-  for (int j = 0; j < Kp; ++j) {
-    const float x = xs[j * kColStr];
-    const float4 w0 = *(const float4*)(ws + j * Kp);
-    const float4 w1 = *(const float4*)(ws + j * Kp + 4);
-    acc[0] = fmaf(w0.x, x, acc[0]);
-    acc[1] = fmaf(w0.y, x, acc[1]);
-    acc[2] = fmaf(w0.z, x, acc[2]);
-    acc[3] = fmaf(w0.w, x, acc[3]);
-    acc[4] = fmaf(w1.x, x, acc[4]);
-    acc[5] = fmaf(w1.y, x, acc[5]);
-    acc[6] = fmaf(w1.z, x, acc[6]);
-    acc[7] = fmaf(w1.w, x, acc[7]);
+    for (int t = 0; t < 4; ++t) v[t] = (k < N && j + t < N) ? WT[(j + t) * Kw + k] : 0.0f;
+    store4<P, C, true>(W, k, j, make_float4(v[0], v[1], v[2], v[3]), sw);
   }
+  fence_async_smem();
+  __syncthreads();
+  const uint32_t tmem = tmem_base;
+  if (tid == 0) {
+    tc_after_sync();
+    issue_stage<P, C>(tmem, su32(A), 0, su32(W), K, K, mb);
+  }
+  const bool ok = mbar_wait(mb, 0);
+  tc_after_sync();
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) st->f.status = PMF_ERR_TIMEOUT;
+  } else {
+    const uint32_t lane = tmem + ((uint32_t)(warp * 32) << 16);
+    const float inv = 1.0f / (sa * sw);
+    float4 v[8];
+    tmem_ld_cols(lane, K < 32 ? K : 32, v);
 #pragma unroll
-  for (int r = 0; r < 8; ++r)
-    if (8 * q + r < N) Y[cbase + (8 * q + r) * inner] = acc[r];
+    for (int q = 0; q < 8; ++q) {
+      const float y[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (mine && 4 * q + t < N) Y[cbase + (4 * q + t) * inner] = y[t] * inv;
+    }
+    if (K > 32) {
+      tmem_ld_cols(lane + 32, K - 32, v);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float y[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (mine && 32 + 4 * q + t < N) Y[cbase + (32 + 4 * q + t) * inner] = y[t] * inv;
+      }
+    }
+  }
+  tc_before_sync();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
 }
 
-void launch_axis(const Dims& d, int a, const float* WT, const DevState* st, int stage, float* b0, float* b1,
+void launch_axis(const Dims& d, int a, const float* WT, DevState* st, int stage, float* b0, float* b1,
                  cudaStream_t s) {
-  const int lines = (int)(d.P / d.N[a]), G = kpad(d.N[a]) / 8;
-  const unsigned blocks = (unsigned)((lines + kCols - 1) / kCols);
-  const size_t smem = axis_smem(d.N[a]);
-  switch (G) {
-    case 1: k_f4_axis<1><<<blocks, kCols * 1, smem, s>>>(d, a, WT, st, stage, b0, b1); break;
-    case 2: k_f4_axis<2><<<blocks, kCols * 2, smem, s>>>(d, a, WT, st, stage, b0, b1); break;
-    case 3: k_f4_axis<3><<<blocks, kCols * 3, smem, s>>>(d, a, WT, st, stage, b0, b1); break;
-    case 4: k_f4_axis<4><<<blocks, kCols * 4, smem, s>>>(d, a, WT, st, stage, b0, b1); break;
-    case 5: k_f4_axis<5><<<blocks, kCols * 5, smem, s>>>(d, a, WT, st, stage, b0, b1); break;
-    case 6: k_f4_axis<6><<<blocks, kCols * 6, smem, s>>>(d, a, WT, st, stage, b0, b1); break;
-    case 7: k_f4_axis<7><<<blocks, kCols * 7, smem, s>>>(d, a, WT, st, stage, b0, b1); break;
-    default: k_f4_axis<8><<<blocks, kCols * 8, smem, s>>>(d, a, WT, st, stage, b0, b1); break;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_f4_axis_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    attr = true;
   }
+  const int lines = (int)(d.P / d.N[a]);
+  k_f4_axis_tc<<<(lines + kTcLines - 1) / kTcLines, kTcLines, kTcSmem, s>>>(d, a, WT, st, stage, b0, b1);
 }
 
 // Both inner axes at once: a block takes kSlabs slabs (j0, j1) of N2 x N3

@@ -318,29 +318,40 @@ __device__ __forceinline__ float meas_e3(const Meas3& m, float u0, float u1, flo
   return 0.5f * e;
 }
 
-__device__ void meas_consts(const MeasParams& mp, const FrameState& fs, Meas3& m) {
-  m.kind = mp.kind;
-  m.nz = mp.nz;
-  for (int i = 0; i < 9; ++i) m.M[i] = (float)fs.M[i];
-  for (int i = 0; i < mp.nz * mp.nz; ++i) m.Rinv[i] = (float)mp.Rinv[i];
+// Frame-relative measurement constants of a 3-D filter, formed by the 32
+// lanes of one warp (lane e < 9 one
+// entry of M, R^-1 and H, lanes < nz one residual at the centre): one
+// float64 step per lane instead of a serial chain in one thread while the
+// rest of the CTA waits.
+__device__ void meas_consts_warp(const MeasParams& mp, const FrameState& fs, Meas3& m) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) {
+    m.kind = mp.kind;
+    m.nz = mp.nz;
+  }
+  if (lane < 9) {
+    m.M[lane] = (float)fs.M[lane];
+    if (lane < mp.nz * mp.nz) m.Rinv[lane] = (float)mp.Rinv[lane];
+  }
   if (mp.kind == PMF_MEAS_LINEAR) {
-    for (int i = 0; i < mp.nz; ++i) {
-      double h = 0.0;
-      for (int b = 0; b < 3; ++b) {
-        h += mp.H[i * 3 + b] * fs.c[b];
-        m.H[i * 3 + b] = (float)mp.H[i * 3 + b];
-      }
-      m.r0[i] = (float)(mp.z[i] - h);
+    if (lane < 9 && lane < mp.nz * 3) m.H[lane] = (float)mp.H[lane];
+    if (lane < mp.nz) {
+      const double h = fma(mp.H[lane * 3], fs.c[0], fma(mp.H[lane * 3 + 1], fs.c[1], mp.H[lane * 3 + 2] * fs.c[2]));
+      m.r0[lane] = (float)(mp.z[lane] - h);
     }
-  } else {
+  } else if (lane == 0) {
     // angle and squared norm of the centre were formed when the frame was committed
     double r = mp.z[0] - fs.hc[0];
     const double two_pi = 6.283185307179586476925286766559, pi = 3.14159265358979323846;
     r -= two_pi * ceil((r - pi) * (1.0 / two_pi));
     m.r0[0] = (float)r;
+  } else if (lane == 1) {
     m.r0[1] = (float)(mp.z[1] - fs.c[2]);
+  } else if (lane == 2) {
     m.c0 = (float)fs.c[0];
+  } else if (lane == 3) {
     m.c1 = (float)fs.c[1];
+  } else if (lane == 4) {
     m.cc = (float)fs.hc[1];
   }
 }
@@ -359,7 +370,7 @@ __global__ void __launch_bounds__(kT) k_meas_min3(const __grid_constant__ Batch3
   int blk, cnt;
   const Job3& job = job_at(b, find_job(b, kKindMeas, blockIdx.x, &blk, &cnt));
   const MeasParams& mp = job.mp;
-  if (threadIdx.x == 0) meas_consts(mp, job.st->f, m);
+  if (threadIdx.x < 32) meas_consts_warp(mp, job.st->f, m);
   __syncthreads();
   const Geo3& g = job.g;
   float e = INFINITY;
@@ -386,7 +397,7 @@ __global__ void __launch_bounds__(kT) k_meas_apply3(const __grid_constant__ Batc
   int blk, cnt;
   const Job3& job = job_at(b, find_job(b, kKindMeas, blockIdx.x, &blk, &cnt));
   const MeasParams& mp = job.mp;
-  if (threadIdx.x == 0) meas_consts(mp, job.st->f, m);
+  if (threadIdx.x < 32) meas_consts_warp(mp, job.st->f, m);
   __syncthreads();
   const Geo3& g = job.g;
   const int cur = job.st->f.cur;
