@@ -415,6 +415,7 @@ struct pmf_batch {
   uint8_t* d_plan = nullptr;          // per filter: the front kernel's results of an epoch
   std::vector<void*> tables;          // per distinct N (and size class)
   std::vector<double> tau;            // tau of the constants resident for each filter
+  std::vector<int> cls;               // size class of each filter's transform kernel
   int* d_ids = nullptr;               // filter ids of a moments/status query
   double* d_gather = nullptr;         // 8 doubles per queried filter
   int* h_ids = nullptr;               // pinned staging of the query
@@ -428,7 +429,8 @@ struct pmf_batch {
   cudaEvent_t evf = nullptr, evj = nullptr;   // fork and join of the two branches
   cudaGraphExec_t gx[2] = {nullptr, nullptr}; // item copy + batch kernel, per parity buffer
   int gk[2] = {0, 0};                         // batch size each graph was captured for
-  int gk128[2] = {0, 0};                      // ... and its number of size-128 filters
+  int gk128[2] = {0, 0};                      // ... and its numbers of size-128
+  int gk96[2] = {0, 0};                       // and size-96 filters
   int per_epoch = 0;                          // kernel launches in one epoch graph
   long long bytes = 0, launches = 0;
   std::string err;
@@ -477,6 +479,7 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
   std::string why;
   const int prec = cfgs[0].precision;
   std::vector<MeasParams> mps(count);
+  std::vector<int> forms(count);      // Hartley form per filter (tc2_form)
   std::vector<int> sizes;             // key N * 1000 + size class of the table
   long long wfloats = 0;
   for (int i = 0; i < count; ++i) {
@@ -489,7 +492,8 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
     if (rc) return rc;
     rc = meas_params(2, &models[i], &mps[i], &why);
     if (rc) return rc;
-    const int cls = tc_class(cfgs[i].N[0], cfgs[i].N[1]);
+    forms[i] = tc2_form(&cfgs[i], (cudaStream_t)cuda_stream);
+    const int cls = tc_class_form(cfgs[i].N[0], cfgs[i].N[1], forms[i]);
     for (int a = 0; a < 2; ++a) {
       const int key = cfgs[i].N[a] * 1000 + cls;
       if (std::find(sizes.begin(), sizes.end(), key) == sizes.end()) sizes.push_back(key);
@@ -511,6 +515,7 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
   b->stream = (cudaStream_t)cuda_stream;
   b->cfgs.assign(cfgs, cfgs + count);
   b->tau.assign(count, -1.0);
+  b->cls.assign(count, 128);
   b->bytes = bytes;
 #define BALLOC(ptr, n)                                                       \
   do {                                                                       \
@@ -572,7 +577,8 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
     sl.buf0 = b->d_w + off;
     sl.buf1 = b->d_w + off + P;
     off += 2 * P;
-    const int cls = tc_class(c.N[0], c.N[1]);
+    const int cls = tc_class_form(c.N[0], c.N[1], forms[i]);
+    b->cls[i] = cls;
     for (int a = 0; a < 2; ++a) {
       const size_t s = std::find(sizes.begin(), sizes.end(), c.N[a] * 1000 + cls) - sizes.begin();
       sl.hart[a] = (const uint8_t*)tabs[s];
@@ -583,7 +589,7 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
     sl.mp = b->d_mp + i;
     sl.tc = b->d_tc + i;
     sl.plan = b->d_plan + tc_plan_bytes() * i;
-    sl.fft = tc2_form(&c, b->stream);
+    sl.fft = forms[i];
   }
   cudaMemcpy(b->d_st, hst.data(), sizeof(DevState) * count, cudaMemcpyHostToDevice);
   cudaMemcpy(b->d_mp, mps.data(), sizeof(MeasParams) * count, cudaMemcpyHostToDevice);
@@ -643,18 +649,19 @@ int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_
       b->tau[id] = tau;
     }
   }
-  // size class 128 first, then 64 (the two transform kernels take the two
-  // ranges); within a class larger grids first: the hardware hands CTAs out
-  // in order, so the longest run first and the tail is made of small filters
-  auto cls = [&](const StepItem& x) { return tc_class(b->cfgs[x.slot].N[0], b->cfgs[x.slot].N[1]); };
+  // size class 128 first, then 96, then 64 (one transform kernel per range);
+  // within a class larger grids first: the hardware hands CTAs out in order,
+  // so the longest run first and the tail is made of small filters
+  auto cls = [&](const StepItem& x) { return b->cls[x.slot]; };
   std::vector<StepItem> sorted(items, items + k);
   std::stable_sort(sorted.begin(), sorted.end(), [&](const StepItem& x, const StepItem& y) {
     const int cx = cls(x), cy = cls(y);
     return cx != cy ? cx > cy : b->npts[x.slot] > b->npts[y.slot];
   });
   std::copy(sorted.begin(), sorted.end(), items);
-  int k128 = 0;
+  int k128 = 0, k96 = 0;
   while (k128 < k && cls(items[k128]) == 128) ++k128;
+  while (k128 + k96 < k && cls(items[k128 + k96]) == 96) ++k96;
   for (int j = 0; j < nchanged; ++j)
     if (cudaMemcpyAsync(b->d_tc + changed[j], &stage[j], sizeof(TimeConsts), cudaMemcpyHostToDevice,
                         b->stream) != cudaSuccess)
@@ -662,7 +669,7 @@ int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_
   // the item copy and the batch kernel replay as one CUDA graph, captured
   // once per parity buffer and batch size (the copy reads this parity's
   // pinned items when the graph runs)
-  if (!b->gx[p] || b->gk[p] != k || b->gk128[p] != k128) {
+  if (!b->gx[p] || b->gk[p] != k || b->gk128[p] != k128 || b->gk96[p] != k96) {
     if (b->gx[p]) {
       cudaGraphExecDestroy(b->gx[p]);
       b->gx[p] = nullptr;
@@ -675,8 +682,8 @@ int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PMF_ERR_CUDA;
     cudaMemcpyAsync(b->d_items, items, sizeof(StepItem) * k, cudaMemcpyHostToDevice, b->cap);
-    b->per_epoch = tc_batch_epoch(b->precision, b->d_slots, b->d_items, k, k128, b->cap, nullptr, b->cap2, b->evf,
-                                  b->evj);
+    b->per_epoch = tc_batch_epoch(b->precision, b->d_slots, b->d_items, k, k128, k96, b->cap, nullptr, b->cap2,
+                                  b->evf, b->evj);
     if (cudaStreamEndCapture(b->cap, &g) != cudaSuccess) return PMF_ERR_CUDA;
     const cudaError_t e = cudaGraphInstantiate(&b->gx[p], g, 0);
     cudaGraphDestroy(g);
@@ -686,6 +693,7 @@ int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_
     }
     b->gk[p] = k;
     b->gk128[p] = k128;
+    b->gk96[p] = k96;
   }
   if (cudaGraphLaunch(b->gx[p], b->stream) != cudaSuccess) return PMF_ERR_CUDA;
   cudaEventRecord(b->ev[p], b->stream);

@@ -118,6 +118,7 @@ struct SFilter {
   TcTables tct{};          // 2-D/3-D: shared tables (owned by the server)
   void* tc3 = nullptr;     // 3-D pipeline state (owned)
   void* plan = nullptr;    // 2-D: the batch front kernel's results (owned)
+  int cls = 128;           // 2-D: size class of its transform kernel
   // request in progress
   bool busy = false;
   long long cur = -1;
@@ -191,8 +192,8 @@ int sync_all(pmf_server* s) {
 
 // Shared device table of an axis size: kind 1 = 1-D kernel table, 2 = split
 // Hartley planes + sinc table of the tensor-core kernels (size class 128),
-// 3 = the same for the size-64 class of the batched 2-D kernels.  Adds new
-// bytes to *add.
+// 3 and 4 = the same for the size-64 and size-96 classes of the batched 2-D
+// kernels.  Adds new bytes to *add.
 int table_for(pmf_server* s, int kind, int N, void** out, size_t* hb, long long* add, bool create) {
   const long long key = (long long)kind * 100000 + N;
   auto it = s->tables.find(key);
@@ -201,7 +202,7 @@ int table_for(pmf_server* s, int kind, int N, void** out, size_t* hb, long long*
     if (hb) *hb = s->hart_bytes[key];
     return PMF_OK;
   }
-  const int cls = kind == 3 ? 64 : 128;
+  const int cls = kind == 3 ? 64 : kind == 4 ? 96 : 128;
   const long long nb =
       kind == 1 ? (long long)tc1_table_bytes(N) : (long long)tc_axis_table_bytes(N, s->precision, cls);
   *add += nb;
@@ -274,16 +275,25 @@ int launch_batch(pmf_server* s, const double* z, const double* taus) {
 
   // host constants (parallel), items
   std::vector<TimeConsts> tc3(its.size());
-  // 2-D items: size class 128 first, then 64 (the two transform kernels take the two ranges)
-  auto cls2 = [&](int id) { return tc_class(s->f[id].cfg.N[0], s->f[id].cfg.N[1]); };
-  int n128 = 0;
+  // 2-D items: size class 128 first, then 96, then 64 (one transform kernel per range)
+  auto cls2 = [&](int id) { return s->f[id].cls; };
+  int n128 = 0, n96 = 0;
   for (const Item& it : its)
-    if (it.kind == 1 && cls2(it.id) == 128) ++n128;
-  int slot[2] = {0, 0}, slot64 = n128;
+    if (it.kind == 1) {
+      const int c = cls2(it.id);
+      n128 += c == 128;
+      n96 += c == 96;
+    }
+  int slot[2] = {0, 0}, slot96 = n128, slot64 = n128 + n96;
   std::vector<int> pos(its.size());
   for (size_t i = 0; i < its.size(); ++i) {
     const int k = its[i].kind;
-    pos[i] = k == 0 ? slot[0]++ : k == 1 ? (cls2(its[i].id) == 128 ? slot[1]++ : slot64++) : 0;
+    if (k != 1) {
+      pos[i] = k == 0 ? slot[0]++ : 0;
+      continue;
+    }
+    const int c = cls2(its[i].id);
+    pos[i] = c == 128 ? slot[1]++ : c == 96 ? slot96++ : slot64++;
   }
   std::atomic<int> bad{0};
   const std::function<void(int)> fill = [&](int i) {
@@ -314,7 +324,7 @@ int launch_batch(pmf_server* s, const double* z, const double* taus) {
             cudaSuccess)
       return sfail(s, PMF_ERR_CUDA, "batch copies");
     s->launches += k == 0 ? tc1_batch_step(s->d_slots1, b.d_items[0], b.d_tc[0], n, s->s[0])
-                          : tc_batch_epoch(s->precision, s->d_slots2, b.d_items[1], n, n128, s->s[1], b.d_tc[1]);
+                          : tc_batch_epoch(s->precision, s->d_slots2, b.d_items[1], n, n128, n96, s->s[1], b.d_tc[1]);
     cudaEventRecord(b.ev[k], s->s[k]);
     b.used[k] = true;
   }
@@ -452,7 +462,14 @@ int pmf_server_admit(pmf_server* s, const pmf_config* cfg, const pmf_meas* model
   if (n == 3) bytes += (long long)tc3_state_bytes();
   if (n == 2) bytes += (long long)tc_plan_bytes();
   // table kind of this filter's axes (the 2-D size-64 class has its own layout)
-  const int tkind = n == 1 ? 1 : (n == 2 && tc_class(cfg->N[0], cfg->N[1]) == 64 ? 3 : 2);
+  int form2 = 0;
+  if (n == 2) {
+    pmf_config fc = *cfg;
+    fc.precision = s->precision;
+    form2 = tc2_form(&fc, s->s[0]);
+  }
+  const int cls = n == 2 ? tc_class_form(cfg->N[0], cfg->N[1], form2) : 128;
+  const int tkind = n == 1 ? 1 : (cls == 64 ? 3 : cls == 96 ? 4 : 2);
   long long tbytes = 0;
   void* tab = nullptr;
   for (int a = 0; a < n; ++a) {
@@ -468,6 +485,7 @@ int pmf_server_admit(pmf_server* s, const pmf_config* cfg, const pmf_meas* model
   f = SFilter{};
   f.cfg = *cfg;
   f.cfg.precision = n == 1 ? PMF_PREC_FP16X3 : s->precision;
+  f.cls = cls;
   f.mp = mp;
   f.P = P;
   bool ok = cudaMalloc(&f.st, sizeof(DevState)) == cudaSuccess &&
@@ -524,9 +542,7 @@ int pmf_server_admit(pmf_server* s, const pmf_config* cfg, const pmf_meas* model
     sl.mp = f.d_mp;
     sl.tc = nullptr;
     sl.plan = f.plan;
-    pmf_config fc = *cfg;
-    fc.precision = s->precision;
-    sl.fft = tc2_form(&fc, st);
+    sl.fft = form2;
     ok = cudaMemcpyAsync(s->d_slots2 + id, &sl, sizeof(sl), cudaMemcpyHostToDevice, st) == cudaSuccess;
   }
   ok = ok && cudaStreamSynchronize(st) == cudaSuccess && cudaGetLastError() == cudaSuccess;

@@ -59,14 +59,22 @@ constexpr uint32_t kTmemCols = 128;
 //            128 rows x 64 (A) and 64 x 64 (W), three CTAs per SM.
 // Dynamic shared memory: A operand planes, W operand planes, float32 staging
 // of C rows x (C + 4) floats (the padding makes row access conflict-free).
+//   C = 96 : 256 threads, planes of 128 rows x 96 and 96 x 96, and the staging
+//            tile shares the W region (alias): the weights are staged there
+//            before the first matrix is built, the spectrum is written there
+//            after the forward transforms and H0 is copied in again for the
+//            inverse; two CTAs per SM.
 template <int P, int C>
 struct Smem {
   static constexpr int threads = C == 128 ? 512 : 256;
   static constexpr int sstr = C + 4;
+  static constexpr bool alias = C == 96;
   static constexpr int offA = 0;
   static constexpr int offW = Fmt<P>::planes * Lay<P, C>::plane;
-  static constexpr int offS = offW + Fmt<P>::planes * Lay<P, C>::wplane;
-  static constexpr int bytes = offS + C * sstr * 4;
+  static constexpr int wbytes = Fmt<P>::planes * Lay<P, C>::wplane;
+  static constexpr int sbytes = C * sstr * 4;
+  static constexpr int offS = alias ? offW : offW + wbytes;
+  static constexpr int bytes = alias ? offW + (wbytes > sbytes ? wbytes : sbytes) : offS + sbytes;
 };
 constexpr int kThreads = 512;                // the single-filter kernel (class 128)
 constexpr int kSmemBytes = Smem<PMF_PREC_FP16X3, 128>::bytes;
@@ -527,6 +535,8 @@ template <int P, bool kOut, bool kPlan = false, int C = 128>
 __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   using SH = SharedT<Smem<P, C>::threads, C, !kPlan>;
   constexpr int kThreads = SH::kT, kSStr = SH::kStr, kGroups = kThreads / 128;
+  constexpr int kNV = C / kGroups / 4;          // float4 accumulator columns per thread
+  constexpr bool kAlias = Smem<P, C>::alias;    // staging tile in the W region
   __shared__ SH sh;
   if (!job.do_meas && !job.do_time) return;   // nothing requested for this filter
   if constexpr (kPlan) {
@@ -784,8 +794,9 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       if constexpr (kOut) stage_to_operand_out<P, C>(A, S, N0, N1, sa_first, tid, kThreads);
       else stage_to_operand<P, C>(A, S, N0, N1, sa_first, tid, kThreads);
     } else if (realign) {
-      // multilinear re-alignment: gather into the (free) W region, copy back
-      float* G = (float*)W;
+      // multilinear re-alignment: gather into the (free) W region, or the A
+      // region when the staging tile lives in W, copy back
+      float* G = (float*)(kAlias ? A : W);
       const int npts = N0 * N1;
       for (int p = tid; p < npts; p += kThreads) {
         const int r = p / N1, c = p - r * N1;
@@ -853,7 +864,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     }
     float inv_scale = 1.0f / (sa * sw);
 
-    if (job.fft) {
+    if (!kAlias && job.fft) {
       // FFT form: the regrid of each axis stays a tensor-core GEMM whose
       // epilogue writes float32 to the staging tile; the four Hartley
       // transforms run in shared memory (fht_lines, scratch in W and A).
@@ -946,7 +957,10 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       int mat = -1;
       if (stage == 0 || stage == 4) mat = 1;
       if (stage == 2) mat = 0;
-      if (tid == 0 && mat >= 0) {
+      // the spectrum goes to the staging tile, which shares W: H0 again for V0
+      // once the tile has been read (below)
+      if (kAlias && stage == 3) mat = 0;
+      if (tid == 0 && mat >= 0 && !(kAlias && stage == 3)) {
         const int Nm = mat == 0 ? N0 : N1;
         const uint32_t pbytes = (uint32_t)Nm * (uint32_t)(Lay<P, C>::rowblk / 8);
         expect_tx(mb_tma, pbytes * Fmt<P>::planes);
@@ -958,10 +972,21 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       const int nout = (stage <= 1 || stage == 5) ? N1 : N0;
       const int ncol = nout / kGroups, c0 = cg * ncol;   // this thread's columns
       const bool lane_ok = row < nlane;
-      float4 v[8];
-      tmem_ld_cols(tlane + c0, ncol, v);
+      float4 v[kNV];
+      if constexpr (kNV == 8) {
+        tmem_ld_cols(tlane + c0, ncol, v);
+      } else {
+        // up to 48 columns: 32 + 16
+        float4 va[8], vb[4];
+        tmem_ld_cols(tlane + c0, ncol < 32 ? ncol : 32, va);
+        tmem_ld_cols4(tlane + c0 + 32, ncol > 32 ? ncol - 32 : 0, vb);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < 8; ++j) v[j] = va[j];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[8 + j] = vb[j];
+      }
+#pragma unroll
+      for (int j = 0; j < kNV; ++j) {
         v[j].x *= inv_scale;
         v[j].y *= inv_scale;
         v[j].z *= inv_scale;
@@ -976,7 +1001,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         float* orow = out + (size_t)row * N1 + c0;
         float ra = 0.0f, rb = 0.0f, rc = 0.0f;   // this row segment: sum x, x u1, x u1^2
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
+        for (int j = 0; j < kNV; ++j)
           if (4 * j < ncol && lane_ok) {
             *(float4*)(orow + 4 * j) = v[j];
             const float4 x = v[j];
@@ -997,7 +1022,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       if (stage == 3) {
         // F0 finished: spectrum T[k1][k0] -> staging, multiplier, operand of V0
 #pragma unroll
-        for (int j = 0; j < 8; ++j)   // valid lanes only: the staging tile has C rows
+        for (int j = 0; j < kNV; ++j)   // valid lanes only: the staging tile has C rows
           if (4 * j < ncol && lane_ok) *(float4*)(S + row * kSStr + c0 + 4 * j) = v[j];
         tc_before_sync();
         __syncthreads();
@@ -1009,12 +1034,12 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       } else {
         float m = 0.0f;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) m = amax4(m, v[j]);
+        for (int j = 0; j < kNV; ++j) m = amax4(m, v[j]);
         sa = op_scale<P>(block_max(sh, lane_ok ? m : 0.0f, stage & 1));
         // R0 and V1 read this operand MN-major; TF32 gets it written transposed
         const bool tr = P == PMF_PREC_TF32 && (stage == 1 || stage == 4);
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
+        for (int j = 0; j < kNV; ++j)
           if (4 * j < ncol) {
             if (tr) {
               // transposed, lanes become columns: a lane >= C would land in the
@@ -1036,6 +1061,12 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       if (tid == 0) {
         tc_after_sync();
         bool ok2 = true;
+        if (kAlias && stage == 3) {
+          const uint32_t pbytes = (uint32_t)N0 * (uint32_t)(Lay<P, C>::rowblk / 8);
+          expect_tx(mb_tma, pbytes * Fmt<P>::planes);
+          for (int pl = 0; pl < Fmt<P>::planes; ++pl)
+            bulk_load(su32(W) + pl * Lay<P, C>::wplane, job.hart[0] + (size_t)pl * pbytes, pbytes, mb_tma);
+        }
         if (mat >= 0) ok2 = mbar_wait(mb_tma, ph_tma);
         if (!ok2) {
           sh.abort = 1;
@@ -1258,7 +1289,7 @@ __global__ void __launch_bounds__(kFrontThreads, 6) k_front2d(const FilterSlot* 
 // Planned transform kernel of a batched epoch (size class C): the time update
 // of the filters whose front kernel ran it, from the weights and plan it left.
 template <int P, int C>
-__global__ void __launch_bounds__(Smem<P, C>::threads, C == 128 ? 1 : 3)
+__global__ void __launch_bounds__(Smem<P, C>::threads, C == 128 ? 1 : (C == 96 ? 2 : 3))
     k_fused2d_planned(const FilterSlot* __restrict__ slots, const StepItem* __restrict__ items,
                       const TimeConsts* __restrict__ tcs) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -1375,7 +1406,7 @@ int tc_supported(const pmf_config* cfg, std::string* why) {
 }
 
 int tc_build_axis_table(int N, int precision, void** dev, size_t* hart_bytes, int cls) {
-  if (cls != 128 && (cls != 64 || N > 64)) return PMF_ERR_ARG;
+  if ((cls != 128 && cls != 96 && cls != 64) || N > cls) return PMF_ERR_ARG;
   const double scale = precision == PMF_PREC_FP16X3 ? 16384.0 : 1.0;
   std::vector<double> H((size_t)N * N);
   const double w = 6.283185307179586476925286766559 / N;
@@ -1415,6 +1446,12 @@ int tc_build_axis_table(int N, int precision, void** dev, size_t* hart_bytes, in
                          Smem<PMF_PREC_TF32, 128>::bytes);
     cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_FP16X3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          Smem<PMF_PREC_FP16X3, 64>::bytes);
+    cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_FP16X3, 96>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         Smem<PMF_PREC_FP16X3, 96>::bytes);
+    cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_BF16X3, 96>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         Smem<PMF_PREC_BF16X3, 96>::bytes);
+    cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_TF32, 96>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         Smem<PMF_PREC_TF32, 96>::bytes);
     cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_BF16X3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          Smem<PMF_PREC_BF16X3, 64>::bytes);
     cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_TF32, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1529,18 +1566,22 @@ size_t tc_plan_bytes() { return sizeof(BatchPlan); }
 
 namespace {
 template <int P>
-void launch_planned(const FilterSlot* slots, const StepItem* items, int k, int k128, cudaStream_t s,
+void launch_planned(const FilterSlot* slots, const StepItem* items, int k, int k128, int k96, cudaStream_t s,
                     const TimeConsts* tcs, cudaStream_t s2) {
   if (k128 > 0)
     k_fused2d_planned<P, 128><<<k128, Smem<P, 128>::threads, Smem<P, 128>::bytes, s>>>(slots, items, tcs);
-  if (k > k128)
-    k_fused2d_planned<P, 64><<<k - k128, Smem<P, 64>::threads, Smem<P, 64>::bytes, s2>>>(
+  if (k96 > 0)
+    k_fused2d_planned<P, 96><<<k96, Smem<P, 96>::threads, Smem<P, 96>::bytes, s2>>>(
         slots, items + k128, tcs ? tcs + k128 : nullptr);
+  const int k64 = k - k128 - k96;
+  if (k64 > 0)
+    k_fused2d_planned<P, 64><<<k64, Smem<P, 64>::threads, Smem<P, 64>::bytes, s2>>>(
+        slots, items + k128 + k96, tcs ? tcs + k128 + k96 : nullptr);
 }
 }  // namespace
 
-int tc_batch_epoch(int precision, const FilterSlot* slots, const StepItem* items, int k, int k128, cudaStream_t s,
-                   const TimeConsts* tcs, cudaStream_t s2, cudaEvent_t ev_fork, cudaEvent_t ev_join) {
+int tc_batch_epoch(int precision, const FilterSlot* slots, const StepItem* items, int k, int k128, int k96,
+                   cudaStream_t s, const TimeConsts* tcs, cudaStream_t s2, cudaEvent_t ev_fork, cudaEvent_t ev_join) {
   if (k <= 0) return 0;
   k_front2d<<<k, kFrontThreads, 0, s>>>(slots, items, tcs);
   const bool fork = s2 && ev_fork && ev_join && k128 > 0 && k > k128;
@@ -1550,16 +1591,16 @@ int tc_batch_epoch(int precision, const FilterSlot* slots, const StepItem* items
   }
   cudaStream_t t = fork ? s2 : s;
   if (precision == PMF_PREC_FP16X3)
-    launch_planned<PMF_PREC_FP16X3>(slots, items, k, k128, s, tcs, t);
+    launch_planned<PMF_PREC_FP16X3>(slots, items, k, k128, k96, s, tcs, t);
   else if (precision == PMF_PREC_BF16X3)
-    launch_planned<PMF_PREC_BF16X3>(slots, items, k, k128, s, tcs, t);
+    launch_planned<PMF_PREC_BF16X3>(slots, items, k, k128, k96, s, tcs, t);
   else
-    launch_planned<PMF_PREC_TF32>(slots, items, k, k128, s, tcs, t);
+    launch_planned<PMF_PREC_TF32>(slots, items, k, k128, k96, s, tcs, t);
   if (fork) {
     cudaEventRecord(ev_join, s2);
     cudaStreamWaitEvent(s, ev_join, 0);
   }
-  return 1 + (k128 > 0) + (k > k128);
+  return 1 + (k128 > 0) + (k96 > 0) + (k - k128 - k96 > 0);
 }
 
 // ---- form of the 2-D Hartley transforms: tensor-core GEMM or shared-memory FFT

@@ -64,8 +64,19 @@ size_t tc_axis_table_bytes(int N, int precision, int cls = 128);
 // variable PMF_2D_FORM=fft|gemm overrides it).
 bool tc2_fft_ok(int N0, int N1);
 int tc2_form(const pmf_config* cfg, cudaStream_t s);
-// Size class of a 2-D filter in batched epochs (64 when both axes are <= 64).
-inline int tc_class(int N0, int N1) { return N0 <= 64 && N1 <= 64 ? 64 : 128; }
+// Size class of a 2-D filter in batched epochs: the largest axis rounded up
+// to 64, 96 or 128.
+inline int tc_class(int N0, int N1) {
+  const int m = N0 > N1 ? N0 : N1;
+  return m <= 64 ? 64 : m <= 96 ? 96 : 128;
+}
+// ... for a filter in the given transform form: the size-96 class keeps its
+// staging tile in the W region, which the FFT form needs as scratch, so an
+// FFT-form filter of that class runs in the size-128 class.
+inline int tc_class_form(int N0, int N1, int fft) {
+  const int c = tc_class(N0, N1);
+  return fft && c == 96 ? 128 : c;
+}
 // Device bytes of one filter's plan (the front kernel's results of an epoch).
 size_t tc_plan_bytes();
 void tc_free_tables(TcTables* t);
@@ -119,11 +130,11 @@ int tc3_batch(const Tc3Item* items, int n, int precision, Tc3Stage* g, cudaStrea
 int tc_batch_step(int precision, const FilterSlot* slots, const StepItem* items, int k, cudaStream_t s,
                   const TimeConsts* tcs = nullptr);
 // A batched epoch as a front kernel over all k items, then the planned
-// transform kernels: items [0, k128) of size class 128, then [k128, k) of
-// class 64 (on stream s2 when it is given, joined back into s through ev,
-// so the two classes share the SMs).  tcs as for tc_batch_step.  Returns the
-// number of launches.
-int tc_batch_epoch(int precision, const FilterSlot* slots, const StepItem* items, int k, int k128,
+// transform kernels: items [0, k128) of size class 128, [k128, k128 + k96) of
+// class 96, the rest of class 64 (the last two on stream s2 when it is given,
+// joined back into s through the events, so the classes share the SMs).  tcs
+// as for tc_batch_step.  Returns the number of launches.
+int tc_batch_epoch(int precision, const FilterSlot* slots, const StepItem* items, int k, int k128, int k96,
                    cudaStream_t s, const TimeConsts* tcs = nullptr, cudaStream_t s2 = nullptr,
                    cudaEvent_t ev_fork = nullptr, cudaEvent_t ev_join = nullptr);
 

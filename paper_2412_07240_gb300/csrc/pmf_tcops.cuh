@@ -105,6 +105,28 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, int ncol, float4 (&
                  "+f"(v[7].x), "+f"(v[7].y), "+f"(v[7].z), "+f"(v[7].w)::"memory");
 }
 
+// Columns [0, ncol) (ncol a multiple of 4, at most 16) of this thread's TMEM
+// lane into v[0..ncol/4), zeros beyond; one wait for all loads.
+__device__ __forceinline__ void tmem_ld_cols4(uint32_t taddr, int ncol, float4 (&v)[4]) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (j * 4 < ncol) {
+      uint32_t r0, r1, r2, r3;
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                   : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                   : "r"(taddr + 4 * j)
+                   : "memory");
+      v[j] = make_float4(__uint_as_float(r0), __uint_as_float(r1), __uint_as_float(r2), __uint_as_float(r3));
+    } else {
+      v[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+  }
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+f"(v[0].x), "+f"(v[0].y), "+f"(v[0].z), "+f"(v[0].w), "+f"(v[1].x), "+f"(v[1].y),
+                 "+f"(v[1].z), "+f"(v[1].w), "+f"(v[2].x), "+f"(v[2].y), "+f"(v[2].z), "+f"(v[2].w),
+                 "+f"(v[3].x), "+f"(v[3].y), "+f"(v[3].z), "+f"(v[3].w)::"memory");
+}
+
 // Bulk copy shared -> global (bulk-group completion), commit, and wait for
 // all of this thread's bulk groups to complete.
 __device__ __forceinline__ void bulk_store(void* dst, uint32_t src, uint32_t bytes) {
