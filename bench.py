@@ -177,7 +177,7 @@ STEP_ITEM_BYTES = 32
 TIME_CONSTS_BYTES = 5832
 TRAFFIC_C2 = 345344.0
 TRAFFIC_C4_PER_POINT = None   # not captured for the current batch kernels
-BATCH_KERNEL = "k_front2d + k_fused2d_planned<128> + k_fused2d_planned<64> (one graph per epoch)"
+BATCH_KERNEL = "k_front2d + k_fused2d_planned<128|96|64> (one graph per epoch)"
 
 
 def _flops_per_step(N):
