@@ -609,6 +609,10 @@ def bench_batch(args, ws, rank, pg):
                                 "sample": f"{t['filters']} filters spread over the batch, {t['epochs']} epochs "
                                           "each, one single-threaded process per core"}
         line["rel_l1_vs_oracle"] = max(errs) if errs else None
+        if errs:
+            q = np.quantile(errs, [0.5, 0.99])
+            line["rel_l1_quantiles"] = {"p50": float(q[0]), "p99": float(q[1]), "max": max(errs),
+                                        "over_1e-5": int(sum(e > 1e-5 for e in errs))}
         line["rel_l1_sample"] = (f"max over the {len(errs)} of {t['filters']} sampled filters whose final frame "
                                  f"equals the oracle's, after {t['epochs']} epochs, same filters in a batch of "
                                  f"their own, both on their own regrid decisions; {len(flipped)} filters on a "

@@ -60,6 +60,14 @@ enum {
  *   BF16X3  : float32 grid, split BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulate.
  *   FP16X3  : float32 grid, split FP16 with power-of-two operand scaling,
  *             (hi*hi + hi*lo + lo*hi), FP32 accumulate.
+ *   BF16X6  : float32 grid, each operand split into three BF16 pieces
+ *             (hi + mid + lo carry its 24 significand bits) and six products
+ *             (hi*hi, hi*mid, mid*hi, hi*lo, lo*hi, mid*mid), FP32
+ *             accumulate: float32-class transforms from BF16 tensor cores.
+ *             n_x = 2 only (single filters, batches and the server's 2-D
+ *             filters, whose 3-D filters then run FP16X3), GEMM form of the
+ *             transforms only (its operand planes fill the shared memory
+ *             the FFT form uses as scratch).
  * Everything else of a step runs in float32 on the non-FP64 paths, with the
  * frame, the normalisation constant and the moment combination in float64.
  * For n_x = 1 every precision other than FP64 selects the float32 CUDA-core
@@ -74,7 +82,8 @@ enum {
   PMF_PREC_TF32 = 1,
   /* 2 is not assigned */
   PMF_PREC_BF16X3 = 3,
-  PMF_PREC_FP16X3 = 4
+  PMF_PREC_FP16X3 = 4,
+  PMF_PREC_BF16X6 = 5
 };
 
 /* Diffusion multiplier of the time update.
@@ -106,7 +115,8 @@ enum { PMF_REALIGN_MULTILINEAR = 0, PMF_REALIGN_SHEAR = 1 };
  *   FFT  : shared-memory FFTs of the real lines (H_k = Re Z_k - Im Z_k):
  *          n_x = 1 with N a power of two (radix 2), n_x = 2 with both axes
  *          2^a 3^b (radix 3 and 2; the regrid stays a tensor-core GEMM);
- *          non-FP64 precision; PMF_ERR_UNSUPPORTED elsewhere. */
+ *          non-FP64 precision other than BF16X6; PMF_ERR_UNSUPPORTED
+ *          elsewhere. */
 enum { PMF_TRANSFORM_AUTO = 0, PMF_TRANSFORM_GEMM = 1, PMF_TRANSFORM_FFT = 2 };
 
 /* Measurement functions h of eq. meas. */
@@ -288,8 +298,9 @@ typedef struct pmf_server pmf_server;
 
 /* hbm_budget: device bytes the server may hold for filters and their tables
  * (0 = no limit); max_filters: size of the id space (ids 0..max_filters-1);
- * precision: PMF_PREC_FP16X3, _BF16X3 or _TF32 for the 2-D and 3-D filters
- * (1-D filters use the float32 kernel).  PMF_ERR_ARG on bad arguments,
+ * precision: PMF_PREC_FP16X3, _BF16X3, _BF16X6 or _TF32 for the 2-D and
+ * 3-D filters (1-D filters use the float32 kernel; with BF16X6 the 3-D
+ * filters run FP16X3, the other split format within 1e-5).  PMF_ERR_ARG on bad arguments,
  * PMF_ERR_OOM / PMF_ERR_CUDA if the server's own buffers cannot be made. */
 int pmf_server_create(pmf_server** out, size_t hbm_budget, int max_filters, int precision);
 

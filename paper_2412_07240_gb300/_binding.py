@@ -19,7 +19,7 @@ MAX_NZ = 3
 MEAS_NPARAM = 24
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_DEGENERATE, ERR_TIMEOUT, ERR_ADMISSION, ERR_UNSUPPORTED = range(8)
-PREC = {"fp64": 0, "tf32": 1, "bf16x3": 3, "fp16x3": 4}
+PREC = {"fp64": 0, "tf32": 1, "bf16x3": 3, "fp16x3": 4, "bf16x6": 5}
 PSI = {"euler": 0, "exact": 1}
 REALIGN = {"multilinear": 0, "shear": 1}
 TRANSFORM = {"auto": 0, "gemm": 1, "fft": 2}

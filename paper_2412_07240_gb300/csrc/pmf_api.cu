@@ -159,7 +159,8 @@ int pmf_create(pmf_ctx** out, const pmf_config* cfg, void* cuda_stream) {
   const long long P = ctx->dims.P;
 
   if (cfg->transform == PMF_TRANSFORM_FFT &&
-      (cfg->precision == PMF_PREC_FP64 || (cfg->nx != 1 && !(cfg->nx == 2 && tc2_fft_ok(cfg->N[0], cfg->N[1]))))) {
+      (cfg->precision == PMF_PREC_FP64 ||
+       (cfg->nx != 1 && !(cfg->nx == 2 && tc2_fft_ok(cfg->N[0], cfg->N[1], cfg->precision))))) {
     free_ctx(ctx);
     return PMF_ERR_UNSUPPORTED;   // the FFT form: 1-D kernel, fused 2-D kernel with axes 2^a 3^b
   }
@@ -486,14 +487,14 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
     int rc = validate_config(&cfgs[i], &why);
     if (rc) return rc;
     if (cfgs[i].nx != 2 || cfgs[i].precision != prec ||
-        (cfgs[i].transform == PMF_TRANSFORM_FFT && !tc2_fft_ok(cfgs[i].N[0], cfgs[i].N[1])))
+        (cfgs[i].transform == PMF_TRANSFORM_FFT && !tc2_fft_ok(cfgs[i].N[0], cfgs[i].N[1], cfgs[i].precision)))
       return PMF_ERR_UNSUPPORTED;
     rc = tc_supported(&cfgs[i], &why);
     if (rc) return rc;
     rc = meas_params(2, &models[i], &mps[i], &why);
     if (rc) return rc;
     forms[i] = tc2_form(&cfgs[i], (cudaStream_t)cuda_stream);
-    const int cls = tc_class_form(cfgs[i].N[0], cfgs[i].N[1], forms[i]);
+    const int cls = tc_class_form(cfgs[i].N[0], cfgs[i].N[1], forms[i], prec);
     for (int a = 0; a < 2; ++a) {
       const int key = cfgs[i].N[a] * 1000 + cls;
       if (std::find(sizes.begin(), sizes.end(), key) == sizes.end()) sizes.push_back(key);
@@ -577,7 +578,7 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
     sl.buf0 = b->d_w + off;
     sl.buf1 = b->d_w + off + P;
     off += 2 * P;
-    const int cls = tc_class_form(c.N[0], c.N[1], forms[i]);
+    const int cls = tc_class_form(c.N[0], c.N[1], forms[i], c.precision);
     b->cls[i] = cls;
     for (int a = 0; a < 2; ++a) {
       const size_t s = std::find(sizes.begin(), sizes.end(), c.N[a] * 1000 + cls) - sizes.begin();

@@ -145,7 +145,7 @@ int validate_config(const pmf_config* c, std::string* why) {
     if (c->Q[i * n + i] < 0) { *why = "Q is not positive semidefinite"; return PMF_ERR_ARG; }
   if (!chol(n, c->P0, L)) { *why = "P0 is not positive definite"; return PMF_ERR_ARG; }
   if (!(c->span_sigma > 0) || !(c->dt_sub > 0) || !(c->realign_rho > 0)) { *why = "span, dt_sub, rho must be > 0"; return PMF_ERR_ARG; }
-  if (c->precision < PMF_PREC_FP64 || c->precision > PMF_PREC_FP16X3 || c->precision == 2) {
+  if (c->precision < PMF_PREC_FP64 || c->precision > PMF_PREC_BF16X6 || c->precision == 2) {
     *why = "unknown precision";
     return PMF_ERR_ARG;
   }

@@ -190,10 +190,19 @@ int sync_all(pmf_server* s) {
   return PMF_OK;
 }
 
+// Precision of a filter of n axes in the server: 1-D filters run the float32
+// kernel (its table has no precision); 3-D filters of a BF16X6 server run
+// FP16X3, the other split format within 1e-5 (the 3-D pipelines hold two
+// operand planes).
+int filter_precision(const pmf_server* s, int n) {
+  return n == 1 || (n == 3 && s->precision == PMF_PREC_BF16X6) ? PMF_PREC_FP16X3 : s->precision;
+}
+
 // Shared device table of an axis size: kind 1 = 1-D kernel table, 2 = split
 // Hartley planes + sinc table of the tensor-core kernels (size class 128),
 // 3 and 4 = the same for the size-64 and size-96 classes of the batched 2-D
-// kernels.  Adds new bytes to *add.
+// kernels, 5 = the class-128 table in FP16X3 for the 3-D filters of a BF16X6
+// server.  Adds new bytes to *add.
 int table_for(pmf_server* s, int kind, int N, void** out, size_t* hb, long long* add, bool create) {
   const long long key = (long long)kind * 100000 + N;
   auto it = s->tables.find(key);
@@ -203,13 +212,13 @@ int table_for(pmf_server* s, int kind, int N, void** out, size_t* hb, long long*
     return PMF_OK;
   }
   const int cls = kind == 3 ? 64 : kind == 4 ? 96 : 128;
-  const long long nb =
-      kind == 1 ? (long long)tc1_table_bytes(N) : (long long)tc_axis_table_bytes(N, s->precision, cls);
+  const int prec = kind == 5 ? PMF_PREC_FP16X3 : s->precision;
+  const long long nb = kind == 1 ? (long long)tc1_table_bytes(N) : (long long)tc_axis_table_bytes(N, prec, cls);
   *add += nb;
   if (!create) return PMF_OK;
   void* t = nullptr;
   size_t h = 0;
-  const int rc = kind == 1 ? tc1_build_table(N, &t) : tc_build_axis_table(N, s->precision, &t, &h, cls);
+  const int rc = kind == 1 ? tc1_build_table(N, &t) : tc_build_axis_table(N, prec, &t, &h, cls);
   if (rc) {
     cudaFree(t);
     return rc;
@@ -347,7 +356,7 @@ int launch_batch(pmf_server* s, const double* z, const double* taus) {
       t3.push_back(Tc3Item{f.tc3, d, &f.tct, (it.flags & 1) ? &mp : nullptr, (it.flags & 2) ? &tc3[i] : nullptr,
                            f.st, f.buf, f.buf + f.P});
     }
-    const int r = tc3_batch(t3.data(), (int)t3.size(), s->precision, &b.stage3, s->s[2]);
+    const int r = tc3_batch(t3.data(), (int)t3.size(), filter_precision(s, 3), &b.stage3, s->s[2]);
     if (r < 0) return sfail(s, -r, "3-D batch");
     s->launches += r;
     cudaEventRecord(b.ev[2], s->s[2]);
@@ -396,7 +405,8 @@ extern "C" {
 
 int pmf_server_create(pmf_server** out, size_t hbm_budget, int max_filters, int precision) {
   if (!out || max_filters < 1 || max_filters > (1 << 24)) return PMF_ERR_ARG;
-  if (precision != PMF_PREC_FP16X3 && precision != PMF_PREC_BF16X3 && precision != PMF_PREC_TF32)
+  if (precision != PMF_PREC_FP16X3 && precision != PMF_PREC_BF16X3 && precision != PMF_PREC_BF16X6 &&
+      precision != PMF_PREC_TF32)
     return PMF_ERR_ARG;
   *out = nullptr;
   pmf_server* s = new (std::nothrow) pmf_server();
@@ -446,7 +456,7 @@ int pmf_server_admit(pmf_server* s, const pmf_config* cfg, const pmf_meas* model
     rc = tc1_supported(cfg, &why);
   } else {
     pmf_config c2 = *cfg;
-    c2.precision = s->precision;
+    c2.precision = filter_precision(s, n);
     rc = tc_supported(&c2, &why);
   }
   if (rc) return sfail(s, rc, why);
@@ -468,8 +478,8 @@ int pmf_server_admit(pmf_server* s, const pmf_config* cfg, const pmf_meas* model
     fc.precision = s->precision;
     form2 = tc2_form(&fc, s->s[0]);
   }
-  const int cls = n == 2 ? tc_class_form(cfg->N[0], cfg->N[1], form2) : 128;
-  const int tkind = n == 1 ? 1 : (cls == 64 ? 3 : cls == 96 ? 4 : 2);
+  const int cls = n == 2 ? tc_class_form(cfg->N[0], cfg->N[1], form2, s->precision) : 128;
+  const int tkind = n == 1 ? 1 : (cls == 64 ? 3 : cls == 96 ? 4 : filter_precision(s, n) != s->precision ? 5 : 2);
   long long tbytes = 0;
   void* tab = nullptr;
   for (int a = 0; a < n; ++a) {
@@ -484,7 +494,7 @@ int pmf_server_admit(pmf_server* s, const pmf_config* cfg, const pmf_meas* model
   SFilter& f = s->f[id];
   f = SFilter{};
   f.cfg = *cfg;
-  f.cfg.precision = n == 1 ? PMF_PREC_FP16X3 : s->precision;
+  f.cfg.precision = filter_precision(s, n);
   f.cls = cls;
   f.mp = mp;
   f.P = P;
@@ -505,7 +515,7 @@ int pmf_server_admit(pmf_server* s, const pmf_config* cfg, const pmf_meas* model
   }
   f.bytes = bytes;
   s->bytes += bytes;
-  f.tct.prec = s->precision;
+  f.tct.prec = f.cfg.precision;
   for (int a = 0; a < n && n > 1; ++a) {
     f.tct.hart[a] = tabs[a];
     f.tct.hart_bytes[a] = hb[a];

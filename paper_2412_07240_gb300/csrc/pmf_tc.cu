@@ -38,6 +38,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "pmf_device.cuh"
@@ -64,21 +65,25 @@ constexpr uint32_t kTmemCols = 128;
 //            before the first matrix is built, the spectrum is written there
 //            after the forward transforms and H0 is copied in again for the
 //            inverse; two CTAs per SM.
+// BF16X6 keeps three planes per operand: class 128 aliases the staging tile
+// on W as class 96 does (192 KiB of planes), and classes 96 and 64 fit one
+// and two CTAs per SM.
 template <int P, int C>
 struct Smem {
   static constexpr int threads = C == 128 ? 512 : 256;
   static constexpr int sstr = C + 4;
-  static constexpr bool alias = C == 96;
+  static constexpr bool alias = C == 96 || (C == 128 && Fmt<P>::planes == 3);
   static constexpr int offA = 0;
   static constexpr int offW = Fmt<P>::planes * Lay<P, C>::plane;
   static constexpr int wbytes = Fmt<P>::planes * Lay<P, C>::wplane;
   static constexpr int sbytes = C * sstr * 4;
   static constexpr int offS = alias ? offW : offW + wbytes;
   static constexpr int bytes = alias ? offW + (wbytes > sbytes ? wbytes : sbytes) : offS + sbytes;
+  // CTAs per SM the shared memory allows (the launch bound of the planned kernel)
+  static constexpr int ctas = C == 128 ? 1 : C == 96 ? (Fmt<P>::planes == 3 ? 1 : 2) : (Fmt<P>::planes == 3 ? 2 : 3);
 };
 constexpr int kThreads = 512;                // the single-filter kernel (class 128)
-constexpr int kSmemBytes = Smem<PMF_PREC_FP16X3, 128>::bytes;
-static_assert(Smem<PMF_PREC_TF32, 128>::bytes == kSmemBytes, "one dynamic size for every class-128 format");
+static_assert(Smem<PMF_PREC_BF16X6, 128>::bytes <= 200 * 1024, "class-128 BF16X6 planes and static state fit");
 
 // One filter launched alone: everything by value in the kernel parameters.
 struct FusedJob {
@@ -635,12 +640,13 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       }
     }
     __syncthreads();
-    // exponents into the (still free) W region while the weights arrive
+    // exponents into the (still free) W region while the weights arrive (the
+    // A region when the weights are staged in W)
     const MeasK mk = meas_k(sh);
     // t = r q1 + c/4 < 2^12: (t + 1/2) / q1 is at least 1/(2 q1) from an
     // integer, so the float product truncates to r exactly
     const float rq1 = 1.0f / (float)q1;
-    float4* E = (float4*)W;
+    float4* E = (float4*)(kAlias ? A : W);
     float emin = INFINITY;
     for (int t = tid; t < np4; t += kThreads) {
       const int r = (int)(((float)t + 0.5f) * rq1), c = (t - r * q1) * 4;
@@ -1289,7 +1295,7 @@ __global__ void __launch_bounds__(kFrontThreads, 6) k_front2d(const FilterSlot* 
 // Planned transform kernel of a batched epoch (size class C): the time update
 // of the filters whose front kernel ran it, from the weights and plan it left.
 template <int P, int C>
-__global__ void __launch_bounds__(Smem<P, C>::threads, C == 128 ? 1 : (C == 96 ? 2 : 3))
+__global__ void __launch_bounds__(Smem<P, C>::threads, Smem<P, C>::ctas)
     k_fused2d_planned(const FilterSlot* __restrict__ slots, const StepItem* __restrict__ items,
                       const TimeConsts* __restrict__ tcs) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -1299,21 +1305,6 @@ __global__ void __launch_bounds__(Smem<P, C>::threads, C == 128 ? 1 : (C == 96 ?
                     sl.N0, sl.N1, 0, (it.flags >> 1) & 1, sl.mp, it.z,
                     tcs ? tcs + blockIdx.x : sl.tc, (const BatchPlan*)sl.plan, sl.fft};
   fused2d<P, false, true, C>(v, smem);
-}
-
-// Many filters, one CTA each: items[blockIdx.x] names the filter slot, the
-// parts of the epoch to run and its measurement.
-template <int P>
-__global__ void __launch_bounds__(kThreads, 1) k_fused2d_batch(const FilterSlot* __restrict__ slots,
-                                                               const StepItem* __restrict__ items,
-                                                               const TimeConsts* __restrict__ tcs) {
-  extern __shared__ __align__(1024) uint8_t smem[];
-  const StepItem& it = items[blockIdx.x];
-  const FilterSlot& sl = slots[it.slot];
-  const FusedView v{sl.st, sl.buf0, sl.buf1, {sl.hart[0], sl.hart[1]}, {sl.sctab[0], sl.sctab[1]},
-                    sl.N0, sl.N1, it.flags & 1, (it.flags >> 1) & 1, sl.mp, it.z,
-                    tcs ? tcs + blockIdx.x : sl.tc};
-  fused2d<P, false>(v, smem);
 }
 
 // Moments and status words of the listed filters (read before any is cleared:
@@ -1356,13 +1347,39 @@ __global__ void k_prior_f32(Dims d, const DevState* st, const double* aux, float
   }
 }
 
+// Host: f(std::integral_constant<int, P>) for the tensor-core format P of a precision.
+template <class F>
+void with_format(int precision, F&& f) {
+  switch (precision) {
+    case PMF_PREC_FP16X3: f(std::integral_constant<int, PMF_PREC_FP16X3>{}); break;
+    case PMF_PREC_BF16X3: f(std::integral_constant<int, PMF_PREC_BF16X3>{}); break;
+    case PMF_PREC_BF16X6: f(std::integral_constant<int, PMF_PREC_BF16X6>{}); break;
+    default: f(std::integral_constant<int, PMF_PREC_TF32>{}); break;
+  }
+}
+
+void launch_fused(int precision, const FusedJob& job, cudaStream_t s) {
+  with_format(precision, [&](auto fmt) {
+    constexpr int P = decltype(fmt)::value;
+    k_fused2d<P><<<1, kThreads, Smem<P, 128>::bytes, s>>>(job);
+  });
+}
+
+template <int P>
+void set_smem_limits() {
+  cudaFuncSetAttribute(k_fused2d<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<P, 128>::bytes);
+  cudaFuncSetAttribute(k_fused2d_planned<P, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<P, 128>::bytes);
+  cudaFuncSetAttribute(k_fused2d_planned<P, 96>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<P, 96>::bytes);
+  cudaFuncSetAttribute(k_fused2d_planned<P, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<P, 64>::bytes);
+}
+
 // Host: split 16-bit (or float32) planes of a matrix in the operand layout.
 void split_planes(const std::vector<double>& Mt, int rows, int cols, int prec, double scale,
                   std::vector<uint8_t>& out, int cls) {
   const int esz = prec == PMF_PREC_TF32 ? 4 : 2;
   const int epc = 16 / esz, rowblk = (cls / epc) * 128;
   const size_t plane = (size_t)rows / 8 * rowblk;
-  const int np = prec == PMF_PREC_TF32 ? 1 : 2;
+  const int np = prec == PMF_PREC_TF32 ? 1 : prec == PMF_PREC_BF16X6 ? 3 : 2;
   out.assign(plane * np, 0);
   for (int r = 0; r < rows; ++r)
     for (int c = 0; c < cols; ++c) {
@@ -1371,11 +1388,15 @@ void split_planes(const std::vector<double>& Mt, int rows, int cols, int prec, d
       if (prec == PMF_PREC_TF32) {
         float f = (float)x;
         std::memcpy(&out[off], &f, 4);
-      } else if (prec == PMF_PREC_BF16X3) {
-        __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
-        __nv_bfloat16 lo = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
-        std::memcpy(&out[off], &hi, 2);
-        std::memcpy(&out[plane + off], &lo, 2);
+      } else if (prec == PMF_PREC_BF16X3 || prec == PMF_PREC_BF16X6) {
+        // pieces of the float64 value: hi, then the remainders
+        __nv_bfloat16 pc[3];
+        double r = x;
+        for (int i = 0; i < np; ++i) {
+          pc[i] = __float2bfloat16_rn((float)r);
+          r -= (double)__bfloat162float(pc[i]);
+          std::memcpy(&out[i * plane + off], &pc[i], 2);
+        }
       } else {
         __half hi = __float2half_rn((float)x);
         __half lo = __float2half_rn((float)(x - (double)__half2float(hi)));
@@ -1398,8 +1419,8 @@ int tc_supported(const pmf_config* cfg, std::string* why) {
       return PMF_ERR_UNSUPPORTED;
     }
   if (cfg->precision != PMF_PREC_FP16X3 && cfg->precision != PMF_PREC_BF16X3 &&
-      cfg->precision != PMF_PREC_TF32) {
-    *why = "the fused tensor-core kernel supports FP16X3, BF16X3 and TF32";
+      cfg->precision != PMF_PREC_TF32 && !(cfg->precision == PMF_PREC_BF16X6 && cfg->nx == 2)) {
+    *why = "the tensor-core kernels support FP16X3, BF16X3 and TF32 (and BF16X6 for n_x = 2)";
     return PMF_ERR_UNSUPPORTED;
   }
   return PMF_OK;
@@ -1432,30 +1453,8 @@ int tc_build_axis_table(int N, int precision, void** dev, size_t* hart_bytes, in
     return PMF_ERR_CUDA;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_fused2d<PMF_PREC_FP16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    cudaFuncSetAttribute(k_fused2d<PMF_PREC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    cudaFuncSetAttribute(k_fused2d<PMF_PREC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    cudaFuncSetAttribute(k_fused2d_batch<PMF_PREC_FP16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    cudaFuncSetAttribute(k_fused2d_batch<PMF_PREC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    cudaFuncSetAttribute(k_fused2d_batch<PMF_PREC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_FP16X3, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         Smem<PMF_PREC_FP16X3, 128>::bytes);
-    cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_BF16X3, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         Smem<PMF_PREC_BF16X3, 128>::bytes);
-    cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_TF32, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         Smem<PMF_PREC_TF32, 128>::bytes);
-    cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_FP16X3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         Smem<PMF_PREC_FP16X3, 64>::bytes);
-    cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_FP16X3, 96>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         Smem<PMF_PREC_FP16X3, 96>::bytes);
-    cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_BF16X3, 96>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         Smem<PMF_PREC_BF16X3, 96>::bytes);
-    cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_TF32, 96>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         Smem<PMF_PREC_TF32, 96>::bytes);
-    cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_BF16X3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         Smem<PMF_PREC_BF16X3, 64>::bytes);
-    cudaFuncSetAttribute(k_fused2d_planned<PMF_PREC_TF32, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         Smem<PMF_PREC_TF32, 64>::bytes);
+    for (int p : {PMF_PREC_FP16X3, PMF_PREC_BF16X3, PMF_PREC_BF16X6, PMF_PREC_TF32})
+      with_format(p, [](auto fmt) { set_smem_limits<decltype(fmt)::value>(); });
     attr = true;
   }
   return PMF_OK;
@@ -1463,7 +1462,8 @@ int tc_build_axis_table(int N, int precision, void** dev, size_t* hart_bytes, in
 
 size_t tc_axis_table_bytes(int N, int precision, int cls) {
   const size_t plane = (size_t)N / 8 * (precision == PMF_PREC_TF32 ? 32 : 16) * cls;
-  return plane * (precision == PMF_PREC_TF32 ? 1 : 2) + 2 * (2 * N + 1) * sizeof(float);
+  const int np = precision == PMF_PREC_TF32 ? 1 : precision == PMF_PREC_BF16X6 ? 3 : 2;
+  return plane * np + 2 * (2 * N + 1) * sizeof(float);
 }
 
 int tc_build_tables(const pmf_config* cfg, TcTables* t, std::string* why) {
@@ -1541,24 +1541,7 @@ int tc_step(const Dims& d, const pmf_config& cfg, const TcTables* t, const MeasP
   if (mp) job.mp = *mp;
   if (tcs) job.tc = *tcs;
   if (!job.do_meas && !job.do_time) return 0;
-  if (cfg.precision == PMF_PREC_FP16X3)
-    k_fused2d<PMF_PREC_FP16X3><<<1, kThreads, kSmemBytes, s>>>(job);
-  else if (cfg.precision == PMF_PREC_BF16X3)
-    k_fused2d<PMF_PREC_BF16X3><<<1, kThreads, kSmemBytes, s>>>(job);
-  else
-    k_fused2d<PMF_PREC_TF32><<<1, kThreads, kSmemBytes, s>>>(job);
-  return 1;
-}
-
-int tc_batch_step(int precision, const FilterSlot* slots, const StepItem* items, int k, cudaStream_t s,
-                  const TimeConsts* tcs) {
-  if (k <= 0) return 0;
-  if (precision == PMF_PREC_FP16X3)
-    k_fused2d_batch<PMF_PREC_FP16X3><<<k, kThreads, kSmemBytes, s>>>(slots, items, tcs);
-  else if (precision == PMF_PREC_BF16X3)
-    k_fused2d_batch<PMF_PREC_BF16X3><<<k, kThreads, kSmemBytes, s>>>(slots, items, tcs);
-  else
-    k_fused2d_batch<PMF_PREC_TF32><<<k, kThreads, kSmemBytes, s>>>(slots, items, tcs);
+  launch_fused(cfg.precision, job, s);
   return 1;
 }
 
@@ -1590,12 +1573,7 @@ int tc_batch_epoch(int precision, const FilterSlot* slots, const StepItem* items
     cudaStreamWaitEvent(s2, ev_fork, 0);
   }
   cudaStream_t t = fork ? s2 : s;
-  if (precision == PMF_PREC_FP16X3)
-    launch_planned<PMF_PREC_FP16X3>(slots, items, k, k128, k96, s, tcs, t);
-  else if (precision == PMF_PREC_BF16X3)
-    launch_planned<PMF_PREC_BF16X3>(slots, items, k, k128, k96, s, tcs, t);
-  else
-    launch_planned<PMF_PREC_TF32>(slots, items, k, k128, k96, s, tcs, t);
+  with_format(precision, [&](auto fmt) { launch_planned<decltype(fmt)::value>(slots, items, k, k128, k96, s, tcs, t); });
   if (fork) {
     cudaEventRecord(ev_join, s2);
     cudaStreamWaitEvent(s, ev_join, 0);
@@ -1604,7 +1582,8 @@ int tc_batch_epoch(int precision, const FilterSlot* slots, const StepItem* items
 }
 
 // ---- form of the 2-D Hartley transforms: tensor-core GEMM or shared-memory FFT
-bool tc2_fft_ok(int N0, int N1) {
+bool tc2_fft_ok(int N0, int N1, int precision) {
+  if (precision == PMF_PREC_BF16X6) return false;
   auto ok = [](int N) {
     while (N % 3 == 0) N /= 3;
     return N >= 2 && (N & (N - 1)) == 0;
@@ -1718,14 +1697,7 @@ double time_form2(int N0, int N1, int prec, int fft, cudaStream_t s) {
     job.do_meas = 1;
     job.do_time = 1;
     job.fft = fft;
-    auto launch = [&]() {
-      if (prec == PMF_PREC_FP16X3)
-        k_fused2d<PMF_PREC_FP16X3><<<1, kThreads, kSmemBytes, s>>>(job);
-      else if (prec == PMF_PREC_BF16X3)
-        k_fused2d<PMF_PREC_BF16X3><<<1, kThreads, kSmemBytes, s>>>(job);
-      else
-        k_fused2d<PMF_PREC_TF32><<<1, kThreads, kSmemBytes, s>>>(job);
-    };
+    auto launch = [&]() { launch_fused(prec, job, s); };
     constexpr int kReps = 20;
     float ms = 0.0f;
     // every epoch starts from the same state and weights
@@ -1750,7 +1722,8 @@ double time_form2(int N0, int N1, int prec, int fft, cudaStream_t s) {
 }  // namespace
 
 int tc2_form(const pmf_config* cfg, cudaStream_t s) {
-  if (cfg->nx != 2 || !tc2_fft_ok(cfg->N[0], cfg->N[1]) || cfg->transform == PMF_TRANSFORM_GEMM) return 0;
+  if (cfg->nx != 2 || !tc2_fft_ok(cfg->N[0], cfg->N[1], cfg->precision) || cfg->transform == PMF_TRANSFORM_GEMM)
+    return 0;
   if (cfg->transform == PMF_TRANSFORM_FFT) return 1;
   if (const char* form = std::getenv("PMF_2D_FORM")) {   // explicit choice, no tuning
     if (!std::strcmp(form, "fft")) return 1;

@@ -58,11 +58,12 @@ int tc_build_tables(const pmf_config* cfg, TcTables* t, std::string* why);
 int tc_build_axis_table(int N, int precision, void** dev, size_t* hart_bytes, int cls = 128);
 size_t tc_axis_table_bytes(int N, int precision, int cls = 128);
 // Form of the Hartley transforms of a 2-D filter: 0 the tensor-core GEMMs,
-// 1 the shared-memory FFT (axis sizes 2^a 3^b only).  TRANSFORM_AUTO times
+// 1 the shared-memory FFT (axis sizes 2^a 3^b, not with BF16X6, whose
+// operand planes fill the scratch the FFT form needs).  TRANSFORM_AUTO times
 // both on a scratch filter the first time a (N0, N1, precision) is used and
 // caches the choice in autotune_2d.json beside the library (the environment
 // variable PMF_2D_FORM=fft|gemm overrides it).
-bool tc2_fft_ok(int N0, int N1);
+bool tc2_fft_ok(int N0, int N1, int precision);
 int tc2_form(const pmf_config* cfg, cudaStream_t s);
 // Size class of a 2-D filter in batched epochs: the largest axis rounded up
 // to 64, 96 or 128.
@@ -70,12 +71,15 @@ inline int tc_class(int N0, int N1) {
   const int m = N0 > N1 ? N0 : N1;
   return m <= 64 ? 64 : m <= 96 ? 96 : 128;
 }
-// ... for a filter in the given transform form: the size-96 class keeps its
-// staging tile in the W region, which the FFT form needs as scratch, so an
-// FFT-form filter of that class runs in the size-128 class.
-inline int tc_class_form(int N0, int N1, int fft) {
+// ... for a filter in the given transform form and precision: the size-96
+// class keeps its staging tile in the W region, which the FFT form needs as
+// scratch, so an FFT-form filter of that class runs in the size-128 class;
+// so does a BF16X6 filter of that class (three operand planes leave one CTA
+// per SM in either class, and the 512-thread class-128 kernel shortens the
+// filter's chain).
+inline int tc_class_form(int N0, int N1, int fft, int precision) {
   const int c = tc_class(N0, N1);
-  return fft && c == 96 ? 128 : c;
+  return (fft || precision == PMF_PREC_BF16X6) && c == 96 ? 128 : c;
 }
 // Device bytes of one filter's plan (the front kernel's results of an epoch).
 size_t tc_plan_bytes();
@@ -125,15 +129,12 @@ void tc3_stage_free(Tc3Stage* g);
 // launches, or minus a PMF_ERR_* code.
 int tc3_batch(const Tc3Item* items, int n, int precision, Tc3Stage* g, cudaStream_t s);
 
-// One launch, one CTA per item (items in device memory); tcs (if not null)
-// holds each item's time-update constants in place of the slot's; returns launches.
-int tc_batch_step(int precision, const FilterSlot* slots, const StepItem* items, int k, cudaStream_t s,
-                  const TimeConsts* tcs = nullptr);
 // A batched epoch as a front kernel over all k items, then the planned
 // transform kernels: items [0, k128) of size class 128, [k128, k128 + k96) of
 // class 96, the rest of class 64 (the last two on stream s2 when it is given,
 // joined back into s through the events, so the classes share the SMs).  tcs
-// as for tc_batch_step.  Returns the number of launches.
+// (if not null, in device memory) holds each item's time-update constants in
+// place of the slot's.  Returns the number of launches.
 int tc_batch_epoch(int precision, const FilterSlot* slots, const StepItem* items, int k, int k128, int k96,
                    cudaStream_t s, const TimeConsts* tcs = nullptr, cudaStream_t s2 = nullptr,
                    cudaEvent_t ev_fork = nullptr, cudaEvent_t ev_join = nullptr);

@@ -163,6 +163,10 @@ template <>
 struct Fmt<PMF_PREC_TF32> {
   static constexpr int esz = 4, rowblk = 4096, planes = 1, kper = 8, code = 2;
 };
+template <>
+struct Fmt<PMF_PREC_BF16X6> {
+  static constexpr int esz = 2, rowblk = 2048, planes = 3, kper = 16, code = 1;
+};
 
 // Operand tiles of a size class C (the largest axis they hold, 64 or 128):
 // an 8-row block covers C elements along K, so a 128-row plane takes
@@ -184,7 +188,9 @@ __device__ __forceinline__ uint32_t h2u(__half2 h) { return *(uint32_t*)&h; }
 __device__ __forceinline__ uint32_t b2u(__nv_bfloat162 h) { return *(uint32_t*)&h; }
 
 // Elements (r, c..c+3) (c a multiple of 4) of the operand planes at base, scaled
-// by s: split into hi + lo 16-bit planes, or one float32 plane for TF32.
+// by s: split into hi + lo 16-bit planes, hi + mid + lo BF16 planes (BF16X6:
+// x - hi and x - hi - mid are exact in float32, so the three pieces keep all
+// 24 significand bits), or one float32 plane for TF32.
 template <int P, int C = 128, bool kW = false>
 __device__ __forceinline__ void store4(uint8_t* base, int r, int c, float4 v, float s) {
   constexpr int kPl = kW ? Lay<P, C>::wplane : Lay<P, C>::plane;
@@ -204,10 +210,17 @@ __device__ __forceinline__ void store4(uint8_t* base, int r, int c, float4 v, fl
   } else {
     const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y), h1 = __floats2bfloat162_rn(v.z, v.w);
     const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
-    const __nv_bfloat162 l0 = __floats2bfloat162_rn(v.x - f0.x, v.y - f0.y);
-    const __nv_bfloat162 l1 = __floats2bfloat162_rn(v.z - f1.x, v.w - f1.y);
+    const float4 r = make_float4(v.x - f0.x, v.y - f0.y, v.z - f1.x, v.w - f1.y);
+    const __nv_bfloat162 l0 = __floats2bfloat162_rn(r.x, r.y);
+    const __nv_bfloat162 l1 = __floats2bfloat162_rn(r.z, r.w);
     *(uint2*)(base + off) = make_uint2(b2u(h0), b2u(h1));
     *(uint2*)(base + kPl + off) = make_uint2(b2u(l0), b2u(l1));
+    if constexpr (P == PMF_PREC_BF16X6) {
+      const float2 g0 = __bfloat1622float2(l0), g1 = __bfloat1622float2(l1);
+      const __nv_bfloat162 e0 = __floats2bfloat162_rn(r.x - g0.x, r.y - g0.y);
+      const __nv_bfloat162 e1 = __floats2bfloat162_rn(r.z - g1.x, r.w - g1.y);
+      *(uint2*)(base + 2 * kPl + off) = make_uint2(b2u(e0), b2u(e1));
+    }
   }
 }
 
@@ -296,9 +309,11 @@ struct Moments {
 };
 
 // Issue one GEMM stage (one thread): D = A * W^T, A read K-major or MN-major.
-// For the split formats the two correction products (hi*lo, lo*hi; ~2^-11 of
-// the result) are accumulated first, while the FP32 accumulator is small, and
-// the hi*hi products last, so that only those see roundings at full magnitude.
+// For the split formats the correction products are accumulated first, while
+// the FP32 accumulator is small, and the hi*hi products last, so that only
+// those see roundings at full magnitude: hi*lo, lo*hi (~2^-11 of the result)
+// for the two-piece formats; for BF16X6 (pieces hi, mid, lo of ~2^0, 2^-9,
+// 2^-18) hi*lo, lo*hi and mid*mid (~2^-18), then hi*mid and mid*hi (~2^-9).
 template <int P, int C = 128>
 __device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t a_base, int a_mn, uint32_t w_base,
                                             int nout, int K, uint32_t mbar) {
@@ -314,6 +329,18 @@ __device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t a_base, int 
   if constexpr (Fmt<P>::planes == 1) {
     for (int ks = 0; ks < K / kp; ++ks)
       mma_tf32(tmem, adesc(a_base, ks), sdesc(w_base + ks * 256, 128, rb), id, ks > 0);
+  } else if constexpr (Fmt<P>::planes == 3) {
+    for (int ks = 0; ks < K / kp; ++ks) {
+      mma_f16(tmem, adesc(a_base, ks), sdesc(w_base + 2 * kWPl + ks * 256, 128, rb), id, ks > 0);
+      mma_f16(tmem, adesc(a_base + 2 * kPl, ks), sdesc(w_base + ks * 256, 128, rb), id, 1);
+      mma_f16(tmem, adesc(a_base + kPl, ks), sdesc(w_base + kWPl + ks * 256, 128, rb), id, 1);
+    }
+    for (int ks = 0; ks < K / kp; ++ks) {
+      mma_f16(tmem, adesc(a_base, ks), sdesc(w_base + kWPl + ks * 256, 128, rb), id, 1);
+      mma_f16(tmem, adesc(a_base + kPl, ks), sdesc(w_base + ks * 256, 128, rb), id, 1);
+    }
+    for (int ks = 0; ks < K / kp; ++ks)
+      mma_f16(tmem, adesc(a_base, ks), sdesc(w_base + ks * 256, 128, rb), id, 1);
   } else {
     for (int ks = 0; ks < K / kp; ++ks) {
       mma_f16(tmem, adesc(a_base, ks), sdesc(w_base + kWPl + ks * 256, 128, rb), id, ks > 0);

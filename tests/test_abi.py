@@ -110,3 +110,28 @@ def test_unassigned_precision_rejected_without_gpu():
     h = ctypes.c_void_p()
     assert lib.pmf_create(ctypes.byref(h), ctypes.byref(c), None) == _binding.ERR_ARG
     assert "tf32x3" not in _binding.PREC
+
+
+def test_bf16x6_scope_without_gpu():
+    """BF16X6 (three BF16 pieces, six products) is a 2-D format: a 3-D filter
+    and the FFT form are refused before any device work; code 6 is unknown."""
+    from paper_2412_07240_gb300 import _binding
+    lib = _binding.load()
+    assert _binding.PREC["bf16x6"] == 5
+    c = _binding.PmfConfig()
+    lib.pmf_config_defaults(ctypes.byref(c))
+    c.nx = 3
+    c.N[0], c.N[1], c.N[2] = 32, 32, 32
+    c.P0[0] = c.P0[4] = c.P0[8] = 1.0
+    c.precision = 5
+    h = ctypes.c_void_p()
+    assert lib.pmf_create(ctypes.byref(h), ctypes.byref(c), None) == _binding.ERR_UNSUPPORTED
+    c.nx = 2
+    c.N[2] = 0
+    c.P0[:] = [0.0] * len(c.P0)
+    c.P0[0] = c.P0[3] = 1.0
+    c.transform = 2                              # PMF_TRANSFORM_FFT
+    assert lib.pmf_create(ctypes.byref(h), ctypes.byref(c), None) == _binding.ERR_UNSUPPORTED
+    c.transform = 0
+    c.precision = 6
+    assert lib.pmf_create(ctypes.byref(h), ctypes.byref(c), None) == _binding.ERR_ARG

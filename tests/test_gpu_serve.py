@@ -70,6 +70,33 @@ def test_server_matches_single_filter_api():
     s.close()
 
 
+def test_bf16x6_server_formats():
+    """A BF16X6 server: its 2-D filters run the six-product BF16 split (equal
+    to the single-filter API in that format to float32 rounding), its 3-D
+    filters FP16X3 (equal to the single-filter API in FP16X3 bit for bit) and
+    its 1-D filters the float32 kernel."""
+    from paper_2412_07240_gb300 import Filter, Server
+    wl = _small_workload(seed=8)
+    s = Server(max_filters=len(wl.cfgs), precision="bf16x6")
+    fid = {i: s.admit(wl.cfgs[i], wl.meas[i]) for i in range(len(wl.cfgs))}
+    s.replay(wl.t_arrival, [fid[i] for i in wl.ids], wl.z, wl.taus)
+    for nx, prec in ((1, "fp16x3"), (2, "bf16x6"), (3, "fp16x3")):
+        f = next(i for i, c in enumerate(wl.cfgs) if c.nx == nx and (wl.ids == i).sum() > 2)
+        sel = np.nonzero(wl.ids == f)[0]
+        g = Filter(wl.cfgs[f], precision=prec)
+        for r in sel:
+            g.step(wl.meas[f], wl.z[r, :nx], wl.taus[r])
+        P1, c1, M1 = g.pdf()
+        P2, c2, M2 = s.pdf(fid[f])
+        if nx == 2:
+            assert rel_l1(P2, P1) <= 1e-6, (nx, rel_l1(P2, P1))
+        else:
+            assert np.array_equal(P2, P1), (nx, rel_l1(P2, P1))
+        assert np.array_equal(c2, c1) and np.array_equal(M2, M1), nx
+        g.close()
+    s.close()
+
+
 def test_server_against_oracle():
     from oracle.filter import OracleFilter
     wl = _small_workload(seed=9, duration=0.1)

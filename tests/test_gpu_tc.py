@@ -2,6 +2,7 @@
 
 Bars (relative L1 of the weights after every update, and moments):
   FP16X3  <= 1e-5   (the mixed-precision target)
+  BF16X6  <= 1e-5   (three BF16 pieces, six products: the BF16 split at the target)
   BF16X3  <= 1e-4   (reported; the 2-term bf16 split keeps ~16 bits)
   TF32    <= 3e-2   (reported; single TF32 products keep ~11 bits)
 Cases: ragged non-square grids (48 x 32, 64 x 112), the full 128 x 128 range
@@ -17,7 +18,7 @@ from workloads import FilterConfig, MeasModel, Scenario, simulate
 
 pytestmark = pytest.mark.gpu
 
-BARS = {"fp16x3": 1e-5, "bf16x3": 1e-4, "tf32": 3e-2}
+BARS = {"fp16x3": 1e-5, "bf16x6": 1e-5, "bf16x3": 1e-4, "tf32": 3e-2}
 
 
 def _check(worst, prec):
@@ -27,7 +28,7 @@ def _check(worst, prec):
     assert worst["mean"] <= bar and worst["cov"] <= 10 * bar, worst
 
 
-@pytest.mark.parametrize("prec", ["fp16x3", "bf16x3", "tf32"])
+@pytest.mark.parametrize("prec", ["fp16x3", "bf16x6", "bf16x3", "tf32"])
 def test_small_2d_range(prec):
     worst, log = max_errors(w.small_2d_scenario(N=(48, 32), epochs=5), precision=prec)
     print(prec, worst)
@@ -40,21 +41,31 @@ def test_ragged_2d_linear_fp16x3():
     _check(worst, "fp16x3")
 
 
-def test_c2_full_size_fp16x3():
-    worst, _ = max_errors(w.c2_scenario(epochs=6), precision="fp16x3")
+@pytest.mark.parametrize("prec", ["fp16x3", "bf16x6"])
+def test_c2_full_size(prec):
+    worst, _ = max_errors(w.c2_scenario(epochs=6), precision=prec)
+    print(prec, worst)
+    _check(worst, prec)
+
+
+def test_c2_sixty_epochs_bf16x6():
+    """The 128 x 128 range workload over 60 epochs in the BF16 split at the
+    target: the error stays at the bar over the whole run, not just per epoch."""
+    worst, _ = max_errors(w.c2_scenario(epochs=60), precision="bf16x6")
     print(worst)
-    _check(worst, "fp16x3")
+    _check(worst, "bf16x6")
 
 
-def test_realignment_fp16x3():
+@pytest.mark.parametrize("prec", ["fp16x3", "bf16x6"])
+def test_realignment(prec):
     cfg = FilterConfig(nx=2, N=(48, 64), A=np.array([[0.0, 1.0], [0.0, 0.0]]), Q=np.diag([0.01, 0.1]),
                        m0=np.array([0.0, 1.0]), P0=np.diag([0.5, 0.5]))
     meas = MeasModel("linear", R=np.array([[0.3 ** 2]]), H=np.array([[1.0, 0.0]]))
     sc = Scenario("cv", cfg, meas, dt=0.2, epochs=6)
     sc.truth, sc.z = simulate(cfg, meas, sc.dt, sc.epochs, seed=11)
-    worst, log = max_errors(sc, precision="fp16x3")
+    worst, log = max_errors(sc, precision=prec)
     assert any(s.endswith("R") for s, _ in log), "re-alignment not exercised"
-    _check(worst, "fp16x3")
+    _check(worst, prec)
 
 
 def test_exact_multiplier_fp16x3():
@@ -63,10 +74,22 @@ def test_exact_multiplier_fp16x3():
     _check(worst, "fp16x3")
 
 
-def test_fused_step_fp16x3():
-    worst, _ = max_errors(w.small_2d_scenario(N=(48, 48), epochs=5), precision="fp16x3",
+@pytest.mark.parametrize("prec", ["fp16x3", "bf16x6"])
+def test_fused_step(prec):
+    worst, _ = max_errors(w.small_2d_scenario(N=(48, 48), epochs=5), precision=prec,
                           fused_step=True)
-    _check(worst, "fp16x3")
+    _check(worst, prec)
+
+
+def test_shear_realignment_bf16x6():
+    cfg = FilterConfig(nx=2, N=(64, 112), A=np.array([[0.0, 1.0], [0.0, 0.0]]), Q=np.diag([0.01, 0.1]),
+                       m0=np.array([0.0, 1.0]), P0=np.diag([0.5, 0.5]), realign_mode="shear")
+    meas = MeasModel("linear", R=np.array([[0.3 ** 2]]), H=np.array([[1.0, 0.0]]))
+    sc = Scenario("cv", cfg, meas, dt=0.2, epochs=6)
+    sc.truth, sc.z = simulate(cfg, meas, sc.dt, sc.epochs, seed=11)
+    worst, log = max_errors(sc, precision="bf16x6")
+    assert any(s.endswith("R") for s, _ in log), "re-alignment not exercised"
+    _check(worst, "bf16x6")
 
 
 def test_unsupported_sizes_are_rejected():
