@@ -56,31 +56,33 @@ constexpr uint32_t kTmemCols = 128;
 // Size classes of the fused kernel: C is the largest axis a CTA holds.
 //   C = 128: 512 threads (4 TMEM lane quadrants x 4 column groups), 16-bit
 //            operand planes of 128 x 128, one CTA per SM;
-//   C = 64 : 256 threads (4 quadrants x 2 column groups), planes of
-//            128 rows x 64 (A) and 64 x 64 (W), three CTAs per SM.
+//   C = 64 : 256 threads (4 quadrants x 2 column groups), planes of 64 x 64
+//            (the lanes >= 64 of every accumulator are garbage, so the A
+//            planes keep 64 rows), three CTAs per SM.
 // Dynamic shared memory: A operand planes, W operand planes, float32 staging
 // of C rows x (C + 4) floats (the padding makes row access conflict-free).
-//   C = 96 : 256 threads, planes of 128 rows x 96 and 96 x 96, and the staging
-//            tile shares the W region (alias): the weights are staged there
-//            before the first matrix is built, the spectrum is written there
-//            after the forward transforms and H0 is copied in again for the
-//            inverse; two CTAs per SM.
+//   C = 96 : 256 threads, planes of 96 x 96, and the staging tile shares the
+//            W region (alias): the weights are staged there before the first
+//            matrix is built, the spectrum is written there after the forward
+//            transforms and H0 is copied in again for the inverse; two CTAs
+//            per SM.
 // BF16X6 keeps three planes per operand: class 128 aliases the staging tile
-// on W as class 96 does (192 KiB of planes), and classes 96 and 64 fit one
-// and two CTAs per SM.
+// on W as class 96 does (192 KiB of planes); class 64 fits three CTAs per SM.
+// In an aliased class the A region is also the scratch of the band-limited
+// re-alignment (C x (C + 2) floats) and of the multilinear gather (C x C).
 template <int P, int C>
 struct Smem {
   static constexpr int threads = C == 128 ? 512 : 256;
   static constexpr int sstr = C + 4;
   static constexpr bool alias = C == 96 || (C == 128 && Fmt<P>::planes == 3);
   static constexpr int offA = 0;
-  static constexpr int offW = Fmt<P>::planes * Lay<P, C>::plane;
+  static constexpr int abytes = Fmt<P>::planes * Lay<P, C, C>::plane;
+  static constexpr int ascr = alias ? C * (C + 2) * 4 : 0;
+  static constexpr int offW = ((abytes > ascr ? abytes : ascr) + 1023) / 1024 * 1024;
   static constexpr int wbytes = Fmt<P>::planes * Lay<P, C>::wplane;
   static constexpr int sbytes = C * sstr * 4;
   static constexpr int offS = alias ? offW : offW + wbytes;
   static constexpr int bytes = alias ? offW + (wbytes > sbytes ? wbytes : sbytes) : offS + sbytes;
-  // CTAs per SM the shared memory allows (the launch bound of the planned kernel)
-  static constexpr int ctas = C == 128 ? 1 : C == 96 ? (Fmt<P>::planes == 3 ? 1 : 2) : (Fmt<P>::planes == 3 ? 2 : 3);
 };
 constexpr int kThreads = 512;                // the single-filter kernel (class 128)
 static_assert(Smem<PMF_PREC_BF16X6, 128>::bytes <= 200 * 1024, "class-128 BF16X6 planes and static state fit");
@@ -132,9 +134,9 @@ struct SharedT : TcHolder<kTc> {
   FrameState fs;           // working copy of the filter's frame state
   uint64_t mbar_mma, mbar_tma;
   uint32_t tmem;
-  int abort, degenerate, realign_mode;
-  float redf[2][16];
-  DF redm[16][6];
+  int abort, degenerate, realign_mode, wmax_bits;
+  float redf[2][T / 32];
+  DF redm[T / 32][6];
   double tot[10];
   double pend[24];
   double Mpi[9];
@@ -157,7 +159,8 @@ struct BatchPlan {
   float pa[MAXL][2];
   float pb[MAXL];
   float g, gsc;
-  int ok, pad;
+  int ok;
+  float wmax;   // max |weight| the front kernel wrote (before the scale pscale); -1 if it wrote none
   RegridRowsT<128> rows[2];
 };
 
@@ -271,7 +274,7 @@ __device__ __forceinline__ void stage_to_operand(uint8_t* A, const float* S, int
   const int q4 = nc / 4;
   for (int t = t0; t < nr * q4; t += tstep) {
     const int r = t % nr, c = (t / nr) * 4;
-    store4<P, C>(A, r, c, *(const float4*)(S + r * (C + 4) + c), s);
+    store4<P, C, false, C>(A, r, c, *(const float4*)(S + r * (C + 4) + c), s);
   }
 }
 
@@ -307,7 +310,7 @@ __device__ __noinline__ void regrid_rows_out(RegridRowsT<R>& rows, double rs, do
 template <int P, int C>
 __device__ __noinline__ void issue_stage_out(uint32_t tmem, uint32_t a_base, int a_mn, uint32_t w_base, int nout,
                                              int K, uint32_t mbar) {
-  issue_stage<P, C>(tmem, a_base, a_mn, w_base, nout, K, mbar);
+  issue_stage<P, C, C>(tmem, a_base, a_mn, w_base, nout, K, mbar);
 }
 template <int P, int C>
 __device__ __noinline__ void stage_to_operand_out(uint8_t* A, const float* S, int nr, int nc, float s, int t0,
@@ -536,12 +539,49 @@ __device__ void fht_lines(float* S, int ls, int es, int L, int N, float2* X, flo
   __syncthreads();
 }
 
+// The planned kernel's copy of the front kernel's results: the first l sub-step
+// coefficients and the regrid rows of both axes (axis 1 by the first half of
+// the block, axis 0 by the second).
+template <class SH>
+__device__ __forceinline__ void plan_rows(SH& sh, const BatchPlan* pl, int l, int N0, int N1) {
+  constexpr int kT = SH::kT;
+  const int tid = threadIdx.x;
+  for (int q = tid; q < l; q += kT) {
+    sh.pa[q][0] = pl->pa[q][0];
+    sh.pa[q][1] = pl->pa[q][1];
+    sh.pb[q] = pl->pb[q];
+  }
+  const int a = tid < kT / 2 ? 1 : 0;
+  const int t0 = tid - (a ? 0 : kT / 2);
+  const RegridRowsT<128>& src = pl->rows[a];
+  auto& dst = sh.rows[a];
+  for (int n = t0; n < (a ? N1 : N0); n += kT / 2) {
+    dst.ri[n] = src.ri[n];
+    dst.rf[n] = src.rf[n];
+    dst.rS[n] = src.rS[n];
+    dst.rcf[n] = src.rcf[n];
+    dst.rsf[n] = src.rsf[n];
+    dst.rzero[n] = src.rzero[n];
+  }
+}
+
 template <int P, bool kOut, bool kPlan = false, int C = 128>
 __device__ void fused2d(const FusedView& job, uint8_t* smem) {
-  using SH = SharedT<Smem<P, C>::threads, C, !kPlan>;
+  using SH = SharedT<kPlan ? Smem<P, C>::threads : kThreads, C, !kPlan>;
   constexpr int kThreads = SH::kT, kSStr = SH::kStr, kGroups = kThreads / 128;
   constexpr int kNV = C / kGroups / 4;          // float4 accumulator columns per thread
+  // columns [c0, c0 + ncol) of an accumulator of nout columns (a multiple of
+  // 16) held by column group cg: whole float4 groups, so that every row
+  // segment starts 16-byte aligned (nout = 48 over 8 groups: 8 + 8 + ... + 0)
+  auto cols = [&](int nout, int g, int& c0, int& ncol) {
+    const int per = ((nout >> 2) + kGroups - 1) / kGroups * 4;
+    c0 = g * per;
+    ncol = nout - c0 < per ? (nout > c0 ? nout - c0 : 0) : per;
+  };
   constexpr bool kAlias = Smem<P, C>::alias;    // staging tile in the W region
+  // only FP16 operands carry a scale (op_scale is 1 otherwise), so only they
+  // need the block maxima of the stage outputs
+  constexpr bool kScaled = P == PMF_PREC_FP16X3;
   __shared__ SH sh;
   if (!job.do_meas && !job.do_time) return;   // nothing requested for this filter
   if constexpr (kPlan) {
@@ -618,6 +658,22 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   float smax = 0.0f;      // max |weight| (operand scale of the first GEMM)
   float sa_first = 1.0f;  // scale of the R1 operand
   int realign = 0, l = 0, exact = 0;
+  // Planned kernel, separable regrid: the front kernel left the max of the
+  // weights it wrote, so the pscale goes into the R1 operand scale instead of
+  // a scaling pass over the tile (fold); with W free (no alias) the plan's
+  // coefficients and rows and the matrix I1 are set up while the weights
+  // arrive (early).
+  bool fold = false, early = false;
+  float wps = 1.0f;   // pscale folded into the R1 operand
+  if constexpr (kPlan) {
+    fold = job.plan->wmax >= 0.0f && !fs.realign;
+    early = fold && !kAlias;
+    if (early) {
+      plan_rows(sh, job.plan, fs.l, N0, N1);
+      __syncthreads();
+      build_interp<P, C, C>(sh.rows[1], W, N1, sh.sct[1], sw, 0, tid, kThreads);
+    }
+  }
 
   // ---- measurement update (eq. filt) ----
   if (!kPlan && job.do_meas) {
@@ -701,22 +757,28 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     }
     ph_tma ^= 1;
     const float ps = (float)fs.pscale;
-    for (int t = tid; t < np4; t += kThreads) {
-      const int r = t / q1, c = (t % q1) * 4;
-      float4 x = *(const float4*)(S + r * kSStr + c);
-      x.x *= ps;
-      x.y *= ps;
-      x.z *= ps;
-      x.w *= ps;
-      *(float4*)(S + r * kSStr + c) = x;
-      smax = amax4(smax, x);
+    if (fold) {
+      smax = job.plan->wmax * ps;   // = the max of the scaled weights (rounding is monotone)
+      wps = ps;
+    } else {
+      for (int t = tid; t < np4; t += kThreads) {
+        const int r = t / q1, c = (t % q1) * 4;
+        float4 x = *(const float4*)(S + r * kSStr + c);
+        x.x *= ps;
+        x.y *= ps;
+        x.z *= ps;
+        x.w *= ps;
+        *(float4*)(S + r * kSStr + c) = x;
+        smax = amax4(smax, x);
+      }
     }
   }
   {
     // Thread 0 finalises the moments and (time update) computes the frame in
     // float64 while warps 1.. convert the staged weights into the R1 operand,
-    // which needs neither.
-    const float sa0 = op_scale<P>(block_max(sh, smax, 1));
+    // which needs neither.  (With fold, every thread has the weights it reads
+    // from its own wait on the copies, and smax is the same in all of them.)
+    const float sa0 = fold ? op_scale<P>(smax) : op_scale<P>(block_max(sh, smax, 1));
     if (warp == 0 && kPlan) {
       // the front kernel decided the frame: pending frame and trace factor
       const BatchPlan* pl = job.plan;
@@ -751,7 +813,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       }
     } else if (job.do_time) {
       if constexpr (kOut) stage_to_operand_out<P, C>(A, S, N0, N1, sa0, tid - 32, kThreads - 32);
-      else stage_to_operand<P, C>(A, S, N0, N1, sa0, tid - 32, kThreads - 32);
+      else stage_to_operand<P, C>(A, S, N0, N1, sa0 * wps, tid - 32, kThreads - 32);
     }
     __syncthreads();
     if (sh.degenerate) goto done;
@@ -778,11 +840,13 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     l = fs.l;
     exact = fs.exact;
     if constexpr (kPlan) {
-      const BatchPlan* pl = job.plan;
-      for (int q = tid; q < l; q += kThreads) {
-        sh.pa[q][0] = pl->pa[q][0];
-        sh.pa[q][1] = pl->pa[q][1];
-        sh.pb[q] = pl->pb[q];
+      if (!early) {
+        const BatchPlan* pl = job.plan;
+        for (int q = tid; q < l; q += kThreads) {
+          sh.pa[q][0] = pl->pa[q][0];
+          sh.pa[q][1] = pl->pa[q][1];
+          sh.pb[q] = pl->pb[q];
+        }
       }
     } else {
       for (int q = tid; q < l; q += kThreads) {
@@ -837,16 +901,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       const int a = tid < kThreads / 2 ? 1 : 0;
       const int t0 = tid - (a ? 0 : kThreads / 2);
       if constexpr (kPlan) {
-        const RegridRowsT<128>& src = job.plan->rows[a];
-        RegridRowsT<C>& dst = sh.rows[a];
-        for (int n = t0; n < (a ? N1 : N0); n += kThreads / 2) {
-          dst.ri[n] = src.ri[n];
-          dst.rf[n] = src.rf[n];
-          dst.rS[n] = src.rS[n];
-          dst.rcf[n] = src.rcf[n];
-          dst.rsf[n] = src.rsf[n];
-          dst.rzero[n] = src.rzero[n];
-        }
+        if (!early) plan_rows(sh, job.plan, 0, N0, N1);
       } else if constexpr (kOut) {
         regrid_rows_out(sh.rows[a], fs.rs[a], fs.rd[a], a ? N1 : N0, t0, kThreads / 2);
       } else {
@@ -860,13 +915,13 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     // ---- the matrix I1; the R1 operand is already written ----
     float sa = sa_first;
     if constexpr (kOut) build_interp_out<P, C, C>(sh.rows[1], W, N1, sh.sct[1], sw, realign, tid, kThreads);
-    else build_interp<P, C, C>(sh.rows[1], W, N1, sh.sct[1], sw, realign, tid, kThreads);
+    else if (!early) build_interp<P, C, C>(sh.rows[1], W, N1, sh.sct[1], sw, realign, tid, kThreads);
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
       tc_after_sync();
       if constexpr (kOut) issue_stage_out<P, C>(tmem, su32(A), 0, su32(W), N1, N1, mb_mma);
-      else issue_stage<P, C>(tmem, su32(A), 0, su32(W), N1, N1, mb_mma);
+      else issue_stage<P, C, C>(tmem, su32(A), 0, su32(W), N1, N1, mb_mma);
     }
     float inv_scale = 1.0f / (sa * sw);
 
@@ -886,7 +941,8 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         }
         tc_after_sync();
         const int nlane = g ? N1 : N0, nout = g ? N0 : N1;
-        const int ncol = nout / kGroups, c0 = cg * ncol;
+        int c0, ncol;
+        cols(nout, cg, c0, ncol);
         float4 v[8];
         tmem_ld_cols(tlane + c0, ncol, v);
 #pragma unroll
@@ -901,7 +957,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         if (g == 0) {
           // F1 along axis 1 (rows of the tile), then the operand of R0 (read MN-major)
           fht_lines<kThreads>(S, kSStr, 1, N0, N1, X, Y, sh.sct[1]);
-          sa = op_scale<P>(block_max(sh, stage_max<kThreads, C>(S, N0, N1), 0));
+          if constexpr (kScaled) sa = op_scale<P>(block_max(sh, stage_max<kThreads, C>(S, N0, N1), 0));
           if constexpr (P == PMF_PREC_TF32) {
             const int q4 = N1 / 4;
             for (int t = tid; t < N0 * q4; t += kThreads) {
@@ -916,7 +972,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
           __syncthreads();
           if (tid == 0) {
             tc_after_sync();
-            issue_stage<P, C>(tmem, su32(A), P != PMF_PREC_TF32, su32(W), N0, N0, mb_mma);
+            issue_stage<P, C, C>(tmem, su32(A), P != PMF_PREC_TF32, su32(W), N0, N0, mb_mma);
           }
           inv_scale = 1.0f / (sa * sw);
         }
@@ -976,11 +1032,14 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       // accumulator of GEMM `stage`: valid lanes and columns
       const int nlane = (stage == 0 || stage == 1 || stage == 5) ? N0 : N1;
       const int nout = (stage <= 1 || stage == 5) ? N1 : N0;
-      const int ncol = nout / kGroups, c0 = cg * ncol;   // this thread's columns
+      int c0, ncol;   // this thread's columns
+      cols(nout, cg, c0, ncol);
       const bool lane_ok = row < nlane;
       float4 v[kNV];
       if constexpr (kNV == 8) {
         tmem_ld_cols(tlane + c0, ncol, v);
+      } else if constexpr (kNV == 4) {
+        tmem_ld_cols4(tlane + c0, ncol, v);
       } else {
         // up to 48 columns: 32 + 16
         float4 va[8], vb[4];
@@ -1034,14 +1093,16 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         __syncthreads();
         psi_stage(sh, S, N0, N1, l, exact);
         __syncthreads();
-        sa = op_scale<P>(block_max(sh, stage_max<kThreads, C>(S, N1, N0), stage & 1));
+        if constexpr (kScaled) sa = op_scale<P>(block_max(sh, stage_max<kThreads, C>(S, N1, N0), stage & 1));
         if constexpr (kOut) stage_to_operand_out<P, C>(A, S, N1, N0, sa, tid, kThreads);
         else stage_to_operand<P, C>(A, S, N1, N0, sa, tid, kThreads);
       } else {
-        float m = 0.0f;
+        if constexpr (kScaled) {
+          float m = 0.0f;
 #pragma unroll
-        for (int j = 0; j < kNV; ++j) m = amax4(m, v[j]);
-        sa = op_scale<P>(block_max(sh, lane_ok ? m : 0.0f, stage & 1));
+          for (int j = 0; j < kNV; ++j) m = amax4(m, v[j]);
+          sa = op_scale<P>(block_max(sh, lane_ok ? m : 0.0f, stage & 1));
+        }
         // R0 and V1 read this operand MN-major; TF32 gets it written transposed
         const bool tr = P == PMF_PREC_TF32 && (stage == 1 || stage == 4);
 #pragma unroll
@@ -1051,8 +1112,9 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
               // transposed, lanes become columns: a lane >= C would land in the
               // next row block of the size-64 layout, so invalid lanes are skipped
               if (lane_ok) store4_t<C>(A, row, c0 + 4 * j, v[j], sa);
-            } else {
-              store4<P, C>(A, row, c0 + 4 * j, v[j], sa);
+            } else if (C == 128 || row < C) {
+              // the planes keep C rows: lanes >= C (garbage) are not stored
+              store4<P, C, false, C>(A, row, c0 + 4 * j, v[j], sa);
             }
           }
         tc_before_sync();
@@ -1081,7 +1143,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
           const int a_mn = (P != PMF_PREC_TF32) && (stage == 1 || stage == 4);
           const int nn = (stage == 0 || stage == 4) ? N1 : N0;
           if constexpr (kOut) issue_stage_out<P, C>(tmem, su32(A), a_mn, su32(W), nn, nn, mb_mma);
-          else issue_stage<P, C>(tmem, su32(A), a_mn, su32(W), nn, nn, mb_mma);
+          else issue_stage<P, C, C>(tmem, su32(A), a_mn, su32(W), nn, nn, mb_mma);
         }
       }
       if (mat >= 0) ph_tma ^= 1;
@@ -1157,7 +1219,10 @@ __global__ void __launch_bounds__(kFrontThreads, 6) k_front2d(const FilterSlot* 
   if (do_meas)
     for (int i = tid; i < (int)(sizeof(MeasParams) / 8); i += kT)
       ((unsigned long long*)&sh.mp)[i] = ((const unsigned long long*)sl.mp)[i];
-  if (tid == 0) sh.degenerate = 0;
+  if (tid == 0) {
+    sh.degenerate = 0;
+    sh.wmax_bits = 0;
+  }
   __syncthreads();
   if (do_meas && tid < PMF_MAX_NZ) sh.mp.z[tid] = it.z[tid];
   __syncthreads();
@@ -1198,6 +1263,7 @@ __global__ void __launch_bounds__(kFrontThreads, 6) k_front2d(const FilterSlot* 
     const float ps = (float)fs.pscale;
     Moments mo;
     mo.zero();
+    float wmax = 0.0f;
     const int tmax = (kT / q1) * q1;
     if (tid < tmax) {
       // float32 column sums over at most 16 rows, then one double-float add per slot
@@ -1212,6 +1278,7 @@ __global__ void __launch_bounds__(kFrontThreads, 6) k_front2d(const FilterSlot* 
         x.z = (x.z * ps) * __expf(emin - meas_e(mk, u0, u1 + 2.0f));
         x.w = (x.w * ps) * __expf(emin - meas_e(mk, u0, u1 + 3.0f));
         *(float4*)(out + (size_t)r * N1 + c) = x;
+        wmax = amax4(wmax, x);
         const float xs[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -1230,6 +1297,9 @@ __global__ void __launch_bounds__(kFrontThreads, 6) k_front2d(const FilterSlot* 
       mo.add_cols4(ca, cb, cc, (tid % q1) * 4 - 0.5f * (N1 - 1));
     }
     block_moments(sh, mo);
+    // non-negative floats order as their bit patterns: one shared atomic per warp
+    for (int o = 16; o; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+    if ((tid & 31) == 0) atomicMax(&sh.wmax_bits, __float_as_int(wmax));
   }
   if (warp == 0) {
     bool ok = true;
@@ -1257,6 +1327,7 @@ __global__ void __launch_bounds__(kFrontThreads, 6) k_front2d(const FilterSlot* 
     }
   }
   __syncthreads();
+  if (tid == 0) plan->wmax = do_meas ? __int_as_float(sh.wmax_bits) : -1.0f;
   if (sh.degenerate) {
     if (tid == 0) plan->ok = 0;
   } else if (!do_time) {
@@ -1292,10 +1363,20 @@ __global__ void __launch_bounds__(kFrontThreads, 6) k_front2d(const FilterSlot* 
   for (int i = tid; i < kFsWords; i += kT) ((unsigned long long*)&st->f)[i] = ((const unsigned long long*)&fs)[i];
 }
 
+// CTAs per SM of the planned kernel of class C: shared memory (dynamic, static
+// and the 1 KiB the hardware keeps per CTA, of 228 KiB per SM) and TMEM (128
+// of 512 columns per CTA).  The launch bound holds the registers to it.
+template <int P, int C>
+constexpr int planned_ctas() {
+  constexpr int per = Smem<P, C>::bytes + (int)sizeof(SharedT<Smem<P, C>::threads, C, false>) + 1024;
+  constexpr int by_smem = 228 * 1024 / per;
+  return by_smem < 4 ? by_smem : 4;
+}
+
 // Planned transform kernel of a batched epoch (size class C): the time update
 // of the filters whose front kernel ran it, from the weights and plan it left.
 template <int P, int C>
-__global__ void __launch_bounds__(Smem<P, C>::threads, Smem<P, C>::ctas)
+__global__ void __launch_bounds__(Smem<P, C>::threads, planned_ctas<P, C>())
     k_fused2d_planned(const FilterSlot* __restrict__ slots, const StepItem* __restrict__ items,
                       const TimeConsts* __restrict__ tcs) {
   extern __shared__ __align__(1024) uint8_t smem[];

@@ -168,13 +168,16 @@ struct Fmt<PMF_PREC_BF16X6> {
   static constexpr int esz = 2, rowblk = 2048, planes = 3, kper = 16, code = 1;
 };
 
-// Operand tiles of a size class C (the largest axis they hold, 64 or 128):
-// an 8-row block covers C elements along K, so a 128-row plane takes
-// 128 * C * esz bytes (class 128, 16-bit: 32 KiB, the kPlane of the fused kernel).
-template <int P, int C>
+// Operand tiles of a size class C (the largest axis they hold): an 8-row
+// block covers C elements along K, so an R-row plane takes R * C * esz bytes
+// (class 128, 16-bit: 32 KiB).  The MMA reads 128 rows (M) of the A operand;
+// a kernel whose lanes >= R are never used keeps R < 128 rows per plane, and
+// the rows the MMA reads past a plane fall into the next plane or region
+// (garbage lanes, discarded).
+template <int P, int C, int R = 128>
 struct Lay {
   static constexpr int rowblk = C * Fmt<P>::esz * 8;
-  static constexpr int plane = 128 * C * Fmt<P>::esz;   // a 128-row (M) operand plane
+  static constexpr int plane = R * C * Fmt<P>::esz;     // an R-row (M) operand plane
   static constexpr int wplane = C * C * Fmt<P>::esz;    // a C-row matrix (W) plane
 };
 
@@ -191,9 +194,9 @@ __device__ __forceinline__ uint32_t b2u(__nv_bfloat162 h) { return *(uint32_t*)&
 // by s: split into hi + lo 16-bit planes, hi + mid + lo BF16 planes (BF16X6:
 // x - hi and x - hi - mid are exact in float32, so the three pieces keep all
 // 24 significand bits), or one float32 plane for TF32.
-template <int P, int C = 128, bool kW = false>
+template <int P, int C = 128, bool kW = false, int R = 128>
 __device__ __forceinline__ void store4(uint8_t* base, int r, int c, float4 v, float s) {
-  constexpr int kPl = kW ? Lay<P, C>::wplane : Lay<P, C>::plane;
+  constexpr int kPl = kW ? Lay<P, C>::wplane : Lay<P, C, R>::plane;
   v.x *= s;
   v.y *= s;
   v.z *= s;
@@ -314,11 +317,11 @@ struct Moments {
 // those see roundings at full magnitude: hi*lo, lo*hi (~2^-11 of the result)
 // for the two-piece formats; for BF16X6 (pieces hi, mid, lo of ~2^0, 2^-9,
 // 2^-18) hi*lo, lo*hi and mid*mid (~2^-18), then hi*mid and mid*hi (~2^-9).
-template <int P, int C = 128>
+template <int P, int C = 128, int R = 128>
 __device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t a_base, int a_mn, uint32_t w_base,
                                             int nout, int K, uint32_t mbar) {
   constexpr uint32_t rb = Lay<P, C>::rowblk;
-  constexpr uint32_t kPl = Lay<P, C>::plane, kWPl = Lay<P, C>::wplane;
+  constexpr uint32_t kPl = Lay<P, C, R>::plane, kWPl = Lay<P, C>::wplane;
   constexpr int kp = Fmt<P>::kper;
   const uint32_t id = idesc(Fmt<P>::code, a_mn, nout);
   // K step of one instruction: 32 bytes = 2 core matrices along K (K-major),
