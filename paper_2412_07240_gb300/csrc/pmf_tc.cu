@@ -145,8 +145,12 @@ struct SharedT : TcHolder<kTc> {
   float g, ps, gsc;
   // frame-relative measurement constants
   float mc[2], mM[4], mr0[3], mRinv[9], mH[6], mcn;
-  RegridRowsT<C> rows[2];      // regrid rows per axis
-  float sct[2][2 * (2 * C + 1)];   // per axis (cos, sin)(pi m / N), m = -N..N
+  // per axis: regrid rows and the (cos, sin)(pi m / N) table, m = -N..N, in
+  // the kernels that compute the frame; the planned transform kernel reads
+  // the plan's rows and the axis tables from global memory instead (its
+  // static shared memory then admits one more CTA per SM in classes 96 / 64)
+  RegridRowsT<kTc ? C : 1> rows[2];
+  float sct[2][kTc ? 2 * (2 * C + 1) : 1];
 };
 using Shared = SharedT<512, 128, true>;
 
@@ -328,7 +332,8 @@ __device__ __noinline__ void stage_to_operand_out(uint8_t* A, const float* S, in
 // m and sincospi of f, then powers by recurrence.  Returns this thread's
 // max |weight| of the re-aligned tile.
 template <class SH>
-__device__ __noinline__ float shear_stage(const SH& sh, float* S, float* C, int N0, int N1) {
+__device__ __noinline__ float shear_stage(const SH& sh, float* S, float* C, int N0, int N1, const float* sct0,
+                                          const float* sct1) {
   constexpr int kThreads = SH::kT, kSStr = SH::kStr;
   const FrameState& fs = sh.fs;
   // pass order making pass 1's line-dependent shift the smaller: |B_10 / B_00| <= |B_01 / B_11|
@@ -341,7 +346,7 @@ __device__ __noinline__ float shear_stage(const SH& sh, float* S, float* C, int 
   float smax = 0.0f;
   for (int pass = 1; pass <= 2; ++pass) {
     const int L = pass == 1 ? Np : Nq, N = pass == 1 ? Nq : Np, H = N / 2;
-    const float* sct = sh.sct[pass == 1 ? q : p];
+    const float* sct = (pass == 1 ? q : p) ? sct1 : sct0;
     const float rN = 1.0f / (float)N;
     for (int it = threadIdx.x; it < L * (H + 1); it += kThreads) {
       const int line = it / (H + 1), sidx = it - line * (H + 1);
@@ -539,29 +544,14 @@ __device__ void fht_lines(float* S, int ls, int es, int L, int N, float2* X, flo
   __syncthreads();
 }
 
-// The planned kernel's copy of the front kernel's results: the first l sub-step
-// coefficients and the regrid rows of both axes (axis 1 by the first half of
-// the block, axis 0 by the second).
+// The planned kernel's copy of the front kernel's sub-step coefficients (the
+// multiplier reads them for every orbit); the regrid rows stay in the plan.
 template <class SH>
-__device__ __forceinline__ void plan_rows(SH& sh, const BatchPlan* pl, int l, int N0, int N1) {
-  constexpr int kT = SH::kT;
-  const int tid = threadIdx.x;
-  for (int q = tid; q < l; q += kT) {
+__device__ __forceinline__ void plan_coeffs(SH& sh, const BatchPlan* pl, int l) {
+  for (int q = threadIdx.x; q < l; q += SH::kT) {
     sh.pa[q][0] = pl->pa[q][0];
     sh.pa[q][1] = pl->pa[q][1];
     sh.pb[q] = pl->pb[q];
-  }
-  const int a = tid < kT / 2 ? 1 : 0;
-  const int t0 = tid - (a ? 0 : kT / 2);
-  const RegridRowsT<128>& src = pl->rows[a];
-  auto& dst = sh.rows[a];
-  for (int n = t0; n < (a ? N1 : N0); n += kT / 2) {
-    dst.ri[n] = src.ri[n];
-    dst.rf[n] = src.rf[n];
-    dst.rS[n] = src.rS[n];
-    dst.rcf[n] = src.rcf[n];
-    dst.rsf[n] = src.rsf[n];
-    dst.rzero[n] = src.rzero[n];
   }
 }
 
@@ -598,6 +588,17 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   const uint32_t mb_mma = su32(&sh.mbar_mma), mb_tma = su32(&sh.mbar_tma);
   uint32_t ph_mma = 0, ph_tma = 0;
   const float sw = P == PMF_PREC_FP16X3 ? 16384.0f : 1.0f;   // scale of the matrix operands
+  // the axis tables and the matrices I_a: from shared memory, or (planned
+  // kernel) from the axis tables and the plan's rows in global memory
+  auto sct = [&](int a) -> const float* {
+    if constexpr (kPlan) return job.sctab[a];
+    else return sh.sct[a];
+  };
+  auto build_I = [&](int a, int Nm, int realign_, uint8_t* Wd) {
+    if constexpr (kPlan) build_interp<P, C, 128>(job.plan->rows[a], Wd, Nm, job.sctab[a], sw, realign_, threadIdx.x, kThreads);
+    else if constexpr (kOut) build_interp_out<P, C, C>(sh.rows[a], Wd, Nm, sh.sct[a], sw, realign_, threadIdx.x, kThreads);
+    else build_interp<P, C, C>(sh.rows[a], Wd, Nm, sh.sct[a], sw, realign_, threadIdx.x, kThreads);
+  };
   constexpr int kFsWords = sizeof(FrameState) / 8;
 
   for (int i = tid; i < kFsWords; i += kThreads)
@@ -609,10 +610,11 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         ((unsigned long long*)&sh.tc)[i] = ((const unsigned long long*)job.tc)[i];
     }
     if (tid == 0) sh.realign_mode = job.tc->realign_mode;
-    for (int a = 0; a < 2; ++a) {
-      const int n = 2 * (2 * (a ? N1 : N0) + 1);
-      for (int i = tid; i < n; i += kThreads) sh.sct[a][i] = job.sctab[a][i];
-    }
+    if constexpr (!kPlan)
+      for (int a = 0; a < 2; ++a) {
+        const int n = 2 * (2 * (a ? N1 : N0) + 1);
+        for (int i = tid; i < n; i += kThreads) sh.sct[a][i] = job.sctab[a][i];
+      }
   }
   if (job.do_meas) {
     for (int i = tid; i < (int)(sizeof(MeasParams) / 8); i += kThreads)
@@ -669,9 +671,8 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     fold = job.plan->wmax >= 0.0f && !fs.realign;
     early = fold && !kAlias;
     if (early) {
-      plan_rows(sh, job.plan, fs.l, N0, N1);
-      __syncthreads();
-      build_interp<P, C, C>(sh.rows[1], W, N1, sh.sct[1], sw, 0, tid, kThreads);
+      plan_coeffs(sh, job.plan, fs.l);
+      build_I(1, N1, 0, W);
     }
   }
 
@@ -840,14 +841,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     l = fs.l;
     exact = fs.exact;
     if constexpr (kPlan) {
-      if (!early) {
-        const BatchPlan* pl = job.plan;
-        for (int q = tid; q < l; q += kThreads) {
-          sh.pa[q][0] = pl->pa[q][0];
-          sh.pa[q][1] = pl->pa[q][1];
-          sh.pb[q] = pl->pb[q];
-        }
-      }
+      if (!early) plan_coeffs(sh, job.plan, l);
     } else {
       for (int q = tid; q < l; q += kThreads) {
         double pa[4], pb[6];
@@ -859,7 +853,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     }
     if (realign && sh.realign_mode == PMF_REALIGN_SHEAR) {
       // band-limited re-alignment in place on the staging tile
-      smax = shear_stage(sh, S, (float*)A, N0, N1);
+      smax = shear_stage(sh, S, (float*)A, N0, N1, sct(0), sct(1));
       sa_first = op_scale<P>(block_max(sh, smax, 0));
       if constexpr (kOut) stage_to_operand_out<P, C>(A, S, N0, N1, sa_first, tid, kThreads);
       else stage_to_operand<P, C>(A, S, N0, N1, sa_first, tid, kThreads);
@@ -901,7 +895,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       const int a = tid < kThreads / 2 ? 1 : 0;
       const int t0 = tid - (a ? 0 : kThreads / 2);
       if constexpr (kPlan) {
-        if (!early) plan_rows(sh, job.plan, 0, N0, N1);
+        // the rows stay in the plan
       } else if constexpr (kOut) {
         regrid_rows_out(sh.rows[a], fs.rs[a], fs.rd[a], a ? N1 : N0, t0, kThreads / 2);
       } else {
@@ -914,8 +908,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   {
     // ---- the matrix I1; the R1 operand is already written ----
     float sa = sa_first;
-    if constexpr (kOut) build_interp_out<P, C, C>(sh.rows[1], W, N1, sh.sct[1], sw, realign, tid, kThreads);
-    else if (!early) build_interp<P, C, C>(sh.rows[1], W, N1, sh.sct[1], sw, realign, tid, kThreads);
+    if (!early) build_I(1, N1, realign, W);
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -956,7 +949,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         __syncthreads();
         if (g == 0) {
           // F1 along axis 1 (rows of the tile), then the operand of R0 (read MN-major)
-          fht_lines<kThreads>(S, kSStr, 1, N0, N1, X, Y, sh.sct[1]);
+          fht_lines<kThreads>(S, kSStr, 1, N0, N1, X, Y, sct(1));
           if constexpr (kScaled) sa = op_scale<P>(block_max(sh, stage_max<kThreads, C>(S, N0, N1), 0));
           if constexpr (P == PMF_PREC_TF32) {
             const int q4 = N1 / 4;
@@ -967,7 +960,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
           } else {
             stage_to_operand<P, C>(A, S, N0, N1, sa, tid, kThreads);
           }
-          build_interp<P, C, C>(sh.rows[0], W, N0, sh.sct[0], sw, realign, tid, kThreads);
+          build_I(0, N0, realign, W);
           fence_async_smem();
           __syncthreads();
           if (tid == 0) {
@@ -980,11 +973,11 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       if (!sh.abort) {
         // F0 along axis 0 (rows of the tile T[k1][.]), the multiplier, V0, then
         // V1 along axis 1 (columns of the tile)
-        fht_lines<kThreads>(S, kSStr, 1, N1, N0, X, Y, sh.sct[0]);
+        fht_lines<kThreads>(S, kSStr, 1, N1, N0, X, Y, sct(0));
         psi_stage(sh, S, N0, N1, l, exact);
         __syncthreads();
-        fht_lines<kThreads>(S, kSStr, 1, N1, N0, X, Y, sh.sct[0]);
-        fht_lines<kThreads>(S, 1, kSStr, N0, N1, X, Y, sh.sct[1]);
+        fht_lines<kThreads>(S, kSStr, 1, N1, N0, X, Y, sct(0));
+        fht_lines<kThreads>(S, 1, kSStr, N0, N1, X, Y, sct(1));
         // final weights: tile [j1][j0] -> row j0 of the output, moments
         Moments mo;
         mo.zero();
@@ -1121,8 +1114,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       }
       if (stage == 1) {
         __syncthreads();
-        if constexpr (kOut) build_interp_out<P, C, C>(sh.rows[0], W, N0, sh.sct[0], sw, realign, tid, kThreads);
-        else build_interp<P, C, C>(sh.rows[0], W, N0, sh.sct[0], sw, realign, tid, kThreads);
+        build_I(0, N0, realign, W);
       }
       fence_async_smem();
       __syncthreads();

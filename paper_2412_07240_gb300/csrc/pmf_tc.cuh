@@ -71,15 +71,14 @@ inline int tc_class(int N0, int N1) {
   const int m = N0 > N1 ? N0 : N1;
   return m <= 64 ? 64 : m <= 96 ? 96 : 128;
 }
-// ... for a filter in the given transform form and precision: the size-96
-// class keeps its staging tile in the W region, which the FFT form needs as
-// scratch, so an FFT-form filter of that class runs in the size-128 class;
-// so does a BF16X6 filter of that class (three operand planes leave one CTA
-// per SM in either class, and the 512-thread class-128 kernel shortens the
-// filter's chain).
+// ... for a filter in the given transform form: the size-96 class keeps its
+// staging tile in the W region, which the FFT form needs as scratch, so an
+// FFT-form filter of that class runs in the size-128 class (the precision
+// does not change the class: BF16X6 has no FFT form).
 inline int tc_class_form(int N0, int N1, int fft, int precision) {
+  (void)precision;
   const int c = tc_class(N0, N1);
-  return (fft || precision == PMF_PREC_BF16X6) && c == 96 ? 128 : c;
+  return fft && c == 96 ? 128 : c;
 }
 // Device bytes of one filter's plan (the front kernel's results of an epoch).
 size_t tc_plan_bytes();

@@ -41,8 +41,9 @@ def test_batch_legs_fit(steps, warmup):
     # timed steps and the end-to-end loop read z[:, warmup + k]
     assert warmup + steps - 1 < z.shape[1]
     assert warmup + min(5, steps) - 1 < z.shape[1]
-    # the oracle sample (8 epochs of its own c4_batch call) sees the same
-    # measurements as the batch's first epochs: draws are made epoch by epoch
+    # the oracle sample and the parity batch (their own c4_batch call over the
+    # whole horizon) see the same measurements as the timed batch's first
+    # epochs: draws are made epoch by epoch
     _, _, _, _, z8 = w.c4_batch(count=8, epochs=8)
     np.testing.assert_array_equal(z8[:, :min(8, epochs)], z[:, :min(8, epochs)])
     ids = bench.c4_sample_ids(4096)
