@@ -9,8 +9,10 @@ c6 select the 128 x 128 oscillator, the 96^3 bearing filter, the serving
 population and the 4-D coordinated turn.
 
 metric : grid-point updates per second (points x epochs / device time)
-value  : the tensor-core path at the chosen precision (default FP16X3),
-         inputs resident in HBM, L2 flushed between timed steps
+value  : the tensor-core path at the chosen precision (default BF16X6, the
+         split-BF16 format within 1e-5, for the 2-D workloads c2 / c4 / c5;
+         FP16X3 for the 3-D and 4-D ones), inputs resident in HBM, L2 flushed
+         between timed steps
 e2e    : the same through the public C-ABI call with the measurements taken
          from host memory and the moments read back every step
 fp64_gpu : the plain float64 GPU path on the same workload (comparator)
@@ -176,7 +178,10 @@ def _launch_names(sc):
 STEP_ITEM_BYTES = 32
 TIME_CONSTS_BYTES = 5832
 TRAFFIC_C2 = 345344.0
-TRAFFIC_C4_PER_POINT = None   # not captured for the current batch kernels
+# DRAM bytes per grid point of one C4 epoch (the four kernels' dram__bytes_read
+# + dram__bytes_write, one ncu capture of the full batch), per format; absent
+# where not captured for the current kernels
+TRAFFIC_C4_PER_POINT = {}
 BATCH_KERNEL = "k_front2d + k_fused2d_planned<128|96|64> (one graph per epoch)"
 
 
@@ -586,7 +591,8 @@ def bench_batch(args, ws, rank, pg):
             "transform_forms": transform_forms(cfgs, args.precision),
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                          "frac": gbs / peaks.get("hbm_gbs"),
-                         "traffic": None if TRAFFIC_C4_PER_POINT is None else TRAFFIC_C4_PER_POINT * float(P.sum()),
+                         "traffic": (TRAFFIC_C4_PER_POINT[args.precision] * float(P.sum())
+                                     if args.precision in TRAFFIC_C4_PER_POINT else None),
                          "kernel": BATCH_KERNEL, "bytes_per_launch": alg_bytes,
                          "peak_source": f"hbm_gbs ({src})",
                          "tensor": {"achieved": ach, "peak": peaks.get("bf16_tflops"), "unit": "TFLOP/s",
@@ -868,6 +874,13 @@ def bench_4d(args, ws, rank, pg, local):
         print(json.dumps(line))
 
 
+def default_precision(workload):
+    """The split format of a workload: BF16X6 (the split-BF16 format within
+    1e-5) where the tensor-core kernels have it (2-D: c2, c4, c5, whose 3-D
+    filters the server runs in FP16X3), FP16X3 for the 3-D and 4-D paths."""
+    return "fp16x3" if workload in ("c3", "c6") else "bf16x6"
+
+
 def make_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -875,7 +888,8 @@ def make_parser():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="c4")
-    ap.add_argument("--precision", default="fp16x3")
+    ap.add_argument("--precision", default=None,
+                    help="tensor-core format (default bf16x6 for c2/c4/c5, fp16x3 for c3/c6)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--count", type=int, default=4096, help="filters of the c4 batch workload (c5: 10000)")
     ap.add_argument("--rate", type=float, default=200e3, help="c5: aggregate request rate per second")
@@ -893,6 +907,7 @@ def make_parser():
 def main(argv=None):
     args = make_parser().parse_args(argv)
     args.warmup = max(3, args.warmup)
+    args.precision = args.precision or default_precision(args.workload)
     MODES["psi"], MODES["realign"] = args.psi, args.realign
     ws, rank, local, pg = _dist()
     if args.impl == "reference":
@@ -942,8 +957,8 @@ def main(argv=None):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (fp16x3 split GEMMs, fp64 frame/moments)"
-        if args.precision == "fp16x3" else args.precision,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": f"f32 ({args.precision} split GEMMs, fp64 frame/moments)" if args.precision != "fp64" else "f64",
         "data": "synthetic (seeded truth and measurements)",
         "config": {"workload": sc.name, "grid": list(sc.cfg.N), "precision": args.precision,
                    "psi": MODES["psi"], "realign": MODES["realign"],

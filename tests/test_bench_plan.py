@@ -16,6 +16,10 @@ def test_default_workload_is_the_batch():
     args = bench.make_parser().parse_args([])
     assert args.workload == "c4"
     assert args.gpus == 1 and args.impl == "native"
+    # split-BF16 differentiation where the kernels have it (2-D), FP16X3 elsewhere
+    assert args.precision is None
+    assert [bench.default_precision(x) for x in ("c2", "c3", "c4", "c5", "c6")] == \
+        ["bf16x6", "fp16x3", "bf16x6", "bf16x6", "fp16x3"]
 
 
 @pytest.mark.parametrize("workload", ["c2", "c3", "c6"])
