@@ -124,8 +124,9 @@ struct TcHolder {
 template <>
 struct TcHolder<false> {};
 
-// Static shared memory of one CTA (threads T, largest axis C).
-template <int T, int C, bool kTc>
+// Static shared memory of one CTA (threads T, largest axis C; kTc: the time
+// constants; kRows: the regrid rows and axis tables of the fused kernel).
+template <int T, int C, bool kTc, bool kRows = kTc>
 struct SharedT : TcHolder<kTc> {
   static constexpr int kT = T;
   static constexpr int kC = C;
@@ -149,8 +150,8 @@ struct SharedT : TcHolder<kTc> {
   // the kernels that compute the frame; the planned transform kernel reads
   // the plan's rows and the axis tables from global memory instead (its
   // static shared memory then admits one more CTA per SM in classes 96 / 64)
-  RegridRowsT<kTc ? C : 1> rows[2];
-  float sct[2][kTc ? 2 * (2 * C + 1) : 1];
+  RegridRowsT<kRows ? C : 1> rows[2];
+  float sct[2][kRows ? 2 * (2 * C + 1) : 1];
 };
 using Shared = SharedT<512, 128, true>;
 
@@ -1187,7 +1188,7 @@ constexpr int kFrontThreads = 128;   // four warps: six or more CTAs (filters) s
 __global__ void __launch_bounds__(kFrontThreads, 6) k_front2d(const FilterSlot* __restrict__ slots,
                                                               const StepItem* __restrict__ items,
                                                               const TimeConsts* __restrict__ tcs) {
-  __shared__ SharedT<kFrontThreads, 128, true> sh;
+  __shared__ SharedT<kFrontThreads, 128, true, false> sh;
   constexpr int kT = kFrontThreads;
   const StepItem& it = items[blockIdx.x];
   const FilterSlot& sl = slots[it.slot];
