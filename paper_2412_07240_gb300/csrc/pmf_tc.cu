@@ -270,16 +270,18 @@ __device__ __forceinline__ float meas_e(const MeasK& k, float u0, float u1) {
   return 0.5f * e;
 }
 
-// Staging rows r < nr, columns < nc -> operand planes (scaled by s).
-// (consecutive threads take consecutive rows: in the core-matrix layout a row's
-// consecutive columns are 128 bytes apart, 8 consecutive rows share 128 bytes)
+// Staging rows r < nr, columns < nc (a multiple of 8) -> operand planes
+// (scaled by s).  Consecutive threads take consecutive rows, eight columns
+// each: in the core-matrix layout 8 consecutive rows of 8 columns are 128
+// contiguous bytes, written with one 16-byte store per thread and plane.
 template <int P, int C = 128>
 __device__ __forceinline__ void stage_to_operand(uint8_t* A, const float* S, int nr, int nc, float s,
                                                  int t0, int tstep) {
-  const int q4 = nc / 4;
-  for (int t = t0; t < nr * q4; t += tstep) {
-    const int r = t % nr, c = (t / nr) * 4;
-    store4<P, C, false, C>(A, r, c, *(const float4*)(S + r * (C + 4) + c), s);
+  const int q8 = nc / 8;
+  for (int t = t0; t < nr * q8; t += tstep) {
+    const int r = t % nr, c = (t / nr) * 8;
+    const float* src = S + r * (C + 4) + c;
+    store8<P, C, false, C>(A, r, c, *(const float4*)src, *(const float4*)(src + 4), s);
   }
 }
 
@@ -562,10 +564,10 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   constexpr int kThreads = SH::kT, kSStr = SH::kStr, kGroups = kThreads / 128;
   constexpr int kNV = C / kGroups / 4;          // float4 accumulator columns per thread
   // columns [c0, c0 + ncol) of an accumulator of nout columns (a multiple of
-  // 16) held by column group cg: whole float4 groups, so that every row
-  // segment starts 16-byte aligned (nout = 48 over 8 groups: 8 + 8 + ... + 0)
+  // 16) held by column group cg: whole groups of 8, so that every row segment
+  // is a run of 16-byte operand stores (nout = 48 over 4 groups: 16 + 16 + 16 + 0)
   auto cols = [&](int nout, int g, int& c0, int& ncol) {
-    const int per = ((nout >> 2) + kGroups - 1) / kGroups * 4;
+    const int per = ((nout >> 3) + kGroups - 1) / kGroups * 8;
     c0 = g * per;
     ncol = nout - c0 < per ? (nout > c0 ? nout - c0 : 0) : per;
   };
@@ -1099,18 +1101,19 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         }
         // R0 and V1 read this operand MN-major; TF32 gets it written transposed
         const bool tr = P == PMF_PREC_TF32 && (stage == 1 || stage == 4);
+        if (tr) {
+          // transposed, lanes become columns: a lane >= C would land in the
+          // next row block of the size-64 layout, so invalid lanes are skipped
 #pragma unroll
-        for (int j = 0; j < kNV; ++j)
-          if (4 * j < ncol) {
-            if (tr) {
-              // transposed, lanes become columns: a lane >= C would land in the
-              // next row block of the size-64 layout, so invalid lanes are skipped
-              if (lane_ok) store4_t<C>(A, row, c0 + 4 * j, v[j], sa);
-            } else if (C == 128 || row < C) {
-              // the planes keep C rows: lanes >= C (garbage) are not stored
-              store4<P, C, false, C>(A, row, c0 + 4 * j, v[j], sa);
-            }
-          }
+          for (int j = 0; j < kNV; ++j)
+            if (4 * j < ncol && lane_ok) store4_t<C>(A, row, c0 + 4 * j, v[j], sa);
+        } else if (C == 128 || row < C) {
+          // the planes keep C rows: lanes >= C (garbage) are not stored; ncol
+          // is a multiple of 8, so the float4 columns pair up
+#pragma unroll
+          for (int j = 0; j < kNV; j += 2)
+            if (4 * j < ncol) store8<P, C, false, C>(A, row, c0 + 4 * j, v[j], v[j + 1], sa);
+        }
         tc_before_sync();
       }
       if (stage == 1) {

@@ -227,6 +227,48 @@ __device__ __forceinline__ void store4(uint8_t* base, int r, int c, float4 v, fl
   }
 }
 
+// Elements (r, c..c+7) (c a multiple of 8): one 16-byte store per plane for the
+// 16-bit formats (a whole core-matrix row; the 8-byte stores of store4 leave
+// half of each bank wavefront unused), two float32 stores for TF32.
+template <int P, int C = 128, bool kW = false, int R = 128>
+__device__ __forceinline__ void store8(uint8_t* base, int r, int c, float4 a, float4 b, float s) {
+  if constexpr (P == PMF_PREC_TF32) {
+    store4<P, C, kW, R>(base, r, c, a, s);
+    store4<P, C, kW, R>(base, r, c + 4, b, s);
+  } else {
+    constexpr int kPl = kW ? Lay<P, C>::wplane : Lay<P, C, R>::plane;
+    const float x[8] = {a.x * s, a.y * s, a.z * s, a.w * s, b.x * s, b.y * s, b.z * s, b.w * s};
+    const uint32_t off = op_off<P, C>(r, c);
+    uint32_t pc[3][4];
+    if constexpr (P == PMF_PREC_FP16X3) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const __half2 h = __floats2half2_rn(x[2 * i], x[2 * i + 1]);
+        const float2 f = __half22float2(h);
+        pc[0][i] = h2u(h);
+        pc[1][i] = h2u(__floats2half2_rn(x[2 * i] - f.x, x[2 * i + 1] - f.y));
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+        const float2 f = __bfloat1622float2(h);
+        const float r0 = x[2 * i] - f.x, r1 = x[2 * i + 1] - f.y;
+        const __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
+        pc[0][i] = b2u(h);
+        pc[1][i] = b2u(m);
+        if constexpr (P == PMF_PREC_BF16X6) {
+          const float2 g = __bfloat1622float2(m);
+          pc[2][i] = b2u(__floats2bfloat162_rn(r0 - g.x, r1 - g.y));
+        }
+      }
+    }
+#pragma unroll
+    for (int pl = 0; pl < Fmt<P>::planes; ++pl)
+      *(uint4*)(base + pl * kPl + off) = make_uint4(pc[pl][0], pc[pl][1], pc[pl][2], pc[pl][3]);
+  }
+}
+
 // TF32 operands are read K-major only: elements (c..c+3, r) of the float32 plane.
 template <int C = 128>
 __device__ __forceinline__ void store4_t(uint8_t* base, int r, int c, float4 v, float s) {
@@ -427,14 +469,14 @@ __device__ void build_interp(const RegridRowsT<R>& sh, uint8_t* W, int N, const 
   if (t0 >= per * N) return;
   const int n = t0 % N;
   const RegridRow r = regrid_row(sh, n);
-  for (int c = (t0 / N) * 4; c < N; c += 4 * per) {
-    float k[4];
+  for (int c = (t0 / N) * 8; c < N; c += 8 * per) {   // N is a multiple of 16
+    float k[8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 8; ++i) {
       const int j = c + i;
       k[i] = realign ? (n == j ? 1.0f : 0.0f) : interp_value(r, j, N, sctab);
     }
-    store4<P, C, true>(W, n, c, make_float4(k[0], k[1], k[2], k[3]), sw);
+    store8<P, C, true>(W, n, c, make_float4(k[0], k[1], k[2], k[3]), make_float4(k[4], k[5], k[6], k[7]), sw);
   }
 }
 
