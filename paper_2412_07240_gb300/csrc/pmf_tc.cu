@@ -58,31 +58,43 @@ constexpr uint32_t kTmemCols = 128;
 //            operand planes of 128 x 128, one CTA per SM;
 //   C = 64 : 256 threads (4 quadrants x 2 column groups), planes of 64 x 64
 //            (the lanes >= 64 of every accumulator are garbage, so the A
-//            planes keep 64 rows), three CTAs per SM.
-// Dynamic shared memory: A operand planes, W operand planes, float32 staging
-// of C rows x (C + 4) floats (the padding makes row access conflict-free).
-//   C = 96 : 256 threads, planes of 96 x 96, and the staging tile shares the
-//            W region (alias): the weights are staged there before the first
-//            matrix is built, the spectrum is written there after the forward
-//            transforms and H0 is copied in again for the inverse; two CTAs
-//            per SM.
-// BF16X6 keeps three planes per operand: class 128 aliases the staging tile
-// on W as class 96 does (192 KiB of planes); class 64 fits three CTAs per SM.
-// In an aliased class the A region is also the scratch of the band-limited
-// re-alignment (C x (C + 2) floats) and of the multilinear gather (C x C).
+//            planes keep 64 rows);
+//   C = 96 : 256 threads, planes of 96 x 96.
+// Dynamic shared memory: the A operand planes, the W operand planes and a
+// float32 staging tile of C rows x (C + 4) floats (the padding makes row
+// access conflict-free).  Where three regions do not fit, the staging tile
+// shares a region:
+//   alias (class 96): the tile lies in the W region.  The weights are staged
+//     there before the first matrix is built, the spectrum is written there
+//     after the forward transforms and H0 is copied in again for the
+//     inverse; the multilinear gather and the band-limited re-alignment use
+//     the A region as scratch.  Two CTAs per SM.
+//   sina (class 128 in BF16X6, three planes per operand): the tile lies in
+//     the A region.  The weights arrive there and the spectrum is written
+//     there once the MMAs that read A have completed; each conversion of the
+//     tile into the A planes goes through registers (all threads read their
+//     part, synchronise, then write).  W is then free whenever the tile is
+//     live, so it holds I1 while the weights arrive, keeps H0 across the
+//     multiplier and is the re-alignments' scratch.  (In class 96 the
+//     registers of the in-place conversion cost more than the reload saves.)
 template <int P, int C>
 struct Smem {
   static constexpr int threads = C == 128 ? 512 : 256;
   static constexpr int sstr = C + 4;
-  static constexpr bool alias = C == 96 || (C == 128 && Fmt<P>::planes == 3);
+  static constexpr bool alias = C == 96;
+  static constexpr bool sina = C == 128 && Fmt<P>::planes == 3;
   static constexpr int offA = 0;
   static constexpr int abytes = Fmt<P>::planes * Lay<P, C, C>::plane;
-  static constexpr int ascr = alias ? C * (C + 2) * 4 : 0;
-  static constexpr int offW = ((abytes > ascr ? abytes : ascr) + 1023) / 1024 * 1024;
-  static constexpr int wbytes = Fmt<P>::planes * Lay<P, C>::wplane;
   static constexpr int sbytes = C * sstr * 4;
-  static constexpr int offS = alias ? offW : offW + wbytes;
-  static constexpr int bytes = alias ? offW + (wbytes > sbytes ? wbytes : sbytes) : offS + sbytes;
+  static constexpr int wbytes = Fmt<P>::planes * Lay<P, C>::wplane;
+  static constexpr int scr = C * (C + 2) * 4;   // band-limited re-alignment scratch
+  static constexpr int areg = alias ? (abytes > scr ? abytes : scr) : sina && sbytes > abytes ? sbytes : abytes;
+  static constexpr int wreg = alias ? (wbytes > sbytes ? wbytes : sbytes) : sina && scr > wbytes ? scr : wbytes;
+  static constexpr int offW = (areg + 1023) / 1024 * 1024;
+  static constexpr int offS = alias ? offW : sina ? offA : offW + (wreg + 1023) / 1024 * 1024;
+  static constexpr int bytes = alias || sina ? offW + wreg : offS + sbytes;
+  // work items (8 columns of a row) per thread of an in-place conversion
+  static constexpr int items = (C * C / 8 + threads - 1) / threads;
 };
 constexpr int kThreads = 512;                // the single-filter kernel (class 128)
 static_assert(Smem<PMF_PREC_BF16X6, 128>::bytes <= 200 * 1024, "class-128 BF16X6 planes and static state fit");
@@ -282,6 +294,32 @@ __device__ __forceinline__ void stage_to_operand(uint8_t* A, const float* S, int
     const int r = t % nr, c = (t / nr) * 8;
     const float* src = S + r * (C + 4) + c;
     store8<P, C, false, C>(A, r, c, *(const float4*)src, *(const float4*)(src + 4), s);
+  }
+}
+
+// The same in place, when the staging tile lies inside the A region: each of
+// the T threads reads its (at most kItems) row segments into registers, the
+// block synchronises, then the planes are written.  The caller makes the
+// tile's writes visible before and fences the planes for the MMA after.
+template <int P, int C, int kItems, int T>
+__device__ __forceinline__ void stage_to_operand_inplace(uint8_t* A, const float* S, int nr, int nc, float s) {
+  const int q8 = nc / 8, tot = nr * q8;
+  float4 v[kItems][2];
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) {
+    const int t = threadIdx.x + k * T;
+    if (t < tot) {
+      const int r = t % nr, c = (t / nr) * 8;
+      const float* src = S + r * (C + 4) + c;
+      v[k][0] = *(const float4*)src;
+      v[k][1] = *(const float4*)(src + 4);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) {
+    const int t = threadIdx.x + k * T;
+    if (t < tot) store8<P, C, false, C>(A, t % nr, (t / nr) * 8, v[k][0], v[k][1], s);
   }
 }
 
@@ -571,7 +609,9 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     c0 = g * per;
     ncol = nout - c0 < per ? (nout > c0 ? nout - c0 : 0) : per;
   };
+  constexpr bool kSina = Smem<P, C>::sina;      // staging tile inside the A region
   constexpr bool kAlias = Smem<P, C>::alias;    // staging tile in the W region
+  static_assert(!kSina || Smem<P, C>::items * kThreads * 8 >= C * C, "in-place conversion items");
   // only FP16 operands carry a scale (op_scale is 1 otherwise), so only they
   // need the block maxima of the stage outputs
   constexpr bool kScaled = P == PMF_PREC_FP16X3;
@@ -596,6 +636,12 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   auto sct = [&](int a) -> const float* {
     if constexpr (kPlan) return job.sctab[a];
     else return sh.sct[a];
+  };
+  // staging tile -> A planes by the whole block (in place in the sina layout)
+  auto to_operand = [&](int nr, int nc, float sc) {
+    if constexpr (kSina) stage_to_operand_inplace<P, C, Smem<P, C>::items, kThreads>(A, S, nr, nc, sc);
+    else if constexpr (kOut) stage_to_operand_out<P, C>(A, S, nr, nc, sc, threadIdx.x, kThreads);
+    else stage_to_operand<P, C>(A, S, nr, nc, sc, threadIdx.x, kThreads);
   };
   auto build_I = [&](int a, int Nm, int realign_, uint8_t* Wd) {
     if constexpr (kPlan) build_interp<P, C, 128>(job.plan->rows[a], Wd, Nm, job.sctab[a], sw, realign_, threadIdx.x, kThreads);
@@ -672,7 +718,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   float wps = 1.0f;   // pscale folded into the R1 operand
   if constexpr (kPlan) {
     fold = job.plan->wmax >= 0.0f && !fs.realign;
-    early = fold && !kAlias;
+    early = fold && !kAlias;   // W is free while the weights arrive
     if (early) {
       plan_coeffs(sh, job.plan, fs.l);
       build_I(1, N1, 0, W);
@@ -815,7 +861,9 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
           sh.gsc = (float)(fs.g / ((double)N0 * (double)N1));
         }
       }
-    } else if (job.do_time) {
+    } else if (job.do_time && !kSina) {
+      // (in the sina layout the tile is converted in place once the regrid
+      // is known, by the whole block: a re-alignment reads it first)
       if constexpr (kOut) stage_to_operand_out<P, C>(A, S, N0, N1, sa0, tid - 32, kThreads - 32);
       else stage_to_operand<P, C>(A, S, N0, N1, sa0 * wps, tid - 32, kThreads - 32);
     }
@@ -856,10 +904,9 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     }
     if (realign && sh.realign_mode == PMF_REALIGN_SHEAR) {
       // band-limited re-alignment in place on the staging tile
-      smax = shear_stage(sh, S, (float*)A, N0, N1, sct(0), sct(1));
+      smax = shear_stage(sh, S, (float*)(kSina ? W : A), N0, N1, sct(0), sct(1));   // scratch beside the tile
       sa_first = op_scale<P>(block_max(sh, smax, 0));
-      if constexpr (kOut) stage_to_operand_out<P, C>(A, S, N0, N1, sa_first, tid, kThreads);
-      else stage_to_operand<P, C>(A, S, N0, N1, sa_first, tid, kThreads);
+      to_operand(N0, N1, sa_first);
     } else if (realign) {
       // multilinear re-alignment: gather into the (free) W region, or the A
       // region when the staging tile lives in W, copy back
@@ -891,8 +938,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         smax = fmaxf(smax, fabsf(G[p]));
       }
       sa_first = op_scale<P>(block_max(sh, smax, 0));
-      if constexpr (kOut) stage_to_operand_out<P, C>(A, S, N0, N1, sa_first, tid, kThreads);
-      else stage_to_operand<P, C>(A, S, N0, N1, sa_first, tid, kThreads);
+      to_operand(N0, N1, sa_first);
     } else {
       // axis 1 by the first half of the block, axis 0 by the second
       const int a = tid < kThreads / 2 ? 1 : 0;
@@ -906,6 +952,9 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       }
     }
     __syncthreads();
+    // the sina layout converts the staged weights now (separable regrid)
+    if constexpr (kSina)
+      if (!realign) to_operand(N0, N1, sa_first * wps);
   }
 
   {
@@ -921,7 +970,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     }
     float inv_scale = 1.0f / (sa * sw);
 
-    if (!kAlias && job.fft) {
+    if (!kSina && !kAlias && job.fft) {
       // FFT form: the regrid of each axis stays a tensor-core GEMM whose
       // epilogue writes float32 to the staging tile; the four Hartley
       // transforms run in shared memory (fht_lines, scratch in W and A).
@@ -1015,8 +1064,8 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       int mat = -1;
       if (stage == 0 || stage == 4) mat = 1;
       if (stage == 2) mat = 0;
-      // the spectrum goes to the staging tile, which shares W: H0 again for V0
-      // once the tile has been read (below)
+      // the spectrum goes to the staging tile, which shares W in the alias
+      // layout: H0 again for V0 once the tile has been read (below)
       if (kAlias && stage == 3) mat = 0;
       if (tid == 0 && mat >= 0 && !(kAlias && stage == 3)) {
         const int Nm = mat == 0 ? N0 : N1;
@@ -1090,8 +1139,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
         psi_stage(sh, S, N0, N1, l, exact);
         __syncthreads();
         if constexpr (kScaled) sa = op_scale<P>(block_max(sh, stage_max<kThreads, C>(S, N1, N0), stage & 1));
-        if constexpr (kOut) stage_to_operand_out<P, C>(A, S, N1, N0, sa, tid, kThreads);
-        else stage_to_operand<P, C>(A, S, N1, N0, sa, tid, kThreads);
+        to_operand(N1, N0, sa);
       } else {
         if constexpr (kScaled) {
           float m = 0.0f;
