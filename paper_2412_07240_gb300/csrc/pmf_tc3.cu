@@ -110,6 +110,7 @@ struct Smem3 {
   int abort;
   float redf[2][16];
   DF redd[16][6];
+  float redw[16][10];   // per-warp float32 moment sums of the measurement kernel
 };
 
 __device__ __forceinline__ float block_max3(Smem3& sh, float v, int slot) {
@@ -405,8 +406,10 @@ __global__ void __launch_bounds__(kT) k_meas_apply3(const __grid_constant__ Batc
   float* out = cur ? job.buf0 : job.buf1;
   const float ps = (float)job.st->f.pscale;
   const float emin = __uint_as_float(*job.emin_bits);
-  DF s[6], s2[6];
-  for (int i = 0; i < 6; ++i) s[i] = s2[i] = DF{0.0f, 0.0f};
+  // the ten moment sums of this thread's points in float32 (a few quads)
+  float f[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) f[i] = 0.0f;
   for (long long q = blk * (long long)kT + threadIdx.x; q < g.P / 4; q += (long long)cnt * kT) {
     int j[3];
     unflat3(g, q * 4, j);
@@ -422,20 +425,40 @@ __global__ void __launch_bounds__(kT) k_meas_apply3(const __grid_constant__ Batc
     const float a1 = x.y + 2.0f * x.z + 3.0f * x.w;
     const float a2 = x.y + 4.0f * x.z + 9.0f * x.w;
     const float b2 = fmaf(u2, a0, a1);
-    s[0] = df_add1(s[0], a0);                                      // S0
-    s[1] = df_add1(s[1], a0 * u0);                                 // S1_0
-    s[2] = df_add1(s[2], a0 * u1);                                 // S1_1
-    s[3] = df_add1(s[3], b2);                                      // S1_2
-    s[4] = df_add1(s[4], a0 * u0 * u0);                            // S2_00
-    s[5] = df_add1(s[5], a0 * u0 * u1);                            // S2_01
-    s2[0] = df_add1(s2[0], b2 * u0);                               // S2_02
-    s2[1] = df_add1(s2[1], a0 * u1 * u1);                          // S2_11
-    s2[2] = df_add1(s2[2], b2 * u1);                               // S2_12
-    s2[3] = df_add1(s2[3], fmaf(u2, fmaf(u2, a0, 2.0f * a1), a2)); // S2_22
+    f[0] += a0;                                       // S0
+    f[1] = fmaf(a0, u0, f[1]);                        // S1_0
+    f[2] = fmaf(a0, u1, f[2]);                        // S1_1
+    f[3] += b2;                                       // S1_2
+    f[4] = fmaf(a0 * u0, u0, f[4]);                   // S2_00
+    f[5] = fmaf(a0 * u0, u1, f[5]);                   // S2_01
+    f[6] = fmaf(b2, u0, f[6]);                        // S2_02
+    f[7] = fmaf(a0 * u1, u1, f[7]);                   // S2_11
+    f[8] = fmaf(b2, u1, f[8]);                        // S2_12
+    f[9] += fmaf(u2, fmaf(u2, a0, 2.0f * a1), a2);    // S2_22
   }
-  block_partials3(sh, s, job.partials + (size_t)blk * 16);
+  // a warp's sums by a float32 tree (at most a few hundred points, so the
+  // tree's rounding stays near 5 ulp), then double-float across the warps:
+  // slots S0, S1[0..2], S2_00, S2_01 | S2_02, S2_11, S2_12, S2_22
+#pragma unroll
+  for (int i = 0; i < 10; ++i)
+    for (int o = 16; o; o >>= 1) f[i] += __shfl_xor_sync(0xffffffffu, f[i], o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < 10; ++i) sh.redw[warp][i] = f[i];
   __syncthreads();
-  block_partials3(sh, s2, job.partials + (size_t)blk * 16 + 6);
+  if (warp == 0) {
+    DF* out = job.partials + (size_t)blk * 16;
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+      DF v{lane < kT / 32 ? sh.redw[lane][i] : 0.0f, 0.0f};
+      for (int o = kT / 64; o; o >>= 1) {
+        DF b{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = df_add(v, b);
+      }
+      if (lane == 0) out[i] = v;
+    }
+  }
 }
 
 // Sum the per-CTA partials (16 double-float slots each: S0, S1[0..2], S2_00,
