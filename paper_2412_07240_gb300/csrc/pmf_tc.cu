@@ -282,6 +282,59 @@ __device__ __forceinline__ float meas_e(const MeasK& k, float u0, float u1) {
   return 0.5f * e;
 }
 
+// Exponent shift of a linear measurement without a pass over the grid: the
+// minimum over the grid box |u_m| <= a_m of the convex quadratic
+// e(u) = 1/2 (r0 - G u)^T Ri (r0 - G u), G = H M (the continuous form of
+// meas_e), by the interior minimiser or, outside the box, the minima along
+// its four edges.  The grid point nearest the minimiser lies at most half a
+// cell away per axis (on a face or at a corner, exactly on it along the
+// normal), so the grid's minimum exceeds the result by at most
+// (Hq00 + Hq11 + 2 |Hq01|) / 8, Hq = G^T Ri G; below 40 the shifted
+// likelihood exp(shift - e) neither overflows (shift <= e) nor leaves the
+// largest weights near float32's range limit.  Returns false beyond that
+// (sharp likelihoods on coarse grids: the caller takes the grid minimum).
+// Every thread computes the same float32 operations, so all hold the same
+// shift.  The shift cancels in the normalisation (eq. filt).
+__device__ __forceinline__ bool linear_eshift(const MeasK& k, float a0, float a1, float* shift) {
+  const bool two = k.nz > 1;
+  const float g00 = k.h00 * k.m00 + k.h01 * k.m10, g01 = k.h00 * k.m01 + k.h01 * k.m11;
+  const float g10 = two ? k.h10 * k.m00 + k.h11 * k.m10 : 0.0f, g11 = two ? k.h10 * k.m01 + k.h11 * k.m11 : 0.0f;
+  const float r00 = k.r00, r01 = two ? k.r01 : 0.0f;
+  const float q00 = k.ri00, q01 = two ? k.ri01 : 0.0f, q11 = two ? k.ri11 : 0.0f;
+  // Ri G (2 x 2), Hq = G^T Ri G, b = G^T Ri r0, c = 1/2 r0^T Ri r0
+  const float p00 = q00 * g00 + q01 * g10, p01 = q00 * g01 + q01 * g11;
+  const float p10 = q01 * g00 + q11 * g10, p11 = q01 * g01 + q11 * g11;
+  const float h00 = g00 * p00 + g10 * p10, h01 = g00 * p01 + g10 * p11, h11 = g01 * p01 + g11 * p11;
+  const float b0 = p00 * r00 + p10 * r01, b1 = p01 * r00 + p11 * r01;
+  const float c = 0.5f * (r00 * (q00 * r00 + q01 * r01) + r01 * (q01 * r00 + q11 * r01));
+  if (!((h00 + h11 + 2.0f * fabsf(h01)) * 0.125f <= 40.0f)) return false;
+  auto ev = [&](float u0, float u1) { return 0.5f * (h00 * u0 * u0 + 2.0f * h01 * u0 * u1 + h11 * u1 * u1) - b0 * u0 - b1 * u1 + c; };
+  const float det = h00 * h11 - h01 * h01;
+  if (det > 1e-6f * (h00 * h11 + 1e-30f)) {
+    const float u0 = (h11 * b0 - h01 * b1) / det, u1 = (h00 * b1 - h01 * b0) / det;
+    if (fabsf(u0) <= a0 && fabsf(u1) <= a1) {
+      *shift = ev(u0, u1);
+      return isfinite(*shift);
+    }
+  }
+  // minimum on the boundary: each edge is a 1-D quadratic in the free coordinate
+  float best = INFINITY;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int fixed = e >> 1;                        // axis held at +-a
+    const float uf = (e & 1) ? (fixed ? a1 : a0) : -(fixed ? a1 : a0);
+    const float af = fixed ? a0 : a1;                // range of the free coordinate
+    const float hoo = fixed ? h00 : h11, hfo = h01, bo = fixed ? b0 : b1;
+    float t = hoo > 0.0f ? (bo - hfo * uf) / hoo : 0.0f;
+    t = fminf(fmaxf(t, -af), af);
+    float v = fixed ? ev(t, uf) : ev(uf, t);
+    if (!(hoo > 0.0f)) v = fminf(fixed ? ev(-af, uf) : ev(uf, -af), fixed ? ev(af, uf) : ev(uf, af));
+    best = fminf(best, v);
+  }
+  *shift = best;
+  return isfinite(best);
+}
+
 // Staging rows r < nr, columns < nc (a multiple of 8) -> operand planes
 // (scaled by s).  Consecutive threads take consecutive rows, eight columns
 // each: in the core-matrix layout 8 consecutive rows of 8 columns are 128
@@ -763,6 +816,12 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
       emin = fminf(emin, fminf(fminf(e.x, e.y), fminf(e.z, e.w)));
     }
     emin = block_min(sh, emin, 0);
+    // the batch front kernel's shift for a linear measurement (same steps as
+    // there; the shift cancels in the normalisation)
+    if (mk.kind == PMF_MEAS_LINEAR) {
+      float shift;
+      if (linear_eshift(mk, 0.5f * (N0 - 1), 0.5f * (N1 - 1), &shift)) emin = shift;
+    }
     if (__syncthreads_or(!mbar_wait(mb_tma, ph_tma))) {
       if (tid == 0) fs.status = PMF_ERR_TIMEOUT;
       goto done;
@@ -1297,13 +1356,18 @@ __global__ void __launch_bounds__(kFrontThreads, 6) k_front2d(const FilterSlot* 
     __syncthreads();
     const MeasK mk = meas_k(sh);
     float emin = INFINITY;
-    for (int t = tid; t < np4; t += kT) {
-      const int r = (int)(((float)t + 0.5f) * rq1), c = (t - r * q1) * 4;
-      const float u0 = r - 0.5f * (N0 - 1), u1 = c - 0.5f * (N1 - 1);
-      emin = fminf(emin, fminf(fminf(meas_e(mk, u0, u1), meas_e(mk, u0, u1 + 1.0f)),
-                               fminf(meas_e(mk, u0, u1 + 2.0f), meas_e(mk, u0, u1 + 3.0f))));
+    // a linear measurement takes its exponent shift from the box minimum of
+    // the quadratic; otherwise (or for a too sharp one) a pass over the grid
+    if (!(mk.kind == PMF_MEAS_LINEAR && linear_eshift(mk, 0.5f * (N0 - 1), 0.5f * (N1 - 1), &emin))) {
+      emin = INFINITY;
+      for (int t = tid; t < np4; t += kT) {
+        const int r = (int)(((float)t + 0.5f) * rq1), c = (t - r * q1) * 4;
+        const float u0 = r - 0.5f * (N0 - 1), u1 = c - 0.5f * (N1 - 1);
+        emin = fminf(emin, fminf(fminf(meas_e(mk, u0, u1), meas_e(mk, u0, u1 + 1.0f)),
+                                 fminf(meas_e(mk, u0, u1 + 2.0f), meas_e(mk, u0, u1 + 3.0f))));
+      }
+      emin = block_min(sh, emin, 0);
     }
-    emin = block_min(sh, emin, 0);
     const float ps = (float)fs.pscale;
     Moments mo;
     mo.zero();

@@ -23,9 +23,12 @@ def _c4(count, epochs, seed=4):
     return cfgs, meas, dt, z
 
 
-# a last-bit difference of the inputs re-rounds the 16-bit (or TF32) operand
-# splits: the two agree to the precision's own resolution
-AGREE = {"fp16x3": 1e-6, "bf16x6": 1e-6, "bf16x3": 1e-4, "tf32": 3e-2}
+# a last-bit difference of the inputs (the front kernel recomputes the
+# likelihood exponents, which the compiler may contract differently) re-rounds
+# the 16-bit (or TF32) operand splits; the weights far from the mass are the
+# transforms' rounding noise (~1e-7 of the peak), different in the two: they
+# agree to twice the precision's own resolution, each within the oracle bar
+AGREE = {"fp16x3": 2e-6, "bf16x6": 2e-6, "bf16x3": 1e-4, "tf32": 3e-2}
 
 
 @pytest.mark.parametrize("prec,psi", [("fp16x3", "euler"), ("bf16x6", "euler"), ("bf16x3", "euler"),

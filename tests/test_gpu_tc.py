@@ -128,4 +128,4 @@ def test_shear_realignment_batch_equals_single():
     Pb, cb, Mb = b.pdf(0)
     Ps, cs, Ms = g.pdf()
     assert np.array_equal(cb, cs) and np.array_equal(Mb, Ms)
-    assert rel_l1(Pb, Ps) <= 1e-6, rel_l1(Pb, Ps)
+    assert rel_l1(Pb, Ps) <= 2e-6, rel_l1(Pb, Ps)
