@@ -69,20 +69,22 @@ constexpr uint32_t kTmemCols = 128;
 //     after the forward transforms and H0 is copied in again for the
 //     inverse; the multilinear gather and the band-limited re-alignment use
 //     the A region as scratch.  Two CTAs per SM.
-//   sina (class 128 in BF16X6, three planes per operand): the tile lies in
-//     the A region.  The weights arrive there and the spectrum is written
+//   sina (class 128 in BF16X6, three planes per operand, in the planned
+//     kernel; the single-filter kernel keeps the alias, where the warps that
+//     convert the weights run beside warp 0's float64 frame decision): the
+//     tile lies in the A region.  The weights arrive there and the spectrum is written
 //     there once the MMAs that read A have completed; each conversion of the
 //     tile into the A planes goes through registers (all threads read their
 //     part, synchronise, then write).  W is then free whenever the tile is
 //     live, so it holds I1 while the weights arrive, keeps H0 across the
 //     multiplier and is the re-alignments' scratch.  (In class 96 the
 //     registers of the in-place conversion cost more than the reload saves.)
-template <int P, int C>
+template <int P, int C, bool kPlanned = true>
 struct Smem {
   static constexpr int threads = C == 128 ? 512 : 256;
   static constexpr int sstr = C + 4;
-  static constexpr bool alias = C == 96;
-  static constexpr bool sina = C == 128 && Fmt<P>::planes == 3;
+  static constexpr bool alias = C == 96 || (!kPlanned && C == 128 && Fmt<P>::planes == 3);
+  static constexpr bool sina = kPlanned && C == 128 && Fmt<P>::planes == 3;
   static constexpr int offA = 0;
   static constexpr int abytes = Fmt<P>::planes * Lay<P, C, C>::plane;
   static constexpr int sbytes = C * sstr * 4;
@@ -97,7 +99,8 @@ struct Smem {
   static constexpr int items = (C * C / 8 + threads - 1) / threads;
 };
 constexpr int kThreads = 512;                // the single-filter kernel (class 128)
-static_assert(Smem<PMF_PREC_BF16X6, 128>::bytes <= 200 * 1024, "class-128 BF16X6 planes and static state fit");
+static_assert(Smem<PMF_PREC_BF16X6, 128>::bytes <= 200 * 1024 && Smem<PMF_PREC_BF16X6, 128, false>::bytes <= 200 * 1024,
+              "class-128 BF16X6 planes and static state fit");
 
 // One filter launched alone: everything by value in the kernel parameters.
 struct FusedJob {
@@ -651,7 +654,8 @@ __device__ __forceinline__ void plan_coeffs(SH& sh, const BatchPlan* pl, int l) 
 
 template <int P, bool kOut, bool kPlan = false, int C = 128>
 __device__ void fused2d(const FusedView& job, uint8_t* smem) {
-  using SH = SharedT<kPlan ? Smem<P, C>::threads : kThreads, C, !kPlan>;
+  using SM = Smem<P, C, kPlan>;
+  using SH = SharedT<kPlan ? SM::threads : kThreads, C, !kPlan>;
   constexpr int kThreads = SH::kT, kSStr = SH::kStr, kGroups = kThreads / 128;
   constexpr int kNV = C / kGroups / 4;          // float4 accumulator columns per thread
   // columns [c0, c0 + ncol) of an accumulator of nout columns (a multiple of
@@ -662,9 +666,9 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
     c0 = g * per;
     ncol = nout - c0 < per ? (nout > c0 ? nout - c0 : 0) : per;
   };
-  constexpr bool kSina = Smem<P, C>::sina;      // staging tile inside the A region
-  constexpr bool kAlias = Smem<P, C>::alias;    // staging tile in the W region
-  static_assert(!kSina || Smem<P, C>::items * kThreads * 8 >= C * C, "in-place conversion items");
+  constexpr bool kSina = SM::sina;      // staging tile inside the A region
+  constexpr bool kAlias = SM::alias;    // staging tile in the W region
+  static_assert(!kSina || SM::items * kThreads * 8 >= C * C, "in-place conversion items");
   // only FP16 operands carry a scale (op_scale is 1 otherwise), so only they
   // need the block maxima of the stage outputs
   constexpr bool kScaled = P == PMF_PREC_FP16X3;
@@ -678,9 +682,9 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   const int tid = threadIdx.x, warp = tid >> 5;
   const int row = tid & 127, cg = tid >> 7;     // TMEM lane and column group of this thread
   const int N0 = job.N0, N1 = job.N1;
-  uint8_t* A = smem + Smem<P, C>::offA;
-  uint8_t* W = smem + Smem<P, C>::offW;
-  float* S = (float*)(smem + Smem<P, C>::offS);
+  uint8_t* A = smem + SM::offA;
+  uint8_t* W = smem + SM::offW;
+  float* S = (float*)(smem + SM::offS);
   const uint32_t mb_mma = su32(&sh.mbar_mma), mb_tma = su32(&sh.mbar_tma);
   uint32_t ph_mma = 0, ph_tma = 0;
   const float sw = P == PMF_PREC_FP16X3 ? 16384.0f : 1.0f;   // scale of the matrix operands
@@ -692,7 +696,7 @@ __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   };
   // staging tile -> A planes by the whole block (in place in the sina layout)
   auto to_operand = [&](int nr, int nc, float sc) {
-    if constexpr (kSina) stage_to_operand_inplace<P, C, Smem<P, C>::items, kThreads>(A, S, nr, nc, sc);
+    if constexpr (kSina) stage_to_operand_inplace<P, C, SM::items, kThreads>(A, S, nr, nc, sc);
     else if constexpr (kOut) stage_to_operand_out<P, C>(A, S, nr, nc, sc, threadIdx.x, kThreads);
     else stage_to_operand<P, C>(A, S, nr, nc, sc, threadIdx.x, kThreads);
   };
@@ -1550,13 +1554,13 @@ void with_format(int precision, F&& f) {
 void launch_fused(int precision, const FusedJob& job, cudaStream_t s) {
   with_format(precision, [&](auto fmt) {
     constexpr int P = decltype(fmt)::value;
-    k_fused2d<P><<<1, kThreads, Smem<P, 128>::bytes, s>>>(job);
+    k_fused2d<P><<<1, kThreads, Smem<P, 128, false>::bytes, s>>>(job);
   });
 }
 
 template <int P>
 void set_smem_limits() {
-  cudaFuncSetAttribute(k_fused2d<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<P, 128>::bytes);
+  cudaFuncSetAttribute(k_fused2d<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<P, 128, false>::bytes);
   cudaFuncSetAttribute(k_fused2d_planned<P, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<P, 128>::bytes);
   cudaFuncSetAttribute(k_fused2d_planned<P, 96>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<P, 96>::bytes);
   cudaFuncSetAttribute(k_fused2d_planned<P, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<P, 64>::bytes);
