@@ -417,6 +417,9 @@ struct pmf_batch {
   std::vector<void*> tables;          // per distinct N (and size class)
   std::vector<double> tau;            // tau of the constants resident for each filter
   std::vector<int> cls;               // size class of each filter's transform kernel
+  std::vector<int> rank;              // position of each filter in the launch order (class, then size)
+  std::vector<int> cnt;               // counting-sort scratch (count + 1)
+  std::vector<StepItem> sorted;       // counting-sort output
   int* d_ids = nullptr;               // filter ids of a moments/status query
   double* d_gather = nullptr;         // 8 doubles per queried filter
   int* h_ids = nullptr;               // pinned staging of the query
@@ -609,6 +612,21 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
     free_batch(b);
     return PMF_ERR_CUDA;
   }
+  // launch order: size class 128 first, then 96, then 64 (one transform
+  // kernel per range); within a class larger grids first (the hardware hands
+  // CTAs out in order, so the longest run first and the tail is made of
+  // small filters); ties by id.  Each step sorts its items by this rank.
+  {
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      return b->cls[x] != b->cls[y] ? b->cls[x] > b->cls[y] : b->npts[x] > b->npts[y];
+    });
+    b->rank.assign(count, 0);
+    for (int r = 0; r < count; ++r) b->rank[order[r]] = r;
+    b->cnt.assign(count + 1, 0);
+    b->sorted.resize(count);
+  }
   *out = b;
   return PMF_OK;
 }
@@ -650,16 +668,18 @@ int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_
       b->tau[id] = tau;
     }
   }
-  // size class 128 first, then 96, then 64 (one transform kernel per range);
-  // within a class larger grids first: the hardware hands CTAs out in order,
-  // so the longest run first and the tail is made of small filters
+  // items in launch order (the rank of each filter, fixed at creation): a
+  // stable counting sort, O(k + count) per step (a filter may be listed twice)
   auto cls = [&](const StepItem& x) { return b->cls[x.slot]; };
-  std::vector<StepItem> sorted(items, items + k);
-  std::stable_sort(sorted.begin(), sorted.end(), [&](const StepItem& x, const StepItem& y) {
-    const int cx = cls(x), cy = cls(y);
-    return cx != cy ? cx > cy : b->npts[x.slot] > b->npts[y.slot];
-  });
-  std::copy(sorted.begin(), sorted.end(), items);
+  {
+    std::vector<int>& c = b->cnt;
+    std::fill(c.begin(), c.end(), 0);
+    for (int i = 0; i < k; ++i) ++c[b->rank[items[i].slot] + 1];
+    for (int r = 0; r < b->count; ++r) c[r + 1] += c[r];
+    if ((int)b->sorted.size() < k) b->sorted.resize(k);
+    for (int i = 0; i < k; ++i) b->sorted[c[b->rank[items[i].slot]]++] = items[i];
+    std::copy(b->sorted.begin(), b->sorted.begin() + k, items);
+  }
   int k128 = 0, k96 = 0;
   while (k128 < k && cls(items[k128]) == 128) ++k128;
   while (k128 + k96 < k && cls(items[k128 + k96]) == 96) ++k96;
