@@ -157,3 +157,26 @@ def test_full_c4_workload_sampled():
         assert rel_l1(P, o.P) <= 1e-5, (i, rel_l1(P, o.P))
         checked += 1
     assert checked == 4
+
+
+@pytest.mark.parametrize("sigma", [0.1, 1e-3])
+def test_linear_measurement_shift_paths(sigma):
+    """A linear measurement's exponent shift: the box minimum of its quadratic
+    (sigma = 0.1, the workload's), or the pass over the grid when the
+    likelihood is sharper than a node (sigma = 1e-3: the box minimum may lie
+    more than 40 below the grid's).  Measurement-only steps against the
+    oracle's Bayes update (eq. filt); the shift cancels in the normalisation."""
+    from oracle.filter import OracleFilter
+    from paper_2412_07240_gb300 import Batch
+    from workloads import MeasModel
+    cfgs, _, dt, z = _c4(6, 1, seed=11)
+    meas = MeasModel("linear", R=sigma ** 2 * np.eye(2), H=np.eye(2))
+    b = Batch(cfgs, [meas] * len(cfgs))
+    zz = np.array([c.m0 + 0.3 for c in cfgs])
+    b.step(np.arange(len(cfgs)), zz, 0.0)
+    for i, c in enumerate(cfgs):
+        o = OracleFilter(c)
+        o.meas_update(meas, zz[i])
+        P, cc, M = b.pdf(i)
+        assert np.allclose(cc, o.c, rtol=0, atol=1e-12) and np.allclose(M, o.M, rtol=1e-12, atol=0)
+        assert rel_l1(P, o.P) <= 1e-5, (i, rel_l1(P, o.P))
