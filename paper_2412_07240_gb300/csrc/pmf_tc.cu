@@ -69,10 +69,11 @@ constexpr uint32_t kTmemCols = 128;
 //     after the forward transforms and H0 is copied in again for the
 //     inverse; the multilinear gather and the band-limited re-alignment use
 //     the A region as scratch.  Two CTAs per SM.
-//   sina (class 128 in BF16X6, three planes per operand, in the planned
-//     kernel; the single-filter kernel keeps the alias, where the warps that
-//     convert the weights run beside warp 0's float64 frame decision): the
-//     tile lies in the A region.  The weights arrive there and the spectrum is written
+//   sina (classes 128 and 64 in BF16X6, three planes per operand, in the
+//     planned kernel; the single-filter kernel keeps the alias, where the
+//     warps that convert the weights run beside warp 0's float64 frame
+//     decision): the tile lies in the A region (class 64: four CTAs per SM
+//     instead of three).  The weights arrive there and the spectrum is written
 //     there once the MMAs that read A have completed; each conversion of the
 //     tile into the A planes goes through registers (all threads read their
 //     part, synchronise, then write).  W is then free whenever the tile is
@@ -84,7 +85,7 @@ struct Smem {
   static constexpr int threads = C == 128 ? 512 : 256;
   static constexpr int sstr = C + 4;
   static constexpr bool alias = C == 96 || (!kPlanned && C == 128 && Fmt<P>::planes == 3);
-  static constexpr bool sina = kPlanned && C == 128 && Fmt<P>::planes == 3;
+  static constexpr bool sina = kPlanned && (C == 128 || C == 64) && Fmt<P>::planes == 3;
   static constexpr int offA = 0;
   static constexpr int abytes = Fmt<P>::planes * Lay<P, C, C>::plane;
   static constexpr int sbytes = C * sstr * 4;
