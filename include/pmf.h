@@ -218,11 +218,13 @@ void pmf_destroy(pmf_ctx* ctx);
 
 /* ---- batches of independent filters ------------------------------------------
  * A batch holds many filters resident on the device (weights, frames, moments,
- * model constants) and advances any subset of them with one kernel launch per
- * epoch, one CTA per filter, larger grids scheduled first.  All filters of a
- * batch share n_x = 2 and the precision of cfgs[0] (a tensor-core format);
- * grid sizes may differ (multiples of 16 up to 128).  The per-filter
- * semantics are those of pmf_step. */
+ * model constants) and advances any subset of them per epoch with one CUDA
+ * graph: a front kernel (measurement update, moments, float64 regrid
+ * decision; one CTA per filter) and one transform kernel per size class
+ * (largest axis up to 64, 96 or 128; one CTA per filter, larger grids
+ * scheduled first).  All filters of a batch share n_x = 2 and the precision
+ * of cfgs[0] (a tensor-core format); grid sizes may differ (multiples of 16
+ * up to 128).  The per-filter semantics are those of pmf_step. */
 typedef struct pmf_batch pmf_batch;
 
 /* Create `count` filters from cfgs[i] with measurement models models[i] (z is
@@ -237,9 +239,9 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
  * z[i*PMF_MAX_NZ ...] (skipped when do_meas[i] == 0; do_meas may be NULL = all)
  * then time update over taus[i] (skipped when taus[i] == 0).  Asynchronous;
  * ids must be distinct within a call.  Model constants are recomputed on the
- * host only for filters whose tau changed.  The item upload and the single
- * batch kernel run as a CUDA graph, captured on the first epoch of each
- * batch size and replayed afterwards. */
+ * host only for filters whose tau changed.  The item upload and the batch
+ * kernels run as a CUDA graph, captured on the first epoch of each batch
+ * size (and split into size classes) and replayed afterwards. */
 int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_meas,
                    const double* taus, int k);
 
@@ -285,9 +287,10 @@ int pmf_fdm_transition(const double* P_in, double* P_out, double* work, int N, i
  * next measurement (pmf_step semantics).  Requests queue per filter; whenever
  * fewer than PMF_SERVE_INFLIGHT batches are on the device the server forms a
  * batch from the head request of every idle filter that has one: the 1-D
- * filters in one launch of the 1-D kernel, the 2-D filters in one launch of
- * the fused batch kernel, the 3-D filters through their pipelines on the third
- * stream, all three overlapping.  A filter has at most one request on the
+ * filters in one launch of the 1-D kernel, the 2-D filters through the
+ * batched 2-D kernels (front kernel and size-class transform kernels), the
+ * 3-D filters through their pipelines on the third stream, all three
+ * overlapping.  A filter has at most one request on the
  * device, and each runs in its own CTAs, so its results do not depend on what
  * else shares the batch.  A tau needing more than PMF_MAX_SUBSTEPS sub-steps
  * runs as consecutive time updates of at most that many.
