@@ -1298,9 +1298,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused2d(const __grid_constant__
 // axes, handed to the planned transform kernel through the filter's plan.
 // The steps are those of the fused kernel (the exponents are recomputed
 // instead of stored).
-constexpr int kFrontThreads = 128;   // four warps: six or more CTAs (filters) share an SM
+constexpr int kFrontThreads = 128;   // four warps, 48 registers: ten CTAs (filters) share an SM
 
-__global__ void __launch_bounds__(kFrontThreads, 6) k_front2d(const FilterSlot* __restrict__ slots,
+__global__ void __launch_bounds__(kFrontThreads, 10) k_front2d(const FilterSlot* __restrict__ slots,
                                                               const StepItem* __restrict__ items,
                                                               const TimeConsts* __restrict__ tcs) {
   __shared__ SharedT<kFrontThreads, 128, true, false> sh;
