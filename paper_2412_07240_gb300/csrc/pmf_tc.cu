@@ -145,7 +145,6 @@ struct TcHolder<false> {};
 template <int T, int C, bool kTc, bool kRows = kTc>
 struct SharedT : TcHolder<kTc> {
   static constexpr int kT = T;
-  static constexpr int kC = C;
   static constexpr int kStr = C + 4;   // staging row stride (floats)
   MeasParams mp;
   FrameState fs;           // working copy of the filter's frame state
@@ -169,7 +168,6 @@ struct SharedT : TcHolder<kTc> {
   RegridRowsT<kRows ? C : 1> rows[2];
   float sct[2][kRows ? 2 * (2 * C + 1) : 1];
 };
-using Shared = SharedT<512, 128, true>;
 
 // What the batch front kernel hands to the planned transform kernel for one
 // filter and epoch: whether the time update runs, the pending frame after the
@@ -560,16 +558,9 @@ __device__ void psi_stage(const SH& sh, float* S, int N0, int N1, int l, int exa
   }
 }
 
-// kPlan: the planned transform kernel of a batch (time update only; the
-// measurement update, moments, frame decision, sub-step coefficients and
-// regrid rows come from the front kernel through job.plan).  C: size class.
 // ---- shared-memory form of the per-axis Hartley transforms ------------------
 // (the FFT form of steps 1 and 5 of the Sec. V-B algorithm, an alternative to
 // the tensor-core contraction for axis sizes 2^a 3^b)
-__device__ __forceinline__ bool fht_size_ok(int N) {
-  while (N % 3 == 0) N /= 3;
-  return N >= 2 && (N & (N - 1)) == 0;
-}
 
 // e^{-2 pi i a / N}, 0 <= a < N, from the (cos, sin)(pi m / N) table (m = -N..N).
 __device__ __forceinline__ float2 twiddle(const float* sct, int a, int N) {
@@ -653,6 +644,11 @@ __device__ __forceinline__ void plan_coeffs(SH& sh, const BatchPlan* pl, int l) 
   }
 }
 
+// One filter's epoch in one CTA (size class C).  kOut: the single-filter
+// kernel (helpers called from several places out of line).  kPlan: the
+// planned transform kernel of a batch (time update only; the measurement
+// update, moments, frame decision, sub-step coefficients and regrid rows come
+// from the front kernel through job.plan).
 template <int P, bool kOut, bool kPlan = false, int C = 128>
 __device__ void fused2d(const FusedView& job, uint8_t* smem) {
   using SM = Smem<P, C, kPlan>;
