@@ -181,7 +181,7 @@ TRAFFIC_C2 = 345344.0
 # DRAM bytes per grid point of one C4 epoch (the four kernels' dram__bytes_read
 # + dram__bytes_write, one ncu capture of the full batch), per format; absent
 # where not captured for the current kernels
-TRAFFIC_C4_PER_POINT = {"bf16x6": 12.983, "fp16x3": 13.034}
+TRAFFIC_C4_PER_POINT = {"bf16x6": 13.373, "fp16x3": 13.434}
 BATCH_KERNEL = "k_front2d + k_fused2d_planned<128|96|64> (one graph per epoch)"
 
 
