@@ -1259,7 +1259,19 @@ void tc3_stage_free(Tc3Stage* g) {
 
 namespace {
 
-int meas_blocks(long long P) { return (int)std::min<long long>(1024, (P / 4 + kT - 1) / kT); }
+// CTAs of the measurement kernels of one filter: one per SM at most, so that
+// each thread takes a few quads (the block reductions and the frame kernel's
+// sum over the per-CTA partials are paid per CTA)
+int meas_blocks(long long P) {
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+      nsm = 128;
+  }
+  return (int)std::min<long long>(std::min(nsm, 1024), (P / 4 + kT - 1) / kT);
+}
 
 template <int P>
 void launch_pipes(const Batch3& b, const int* tot, cudaStream_t s) {
