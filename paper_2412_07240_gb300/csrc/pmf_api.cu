@@ -729,8 +729,9 @@ namespace {
 int batch_query(pmf_batch* b, const int* ids, int k) {
   for (int i = 0; i < k; ++i)
     if (ids[i] < 0 || ids[i] >= b->count) return PMF_ERR_ARG;
-  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return PMF_ERR_CUDA;
-  if (k == 0) return PMF_OK;
+  if (k == 0) return cudaStreamSynchronize(b->stream) == cudaSuccess ? PMF_OK : PMF_ERR_CUDA;
+  // the copies and the gather follow the batch's epochs on its stream; the
+  // previous query ended with a synchronisation, so the pinned ids are free
   std::memcpy(b->h_ids, ids, sizeof(int) * k);
   if (cudaMemcpyAsync(b->d_ids, b->h_ids, sizeof(int) * k, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
     return PMF_ERR_CUDA;
