@@ -23,8 +23,11 @@
 //
 // Precisions: FP16X3 / BF16X3 split each operand into hi + lo 16-bit planes and
 // issue hi*hi + hi*lo + lo*hi (FP32 accumulate); FP16 operands carry a
-// power-of-two scale per stage (max |value| -> 2^14).  TF32 issues one
-// kind::tf32 product on float32 planes.
+// power-of-two scale per stage (max |value| -> 2^14).  BF16X6 (2-D filters
+// only) splits each operand into hi + mid + lo BF16 planes and issues the six
+// products of combined order at most two, smallest first (hi*lo, lo*hi,
+// mid*mid, hi*mid, mid*hi, hi*hi).  TF32 issues one kind::tf32 product on
+// float32 planes.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
