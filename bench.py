@@ -582,7 +582,9 @@ def bench_batch(args, ws, rank, pg):
                        "precision": args.precision, "l2": "flushed between timed steps",
                        "parallelism": f"replicas x{ws}"},
             "e2e": {"value": ws * P.sum() / (e2e_ms * 1e-3), "unit": UNIT,
-                    "h2d_bytes_per_step": int(len(cfgs) * 24), "d2h_bytes_per_step": int(len(cfgs) * 48),
+                    # copied per filter: a 32-byte step item (slot, flags, z[3]) and a
+                    # 4-byte id in, a 64-byte gather record (mean, cov, status, pad) out
+                    "h2d_bytes_per_step": int(len(cfgs) * 36), "d2h_bytes_per_step": int(len(cfgs) * 64),
                     "ms_per_step": e2e_ms},
             "gpu_launches": int(launches),
             "fp64_gpu": {"value": fp64_rate, "unit": UNIT, "filters_timed": int(len(sub))},
@@ -730,7 +732,8 @@ def bench_serve(args, ws, rank, pg):
             "capacity": capacity,
             "e2e": {"value": value, "unit": UNIT,
                     "h2d_bytes_per_step": int(st["mean_batch"] * (STEP_ITEM_BYTES + TIME_CONSTS_BYTES)),
-                    "d2h_bytes_per_step": 0, "note": "the replay is end to end: requests from host arrays"},
+                    "d2h_bytes_per_step": 0, "note": "the replay is end to end: requests from host arrays; the results stay resident "
+                            "(read on demand), so nothing is copied back per batch"},
             "gpu_launches": int(st["launches"]),
             "fp64_gpu": {"value": f64_pts / f64_s if f64_s > 0 else None, "unit": UNIT,
                          "sample": "8 1-D, 8 2-D, 3 3-D filters, plain float64 path, one update each"},
