@@ -325,8 +325,10 @@ class Batch:
         zz = np.zeros((k, MAX_NZ))
         if z is not None:
             z = np.asarray(z, dtype=np.float64).reshape(k, -1)
-            zz[:, :z.shape[1]] = z
-        taus = np.ascontiguousarray(np.broadcast_to(np.asarray(taus, dtype=np.float64), (k,)))
+            for j in range(z.shape[1]):   # column by column: a third of one strided 2-D copy
+                zz[:, j] = z[:, j]
+        t = np.asarray(taus, dtype=np.float64)
+        taus = np.full(k, float(t)) if t.ndim == 0 else np.ascontiguousarray(np.broadcast_to(t, (k,)))
         dm = None if do_meas is None else np.ascontiguousarray(do_meas, dtype=np.int32)
         rc = self._lib.pmf_batch_step(self._h, _iptr(ids), _dptr(zz), None if dm is None else _iptr(dm),
                                       _dptr(taus), k)

@@ -418,8 +418,7 @@ struct pmf_batch {
   std::vector<double> tau;            // tau of the constants resident for each filter
   std::vector<int> cls;               // size class of each filter's transform kernel
   std::vector<int> rank;              // position of each filter in the launch order (class, then size)
-  std::vector<int> cnt;               // counting-sort scratch (count + 1)
-  std::vector<StepItem> sorted;       // counting-sort output
+  std::vector<int> cnt;               // counting-sort positions (count + 1)
   int* d_ids = nullptr;               // filter ids of a moments/status query
   double* d_gather = nullptr;         // 8 doubles per queried filter
   int* h_ids = nullptr;               // pinned staging of the query
@@ -625,7 +624,6 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
     b->rank.assign(count, 0);
     for (int r = 0; r < count; ++r) b->rank[order[r]] = r;
     b->cnt.assign(count + 1, 0);
-    b->sorted.resize(count);
   }
   *out = b;
   return PMF_OK;
@@ -648,11 +646,18 @@ int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_
   TimeConsts* stage = b->h_tc[p];
   int nchanged = 0;
   std::vector<int> changed;
+  // items in launch order (the rank of each filter, fixed at creation): a
+  // counting sort over the ranks of the listed ids, each item written once,
+  // straight into its position (ids are distinct, so the order is unique)
+  std::vector<int>& pos = b->cnt;
+  std::fill(pos.begin(), pos.end(), 0);
+  for (int i = 0; i < k; ++i) ++pos[b->rank[ids[i]] + 1];
+  for (int r = 0; r < b->count; ++r) pos[r + 1] += pos[r];
   for (int i = 0; i < k; ++i) {
     const int id = ids[i];
     const double tau = taus[i];
     const bool meas = !do_meas || do_meas[i];
-    StepItem& it = items[i];
+    StepItem& it = items[pos[b->rank[id]]++];
     it.slot = id;
     it.flags = (meas ? 1 : 0) | (tau > 0 ? 2 : 0);
     for (int j = 0; j < PMF_MAX_NZ; ++j) it.z[j] = meas ? z[(size_t)i * PMF_MAX_NZ + j] : 0.0;
@@ -668,18 +673,7 @@ int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_
       b->tau[id] = tau;
     }
   }
-  // items in launch order (the rank of each filter, fixed at creation): a
-  // stable counting sort, O(k + count) per step (a filter may be listed twice)
   auto cls = [&](const StepItem& x) { return b->cls[x.slot]; };
-  {
-    std::vector<int>& c = b->cnt;
-    std::fill(c.begin(), c.end(), 0);
-    for (int i = 0; i < k; ++i) ++c[b->rank[items[i].slot] + 1];
-    for (int r = 0; r < b->count; ++r) c[r + 1] += c[r];
-    if ((int)b->sorted.size() < k) b->sorted.resize(k);
-    for (int i = 0; i < k; ++i) b->sorted[c[b->rank[items[i].slot]]++] = items[i];
-    std::copy(b->sorted.begin(), b->sorted.begin() + k, items);
-  }
   int k128 = 0, k96 = 0;
   while (k128 < k && cls(items[k128]) == 128) ++k128;
   while (k128 + k96 < k && cls(items[k128 + k96]) == 96) ++k96;
