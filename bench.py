@@ -548,7 +548,7 @@ def bench_batch(args, ws, rank, pg):
     # end to end: measurements from host, moments back, every epoch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ne = min(5, args.steps)
+    ne = min(20, args.steps)
     for k in range(ne):
         b.step(ids, z[:, args.warmup + k], dt)
         b.moments(strict=False)
