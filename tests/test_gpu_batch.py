@@ -7,6 +7,8 @@
 * the full 4096-filter workload in the benchmarked launch configuration keeps
   unit mass, finite weights and PSD covariances, and its sampled filters match
   the oracle;
+* per-item step options (shuffled subsets, measurement masks, changing taus,
+  tau = 0) equal the same filters run alone;
 * stepping a subset leaves the others untouched; admission by a memory budget.
 """
 import numpy as np
@@ -90,6 +92,52 @@ def test_subset_step_leaves_others():
     for i in range(6):
         same = np.array_equal(b.pdf(i)[0], before[i])
         assert same == (i not in (1, 4))
+
+
+def test_step_options_match_single_filters():
+    """The per-item options of a batch step against the same filters run alone:
+    ids in shuffled order and as changing subsets (the host places each item
+    at its filter's position in the launch order by size class), measurement
+    masks (a filter that skips its measurement only predicts), per-filter
+    taus that change every two epochs (their time constants are recomputed
+    and uploaded by the host), and tau = 0 (measurement only; with the mask
+    also off, the filter is left as it was)."""
+    from paper_2412_07240_gb300 import Batch, Filter
+    cfgs, meas, dt, z = _c4(10, 6, seed=11)
+    n = len(cfgs)
+    b = Batch(cfgs, [meas] * n, precision="bf16x6")
+    singles = [Filter(c, precision="bf16x6") for c in cfgs]
+    rng = np.random.default_rng(5)
+    untouched = 0
+    for k in range(6):
+        ids = rng.permutation(n)[: n - k % 3]
+        taus = dt * (1.0 + 0.5 * ((ids + k // 2) % 3))
+        if k == 4:
+            taus[::4] = 0.0
+        dm = ((ids + k) % 4 != 0).astype(np.int32)
+        before = {i: b.pdf(i)[0].copy() for i, t, m in zip(ids, taus, dm) if t == 0.0 and not m}
+        b.step(ids, z[ids, k], taus, do_meas=dm)
+        for i, t, m in zip(ids, taus, dm):
+            f = singles[i]
+            if m and t > 0.0:
+                f.step(meas, z[i, k], t)
+            elif m:
+                f.meas_update(meas, z[i, k])
+            elif t > 0.0:
+                f.time_update(t)
+        for i, P0 in before.items():
+            assert np.array_equal(b.pdf(i)[0], P0), i
+            untouched += 1
+    assert untouched >= 1
+    classes = set()
+    for i, f in enumerate(singles):
+        Pb, cb, Mb = b.pdf(i)
+        Ps, cs, Ms = f.pdf()
+        assert np.array_equal(cb, cs) and np.array_equal(Mb, Ms), i
+        assert rel_l1(Pb, Ps) <= AGREE["bf16x6"], (i, rel_l1(Pb, Ps))
+        m = max(cfgs[i].N)
+        classes.add(64 if m <= 64 else 96 if m <= 96 else 128)
+    assert classes == {64, 96, 128}
 
 
 def test_admission_by_budget():
