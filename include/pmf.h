@@ -364,8 +364,8 @@ void pmf_server_destroy(pmf_server* s);
  * It calls no allocating routine.  Its block partial sums live in one fixed
  * device array of PMF_NOALLOC_MAX_POINTS / 256 * 15 float64 (480 KiB) that
  * every GPU which loads the library holds until the process exits.  The first
- * call on a device looks up that array's device address (once per device, with
- * the device current); make that first call before any stream capture.  All
+ * call on a device looks up that array's device address (a runtime query,
+ * once per device, with the device current); later calls reuse it.  All
  * calls share the array, so calls whose kernels overlap on the GPU (different
  * streams, or other host threads) race: serialise them on one stream.  Each
  * call rewrites every partial it reads, so nothing needs clearing between
