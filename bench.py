@@ -494,6 +494,32 @@ def run_reference(args, ws, rank, pg):
     print(json.dumps(line))
 
 
+# tensor-core products per K step of each format (split planes)
+MMA_PRODUCTS = {"bf16x6": 6, "fp16x3": 3, "bf16x3": 3, "tf32": 1}
+# dense tensor rate of each format relative to bf16 (nominal figures)
+MMA_RATE = {"bf16x6": 1.0, "fp16x3": 1.0, "bf16x3": 1.0, "tf32": 1.1 / 2.25}
+
+
+def executed_mma_flops(cfgs, precision):
+    """Tensor-core flops one epoch of the batch issues.  Every GEMM stage is a
+    128 (lines, unused ones included) x N x K product per split-format
+    product, N = K = the axis size; the GEMM form runs six stages per filter
+    (regrid, Hartley transform and inverse along each axis), the FFT form the
+    two regrid stages only.  The regrid GEMMs are counted for every filter."""
+    from paper_2412_07240_gb300 import _binding, lib_path
+    path = os.path.join(os.path.dirname(lib_path()), "autotune_2d.json")
+    rec = json.load(open(path)) if os.path.exists(path) else {}
+    code = _binding.PREC[precision]
+    env = os.environ.get("PMF_2D_FORM")
+    total = 0.0
+    for c in cfgs:
+        e = rec.get(f"2d:{c.N[0]}x{c.N[1]}:{code}")
+        fft = env == "fft" if env in ("gemm", "fft") else bool(e is not None and e["form"])
+        stages_per_axis = 1 if fft else 3
+        total += MMA_PRODUCTS[precision] * 2.0 * 128 * stages_per_axis * (c.N[0] ** 2 + c.N[1] ** 2)
+    return total
+
+
 def transform_forms(cfgs, precision):
     """Filters per Hartley form (tensor-core GEMM or shared-memory FFT), from the
     2-D autotuner's record beside the library, and the record's entries."""
@@ -570,6 +596,9 @@ def bench_batch(args, ws, rank, pg):
     kernel_ms = float(np.mean(ms))
     peaks, src = _peaks()
     ach = flops / (kernel_ms * 1e-3) / 1e12
+    ex_flops = executed_mma_flops(cfgs, args.precision)
+    ex_ach = ex_flops / (kernel_ms * 1e-3) / 1e12
+    ex_peak = peaks.get("bf16_tflops") * MMA_RATE[args.precision]
     # the epoch's algorithmic intensity (flops / 8 B per point) is below the
     # bf16 ridge, so the HBM roofline binds: float32 weights in and out
     alg_bytes = 8.0 * float(P.sum())
@@ -599,7 +628,11 @@ def bench_batch(args, ws, rank, pg):
                          "peak_source": f"hbm_gbs ({src})",
                          "tensor": {"achieved": ach, "peak": peaks.get("bf16_tflops"), "unit": "TFLOP/s",
                                     "frac": ach / peaks.get("bf16_tflops"), "flops_per_launch": flops,
-                                    "note": "algorithmic transform flops (forward + inverse per axis)"}},
+                                    "note": "algorithmic transform flops (forward + inverse per axis)",
+                                    "executed": {"achieved": ex_ach, "peak": ex_peak, "unit": "TFLOP/s",
+                                                 "frac": ex_ach / ex_peak, "flops_per_launch": ex_flops,
+                                                 "note": "tensor-core flops issued (M = 128 lanes, every "
+                                                         "split product, regrid GEMMs included)"}}},
             "clocks": clk.summary()}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import tempfile

@@ -53,3 +53,18 @@ def test_batch_legs_fit(steps, warmup):
     ids = bench.c4_sample_ids(4096)
     assert len(ids) == 256 and ids[0] == 0 and ids[-1] == 4095 and len(set(ids)) == 256
     assert len(bench.c4_sample_ids(100)) == 100
+
+
+def test_executed_mma_flops_closed_form(monkeypatch):
+    """Issued tensor-core flops of one epoch: 128 lanes x N x K per stage and
+    split product; six stages in the GEMM form, the two regrid stages in the
+    FFT form."""
+    cfgs = [w.FilterConfig(nx=2, N=(32, 64), A=np.zeros((2, 2)), Q=np.eye(2), m0=np.zeros(2), P0=np.eye(2)),
+            w.FilterConfig(nx=2, N=(128, 128), A=np.zeros((2, 2)), Q=np.eye(2), m0=np.zeros(2), P0=np.eye(2))]
+    sq = 32 ** 2 + 64 ** 2 + 2 * 128 ** 2
+    monkeypatch.setenv("PMF_2D_FORM", "gemm")
+    assert bench.executed_mma_flops(cfgs, "bf16x6") == 6 * 2 * 128 * 3 * sq
+    assert bench.executed_mma_flops(cfgs, "fp16x3") == 3 * 2 * 128 * 3 * sq
+    assert bench.executed_mma_flops(cfgs, "tf32") == 1 * 2 * 128 * 3 * sq
+    monkeypatch.setenv("PMF_2D_FORM", "fft")
+    assert bench.executed_mma_flops(cfgs, "fp16x3") == 3 * 2 * 128 * 1 * sq
