@@ -646,6 +646,7 @@ int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_
   TimeConsts* stage = b->h_tc[p];
   int nchanged = 0;
   std::vector<int> changed;
+  std::vector<double> changed_tau;
   // items in launch order (the rank of each filter, fixed at creation): a
   // counting sort over the ranks of the listed ids, each item written once,
   // straight into its position (ids are distinct, so the order is unique)
@@ -669,8 +670,8 @@ int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_
         return rc;
       }
       changed.push_back(id);
+      changed_tau.push_back(tau);
       ++nchanged;
-      b->tau[id] = tau;
     }
   }
   auto cls = [&](const StepItem& x) { return b->cls[x.slot]; };
@@ -681,6 +682,9 @@ int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_
     if (cudaMemcpyAsync(b->d_tc + changed[j], &stage[j], sizeof(TimeConsts), cudaMemcpyHostToDevice,
                         b->stream) != cudaSuccess)
       return PMF_ERR_CUDA;
+  // the resident constants are those of the new taus only once all of them
+  // are computed and on their way (a rejected tau leaves every filter as it was)
+  for (int j = 0; j < nchanged; ++j) b->tau[changed[j]] = changed_tau[j];
   // the item copy and the batch kernel replay as one CUDA graph, captured
   // once per parity buffer and batch size (the copy reads this parity's
   // pinned items when the graph runs)

@@ -140,6 +140,33 @@ def test_step_options_match_single_filters():
     assert classes == {64, 96, 128}
 
 
+def test_rejected_tau_steps_nothing():
+    """A tau beyond the sub-step limit is rejected on the host before anything
+    runs: no filter of the call is stepped, the filters listed before it keep
+    their resident constants, and a retry with valid taus recomputes them (the
+    filters then equal the same filters run alone)."""
+    from paper_2412_07240_gb300 import Batch, Filter, PmfError
+    cfgs, meas, dt, z = _c4(4, 1, seed=12)
+    b = Batch(cfgs, [meas] * 4, precision="bf16x6")
+    singles = [Filter(c, precision="bf16x6") for c in cfgs]
+    ids = np.arange(4)
+    before = [b.pdf(i)[0].copy() for i in range(4)]
+    taus = np.array([2 * dt, 2 * dt, 2 * dt, 1.0])   # 1.0 needs 100 sub-steps of 0.01
+    with pytest.raises(PmfError):
+        b.step(ids, z[:, 0], taus)
+    for i in range(4):
+        assert np.array_equal(b.pdf(i)[0], before[i]), i
+    taus[3] = 2 * dt
+    b.step(ids, z[:, 0], taus)
+    for i, f in enumerate(singles):
+        f.step(meas, z[i, 0], 2 * dt)
+    for i, f in enumerate(singles):
+        Pb, cb, Mb = b.pdf(i)
+        Ps, cs, Ms = f.pdf()
+        assert np.array_equal(cb, cs) and np.array_equal(Mb, Ms), i
+        assert rel_l1(Pb, Ps) <= AGREE["bf16x6"], (i, rel_l1(Pb, Ps))
+
+
 def test_admission_by_budget():
     from paper_2412_07240_gb300 import Batch, PmfError
     from paper_2412_07240_gb300._binding import ERR_ADMISSION
