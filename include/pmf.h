@@ -242,10 +242,10 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
  * host only for filters whose tau changed.  The item upload and the batch
  * kernels run as a CUDA graph, captured on the first epoch of each batch
  * size (and split into size classes) and replayed afterwards.  PMF_ERR_ARG
- * for an id out of range, a negative or non-finite tau, a non-finite z of a
- * measured filter, or a tau needing more than PMF_MAX_SUBSTEPS sub-steps
- * (then no filter of the call is stepped); PMF_ERR_CUDA on a copy or
- * launch error. */
+ * for an id out of range or listed twice, a negative or non-finite tau, a
+ * non-finite z of a measured filter, or a tau needing more than
+ * PMF_MAX_SUBSTEPS sub-steps (then no filter of the call is stepped);
+ * PMF_ERR_CUDA on a copy or launch error. */
 int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_meas,
                    const double* taus, int k);
 

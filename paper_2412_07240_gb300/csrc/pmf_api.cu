@@ -649,10 +649,15 @@ int pmf_batch_step(pmf_batch* b, const int* ids, const double* z, const int* do_
   std::vector<double> changed_tau;
   // items in launch order (the rank of each filter, fixed at creation): a
   // counting sort over the ranks of the listed ids, each item written once,
-  // straight into its position (ids are distinct, so the order is unique)
+  // straight into its position.  Ranks are one per filter, so a count above
+  // one is an id listed twice, which would step one filter in two CTAs.
   std::vector<int>& pos = b->cnt;
   std::fill(pos.begin(), pos.end(), 0);
-  for (int i = 0; i < k; ++i) ++pos[b->rank[ids[i]] + 1];
+  for (int i = 0; i < k; ++i)
+    if (++pos[b->rank[ids[i]] + 1] > 1) {
+      b->err = "an id is listed twice in one step";
+      return PMF_ERR_ARG;
+    }
   for (int r = 0; r < b->count; ++r) pos[r + 1] += pos[r];
   for (int i = 0; i < k; ++i) {
     const int id = ids[i];

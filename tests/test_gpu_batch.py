@@ -9,7 +9,9 @@
   the oracle;
 * per-item step options (shuffled subsets, measurement masks, changing taus,
   tau = 0) equal the same filters run alone;
-* stepping a subset leaves the others untouched; admission by a memory budget.
+* stepping a subset leaves the others untouched; a step rejected for a tau
+  beyond the sub-step limit or an id listed twice steps nothing; admission by
+  a memory budget.
 """
 import numpy as np
 import pytest
@@ -165,6 +167,21 @@ def test_rejected_tau_steps_nothing():
         Ps, cs, Ms = f.pdf()
         assert np.array_equal(cb, cs) and np.array_equal(Mb, Ms), i
         assert rel_l1(Pb, Ps) <= AGREE["bf16x6"], (i, rel_l1(Pb, Ps))
+
+
+def test_repeated_id_rejected():
+    """An id listed twice in one step is an argument error and steps nothing."""
+    from paper_2412_07240_gb300 import Batch, PmfError
+    cfgs, meas, dt, z = _c4(3, 1, seed=13)
+    b = Batch(cfgs, [meas] * 3, precision="bf16x6")
+    before = [b.pdf(i)[0].copy() for i in range(3)]
+    with pytest.raises(PmfError):
+        b.step([0, 2, 0], z[[0, 2, 0], 0], dt)
+    for i in range(3):
+        assert np.array_equal(b.pdf(i)[0], before[i]), i
+    b.step([0, 2], z[[0, 2], 0], dt)
+    for i in range(3):
+        assert np.array_equal(b.pdf(i)[0], before[i]) == (i == 1), i
 
 
 def test_admission_by_budget():
