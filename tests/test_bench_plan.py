@@ -2,8 +2,9 @@
 
 Every leg of a bench run (warm-up and timed steps, the end-to-end loop, the
 float64 comparator, the oracle parity sample) indexes into a seeded scenario;
-these tests build the scenarios the way bench.py does, for the driver's
-arguments and for edge cases, and check that each leg stays inside.
+these tests build the scenarios the way bench.py does, for the usual
+arguments (--steps 20 --warmup 5) and for edge cases, and check that each
+leg stays inside.
 """
 import numpy as np
 import pytest
