@@ -67,6 +67,36 @@ def test_2d_linear_exact_time_matches_kalman():
     assert errs.max() < 1e-7, errs.max(axis=0)
 
 
+def _general_linear_2d(epochs=6, seed=21):
+    """The 2-D linear problem with a full, non-symmetric H and a correlated R,
+    so that every entry of H and of R^-1 enters the likelihood."""
+    import dataclasses
+    sc = w.small_2d_scenario(N=(128, 128), kind="linear", epochs=epochs)
+    sc.cfg = dataclasses.replace(sc.cfg, realign_rho=10.0)
+    sc.meas = MeasModel("linear", R=np.array([[0.02, 0.006], [0.006, 0.015]]),
+                        H=np.array([[1.0, 0.4], [-0.3, 0.8]]))
+    sc.truth, sc.z = simulate(sc.cfg, sc.meas, sc.dt, epochs, seed=seed)
+    return sc
+
+
+def test_2d_linear_general_h_and_correlated_r_match_kalman():
+    sc = _general_linear_2d()
+    errs, realigns = _kalman_errors(sc, "exact")
+    assert realigns == 0
+    assert errs.max() < 1e-7, errs.max(axis=0)
+
+
+def test_mutation_transposed_measurement_matrix(monkeypatch):
+    h_right = model.h
+
+    def h_transposed(kind, x, H=None, params=None):
+        return x @ np.asarray(H) if kind == "linear" else h_right(kind, x, H, params)
+
+    monkeypatch.setattr(model, "h", h_transposed)
+    errs, _ = _kalman_errors(_general_linear_2d(epochs=3), "exact", epochs=3)
+    assert errs.max() > 1e-3, errs.max()
+
+
 def _turn_4d(N, epochs, R=25.0):
     """Coordinated turn with position measurements (linear h), no re-alignment."""
     a = np.deg2rad(30.0)
