@@ -67,7 +67,11 @@ int make_time_consts(pmf_ctx* ctx, double tau, TimeConsts* tc) {
 int build_meas(pmf_ctx* ctx, const pmf_meas* m, MeasParams* mp) {
   std::string why;
   const int rc = meas_params(ctx->cfg.nx, m, mp, &why);
-  return rc ? fail(ctx, rc, why) : PMF_OK;
+  if (rc) return fail(ctx, rc, why);
+  // the 2-D tensor-core kernels form the likelihood of at most two components
+  if (ctx->path == 1 && mp->nz > 2)
+    return fail(ctx, PMF_ERR_UNSUPPORTED, "the 2-D tensor-core path takes at most two measurement components");
+  return PMF_OK;
 }
 
 
@@ -495,6 +499,7 @@ int pmf_batch_create(pmf_batch** out, const pmf_config* cfgs, const pmf_meas* mo
     if (rc) return rc;
     rc = meas_params(2, &models[i], &mps[i], &why);
     if (rc) return rc;
+    if (mps[i].nz > 2) return PMF_ERR_UNSUPPORTED;   // two likelihood components at most
     forms[i] = tc2_form(&cfgs[i], (cudaStream_t)cuda_stream);
     const int cls = tc_class_form(cfgs[i].N[0], cfgs[i].N[1], forms[i], prec);
     for (int a = 0; a < 2; ++a) {

@@ -135,3 +135,20 @@ def test_bf16x6_scope_without_gpu():
     c.transform = 0
     c.precision = 6
     assert lib.pmf_create(ctypes.byref(h), ctypes.byref(c), None) == _binding.ERR_ARG
+
+
+def test_batch_refuses_three_component_linear_without_gpu():
+    """The 2-D tensor-core kernels form the likelihood of at most two
+    measurement components: a batch whose 2-D filter has a three-component
+    linear model is refused (PMF_ERR_UNSUPPORTED) before any device work."""
+    import numpy as np
+    from paper_2412_07240_gb300 import _binding
+    from workloads import FilterConfig, MeasModel
+    lib = _binding.load()
+    cfg = FilterConfig(nx=2, N=(32, 32), A=np.zeros((2, 2)), Q=np.eye(2), m0=np.zeros(2), P0=np.eye(2))
+    three = MeasModel("linear", R=np.eye(3), H=np.array([[1.0, 0.0], [0.0, 1.0], [1.0, 1.0]]))
+    carr = (_binding.PmfConfig * 1)(_binding.make_config(cfg, "bf16x6", "euler", "auto"))
+    marr = (_binding.PmfMeas * 1)(_binding.make_meas(three, np.zeros(3), 2))
+    h = ctypes.c_void_p()
+    assert lib.pmf_batch_create(ctypes.byref(h), carr, marr, 1, 0, None) == _binding.ERR_UNSUPPORTED
+    assert not h.value
