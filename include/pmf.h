@@ -156,7 +156,9 @@ typedef struct pmf_meas {
   int kind;                     /* PMF_MEAS_* */
   int nz;                       /* measurement dimension (1..PMF_MAX_NZ; at most 2
                                    for 2-D filters on the tensor-core path, in
-                                   batches and in the server: PMF_ERR_UNSUPPORTED) */
+                                   batches and in the server: PMF_ERR_UNSUPPORTED;
+                                   3-D tensor-core filters take LINEAR and
+                                   BEARING_LINEAR3, not RANGE) */
   double z[PMF_MAX_NZ];         /* measurement */
   double R[PMF_MAX_NZ * PMF_MAX_NZ];   /* noise covariance, symmetric PD, nz x nz packed */
   double H[PMF_MAX_NZ * PMF_MAX_NX];   /* LINEAR only: nz x nx row-major packed */

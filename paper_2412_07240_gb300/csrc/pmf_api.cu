@@ -68,9 +68,12 @@ int build_meas(pmf_ctx* ctx, const pmf_meas* m, MeasParams* mp) {
   std::string why;
   const int rc = meas_params(ctx->cfg.nx, m, mp, &why);
   if (rc) return fail(ctx, rc, why);
-  // the 2-D tensor-core kernels form the likelihood of at most two components
+  // the 2-D tensor-core kernels form the likelihood of at most two components;
+  // the 3-D pipelines form linear and bearing + linear measurements only
   if (ctx->path == 1 && mp->nz > 2)
     return fail(ctx, PMF_ERR_UNSUPPORTED, "the 2-D tensor-core path takes at most two measurement components");
+  if (ctx->path == 2 && mp->kind == PMF_MEAS_RANGE)
+    return fail(ctx, PMF_ERR_UNSUPPORTED, "the 3-D tensor-core pipelines take linear and bearing + linear measurements");
   return PMF_OK;
 }
 

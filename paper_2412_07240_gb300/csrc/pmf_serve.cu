@@ -467,6 +467,8 @@ int pmf_server_admit(pmf_server* s, const pmf_config* cfg, const pmf_meas* model
   if (rc) return sfail(s, rc, why);
   if (n == 2 && mp.nz > 2)   // the batched 2-D kernels form at most two likelihood components
     return sfail(s, PMF_ERR_UNSUPPORTED, "2-D filters take at most two measurement components");
+  if (n == 3 && mp.kind == PMF_MEAS_RANGE)   // the 3-D pipelines: linear and bearing + linear
+    return sfail(s, PMF_ERR_UNSUPPORTED, "3-D filters take linear and bearing + linear measurements");
   if (s->free_ids.empty()) return sfail(s, PMF_ERR_ADMISSION, "no free filter id");
   long long P = 1;
   for (int a = 0; a < n; ++a) P *= cfg->N[a];
